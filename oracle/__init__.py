@@ -1,0 +1,251 @@
+"""Plain FP64 CPU oracle of the LBRS time step.
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` use it to check and to time against.  The
+product path (``paper_1504_07034_gb300``) never imports it, and the two share
+no code.  The arithmetic lives in ``lbrs_oracle.c`` (plain C, float64, no FMA
+contraction, OpenMP over rows); this module only compiles it and marshals
+numpy arrays through ctypes.
+
+Array layout: distributions ``fs[q, k, j, i]`` (2-D) or ``fs[q, k, i]`` (1-D),
+conserved fields ``U[k, j, i]`` / ``U[k, i]``.  Lattice velocity order
+follows the paper: D1Q2 (-lambda, +lambda); D2Q4 f1..f4 with signs
+(-,-), (+,-), (+,+), (-,+).
+
+Every function is pinned by ``tests/test_oracle_pins.py`` against what the
+paper and the mathematics fix (moment identities, the exact Lax-Friedrichs
+form at omega = 1, uniform-flow and contact invariants, conservation,
+mirror symmetries, the exact Riemann solution, the Chapman-Enskog diffusion
+rate, the wall relations, brute force on tiny grids).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import time
+from pathlib import Path
+
+import numpy as np
+
+HERE = Path(__file__).resolve().parent
+SRC = HERE / "lbrs_oracle.c"
+LIB = HERE / "_build" / "liblbrs_oracle.so"
+
+BC_KINDS = {"periodic": 0, "transmissive": 1, "dirichlet": 2, "wall": 3}
+D1Q2, D2Q4 = 2, 4
+
+
+def build(force: bool = False) -> Path:
+    """Compile the oracle with gcc (no FMA contraction; OpenMP).
+
+    The environment variable LBRS_ORACLE_LIB points the module at another
+    compiled copy instead (the mutation tests use it to load deliberately
+    broken oracles and check that the pins catch them).
+    """
+    alt = os.environ.get("LBRS_ORACLE_LIB")
+    if alt:
+        return Path(alt)
+    if LIB.exists() and not force and LIB.stat().st_mtime >= SRC.stat().st_mtime:
+        return LIB
+    LIB.parent.mkdir(parents=True, exist_ok=True)
+    tmp = LIB.with_suffix(f".{os.getpid()}.tmp")
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-shared", "-fPIC",
+           str(SRC), "-o", str(tmp), "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [
+        ("lattice", ctypes.c_int32),
+        ("nthreads", ctypes.c_int32),
+        ("nx", ctypes.c_int64),
+        ("ny", ctypes.c_int64),
+        ("gamma", ctypes.c_double),
+        ("lam", ctypes.c_double),
+        ("omega", ctypes.c_double),
+        ("bc_kind", ctypes.c_int32 * 4),
+        ("bc_prim", (ctypes.c_double * 4) * 4),
+    ]
+
+
+class _Check(ctypes.Structure):
+    _fields_ = [
+        ("first_bad_step", ctypes.c_int64),
+        ("n_nonphysical", ctypes.c_int64),
+        ("n_subchar", ctypes.c_int64),
+        ("max_lambda_local", ctypes.c_double),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(str(build()))
+        P = ctypes.POINTER(_Params)
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.orc_prim_to_cons.argtypes = [P, dp, dp]
+        L.orc_cons_to_prim.argtypes = [P, dp, dp]
+        L.orc_feq.argtypes = [P, ctypes.c_int64, dp, dp]
+        L.orc_init.argtypes = [P, dp, dp]
+        L.orc_moments.argtypes = [P, dp, dp]
+        L.orc_validate.argtypes = [P]
+        L.orc_validate.restype = ctypes.c_int
+        L.orc_stream.argtypes = [P, dp, dp]
+        L.orc_stream.restype = ctypes.c_int
+        L.orc_collide.argtypes = [P, dp, dp, dp, ctypes.POINTER(_Check), ctypes.c_int64]
+        L.orc_run.argtypes = [P, dp, dp, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(_Check)]
+        L.orc_run.restype = ctypes.c_int
+        L.orc_totals.argtypes = [P, dp, ctypes.c_double, dp]
+        L.orc_max_threads.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def max_threads() -> int:
+    return int(lib().orc_max_threads())
+
+
+class Oracle:
+    """One LBRS problem: lattice, grid, gamma, lambda, omega, boundary conditions."""
+
+    def __init__(self, lattice: int, nx: int, ny: int = 1, *, gamma: float = 1.4, lam: float,
+                 omega: float = 1.0, bc=None, nthreads: int = 0):
+        self.lattice = lattice
+        self.Q, self.K = (4, 4) if lattice == D2Q4 else (2, 3)
+        self.nx, self.ny = int(nx), int(ny)
+        sides = 4 if lattice == D2Q4 else 2
+        bc = list(bc) if bc is not None else [("periodic", None)] * sides
+        if len(bc) != sides:
+            raise ValueError(f"need {sides} boundary conditions")
+        p = _Params()
+        p.lattice, p.nthreads = lattice, nthreads
+        p.nx, p.ny = self.nx, self.ny
+        p.gamma, p.lam, p.omega = gamma, lam, omega
+        for s, (kind, state) in enumerate(bc):
+            p.bc_kind[s] = BC_KINDS[kind]
+            if state is not None:
+                for k, val in enumerate(state):
+                    p.bc_prim[s][k] = float(val)
+        self.p = p
+        err = lib().orc_validate(ctypes.byref(p))
+        if err:
+            raise ValueError(f"invalid oracle parameters (code {err})")
+
+    @classmethod
+    def from_workload(cls, wl, nthreads: int = 0, omega=None):
+        if hasattr(wl, "ny"):
+            return cls(D2Q4, wl.nx, wl.ny, gamma=wl.gamma, lam=wl.lam,
+                       omega=wl.omega if omega is None else omega, bc=wl.bc, nthreads=nthreads)
+        return cls(D1Q2, wl.nx, 1, gamma=wl.gamma, lam=wl.lam,
+                   omega=wl.omega if omega is None else omega, bc=wl.bc, nthreads=nthreads)
+
+    # shapes -------------------------------------------------------------
+    @property
+    def grid(self):
+        return (self.ny, self.nx) if self.lattice == D2Q4 else (self.nx,)
+
+    def _fields(self, a) -> np.ndarray:
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        if a.shape != (self.K,) + self.grid:
+            raise ValueError(f"expected shape {(self.K,) + self.grid}, got {a.shape}")
+        return a
+
+    def _dists(self, a) -> np.ndarray:
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        if a.shape != (self.Q, self.K) + self.grid:
+            raise ValueError(f"expected shape {(self.Q, self.K) + self.grid}, got {a.shape}")
+        return a
+
+    # operations ----------------------------------------------------------
+    def prim_to_cons(self, W) -> np.ndarray:
+        W = self._fields(W)
+        U = np.empty_like(W)
+        lib().orc_prim_to_cons(ctypes.byref(self.p), _ptr(W), _ptr(U))
+        return U
+
+    def cons_to_prim(self, U) -> np.ndarray:
+        U = self._fields(U)
+        W = np.empty_like(U)
+        lib().orc_cons_to_prim(ctypes.byref(self.p), _ptr(U), _ptr(W))
+        return W
+
+    def feq(self, U) -> np.ndarray:
+        """Equilibria of arbitrary states U[K, ...] -> feq[Q, K, ...]."""
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        shape = U.shape[1:]
+        n = int(np.prod(shape)) if shape else 1
+        out = np.empty((self.Q, self.K) + shape)
+        lib().orc_feq(ctypes.byref(self.p), n, _ptr(U), _ptr(out))
+        return out
+
+    def init(self, U0) -> np.ndarray:
+        U0 = self._fields(U0)
+        fs = np.empty((self.Q, self.K) + self.grid)
+        lib().orc_init(ctypes.byref(self.p), _ptr(U0), _ptr(fs))
+        return fs
+
+    def stream(self, fs) -> np.ndarray:
+        """Streaming plus boundary conditions (the streamed f before collision)."""
+        fs = self._dists(fs)
+        f = np.empty_like(fs)
+        err = lib().orc_stream(ctypes.byref(self.p), _ptr(fs), _ptr(f))
+        if err:
+            raise ValueError(f"oracle stream error {err}")
+        return f
+
+    def collide(self, f, step: int = 0):
+        """Returns (fs, U, check) for a streamed f."""
+        f = self._dists(f)
+        fs = np.empty_like(f)
+        U = np.empty((self.K,) + self.grid)
+        chk = _Check(-1, 0, 0, 0.0)
+        lib().orc_collide(ctypes.byref(self.p), _ptr(f), _ptr(fs), _ptr(U), ctypes.byref(chk), step)
+        return fs, U, _check_dict(chk)
+
+    def run(self, fs, nsteps: int, step0: int = 0):
+        """Advance a copy of fs by nsteps steps. Returns (fs, check)."""
+        fs = self._dists(fs).copy()
+        work = np.empty_like(fs)
+        chk = _Check(-1, 0, 0, 0.0)
+        err = lib().orc_run(ctypes.byref(self.p), _ptr(fs), _ptr(work), int(nsteps), int(step0),
+                            ctypes.byref(chk))
+        if err:
+            raise ValueError(f"oracle run error {err}")
+        return fs, _check_dict(chk)
+
+    def moments(self, fs) -> np.ndarray:
+        fs = self._dists(fs)
+        U = np.empty((self.K,) + self.grid)
+        lib().orc_moments(ctypes.byref(self.p), _ptr(fs), _ptr(U))
+        return U
+
+    def totals(self, fs, cell_volume: float) -> np.ndarray:
+        fs = self._dists(fs)
+        out = np.empty(self.K)
+        lib().orc_totals(ctypes.byref(self.p), _ptr(fs), float(cell_volume), _ptr(out))
+        return out
+
+    def timed_run(self, fs, nsteps: int):
+        """Advance fs by nsteps and return (fs, seconds) measured around the step loop only."""
+        fs = self._dists(fs).copy()
+        work = np.empty_like(fs)
+        chk = _Check(-1, 0, 0, 0.0)
+        t0 = time.perf_counter()
+        lib().orc_run(ctypes.byref(self.p), _ptr(fs), _ptr(work), int(nsteps), 0, ctypes.byref(chk))
+        return fs, time.perf_counter() - t0
+
+
+def _check_dict(c: _Check) -> dict:
+    return {"first_bad_step": int(c.first_bad_step), "n_nonphysical": int(c.n_nonphysical),
+            "n_subchar": int(c.n_subchar), "max_lambda_local": float(c.max_lambda_local)}

@@ -1,0 +1,406 @@
+/*
+ * Plain FP64 CPU oracle of the Lattice Boltzmann Relaxation Scheme (LBRS).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, literal reference that
+ * the CUDA path is checked against.  Only the tests, the smoke check and the
+ * CPU-baseline leg of the benchmark may load it; the product path never
+ * does, and it shares no code with the CUDA library.
+ *
+ * It follows the paper (Raghurama Rao, Deshmukh, Kotnala, "A Lattice
+ * Boltzmann Relaxation Scheme for Inviscid Compressible Flows") step by step,
+ * in the paper's order, on separate arrays:
+ *
+ *   state      fs[q][k][cell] : post-collision distributions at time n
+ *   initialise fs = f^eq(U0)                                 (Section II.A)
+ *   one step   1. stream:   f_q(x) = fs_q(x - c_q dt)       (discrete LBRS update)
+ *              2. boundary: ghosts / wall relations          (Section II.E)
+ *              3. moments:  U_k = sum_q f_{q,k}               (moment relations)
+ *              4. fluxes:   Euler F(U), G(U), ideal gas       (Sections II.C, II.D)
+ *              5. equilibria f^eq from U and the fluxes        (Sections II.C, II.D)
+ *              6. relax:    fs = (1 - w) f + w f^eq           (discrete LBRS update)
+ *
+ * Lattices (q is 0-based; the paper numbers them from 1):
+ *   D1Q2 : c = (-1, +1) lattice units, K = 3 fields (rho, rho u, rho E).
+ *          f^eq_{1,2} = U/2 -/+ G/(2 lambda)                  (Section II.C)
+ *   D2Q4 : c = (-1,-1), (+1,-1), (+1,+1), (-1,+1), K = 4 fields
+ *          (rho, rho u, rho v, rho E);
+ *          f^eq_q = U/4 + sx_q F/(4 lambda) + sy_q G/(4 lambda) (Section II.D)
+ *
+ * Readings where the paper is silent (stated once here):
+ *   - lambda is one global constant and dt = dx / lambda (exact hopping).
+ *   - transmissive boundary: the pull source index is clamped into the domain;
+ *     Dirichlet boundary: the ghost holds f^eq of the boundary state with the
+ *     run's lambda; periodic: the source index wraps.
+ *   - the free-slip wall (Section II.E) is applied on the wall row itself
+ *     after streaming: at a top wall the unknown downward populations are
+ *     f1 = f4, f2 = f3 (negated for the rho v field); a bottom wall mirrors
+ *     it: f4 = f1, f3 = f2 (negated for rho v).  Walls exist on the y sides.
+ *   - priority at a corner: a wall on the y side first, then a Dirichlet
+ *     ghost on the x side, then a Dirichlet ghost on the y side, otherwise the
+ *     source index is wrapped/clamped coordinate by coordinate.
+ *   - the pressure is p = (gamma - 1)(rho E - |rho u|^2 / (2 rho)), written as
+ *     (gamma - 1)(rho E - (rho u * u + rho v * v) / 2) with u = rho u / rho.
+ *
+ * Build (the flags matter: no FMA contraction, so that rounding is that of
+ * the plain expressions below):
+ *   gcc -O2 -std=c11 -ffp-contract=off -fopenmp -shared -fPIC lbrs_oracle.c -o liblbrs_oracle.so -lm
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <omp.h>
+
+enum { ORC_PERIODIC = 0, ORC_TRANSMISSIVE = 1, ORC_DIRICHLET = 2, ORC_WALL = 3 };
+enum { ORC_D1Q2 = 2, ORC_D2Q4 = 4 };
+
+typedef struct {
+    int32_t lattice;      /* ORC_D1Q2 or ORC_D2Q4 */
+    int32_t nthreads;     /* OpenMP threads, 0 = library default */
+    int64_t nx, ny;       /* ny = 1 for D1Q2 */
+    double gamma, lambda, omega;
+    int32_t bc_kind[4];   /* x-lo, x-hi, y-lo, y-hi */
+    double bc_prim[4][4]; /* Dirichlet primitive state per side: (rho,u,p) in 1-D, (rho,u,v,p) in 2-D */
+} orc_params;
+
+typedef struct {
+    int64_t first_bad_step;   /* first step with rho <= 0, p <= 0, NaN or lambda_loc > lambda; -1 if none */
+    int64_t n_nonphysical;    /* cells with rho <= 0, p <= 0 or a non-finite value (last bad step) */
+    int64_t n_subchar;        /* cells with lambda_loc > lambda (last bad step) */
+    double max_lambda_local;  /* max over all checked steps and cells */
+} orc_check;
+
+/* velocity signs, q = 0..3 <-> the paper's f1..f4 */
+static const int SX2[4] = {-1, +1, +1, -1};
+static const int SY2[4] = {-1, -1, +1, +1};
+static const int SX1[2] = {-1, +1};
+
+static int threads_of(const orc_params* P) { return P->nthreads > 0 ? P->nthreads : omp_get_max_threads(); }
+static int nq(const orc_params* P) { return P->lattice == ORC_D2Q4 ? 4 : 2; }
+static int nk(const orc_params* P) { return P->lattice == ORC_D2Q4 ? 4 : 3; }
+
+/* ---------------------------------------------------------------- state */
+
+/* Conserved variables from primitive ones, E = p/(rho (gamma-1)) + |u|^2/2 (Section II.C). */
+static void prim_to_cons_cell(const orc_params* P, const double* w, double* U)
+{
+    double g = P->gamma;
+    if (P->lattice == ORC_D2Q4) {
+        double rho = w[0], u = w[1], v = w[2], p = w[3];
+        U[0] = rho;
+        U[1] = rho * u;
+        U[2] = rho * v;
+        U[3] = p / (g - 1.0) + 0.5 * rho * (u * u + v * v);
+    } else {
+        double rho = w[0], u = w[1], p = w[2];
+        U[0] = rho;
+        U[1] = rho * u;
+        U[2] = p / (g - 1.0) + 0.5 * rho * (u * u);
+    }
+}
+
+/* Ideal-gas pressure from conserved variables (inverse of the E definition). */
+static double pressure(const orc_params* P, const double* U)
+{
+    double g = P->gamma;
+    if (P->lattice == ORC_D2Q4) {
+        double u = U[1] / U[0], v = U[2] / U[0];
+        return (g - 1.0) * (U[3] - 0.5 * (U[1] * u + U[2] * v));
+    }
+    double u = U[1] / U[0];
+    return (g - 1.0) * (U[2] - 0.5 * (U[1] * u));
+}
+
+/* Equilibria of one cell, feq[q*K + k] (Sections II.C and II.D). */
+static void feq_cell(const orc_params* P, const double* U, double* feq)
+{
+    double g = P->gamma;
+    if (P->lattice == ORC_D2Q4) {
+        /* 2-D Euler fluxes: F = (rho u, rho u^2 + p, rho u v, u(rho E + p)),
+         *                   G = (rho v, rho v u, rho v^2 + p, v(rho E + p)). */
+        double rho = U[0], mx = U[1], my = U[2], en = U[3];
+        double u = mx / rho, v = my / rho;
+        double p = (g - 1.0) * (en - 0.5 * (mx * u + my * v));
+        double F[4], G[4];
+        F[0] = mx;         G[0] = my;
+        F[1] = mx * u + p; G[1] = my * u;
+        F[2] = mx * v;     G[2] = my * v + p;
+        F[3] = u * (en + p); G[3] = v * (en + p);
+        double c = 1.0 / (4.0 * P->lambda);
+        for (int q = 0; q < 4; ++q)
+            for (int k = 0; k < 4; ++k) {
+                double a = 0.25 * U[k];
+                double b = c * F[k];
+                double d = c * G[k];
+                /* U/4 + sx F/(4 lambda) + sy G/(4 lambda), summed left to right */
+                double t = SX2[q] < 0 ? a - b : a + b;
+                feq[q * 4 + k] = SY2[q] < 0 ? t - d : t + d;
+            }
+    } else {
+        /* 1-D Euler flux G = (rho u, p + rho u^2, p u + rho u E) */
+        double rho = U[0], m = U[1], en = U[2];
+        double u = m / rho;
+        double p = (g - 1.0) * (en - 0.5 * (m * u));
+        double G[3] = {m, m * u + p, u * (en + p)};
+        double c = 1.0 / (2.0 * P->lambda);
+        for (int k = 0; k < 3; ++k) {
+            double a = 0.5 * U[k];
+            double b = c * G[k];
+            feq[0 * 3 + k] = a - b;   /* velocity -lambda */
+            feq[1 * 3 + k] = a + b;   /* velocity +lambda */
+        }
+    }
+}
+
+/* Local wave-speed bound: |u| + a in 1-D (Section II.C), max(|u+v|,|u-v|) + sqrt(2) a in 2-D (Section II.D). */
+static double lambda_local(const orc_params* P, const double* U, double p)
+{
+    double a = sqrt(P->gamma * p / U[0]);
+    if (P->lattice == ORC_D2Q4) {
+        double u = U[1] / U[0], v = U[2] / U[0];
+        double s1 = fabs(u + v), s2 = fabs(u - v);
+        return (s1 > s2 ? s1 : s2) + sqrt(2.0) * a;
+    }
+    return fabs(U[1] / U[0]) + a;
+}
+
+/* ---------------------------------------------------------------- exported */
+
+void orc_prim_to_cons(const orc_params* P, const double* W, double* U)
+{
+    int64_t N = P->nx * P->ny;
+    int K = nk(P);
+    for (int64_t c = 0; c < N; ++c) {
+        double w[4], u[4];
+        for (int k = 0; k < K; ++k) w[k] = W[k * N + c];
+        prim_to_cons_cell(P, w, u);
+        for (int k = 0; k < K; ++k) U[k * N + c] = u[k];
+    }
+}
+
+/* Primitive variables (rho, u, [v,] p) from conserved ones. */
+void orc_cons_to_prim(const orc_params* P, const double* U, double* W)
+{
+    int64_t N = P->nx * P->ny;
+    int K = nk(P);
+    for (int64_t c = 0; c < N; ++c) {
+        double u[4];
+        for (int k = 0; k < K; ++k) u[k] = U[k * N + c];
+        W[0 * N + c] = u[0];
+        W[1 * N + c] = u[1] / u[0];
+        if (K == 4) W[2 * N + c] = u[2] / u[0];
+        W[(K - 1) * N + c] = pressure(P, u);
+    }
+}
+
+/* f^eq of a batch of states: U[k*n + c] -> feq[(q*K + k)*n + c]. */
+void orc_feq(const orc_params* P, int64_t n, const double* U, double* feq)
+{
+    int Q = nq(P), K = nk(P);
+    for (int64_t c = 0; c < n; ++c) {
+        double u[4], f[16];
+        for (int k = 0; k < K; ++k) u[k] = U[k * n + c];
+        feq_cell(P, u, f);
+        for (int q = 0; q < Q; ++q)
+            for (int k = 0; k < K; ++k) feq[(q * K + k) * n + c] = f[q * K + k];
+    }
+}
+
+/* Initialisation f_i = f^eq_i(U0) (Section II.A). */
+void orc_init(const orc_params* P, const double* U0, double* fs)
+{
+    orc_feq(P, P->nx * P->ny, U0, fs);
+}
+
+/* Moments U_k = sum_q fs_{q,k}, summed in q order (moment relations, Section II). */
+void orc_moments(const orc_params* P, const double* fs, double* U)
+{
+    int64_t N = P->nx * P->ny;
+    int Q = nq(P), K = nk(P);
+    for (int k = 0; k < K; ++k)
+        for (int64_t c = 0; c < N; ++c) {
+            double s = fs[(0 * K + k) * N + c];
+            for (int q = 1; q < Q; ++q) s += fs[(q * K + k) * N + c];
+            U[k * N + c] = s;
+        }
+}
+
+int orc_validate(const orc_params* P)
+{
+    if (P->lattice != ORC_D1Q2 && P->lattice != ORC_D2Q4) return 1;
+    if (P->nx < 1 || P->ny < 1) return 2;
+    if (P->lattice == ORC_D1Q2 && P->ny != 1) return 3;
+    if (!(P->lambda > 0.0) || !(P->omega > 0.0 && P->omega < 2.0) || !(P->gamma > 1.0)) return 4;
+    int sides = P->lattice == ORC_D2Q4 ? 4 : 2;
+    for (int s = 0; s < sides; ++s) {
+        int kind = P->bc_kind[s];
+        if (kind < ORC_PERIODIC || kind > ORC_WALL) return 5;
+        if (kind == ORC_WALL && s < 2) return 6;              /* walls on the y sides only */
+        if (kind == ORC_PERIODIC && P->bc_kind[s ^ 1] != ORC_PERIODIC) return 7;
+    }
+    if (P->lattice == ORC_D2Q4 && (P->bc_kind[2] == ORC_WALL || P->bc_kind[3] == ORC_WALL) && P->ny < 2)
+        return 8;
+    return 0;
+}
+
+/* Ghost distributions of each Dirichlet side: f^eq of the boundary state. */
+static void ghost_tables(const orc_params* P, double ghost[4][16])
+{
+    int sides = P->lattice == ORC_D2Q4 ? 4 : 2;
+    for (int s = 0; s < sides; ++s) {
+        double U[4];
+        prim_to_cons_cell(P, P->bc_prim[s], U);
+        feq_cell(P, U, ghost[s]);
+    }
+}
+
+/*
+ * Streaming plus boundary conditions: f_q(x) = fs_q(x - c_q), then the
+ * free-slip wall relations on wall rows (Section II.E).  fs and f are
+ * [Q][K][ny][nx].  Returns 0, or a nonzero code if the parameters are invalid.
+ */
+int orc_stream(const orc_params* P, const double* fs, double* f)
+{
+    int err = orc_validate(P);
+    if (err) return err;
+    const int64_t nx = P->nx, ny = P->ny, N = nx * ny;
+    const int Q = nq(P), K = nk(P);
+    double ghost[4][16];
+    ghost_tables(P, ghost);
+    const int two_d = P->lattice == ORC_D2Q4;
+
+#pragma omp parallel for schedule(static) num_threads(threads_of(P))
+    for (int64_t j = 0; j < ny; ++j) {
+        for (int64_t i = 0; i < nx; ++i) {
+            const int64_t c = j * nx + i;
+            int wall_pop[4] = {0, 0, 0, 0};
+            for (int q = 0; q < Q; ++q) {
+                int sx = two_d ? SX2[q] : SX1[q];
+                int sy = two_d ? SY2[q] : 0;
+                int64_t si = i - sx, sj = j - sy;
+                int side_y = sj < 0 ? 2 : (sj >= ny ? 3 : -1);
+                int side_x = si < 0 ? 0 : (si >= nx ? 1 : -1);
+                const double* g = NULL;
+                if (side_y >= 0 && P->bc_kind[side_y] == ORC_WALL) {
+                    wall_pop[q] = 1;          /* set below from the wall relation */
+                    continue;
+                }
+                if (side_x >= 0) {
+                    int kind = P->bc_kind[side_x];
+                    if (kind == ORC_DIRICHLET) g = ghost[side_x];
+                    else if (kind == ORC_PERIODIC) si = (si + nx) % nx;
+                    else si = si < 0 ? 0 : nx - 1;              /* transmissive */
+                }
+                if (!g && side_y >= 0) {
+                    int kind = P->bc_kind[side_y];
+                    if (kind == ORC_DIRICHLET) g = ghost[side_y];
+                    else if (kind == ORC_PERIODIC) sj = (sj + ny) % ny;
+                    else sj = sj < 0 ? 0 : ny - 1;              /* transmissive */
+                }
+                for (int k = 0; k < K; ++k)
+                    f[(q * K + k) * N + c] = g ? g[q * K + k] : fs[(q * K + k) * N + sj * nx + si];
+            }
+            /* Free-slip wall (Section II.E).  Top wall: the incoming downward
+             * populations f1, f2 (q = 0, 1) take f1 = f4, f2 = f3, negated for
+             * the rho v field.  Bottom wall: f4 = f1, f3 = f2, negated for rho v. */
+            if (wall_pop[0] || wall_pop[1]) {
+                for (int k = 0; k < K; ++k) {
+                    double sgn = (k == 2) ? -1.0 : 1.0;
+                    f[(0 * K + k) * N + c] = sgn * f[(3 * K + k) * N + c];
+                    f[(1 * K + k) * N + c] = sgn * f[(2 * K + k) * N + c];
+                }
+            }
+            if (wall_pop[2] || wall_pop[3]) {
+                for (int k = 0; k < K; ++k) {
+                    double sgn = (k == 2) ? -1.0 : 1.0;
+                    f[(3 * K + k) * N + c] = sgn * f[(0 * K + k) * N + c];
+                    f[(2 * K + k) * N + c] = sgn * f[(1 * K + k) * N + c];
+                }
+            }
+        }
+    }
+    return 0;
+}
+
+/*
+ * Collision: moments, fluxes, equilibria, relaxation fs = (1-w) f + w f^eq.
+ * Writes the moments of the streamed f to U (nullable).  Updates chk with the
+ * physical-admissibility and sub-characteristic checks (nullable), tagging a
+ * violation with `step`.
+ */
+void orc_collide(const orc_params* P, const double* f, double* fs, double* U, orc_check* chk, int64_t step)
+{
+    const int64_t N = P->nx * P->ny;
+    const int Q = nq(P), K = nk(P);
+    const double om = P->omega, om1 = 1.0 - P->omega;
+    int64_t bad = 0, sub = 0;
+    double lmax = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : bad, sub) reduction(max : lmax) \
+    num_threads(threads_of(P))
+    for (int64_t c = 0; c < N; ++c) {
+        double u[4], feq[16];
+        for (int k = 0; k < K; ++k) {
+            double s = f[(0 * K + k) * N + c];
+            for (int q = 1; q < Q; ++q) s += f[(q * K + k) * N + c];
+            u[k] = s;
+            if (U) U[k * N + c] = s;
+        }
+        feq_cell(P, u, feq);
+        for (int q = 0; q < Q; ++q)
+            for (int k = 0; k < K; ++k) {
+                int64_t idx = (q * K + k) * N + c;
+                fs[idx] = om1 * f[idx] + om * feq[q * K + k];
+            }
+        double p = pressure(P, u);
+        int finite = 1;
+        for (int k = 0; k < K; ++k) finite &= isfinite(u[k]);
+        if (!finite || !(u[0] > 0.0) || !(p > 0.0)) {
+            ++bad;
+        } else {
+            double l = lambda_local(P, u, p);
+            if (l > lmax) lmax = l;
+            if (l > P->lambda) ++sub;
+        }
+    }
+    if (chk) {
+        if (lmax > chk->max_lambda_local) chk->max_lambda_local = lmax;
+        if (bad || sub) {
+            if (chk->first_bad_step < 0) chk->first_bad_step = step;
+            chk->n_nonphysical = bad;
+            chk->n_subchar = sub;
+        }
+    }
+}
+
+/*
+ * Advance fs (in place) by nsteps steps; work is scratch of the same size.
+ * The step counter of the checks starts at step0 + 1.  Returns 0 or an error code.
+ */
+int orc_run(const orc_params* P, double* fs, double* work, int64_t nsteps, int64_t step0, orc_check* chk)
+{
+    int err = orc_validate(P);
+    if (err) return err;
+    for (int64_t n = 0; n < nsteps; ++n) {
+        orc_stream(P, fs, work);
+        orc_collide(P, work, fs, NULL, chk, step0 + n + 1);
+    }
+    return 0;
+}
+
+/* FP64 totals sum_cells U_k * cell volume (cell volume = dx for 1-D, dx^2 for 2-D). */
+void orc_totals(const orc_params* P, const double* fs, double cell_volume, double* totals)
+{
+    const int64_t N = P->nx * P->ny;
+    const int Q = nq(P), K = nk(P);
+    for (int k = 0; k < K; ++k) {
+        double s = 0.0;
+        for (int64_t c = 0; c < N; ++c) {
+            double u = fs[(0 * K + k) * N + c];
+            for (int q = 1; q < Q; ++q) u += fs[(q * K + k) * N + c];
+            s += u;
+        }
+        totals[k] = s * cell_volume;
+    }
+}
+
+int orc_max_threads(void) { return omp_get_max_threads(); }

@@ -1,0 +1,53 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one mistake in a copy of the oracle's C source (on the CPU,
+in a temporary directory), compiles it, and runs the pin suite against it
+through LBRS_ORACLE_LIB.  The pin suite must fail for every mutant.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "lbrs_oracle.c")
+
+MUTANTS = {
+    "relaxation_weights_swapped": ("fs[idx] = om1 * f[idx] + om * feq[q * K + k];",
+                                   "fs[idx] = om * f[idx] + om1 * feq[q * K + k];"),
+    "energy_flux_drops_pressure": ("F[3] = u * (en + p);", "F[3] = u * en;"),
+    "momentum_flux_drops_pressure": ("F[1] = mx * u + p;", "F[1] = mx * u;"),
+    "pressure_drops_v_term": ("double p = (g - 1.0) * (en - 0.5 * (mx * u + my * v));",
+                              "double p = (g - 1.0) * (en - 0.5 * (mx * u));"),
+    "stream_direction_reversed": ("int64_t si = i - sx, sj = j - sy;", "int64_t si = i + sx, sj = j - sy;"),
+    "populations_f2_f4_swapped": ("static const int SY2[4] = {-1, -1, +1, +1};",
+                                  "static const int SY2[4] = {-1, +1, +1, -1};"),
+    "wall_no_sign_flip": ("double sgn = (k == 2) ? -1.0 : 1.0;", "double sgn = 1.0;"),
+    "transmissive_clamps_inward": ("else si = si < 0 ? 0 : nx - 1;              /* transmissive */",
+                                   "else si = si < 0 ? 1 : nx - 2;              /* transmissive */"),
+    "flux_scale_2lambda": ("double c = 1.0 / (4.0 * P->lambda);", "double c = 1.0 / (2.0 * P->lambda);"),
+    "d1q2_flux_drops_pressure": ("double G[3] = {m, m * u + p, u * (en + p)};",
+                                 "double G[3] = {m, m * u, u * (en + p)};"),
+    "gamma_in_place_of_gamma_minus_1": ("return (g - 1.0) * (U[3] - 0.5 * (U[1] * u + U[2] * v));",
+                                        "return g * (U[3] - 0.5 * (U[1] * u + U[2] * v));"),
+    "ghost_uses_wrong_side": ("if (kind == ORC_DIRICHLET) g = ghost[side_x];",
+                              "if (kind == ORC_DIRICHLET) g = ghost[side_x ^ 1];"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation site for {name} not found"
+    mutated = tmp_path / "lbrs_oracle_mut.c"
+    mutated.write_text(src.replace(old, new))
+    so = tmp_path / "liblbrs_oracle_mut.so"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-shared", "-fPIC",
+                    str(mutated), "-o", str(so), "-lm"], check=True)
+    env = dict(os.environ, LBRS_ORACLE_LIB=str(so), OMP_NUM_THREADS="2")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"pins did not catch mutant {name}:\n{r.stdout[-2000:]}"

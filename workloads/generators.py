@@ -1,0 +1,375 @@
+"""Workload builders: the paper's test problems and their seeded synthetic stand-ins.
+
+Conventions shared by every consumer:
+
+* cells are cell-centred, x_i = x0 + (i + 1/2) dx (and likewise in y);
+* 2-D primitive fields have shape (4, ny, nx) in the order (rho, u, v, p),
+  1-D fields shape (3, nx) in the order (rho, u, p);
+* boundary conditions are given per side (x-lo, x-hi[, y-lo, y-hi]) as
+  ``(kind, state)`` with kind one of "periodic", "transmissive", "dirichlet",
+  "wall" and state the primitive Dirichlet state (or None);
+* lambda is one global lattice speed for the whole run (exact hopping needs a
+  single dt = dx / lambda, Eq. for the discrete LBRS update, Section II.A).
+
+Lambda is chosen from the exact Riemann solutions of the initial
+discontinuities: the largest local speed over every constant state of those
+solutions (the 1-D formula max(|u-a|, |u|, |u+a|) of Section II.C, or the
+Bouchut bound of Section II.D for D2Q4, read as max(|u+v|, |u-v|) + sqrt(2) a),
+times a safety factor.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import riemann
+from .oblique import post_shock_state
+
+GAMMA = 1.4
+
+
+@dataclass
+class Workload1D:
+    name: str
+    nx: int
+    dx: float
+    x0: float
+    prim: np.ndarray            # (3, nx) rho, u, p
+    bc: list                    # [(kind, state_or_None)] * 2
+    lam: float
+    omega: float
+    steps: int
+    gamma: float = GAMMA
+    t_final: float = 0.0
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def x(self) -> np.ndarray:
+        return self.x0 + (np.arange(self.nx) + 0.5) * self.dx
+
+
+@dataclass
+class Workload2D:
+    name: str
+    nx: int
+    ny: int
+    dx: float
+    x0: float
+    y0: float
+    prim: np.ndarray            # (4, ny, nx) rho, u, v, p
+    bc: list                    # [(kind, state_or_None)] * 4: x-lo, x-hi, y-lo, y-hi
+    lam: float
+    omega: float
+    steps: int
+    gamma: float = GAMMA
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def cells(self) -> int:
+        return self.nx * self.ny
+
+
+@dataclass
+class TubeBatch:
+    """Many independent 1-D shock tubes of uneven length, each on [0, 1]."""
+
+    lengths: np.ndarray         # (B,) int64 cells per tube
+    left: np.ndarray            # (B, 3) rho, u, p left of x = 0.5
+    right: np.ndarray           # (B, 3)
+    lam: np.ndarray             # (B,) lattice speed per tube
+    steps: np.ndarray           # (B,) steps per tube to reach t_final
+    t_final: float
+    omega: float
+    gamma: float = GAMMA
+
+    @property
+    def total_cells(self) -> int:
+        return int(self.lengths.sum())
+
+    @property
+    def total_updates(self) -> int:
+        return int((self.lengths * self.steps).sum())
+
+    def prim(self) -> np.ndarray:
+        """Concatenated primitive fields, shape (3, sum N), tube b at offset sum_{c<b} N_c."""
+        out = np.empty((3, self.total_cells))
+        off = 0
+        for b, n in enumerate(self.lengths):
+            n = int(n)
+            xc = (np.arange(n) + 0.5) / n
+            for k in range(3):
+                out[k, off:off + n] = np.where(xc < 0.5, self.left[b, k], self.right[b, k])
+            off += n
+        return out
+
+
+def sound(gamma, rho, p):
+    return math.sqrt(gamma * p / rho)
+
+
+def bouchut_speed(gamma, rho, u, v, p) -> float:
+    """Largest of |u+v|, |u-v| plus sqrt(2) a: the D2Q4 Euler bound of Section II.D."""
+    return max(abs(u + v), abs(u - v)) + math.sqrt(2.0) * sound(gamma, rho, p)
+
+
+def _round_lambda(lam: float, dx: float, t_final: float):
+    """Raise lambda so that t_final / dt = t_final * lambda / dx is an integer."""
+    n = int(math.ceil(t_final * lam / dx - 1e-9))
+    return n * dx / t_final, n
+
+
+def lambda_1d_riemann(gamma, wl, wr, safety=1.05, lam_min=0.0) -> float:
+    """max(|u|+a) over the constant states of the exact solution, times safety."""
+    states = riemann.star_states(gamma, wl, wr)
+    lam = max(abs(u) + sound(gamma, r, p) for (r, u, p) in states)
+    return max(lam_min, safety * lam)
+
+
+def lambda_2d_quadrants(gamma, q, safety=1.1) -> float:
+    """Bouchut bound over the four interface Riemann problems of a quadrant problem.
+
+    q maps 1..4 (quadrants counter-clockwise from the top right) to (rho, u, v, p).
+    Across an x-interface u is normal and v is carried by each side; across a
+    y-interface v is normal and u is carried.
+    """
+    lam = 0.0
+    # x-interfaces: (left, right) = (2, 1) on top, (3, 4) at the bottom
+    for a, b in ((2, 1), (3, 4)):
+        (ra, ua, va, pa), (rb, ub, vb, pb) = q[a], q[b]
+        sts = riemann.star_states(gamma, (ra, ua, pa), (rb, ub, pb))
+        tang = (va, va, vb, vb)
+        for (r, un, p), vt in zip(sts, tang):
+            lam = max(lam, bouchut_speed(gamma, r, un, vt, p))
+    # y-interfaces: (lower, upper) = (4, 1) right, (3, 2) left
+    for a, b in ((4, 1), (3, 2)):
+        (ra, ua, va, pa), (rb, ub, vb, pb) = q[a], q[b]
+        sts = riemann.star_states(gamma, (ra, va, pa), (rb, vb, pb))
+        tang = (ua, ua, ub, ub)
+        for (r, vn, p), ut in zip(sts, tang):
+            lam = max(lam, bouchut_speed(gamma, r, ut, vn, p))
+    return safety * lam
+
+
+# --------------------------------------------------------------------------- 1-D
+
+def sod(nx: int = 1000, omega: float = 1.0, t_final: float = 0.2) -> Workload1D:
+    """Sod's shock tube in nondimensional form on [0, 1], diaphragm at 0.5 (Section III).
+
+    The paper runs the dimensional version (1 kg/m^3, 0, 1e5 Pa | 0.125, 0,
+    1e4 Pa) on [-10, 10]; this is the usual scaled form with the same ratios.
+    """
+    wl, wr = (1.0, 0.0, 1.0), (0.125, 0.0, 0.1)
+    dx = 1.0 / nx
+    x = (np.arange(nx) + 0.5) * dx
+    prim = np.empty((3, nx))
+    for k in range(3):
+        prim[k] = np.where(x < 0.5, wl[k], wr[k])
+    lam, steps = _round_lambda(lambda_1d_riemann(GAMMA, wl, wr), dx, t_final)
+    return Workload1D("sod", nx, dx, 0.0, prim, [("transmissive", None)] * 2, lam, omega, steps,
+                      t_final=t_final, meta={"left": wl, "right": wr, "x_interface": 0.5})
+
+
+def steady_contact(nx: int = 100, omega: float = 1.0, t_final: float = 2.0) -> Workload1D:
+    """Stationary contact (rho 1.4 | 1.0, u = 0, p = 1) on [0, 1] (Section III)."""
+    wl, wr = (1.4, 0.0, 1.0), (1.0, 0.0, 1.0)
+    dx = 1.0 / nx
+    x = (np.arange(nx) + 0.5) * dx
+    prim = np.empty((3, nx))
+    for k in range(3):
+        prim[k] = np.where(x < 0.5, wl[k], wr[k])
+    lam0 = 1.05 * max(sound(GAMMA, 1.0, 1.0), sound(GAMMA, 1.4, 1.0))
+    lam, steps = _round_lambda(lam0, dx, t_final)
+    return Workload1D("steady_contact", nx, dx, 0.0, prim, [("transmissive", None)] * 2, lam, omega,
+                      steps, t_final=t_final, meta={"left": wl, "right": wr})
+
+
+def steady_shock(nx: int = 400, mach: float = 2.0, omega: float = 1.0, steps: int = 1000) -> Workload1D:
+    """Stationary Mach-2 normal shock at x = 0 on [-1, 1] (Section III, steady shock).
+
+    Pre-shock state (1, M a, 1/gamma) so that a = 1; the post-shock state
+    comes from the normal-shock relations.
+    """
+    r1, p1 = 1.0, 1.0 / GAMMA
+    u1 = mach * sound(GAMMA, r1, p1)
+    r2 = r1 * (GAMMA + 1) * mach ** 2 / ((GAMMA - 1) * mach ** 2 + 2)
+    p2 = p1 * (1 + 2 * GAMMA / (GAMMA + 1) * (mach ** 2 - 1))
+    u2 = u1 * r1 / r2
+    dx = 2.0 / nx
+    x = -1.0 + (np.arange(nx) + 0.5) * dx
+    prim = np.empty((3, nx))
+    for k, (a, b) in enumerate(zip((r1, u1, p1), (r2, u2, p2))):
+        prim[k] = np.where(x < 0.0, a, b)
+    lam = 1.1 * max(abs(u1) + sound(GAMMA, r1, p1), abs(u2) + sound(GAMMA, r2, p2))
+    bc = [("dirichlet", (r1, u1, p1)), ("dirichlet", (r2, u2, p2))]
+    return Workload1D("steady_shock", nx, dx, -1.0, prim, bc, lam, omega, steps,
+                      meta={"pre": (r1, u1, p1), "post": (r2, u2, p2)})
+
+
+def batched_tubes(seed: int = 0, count: int = 4096, n_min: int = 200, n_max: int = 20000,
+                  t_final: float = 0.15, omega: float = 1.0) -> TubeBatch:
+    """Seeded shock tubes on [0, 1] with log-uniform lengths.
+
+    Left/right rho, p ~ U[0.05, 2], u ~ U[-1, 1]; a draw whose Riemann problem
+    generates vacuum is replaced by the next draw.  Lambda per tube from its
+    exact solution, rounded so t_final is reached in a whole number of steps.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lengths = np.rint(np.exp(rng.uniform(math.log(n_min), math.log(n_max), size=count))).astype(np.int64)
+    left = np.empty((count, 3))
+    right = np.empty((count, 3))
+    lam = np.empty(count)
+    steps = np.empty(count, dtype=np.int64)
+    for b in range(count):
+        while True:
+            d = rng.uniform(size=6)
+            wl = (0.05 + 1.95 * d[0], -1.0 + 2.0 * d[1], 0.05 + 1.95 * d[2])
+            wr = (0.05 + 1.95 * d[3], -1.0 + 2.0 * d[4], 0.05 + 1.95 * d[5])
+            if not riemann.has_vacuum(GAMMA, wl, wr):
+                break
+        left[b], right[b] = wl, wr
+        dx = 1.0 / lengths[b]
+        lam[b], steps[b] = _round_lambda(lambda_1d_riemann(GAMMA, wl, wr), dx, t_final)
+    return TubeBatch(lengths, left, right, lam, steps, t_final, omega)
+
+
+# --------------------------------------------------------------------------- 2-D
+
+def _cell_centres(n, x0, dx):
+    return x0 + (np.arange(n) + 0.5) * dx
+
+
+def _quadrant_fields(nx, ny, dx, x0, y0, xc, yc, q):
+    x = _cell_centres(nx, x0, dx)[None, :]
+    y = _cell_centres(ny, y0, dx)[:, None]
+    right, top = x >= xc, y >= yc
+    prim = np.empty((4, ny, nx))
+    for k in range(4):
+        prim[k] = np.where(top, np.where(right, q[1][k], q[2][k]), np.where(right, q[4][k], q[3][k]))
+    return prim
+
+
+def quadrant_riemann(seed: int = 0, n: int = 1024, omega: float = 1.0, steps: int = 1000) -> Workload2D:
+    """Seeded four-quadrant 2-D Riemann problem on [0, 1]^2, split at (0.5, 0.5).
+
+    Quadrant states: rho ~ U[0.1, 1.5], p ~ U[0.03, 1.5], u, v ~ U[-1.2, 1.2].
+    A draw for which any of the four interface Riemann problems generates
+    vacuum is replaced by the next draw.  Transmissive boundaries all round.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    while True:
+        d = rng.uniform(size=(4, 4))
+        q = {i + 1: (0.1 + 1.4 * d[i, 0], -1.2 + 2.4 * d[i, 1], -1.2 + 2.4 * d[i, 2], 0.03 + 1.47 * d[i, 3])
+             for i in range(4)}
+        ok = True
+        for a, b in ((2, 1), (3, 4)):
+            ok &= not riemann.has_vacuum(GAMMA, (q[a][0], q[a][1], q[a][3]), (q[b][0], q[b][1], q[b][3]))
+        for a, b in ((4, 1), (3, 2)):
+            ok &= not riemann.has_vacuum(GAMMA, (q[a][0], q[a][2], q[a][3]), (q[b][0], q[b][2], q[b][3]))
+        if ok:
+            break
+    dx = 1.0 / n
+    prim = _quadrant_fields(n, n, dx, 0.0, 0.0, 0.5, 0.5, q)
+    lam = lambda_2d_quadrants(GAMMA, q)
+    return Workload2D(f"quadrant_riemann_s{seed}", n, n, dx, 0.0, 0.0, prim, [("transmissive", None)] * 4,
+                      lam, omega, steps, meta={"quadrants": q, "seed": seed})
+
+
+def paper_riemann_case4(n: int = 400, omega: float = 1.0, steps: int = 100) -> Workload2D:
+    """The paper's 2-D Riemann problem (Liska-Wendroff case 4), Section III.
+
+    The paper writes the quadrants around the origin while solving on
+    [0, 1]^2; they are placed here around the centre (0.5, 0.5).
+    """
+    q = {1: (1.1, 0.0, 0.0, 1.1), 2: (0.5065, 0.8939, 0.0, 0.35),
+         3: (1.1, 0.8939, 0.8939, 1.1), 4: (0.5065, 0.0, 0.8939, 0.35)}
+    dx = 1.0 / n
+    prim = _quadrant_fields(n, n, dx, 0.0, 0.0, 0.5, 0.5, q)
+    lam = lambda_2d_quadrants(GAMMA, q)
+    return Workload2D("paper_riemann_case4", n, n, dx, 0.0, 0.0, prim, [("transmissive", None)] * 4,
+                      lam, omega, steps, meta={"quadrants": q})
+
+
+def explosion(n: int = 400, omega: float = 1.0, steps: int = 100) -> Workload2D:
+    """Cylindrical explosion on [-1, 1]^2: (1, 0, 0, 1) inside r < 0.4, (0.125, 0, 0, 0.1) outside."""
+    dx = 2.0 / n
+    x = _cell_centres(n, -1.0, dx)[None, :]
+    y = _cell_centres(n, -1.0, dx)[:, None]
+    inside = x * x + y * y < 0.16
+    prim = np.empty((4, n, n))
+    for k, (a, b) in enumerate(zip((1.0, 0.0, 0.0, 1.0), (0.125, 0.0, 0.0, 0.1))):
+        prim[k] = np.where(inside, a, b)
+    lam = 1.1 * max(bouchut_speed(GAMMA, *s) for s in
+                    [(1.0, 0.0, 0.0, 1.0), (0.125, 0.0, 0.0, 0.1)] +
+                    [(r, u, 0.0, p) for (r, u, p) in
+                     riemann.star_states(GAMMA, (1.0, 0.0, 1.0), (0.125, 0.0, 0.1))])
+    return Workload2D("explosion", n, n, dx, -1.0, -1.0, prim, [("transmissive", None)] * 4, lam, omega, steps)
+
+
+OBLIQUE_INFLOW = (1.0, 2.9, 0.0, 1.0 / 1.4)
+OBLIQUE_BETA_DEG = 29.0
+
+
+def oblique_shock_reflection(nx: int = 4096, ny: int = 1024, omega: float = 1.0,
+                             steps: int = 20000, top_state=None) -> Workload2D:
+    """Oblique shock reflection on [0, 4] x [0, 1] (Section III).
+
+    Inflow (1, 2.9, 0, 1/1.4) on the left; the top held at the state behind a
+    29-degree oblique shock; free-slip wall at the bottom; transmissive
+    outflow on the right; interior initialised to the inflow state.
+    """
+    dx = 4.0 / nx
+    if abs(dx - 1.0 / ny) > 1e-15:
+        raise ValueError("D2Q4 needs dx == dy: use nx = 4 ny")
+    inflow = OBLIQUE_INFLOW
+    top = top_state or post_shock_state(GAMMA, inflow[0], inflow[1], inflow[3], OBLIQUE_BETA_DEG)
+    prim = np.empty((4, ny, nx))
+    for k in range(4):
+        prim[k] = inflow[k]
+    lam = 1.1 * max(bouchut_speed(GAMMA, *inflow), bouchut_speed(GAMMA, *top))
+    bc = [("dirichlet", inflow), ("transmissive", None), ("wall", None), ("dirichlet", tuple(top))]
+    return Workload2D("oblique_shock", nx, ny, dx, 0.0, 0.0, prim, bc, lam, omega, steps,
+                      meta={"top": tuple(top)})
+
+
+def uniform_2d(nx, ny, state=(1.0, 0.5, 0.3, 1.0), bc="periodic", lam=None, omega=1.0, steps=10) -> Workload2D:
+    """Uniform flow; every boundary of the given kind (Dirichlet at the same state)."""
+    prim = np.empty((4, ny, nx))
+    for k in range(4):
+        prim[k] = state[k]
+    lam = lam or 1.2 * bouchut_speed(GAMMA, *state)
+    b = (bc, tuple(state) if bc == "dirichlet" else None)
+    return Workload2D("uniform", nx, ny, 1.0 / nx, 0.0, 0.0, prim, [b] * 4, lam, omega, steps)
+
+
+def adjoint_pulses(seed: int = 0, n: int = 2048, pulses: int = 8, amp: float = 0.1, width: float = 0.05,
+                   omega: float = 1.0, steps: int = 2000, lam: float = 3.0):
+    """Uniform flow (1, 0.5, 0.3, 1) plus seeded Gaussian pulses in rho and p, periodic [0, 1]^2.
+
+    Returns (workload, rho_target) where the target density is 1 plus pulses
+    drawn from seed + 1.  Distances use the periodic minimum image.
+    """
+    def pulses_field(rng):
+        c = rng.uniform(size=(pulses, 2))
+        x = _cell_centres(n, 0.0, 1.0 / n)
+        f = np.zeros((n, n))
+        for cx, cy in c:
+            dxp = np.abs(x - cx)
+            dxp = np.minimum(dxp, 1.0 - dxp)
+            dyp = np.abs(x - cy)
+            dyp = np.minimum(dyp, 1.0 - dyp)
+            f += amp * np.exp(-(dyp[:, None] ** 2 + dxp[None, :] ** 2) / (2.0 * width ** 2))
+        return f
+
+    base = (1.0, 0.5, 0.3, 1.0)
+    bump = pulses_field(np.random.Generator(np.random.PCG64(seed)))
+    prim = np.empty((4, n, n))
+    prim[0] = base[0] + bump
+    prim[1] = base[1]
+    prim[2] = base[2]
+    prim[3] = base[3] + bump
+    target = 1.0 + pulses_field(np.random.Generator(np.random.PCG64(seed + 1)))
+    wl = Workload2D(f"adjoint_pulses_s{seed}", n, n, 1.0 / n, 0.0, 0.0, prim, [("periodic", None)] * 4,
+                    lam, omega, steps)
+    return wl, target
