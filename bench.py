@@ -1,0 +1,330 @@
+"""Benchmark of the LBRS time step on one GB300 (or N replicas under torchrun).
+
+Workload: the 2-D D2Q4 four-quadrant Riemann problem, 1024 x 1024 cells on
+[0, 1]^2, quadrant states from seed 0 (rho ~ U[0.1, 1.5], p ~ U[0.03, 1.5],
+u, v ~ U[-1.2, 1.2]), transmissive boundaries, gamma = 1.4, omega = 1,
+FP32 distributions.  One bench "step" is one LBRS time step over the whole
+grid (stream, boundary conditions, moments, fluxes, equilibria, relaxation).
+
+Printed: one JSON line with MLUPS (million lattice updates per second) of the
+FP32 path with the L2 cache flushed before every timed step, the FP64 path's
+MLUPS and the FP32 density L1 error after the configuration's 1000 steps,
+the HBM roofline of the step kernel, an end-to-end figure through the public
+API with host buffers, and the FP64 CPU oracle timed on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "2D LBRS MLUPS FP32 vs FP64 at stated L1 error; % HBM roofline; adjoint/fwd cost"
+UNIT = "MLUPS"
+BYTES_PER_LUP_F32 = 128      # 16 FP32 distributions read + 16 written per cell and step
+BYTES_PER_LUP_F64 = 256
+L2_FLUSH_BYTES = 256 << 20   # twice the 129 MB L2
+CONFIG_STEPS = 1000
+
+
+def workload():
+    return workloads.quadrant_riemann(seed=0, n=1024, steps=CONFIG_STEPS)
+
+
+def config_dict(wl, extra=None):
+    d = {"workload": "2-D D2Q4 four-quadrant Riemann 1024x1024, seed 0, transmissive, 1000-step configuration",
+         "nx": wl.nx, "ny": wl.ny, "lattice": "D2Q4", "gamma": wl.gamma, "omega": wl.omega,
+         "lambda": wl.lam, "precision": "f32",
+         "l2": "flushed (256 MiB write) before every timed step, outside the step's CUDA events"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for rel in ("paper_1504_07034_gb300/csrc/lbrs_kernels.cuh", "paper_1504_07034_gb300/csrc/lbrs_kernels_f32.cu"):
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(cells: int):
+    """DRAM bytes per launch of the FP32 step from the committed ncu summary, if it is current."""
+    path = os.path.join(ROOT, "profiles", "step2d_f32_traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_sha") != kernel_source_sha():
+        return None
+    return rec["dram_bytes_per_launch"] * cells / rec["cells"]
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 100 ms while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.t0 = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        self.t0 = time.time()
+        return self
+
+    def stop(self):
+        if not self.proc:
+            return []
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = []
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        return rows
+
+    def __exit__(self, *a):
+        return False
+
+
+def summarise_clocks(rows):
+    if not rows:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+    sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+    smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+            "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def oracle_sample(wl, seconds=12.0):
+    """The FP64 oracle as it stands on the host cores: MLUPS over a bounded number of steps."""
+    import oracle
+    o = oracle.Oracle.from_workload(wl)
+    fs = o.init(o.prim_to_cons(wl.prim))
+    fs, t1 = o.timed_run(fs, 2)
+    n = max(2, min(wl.steps, int(seconds / max(t1 / 2, 1e-6))))
+    _, t = o.timed_run(fs, n)
+    return {"value": wl.cells * n / t / 1e6, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"FP64 C oracle, full {wl.nx}x{wl.ny} grid, steps 3..{n + 2} of the 1000-step run "
+                      f"({t:.1f} s, OpenMP over rows)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    wl = workload()
+    o = oracle.Oracle.from_workload(wl)
+    fs = o.init(o.prim_to_cons(wl.prim))
+    for _ in range(args.warmup):
+        fs, _ = o.timed_run(fs, 1)
+    total = 0.0
+    for _ in range(args.steps):
+        fs, t = o.timed_run(fs, 1)
+        total += t
+    value = wl.cells * args.steps / total / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded quadrant states)", "config": config_dict(wl, {"precision": "f64"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": f"full {wl.nx}x{wl.ny} grid, {args.steps} steps after {args.warmup} warm-up"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_ours(args):
+    import torch
+    from paper_1504_07034_gb300.build import build as build_lib
+    build_lib()
+    from paper_1504_07034_gb300.solver import Solver
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    wl = workload()
+    stream = torch.cuda.Stream()
+    W0 = torch.from_numpy(wl.prim).cuda()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed_steps(s, k, warm):
+        with torch.cuda.stream(stream):
+            for _ in range(warm):
+                flush.fill_(1.0)
+                s.step(1)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+            barrier()
+            l0 = s.launch_count
+            for a, b in ev:
+                flush.fill_(1.0)
+                a.record(stream)
+                s.step(1)
+                b.record(stream)
+            barrier()
+            launches = s.launch_count - l0
+        ms = [a.elapsed_time(b) for a, b in ev]
+        return ms, launches
+
+    # --- FP32 path: the headline ---------------------------------------------------
+    s32 = Solver.from_workload(wl, precision="f32", stream=stream)
+    s32.set_state(W0)
+    props = torch.cuda.get_device_properties(local)
+    gpu_id = f"GPU-{props.uuid}" if getattr(props, "uuid", None) else str(local)
+    with ClockSampler(gpu_id) as clk:
+        ms32, launches = timed_steps(s32, args.steps, args.warmup)
+        rows = clk.stop()
+    clocks = summarise_clocks(rows)
+    t32 = sum(ms32) / 1e3
+    if dist is not None:
+        t = torch.tensor([t32], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t32 = float(t.item())
+    value = ws * wl.cells * args.steps / t32 / 1e6
+    avg_kernel_s = t32 / args.steps
+    peak, peak_kind = hbm_peak()
+    achieved = BYTES_PER_LUP_F32 * wl.cells / avg_kernel_s / 1e9
+    traffic = measured_traffic(wl.cells)
+
+    # --- FP64 path and FP32 accuracy over the full 1000-step configuration -----------
+    s64 = Solver.from_workload(wl, precision="f64", stream=stream)
+    s64.set_state(W0)
+    ms64, _ = timed_steps(s64, min(args.steps, 200), 3)
+    mlups64 = wl.cells * len(ms64) / (sum(ms64) / 1e3) / 1e6
+    with torch.cuda.stream(stream):
+        s64.set_state(W0)
+        s64.step(CONFIG_STEPS)
+        s32.set_state(W0)
+        s32.step(CONFIG_STEPS)
+        rho64 = s64.moments(torch.float64)[0]
+        rho32 = s32.moments(torch.float64)[0]
+        d64 = s64.diagnostics()
+    stream.synchronize()
+    l1 = float((rho32 - rho64).abs().mean().item())
+
+    # --- end to end through the public API with host buffers -------------------------
+    prim_host = torch.from_numpy(wl.prim).pin_memory()
+    out_host = torch.empty((4, wl.ny, wl.nx), dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for rep in range(3):
+        with torch.cuda.stream(stream):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            barrier()
+            a.record(stream)
+            s32.set_state(prim_host)
+            s32.step(CONFIG_STEPS)
+            s32.moments(out=out_host)
+            b.record(stream)
+            barrier()
+            e2e_ms.append(a.elapsed_time(b))
+    e2e_s = min(e2e_ms[1:]) / 1e3
+    e2e_value = ws * wl.cells * CONFIG_STEPS / e2e_s / 1e6
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t32 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded four-quadrant Riemann states)",
+            "config": config_dict(wl, {"parallelism": f"{ws} independent replicas" if ws > 1 else "1 GPU"}),
+            "gpu_launches": launches,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "step2d_kernel<float>", "peak_kind": f"{peak_kind} hbm_gbs",
+                         "algorithmic_bytes_per_lup": BYTES_PER_LUP_F32},
+            "fp64": {"value": mlups64, "unit": UNIT, "achieved_gbs": BYTES_PER_LUP_F64 * mlups64 / 1e3,
+                     "diag_after_1000_steps": {k: d64[k] for k in ("status", "min_rho", "min_p", "max_lambda_local")}},
+            "accuracy": {"l1_rho_fp32_vs_fp64_gpu_after_1000_steps": l1,
+                         "note": "the FP64 GPU path matches the FP64 CPU oracle to <= 1e-12 (tests)"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(prim_host.numel() * 8),
+                    "d2h_bytes_per_step": int(out_host.numel() * 8),
+                    "step": "set_state(host) + 1000 steps + moments(host)"},
+            "clocks": clocks}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sample(wl)
+    if rank == 0:
+        print(json.dumps(line))
+    s32.close()
+    s64.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

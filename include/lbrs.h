@@ -1,0 +1,182 @@
+/*
+ * lbrs.h -- C ABI of the GB300 Lattice Boltzmann Relaxation Scheme (LBRS) solver.
+ *
+ * The method (Raghurama Rao, Deshmukh, Kotnala, "A Lattice Boltzmann
+ * Relaxation Scheme for Inviscid Compressible Flows"):
+ *
+ *   distributions f_q, one per lattice velocity c_q and conserved field k;
+ *   one time step = stream every population one lattice spacing along its
+ *   velocity (exact hopping, lambda dt = dx), apply the boundary conditions,
+ *   take the moments U_k = sum_q f_{q,k}, evaluate the Euler fluxes with the
+ *   ideal-gas pressure, build the algebraic equilibria and relax:
+ *       f*_q = (1 - omega) f_q + omega f^eq_q(U)      (discrete LBRS update, Section II.A)
+ *
+ *   D1Q2 (Section II.C): velocities (-lambda, +lambda), fields (rho, rho u, rho E),
+ *       f^eq_{1,2} = U/2 -/+ G(U)/(2 lambda).
+ *   D2Q4 (Section II.D): diagonal velocities f1 (-,-), f2 (+,-), f3 (+,+), f4 (-,+)
+ *       times lambda, fields (rho, rho u, rho v, rho E),
+ *       f^eq_q = U/4 + sx_q F(U)/(4 lambda) + sy_q G(U)/(4 lambda).
+ *   Free-slip wall (Section II.E): the populations entering through a wall
+ *       are replaced by specular reflection of the outgoing ones, negated for
+ *       the wall-normal momentum field.
+ *
+ * Conventions
+ *   Layout.    Distributions are structure-of-arrays f[q][k][j][i] (i fastest),
+ *              q in the paper's order, Q = 2 or 4, K = 3 or 4, N = nx * ny.
+ *              Field arrays are [k][j][i].  1-D problems have ny = 1.
+ *              Cells are cell-centred; dx = dy (exact hopping on the diagonals).
+ *   Memory.    The caller owns every buffer.  Device memory for the solver
+ *              state is ONE caller-provided workspace (e.g. a torch tensor) of
+ *              lbrs_workspace_size() bytes, 256-byte aligned, which must
+ *              outlive the context.  The library itself never allocates device
+ *              memory; it allocates its host-side context and, on first use
+ *              of a multi-step call, one private capture stream and CUDA
+ *              graphs, released by lbrs_destroy.
+ *   Streams.   All device work is enqueued on cfg.cuda_stream (0 = legacy
+ *              default stream).  Calls are asynchronous unless they return
+ *              data to host memory.  One context per stream; a context is not
+ *              thread-safe.
+ *   Errors.    Every call returns an lbrs_status; nothing aborts, traps or
+ *              throws across the ABI.  LBRS_EINVAL leaves the state unchanged.
+ *              lbrs_last_error() gives a one-line description of the last
+ *              failure on a context.
+ */
+#ifndef LBRS_H
+#define LBRS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBRS_ABI_VERSION 1
+
+typedef struct lbrs_ctx lbrs_ctx;
+
+typedef enum {
+    LBRS_OK = 0,
+    LBRS_EINVAL = 1,    /* invalid argument or configuration */
+    LBRS_ENOMEM = 2,    /* workspace too small */
+    LBRS_ECUDA = 3,     /* a CUDA runtime call failed (see lbrs_last_error) */
+    LBRS_ENONPHYS = 4,  /* a cell has rho <= 0, p <= 0 or a non-finite value */
+    LBRS_ESUBCHAR = 5,  /* a cell violates lambda >= local wave-speed bound (Sections II.A, II.D) */
+    LBRS_ETIMEOUT = 6,  /* reserved: a bounded device wait gave up */
+    LBRS_ESTATE = 7     /* call out of order (e.g. stepping before a state was set) */
+} lbrs_status;
+
+typedef enum { LBRS_D1Q2 = 0, LBRS_D2Q4 = 1 } lbrs_lattice;
+
+/* Storage and arithmetic precision of the distributions. */
+typedef enum { LBRS_F64 = 0, LBRS_F32 = 1 } lbrs_precision;
+
+/* Boundary kinds.  The paper defines only the free-slip wall (Section II.E);
+ * the others are this library's readings:
+ *   PERIODIC     the pull source wraps around (both sides of an axis must be periodic);
+ *   TRANSMISSIVE the pull source index is clamped into the domain (zero-order extrapolation);
+ *   DIRICHLET    populations entering from outside are f^eq of the given state;
+ *   WALL         free-slip wall on a y side (D2Q4 only), applied on the wall row. */
+typedef enum { LBRS_BC_PERIODIC = 0, LBRS_BC_TRANSMISSIVE = 1, LBRS_BC_DIRICHLET = 2, LBRS_BC_WALL = 3 } lbrs_bc_kind;
+
+/* Kind of the fields passed to lbrs_set_state. */
+typedef enum { LBRS_CONSERVED = 0, LBRS_PRIMITIVE = 1 } lbrs_state_kind;
+
+typedef struct {
+    int32_t kind;       /* lbrs_bc_kind */
+    int32_t reserved;
+    double prim[4];     /* DIRICHLET state: (rho, u, v, p) in 2-D, (rho, u, p) in 1-D */
+} lbrs_bc;
+
+typedef struct {
+    uint32_t struct_size;   /* = sizeof(lbrs_config), for ABI growth */
+    int32_t lattice;        /* lbrs_lattice */
+    int32_t precision;      /* lbrs_precision */
+    int32_t reserved0;
+    int64_t nx, ny;         /* cells; ny = 1 for D1Q2 */
+    double gamma;           /* ratio of specific heats, > 1 */
+    double lambda;          /* lattice speed, > 0; dt = dx / lambda */
+    double omega;           /* relaxation parameter dt/epsilon, in (0, 2) (Section II.B) */
+    double dx;              /* lattice spacing, > 0 (cell volume of the totals) */
+    lbrs_bc bc[4];          /* x-lo, x-hi, y-lo, y-hi; 1-D uses the first two */
+    void* cuda_stream;      /* cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream */
+} lbrs_config;
+
+/* Global diagnostics of the current state, reduced in FP64 in a fixed order
+ * (bitwise reproducible run to run). */
+typedef struct {
+    double totals[4];          /* sum over cells of U_k * dx^d (d = 1 or 2); K entries used */
+    double min_rho;            /* minimum density */
+    double min_p;              /* minimum pressure */
+    double max_lambda_local;   /* max |u| + a (1-D) or max(|u+v|,|u-v|) + sqrt(2) a (2-D), Sections II.C, II.D */
+    double reserved;
+    int64_t n_nonphysical;     /* cells with rho <= 0, p <= 0 or a non-finite moment */
+    int64_t n_subchar;         /* cells whose local bound exceeds lambda */
+} lbrs_diag;
+
+/* Library ABI version (LBRS_ABI_VERSION of the build). */
+int lbrs_abi_version(void);
+
+/* Human-readable name of a status code. Never NULL. */
+const char* lbrs_status_string(lbrs_status s);
+
+/* Bytes of device workspace a configuration needs: two distribution buffers
+ * (ping-pong), boundary tables and reduction scratch.  EINVAL on a bad config. */
+lbrs_status lbrs_workspace_size(const lbrs_config* cfg, size_t* bytes);
+
+/* Create a solver context on the caller's workspace.  Validates cfg (EINVAL),
+ * checks bytes >= lbrs_workspace_size (ENOMEM), computes the Dirichlet ghost
+ * tables on the device.  *out receives the context; no state is set yet. */
+lbrs_status lbrs_create(const lbrs_config* cfg, void* d_workspace, size_t bytes, lbrs_ctx** out);
+
+/* Release a context (host memory, graphs, private stream).  NULL is a no-op.
+ * Does not free the workspace. */
+void lbrs_destroy(lbrs_ctx* ctx);
+
+/* Set the state at step 0: f = f^eq(U0) (initialisation, Section II.A).
+ *   W        K fields [k][ny][nx]; conserved (rho, rho u, [rho v,] rho E) or primitive
+ *            (rho, u, [v,] p) according to `kind`;
+ *   on_device nonzero if W is device memory, zero for host memory (copied on the stream
+ *            through the idle half of the workspace);
+ *   dtype    LBRS_F64 or LBRS_F32: element type of W.
+ * The conversion and f^eq are computed in FP64 and rounded to the storage precision. */
+lbrs_status lbrs_set_state(lbrs_ctx* ctx, const void* W, int on_device, int dtype, int kind);
+
+/* Enqueue n >= 0 time steps (stream, boundary conditions, moments, fluxes,
+ * equilibria, relaxation; discrete LBRS update, Sections II.A and II.D).
+ * Asynchronous.  ESTATE if no state was set. */
+lbrs_status lbrs_step(lbrs_ctx* ctx, int64_t n);
+
+/* Wait for the context's stream; reports a CUDA error raised by earlier work. */
+lbrs_status lbrs_sync(lbrs_ctx* ctx);
+
+/* Conserved moments U_k = sum_q f_{q,k} of the current state (moment relations,
+ * Section II), summed in FP64 in q order and written as `dtype` to U_out [K][ny][nx].
+ * Host output (on_device == 0) synchronises the stream before returning. */
+lbrs_status lbrs_moments(lbrs_ctx* ctx, void* U_out, int on_device, int dtype);
+
+/* FP64 diagnostics of the current state (see lbrs_diag); synchronises.
+ * Returns ENONPHYS if any cell is non-physical, else ESUBCHAR if any cell
+ * violates the sub-characteristic bound, else OK; *out is filled in every case. */
+lbrs_status lbrs_diagnostics(lbrs_ctx* ctx, lbrs_diag* out);
+
+/* Copy the raw distributions f[q][k][j][i] (storage precision) out of / into
+ * the context, e.g. for checkpoints.  Host transfers synchronise.  set also
+ * sets the step counter. */
+lbrs_status lbrs_get_distributions(lbrs_ctx* ctx, void* dst, int on_device);
+lbrs_status lbrs_set_distributions(lbrs_ctx* ctx, const void* src, int on_device, int64_t step);
+
+/* Number of time steps taken since the state was set. */
+lbrs_status lbrs_step_count(const lbrs_ctx* ctx, int64_t* steps);
+
+/* Number of kernels this context has launched (graph launches count each kernel). */
+lbrs_status lbrs_launch_count(const lbrs_ctx* ctx, int64_t* launches);
+
+/* Description of the last error on ctx ("" if none). Never NULL. */
+const char* lbrs_last_error(const lbrs_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBRS_H */

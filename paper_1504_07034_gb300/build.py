@@ -1,0 +1,83 @@
+"""Build the LBRS CUDA library (liblbrs.so) in-tree for sm_103a.
+
+Three translation units compiled in parallel with nvcc, then linked into one
+shared library with the CUDA runtime linked statically:
+
+  csrc/lbrs_kernels_f64.cu  FP64 kernels, -fmad=false (rounding as written)
+  csrc/lbrs_kernels_f32.cu  FP32 step kernels
+  csrc/lbrs_runtime.cu      host C ABI (include/lbrs.h)
+
+Usage: python -m paper_1504_07034_gb300.build [--force]
+"""
+from __future__ import annotations
+
+import os
+import shutil
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+from pathlib import Path
+
+PKG = Path(__file__).resolve().parent
+ROOT = PKG.parent
+CSRC = PKG / "csrc"
+INCLUDE = ROOT / "include"
+BUILD = PKG / "_build"
+LIB = PKG / "liblbrs.so"
+
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+          "-Xptxas", "-v", "-I", str(INCLUDE), "-I", str(CSRC)]
+UNITS = {
+    "lbrs_kernels_f64.cu": ["-fmad=false"],
+    "lbrs_kernels_f32.cu": [],
+    "lbrs_runtime.cu": [],
+}
+HEADERS = [CSRC / "lbrs_kernels.cuh", CSRC / "lbrs_launch.h", INCLUDE / "lbrs.h"]
+
+
+def nvcc() -> str:
+    exe = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(exe):
+        raise RuntimeError("nvcc not found: the CUDA toolkit is required to build liblbrs.so")
+    return exe
+
+
+def _stale(target: Path, deps) -> bool:
+    if not target.exists():
+        return True
+    t = target.stat().st_mtime
+    return any(Path(d).stat().st_mtime > t for d in deps)
+
+
+def _compile(unit: str, extra) -> Path:
+    src = CSRC / unit
+    obj = BUILD / (unit + ".o")
+    log = BUILD / (unit + ".ptxas.log")
+    cmd = [nvcc(), *ARCH, *COMMON, *extra, "-c", str(src), "-o", str(obj)]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    log.write_text(" ".join(cmd) + "\n" + r.stdout + r.stderr)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {unit}:\n{r.stderr[-4000:]}")
+    return obj
+
+
+def build(force: bool = False) -> Path:
+    BUILD.mkdir(parents=True, exist_ok=True)
+    todo = [(u, x) for u, x in UNITS.items()
+            if force or _stale(BUILD / (u + ".o"), [CSRC / u, *HEADERS])]
+    with ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
+        list(ex.map(lambda ux: _compile(*ux), todo))
+    objs = [BUILD / (u + ".o") for u in UNITS]
+    if force or todo or _stale(LIB, objs):
+        tmp = LIB.with_name(f"liblbrs.{os.getpid()}.tmp.so")
+        cmd = [nvcc(), *ARCH, "-shared", "-o", str(tmp), *map(str, objs)]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stderr[-4000:]}")
+        os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv))

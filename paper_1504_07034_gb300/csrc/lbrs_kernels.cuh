@@ -1,0 +1,263 @@
+// Device code of the LBRS time step (sm_103a).
+//
+// One step of the Lattice Boltzmann Relaxation Scheme, fused into one kernel
+// per lattice: every thread owns one cell and
+//   1. pulls its Q*K post-collision populations from the upwind neighbours
+//      (f_q(x) = f*_q(x - c_q), exact hopping, discrete LBRS update of
+//      Section II.A / multi-D update of Section II.D), resolving sources
+//      outside the domain by the boundary kind; on a wall row the entering
+//      populations follow the free-slip relations of Section II.E;
+//   2. forms the moments U_k = sum_q f_{q,k} (moment relations);
+//   3. evaluates the ideal-gas pressure and the Euler fluxes (Section II.C,
+//      and their 2-D counterparts for Section II.D);
+//   4. builds the equilibria f^eq (Sections II.C, II.D) and relaxes
+//      f* = (1 - omega) f + omega f^eq, writing to the other ping-pong buffer.
+//
+// Storage is structure-of-arrays f[q][k][j][i]: each (q, k) plane is read
+// once at a constant (+-1, +-1) offset and written once, so one step moves
+// exactly Q*K*(read + write) elements per cell.
+//
+// The FP64 instantiation is compiled without FMA contraction and with IEEE
+// division so that its rounding is that of the plain expressions; the FP32
+// one uses one reciprocal per cell and lets the compiler contract.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+namespace lbrs {
+
+enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_DIRICHLET = 2, BC_WALL = 3 };
+enum { LAT_D1Q2 = 0, LAT_D2Q4 = 1 };
+enum { KIND_CONSERVED = 0, KIND_PRIMITIVE = 1 };
+
+// Ghost-table stride: one Dirichlet side holds Q*K <= 16 values.
+constexpr int GHOST_STRIDE = 16;
+// Width of one block's diagnostic partial record (doubles).
+constexpr int DIAG_W = 10;
+
+template <typename T>
+struct StepArgs {
+    const T* __restrict__ src;    // f* at time n, [Q][K][ny][nx]
+    T* __restrict__ dst;          // f* at time n + 1
+    const T* __restrict__ ghost;  // [4][GHOST_STRIDE]: f^eq of each Dirichlet side's state
+    int64_t N;                    // plane stride nx * ny
+    int nx, ny;
+    int bc[4];                    // x-lo, x-hi, y-lo, y-hi
+    T om, om1;                    // omega, 1 - omega
+    T c;                          // 1/(4 lambda) in 2-D, 1/(2 lambda) in 1-D
+    T gm1;                        // gamma - 1
+};
+
+// ---------------------------------------------------------------- arithmetic
+
+// Velocities from momenta: IEEE divisions in FP64 (same rounding as the plain
+// expressions), one correctly rounded reciprocal in FP32.
+template <typename T>
+__device__ __forceinline__ void velocity2(T rho, T mx, T my, T& u, T& v)
+{
+    if constexpr (std::is_same<T, double>::value) {
+        u = mx / rho;
+        v = my / rho;
+    } else {
+        const float inv = __frcp_rn(rho);
+        u = mx * inv;
+        v = my * inv;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T velocity1(T rho, T m)
+{
+    if constexpr (std::is_same<T, double>::value) {
+        return m / rho;
+    } else {
+        return m * __frcp_rn(rho);
+    }
+}
+
+// D2Q4 equilibria of one state (Section II.D), e[q][k]:
+//   F = (rho u, rho u^2 + p, rho u v, u (rho E + p)),
+//   G = (rho v, rho v u, rho v^2 + p, v (rho E + p)),
+//   f^eq_q = U/4 + sx_q c F + sy_q c G with c = 1/(4 lambda), q = (-,-), (+,-), (+,+), (-,+).
+template <typename T>
+__device__ __forceinline__ void equilibria2d(const T U[4], T gm1, T c, T e[4][4])
+{
+    T u, v;
+    velocity2<T>(U[0], U[1], U[2], u, v);
+    const T p = gm1 * (U[3] - T(0.5) * (U[1] * u + U[2] * v));
+    const T F[4] = {U[1], U[1] * u + p, U[1] * v, u * (U[3] + p)};
+    const T G[4] = {U[2], U[2] * u, U[2] * v + p, v * (U[3] + p)};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const T a = T(0.25) * U[k];
+        const T b = c * F[k];
+        const T d = c * G[k];
+        e[0][k] = (a - b) - d;
+        e[1][k] = (a + b) - d;
+        e[2][k] = (a + b) + d;
+        e[3][k] = (a - b) + d;
+    }
+}
+
+// D1Q2 equilibria (Section II.C): G = (rho u, rho u^2 + p, u (rho E + p)),
+// f^eq_{1,2} = U/2 -/+ c G with c = 1/(2 lambda).
+template <typename T>
+__device__ __forceinline__ void equilibria1d(const T U[3], T gm1, T c, T e[2][3])
+{
+    const T u = velocity1<T>(U[0], U[1]);
+    const T p = gm1 * (U[2] - T(0.5) * (U[1] * u));
+    const T G[3] = {U[1], U[1] * u + p, u * (U[2] + p)};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const T a = T(0.5) * U[k];
+        const T b = c * G[k];
+        e[0][k] = a - b;
+        e[1][k] = a + b;
+    }
+}
+
+// Conserved variables from primitive ones, rho E = p/(gamma - 1) + rho |u|^2 / 2.
+__device__ __forceinline__ void prim_to_cons2d(const double w[4], double gamma, double U[4])
+{
+    const double rho = w[0], u = w[1], v = w[2], p = w[3];
+    U[0] = rho;
+    U[1] = rho * u;
+    U[2] = rho * v;
+    U[3] = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v);
+}
+
+__device__ __forceinline__ void prim_to_cons1d(const double w[3], double gamma, double U[3])
+{
+    const double rho = w[0], u = w[1], p = w[2];
+    U[0] = rho;
+    U[1] = rho * u;
+    U[2] = p / (gamma - 1.0) + 0.5 * rho * (u * u);
+}
+
+// ---------------------------------------------------------------- D2Q4 step
+
+// Pull with boundary resolution for cells on the domain edge.
+// Priority: a wall on the y side; a Dirichlet ghost on the x side; a Dirichlet
+// ghost on the y side; otherwise wrap (periodic) / clamp (transmissive) each
+// coordinate.  Then the free-slip wall relations (Section II.E).
+template <typename T>
+__device__ __forceinline__ void pull_edge_2d(const StepArgs<T>& a, int i, int j, T f[4][4])
+{
+    const int SX[4] = {-1, 1, 1, -1};
+    const int SY[4] = {-1, -1, 1, 1};
+    bool wall_top = false, wall_bottom = false;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        int si = i - SX[q], sj = j - SY[q];
+        const int side_y = sj < 0 ? 2 : (sj >= a.ny ? 3 : -1);
+        const int side_x = si < 0 ? 0 : (si >= a.nx ? 1 : -1);
+        if (side_y >= 0 && a.bc[side_y] == BC_WALL) {
+            if (side_y == 3) wall_top = true; else wall_bottom = true;
+            continue;
+        }
+        const T* g = nullptr;
+        if (side_x >= 0) {
+            const int kind = a.bc[side_x];
+            if (kind == BC_DIRICHLET) g = a.ghost + side_x * GHOST_STRIDE + q * 4;
+            else if (kind == BC_PERIODIC) si = si < 0 ? si + a.nx : si - a.nx;
+            else si = si < 0 ? 0 : a.nx - 1;
+        }
+        if (!g && side_y >= 0) {
+            const int kind = a.bc[side_y];
+            if (kind == BC_DIRICHLET) g = a.ghost + side_y * GHOST_STRIDE + q * 4;
+            else if (kind == BC_PERIODIC) sj = sj < 0 ? sj + a.ny : sj - a.ny;
+            else sj = sj < 0 ? 0 : a.ny - 1;
+        }
+        const int64_t s = (int64_t)sj * a.nx + si;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) f[q][k] = g ? g[k] : a.src[(q * 4 + k) * a.N + s];
+    }
+    // top wall: f1 = f4, f2 = f3; bottom wall: f4 = f1, f3 = f2; rho v negated
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const T sgn = k == 2 ? T(-1) : T(1);
+        if (wall_top) {
+            f[0][k] = sgn * f[3][k];
+            f[1][k] = sgn * f[2][k];
+        }
+        if (wall_bottom) {
+            f[3][k] = sgn * f[0][k];
+            f[2][k] = sgn * f[1][k];
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void collide_store_2d(const StepArgs<T>& a, int64_t c, const T f[4][4])
+{
+    T U[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) U[k] = ((f[0][k] + f[1][k]) + f[2][k]) + f[3][k];
+    T e[4][4];
+    equilibria2d<T>(U, a.gm1, a.c, e);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a.dst[(q * 4 + k) * a.N + c] = a.om1 * f[q][k] + a.om * e[q][k];
+}
+
+// One thread per cell; blockDim.x along i (coalesced), blockDim.y along j.
+template <typename T>
+__global__ void __launch_bounds__(256) step2d_kernel(const StepArgs<T> a)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= a.nx || j >= a.ny) return;
+    const int64_t c = (int64_t)j * a.nx + i;
+    T f[4][4];
+    if (i > 0 && i < a.nx - 1 && j > 0 && j < a.ny - 1) {
+        // sources: q0 (-,-) <- (i+1, j+1); q1 (+,-) <- (i-1, j+1);
+        //          q2 (+,+) <- (i-1, j-1); q3 (-,+) <- (i+1, j-1)
+        const int64_t s[4] = {c + a.nx + 1, c + a.nx - 1, c - a.nx - 1, c - a.nx + 1};
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) f[q][k] = a.src[(q * 4 + k) * a.N + s[q]];
+    } else {
+        pull_edge_2d<T>(a, i, j, f);
+    }
+    collide_store_2d<T>(a, c, f);
+}
+
+// ---------------------------------------------------------------- D1Q2 step
+
+template <typename T>
+__global__ void __launch_bounds__(256) step1d_kernel(const StepArgs<T> a)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.nx) return;
+    T f[2][3];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        int si = q == 0 ? i + 1 : i - 1;      // velocity -lambda pulls from i+1, +lambda from i-1
+        const T* g = nullptr;
+        if (si < 0 || si >= a.nx) {
+            const int side = si < 0 ? 0 : 1;
+            const int kind = a.bc[side];
+            if (kind == BC_DIRICHLET) g = a.ghost + side * GHOST_STRIDE + q * 3;
+            else if (kind == BC_PERIODIC) si = si < 0 ? si + a.nx : si - a.nx;
+            else si = si < 0 ? 0 : a.nx - 1;
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) f[q][k] = g ? g[k] : a.src[(q * 3 + k) * a.N + si];
+    }
+    T U[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) U[k] = f[0][k] + f[1][k];
+    T e[2][3];
+    equilibria1d<T>(U, a.gm1, a.c, e);
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) a.dst[(q * 3 + k) * a.N + i] = a.om1 * f[q][k] + a.om * e[q][k];
+}
+
+}  // namespace lbrs

@@ -1,0 +1,334 @@
+// FP64 kernels of the LBRS solver: the FP64 time step and every helper whose
+// arithmetic is FP64 whatever the storage precision (initial equilibria,
+// Dirichlet ghost tables, moments read-out, diagnostics).
+//
+// Compiled with -fmad=false: no FMA contraction, IEEE division and square
+// root, so each expression rounds as written.
+#include <math.h>
+
+#include "lbrs_kernels.cuh"
+#include "lbrs_launch.h"
+
+namespace lbrs {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kDiagBlocks = 608;   // 4 x 152 SMs; fixed so the reduction order never changes
+
+int grid_for(int64_t n)
+{
+    int64_t b = (n + kThreads - 1) / kThreads;
+    const int64_t cap = 152 * 16;
+    if (b > cap) b = cap;
+    return b < 1 ? 1 : (int)b;
+}
+
+template <int LAT>
+struct Dims;
+template <>
+struct Dims<LAT_D2Q4> {
+    static constexpr int Q = 4, K = 4;
+};
+template <>
+struct Dims<LAT_D1Q2> {
+    static constexpr int Q = 2, K = 3;
+};
+
+// f^eq in FP64 for either lattice, e[q*K + k]
+template <int LAT>
+__device__ __forceinline__ void equilibria_flat(const double* U, double gm1, double c, double* e)
+{
+    if constexpr (LAT == LAT_D2Q4) {
+        double t[4][4];
+        equilibria2d<double>(U, gm1, c, t);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) e[q * 4 + k] = t[q][k];
+    } else {
+        double t[2][3];
+        equilibria1d<double>(U, gm1, c, t);
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) e[q * 3 + k] = t[q][k];
+    }
+}
+
+template <int LAT>
+__device__ __forceinline__ void prim_to_cons(const double* w, double gamma, double* U)
+{
+    if constexpr (LAT == LAT_D2Q4) prim_to_cons2d(w, gamma, U);
+    else prim_to_cons1d(w, gamma, U);
+}
+
+template <typename Ts, int LAT>
+__global__ void ghost_kernel(GhostSpec g, double gamma, double c, Ts* ghost)
+{
+    constexpr int Q = Dims<LAT>::Q, K = Dims<LAT>::K;
+    const int side = threadIdx.x;
+    if (side >= 4) return;
+    double e[16];
+    for (int n = 0; n < GHOST_STRIDE; ++n) e[n] = 0.0;
+    if (g.kind[side] == BC_DIRICHLET) {
+        double U[4];
+        prim_to_cons<LAT>(g.prim[side], gamma, U);
+        equilibria_flat<LAT>(U, gamma - 1.0, c, e);
+    }
+    for (int n = 0; n < Q * K; ++n) ghost[side * GHOST_STRIDE + n] = (Ts)e[n];
+    for (int n = Q * K; n < GHOST_STRIDE; ++n) ghost[side * GHOST_STRIDE + n] = (Ts)0;
+}
+
+template <typename Tin, typename Ts, int LAT>
+__global__ void __launch_bounds__(kThreads) set_state_kernel(const Tin* __restrict__ W, Ts* __restrict__ fs,
+                                                             int64_t N, int kind, double gamma, double c)
+{
+    constexpr int Q = Dims<LAT>::Q, K = Dims<LAT>::K;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        double w[4], U[4], e[16];
+#pragma unroll
+        for (int k = 0; k < K; ++k) w[k] = (double)W[k * N + i];
+        if (kind == KIND_PRIMITIVE) {
+            prim_to_cons<LAT>(w, gamma, U);
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; ++k) U[k] = w[k];
+        }
+        equilibria_flat<LAT>(U, gamma - 1.0, c, e);
+#pragma unroll
+        for (int n = 0; n < Q * K; ++n) fs[n * N + i] = (Ts)e[n];
+    }
+}
+
+template <typename Ts, typename To, int LAT>
+__global__ void __launch_bounds__(kThreads) moments_kernel(const Ts* __restrict__ fs, To* __restrict__ U, int64_t N)
+{
+    constexpr int Q = Dims<LAT>::Q, K = Dims<LAT>::K;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double s = (double)fs[(0 * K + k) * N + i];
+#pragma unroll
+            for (int q = 1; q < Q; ++q) s += (double)fs[(q * K + k) * N + i];
+            U[k * N + i] = (To)s;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- diagnostics
+
+struct DiagAcc {
+    double tot[4];
+    double min_rho, min_p, max_lam, nbad, nsub;
+};
+
+__device__ __forceinline__ void diag_combine(DiagAcc& a, const DiagAcc& b)
+{
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a.tot[k] += b.tot[k];
+    a.min_rho = fmin(a.min_rho, b.min_rho);
+    a.min_p = fmin(a.min_p, b.min_p);
+    a.max_lam = fmax(a.max_lam, b.max_lam);
+    a.nbad += b.nbad;
+    a.nsub += b.nsub;
+}
+
+__device__ __forceinline__ DiagAcc diag_shfl_down(const DiagAcc& a, int off)
+{
+    DiagAcc b;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) b.tot[k] = __shfl_down_sync(0xffffffffu, a.tot[k], off);
+    b.min_rho = __shfl_down_sync(0xffffffffu, a.min_rho, off);
+    b.min_p = __shfl_down_sync(0xffffffffu, a.min_p, off);
+    b.max_lam = __shfl_down_sync(0xffffffffu, a.max_lam, off);
+    b.nbad = __shfl_down_sync(0xffffffffu, a.nbad, off);
+    b.nsub = __shfl_down_sync(0xffffffffu, a.nsub, off);
+    return b;
+}
+
+// Per-cell checks of Sections II.A/II.D: rho > 0, p > 0, finite moments, and
+// the local bound |u| + a (1-D) or max(|u+v|, |u-v|) + sqrt(2) a (2-D) <= lambda.
+template <typename Ts, int LAT>
+__global__ void __launch_bounds__(kThreads) diag_partial_kernel(const Ts* __restrict__ fs, int64_t N, double gamma,
+                                                                double lambda, double* __restrict__ partials)
+{
+    constexpr int Q = Dims<LAT>::Q, K = Dims<LAT>::K;
+    DiagAcc acc;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc.tot[k] = 0.0;
+    acc.min_rho = acc.min_p = INFINITY;
+    acc.max_lam = 0.0;
+    acc.nbad = acc.nsub = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        double U[4] = {0.0, 0.0, 0.0, 0.0};
+        bool finite = true;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double s = (double)fs[(0 * K + k) * N + i];
+#pragma unroll
+            for (int q = 1; q < Q; ++q) s += (double)fs[(q * K + k) * N + i];
+            U[k] = s;
+            acc.tot[k] += s;
+            finite = finite && isfinite(s);
+        }
+        double p, lam;
+        if constexpr (LAT == LAT_D2Q4) {
+            const double u = U[1] / U[0], v = U[2] / U[0];
+            p = (gamma - 1.0) * (U[3] - 0.5 * (U[1] * u + U[2] * v));
+            const double s1 = fabs(u + v), s2 = fabs(u - v);
+            lam = (s1 > s2 ? s1 : s2) + sqrt(2.0) * sqrt(gamma * p / U[0]);
+        } else {
+            const double u = U[1] / U[0];
+            p = (gamma - 1.0) * (U[2] - 0.5 * (U[1] * u));
+            lam = fabs(u) + sqrt(gamma * p / U[0]);
+        }
+        if (finite) {
+            acc.min_rho = fmin(acc.min_rho, U[0]);
+            acc.min_p = fmin(acc.min_p, p);
+        }
+        if (!finite || !(U[0] > 0.0) || !(p > 0.0)) {
+            acc.nbad += 1.0;
+        } else {
+            acc.max_lam = fmax(acc.max_lam, lam);
+            if (lam > lambda) acc.nsub += 1.0;
+        }
+    }
+    // warp, then block, in a fixed order
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) diag_combine(acc, diag_shfl_down(acc, off));
+    __shared__ DiagAcc warp_acc[kThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) warp_acc[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        DiagAcc b = warp_acc[0];
+        for (int w = 1; w < kThreads / 32; ++w) diag_combine(b, warp_acc[w]);
+        double* out = partials + (int64_t)blockIdx.x * DIAG_W;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) out[k] = b.tot[k];
+        out[4] = b.min_rho;
+        out[5] = b.min_p;
+        out[6] = b.max_lam;
+        out[7] = b.nbad;
+        out[8] = b.nsub;
+        out[9] = 0.0;
+    }
+}
+
+__global__ void diag_final_kernel(const double* __restrict__ partials, int nblocks, double cell_volume,
+                                  double* __restrict__ out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double tot[4] = {0.0, 0.0, 0.0, 0.0};
+    double mn_r = INFINITY, mn_p = INFINITY, mx_l = 0.0, nb = 0.0, ns = 0.0;
+    for (int b = 0; b < nblocks; ++b) {
+        const double* p = partials + (int64_t)b * DIAG_W;
+        for (int k = 0; k < 4; ++k) tot[k] += p[k];
+        mn_r = fmin(mn_r, p[4]);
+        mn_p = fmin(mn_p, p[5]);
+        mx_l = fmax(mx_l, p[6]);
+        nb += p[7];
+        ns += p[8];
+    }
+    for (int k = 0; k < 4; ++k) out[k] = tot[k] * cell_volume;
+    out[4] = mn_r;
+    out[5] = mn_p;
+    out[6] = mx_l;
+    out[7] = nb;
+    out[8] = ns;
+    out[9] = 0.0;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+
+cudaError_t launch_step_f64(int lattice, const StepArgs<double>& a, cudaStream_t s)
+{
+    if (lattice == LAT_D2Q4) {
+        const dim3 block(128, 2);
+        unsigned gy = (unsigned)((a.ny + block.y - 1) / block.y);
+        const dim3 grid((unsigned)((a.nx + block.x - 1) / block.x), gy);
+        step2d_kernel<double><<<grid, block, 0, s>>>(a);
+    } else {
+        step1d_kernel<double><<<(unsigned)((a.nx + 255) / 256), 256, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ghost(int lattice, int storage_f64, const GhostSpec& g, double gamma, double c, void* ghost,
+                         cudaStream_t s)
+{
+    if (lattice == LAT_D2Q4) {
+        if (storage_f64) ghost_kernel<double, LAT_D2Q4><<<1, 32, 0, s>>>(g, gamma, c, (double*)ghost);
+        else ghost_kernel<float, LAT_D2Q4><<<1, 32, 0, s>>>(g, gamma, c, (float*)ghost);
+    } else {
+        if (storage_f64) ghost_kernel<double, LAT_D1Q2><<<1, 32, 0, s>>>(g, gamma, c, (double*)ghost);
+        else ghost_kernel<float, LAT_D1Q2><<<1, 32, 0, s>>>(g, gamma, c, (float*)ghost);
+    }
+    return cudaGetLastError();
+}
+
+template <int LAT>
+static void set_state_dispatch(int storage_f64, const void* W, int w_dtype, int kind, void* fs, int64_t N,
+                               double gamma, double c, cudaStream_t s)
+{
+    const int g = grid_for(N);
+    if (storage_f64) {
+        if (w_dtype == 0) set_state_kernel<double, double, LAT><<<g, kThreads, 0, s>>>((const double*)W, (double*)fs, N, kind, gamma, c);
+        else set_state_kernel<float, double, LAT><<<g, kThreads, 0, s>>>((const float*)W, (double*)fs, N, kind, gamma, c);
+    } else {
+        if (w_dtype == 0) set_state_kernel<double, float, LAT><<<g, kThreads, 0, s>>>((const double*)W, (float*)fs, N, kind, gamma, c);
+        else set_state_kernel<float, float, LAT><<<g, kThreads, 0, s>>>((const float*)W, (float*)fs, N, kind, gamma, c);
+    }
+}
+
+cudaError_t launch_set_state(int lattice, int storage_f64, const void* W, int w_dtype, int kind, void* fs,
+                             int64_t N, double gamma, double c, cudaStream_t s)
+{
+    if (lattice == LAT_D2Q4) set_state_dispatch<LAT_D2Q4>(storage_f64, W, w_dtype, kind, fs, N, gamma, c, s);
+    else set_state_dispatch<LAT_D1Q2>(storage_f64, W, w_dtype, kind, fs, N, gamma, c, s);
+    return cudaGetLastError();
+}
+
+template <int LAT>
+static void moments_dispatch(int storage_f64, const void* fs, void* U, int out_dtype, int64_t N, cudaStream_t s)
+{
+    const int g = grid_for(N);
+    if (storage_f64) {
+        if (out_dtype == 0) moments_kernel<double, double, LAT><<<g, kThreads, 0, s>>>((const double*)fs, (double*)U, N);
+        else moments_kernel<double, float, LAT><<<g, kThreads, 0, s>>>((const double*)fs, (float*)U, N);
+    } else {
+        if (out_dtype == 0) moments_kernel<float, double, LAT><<<g, kThreads, 0, s>>>((const float*)fs, (double*)U, N);
+        else moments_kernel<float, float, LAT><<<g, kThreads, 0, s>>>((const float*)fs, (float*)U, N);
+    }
+}
+
+cudaError_t launch_moments(int lattice, int storage_f64, const void* fs, void* U, int out_dtype, int64_t N,
+                           cudaStream_t s)
+{
+    if (lattice == LAT_D2Q4) moments_dispatch<LAT_D2Q4>(storage_f64, fs, U, out_dtype, N, s);
+    else moments_dispatch<LAT_D1Q2>(storage_f64, fs, U, out_dtype, N, s);
+    return cudaGetLastError();
+}
+
+int diag_blocks() { return kDiagBlocks; }
+
+cudaError_t launch_diag(int lattice, int storage_f64, const void* fs, int64_t N, double gamma, double lambda,
+                        double cell_volume, double* partials, double* out, cudaStream_t s)
+{
+    if (lattice == LAT_D2Q4) {
+        if (storage_f64) diag_partial_kernel<double, LAT_D2Q4><<<kDiagBlocks, kThreads, 0, s>>>((const double*)fs, N, gamma, lambda, partials);
+        else diag_partial_kernel<float, LAT_D2Q4><<<kDiagBlocks, kThreads, 0, s>>>((const float*)fs, N, gamma, lambda, partials);
+    } else {
+        if (storage_f64) diag_partial_kernel<double, LAT_D1Q2><<<kDiagBlocks, kThreads, 0, s>>>((const double*)fs, N, gamma, lambda, partials);
+        else diag_partial_kernel<float, LAT_D1Q2><<<kDiagBlocks, kThreads, 0, s>>>((const float*)fs, N, gamma, lambda, partials);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    diag_final_kernel<<<1, 32, 0, s>>>(partials, kDiagBlocks, cell_volume, out);
+    return cudaGetLastError();
+}
+
+}  // namespace lbrs

@@ -1,0 +1,44 @@
+// Host-side launchers of the LBRS kernels (internal to the library).
+//
+// The FP64 step and every FP64-arithmetic helper kernel live in
+// lbrs_kernels_f64.cu (compiled without FMA contraction); the FP32 step lives
+// in lbrs_kernels_f32.cu.  The runtime (lbrs_runtime.cu) calls only these.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbrs {
+
+template <typename T>
+struct StepArgs;
+
+// One time step src -> dst.  lattice: LAT_D1Q2 / LAT_D2Q4.
+cudaError_t launch_step_f64(int lattice, const StepArgs<double>& a, cudaStream_t s);
+cudaError_t launch_step_f32(int lattice, const StepArgs<float>& a, cudaStream_t s);
+
+// Dirichlet ghost tables: ghost[side][q*K + k] = f^eq(U(prim[side])) for every
+// side whose kind is DIRICHLET, computed in FP64 and rounded to the storage type.
+struct GhostSpec {
+    double prim[4][4];
+    int kind[4];
+};
+cudaError_t launch_ghost(int lattice, int storage_f64, const GhostSpec& g, double gamma, double c, void* ghost,
+                         cudaStream_t s);
+
+// f = f^eq(U(W)) for every cell; W is [K][N] of w_dtype (0 f64, 1 f32), conserved or primitive.
+cudaError_t launch_set_state(int lattice, int storage_f64, const void* W, int w_dtype, int kind, void* fs,
+                             int64_t N, double gamma, double c, cudaStream_t s);
+
+// U[k][c] = sum_q fs[q][k][c] in FP64, written as out_dtype (0 f64, 1 f32).
+cudaError_t launch_moments(int lattice, int storage_f64, const void* fs, void* U, int out_dtype, int64_t N,
+                           cudaStream_t s);
+
+// Fixed-order FP64 diagnostics: nblocks partial records of DIAG_W doubles, then
+// one finalising pass into out[DIAG_W] = totals[4], min_rho, min_p,
+// max_lambda_local, n_nonphysical, n_subchar, (unused).
+int diag_blocks();
+cudaError_t launch_diag(int lattice, int storage_f64, const void* fs, int64_t N, double gamma, double lambda,
+                        double cell_volume, double* partials, double* out, cudaStream_t s);
+
+}  // namespace lbrs

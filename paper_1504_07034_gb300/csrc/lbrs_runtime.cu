@@ -1,0 +1,430 @@
+// Host runtime of the LBRS solver: the C ABI declared in include/lbrs.h.
+//
+// Owns nothing on the device: the caller's workspace is carved into two
+// ping-pong distribution buffers, the Dirichlet ghost tables and the
+// diagnostics scratch.  Steps are enqueued on the caller's stream; runs of
+// many steps replay a CUDA graph of kGraphSteps step kernels (captured once per
+// context and buffer parity on a private stream).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <cuda_runtime.h>
+
+#include "lbrs.h"
+#include "lbrs_kernels.cuh"
+#include "lbrs_launch.h"
+
+using namespace lbrs;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kGraphSteps = 32;   // even: a graph returns the buffers to their parity
+
+thread_local char g_err[512] = "";
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+    size_t f_bytes, f0, f1, ghost, partials, diag_out, total;
+};
+
+int lattice_q(int lat) { return lat == LBRS_D2Q4 ? 4 : 2; }
+int lattice_k(int lat) { return lat == LBRS_D2Q4 ? 4 : 3; }
+
+Layout layout_of(const lbrs_config* c)
+{
+    Layout L;
+    const size_t elem = c->precision == LBRS_F64 ? 8 : 4;
+    const size_t N = (size_t)c->nx * (size_t)c->ny;
+    L.f_bytes = N * (size_t)(lattice_q(c->lattice) * lattice_k(c->lattice)) * elem;
+    size_t off = 0;
+    L.f0 = off;
+    off += align_up(L.f_bytes);
+    L.f1 = off;
+    off += align_up(L.f_bytes);
+    L.ghost = off;
+    off += align_up(4 * GHOST_STRIDE * elem);
+    L.partials = off;
+    off += align_up((size_t)diag_blocks() * DIAG_W * sizeof(double));
+    L.diag_out = off;
+    off += align_up(DIAG_W * sizeof(double));
+    L.total = off;
+    return L;
+}
+
+}  // namespace
+
+struct lbrs_ctx {
+    lbrs_config cfg;
+    Layout L;
+    int lattice, f64, Q, K;
+    int64_t N;
+    char* ws;
+    char* f[2];
+    int cur;                 // index of the buffer holding the current state
+    cudaStream_t stream;
+    bool has_state;
+    int64_t step;
+    int64_t launches;
+    double c;                // 1/(4 lambda) in 2-D, 1/(2 lambda) in 1-D
+    cudaStream_t cap_stream;
+    cudaGraphExec_t graph[2];
+    char err[512];
+};
+
+namespace {
+
+lbrs_status fail(lbrs_ctx* ctx, lbrs_status s, const char* fmt, ...)
+{
+    char* buf = ctx ? ctx->err : g_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, 512, fmt, ap);
+    va_end(ap);
+    if (ctx) snprintf(g_err, sizeof g_err, "%s", ctx->err);
+    return s;
+}
+
+lbrs_status cuda_fail(lbrs_ctx* ctx, cudaError_t e, const char* what)
+{
+    return fail(ctx, LBRS_ECUDA, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+#define LBRS_CUDA(ctx, call)                                        \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);  \
+    } while (0)
+
+bool finite_pos(double x) { return isfinite(x) && x > 0.0; }
+
+lbrs_status validate(const lbrs_config* c)
+{
+    if (!c) return fail(nullptr, LBRS_EINVAL, "config is NULL");
+    if (c->struct_size != sizeof(lbrs_config))
+        return fail(nullptr, LBRS_EINVAL, "config.struct_size %u != sizeof(lbrs_config) %zu", c->struct_size,
+                    sizeof(lbrs_config));
+    if (c->lattice != LBRS_D1Q2 && c->lattice != LBRS_D2Q4)
+        return fail(nullptr, LBRS_EINVAL, "unknown lattice %d", c->lattice);
+    if (c->precision != LBRS_F64 && c->precision != LBRS_F32)
+        return fail(nullptr, LBRS_EINVAL, "unknown precision %d", c->precision);
+    if (c->nx < 1 || c->ny < 1) return fail(nullptr, LBRS_EINVAL, "grid must have nx, ny >= 1");
+    if (c->nx > (1LL << 30)) return fail(nullptr, LBRS_EINVAL, "nx too large (max 2^30)");
+    if (c->lattice == LBRS_D1Q2 && c->ny != 1) return fail(nullptr, LBRS_EINVAL, "D1Q2 needs ny == 1");
+    if (c->lattice == LBRS_D2Q4 && c->ny > 2LL * 65535) return fail(nullptr, LBRS_EINVAL, "ny too large (max 131070)");
+    if (!(c->gamma > 1.0) || !isfinite(c->gamma)) return fail(nullptr, LBRS_EINVAL, "gamma must be > 1");
+    if (!finite_pos(c->lambda)) return fail(nullptr, LBRS_EINVAL, "lambda must be positive");
+    if (!(c->omega > 0.0 && c->omega < 2.0)) return fail(nullptr, LBRS_EINVAL, "omega must lie in (0, 2)");
+    if (!finite_pos(c->dx)) return fail(nullptr, LBRS_EINVAL, "dx must be positive");
+    const int sides = c->lattice == LBRS_D2Q4 ? 4 : 2;
+    for (int s = 0; s < sides; ++s) {
+        const int kind = c->bc[s].kind;
+        if (kind < LBRS_BC_PERIODIC || kind > LBRS_BC_WALL)
+            return fail(nullptr, LBRS_EINVAL, "side %d: unknown boundary kind %d", s, kind);
+        if (kind == LBRS_BC_WALL && (c->lattice != LBRS_D2Q4 || s < 2))
+            return fail(nullptr, LBRS_EINVAL, "side %d: walls are defined on the y sides of D2Q4 only", s);
+        if (kind == LBRS_BC_PERIODIC && c->bc[s ^ 1].kind != LBRS_BC_PERIODIC)
+            return fail(nullptr, LBRS_EINVAL, "side %d: periodic must pair with periodic", s);
+        if (kind == LBRS_BC_DIRICHLET) {
+            const double* w = c->bc[s].prim;
+            const int K = lattice_k(c->lattice);
+            for (int k = 0; k < K; ++k)
+                if (!isfinite(w[k])) return fail(nullptr, LBRS_EINVAL, "side %d: non-finite Dirichlet state", s);
+            if (!(w[0] > 0.0) || !(w[K - 1] > 0.0))
+                return fail(nullptr, LBRS_EINVAL, "side %d: Dirichlet state needs rho > 0 and p > 0", s);
+        }
+    }
+    if (c->lattice == LBRS_D2Q4 && (c->bc[2].kind == LBRS_BC_WALL || c->bc[3].kind == LBRS_BC_WALL) && c->ny < 2)
+        return fail(nullptr, LBRS_EINVAL, "walls need ny >= 2");
+    return LBRS_OK;
+}
+
+template <typename T>
+StepArgs<T> step_args(const lbrs_ctx* ctx, int from)
+{
+    StepArgs<T> a;
+    a.src = (const T*)ctx->f[from];
+    a.dst = (T*)ctx->f[from ^ 1];
+    a.ghost = (const T*)(ctx->ws + ctx->L.ghost);
+    a.N = ctx->N;
+    a.nx = (int)ctx->cfg.nx;
+    a.ny = (int)ctx->cfg.ny;
+    for (int s = 0; s < 4; ++s) a.bc[s] = ctx->cfg.bc[s].kind;
+    a.om = (T)ctx->cfg.omega;
+    a.om1 = (T)(1.0 - ctx->cfg.omega);
+    a.c = (T)ctx->c;
+    a.gm1 = (T)(ctx->cfg.gamma - 1.0);
+    return a;
+}
+
+cudaError_t launch_one_step(lbrs_ctx* ctx, int from, cudaStream_t s)
+{
+    const int lat = ctx->lattice == LBRS_D2Q4 ? LAT_D2Q4 : LAT_D1Q2;
+    if (ctx->f64) return launch_step_f64(lat, step_args<double>(ctx, from), s);
+    return launch_step_f32(lat, step_args<float>(ctx, from), s);
+}
+
+// Capture kGraphSteps step kernels starting from buffer `from` into graph[from].
+lbrs_status ensure_graph(lbrs_ctx* ctx, int from)
+{
+    if (ctx->graph[from]) return LBRS_OK;
+    if (!ctx->cap_stream) LBRS_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    LBRS_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t le = cudaSuccess;
+    int b = from;
+    for (int n = 0; n < kGraphSteps && le == cudaSuccess; ++n) {
+        le = launch_one_step(ctx, b, ctx->cap_stream);
+        b ^= 1;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(ctx->cap_stream, &g);
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(ctx, le, "step launch during graph capture");
+    }
+    if (ee != cudaSuccess) return cuda_fail(ctx, ee, "cudaStreamEndCapture");
+    cudaError_t ie = cudaGraphInstantiate(&ctx->graph[from], g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+        ctx->graph[from] = nullptr;
+        return cuda_fail(ctx, ie, "cudaGraphInstantiate");
+    }
+    return LBRS_OK;
+}
+
+size_t field_bytes(const lbrs_ctx* ctx, int dtype) { return (size_t)ctx->K * (size_t)ctx->N * (dtype == LBRS_F64 ? 8 : 4); }
+
+}  // namespace
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+int lbrs_abi_version(void) { return LBRS_ABI_VERSION; }
+
+const char* lbrs_status_string(lbrs_status s)
+{
+    switch (s) {
+        case LBRS_OK: return "LBRS_OK";
+        case LBRS_EINVAL: return "LBRS_EINVAL";
+        case LBRS_ENOMEM: return "LBRS_ENOMEM";
+        case LBRS_ECUDA: return "LBRS_ECUDA";
+        case LBRS_ENONPHYS: return "LBRS_ENONPHYS";
+        case LBRS_ESUBCHAR: return "LBRS_ESUBCHAR";
+        case LBRS_ETIMEOUT: return "LBRS_ETIMEOUT";
+        case LBRS_ESTATE: return "LBRS_ESTATE";
+    }
+    return "LBRS_UNKNOWN";
+}
+
+lbrs_status lbrs_workspace_size(const lbrs_config* cfg, size_t* bytes)
+{
+    if (!bytes) return fail(nullptr, LBRS_EINVAL, "bytes is NULL");
+    lbrs_status st = validate(cfg);
+    if (st != LBRS_OK) return st;
+    *bytes = layout_of(cfg).total;
+    return LBRS_OK;
+}
+
+lbrs_status lbrs_create(const lbrs_config* cfg, void* d_workspace, size_t bytes, lbrs_ctx** out)
+{
+    if (!out) return fail(nullptr, LBRS_EINVAL, "out is NULL");
+    *out = nullptr;
+    lbrs_status st = validate(cfg);
+    if (st != LBRS_OK) return st;
+    const Layout L = layout_of(cfg);
+    if (!d_workspace) return fail(nullptr, LBRS_EINVAL, "workspace is NULL");
+    if ((uintptr_t)d_workspace % kAlign) return fail(nullptr, LBRS_EINVAL, "workspace must be 256-byte aligned");
+    if (bytes < L.total)
+        return fail(nullptr, LBRS_ENOMEM, "workspace has %zu bytes, needs %zu", bytes, L.total);
+
+    lbrs_ctx* ctx = (lbrs_ctx*)calloc(1, sizeof(lbrs_ctx));
+    if (!ctx) return fail(nullptr, LBRS_ENOMEM, "host allocation of the context failed");
+    ctx->cfg = *cfg;
+    ctx->L = L;
+    ctx->lattice = cfg->lattice;
+    ctx->f64 = cfg->precision == LBRS_F64;
+    ctx->Q = lattice_q(cfg->lattice);
+    ctx->K = lattice_k(cfg->lattice);
+    ctx->N = cfg->nx * cfg->ny;
+    ctx->ws = (char*)d_workspace;
+    ctx->f[0] = ctx->ws + L.f0;
+    ctx->f[1] = ctx->ws + L.f1;
+    ctx->stream = (cudaStream_t)cfg->cuda_stream;
+    ctx->c = cfg->lattice == LBRS_D2Q4 ? 1.0 / (4.0 * cfg->lambda) : 1.0 / (2.0 * cfg->lambda);
+
+    GhostSpec g;
+    memset(&g, 0, sizeof g);
+    for (int s = 0; s < 4; ++s) {
+        g.kind[s] = cfg->bc[s].kind;
+        for (int k = 0; k < 4; ++k) g.prim[s][k] = cfg->bc[s].prim[k];
+    }
+    const int lat = cfg->lattice == LBRS_D2Q4 ? LAT_D2Q4 : LAT_D1Q2;
+    cudaError_t e = launch_ghost(lat, ctx->f64, g, cfg->gamma, ctx->c, ctx->ws + L.ghost, ctx->stream);
+    if (e != cudaSuccess) {
+        lbrs_status s = cuda_fail(nullptr, e, "ghost-table kernel");
+        free(ctx);
+        return s;
+    }
+    ctx->launches = 1;
+    *out = ctx;
+    return LBRS_OK;
+}
+
+void lbrs_destroy(lbrs_ctx* ctx)
+{
+    if (!ctx) return;
+    for (int b = 0; b < 2; ++b)
+        if (ctx->graph[b]) cudaGraphExecDestroy(ctx->graph[b]);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    free(ctx);
+}
+
+lbrs_status lbrs_set_state(lbrs_ctx* ctx, const void* W, int on_device, int dtype, int kind)
+{
+    if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
+    if (!W) return fail(ctx, LBRS_EINVAL, "W is NULL");
+    if (dtype != LBRS_F64 && dtype != LBRS_F32) return fail(ctx, LBRS_EINVAL, "dtype must be LBRS_F64 or LBRS_F32");
+    if (kind != LBRS_CONSERVED && kind != LBRS_PRIMITIVE) return fail(ctx, LBRS_EINVAL, "unknown state kind %d", kind);
+    const void* src = W;
+    if (!on_device) {
+        // stage through the idle buffer: K*N*8 bytes always fit in Q*K*N*elem
+        char* stage = ctx->f[ctx->cur ^ 1];
+        LBRS_CUDA(ctx, cudaMemcpyAsync(stage, W, field_bytes(ctx, dtype), cudaMemcpyHostToDevice, ctx->stream));
+        src = stage;
+    }
+    const int lat = ctx->lattice == LBRS_D2Q4 ? LAT_D2Q4 : LAT_D1Q2;
+    LBRS_CUDA(ctx, launch_set_state(lat, ctx->f64, src, dtype == LBRS_F32, kind, ctx->f[ctx->cur], ctx->N,
+                                    ctx->cfg.gamma, ctx->c, ctx->stream));
+    ctx->launches += 1;
+    if (!on_device) LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));   // host W is consumed on return
+    ctx->has_state = true;
+    ctx->step = 0;
+    return LBRS_OK;
+}
+
+lbrs_status lbrs_step(lbrs_ctx* ctx, int64_t n)
+{
+    if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
+    if (n < 0) return fail(ctx, LBRS_EINVAL, "negative step count");
+    if (!ctx->has_state) return fail(ctx, LBRS_ESTATE, "no state set");
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    LBRS_CUDA(ctx, cudaStreamIsCapturing(ctx->stream, &cap));
+    int64_t left = n;
+    if (cap == cudaStreamCaptureStatusNone && n >= 2 * kGraphSteps) {
+        lbrs_status st = ensure_graph(ctx, ctx->cur);
+        if (st != LBRS_OK) return st;
+        while (left >= kGraphSteps) {
+            LBRS_CUDA(ctx, cudaGraphLaunch(ctx->graph[ctx->cur], ctx->stream));
+            left -= kGraphSteps;
+            ctx->step += kGraphSteps;
+            ctx->launches += kGraphSteps;
+        }
+    }
+    for (; left > 0; --left) {
+        LBRS_CUDA(ctx, launch_one_step(ctx, ctx->cur, ctx->stream));
+        ctx->cur ^= 1;
+        ctx->step += 1;
+        ctx->launches += 1;
+    }
+    return LBRS_OK;
+}
+
+lbrs_status lbrs_sync(lbrs_ctx* ctx)
+{
+    if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
+    LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return LBRS_OK;
+}
+
+lbrs_status lbrs_moments(lbrs_ctx* ctx, void* U_out, int on_device, int dtype)
+{
+    if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
+    if (!U_out) return fail(ctx, LBRS_EINVAL, "U_out is NULL");
+    if (dtype != LBRS_F64 && dtype != LBRS_F32) return fail(ctx, LBRS_EINVAL, "dtype must be LBRS_F64 or LBRS_F32");
+    if (!ctx->has_state) return fail(ctx, LBRS_ESTATE, "no state set");
+    const int lat = ctx->lattice == LBRS_D2Q4 ? LAT_D2Q4 : LAT_D1Q2;
+    void* dst = on_device ? U_out : (void*)ctx->f[ctx->cur ^ 1];
+    LBRS_CUDA(ctx, launch_moments(lat, ctx->f64, ctx->f[ctx->cur], dst, dtype == LBRS_F32, ctx->N, ctx->stream));
+    ctx->launches += 1;
+    if (!on_device) {
+        LBRS_CUDA(ctx, cudaMemcpyAsync(U_out, dst, field_bytes(ctx, dtype), cudaMemcpyDeviceToHost, ctx->stream));
+        LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    return LBRS_OK;
+}
+
+lbrs_status lbrs_diagnostics(lbrs_ctx* ctx, lbrs_diag* out)
+{
+    if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
+    if (!out) return fail(ctx, LBRS_EINVAL, "out is NULL");
+    if (!ctx->has_state) return fail(ctx, LBRS_ESTATE, "no state set");
+    const int lat = ctx->lattice == LBRS_D2Q4 ? LAT_D2Q4 : LAT_D1Q2;
+    const double vol = ctx->lattice == LBRS_D2Q4 ? ctx->cfg.dx * ctx->cfg.dx : ctx->cfg.dx;
+    double* partials = (double*)(ctx->ws + ctx->L.partials);
+    double* dout = (double*)(ctx->ws + ctx->L.diag_out);
+    LBRS_CUDA(ctx, launch_diag(lat, ctx->f64, ctx->f[ctx->cur], ctx->N, ctx->cfg.gamma, ctx->cfg.lambda, vol,
+                               partials, dout, ctx->stream));
+    ctx->launches += 2;
+    double h[DIAG_W];
+    LBRS_CUDA(ctx, cudaMemcpyAsync(h, dout, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+    LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    memset(out, 0, sizeof *out);
+    for (int k = 0; k < ctx->K; ++k) out->totals[k] = h[k];
+    out->min_rho = h[4];
+    out->min_p = h[5];
+    out->max_lambda_local = h[6];
+    out->n_nonphysical = (int64_t)h[7];
+    out->n_subchar = (int64_t)h[8];
+    if (out->n_nonphysical > 0) return fail(ctx, LBRS_ENONPHYS, "%lld non-physical cells at step %lld",
+                                            (long long)out->n_nonphysical, (long long)ctx->step);
+    if (out->n_subchar > 0) return fail(ctx, LBRS_ESUBCHAR, "%lld cells exceed lambda at step %lld",
+                                        (long long)out->n_subchar, (long long)ctx->step);
+    return LBRS_OK;
+}
+
+lbrs_status lbrs_get_distributions(lbrs_ctx* ctx, void* dst, int on_device)
+{
+    if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
+    if (!dst) return fail(ctx, LBRS_EINVAL, "dst is NULL");
+    if (!ctx->has_state) return fail(ctx, LBRS_ESTATE, "no state set");
+    LBRS_CUDA(ctx, cudaMemcpyAsync(dst, ctx->f[ctx->cur], ctx->L.f_bytes,
+                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+    if (!on_device) LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return LBRS_OK;
+}
+
+lbrs_status lbrs_set_distributions(lbrs_ctx* ctx, const void* src, int on_device, int64_t step)
+{
+    if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
+    if (!src) return fail(ctx, LBRS_EINVAL, "src is NULL");
+    if (step < 0) return fail(ctx, LBRS_EINVAL, "negative step");
+    LBRS_CUDA(ctx, cudaMemcpyAsync(ctx->f[ctx->cur], src, ctx->L.f_bytes,
+                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+    if (!on_device) LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->has_state = true;
+    ctx->step = step;
+    return LBRS_OK;
+}
+
+lbrs_status lbrs_step_count(const lbrs_ctx* ctx, int64_t* steps)
+{
+    if (!ctx || !steps) return fail(nullptr, LBRS_EINVAL, "NULL argument");
+    *steps = ctx->step;
+    return LBRS_OK;
+}
+
+lbrs_status lbrs_launch_count(const lbrs_ctx* ctx, int64_t* launches)
+{
+    if (!ctx || !launches) return fail(nullptr, LBRS_EINVAL, "NULL argument");
+    *launches = ctx->launches;
+    return LBRS_OK;
+}
+
+const char* lbrs_last_error(const lbrs_ctx* ctx) { return ctx ? ctx->err : g_err; }
+
+}  // extern "C"

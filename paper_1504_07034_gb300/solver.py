@@ -1,0 +1,176 @@
+"""Python face of the LBRS solver: torch tensors in, C ABI calls out.
+
+``Solver`` owns a torch uint8 workspace on the GPU (PyTorch is only the
+allocator and the stream provider here) and a context of liblbrs.so.  Every
+step of the method runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import abi
+
+_DTYPE_CODE = {torch.float64: abi.LBRS_F64, torch.float32: abi.LBRS_F32,
+               np.dtype(np.float64): abi.LBRS_F64, np.dtype(np.float32): abi.LBRS_F32}
+_PRECISION = {"f64": abi.LBRS_F64, "f32": abi.LBRS_F32}
+
+
+def make_config(lattice: str, nx: int, ny: int, *, gamma: float, lam: float, omega: float, dx: float,
+                bc, precision: str, stream_handle: int) -> abi.lbrs_config:
+    cfg = abi.lbrs_config()
+    cfg.struct_size = ctypes.sizeof(abi.lbrs_config)
+    cfg.lattice = abi.LBRS_D2Q4 if lattice == "d2q4" else abi.LBRS_D1Q2
+    cfg.precision = _PRECISION[precision]
+    cfg.nx, cfg.ny = int(nx), int(ny)
+    cfg.gamma, cfg.lam, cfg.omega, cfg.dx = float(gamma), float(lam), float(omega), float(dx)
+    for s, (kind, state) in enumerate(bc):
+        cfg.bc[s].kind = abi.BC_KINDS[kind]
+        if state is not None:
+            for k, v in enumerate(state):
+                cfg.bc[s].prim[k] = float(v)
+    cfg.cuda_stream = stream_handle or None
+    return cfg
+
+
+class Solver:
+    """One LBRS problem on one GPU.
+
+    lattice   "d1q2" or "d2q4"
+    bc        per side (x-lo, x-hi[, y-lo, y-hi]): (kind, primitive_state_or_None)
+    precision "f64" (plain FP64 path) or "f32" (FP32 distributions)
+    stream    a torch.cuda.Stream (default: the current stream)
+    """
+
+    def __init__(self, lattice: str, nx: int, ny: int = 1, *, lam: float, dx: float, bc, gamma: float = 1.4,
+                 omega: float = 1.0, precision: str = "f32", stream: torch.cuda.Stream | None = None,
+                 device: torch.device | str | None = None):
+        self.lib = abi.load()
+        self.lattice = lattice
+        self.Q, self.K = (4, 4) if lattice == "d2q4" else (2, 3)
+        self.nx, self.ny = int(nx), int(ny)
+        self.precision = precision
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        sides = 4 if lattice == "d2q4" else 2
+        bc = list(bc)
+        if len(bc) < sides:
+            raise ValueError(f"need {sides} boundary conditions")
+        bc = bc + [("periodic", None)] * (4 - len(bc))
+        self.cfg = make_config(lattice, nx, ny, gamma=gamma, lam=lam, omega=omega, dx=dx, bc=bc,
+                               precision=precision, stream_handle=self.stream.cuda_stream)
+        size = ctypes.c_size_t()
+        abi.check(self.lib.lbrs_workspace_size(ctypes.byref(self.cfg), ctypes.byref(size)))
+        self.workspace = torch.empty(size.value, dtype=torch.uint8, device=self.device)
+        ctx = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            abi.check(self.lib.lbrs_create(ctypes.byref(self.cfg), ctypes.c_void_p(self.workspace.data_ptr()),
+                                           size.value, ctypes.byref(ctx)))
+        self.ctx = ctx
+
+    @classmethod
+    def from_workload(cls, wl, precision: str = "f32", stream=None, omega=None):
+        if hasattr(wl, "ny"):
+            return cls("d2q4", wl.nx, wl.ny, lam=wl.lam, dx=wl.dx, bc=wl.bc, gamma=wl.gamma,
+                       omega=wl.omega if omega is None else omega, precision=precision, stream=stream)
+        return cls("d1q2", wl.nx, 1, lam=wl.lam, dx=wl.dx, bc=wl.bc, gamma=wl.gamma,
+                   omega=wl.omega if omega is None else omega, precision=precision, stream=stream)
+
+    # ------------------------------------------------------------------ helpers
+    @property
+    def grid(self):
+        return (self.ny, self.nx) if self.lattice == "d2q4" else (self.nx,)
+
+    @property
+    def storage_dtype(self):
+        return torch.float64 if self.precision == "f64" else torch.float32
+
+    def _check(self, status):
+        return abi.check(status, self.ctx)
+
+    # ------------------------------------------------------------------ C ABI calls
+    def set_state(self, W, primitive: bool = True):
+        """f = f^eq(U0); W of shape (K, *grid): torch tensor (GPU or CPU) or numpy array."""
+        kind = abi.LBRS_PRIMITIVE if primitive else abi.LBRS_CONSERVED
+        if isinstance(W, np.ndarray):
+            W = np.ascontiguousarray(W)
+            if W.dtype not in (np.float64, np.float32):
+                W = W.astype(np.float64)
+            if W.shape != (self.K,) + self.grid:
+                raise ValueError(f"expected shape {(self.K,) + self.grid}, got {W.shape}")
+            self._check(self.lib.lbrs_set_state(self.ctx, ctypes.c_void_p(W.ctypes.data), 0,
+                                                _DTYPE_CODE[W.dtype], kind))
+            return
+        if tuple(W.shape) != (self.K,) + self.grid:
+            raise ValueError(f"expected shape {(self.K,) + self.grid}, got {tuple(W.shape)}")
+        if W.dtype not in (torch.float64, torch.float32):
+            raise TypeError("W must be float64 or float32")
+        W = W.contiguous()
+        on_dev = 1 if W.is_cuda else 0
+        self._check(self.lib.lbrs_set_state(self.ctx, ctypes.c_void_p(W.data_ptr()), on_dev, _DTYPE_CODE[W.dtype],
+                                            kind))
+        self._keep = W  # device input stays referenced until the next call
+
+    def step(self, n: int = 1):
+        self._check(self.lib.lbrs_step(self.ctx, int(n)))
+
+    def sync(self):
+        self._check(self.lib.lbrs_sync(self.ctx))
+
+    def moments(self, dtype=torch.float64, out: torch.Tensor | None = None) -> torch.Tensor:
+        """Conserved fields U (K, *grid); on the GPU unless `out` is a CPU tensor."""
+        if out is None:
+            out = torch.empty((self.K,) + self.grid, dtype=dtype, device=self.device)
+        if tuple(out.shape) != (self.K,) + self.grid or not out.is_contiguous():
+            raise ValueError("out must be a contiguous (K, *grid) tensor")
+        self._check(self.lib.lbrs_moments(self.ctx, ctypes.c_void_p(out.data_ptr()), 1 if out.is_cuda else 0,
+                                          _DTYPE_CODE[out.dtype]))
+        return out
+
+    def diagnostics(self) -> dict:
+        d = abi.lbrs_diag()
+        st = self.lib.lbrs_diagnostics(self.ctx, ctypes.byref(d))
+        if st not in (abi.LBRS_OK, abi.LBRS_ENONPHYS, abi.LBRS_ESUBCHAR):
+            self._check(st)
+        return {"status": abi.status_name(st), "totals": [d.totals[k] for k in range(self.K)],
+                "min_rho": d.min_rho, "min_p": d.min_p, "max_lambda_local": d.max_lambda_local,
+                "n_nonphysical": d.n_nonphysical, "n_subchar": d.n_subchar}
+
+    def get_distributions(self, out: torch.Tensor | None = None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty((self.Q, self.K) + self.grid, dtype=self.storage_dtype, device=self.device)
+        if out.dtype != self.storage_dtype or not out.is_contiguous() or out.numel() != self.Q * self.K * self.nx * self.ny:
+            raise ValueError("out must be a contiguous (Q, K, *grid) tensor of the storage dtype")
+        self._check(self.lib.lbrs_get_distributions(self.ctx, ctypes.c_void_p(out.data_ptr()), 1 if out.is_cuda else 0))
+        return out
+
+    def set_distributions(self, f: torch.Tensor, step: int = 0):
+        if f.dtype != self.storage_dtype or not f.is_contiguous() or f.numel() != self.Q * self.K * self.nx * self.ny:
+            raise ValueError("f must be a contiguous (Q, K, *grid) tensor of the storage dtype")
+        self._check(self.lib.lbrs_set_distributions(self.ctx, ctypes.c_void_p(f.data_ptr()), 1 if f.is_cuda else 0,
+                                                    int(step)))
+
+    @property
+    def step_count(self) -> int:
+        v = ctypes.c_int64()
+        self._check(self.lib.lbrs_step_count(self.ctx, ctypes.byref(v)))
+        return v.value
+
+    @property
+    def launch_count(self) -> int:
+        v = ctypes.c_int64()
+        self._check(self.lib.lbrs_launch_count(self.ctx, ctypes.byref(v)))
+        return v.value
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.lbrs_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
