@@ -160,6 +160,27 @@ lbrs_status lbrs_moments(lbrs_ctx* ctx, void* U_out, int on_device, int dtype);
  * violates the sub-characteristic bound, else OK; *out is filled in every case. */
 lbrs_status lbrs_diagnostics(lbrs_ctx* ctx, lbrs_diag* out);
 
+/* The same diagnostics for callers that cannot allocate device memory: no
+ * context, no workspace, and no cudaMalloc/cudaFree or allocating library call.
+ * The paper has no counterpart; it exists because some callers cannot provide
+ * scratch memory -- code running while a CUDA graph is captured (allocation is
+ * not allowed there), loops that must not stall on the implicit device
+ * synchronisation of cudaMalloc/cudaFree, and processes whose device memory is
+ * fully held by another allocator.
+ *   cfg   the configuration the distributions belong to (lattice, precision,
+ *         nx, ny, gamma, lambda, dx are used; cuda_stream is the stream);
+ *   d_fs  device distributions f[q][k][j][i] in cfg->precision, e.g. from
+ *         lbrs_get_distributions;
+ *   out   host struct, filled as by lbrs_diagnostics (same status rules).
+ * Scratch: a static device array of 320.1 KiB inside the library, held on every
+ * GPU that loads the library until the process exits.  Grids of more than
+ * 33,554,432 cells are rejected with LBRS_EINVAL.  The first call on each
+ * device (made while that device is current) looks up the array's device
+ * address with cudaGetSymbolAddress; make that first call before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race.
+ * Synchronises cfg->cuda_stream. */
+lbrs_status lbrs_diagnostics_noalloc(const lbrs_config* cfg, const void* d_fs, lbrs_diag* out);
+
 /* Copy the raw distributions f[q][k][j][i] (storage precision) out of / into
  * the context, e.g. for checkpoints.  Host transfers synchronise.  set also
  * sets the step counter. */

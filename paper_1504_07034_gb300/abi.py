@@ -73,6 +73,7 @@ SIGNATURES = {
     "lbrs_sync": (ctypes.c_int, [_CTX]),
     "lbrs_moments": (ctypes.c_int, [_CTX, _P, ctypes.c_int, ctypes.c_int]),
     "lbrs_diagnostics": (ctypes.c_int, [_CTX, ctypes.POINTER(lbrs_diag)]),
+    "lbrs_diagnostics_noalloc": (ctypes.c_int, [ctypes.POINTER(lbrs_config), _P, ctypes.POINTER(lbrs_diag)]),
     "lbrs_get_distributions": (ctypes.c_int, [_CTX, _P, ctypes.c_int]),
     "lbrs_set_distributions": (ctypes.c_int, [_CTX, _P, ctypes.c_int, ctypes.c_int64]),
     "lbrs_step_count": (ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_int64)]),

@@ -1,11 +1,12 @@
 """Build the LBRS CUDA library (liblbrs.so) in-tree for sm_103a.
 
-Three translation units compiled in parallel with nvcc, then linked into one
+Four translation units compiled in parallel with nvcc, then linked into one
 shared library with the CUDA runtime linked statically:
 
   csrc/lbrs_kernels_f64.cu  FP64 kernels, -fmad=false (rounding as written)
   csrc/lbrs_kernels_f32.cu  FP32 step kernels
   csrc/lbrs_runtime.cu      host C ABI (include/lbrs.h)
+  csrc/lbrs_noalloc.cu      diagnostics variant with static scratch, -fmad=false
 
 Usage: python -m paper_1504_07034_gb300.build [--force]
 """
@@ -32,6 +33,7 @@ UNITS = {
     "lbrs_kernels_f64.cu": ["-fmad=false"],
     "lbrs_kernels_f32.cu": [],
     "lbrs_runtime.cu": [],
+    "lbrs_noalloc.cu": ["-fmad=false"],
 }
 HEADERS = [CSRC / "lbrs_kernels.cuh", CSRC / "lbrs_launch.h", INCLUDE / "lbrs.h"]
 

@@ -200,6 +200,13 @@ size_t field_bytes(const lbrs_ctx* ctx, int dtype) { return (size_t)ctx->K * (si
 
 }  // namespace
 
+// Shared with other translation units of the library: configuration checks
+// and the thread's last-error text for calls that have no context.
+namespace lbrs {
+lbrs_status validate_config(const lbrs_config* c) { return validate(c); }
+lbrs_status set_error(lbrs_status s, const char* msg) { return fail(nullptr, s, "%s", msg); }
+}  // namespace lbrs
+
 // ====================================================================== C ABI
 
 extern "C" {
