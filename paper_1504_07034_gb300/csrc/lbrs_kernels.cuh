@@ -154,19 +154,23 @@ __device__ __forceinline__ void pull_edge_2d(const StepArgs<T>& a, int i, int j,
         int si = i - SX[q], sj = j - SY[q];
         const int side_y = sj < 0 ? 2 : (sj >= a.ny ? 3 : -1);
         const int side_x = si < 0 ? 0 : (si >= a.nx ? 1 : -1);
-        if (side_y >= 0 && a.bc[side_y] == BC_WALL) {
+        // side kinds by selection, not by a runtime index into the parameter
+        // block (which would force a local-memory copy of it)
+        const int kind_y = side_y == 2 ? a.bc[2] : a.bc[3];
+        const int kind_x = side_x == 0 ? a.bc[0] : a.bc[1];
+        if (side_y >= 0 && kind_y == BC_WALL) {
             if (side_y == 3) wall_top = true; else wall_bottom = true;
             continue;
         }
         const T* g = nullptr;
         if (side_x >= 0) {
-            const int kind = a.bc[side_x];
+            const int kind = kind_x;
             if (kind == BC_DIRICHLET) g = a.ghost + side_x * GHOST_STRIDE + q * 4;
             else if (kind == BC_PERIODIC) si = si < 0 ? si + a.nx : si - a.nx;
             else si = si < 0 ? 0 : a.nx - 1;
         }
         if (!g && side_y >= 0) {
-            const int kind = a.bc[side_y];
+            const int kind = kind_y;
             if (kind == BC_DIRICHLET) g = a.ghost + side_y * GHOST_STRIDE + q * 4;
             else if (kind == BC_PERIODIC) sj = sj < 0 ? sj + a.ny : sj - a.ny;
             else sj = sj < 0 ? 0 : a.ny - 1;
@@ -241,7 +245,7 @@ __global__ void __launch_bounds__(256) step1d_kernel(const StepArgs<T> a)
         const T* g = nullptr;
         if (si < 0 || si >= a.nx) {
             const int side = si < 0 ? 0 : 1;
-            const int kind = a.bc[side];
+            const int kind = side == 0 ? a.bc[0] : a.bc[1];
             if (kind == BC_DIRICHLET) g = a.ghost + side * GHOST_STRIDE + q * 3;
             else if (kind == BC_PERIODIC) si = si < 0 ? si + a.nx : si - a.nx;
             else si = si < 0 ? 0 : a.nx - 1;
