@@ -103,6 +103,10 @@ def lib():
         L.orc_run.restype = ctypes.c_int
         L.orc_totals.argtypes = [P, dp, ctypes.c_double, dp]
         L.orc_max_threads.restype = ctypes.c_int
+        L.orc_adjoint_step.argtypes = [P, dp, dp, dp]
+        L.orc_adjoint_step.restype = ctypes.c_int
+        L.orc_vjp_equilibrium.argtypes = [P, dp, dp, dp]
+        L.orc_vjp_equilibrium.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -235,6 +239,37 @@ class Oracle:
         out = np.empty(self.K)
         lib().orc_totals(ctypes.byref(self.p), _ptr(fs), float(cell_volume), _ptr(out))
         return out
+
+    # adjoint (periodic D2Q4 only) ----------------------------------------
+    def adjoint_step(self, U_next, gbar):
+        """dL/dfs^n from gbar = dL/dfs^{n+1} and the moments U_next of step n+1."""
+        U_next, gbar = self._fields(U_next), self._dists(gbar)
+        out = np.empty_like(gbar)
+        if lib().orc_adjoint_step(ctypes.byref(self.p), _ptr(U_next), _ptr(gbar), _ptr(out)):
+            raise ValueError("the oracle adjoint covers periodic D2Q4 problems only")
+        return out
+
+    def vjp_equilibrium(self, U0, gbar0):
+        """dL/dU0 = J_E(U0)^T gbar0 per cell."""
+        U0, gbar0 = self._fields(U0), self._dists(gbar0)
+        out = np.empty_like(U0)
+        if lib().orc_vjp_equilibrium(ctypes.byref(self.p), _ptr(U0), _ptr(gbar0), _ptr(out)):
+            raise ValueError("the oracle adjoint covers periodic D2Q4 problems only")
+        return out
+
+    def gradient(self, U0, nsteps: int, dLdU_T):
+        """dL/dU0 for a loss L(U(T)) with dL/dU(T) given: forward storing every
+        step's moments, then the backward sweep (plain full storage)."""
+        fs = self.init(U0)
+        Us = []
+        for n in range(nsteps):
+            f = self.stream(fs)
+            fs, U, _ = self.collide(f, n + 1)
+            Us.append(U)
+        g = np.broadcast_to(np.asarray(dLdU_T)[None], (self.Q,) + np.shape(dLdU_T)).copy()
+        for n in range(nsteps - 1, -1, -1):
+            g = self.adjoint_step(Us[n], g)
+        return self.vjp_equilibrium(U0, g), fs
 
     def timed_run(self, fs, nsteps: int):
         """Advance fs by nsteps and return (fs, seconds) measured around the step loop only."""

@@ -404,3 +404,107 @@ void orc_totals(const orc_params* P, const double* fs, double cell_volume, doubl
 }
 
 int orc_max_threads(void) { return omp_get_max_threads(); }
+
+/* ====================================================================== adjoint
+ *
+ * Discrete adjoint of the D2Q4 step on a fully periodic domain (not in the
+ * paper; the transpose of the step defined above, used for gradients).
+ *
+ * Forward step n -> n+1:  f = S fs^n,  U = M f,  fs^{n+1} = (1-w) f + w E(U),
+ * with S the periodic shift f_q(x) = fs_q(x - c_q), M the moment sum over q and
+ * E the equilibria.  With gbar = dL/dfs^{n+1}:
+ *   fbar_{q,k} = (1-w) gbar_{q,k} + w ubar_k,   ubar = J_E(U)^T gbar,
+ *   dL/dfs^n_q(x) = fbar_q(x + c_q)   (S^T: the shift back along c_q).
+ * J_E^T gbar = a/4 + c A_F^T bx + c A_G^T by with a_k = sum_q gbar_{q,k},
+ * bx_k = sum_q sx_q gbar_{q,k}, by_k = sum_q sy_q gbar_{q,k}, c = 1/(4 lambda),
+ * and A_F = dF/dU, A_G = dG/dU the Euler flux Jacobians of the ideal gas.
+ */
+
+/* ubar_k = sum_{q,k'} gq[q*4+k'] dE_{q,k'}/dU_k at state U. */
+static void equilibrium_vjp_2d(const orc_params* P, const double* U, const double* gq, double* ubar)
+{
+    const double g = P->gamma, gm1 = P->gamma - 1.0;
+    const double rho = U[0], mx = U[1], my = U[2], en = U[3];
+    const double u = mx / rho, v = my / rho;
+    const double p = gm1 * (en - 0.5 * (mx * u + my * v));
+    const double H = (en + p) / rho;
+    const double q2h = 0.5 * gm1 * (u * u + v * v);
+    /* dF[r][k] = dF_r / dU_k, dG likewise */
+    const double dF[4][4] = {{0.0, 1.0, 0.0, 0.0},
+                             {q2h - u * u, (3.0 - g) * u, -gm1 * v, gm1},
+                             {-u * v, v, u, 0.0},
+                             {u * (q2h - H), H - gm1 * u * u, -gm1 * u * v, g * u}};
+    const double dG[4][4] = {{0.0, 0.0, 1.0, 0.0},
+                             {-u * v, v, u, 0.0},
+                             {q2h - v * v, -gm1 * u, (3.0 - g) * v, gm1},
+                             {v * (q2h - H), -gm1 * u * v, H - gm1 * v * v, g * v}};
+    const double c = 1.0 / (4.0 * P->lambda);
+    double a[4], bx[4], by[4];
+    for (int k = 0; k < 4; ++k) {
+        a[k] = bx[k] = by[k] = 0.0;
+        for (int q = 0; q < 4; ++q) {
+            a[k] += gq[q * 4 + k];
+            bx[k] += SX2[q] * gq[q * 4 + k];
+            by[k] += SY2[q] * gq[q * 4 + k];
+        }
+    }
+    for (int k = 0; k < 4; ++k) {
+        double sf = 0.0, sg = 0.0;
+        for (int r = 0; r < 4; ++r) {
+            sf += dF[r][k] * bx[r];
+            sg += dG[r][k] * by[r];
+        }
+        ubar[k] = 0.25 * a[k] + c * sf + c * sg;
+    }
+}
+
+static int adjoint_supported(const orc_params* P)
+{
+    if (orc_validate(P)) return 0;
+    if (P->lattice != ORC_D2Q4) return 0;
+    for (int s = 0; s < 4; ++s)
+        if (P->bc_kind[s] != ORC_PERIODIC) return 0;
+    return 1;
+}
+
+/* One backward step: gout = dL/dfs^n from gin = dL/dfs^{n+1} and U_next =
+ * the moments of step n+1 (the U the forward collision used). Returns 0, or
+ * nonzero if the problem is not a periodic D2Q4 one. */
+int orc_adjoint_step(const orc_params* P, const double* U_next, const double* gin, double* gout)
+{
+    if (!adjoint_supported(P)) return 1;
+    const int64_t nx = P->nx, ny = P->ny, N = nx * ny;
+    const double om = P->omega, om1 = 1.0 - P->omega;
+#pragma omp parallel for schedule(static) num_threads(threads_of(P))
+    for (int64_t j = 0; j < ny; ++j) {
+        for (int64_t i = 0; i < nx; ++i) {
+            const int64_t c = j * nx + i;
+            double gq[16], U[4], ubar[4];
+            for (int n = 0; n < 16; ++n) gq[n] = gin[n * N + c];
+            for (int k = 0; k < 4; ++k) U[k] = U_next[k * N + c];
+            equilibrium_vjp_2d(P, U, gq, ubar);
+            for (int q = 0; q < 4; ++q) {
+                const int64_t ti = (i - SX2[q] + nx) % nx, tj = (j - SY2[q] + ny) % ny;
+                for (int k = 0; k < 4; ++k)
+                    gout[(q * 4 + k) * N + tj * nx + ti] = om1 * gq[q * 4 + k] + om * ubar[k];
+            }
+        }
+    }
+    return 0;
+}
+
+/* Gradient with respect to the initial conserved state: fs^0 = E(U0), so
+ * dL/dU0 = J_E(U0)^T dL/dfs^0, per cell. Returns 0 or nonzero as above. */
+int orc_vjp_equilibrium(const orc_params* P, const double* U0, const double* g0, double* grad)
+{
+    if (!adjoint_supported(P)) return 1;
+    const int64_t N = P->nx * P->ny;
+    for (int64_t c = 0; c < N; ++c) {
+        double gq[16], U[4], ubar[4];
+        for (int n = 0; n < 16; ++n) gq[n] = g0[n * N + c];
+        for (int k = 0; k < 4; ++k) U[k] = U0[k * N + c];
+        equilibrium_vjp_2d(P, U, gq, ubar);
+        for (int k = 0; k < 4; ++k) grad[k * N + c] = ubar[k];
+    }
+    return 0;
+}

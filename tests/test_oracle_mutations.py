@@ -33,6 +33,14 @@ MUTANTS = {
                                         "return g * (U[3] - 0.5 * (U[1] * u + U[2] * v));"),
     "ghost_uses_wrong_side": ("if (kind == ORC_DIRICHLET) g = ghost[side_x];",
                               "if (kind == ORC_DIRICHLET) g = ghost[side_x ^ 1];"),
+    # adjoint
+    "adjoint_drops_y_flux_jacobian": ("ubar[k] = 0.25 * a[k] + c * sf + c * sg;", "ubar[k] = 0.25 * a[k] + c * sf;"),
+    "adjoint_wrong_momentum_jacobian": ("{q2h - u * u, (3.0 - g) * u, -gm1 * v, gm1},",
+                                        "{q2h - u * u, (2.0 - g) * u, -gm1 * v, gm1},"),
+    "adjoint_pushes_the_wrong_way": ("const int64_t ti = (i - SX2[q] + nx) % nx, tj = (j - SY2[q] + ny) % ny;",
+                                     "const int64_t ti = (i + SX2[q] + nx) % nx, tj = (j + SY2[q] + ny) % ny;"),
+    "adjoint_relaxation_weights_swapped": ("gout[(q * 4 + k) * N + tj * nx + ti] = om1 * gq[q * 4 + k] + om * ubar[k];",
+                                           "gout[(q * 4 + k) * N + tj * nx + ti] = om * gq[q * 4 + k] + om1 * ubar[k];"),
 }
 
 
@@ -48,6 +56,7 @@ def test_pins_catch_mutant(name, tmp_path):
                     str(mutated), "-o", str(so), "-lm"], check=True)
     env = dict(os.environ, LBRS_ORACLE_LIB=str(so), OMP_NUM_THREADS="2")
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_adjoint.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"pins did not catch mutant {name}:\n{r.stdout[-2000:]}"
