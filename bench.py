@@ -19,6 +19,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -186,6 +187,83 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ GPU arm
 
+def adjoint_measurement(Solver, stream, barrier, n=2048, steps=2000):
+    """Forward (checkpointed) vs backward (recompute + adjoint) time of the density-loss gradient,
+    and the FP32 gradient's error against FP64 central differences on a 64 x 64 copy."""
+    import torch
+    wl, target = workloads.adjoint_pulses(seed=0, n=n, steps=steps)
+    s = Solver.from_workload(wl, precision="f32", stream=stream)
+    tgt = torch.from_numpy(target).float().cuda()
+    W0 = torch.from_numpy(wl.prim).cuda()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    with torch.cuda.stream(stream):
+        s.set_state(W0)
+        s.forward_checkpointed(64, 8)              # warm-up: graphs and kernels
+        _, g = s.vjp_loss(tgt)
+        s.backward_checkpointed(g)
+        s.set_state(W0)
+        barrier()
+        ev[0].record(stream)
+        s.forward_checkpointed(steps)
+        ev[1].record(stream)
+        loss, g = s.vjp_loss(tgt)
+        ev2 = torch.cuda.Event(enable_timing=True)
+        ev2.record(stream)
+        grad = s.backward_checkpointed(g)
+        ev[2].record(stream)
+        barrier()
+    t_fwd = ev[0].elapsed_time(ev[1]) / 1e3
+    t_bwd = ev2.elapsed_time(ev[2]) / 1e3
+    gnorm = float(grad.double().norm().item())
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+
+    # FD check on a 64 x 64 copy run to the same final time (2000 * 64 / 2048 -> 63 steps):
+    # FP32 and FP64 adjoint gradients against FP64 central differences
+    fd_steps = math.ceil(steps * 64 / n)
+    small, tsmall = workloads.adjoint_pulses(seed=0, n=64, steps=fd_steps)
+    s32 = Solver.from_workload(small, precision="f32", stream=stream)
+    s64 = Solver.from_workload(small, precision="f64", stream=stream)
+    tt = torch.from_numpy(tsmall).cuda()
+    with torch.cuda.stream(stream):
+        s64.set_state(torch.from_numpy(small.prim).cuda())
+        U0 = s64.moments(torch.float64)                # conserved initial fields
+        grads = {}
+        for name, sv in (("f32", s32), ("f64", s64)):
+            sv.set_state(U0, primitive=False)
+            sv.forward_checkpointed(fd_steps)
+            _, gT = sv.vjp_loss(tt)
+            grads[name] = sv.backward_checkpointed(gT).double()
+
+        def loss64(U):
+            s64.set_state(U, primitive=False)
+            s64.step(fd_steps)
+            return s64.vjp_loss(tt)[0]
+
+        gen = torch.Generator(device="cpu").manual_seed(5)
+        errs = {"f32": [], "f64": []}
+        for _ in range(4):
+            d = torch.randn(U0.shape, generator=gen, dtype=torch.float64).cuda()
+            h = 1e-6 * float(U0.norm() / d.norm())
+            fd = (loss64(U0 + h * d) - loss64(U0 - h * d)) / (2 * h)
+            for name in errs:
+                errs[name].append(abs(float((grads[name] * d).sum()) - fd) / abs(fd))
+        normwise = float((grads["f32"] - grads["f64"]).norm() / grads["f64"].norm())
+    stream.synchronize()
+    s32.close()
+    s64.close()
+    return {"workload": f"{n}x{n} periodic, uniform (1, 0.5, 0.3, 1) + 8 Gaussian pulses, {steps} FP32 steps, "
+                        f"density L2 loss, sqrt(T) checkpointing (segment {math.ceil(math.sqrt(steps))})",
+            "forward_s": t_fwd, "backward_s": t_bwd, "backward_over_forward": t_bwd / t_fwd,
+            "forward_mlups": n * n * steps / t_fwd / 1e6, "loss": loss, "grad_norm": gnorm,
+            "fd_check_64x64": {"steps": fd_steps, "directions": 4,
+                               "f32_max_rel_err_vs_fd": max(errs["f32"]),
+                               "f64_max_rel_err_vs_fd": max(errs["f64"]),
+                               "f32_vs_f64_gradient_normwise": normwise,
+                               "reference": "FP64 GPU path central differences; 64x64 copy run to the same "
+                                            "final time as the 2048^2 x 2000-step workload"}}
+
 def run_ours(args):
     import torch
     from paper_1504_07034_gb300.build import build as build_lib
@@ -285,6 +363,9 @@ def run_ours(args):
               "achieved_gbs": BYTES_PER_LUP_F32 * mlups_big / 1e3,
               "frac": BYTES_PER_LUP_F32 * mlups_big / 1e3 / peak, "status": d_big["status"]}
 
+    # --- adjoint: 2048^2 periodic pulses, 2000 FP32 steps, sqrt(T) checkpointing ------
+    adjoint = adjoint_measurement(Solver, stream, barrier)
+
     # --- end to end through the public API with host buffers -------------------------
     prim_host = torch.from_numpy(wl.prim).pin_memory()
     out_host = torch.empty((4, wl.ny, wl.nx), dtype=torch.float64).pin_memory()
@@ -314,6 +395,7 @@ def run_ours(args):
                          "kernel": "step2d_kernel<float>", "peak_kind": f"{peak_kind} hbm_gbs",
                          "algorithmic_bytes_per_lup": BYTES_PER_LUP_F32},
             "steady_large_grid": steady,
+            "adjoint": adjoint,
             "fp64": {"value": mlups64, "unit": UNIT, "achieved_gbs": BYTES_PER_LUP_F64 * mlups64 / 1e3,
                      "diag_after_1000_steps": {k: d64[k] for k in ("status", "min_rho", "min_p", "max_lambda_local")}},
             "accuracy": {"l1_rho_fp32_vs_fp64_gpu_after_1000_steps": l1,

@@ -187,6 +187,55 @@ lbrs_status lbrs_diagnostics_noalloc(const lbrs_config* cfg, const void* d_fs, l
 lbrs_status lbrs_get_distributions(lbrs_ctx* ctx, void* dst, int on_device);
 lbrs_status lbrs_set_distributions(lbrs_ctx* ctx, const void* src, int on_device, int64_t step);
 
+/* ---------------------------------------------------------------- adjoint
+ *
+ * Discrete adjoint of the D2Q4 step on a fully periodic domain.  The paper
+ * has no adjoint; these calls transpose the step defined above so that
+ * gradients of a loss of the final state with respect to the initial
+ * conserved fields can be computed:
+ *   forward   f = S f*^n, U = M f, f*^{n+1} = (1 - omega) f + omega E(U)
+ *   backward  fbar = (1 - omega) gbar + omega J_E(U)^T gbar,
+ *             dL/df*^n_q(x - c_q) = fbar_q(x)       (gbar = dL/df*^{n+1})
+ * with J_E the Jacobian of the equilibria (through the ideal-gas Euler flux
+ * Jacobians).  Buffers are device memory in the storage precision unless a
+ * dtype is given; distributions are [4][4][ny][nx], fields [4][ny][nx].
+ * Non-periodic or D1Q2 contexts get LBRS_EINVAL. */
+
+/* Enqueue n steps like lbrs_step, also writing each step's moments U^{s+m+1}
+ * (the U its collision used) to d_U_hist + m*K*N elements, m = 0..n-1. */
+lbrs_status lbrs_step_record(lbrs_ctx* ctx, int64_t n, void* d_U_hist);
+
+/* gbar[q][k] = dL/dU_k for every q (U_k = sum_q f*_{q,k}); d_dLdU is [K][ny][nx] of dtype. */
+lbrs_status lbrs_adjoint_seed(lbrs_ctx* ctx, const void* d_dLdU, int dtype, void* d_gbar);
+
+/* Density mismatch loss of the current state, L = 1/2 sum_cells (rho - rho_target)^2 dx^d,
+ * reduced in FP64 in a fixed order (loss: host pointer, nullable; synchronises
+ * when given), and its seed d_gbar = dL/df*.  d_rho_target is [ny][nx] of dtype. */
+lbrs_status lbrs_vjp_loss(lbrs_ctx* ctx, const void* d_rho_target, int dtype, void* d_gbar, double* loss);
+
+/* One backward step: d_gbar_out = dL/df*^n from d_gbar_in = dL/df*^{n+1} and
+ * d_U_next = the moments of step n+1.  In and out buffers must differ. */
+lbrs_status lbrs_adjoint_step(lbrs_ctx* ctx, const void* d_U_next, const void* d_gbar_in, void* d_gbar_out);
+
+/* dL/dU0 = J_E(U0)^T dL/df*^0 per cell (the initial state is f*^0 = E(U0)). */
+lbrs_status lbrs_vjp_equilibrium(lbrs_ctx* ctx, const void* d_U0, const void* d_gbar0, void* d_gradU0);
+
+/* sqrt(T) checkpointing.  Bytes of the caller-owned adjoint workspace for a run
+ * of n_steps in segments of `segment` steps: ceil(n/segment)+1 distribution
+ * checkpoints, `segment` recorded moment fields and two gradient buffers. */
+lbrs_status lbrs_adjoint_workspace_size(const lbrs_ctx* ctx, int64_t n_steps, int64_t segment, size_t* bytes);
+
+/* Run n_steps from the current state, storing the state at each segment start
+ * and at the end in d_adj_ws (256-byte aligned, >= lbrs_adjoint_workspace_size). */
+lbrs_status lbrs_forward_checkpointed(lbrs_ctx* ctx, int64_t n_steps, int64_t segment, void* d_adj_ws, size_t bytes);
+
+/* Backward sweep of the run recorded by lbrs_forward_checkpointed on d_adj_ws:
+ * each segment, last first, is recomputed from its checkpoint while recording
+ * its moments, then swept with lbrs_adjoint_step; finally d_gradU0 = dL/dU0.
+ * d_gbar_T = dL/df* of the final state (e.g. from lbrs_vjp_loss).  The
+ * context's state is the final forward state again on return. */
+lbrs_status lbrs_backward_checkpointed(lbrs_ctx* ctx, void* d_adj_ws, const void* d_gbar_T, void* d_gradU0);
+
 /* Number of time steps taken since the state was set. */
 lbrs_status lbrs_step_count(const lbrs_ctx* ctx, int64_t* steps);
 

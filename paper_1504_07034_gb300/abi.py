@@ -79,6 +79,14 @@ SIGNATURES = {
     "lbrs_step_count": (ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_int64)]),
     "lbrs_launch_count": (ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_int64)]),
     "lbrs_last_error": (ctypes.c_char_p, [_CTX]),
+    "lbrs_step_record": (ctypes.c_int, [_CTX, ctypes.c_int64, _P]),
+    "lbrs_adjoint_seed": (ctypes.c_int, [_CTX, _P, ctypes.c_int, _P]),
+    "lbrs_vjp_loss": (ctypes.c_int, [_CTX, _P, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_double)]),
+    "lbrs_adjoint_step": (ctypes.c_int, [_CTX, _P, _P, _P]),
+    "lbrs_vjp_equilibrium": (ctypes.c_int, [_CTX, _P, _P, _P]),
+    "lbrs_adjoint_workspace_size": (ctypes.c_int, [_CTX, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)]),
+    "lbrs_forward_checkpointed": (ctypes.c_int, [_CTX, ctypes.c_int64, ctypes.c_int64, _P, ctypes.c_size_t]),
+    "lbrs_backward_checkpointed": (ctypes.c_int, [_CTX, _P, _P, _P]),
 }
 
 _lib = None

@@ -49,6 +49,7 @@ struct StepArgs {
     T om, om1;                    // omega, 1 - omega
     T c;                          // 1/(4 lambda) in 2-D, 1/(2 lambda) in 1-D
     T gm1;                        // gamma - 1
+    T* __restrict__ Uout;         // recording steps only: moments U_k of the step, [K][ny][nx]
 };
 
 // ---------------------------------------------------------------- arithmetic
@@ -194,12 +195,16 @@ __device__ __forceinline__ void pull_edge_2d(const StepArgs<T>& a, int i, int j,
     }
 }
 
-template <typename T>
+template <typename T, bool STORE_U = false>
 __device__ __forceinline__ void collide_store_2d(const StepArgs<T>& a, int64_t c, const T f[4][4])
 {
     T U[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) U[k] = ((f[0][k] + f[1][k]) + f[2][k]) + f[3][k];
+    if constexpr (STORE_U) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a.Uout[k * a.N + c] = U[k];
+    }
     T e[4][4];
     equilibria2d<T>(U, a.gm1, a.c, e);
 #pragma unroll
@@ -209,7 +214,8 @@ __device__ __forceinline__ void collide_store_2d(const StepArgs<T>& a, int64_t c
 }
 
 // One thread per cell; blockDim.x along i (coalesced), blockDim.y along j.
-template <typename T>
+// STORE_U also writes the step's moments (the recording step of the adjoint).
+template <typename T, bool STORE_U = false>
 __global__ void __launch_bounds__(256) step2d_kernel(const StepArgs<T> a)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -228,7 +234,7 @@ __global__ void __launch_bounds__(256) step2d_kernel(const StepArgs<T> a)
     } else {
         pull_edge_2d<T>(a, i, j, f);
     }
-    collide_store_2d<T>(a, c, f);
+    collide_store_2d<T, STORE_U>(a, c, f);
 }
 
 // ---------------------------------------------------------------- D1Q2 step
@@ -262,6 +268,113 @@ __global__ void __launch_bounds__(256) step1d_kernel(const StepArgs<T> a)
     for (int q = 0; q < 2; ++q)
 #pragma unroll
         for (int k = 0; k < 3; ++k) a.dst[(q * 3 + k) * a.N + i] = a.om1 * f[q][k] + a.om * e[q][k];
+}
+
+// ---------------------------------------------------------------- adjoint (periodic D2Q4)
+//
+// Discrete adjoint of the step above (not in the paper).  Forward:
+// f = S f*^n, U = M f, f*^{n+1} = (1 - w) f + w E(U).  With g = dL/df*^{n+1}:
+//   fbar_{q,k} = (1 - w) g_{q,k} + w ubar_k,  ubar = J_E(U)^T g,
+//   dL/df*^n_q(x - c_q) = fbar_q(x)   (transposed shift: push back along -c_q).
+// J_E^T g = a/4 + c A_F^T bx + c A_G^T by, a_k = sum_q g_{q,k},
+// bx_k = sum_q sx_q g_{q,k}, by_k = sum_q sy_q g_{q,k}, c = 1/(4 lambda), with
+// A_F = dF/dU, A_G = dG/dU the ideal-gas Euler flux Jacobians.
+
+template <typename T>
+__device__ __forceinline__ void equilibrium_vjp2d(const T U[4], const T g[4][4], T gamma, T gm1, T c, T ubar[4])
+{
+    const T rho = U[0], mx = U[1], my = U[2], en = U[3];
+    T u, v;
+    velocity2<T>(rho, mx, my, u, v);
+    const T p = gm1 * (en - T(0.5) * (mx * u + my * v));
+    const T H = (en + p) / rho;
+    const T q2h = T(0.5) * gm1 * (u * u + v * v);
+    const T dF[4][4] = {{T(0), T(1), T(0), T(0)},
+                        {q2h - u * u, (T(3) - gamma) * u, -gm1 * v, gm1},
+                        {-u * v, v, u, T(0)},
+                        {u * (q2h - H), H - gm1 * u * u, -gm1 * u * v, gamma * u}};
+    const T dG[4][4] = {{T(0), T(0), T(1), T(0)},
+                        {-u * v, v, u, T(0)},
+                        {q2h - v * v, -gm1 * u, (T(3) - gamma) * v, gm1},
+                        {v * (q2h - H), -gm1 * u * v, H - gm1 * v * v, gamma * v}};
+    const T SXv[4] = {T(-1), T(1), T(1), T(-1)};
+    const T SYv[4] = {T(-1), T(-1), T(1), T(1)};
+    T av[4], bx[4], by[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        av[k] = bx[k] = by[k] = T(0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            av[k] += g[q][k];
+            bx[k] += SXv[q] * g[q][k];
+            by[k] += SYv[q] * g[q][k];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        T sf = T(0), sg = T(0);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            sf += dF[r][k] * bx[r];
+            sg += dG[r][k] * by[r];
+        }
+        ubar[k] = T(0.25) * av[k] + c * sf + c * sg;
+    }
+}
+
+template <typename T>
+struct AdjArgs {
+    const T* __restrict__ U;      // moments of step n+1 (or U0 for the equilibrium VJP), [4][ny][nx]
+    const T* __restrict__ gin;    // dL/df*^{n+1}, [4][4][ny][nx]
+    T* __restrict__ gout;         // dL/df*^n (or dL/dU0), written
+    int64_t N;
+    int nx, ny;
+    T om, om1, c, gm1, gamma;
+};
+
+// One thread per source cell x: read g(x) and U(x), push fbar_q(x) to x - c_q (periodic).
+template <typename T>
+__global__ void __launch_bounds__(256) adjoint2d_kernel(const AdjArgs<T> a)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= a.nx || j >= a.ny) return;
+    const int64_t c = (int64_t)j * a.nx + i;
+    T g[4][4], U[4], ubar[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) g[q][k] = a.gin[(q * 4 + k) * a.N + c];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) U[k] = a.U[k * a.N + c];
+    equilibrium_vjp2d<T>(U, g, a.gamma, a.gm1, a.c, ubar);
+    // targets x - c_q: q0 (-,-) -> (i+1, j+1); q1 (+,-) -> (i-1, j+1); q2 (+,+) -> (i-1, j-1); q3 (-,+) -> (i+1, j-1)
+    const int ip = i + 1 == a.nx ? 0 : i + 1, im = i == 0 ? a.nx - 1 : i - 1;
+    const int jp = j + 1 == a.ny ? 0 : j + 1, jm = j == 0 ? a.ny - 1 : j - 1;
+    const int64_t t[4] = {(int64_t)jp * a.nx + ip, (int64_t)jp * a.nx + im, (int64_t)jm * a.nx + im,
+                          (int64_t)jm * a.nx + ip};
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a.gout[(q * 4 + k) * a.N + t[q]] = a.om1 * g[q][k] + a.om * ubar[k];
+}
+
+// dL/dU0 = J_E(U0)^T dL/df*^0, per cell.
+template <typename T>
+__global__ void __launch_bounds__(256) vjp_equilibrium2d_kernel(const AdjArgs<T> a)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < a.N; c += (int64_t)gridDim.x * blockDim.x) {
+        T g[4][4], U[4], ubar[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) g[q][k] = a.gin[(q * 4 + k) * a.N + c];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) U[k] = a.U[k * a.N + c];
+        equilibrium_vjp2d<T>(U, g, a.gamma, a.gm1, a.c, ubar);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a.gout[k * a.N + c] = ubar[k];
+    }
 }
 
 }  // namespace lbrs

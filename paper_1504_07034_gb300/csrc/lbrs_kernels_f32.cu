@@ -250,4 +250,28 @@ cudaError_t launch_step_f32(int lattice, const StepArgs<float>& a, cudaStream_t 
     return cudaGetLastError();
 }
 
+cudaError_t launch_step_record_f32(const StepArgs<float>& a, cudaStream_t s)
+{
+    const dim3 block(128, 2);
+    const dim3 grid((unsigned)((a.nx + block.x - 1) / block.x), (unsigned)((a.ny + block.y - 1) / block.y));
+    step2d_kernel<float, true><<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_f32(const AdjArgs<float>& a, cudaStream_t s)
+{
+    const dim3 block(128, 2);
+    const dim3 grid((unsigned)((a.nx + block.x - 1) / block.x), (unsigned)((a.ny + block.y - 1) / block.y));
+    adjoint2d_kernel<float><<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vjp_equilibrium_f32(const AdjArgs<float>& a, cudaStream_t s)
+{
+    int64_t b = (a.N + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    vjp_equilibrium2d_kernel<float><<<(unsigned)(b < 1 ? 1 : b), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 }  // namespace lbrs

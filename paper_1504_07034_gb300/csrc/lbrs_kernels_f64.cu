@@ -240,9 +240,114 @@ __global__ void diag_final_kernel(const double* __restrict__ partials, int nbloc
     out[9] = 0.0;
 }
 
+template <typename Ts, typename Tin>
+__global__ void __launch_bounds__(kThreads) adjoint_seed_kernel(int Q, int K, const Tin* __restrict__ dLdU,
+                                                                Ts* __restrict__ gbar, int64_t N)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        for (int k = 0; k < K; ++k) {
+            const Ts g = (Ts)dLdU[k * N + i];
+            for (int q = 0; q < Q; ++q) gbar[(q * K + k) * N + i] = g;
+        }
+}
+
+template <typename Ts, typename Tt>
+__global__ void __launch_bounds__(kThreads) density_loss_kernel(int Q, int K, const Ts* __restrict__ fs,
+                                                                const Tt* __restrict__ target, Ts* __restrict__ gbar,
+                                                                int64_t N, double cell, double* __restrict__ partials)
+{
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        double rho = (double)fs[i];
+        for (int q = 1; q < Q; ++q) rho += (double)fs[(q * K) * N + i];
+        const double r = rho - (double)target[i];
+        acc += 0.5 * r * r;
+        const Ts g = (Ts)(r * cell);
+        for (int q = 0; q < Q; ++q) {
+            gbar[(q * K) * N + i] = g;
+            for (int k = 1; k < K; ++k) gbar[(q * K + k) * N + i] = (Ts)0;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    __shared__ double warp_acc[kThreads / 32];
+    if ((threadIdx.x & 31) == 0) warp_acc[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = warp_acc[0];
+        for (int w = 1; w < kThreads / 32; ++w) b += warp_acc[w];
+        partials[blockIdx.x] = b;
+    }
+}
+
+__global__ void sum_final_kernel(const double* __restrict__ partials, int n, double scale, double* __restrict__ out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double s = 0.0;
+    for (int b = 0; b < n; ++b) s += partials[b];
+    out[0] = s * scale;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
+
+static dim3 grid2d(int nx, int ny, dim3 block)
+{
+    return dim3((unsigned)((nx + block.x - 1) / block.x), (unsigned)((ny + block.y - 1) / block.y));
+}
+
+cudaError_t launch_step_record_f64(const StepArgs<double>& a, cudaStream_t s)
+{
+    const dim3 block(128, 2);
+    step2d_kernel<double, true><<<grid2d(a.nx, a.ny, block), block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_f64(const AdjArgs<double>& a, cudaStream_t s)
+{
+    const dim3 block(128, 2);
+    adjoint2d_kernel<double><<<grid2d(a.nx, a.ny, block), block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vjp_equilibrium_f64(const AdjArgs<double>& a, cudaStream_t s)
+{
+    vjp_equilibrium2d_kernel<double><<<grid_for(a.N), kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_seed(int Q, int K, int storage_f64, const void* dLdU, int in_dtype, void* gbar, int64_t N,
+                                cudaStream_t s)
+{
+    const int g = grid_for(N);
+    if (storage_f64) {
+        if (in_dtype == 0) adjoint_seed_kernel<double, double><<<g, kThreads, 0, s>>>(Q, K, (const double*)dLdU, (double*)gbar, N);
+        else adjoint_seed_kernel<double, float><<<g, kThreads, 0, s>>>(Q, K, (const float*)dLdU, (double*)gbar, N);
+    } else {
+        if (in_dtype == 0) adjoint_seed_kernel<float, double><<<g, kThreads, 0, s>>>(Q, K, (const double*)dLdU, (float*)gbar, N);
+        else adjoint_seed_kernel<float, float><<<g, kThreads, 0, s>>>(Q, K, (const float*)dLdU, (float*)gbar, N);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_density_loss(int Q, int K, int storage_f64, const void* fs, const void* target, int t_dtype,
+                                void* gbar, int64_t N, double cell_volume, double* partials, double* out,
+                                cudaStream_t s)
+{
+    const int g = kDiagBlocks;
+    if (storage_f64) {
+        if (t_dtype == 0) density_loss_kernel<double, double><<<g, kThreads, 0, s>>>(Q, K, (const double*)fs, (const double*)target, (double*)gbar, N, cell_volume, partials);
+        else density_loss_kernel<double, float><<<g, kThreads, 0, s>>>(Q, K, (const double*)fs, (const float*)target, (double*)gbar, N, cell_volume, partials);
+    } else {
+        if (t_dtype == 0) density_loss_kernel<float, double><<<g, kThreads, 0, s>>>(Q, K, (const float*)fs, (const double*)target, (float*)gbar, N, cell_volume, partials);
+        else density_loss_kernel<float, float><<<g, kThreads, 0, s>>>(Q, K, (const float*)fs, (const float*)target, (float*)gbar, N, cell_volume, partials);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    sum_final_kernel<<<1, 32, 0, s>>>(partials, g, cell_volume, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_step_f64(int lattice, const StepArgs<double>& a, cudaStream_t s)
 {

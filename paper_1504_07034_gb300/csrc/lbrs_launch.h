@@ -12,6 +12,8 @@ namespace lbrs {
 
 template <typename T>
 struct StepArgs;
+template <typename T>
+struct AdjArgs;
 
 // One time step src -> dst.  lattice: LAT_D1Q2 / LAT_D2Q4.
 cudaError_t launch_step_f64(int lattice, const StepArgs<double>& a, cudaStream_t s);
@@ -40,5 +42,26 @@ cudaError_t launch_moments(int lattice, int storage_f64, const void* fs, void* U
 int diag_blocks();
 cudaError_t launch_diag(int lattice, int storage_f64, const void* fs, int64_t N, double gamma, double lambda,
                         double cell_volume, double* partials, double* out, cudaStream_t s);
+
+// Recording step (D2Q4): the step above that also writes its moments to a.Uout.
+cudaError_t launch_step_record_f64(const StepArgs<double>& a, cudaStream_t s);
+cudaError_t launch_step_record_f32(const StepArgs<float>& a, cudaStream_t s);
+
+// Adjoint of one periodic D2Q4 step, and the equilibrium VJP dL/dU0 (see lbrs_kernels.cuh).
+cudaError_t launch_adjoint_f64(const AdjArgs<double>& a, cudaStream_t s);
+cudaError_t launch_adjoint_f32(const AdjArgs<float>& a, cudaStream_t s);
+cudaError_t launch_vjp_equilibrium_f64(const AdjArgs<double>& a, cudaStream_t s);
+cudaError_t launch_vjp_equilibrium_f32(const AdjArgs<float>& a, cudaStream_t s);
+
+// gbar[q][k][c] = dLdU[k][c] for every q (dLdU of in_dtype 0 f64 / 1 f32; gbar in storage type).
+cudaError_t launch_adjoint_seed(int Q, int K, int storage_f64, const void* dLdU, int in_dtype, void* gbar, int64_t N,
+                                cudaStream_t s);
+
+// Density mismatch loss 0.5 sum (rho - target)^2 * cell_volume of fs (rho = sum_q fs[q][0]),
+// reduced in FP64 in a fixed order into out[0], and its gradient seed
+// gbar[q][0] = (rho - target) * cell_volume, gbar[q][k>0] = 0.
+cudaError_t launch_density_loss(int Q, int K, int storage_f64, const void* fs, const void* target, int t_dtype,
+                                void* gbar, int64_t N, double cell_volume, double* partials, double* out,
+                                cudaStream_t s);
 
 }  // namespace lbrs

@@ -73,6 +73,10 @@ struct lbrs_ctx {
     double c;                // 1/(4 lambda) in 2-D, 1/(2 lambda) in 1-D
     cudaStream_t cap_stream;
     cudaGraphExec_t graph[2];
+    // checkpointed adjoint: the run recorded by lbrs_forward_checkpointed
+    char* adj_ws;
+    size_t adj_bytes;
+    int64_t adj_n, adj_seg, adj_step0;
     char err[512];
 };
 
@@ -158,6 +162,7 @@ StepArgs<T> step_args(const lbrs_ctx* ctx, int from)
     a.om1 = (T)(1.0 - ctx->cfg.omega);
     a.c = (T)ctx->c;
     a.gm1 = (T)(ctx->cfg.gamma - 1.0);
+    a.Uout = nullptr;
     return a;
 }
 
@@ -197,6 +202,84 @@ lbrs_status ensure_graph(lbrs_ctx* ctx, int from)
 }
 
 size_t field_bytes(const lbrs_ctx* ctx, int dtype) { return (size_t)ctx->K * (size_t)ctx->N * (dtype == LBRS_F64 ? 8 : 4); }
+
+size_t elem_bytes(const lbrs_ctx* ctx) { return ctx->f64 ? 8 : 4; }
+
+// The adjoint covers the periodic D2Q4 step.
+lbrs_status adjoint_supported(lbrs_ctx* ctx)
+{
+    if (ctx->lattice != LBRS_D2Q4) return fail(ctx, LBRS_EINVAL, "the adjoint covers D2Q4 only");
+    for (int s = 0; s < 4; ++s)
+        if (ctx->cfg.bc[s].kind != LBRS_BC_PERIODIC)
+            return fail(ctx, LBRS_EINVAL, "the adjoint covers fully periodic domains only");
+    return LBRS_OK;
+}
+
+template <typename T>
+AdjArgs<T> adj_args(const lbrs_ctx* ctx, const void* U, const void* gin, void* gout)
+{
+    AdjArgs<T> a;
+    a.U = (const T*)U;
+    a.gin = (const T*)gin;
+    a.gout = (T*)gout;
+    a.N = ctx->N;
+    a.nx = (int)ctx->cfg.nx;
+    a.ny = (int)ctx->cfg.ny;
+    a.om = (T)ctx->cfg.omega;
+    a.om1 = (T)(1.0 - ctx->cfg.omega);
+    a.c = (T)ctx->c;
+    a.gm1 = (T)(ctx->cfg.gamma - 1.0);
+    a.gamma = (T)ctx->cfg.gamma;
+    return a;
+}
+
+// One recording step from the current buffer: writes the step's moments to Uout.
+cudaError_t launch_record_step(lbrs_ctx* ctx, void* Uout)
+{
+    if (ctx->f64) {
+        StepArgs<double> a = step_args<double>(ctx, ctx->cur);
+        a.Uout = (double*)Uout;
+        return launch_step_record_f64(a, ctx->stream);
+    }
+    StepArgs<float> a = step_args<float>(ctx, ctx->cur);
+    a.Uout = (float*)Uout;
+    return launch_step_record_f32(a, ctx->stream);
+}
+
+cudaError_t launch_adjoint_step_raw(lbrs_ctx* ctx, const void* U_next, const void* gin, void* gout)
+{
+    if (ctx->f64) return launch_adjoint_f64(adj_args<double>(ctx, U_next, gin, gout), ctx->stream);
+    return launch_adjoint_f32(adj_args<float>(ctx, U_next, gin, gout), ctx->stream);
+}
+
+cudaError_t launch_vjp_eq_raw(lbrs_ctx* ctx, const void* U0, const void* g0, void* grad)
+{
+    if (ctx->f64) return launch_vjp_equilibrium_f64(adj_args<double>(ctx, U0, g0, grad), ctx->stream);
+    return launch_vjp_equilibrium_f32(adj_args<float>(ctx, U0, g0, grad), ctx->stream);
+}
+
+struct AdjLayout {
+    int64_t nseg;
+    size_t ckpt0, ckpt_stride, uhist, gbar0, gbar1, total;
+};
+
+AdjLayout adj_layout(const lbrs_ctx* ctx, int64_t n, int64_t seg)
+{
+    AdjLayout A;
+    A.nseg = (n + seg - 1) / seg;
+    A.ckpt_stride = align_up(ctx->L.f_bytes);
+    size_t off = 0;
+    A.ckpt0 = off;
+    off += (size_t)(A.nseg + 1) * A.ckpt_stride;          // segment starts plus the final state
+    A.uhist = off;
+    off += align_up((size_t)seg * ctx->K * ctx->N * elem_bytes(ctx));
+    A.gbar0 = off;
+    off += A.ckpt_stride;
+    A.gbar1 = off;
+    off += A.ckpt_stride;
+    A.total = off;
+    return A;
+}
 
 }  // namespace
 
@@ -429,6 +512,154 @@ lbrs_status lbrs_launch_count(const lbrs_ctx* ctx, int64_t* launches)
 {
     if (!ctx || !launches) return fail(nullptr, LBRS_EINVAL, "NULL argument");
     *launches = ctx->launches;
+    return LBRS_OK;
+}
+
+lbrs_status lbrs_step_record(lbrs_ctx* ctx, int64_t n, void* d_U_hist)
+{
+    if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
+    if (n < 0) return fail(ctx, LBRS_EINVAL, "negative step count");
+    if (n > 0 && !d_U_hist) return fail(ctx, LBRS_EINVAL, "d_U_hist is NULL");
+    if (ctx->lattice != LBRS_D2Q4) return fail(ctx, LBRS_EINVAL, "recording steps cover D2Q4 only");
+    if (!ctx->has_state) return fail(ctx, LBRS_ESTATE, "no state set");
+    const size_t stride = (size_t)ctx->K * ctx->N * elem_bytes(ctx);
+    for (int64_t m = 0; m < n; ++m) {
+        LBRS_CUDA(ctx, launch_record_step(ctx, (char*)d_U_hist + m * stride));
+        ctx->cur ^= 1;
+        ctx->step += 1;
+        ctx->launches += 1;
+    }
+    return LBRS_OK;
+}
+
+lbrs_status lbrs_adjoint_seed(lbrs_ctx* ctx, const void* d_dLdU, int dtype, void* d_gbar)
+{
+    if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
+    if (!d_dLdU || !d_gbar) return fail(ctx, LBRS_EINVAL, "NULL buffer");
+    if (dtype != LBRS_F64 && dtype != LBRS_F32) return fail(ctx, LBRS_EINVAL, "dtype must be LBRS_F64 or LBRS_F32");
+    LBRS_CUDA(ctx, launch_adjoint_seed(ctx->Q, ctx->K, ctx->f64, d_dLdU, dtype == LBRS_F32, d_gbar, ctx->N, ctx->stream));
+    ctx->launches += 1;
+    return LBRS_OK;
+}
+
+lbrs_status lbrs_vjp_loss(lbrs_ctx* ctx, const void* d_rho_target, int dtype, void* d_gbar, double* loss)
+{
+    if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
+    if (!d_rho_target || !d_gbar) return fail(ctx, LBRS_EINVAL, "NULL buffer");
+    if (dtype != LBRS_F64 && dtype != LBRS_F32) return fail(ctx, LBRS_EINVAL, "dtype must be LBRS_F64 or LBRS_F32");
+    if (!ctx->has_state) return fail(ctx, LBRS_ESTATE, "no state set");
+    const double vol = ctx->lattice == LBRS_D2Q4 ? ctx->cfg.dx * ctx->cfg.dx : ctx->cfg.dx;
+    double* partials = (double*)(ctx->ws + ctx->L.partials);
+    double* dout = (double*)(ctx->ws + ctx->L.diag_out);
+    LBRS_CUDA(ctx, launch_density_loss(ctx->Q, ctx->K, ctx->f64, ctx->f[ctx->cur], d_rho_target, dtype == LBRS_F32,
+                                       d_gbar, ctx->N, vol, partials, dout, ctx->stream));
+    ctx->launches += 2;
+    if (loss) {
+        LBRS_CUDA(ctx, cudaMemcpyAsync(loss, dout, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    return LBRS_OK;
+}
+
+lbrs_status lbrs_adjoint_step(lbrs_ctx* ctx, const void* d_U_next, const void* d_gbar_in, void* d_gbar_out)
+{
+    if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
+    lbrs_status st = adjoint_supported(ctx);
+    if (st != LBRS_OK) return st;
+    if (!d_U_next || !d_gbar_in || !d_gbar_out) return fail(ctx, LBRS_EINVAL, "NULL buffer");
+    if (d_gbar_in == d_gbar_out) return fail(ctx, LBRS_EINVAL, "d_gbar_in and d_gbar_out must differ");
+    LBRS_CUDA(ctx, launch_adjoint_step_raw(ctx, d_U_next, d_gbar_in, d_gbar_out));
+    ctx->launches += 1;
+    return LBRS_OK;
+}
+
+lbrs_status lbrs_vjp_equilibrium(lbrs_ctx* ctx, const void* d_U0, const void* d_gbar0, void* d_gradU0)
+{
+    if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
+    lbrs_status st = adjoint_supported(ctx);
+    if (st != LBRS_OK) return st;
+    if (!d_U0 || !d_gbar0 || !d_gradU0) return fail(ctx, LBRS_EINVAL, "NULL buffer");
+    LBRS_CUDA(ctx, launch_vjp_eq_raw(ctx, d_U0, d_gbar0, d_gradU0));
+    ctx->launches += 1;
+    return LBRS_OK;
+}
+
+lbrs_status lbrs_adjoint_workspace_size(const lbrs_ctx* ctx, int64_t n_steps, int64_t segment, size_t* bytes)
+{
+    if (!ctx || !bytes) return fail(nullptr, LBRS_EINVAL, "NULL argument");
+    if (n_steps < 1 || segment < 1) return fail(nullptr, LBRS_EINVAL, "n_steps and segment must be >= 1");
+    *bytes = adj_layout(ctx, n_steps, segment).total;
+    return LBRS_OK;
+}
+
+lbrs_status lbrs_forward_checkpointed(lbrs_ctx* ctx, int64_t n_steps, int64_t segment, void* d_adj_ws, size_t bytes)
+{
+    if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
+    lbrs_status st = adjoint_supported(ctx);
+    if (st != LBRS_OK) return st;
+    if (n_steps < 1 || segment < 1) return fail(ctx, LBRS_EINVAL, "n_steps and segment must be >= 1");
+    if (!ctx->has_state) return fail(ctx, LBRS_ESTATE, "no state set");
+    if (!d_adj_ws || (uintptr_t)d_adj_ws % kAlign) return fail(ctx, LBRS_EINVAL, "adjoint workspace NULL or not 256-byte aligned");
+    const AdjLayout A = adj_layout(ctx, n_steps, segment);
+    if (bytes < A.total) return fail(ctx, LBRS_ENOMEM, "adjoint workspace has %zu bytes, needs %zu", bytes, A.total);
+    char* ws = (char*)d_adj_ws;
+    ctx->adj_ws = nullptr;
+    ctx->adj_step0 = ctx->step;
+    for (int64_t s = 0; s < A.nseg; ++s) {
+        LBRS_CUDA(ctx, cudaMemcpyAsync(ws + A.ckpt0 + s * A.ckpt_stride, ctx->f[ctx->cur], ctx->L.f_bytes,
+                                       cudaMemcpyDeviceToDevice, ctx->stream));
+        const int64_t len = (s + 1) * segment <= n_steps ? segment : n_steps - s * segment;
+        st = lbrs_step(ctx, len);
+        if (st != LBRS_OK) return st;
+    }
+    LBRS_CUDA(ctx, cudaMemcpyAsync(ws + A.ckpt0 + A.nseg * A.ckpt_stride, ctx->f[ctx->cur], ctx->L.f_bytes,
+                                   cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->adj_ws = ws;
+    ctx->adj_bytes = bytes;
+    ctx->adj_n = n_steps;
+    ctx->adj_seg = segment;
+    return LBRS_OK;
+}
+
+lbrs_status lbrs_backward_checkpointed(lbrs_ctx* ctx, void* d_adj_ws, const void* d_gbar_T, void* d_gradU0)
+{
+    if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
+    if (!ctx->adj_ws || d_adj_ws != ctx->adj_ws)
+        return fail(ctx, LBRS_ESTATE, "no checkpointed forward run recorded on this adjoint workspace");
+    if (!d_gbar_T || !d_gradU0) return fail(ctx, LBRS_EINVAL, "NULL buffer");
+    const AdjLayout A = adj_layout(ctx, ctx->adj_n, ctx->adj_seg);
+    char* ws = ctx->adj_ws;
+    char* g[2] = {ws + A.gbar0, ws + A.gbar1};
+    char* uhist = ws + A.uhist;
+    const size_t ustride = (size_t)ctx->K * ctx->N * elem_bytes(ctx);
+    LBRS_CUDA(ctx, cudaMemcpyAsync(g[0], d_gbar_T, ctx->L.f_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    int gc = 0;
+    for (int64_t s = A.nseg - 1; s >= 0; --s) {
+        const int64_t start = s * ctx->adj_seg;
+        const int64_t len = start + ctx->adj_seg <= ctx->adj_n ? ctx->adj_seg : ctx->adj_n - start;
+        // recompute the segment from its checkpoint, recording U^{start+1 .. start+len}
+        LBRS_CUDA(ctx, cudaMemcpyAsync(ctx->f[ctx->cur], ws + A.ckpt0 + s * A.ckpt_stride, ctx->L.f_bytes,
+                                       cudaMemcpyDeviceToDevice, ctx->stream));
+        for (int64_t m = 0; m < len; ++m) {
+            LBRS_CUDA(ctx, launch_record_step(ctx, uhist + m * ustride));
+            ctx->cur ^= 1;
+            ctx->launches += 1;
+        }
+        for (int64_t m = len - 1; m >= 0; --m) {
+            LBRS_CUDA(ctx, launch_adjoint_step_raw(ctx, uhist + m * ustride, g[gc], g[gc ^ 1]));
+            gc ^= 1;
+            ctx->launches += 1;
+        }
+    }
+    // dL/dU0 = J_E(U0)^T gbar^0 with U0 the moments of the first checkpoint
+    const int lat = LAT_D2Q4;
+    LBRS_CUDA(ctx, launch_moments(lat, ctx->f64, ws + A.ckpt0, uhist, ctx->f64 ? 0 : 1, ctx->N, ctx->stream));
+    LBRS_CUDA(ctx, launch_vjp_eq_raw(ctx, uhist, g[gc], d_gradU0));
+    ctx->launches += 2;
+    // restore the final forward state
+    LBRS_CUDA(ctx, cudaMemcpyAsync(ctx->f[ctx->cur], ws + A.ckpt0 + A.nseg * A.ckpt_stride, ctx->L.f_bytes,
+                                   cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->step = ctx->adj_step0 + ctx->adj_n;
     return LBRS_OK;
 }
 

@@ -152,6 +152,68 @@ class Solver:
         self._check(self.lib.lbrs_set_distributions(self.ctx, ctypes.c_void_p(f.data_ptr()), 1 if f.is_cuda else 0,
                                                     int(step)))
 
+    # ------------------------------------------------------------------ adjoint (periodic D2Q4)
+    def _fields_tensor(self, n=None):
+        shape = ((n,) if n is not None else ()) + (self.K,) + self.grid
+        return torch.empty(shape, dtype=self.storage_dtype, device=self.device)
+
+    def _dists_tensor(self):
+        return torch.empty((self.Q, self.K) + self.grid, dtype=self.storage_dtype, device=self.device)
+
+    @staticmethod
+    def _ptr(t: torch.Tensor):
+        if not (t.is_cuda and t.is_contiguous()):
+            raise ValueError("expected a contiguous CUDA tensor")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def step_record(self, n: int, U_hist: torch.Tensor | None = None) -> torch.Tensor:
+        """n steps, returning the moments each step's collision used: (n, K, *grid)."""
+        U_hist = self._fields_tensor(n) if U_hist is None else U_hist
+        self._check(self.lib.lbrs_step_record(self.ctx, int(n), self._ptr(U_hist)))
+        return U_hist
+
+    def adjoint_seed(self, dLdU: torch.Tensor) -> torch.Tensor:
+        g = self._dists_tensor()
+        dLdU = dLdU.contiguous()
+        self._check(self.lib.lbrs_adjoint_seed(self.ctx, self._ptr(dLdU), _DTYPE_CODE[dLdU.dtype], self._ptr(g)))
+        return g
+
+    def vjp_loss(self, rho_target: torch.Tensor):
+        """(L, dL/df*) of L = 1/2 sum (rho - rho_target)^2 dx^d for the current state."""
+        g = self._dists_tensor()
+        rho_target = rho_target.contiguous()
+        loss = ctypes.c_double()
+        self._check(self.lib.lbrs_vjp_loss(self.ctx, self._ptr(rho_target), _DTYPE_CODE[rho_target.dtype],
+                                           self._ptr(g), ctypes.byref(loss)))
+        return loss.value, g
+
+    def adjoint_step(self, U_next: torch.Tensor, gbar: torch.Tensor, out: torch.Tensor | None = None):
+        out = self._dists_tensor() if out is None else out
+        self._check(self.lib.lbrs_adjoint_step(self.ctx, self._ptr(U_next), self._ptr(gbar), self._ptr(out)))
+        return out
+
+    def vjp_equilibrium(self, U0: torch.Tensor, gbar0: torch.Tensor) -> torch.Tensor:
+        grad = self._fields_tensor()
+        self._check(self.lib.lbrs_vjp_equilibrium(self.ctx, self._ptr(U0), self._ptr(gbar0), self._ptr(grad)))
+        return grad
+
+    def forward_checkpointed(self, n_steps: int, segment: int | None = None):
+        """n_steps with checkpoints every `segment` steps (default ceil(sqrt(n_steps)))."""
+        import math
+        segment = int(segment or math.ceil(math.sqrt(n_steps)))
+        size = ctypes.c_size_t()
+        self._check(self.lib.lbrs_adjoint_workspace_size(self.ctx, int(n_steps), segment, ctypes.byref(size)))
+        self.adj_ws = torch.empty(size.value, dtype=torch.uint8, device=self.device)
+        self._check(self.lib.lbrs_forward_checkpointed(self.ctx, int(n_steps), segment,
+                                                       self._ptr(self.adj_ws), size.value))
+        return self.adj_ws
+
+    def backward_checkpointed(self, gbar_T: torch.Tensor) -> torch.Tensor:
+        grad = self._fields_tensor()
+        self._check(self.lib.lbrs_backward_checkpointed(self.ctx, self._ptr(self.adj_ws), self._ptr(gbar_T),
+                                                        self._ptr(grad)))
+        return grad
+
     @property
     def step_count(self) -> int:
         v = ctypes.c_int64()
