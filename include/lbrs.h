@@ -236,6 +236,68 @@ lbrs_status lbrs_forward_checkpointed(lbrs_ctx* ctx, int64_t n_steps, int64_t se
  * context's state is the final forward state again on return. */
 lbrs_status lbrs_backward_checkpointed(lbrs_ctx* ctx, void* d_adj_ws, const void* d_gbar_T, void* d_gradU0);
 
+/* ---------------------------------------------------------------- batched D1Q2 tubes
+ *
+ * Many independent 1-D problems (shock tubes) of uneven length advanced
+ * together, each with its own lattice speed lambda_b and number of steps.
+ * All tubes share gamma, omega and the end condition (transmissive or
+ * periodic at both ends).  Distributions are stored concatenated:
+ * f[q][k][off_b + x], off_b = sum of the lengths of the tubes before b;
+ * field arrays are [3][sum N_b].  The step per cell is the D1Q2 step of
+ * Section II.C, identical in arithmetic to the single-tube path; the
+ * kernels advance a tile of a tube by up to `halo` steps in shared memory per
+ * launch (temporal blocking, see lbrs_batch_tuning). */
+typedef struct lbrs_batch lbrs_batch;
+
+typedef struct {
+    uint32_t struct_size;    /* = sizeof(lbrs_batch_config) */
+    int32_t precision;       /* LBRS_F64 or LBRS_F32 */
+    int32_t boundary;        /* LBRS_BC_TRANSMISSIVE or LBRS_BC_PERIODIC, both ends of every tube */
+    int32_t reserved0;
+    int64_t batch;           /* number of tubes, >= 1 */
+    const int64_t* lengths;  /* host [batch]: cells per tube (>= 1); copied at create */
+    const double* lambda;    /* host [batch]: lattice speed per tube (> 0); copied at create */
+    double gamma, omega;
+    void* cuda_stream;
+} lbrs_batch_config;
+
+/* Launch shape of the batched kernel: `block` threads (128, 256 or 512), each
+ * owning `cells_per_thread` window cells; a window is block*cells_per_thread
+ * cells, of which `halo` on each side are recomputed context and the rest
+ * (the tile, >= 32 cells) is advanced by up to `halo` steps per launch. */
+typedef struct {
+    int32_t block, cells_per_thread, halo, reserved;
+} lbrs_batch_tuning;
+
+lbrs_status lbrs_batch_workspace_size(const lbrs_batch_config* cfg, size_t* bytes);
+lbrs_status lbrs_batch_create(const lbrs_batch_config* cfg, void* d_workspace, size_t bytes, lbrs_batch** out);
+void        lbrs_batch_destroy(lbrs_batch* batch);
+
+/* f = f^eq(U(W)) per cell with the cell's tube lambda; W [3][sum N] as in lbrs_set_state. */
+lbrs_status lbrs_batch_set_state(lbrs_batch* batch, const void* W, int on_device, int dtype, int kind);
+
+/* Advance tube b by steps[b] >= 0 steps (host array [batch]).  Asynchronous.
+ * The launch sequence is captured in a CUDA graph and replayed while steps and
+ * tuning stay the same. */
+lbrs_status lbrs_batch_run(lbrs_batch* batch, const int64_t* steps);
+
+/* Conserved fields [3][sum N] of the current state (FP64 sums, written as dtype). */
+lbrs_status lbrs_batch_moments(lbrs_batch* batch, void* U_out, int on_device, int dtype);
+lbrs_status lbrs_batch_get_distributions(lbrs_batch* batch, void* dst, int on_device);
+
+lbrs_status lbrs_batch_get_tuning(const lbrs_batch* batch, lbrs_batch_tuning* tuning);
+lbrs_status lbrs_batch_set_tuning(lbrs_batch* batch, const lbrs_batch_tuning* tuning);
+
+/* Time one launch of every candidate tuning (block in {128, 256, 512},
+ * cells per thread in {1, 2, 4, 8}, halo in {8, 16, 32, 64}) from the current
+ * state for the given steps, keep the fastest per lattice update and return
+ * it (chosen, ns_per_update nullable).  The state is not changed. */
+lbrs_status lbrs_batch_autotune(lbrs_batch* batch, const int64_t* steps, lbrs_batch_tuning* chosen,
+                                double* ns_per_update);
+
+lbrs_status lbrs_batch_launch_count(const lbrs_batch* batch, int64_t* launches);
+const char* lbrs_batch_last_error(const lbrs_batch* batch);
+
 /* Number of time steps taken since the state was set. */
 lbrs_status lbrs_step_count(const lbrs_ctx* ctx, int64_t* steps);
 

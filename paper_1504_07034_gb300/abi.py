@@ -59,6 +59,26 @@ class lbrs_diag(ctypes.Structure):
     ]
 
 
+class lbrs_batch_config(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_uint32),
+        ("precision", ctypes.c_int32),
+        ("boundary", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
+        ("batch", ctypes.c_int64),
+        ("lengths", ctypes.POINTER(ctypes.c_int64)),
+        ("lam", ctypes.POINTER(ctypes.c_double)),
+        ("gamma", ctypes.c_double),
+        ("omega", ctypes.c_double),
+        ("cuda_stream", ctypes.c_void_p),
+    ]
+
+
+class lbrs_batch_tuning(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int32), ("cells_per_thread", ctypes.c_int32), ("halo", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
 # name -> (restype, argtypes)
 _P = ctypes.c_void_p
 _CTX = ctypes.c_void_p
@@ -87,6 +107,19 @@ SIGNATURES = {
     "lbrs_adjoint_workspace_size": (ctypes.c_int, [_CTX, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)]),
     "lbrs_forward_checkpointed": (ctypes.c_int, [_CTX, ctypes.c_int64, ctypes.c_int64, _P, ctypes.c_size_t]),
     "lbrs_backward_checkpointed": (ctypes.c_int, [_CTX, _P, _P, _P]),
+    "lbrs_batch_workspace_size": (ctypes.c_int, [ctypes.POINTER(lbrs_batch_config), ctypes.POINTER(ctypes.c_size_t)]),
+    "lbrs_batch_create": (ctypes.c_int, [ctypes.POINTER(lbrs_batch_config), _P, ctypes.c_size_t, ctypes.POINTER(_CTX)]),
+    "lbrs_batch_destroy": (None, [_CTX]),
+    "lbrs_batch_set_state": (ctypes.c_int, [_CTX, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "lbrs_batch_run": (ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_int64)]),
+    "lbrs_batch_moments": (ctypes.c_int, [_CTX, _P, ctypes.c_int, ctypes.c_int]),
+    "lbrs_batch_get_distributions": (ctypes.c_int, [_CTX, _P, ctypes.c_int]),
+    "lbrs_batch_get_tuning": (ctypes.c_int, [_CTX, ctypes.POINTER(lbrs_batch_tuning)]),
+    "lbrs_batch_set_tuning": (ctypes.c_int, [_CTX, ctypes.POINTER(lbrs_batch_tuning)]),
+    "lbrs_batch_autotune": (ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(lbrs_batch_tuning),
+                                           ctypes.POINTER(ctypes.c_double)]),
+    "lbrs_batch_launch_count": (ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_int64)]),
+    "lbrs_batch_last_error": (ctypes.c_char_p, [_CTX]),
 }
 
 _lib = None

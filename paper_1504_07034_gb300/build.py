@@ -1,12 +1,13 @@
 """Build the LBRS CUDA library (liblbrs.so) in-tree for sm_103a.
 
-Four translation units compiled in parallel with nvcc, then linked into one
+Five translation units compiled in parallel with nvcc, then linked into one
 shared library with the CUDA runtime linked statically:
 
   csrc/lbrs_kernels_f64.cu  FP64 kernels, -fmad=false (rounding as written)
   csrc/lbrs_kernels_f32.cu  FP32 step kernels
   csrc/lbrs_runtime.cu      host C ABI (include/lbrs.h)
   csrc/lbrs_noalloc.cu      diagnostics variant with static scratch, -fmad=false
+  csrc/lbrs_batch_runtime.cu host runtime of the batched tubes
 
 Usage: python -m paper_1504_07034_gb300.build [--force]
 """
@@ -34,8 +35,9 @@ UNITS = {
     "lbrs_kernels_f32.cu": [],
     "lbrs_runtime.cu": [],
     "lbrs_noalloc.cu": ["-fmad=false"],
+    "lbrs_batch_runtime.cu": [],
 }
-HEADERS = [CSRC / "lbrs_kernels.cuh", CSRC / "lbrs_launch.h", INCLUDE / "lbrs.h"]
+HEADERS = [CSRC / "lbrs_kernels.cuh", CSRC / "lbrs_batch.cuh", CSRC / "lbrs_launch.h", INCLUDE / "lbrs.h"]
 
 
 def nvcc() -> str:

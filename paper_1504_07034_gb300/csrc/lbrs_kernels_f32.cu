@@ -15,6 +15,7 @@
 #include <string.h>
 
 #include "lbrs_kernels.cuh"
+#include "lbrs_batch.cuh"
 #include "lbrs_launch.h"
 
 namespace lbrs {
@@ -271,6 +272,51 @@ cudaError_t launch_vjp_equilibrium_f32(const AdjArgs<float>& a, cudaStream_t s)
     int64_t b = (a.N + 255) / 256;
     if (b > 152 * 16) b = 152 * 16;
     vjp_equilibrium2d_kernel<float><<<(unsigned)(b < 1 ? 1 : b), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- batched tubes
+
+cudaError_t launch_batch_f32(const BatchArgs<float>& a, int ntiles, int block, cudaStream_t s)
+{
+    if (ntiles <= 0) return cudaSuccess;
+    const size_t smem = 2 * 6 * (size_t)(a.tile_cells + 2 * a.halo) * sizeof(float);
+    switch (block) {
+        case 128:
+            batch1d_kernel<float, 128><<<ntiles, 128, smem, s>>>(a);
+            break;
+        case 256:
+            batch1d_kernel<float, 256><<<ntiles, 256, smem, s>>>(a);
+            break;
+        case 512:
+            batch1d_kernel<float, 512><<<ntiles, 512, smem, s>>>(a);
+            break;
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t prepare_batch_f32(int block, size_t smem)
+{
+    // opt in to more than the default 48 KiB of dynamic shared memory
+    switch (block) {
+        case 128:
+            return cudaFuncSetAttribute(batch1d_kernel<float, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        case 256:
+            return cudaFuncSetAttribute(batch1d_kernel<float, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        case 512:
+            return cudaFuncSetAttribute(batch1d_kernel<float, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_batch_copy_f32(const float* src, float* dst, int64_t N, const BatchTile* tiles, int ntiles,
+                                     const int64_t* tube_off, cudaStream_t s)
+{
+    if (ntiles <= 0) return cudaSuccess;
+    batch_copy_kernel<float><<<ntiles, 256, 0, s>>>(src, dst, N, tiles, tube_off);
     return cudaGetLastError();
 }
 

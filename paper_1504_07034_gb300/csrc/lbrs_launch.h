@@ -14,6 +14,9 @@ template <typename T>
 struct StepArgs;
 template <typename T>
 struct AdjArgs;
+template <typename T>
+struct BatchArgs;
+struct BatchTile;
 
 // One time step src -> dst.  lattice: LAT_D1Q2 / LAT_D2Q4.
 cudaError_t launch_step_f64(int lattice, const StepArgs<double>& a, cudaStream_t s);
@@ -63,5 +66,22 @@ cudaError_t launch_adjoint_seed(int Q, int K, int storage_f64, const void* dLdU,
 cudaError_t launch_density_loss(int Q, int K, int storage_f64, const void* fs, const void* target, int t_dtype,
                                 void* gbar, int64_t N, double cell_volume, double* partials, double* out,
                                 cudaStream_t s);
+
+// Batched D1Q2 tubes with temporal blocking (lbrs_batch.cuh): one CTA of
+// `block` threads per active tile; dynamic shared memory 2*6*(TILE+2H) elements.
+cudaError_t launch_batch_f64(const BatchArgs<double>& a, int ntiles, int block, cudaStream_t s);
+cudaError_t launch_batch_f32(const BatchArgs<float>& a, int ntiles, int block, cudaStream_t s);
+// Raise the kernel's dynamic shared-memory limit to smem bytes (call before launching or capturing).
+cudaError_t prepare_batch_f64(int block, size_t smem);
+cudaError_t prepare_batch_f32(int block, size_t smem);
+cudaError_t launch_batch_copy_f64(const double* src, double* dst, int64_t N, const BatchTile* tiles, int ntiles,
+                                  const int64_t* tube_off, cudaStream_t s);
+cudaError_t launch_batch_copy_f32(const float* src, float* dst, int64_t N, const BatchTile* tiles, int ntiles,
+                                  const int64_t* tube_off, cudaStream_t s);
+
+// Batched tubes: f = f^eq(U(W)) with each cell's tube lambda (bisection in tube_off).
+cudaError_t launch_batch_set_state(int storage_f64, const void* W, int w_dtype, int kind, void* fs, int64_t N,
+                                   const int64_t* tube_off, int64_t nb, const double* tube_lam, double gamma,
+                                   cudaStream_t s);
 
 }  // namespace lbrs

@@ -236,3 +236,120 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+class BatchSolver:
+    """Many independent D1Q2 tubes (uneven lengths, per-tube lambda) on one GPU.
+
+    lengths, lam  per-tube cell counts and lattice speeds
+    boundary      "transmissive" or "periodic" (both ends of every tube)
+    The state is concatenated: fields (3, sum N), tube b at offsets[b].
+    """
+
+    def __init__(self, lengths, lam, *, gamma: float = 1.4, omega: float = 1.0, boundary: str = "transmissive",
+                 precision: str = "f32", stream: torch.cuda.Stream | None = None):
+        self.lib = abi.load()
+        self.lengths = np.ascontiguousarray(lengths, dtype=np.int64)
+        self.lam = np.ascontiguousarray(lam, dtype=np.float64)
+        self.batch = len(self.lengths)
+        self.N = int(self.lengths.sum())
+        self.offsets = np.concatenate([[0], np.cumsum(self.lengths)[:-1]]).astype(np.int64)
+        self.precision = precision
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        cfg = abi.lbrs_batch_config()
+        cfg.struct_size = ctypes.sizeof(abi.lbrs_batch_config)
+        cfg.precision = _PRECISION[precision]
+        cfg.boundary = abi.BC_KINDS[boundary]
+        cfg.batch = self.batch
+        cfg.lengths = self.lengths.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        cfg.lam = self.lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        cfg.gamma, cfg.omega = float(gamma), float(omega)
+        cfg.cuda_stream = self.stream.cuda_stream or None
+        self.cfg = cfg
+        size = ctypes.c_size_t()
+        abi.check(self.lib.lbrs_batch_workspace_size(ctypes.byref(cfg), ctypes.byref(size)))
+        self.workspace = torch.empty(size.value, dtype=torch.uint8, device=self.device)
+        ctx = ctypes.c_void_p()
+        abi.check(self.lib.lbrs_batch_create(ctypes.byref(cfg), ctypes.c_void_p(self.workspace.data_ptr()),
+                                             size.value, ctypes.byref(ctx)))
+        self.ctx = ctx
+
+    @classmethod
+    def from_tubes(cls, tubes, precision: str = "f32", stream=None):
+        return cls(tubes.lengths, tubes.lam, gamma=tubes.gamma, omega=tubes.omega, precision=precision,
+                   stream=stream)
+
+    @property
+    def storage_dtype(self):
+        return torch.float64 if self.precision == "f64" else torch.float32
+
+    def _check(self, status):
+        if status != abi.LBRS_OK:
+            msg = self.lib.lbrs_batch_last_error(self.ctx) if self.ctx else b""
+            raise abi.LbrsError(status, (msg or b"").decode())
+
+    def set_state(self, W, primitive: bool = True):
+        kind = abi.LBRS_PRIMITIVE if primitive else abi.LBRS_CONSERVED
+        if isinstance(W, np.ndarray):
+            W = torch.from_numpy(np.ascontiguousarray(W))
+        if tuple(W.shape) != (3, self.N):
+            raise ValueError(f"expected shape (3, {self.N}), got {tuple(W.shape)}")
+        W = W.contiguous()
+        self._check(self.lib.lbrs_batch_set_state(self.ctx, ctypes.c_void_p(W.data_ptr()), 1 if W.is_cuda else 0,
+                                                  _DTYPE_CODE[W.dtype], kind))
+        self._keep = W
+
+    def run(self, steps):
+        steps = np.ascontiguousarray(steps, dtype=np.int64)
+        if steps.shape != (self.batch,):
+            raise ValueError("steps must have one entry per tube")
+        self._check(self.lib.lbrs_batch_run(self.ctx, steps.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+
+    def moments(self, dtype=torch.float64, out: torch.Tensor | None = None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty((3, self.N), dtype=dtype, device=self.device)
+        self._check(self.lib.lbrs_batch_moments(self.ctx, ctypes.c_void_p(out.data_ptr()), 1 if out.is_cuda else 0,
+                                                _DTYPE_CODE[out.dtype]))
+        return out
+
+    def get_distributions(self) -> torch.Tensor:
+        out = torch.empty((2, 3, self.N), dtype=self.storage_dtype, device=self.device)
+        self._check(self.lib.lbrs_batch_get_distributions(self.ctx, ctypes.c_void_p(out.data_ptr()), 1))
+        return out
+
+    @property
+    def tuning(self):
+        t = abi.lbrs_batch_tuning()
+        self._check(self.lib.lbrs_batch_get_tuning(self.ctx, ctypes.byref(t)))
+        return (t.block, t.cells_per_thread, t.halo)
+
+    @tuning.setter
+    def tuning(self, value):
+        t = abi.lbrs_batch_tuning(*value, 0)
+        self._check(self.lib.lbrs_batch_set_tuning(self.ctx, ctypes.byref(t)))
+
+    def autotune(self, steps):
+        steps = np.ascontiguousarray(steps, dtype=np.int64)
+        t = abi.lbrs_batch_tuning()
+        ns = ctypes.c_double()
+        self._check(self.lib.lbrs_batch_autotune(self.ctx, steps.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                                 ctypes.byref(t), ctypes.byref(ns)))
+        return (t.block, t.cells_per_thread, t.halo), ns.value
+
+    @property
+    def launch_count(self) -> int:
+        v = ctypes.c_int64()
+        self._check(self.lib.lbrs_batch_launch_count(self.ctx, ctypes.byref(v)))
+        return v.value
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.lbrs_batch_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
