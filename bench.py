@@ -37,6 +37,7 @@ METRIC = "2D LBRS MLUPS FP32 vs FP64 at stated L1 error; % HBM roofline; adjoint
 UNIT = "MLUPS"
 BYTES_PER_LUP_F32 = 128      # 16 FP32 distributions read + 16 written per cell and step
 BYTES_PER_LUP_F64 = 256
+BYTES_PER_LUP_F16NEQ = 80     # U (4 x FP32) + 12 FP16 non-equilibrium parts, read + written
 L2_FLUSH_BYTES = 256 << 20   # twice the 129 MB L2
 CONFIG_STEPS = 1000
 
@@ -186,6 +187,51 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU arm
+
+def oblique_measurement(Solver, stream, barrier, peak):
+    """Oblique shock reflection 4096 x 1024 (512 MiB FP32 state > L2): steady MLUPS of the FP32 and the
+    FP16 non-equilibrium forms, and their density L1 against the FP64 path after the full 20000 steps
+    (omega = 1) and after 2000 steps at omega = 1.5 (where the non-equilibrium part is nonzero)."""
+    import torch
+    out = {"workload": "oblique shock reflection 4096x1024, 200 timed steps per form, CUDA-graph replay, "
+                       "working set larger than L2 (no flush needed)"}
+    for precision, bpl in (("f32", BYTES_PER_LUP_F32), ("f16neq", BYTES_PER_LUP_F16NEQ)):
+        big = workloads.oblique_shock_reflection(steps=200)
+        s = Solver.from_workload(big, precision=precision, stream=stream)
+        with torch.cuda.stream(stream):
+            s.set_state(torch.from_numpy(big.prim).cuda())
+            s.step(64)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            barrier()
+            a.record(stream)
+            s.step(big.steps)
+            b.record(stream)
+            barrier()
+        t = a.elapsed_time(b) / 1e3
+        mlups = big.cells * big.steps / t / 1e6
+        out[precision] = {"value": mlups, "unit": UNIT, "algorithmic_bytes_per_lup": bpl,
+                          "achieved_gbs": bpl * mlups / 1e3, "frac": bpl * mlups / 1e3 / peak}
+        s.close()
+    for omega, steps in ((1.0, 20000), (1.5, 2000)):
+        wl = workloads.oblique_shock_reflection(steps=steps, omega=omega)
+        rho = {}
+        with torch.cuda.stream(stream):
+            for precision in ("f64", "f32", "f16neq"):
+                s = Solver.from_workload(wl, precision=precision, stream=stream)
+                s.set_state(torch.from_numpy(wl.prim).cuda())
+                s.step(steps)
+                rho[precision] = s.moments(torch.float64)[0].clone()
+                if precision == "f64":
+                    out_diag = s.diagnostics()
+                s.close()
+        stream.synchronize()
+        out[f"l1_rho_vs_fp64_omega{omega}_steps{steps}"] = {
+            p: float((rho[p] - rho["f64"]).abs().mean().item()) for p in ("f32", "f16neq")}
+        out[f"fp64_status_omega{omega}"] = out_diag["status"]
+    out["value"] = out["f32"]["value"]
+    out["frac"] = out["f32"]["frac"]
+    return out
+
 
 def batch_measurement(stream, barrier):
     """4096 shock tubes, N log-uniform in [200, 20000], to t = 0.15 in FP32 (temporal blocking)."""
@@ -377,25 +423,7 @@ def run_ours(args):
     l1 = float((rho32 - rho64).abs().mean().item())
 
     # --- steady stepping on a grid larger than L2: the oblique-shock case ------------
-    big = workloads.oblique_shock_reflection(steps=200)
-    sb = Solver.from_workload(big, precision="f32", stream=stream)
-    with torch.cuda.stream(stream):
-        sb.set_state(torch.from_numpy(big.prim).cuda())
-        sb.step(64)                                   # warm-up (graph capture)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        barrier()
-        a.record(stream)
-        sb.step(big.steps)
-        b.record(stream)
-        barrier()
-        d_big = sb.diagnostics()
-    t_big = a.elapsed_time(b) / 1e3
-    mlups_big = big.cells * big.steps / t_big / 1e6
-    sb.close()
-    steady = {"workload": "oblique shock reflection 4096x1024 FP32 (working set 512 MiB > L2), 200 steps, "
-                          "CUDA-graph replay, no flush needed", "value": mlups_big, "unit": UNIT,
-              "achieved_gbs": BYTES_PER_LUP_F32 * mlups_big / 1e3,
-              "frac": BYTES_PER_LUP_F32 * mlups_big / 1e3 / peak, "status": d_big["status"]}
+    steady = oblique_measurement(Solver, stream, barrier, peak)
 
     # --- batched 1-D tubes ---------------------------------------------------------
     batched = batch_measurement(stream, barrier)

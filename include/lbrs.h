@@ -68,8 +68,18 @@ typedef enum {
 
 typedef enum { LBRS_D1Q2 = 0, LBRS_D2Q4 = 1 } lbrs_lattice;
 
-/* Storage and arithmetic precision of the distributions. */
-typedef enum { LBRS_F64 = 0, LBRS_F32 = 1 } lbrs_precision;
+/* Storage and arithmetic precision of the distributions.
+ *   LBRS_F64     FP64 storage and arithmetic (the parity path);
+ *   LBRS_F32     FP32 storage and arithmetic;
+ *   LBRS_F16NEQ  D2Q4 only: per cell the moments U in FP32 plus the
+ *                post-collision non-equilibrium parts f*_q - f^eq_q(U) of
+ *                populations 1-3 in FP16 (per-field power-of-two scale; the
+ *                fourth follows from their zero sum), FP32 arithmetic.
+ *                40 instead of 64 bytes per cell.  Not differentiable (the
+ *                adjoint calls reject it); lbrs_get/set_distributions move the
+ *                raw buffer: U [4][N] FP32, g [3][4][N] FP16, 4 FP32 scales
+ *                (40 N + 16 bytes). */
+typedef enum { LBRS_F64 = 0, LBRS_F32 = 1, LBRS_F16NEQ = 2 } lbrs_precision;
 
 /* Boundary kinds.  The paper defines only the free-slip wall (Section II.E);
  * the others are this library's readings:

@@ -1,10 +1,11 @@
 """Build the LBRS CUDA library (liblbrs.so) in-tree for sm_103a.
 
-Five translation units compiled in parallel with nvcc, then linked into one
+Six translation units compiled in parallel with nvcc, then linked into one
 shared library with the CUDA runtime linked statically:
 
   csrc/lbrs_kernels_f64.cu  FP64 kernels, -fmad=false (rounding as written)
   csrc/lbrs_kernels_f32.cu  FP32 step kernels
+  csrc/lbrs_kernels_f16.cu  D2Q4 step with FP16 non-equilibrium storage
   csrc/lbrs_runtime.cu      host C ABI (include/lbrs.h)
   csrc/lbrs_noalloc.cu      diagnostics variant with static scratch, -fmad=false
   csrc/lbrs_batch_runtime.cu host runtime of the batched tubes
@@ -33,6 +34,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler",
 UNITS = {
     "lbrs_kernels_f64.cu": ["-fmad=false"],
     "lbrs_kernels_f32.cu": [],
+    "lbrs_kernels_f16.cu": [],
     "lbrs_runtime.cu": [],
     "lbrs_noalloc.cu": ["-fmad=false"],
     "lbrs_batch_runtime.cu": [],

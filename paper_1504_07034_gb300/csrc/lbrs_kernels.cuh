@@ -30,7 +30,10 @@
 namespace lbrs {
 
 enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_DIRICHLET = 2, BC_WALL = 3 };
-enum { LAT_D1Q2 = 0, LAT_D2Q4 = 1 };
+// LAT_U2D: a D2Q4 state stored as its moments U directly (the FP16
+// non-equilibrium form keeps U in FP32): read-outs treat it as one
+// "population" per field.
+enum { LAT_D1Q2 = 0, LAT_D2Q4 = 1, LAT_U2D = 2 };
 enum { KIND_CONSERVED = 0, KIND_PRIMITIVE = 1 };
 
 // Ghost-table stride: one Dirichlet side holds Q*K <= 16 values.

@@ -35,6 +35,10 @@ template <>
 struct Dims<LAT_D1Q2> {
     static constexpr int Q = 2, K = 3;
 };
+template <>
+struct Dims<LAT_U2D> {
+    static constexpr int Q = 1, K = 4;
+};
 
 // f^eq in FP64 for either lattice, e[q*K + k]
 template <int LAT>
@@ -174,7 +178,7 @@ __global__ void __launch_bounds__(kThreads) diag_partial_kernel(const Ts* __rest
             finite = finite && isfinite(s);
         }
         double p, lam;
-        if constexpr (LAT == LAT_D2Q4) {
+        if constexpr (K == 4) {
             const double u = U[1] / U[0], v = U[2] / U[0];
             p = (gamma - 1.0) * (U[3] - 0.5 * (U[1] * u + U[2] * v));
             const double s1 = fabs(u + v), s2 = fabs(u - v);
@@ -458,7 +462,8 @@ static void moments_dispatch(int storage_f64, const void* fs, void* U, int out_d
 cudaError_t launch_moments(int lattice, int storage_f64, const void* fs, void* U, int out_dtype, int64_t N,
                            cudaStream_t s)
 {
-    if (lattice == LAT_D2Q4) moments_dispatch<LAT_D2Q4>(storage_f64, fs, U, out_dtype, N, s);
+    if (lattice == LAT_U2D) moments_dispatch<LAT_U2D>(0, fs, U, out_dtype, N, s);
+    else if (lattice == LAT_D2Q4) moments_dispatch<LAT_D2Q4>(storage_f64, fs, U, out_dtype, N, s);
     else moments_dispatch<LAT_D1Q2>(storage_f64, fs, U, out_dtype, N, s);
     return cudaGetLastError();
 }
@@ -468,7 +473,9 @@ int diag_blocks() { return kDiagBlocks; }
 cudaError_t launch_diag(int lattice, int storage_f64, const void* fs, int64_t N, double gamma, double lambda,
                         double cell_volume, double* partials, double* out, cudaStream_t s)
 {
-    if (lattice == LAT_D2Q4) {
+    if (lattice == LAT_U2D) {
+        diag_partial_kernel<float, LAT_U2D><<<kDiagBlocks, kThreads, 0, s>>>((const float*)fs, N, gamma, lambda, partials);
+    } else if (lattice == LAT_D2Q4) {
         if (storage_f64) diag_partial_kernel<double, LAT_D2Q4><<<kDiagBlocks, kThreads, 0, s>>>((const double*)fs, N, gamma, lambda, partials);
         else diag_partial_kernel<float, LAT_D2Q4><<<kDiagBlocks, kThreads, 0, s>>>((const float*)fs, N, gamma, lambda, partials);
     } else {

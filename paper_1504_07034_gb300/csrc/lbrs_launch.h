@@ -84,4 +84,21 @@ cudaError_t launch_batch_set_state(int storage_f64, const void* W, int w_dtype, 
                                    const int64_t* tube_off, int64_t nb, const double* tube_lam, double gamma,
                                    cudaStream_t s);
 
+// FP16 non-equilibrium form (lbrs_kernels_f16.cu).  A state buffer holds U as
+// [4][N] FP32, g as [3][4][N] FP16 and the four per-field scales (FP32):
+// 40 N + 16 bytes.
+struct F16StepArgs {
+    const void* src;
+    void* dst;
+    const float* ghost;    // [4][GHOST_STRIDE] f of the Dirichlet states (FP32)
+    int64_t N;
+    int nx, ny;
+    int bc[4];
+    float om, om1, c, gm1;
+};
+cudaError_t launch_step_f16neq(const F16StepArgs& a, cudaStream_t s);
+// U = U(W) in FP32, g = 0, then the per-field scales from max |U_k| (absmax_bits: 4 words of scratch).
+cudaError_t launch_set_state_f16neq(const void* W, int w_dtype, int kind, void* fs, int64_t N, double gamma,
+                                    unsigned int* absmax_bits, cudaStream_t s);
+
 }  // namespace lbrs

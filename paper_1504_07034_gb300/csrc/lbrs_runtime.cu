@@ -29,7 +29,7 @@ thread_local char g_err[512] = "";
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t f_bytes, f0, f1, ghost, partials, diag_out, total;
+    size_t f_bytes, f0, f1, ghost, partials, diag_out, scale, total;
 };
 
 int lattice_q(int lat) { return lat == LBRS_D2Q4 ? 4 : 2; }
@@ -40,7 +40,8 @@ Layout layout_of(const lbrs_config* c)
     Layout L;
     const size_t elem = c->precision == LBRS_F64 ? 8 : 4;
     const size_t N = (size_t)c->nx * (size_t)c->ny;
-    L.f_bytes = N * (size_t)(lattice_q(c->lattice) * lattice_k(c->lattice)) * elem;
+    L.f_bytes = c->precision == LBRS_F16NEQ ? N * (4 * 4 + 12 * 2) + 4 * sizeof(float)
+                                            : N * (size_t)(lattice_q(c->lattice) * lattice_k(c->lattice)) * elem;
     size_t off = 0;
     L.f0 = off;
     off += align_up(L.f_bytes);
@@ -52,6 +53,8 @@ Layout layout_of(const lbrs_config* c)
     off += align_up((size_t)diag_blocks() * DIAG_W * sizeof(double));
     L.diag_out = off;
     off += align_up(DIAG_W * sizeof(double));
+    L.scale = off;                                   // FP16 form: 4 words of scratch for the scales
+    off += align_up(4 * sizeof(float));
     L.total = off;
     return L;
 }
@@ -61,7 +64,7 @@ Layout layout_of(const lbrs_config* c)
 struct lbrs_ctx {
     lbrs_config cfg;
     Layout L;
-    int lattice, f64, Q, K;
+    int lattice, f64, f16, Q, K;
     int64_t N;
     char* ws;
     char* f[2];
@@ -114,8 +117,10 @@ lbrs_status validate(const lbrs_config* c)
                     sizeof(lbrs_config));
     if (c->lattice != LBRS_D1Q2 && c->lattice != LBRS_D2Q4)
         return fail(nullptr, LBRS_EINVAL, "unknown lattice %d", c->lattice);
-    if (c->precision != LBRS_F64 && c->precision != LBRS_F32)
+    if (c->precision != LBRS_F64 && c->precision != LBRS_F32 && c->precision != LBRS_F16NEQ)
         return fail(nullptr, LBRS_EINVAL, "unknown precision %d", c->precision);
+    if (c->precision == LBRS_F16NEQ && c->lattice != LBRS_D2Q4)
+        return fail(nullptr, LBRS_EINVAL, "LBRS_F16NEQ is a D2Q4 storage form");
     if (c->nx < 1 || c->ny < 1) return fail(nullptr, LBRS_EINVAL, "grid must have nx, ny >= 1");
     if (c->nx > (1LL << 30)) return fail(nullptr, LBRS_EINVAL, "nx too large (max 2^30)");
     if (c->lattice == LBRS_D1Q2 && c->ny != 1) return fail(nullptr, LBRS_EINVAL, "D1Q2 needs ny == 1");
@@ -170,7 +175,29 @@ cudaError_t launch_one_step(lbrs_ctx* ctx, int from, cudaStream_t s)
 {
     const int lat = ctx->lattice == LBRS_D2Q4 ? LAT_D2Q4 : LAT_D1Q2;
     if (ctx->f64) return launch_step_f64(lat, step_args<double>(ctx, from), s);
+    if (ctx->f16) {
+        F16StepArgs a;
+        a.src = ctx->f[from];
+        a.dst = ctx->f[from ^ 1];
+        a.ghost = (const float*)(ctx->ws + ctx->L.ghost);
+        a.N = ctx->N;
+        a.nx = (int)ctx->cfg.nx;
+        a.ny = (int)ctx->cfg.ny;
+        for (int k = 0; k < 4; ++k) a.bc[k] = ctx->cfg.bc[k].kind;
+        a.om = (float)ctx->cfg.omega;
+        a.om1 = (float)(1.0 - ctx->cfg.omega);
+        a.c = (float)ctx->c;
+        a.gm1 = (float)(ctx->cfg.gamma - 1.0);
+        return launch_step_f16neq(a, s);
+    }
     return launch_step_f32(lat, step_args<float>(ctx, from), s);
+}
+
+// Lattice code of the read-out kernels (moments, diagnostics) for this storage.
+int readout_lattice(const lbrs_ctx* ctx)
+{
+    if (ctx->f16) return LAT_U2D;
+    return ctx->lattice == LBRS_D2Q4 ? LAT_D2Q4 : LAT_D1Q2;
 }
 
 // Capture kGraphSteps step kernels starting from buffer `from` into graph[from].
@@ -209,6 +236,7 @@ size_t elem_bytes(const lbrs_ctx* ctx) { return ctx->f64 ? 8 : 4; }
 lbrs_status adjoint_supported(lbrs_ctx* ctx)
 {
     if (ctx->lattice != LBRS_D2Q4) return fail(ctx, LBRS_EINVAL, "the adjoint covers D2Q4 only");
+    if (ctx->f16) return fail(ctx, LBRS_EINVAL, "the adjoint covers the F64 and F32 forms only");
     for (int s = 0; s < 4; ++s)
         if (ctx->cfg.bc[s].kind != LBRS_BC_PERIODIC)
             return fail(ctx, LBRS_EINVAL, "the adjoint covers fully periodic domains only");
@@ -338,6 +366,7 @@ lbrs_status lbrs_create(const lbrs_config* cfg, void* d_workspace, size_t bytes,
     ctx->L = L;
     ctx->lattice = cfg->lattice;
     ctx->f64 = cfg->precision == LBRS_F64;
+    ctx->f16 = cfg->precision == LBRS_F16NEQ;
     ctx->Q = lattice_q(cfg->lattice);
     ctx->K = lattice_k(cfg->lattice);
     ctx->N = cfg->nx * cfg->ny;
@@ -388,8 +417,14 @@ lbrs_status lbrs_set_state(lbrs_ctx* ctx, const void* W, int on_device, int dtyp
         src = stage;
     }
     const int lat = ctx->lattice == LBRS_D2Q4 ? LAT_D2Q4 : LAT_D1Q2;
-    LBRS_CUDA(ctx, launch_set_state(lat, ctx->f64, src, dtype == LBRS_F32, kind, ctx->f[ctx->cur], ctx->N,
-                                    ctx->cfg.gamma, ctx->c, ctx->stream));
+    if (ctx->f16) {
+        LBRS_CUDA(ctx, launch_set_state_f16neq(src, dtype == LBRS_F32, kind, ctx->f[ctx->cur], ctx->N, ctx->cfg.gamma,
+                                               (unsigned int*)(ctx->ws + ctx->L.scale), ctx->stream));
+        ctx->launches += 3;
+    } else {
+        LBRS_CUDA(ctx, launch_set_state(lat, ctx->f64, src, dtype == LBRS_F32, kind, ctx->f[ctx->cur], ctx->N,
+                                        ctx->cfg.gamma, ctx->c, ctx->stream));
+    }
     ctx->launches += 1;
     if (!on_device) LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));   // host W is consumed on return
     ctx->has_state = true;
@@ -437,9 +472,9 @@ lbrs_status lbrs_moments(lbrs_ctx* ctx, void* U_out, int on_device, int dtype)
     if (!U_out) return fail(ctx, LBRS_EINVAL, "U_out is NULL");
     if (dtype != LBRS_F64 && dtype != LBRS_F32) return fail(ctx, LBRS_EINVAL, "dtype must be LBRS_F64 or LBRS_F32");
     if (!ctx->has_state) return fail(ctx, LBRS_ESTATE, "no state set");
-    const int lat = ctx->lattice == LBRS_D2Q4 ? LAT_D2Q4 : LAT_D1Q2;
     void* dst = on_device ? U_out : (void*)ctx->f[ctx->cur ^ 1];
-    LBRS_CUDA(ctx, launch_moments(lat, ctx->f64, ctx->f[ctx->cur], dst, dtype == LBRS_F32, ctx->N, ctx->stream));
+    LBRS_CUDA(ctx, launch_moments(readout_lattice(ctx), ctx->f64, ctx->f[ctx->cur], dst, dtype == LBRS_F32, ctx->N,
+                                  ctx->stream));
     ctx->launches += 1;
     if (!on_device) {
         LBRS_CUDA(ctx, cudaMemcpyAsync(U_out, dst, field_bytes(ctx, dtype), cudaMemcpyDeviceToHost, ctx->stream));
@@ -453,7 +488,7 @@ lbrs_status lbrs_diagnostics(lbrs_ctx* ctx, lbrs_diag* out)
     if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
     if (!out) return fail(ctx, LBRS_EINVAL, "out is NULL");
     if (!ctx->has_state) return fail(ctx, LBRS_ESTATE, "no state set");
-    const int lat = ctx->lattice == LBRS_D2Q4 ? LAT_D2Q4 : LAT_D1Q2;
+    const int lat = readout_lattice(ctx);
     const double vol = ctx->lattice == LBRS_D2Q4 ? ctx->cfg.dx * ctx->cfg.dx : ctx->cfg.dx;
     double* partials = (double*)(ctx->ws + ctx->L.partials);
     double* dout = (double*)(ctx->ws + ctx->L.diag_out);
@@ -520,7 +555,8 @@ lbrs_status lbrs_step_record(lbrs_ctx* ctx, int64_t n, void* d_U_hist)
     if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
     if (n < 0) return fail(ctx, LBRS_EINVAL, "negative step count");
     if (n > 0 && !d_U_hist) return fail(ctx, LBRS_EINVAL, "d_U_hist is NULL");
-    if (ctx->lattice != LBRS_D2Q4) return fail(ctx, LBRS_EINVAL, "recording steps cover D2Q4 only");
+    if (ctx->lattice != LBRS_D2Q4 || ctx->f16)
+        return fail(ctx, LBRS_EINVAL, "recording steps cover the F64 and F32 D2Q4 forms only");
     if (!ctx->has_state) return fail(ctx, LBRS_ESTATE, "no state set");
     const size_t stride = (size_t)ctx->K * ctx->N * elem_bytes(ctx);
     for (int64_t m = 0; m < n; ++m) {
@@ -548,6 +584,7 @@ lbrs_status lbrs_vjp_loss(lbrs_ctx* ctx, const void* d_rho_target, int dtype, vo
     if (!d_rho_target || !d_gbar) return fail(ctx, LBRS_EINVAL, "NULL buffer");
     if (dtype != LBRS_F64 && dtype != LBRS_F32) return fail(ctx, LBRS_EINVAL, "dtype must be LBRS_F64 or LBRS_F32");
     if (!ctx->has_state) return fail(ctx, LBRS_ESTATE, "no state set");
+    if (ctx->f16) return fail(ctx, LBRS_EINVAL, "the adjoint covers the F64 and F32 forms only");
     const double vol = ctx->lattice == LBRS_D2Q4 ? ctx->cfg.dx * ctx->cfg.dx : ctx->cfg.dx;
     double* partials = (double*)(ctx->ws + ctx->L.partials);
     double* dout = (double*)(ctx->ws + ctx->L.diag_out);
