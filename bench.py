@@ -188,6 +188,33 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ GPU arm
 
+def sod_measurement(Solver, stream, barrier):
+    """Sod shock tube, D1Q2, 1000 cells, t = 0.2 (461 steps): wall time of the FP64 and FP32 runs and the
+    density L1 against the exact Riemann solution (a latency-bound case, not a roofline case)."""
+    import torch
+    from workloads import riemann
+    wl = workloads.sod(1000)
+    exact = riemann.sample(wl.gamma, wl.meta["left"], wl.meta["right"], (wl.x - 0.5) / wl.t_final)[0]
+    out = {"workload": "Sod D1Q2, 1000 cells on [0, 1], t = 0.2, %d steps, lambda %.4f" % (wl.steps, wl.lam)}
+    for precision in ("f64", "f32"):
+        s = Solver.from_workload(wl, precision=precision, stream=stream)
+        with torch.cuda.stream(stream):
+            s.set_state(torch.from_numpy(wl.prim).cuda())
+            s.step(wl.steps)                      # warm-up (graph capture)
+            s.set_state(torch.from_numpy(wl.prim).cuda())
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            barrier()
+            a.record(stream)
+            s.step(wl.steps)
+            b.record(stream)
+            barrier()
+            rho = s.moments(torch.float64)[0].cpu().numpy()
+        out[precision] = {"ms": a.elapsed_time(b), "mlups": wl.nx * wl.steps / (a.elapsed_time(b) / 1e3) / 1e6,
+                          "l1_rho_vs_exact_riemann": float(np.mean(np.abs(rho - exact)))}
+        s.close()
+    return out
+
+
 def oblique_measurement(Solver, stream, barrier, peak):
     """Oblique shock reflection 4096 x 1024 (512 MiB FP32 state > L2): steady MLUPS of the FP32 and the
     FP16 non-equilibrium forms, and their density L1 against the FP64 path after the full 20000 steps
@@ -425,6 +452,9 @@ def run_ours(args):
     # --- steady stepping on a grid larger than L2: the oblique-shock case ------------
     steady = oblique_measurement(Solver, stream, barrier, peak)
 
+    # --- Sod shock tube (1-D, latency-bound) ------------------------------------------
+    sod = sod_measurement(Solver, stream, barrier)
+
     # --- batched 1-D tubes ---------------------------------------------------------
     batched = batch_measurement(stream, barrier)
 
@@ -461,6 +491,7 @@ def run_ours(args):
                          "algorithmic_bytes_per_lup": BYTES_PER_LUP_F32},
             "steady_large_grid": steady,
             "adjoint": adjoint,
+            "sod_1d": sod,
             "batched_tubes": batched,
             "fp64": {"value": mlups64, "unit": UNIT, "achieved_gbs": BYTES_PER_LUP_F64 * mlups64 / 1e3,
                      "diag_after_1000_steps": {k: d64[k] for k in ("status", "min_rho", "min_p", "max_lambda_local")}},

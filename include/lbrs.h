@@ -102,7 +102,7 @@ typedef struct {
     uint32_t struct_size;   /* = sizeof(lbrs_config), for ABI growth */
     int32_t lattice;        /* lbrs_lattice */
     int32_t precision;      /* lbrs_precision */
-    int32_t reserved0;
+    int32_t diag_every;     /* > 0: check the state every diag_every steps on the device (see lbrs_sync); 0: off */
     int64_t nx, ny;         /* cells; ny = 1 for D1Q2 */
     double gamma;           /* ratio of specific heats, > 1 */
     double lambda;          /* lattice speed, > 0; dt = dx / lambda */
@@ -157,8 +157,18 @@ lbrs_status lbrs_set_state(lbrs_ctx* ctx, const void* W, int on_device, int dtyp
  * Asynchronous.  ESTATE if no state was set. */
 lbrs_status lbrs_step(lbrs_ctx* ctx, int64_t n);
 
-/* Wait for the context's stream; reports a CUDA error raised by earlier work. */
+/* Wait for the context's stream; reports a CUDA error raised by earlier work.
+ * With cfg.diag_every > 0, lbrs_step runs the FP64 diagnostics reduction of
+ * lbrs_diagnostics on the device after every diag_every-th step and records
+ * the first step at which a cell was non-physical or exceeded the lattice
+ * speed bound (Sections II.A, II.D); lbrs_sync then returns LBRS_ENONPHYS or
+ * LBRS_ESUBCHAR from that step on (the state is left as computed, for
+ * inspection) and lbrs_first_bad_step gives the step.  Setting a state clears
+ * the record. */
 lbrs_status lbrs_sync(lbrs_ctx* ctx);
+
+/* First step flagged by the periodic device checks (-1 if none); synchronises. */
+lbrs_status lbrs_first_bad_step(lbrs_ctx* ctx, int64_t* step);
 
 /* Conserved moments U_k = sum_q f_{q,k} of the current state (moment relations,
  * Section II), summed in FP64 in q order and written as `dtype` to U_out [K][ny][nx].

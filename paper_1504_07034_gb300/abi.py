@@ -35,7 +35,7 @@ class lbrs_config(ctypes.Structure):
         ("struct_size", ctypes.c_uint32),
         ("lattice", ctypes.c_int32),
         ("precision", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32),
+        ("diag_every", ctypes.c_int32),
         ("nx", ctypes.c_int64),
         ("ny", ctypes.c_int64),
         ("gamma", ctypes.c_double),
@@ -91,6 +91,7 @@ SIGNATURES = {
     "lbrs_set_state": (ctypes.c_int, [_CTX, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "lbrs_step": (ctypes.c_int, [_CTX, ctypes.c_int64]),
     "lbrs_sync": (ctypes.c_int, [_CTX]),
+    "lbrs_first_bad_step": (ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_int64)]),
     "lbrs_moments": (ctypes.c_int, [_CTX, _P, ctypes.c_int, ctypes.c_int]),
     "lbrs_diagnostics": (ctypes.c_int, [_CTX, ctypes.POINTER(lbrs_diag)]),
     "lbrs_diagnostics_noalloc": (ctypes.c_int, [ctypes.POINTER(lbrs_config), _P, ctypes.POINTER(lbrs_diag)]),

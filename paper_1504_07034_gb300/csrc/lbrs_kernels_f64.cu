@@ -154,51 +154,60 @@ __device__ __forceinline__ DiagAcc diag_shfl_down(const DiagAcc& a, int off)
 
 // Per-cell checks of Sections II.A/II.D: rho > 0, p > 0, finite moments, and
 // the local bound |u| + a (1-D) or max(|u+v|, |u-v|) + sqrt(2) a (2-D) <= lambda.
+// The checks run in the storage precision R (FP64 arithmetic is slow on this
+// GPU and FP32 states gain nothing from it); the totals accumulate in FP64.
 template <typename Ts, int LAT>
 __global__ void __launch_bounds__(kThreads) diag_partial_kernel(const Ts* __restrict__ fs, int64_t N, double gamma,
                                                                 double lambda, double* __restrict__ partials)
 {
     constexpr int Q = Dims<LAT>::Q, K = Dims<LAT>::K;
+    using R = Ts;
+    const R g = (R)gamma, gm1 = (R)(gamma - 1.0), lam_max = (R)lambda;
     DiagAcc acc;
 #pragma unroll
     for (int k = 0; k < 4; ++k) acc.tot[k] = 0.0;
     acc.min_rho = acc.min_p = INFINITY;
     acc.max_lam = 0.0;
     acc.nbad = acc.nsub = 0.0;
+    R mn_rho = (R)INFINITY, mn_p = (R)INFINITY, mx_lam = (R)0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        double U[4] = {0.0, 0.0, 0.0, 0.0};
+        R U[4] = {0, 0, 0, 0};
         bool finite = true;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            double s = (double)fs[(0 * K + k) * N + i];
+            R s = fs[(0 * K + k) * N + i];
 #pragma unroll
-            for (int q = 1; q < Q; ++q) s += (double)fs[(q * K + k) * N + i];
+            for (int q = 1; q < Q; ++q) s += fs[(q * K + k) * N + i];
             U[k] = s;
-            acc.tot[k] += s;
+            acc.tot[k] += (double)s;
             finite = finite && isfinite(s);
         }
-        double p, lam;
+        const R inv = (R)1 / U[0];
+        R p, lam;
         if constexpr (K == 4) {
-            const double u = U[1] / U[0], v = U[2] / U[0];
-            p = (gamma - 1.0) * (U[3] - 0.5 * (U[1] * u + U[2] * v));
-            const double s1 = fabs(u + v), s2 = fabs(u - v);
-            lam = (s1 > s2 ? s1 : s2) + sqrt(2.0) * sqrt(gamma * p / U[0]);
+            const R u = U[1] * inv, v = U[2] * inv;
+            p = gm1 * (U[3] - (R)0.5 * (U[1] * u + U[2] * v));
+            const R s1 = fabs(u + v), s2 = fabs(u - v);
+            lam = (s1 > s2 ? s1 : s2) + sqrt((R)2 * g * p * inv);
         } else {
-            const double u = U[1] / U[0];
-            p = (gamma - 1.0) * (U[2] - 0.5 * (U[1] * u));
-            lam = fabs(u) + sqrt(gamma * p / U[0]);
+            const R u = U[1] * inv;
+            p = gm1 * (U[2] - (R)0.5 * (U[1] * u));
+            lam = fabs(u) + sqrt(g * p * inv);
         }
         if (finite) {
-            acc.min_rho = fmin(acc.min_rho, U[0]);
-            acc.min_p = fmin(acc.min_p, p);
+            mn_rho = fmin(mn_rho, U[0]);
+            mn_p = fmin(mn_p, p);
         }
-        if (!finite || !(U[0] > 0.0) || !(p > 0.0)) {
+        if (!finite || !(U[0] > (R)0) || !(p > (R)0)) {
             acc.nbad += 1.0;
         } else {
-            acc.max_lam = fmax(acc.max_lam, lam);
-            if (lam > lambda) acc.nsub += 1.0;
+            mx_lam = fmax(mx_lam, lam);
+            if (lam > lam_max) acc.nsub += 1.0;
         }
     }
+    acc.min_rho = (double)mn_rho;
+    acc.min_p = (double)mn_p;
+    acc.max_lam = (double)mx_lam;
     // warp, then block, in a fixed order
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) diag_combine(acc, diag_shfl_down(acc, off));
@@ -322,9 +331,42 @@ __global__ void __launch_bounds__(kThreads) batch_set_state_kernel(const Tin* __
     }
 }
 
+// Record of the periodic checks: [0] first bad step (-1 none), [1] non-physical
+// cells then, [2] cells over lambda then, [3] max local bound over all checks.
+__global__ void status_reset_kernel(double* status)
+{
+    if (threadIdx.x == 0) {
+        status[0] = -1.0;
+        status[1] = status[2] = status[3] = 0.0;
+    }
+}
+
+__global__ void status_update_kernel(const double* __restrict__ diag, double* __restrict__ status, double step)
+{
+    if (threadIdx.x != 0) return;
+    status[3] = fmax(status[3], diag[6]);
+    if ((diag[7] > 0.0 || diag[8] > 0.0) && status[0] < 0.0) {
+        status[0] = step;
+        status[1] = diag[7];
+        status[2] = diag[8];
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
+
+cudaError_t launch_status_reset(double* status, cudaStream_t s)
+{
+    status_reset_kernel<<<1, 32, 0, s>>>(status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_status_update(const double* diag_out, double* status, int64_t step, cudaStream_t s)
+{
+    status_update_kernel<<<1, 32, 0, s>>>(diag_out, status, (double)step);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_batch_set_state(int storage_f64, const void* W, int w_dtype, int kind, void* fs, int64_t N,
                                    const int64_t* tube_off, int64_t nb, const double* tube_lam, double gamma,

@@ -46,6 +46,10 @@ int diag_blocks();
 cudaError_t launch_diag(int lattice, int storage_f64, const void* fs, int64_t N, double gamma, double lambda,
                         double cell_volume, double* partials, double* out, cudaStream_t s);
 
+// Periodic device checks: reset the status record, fold one diagnostics result into it.
+cudaError_t launch_status_reset(double* status, cudaStream_t s);
+cudaError_t launch_status_update(const double* diag_out, double* status, int64_t step, cudaStream_t s);
+
 // Recording step (D2Q4): the step above that also writes its moments to a.Uout.
 cudaError_t launch_step_record_f64(const StepArgs<double>& a, cudaStream_t s);
 cudaError_t launch_step_record_f32(const StepArgs<float>& a, cudaStream_t s);

@@ -88,52 +88,58 @@ __device__ __forceinline__ Acc shfl_down(const Acc& a, int off)
     return b;
 }
 
-// Same per-cell checks and fixed-order reduction as lbrs_diagnostics; the
-// partial records go to the static scratch (its device address is `scratch`).
+// Same per-cell checks (in the storage precision, totals in FP64) and fixed-order
+// reduction as lbrs_diagnostics; the partial records go to the static scratch
+// (its device address is `scratch`).
 template <typename Ts, int Q, int K>
 __global__ void __launch_bounds__(kThreads) noalloc_partial_kernel(const Ts* __restrict__ fs, int64_t N, double gamma,
                                                                    double lambda, double* __restrict__ scratch)
 {
+    using R = Ts;
+    const R g = (R)gamma, gm1 = (R)(gamma - 1.0), lam_max = (R)lambda;
     Acc acc;
 #pragma unroll
     for (int k = 0; k < 4; ++k) acc.tot[k] = 0.0;
-    acc.min_rho = acc.min_p = INFINITY;
-    acc.max_lam = 0.0;
     acc.nbad = acc.nsub = 0.0;
+    R mn_rho = (R)INFINITY, mn_p = (R)INFINITY, mx_lam = (R)0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        double U[4] = {0.0, 0.0, 0.0, 0.0};
+        R U[4] = {0, 0, 0, 0};
         bool finite = true;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            double s = (double)fs[(0 * K + k) * N + i];
+            R s = fs[(0 * K + k) * N + i];
 #pragma unroll
-            for (int q = 1; q < Q; ++q) s += (double)fs[(q * K + k) * N + i];
+            for (int q = 1; q < Q; ++q) s += fs[(q * K + k) * N + i];
             U[k] = s;
-            acc.tot[k] += s;
+            acc.tot[k] += (double)s;
             finite = finite && isfinite(s);
         }
-        double p, lam;
+        const R inv = (R)1 / U[0];
+        R p, lam;
         if (K == 4) {
-            const double u = U[1] / U[0], v = U[2] / U[0];
-            p = (gamma - 1.0) * (U[3] - 0.5 * (U[1] * u + U[2] * v));
-            const double s1 = fabs(u + v), s2 = fabs(u - v);
-            lam = (s1 > s2 ? s1 : s2) + sqrt(2.0) * sqrt(gamma * p / U[0]);
+            const R u = U[1] * inv, v = U[2] * inv;
+            p = gm1 * (U[3] - (R)0.5 * (U[1] * u + U[2] * v));
+            const R s1 = fabs(u + v), s2 = fabs(u - v);
+            lam = (s1 > s2 ? s1 : s2) + sqrt((R)2 * g * p * inv);
         } else {
-            const double u = U[1] / U[0];
-            p = (gamma - 1.0) * (U[2] - 0.5 * (U[1] * u));
-            lam = fabs(u) + sqrt(gamma * p / U[0]);
+            const R u = U[1] * inv;
+            p = gm1 * (U[2] - (R)0.5 * (U[1] * u));
+            lam = fabs(u) + sqrt(g * p * inv);
         }
         if (finite) {
-            acc.min_rho = fmin(acc.min_rho, U[0]);
-            acc.min_p = fmin(acc.min_p, p);
+            mn_rho = fmin(mn_rho, U[0]);
+            mn_p = fmin(mn_p, p);
         }
-        if (!finite || !(U[0] > 0.0) || !(p > 0.0)) {
+        if (!finite || !(U[0] > (R)0) || !(p > (R)0)) {
             acc.nbad += 1.0;
         } else {
-            acc.max_lam = fmax(acc.max_lam, lam);
-            if (lam > lambda) acc.nsub += 1.0;
+            mx_lam = fmax(mx_lam, lam);
+            if (lam > lam_max) acc.nsub += 1.0;
         }
     }
+    acc.min_rho = (double)mn_rho;
+    acc.min_p = (double)mn_p;
+    acc.max_lam = (double)mx_lam;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) combine(acc, shfl_down(acc, off));
     __shared__ Acc warp_acc[kThreads / 32];

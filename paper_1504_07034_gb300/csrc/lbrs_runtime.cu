@@ -29,7 +29,7 @@ thread_local char g_err[512] = "";
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t f_bytes, f0, f1, ghost, partials, diag_out, scale, total;
+    size_t f_bytes, f0, f1, ghost, partials, diag_out, scale, status, total;
 };
 
 int lattice_q(int lat) { return lat == LBRS_D2Q4 ? 4 : 2; }
@@ -55,6 +55,8 @@ Layout layout_of(const lbrs_config* c)
     off += align_up(DIAG_W * sizeof(double));
     L.scale = off;                                   // FP16 form: 4 words of scratch for the scales
     off += align_up(4 * sizeof(float));
+    L.status = off;                                  // record of the periodic device checks
+    off += align_up(4 * sizeof(double));
     L.total = off;
     return L;
 }
@@ -129,6 +131,7 @@ lbrs_status validate(const lbrs_config* c)
     if (!finite_pos(c->lambda)) return fail(nullptr, LBRS_EINVAL, "lambda must be positive");
     if (!(c->omega > 0.0 && c->omega < 2.0)) return fail(nullptr, LBRS_EINVAL, "omega must lie in (0, 2)");
     if (!finite_pos(c->dx)) return fail(nullptr, LBRS_EINVAL, "dx must be positive");
+    if (c->diag_every < 0) return fail(nullptr, LBRS_EINVAL, "diag_every must be >= 0");
     const int sides = c->lattice == LBRS_D2Q4 ? 4 : 2;
     for (int s = 0; s < sides; ++s) {
         const int kind = c->bc[s].kind;
@@ -231,6 +234,29 @@ lbrs_status ensure_graph(lbrs_ctx* ctx, int from)
 size_t field_bytes(const lbrs_ctx* ctx, int dtype) { return (size_t)ctx->K * (size_t)ctx->N * (dtype == LBRS_F64 ? 8 : 4); }
 
 size_t elem_bytes(const lbrs_ctx* ctx) { return ctx->f64 ? 8 : 4; }
+
+int readout_lattice(const lbrs_ctx* ctx);
+
+// One periodic check of the current state: the FP64 diagnostics reduction,
+// folded into the device status record under the current step number.
+cudaError_t periodic_check(lbrs_ctx* ctx)
+{
+    const double vol = ctx->lattice == LBRS_D2Q4 ? ctx->cfg.dx * ctx->cfg.dx : ctx->cfg.dx;
+    double* partials = (double*)(ctx->ws + ctx->L.partials);
+    double* dout = (double*)(ctx->ws + ctx->L.diag_out);
+    cudaError_t e = launch_diag(readout_lattice(ctx), ctx->f64, ctx->f[ctx->cur], ctx->N, ctx->cfg.gamma,
+                                ctx->cfg.lambda, vol, partials, dout, ctx->stream);
+    if (e != cudaSuccess) return e;
+    ctx->launches += 3;
+    return launch_status_update(dout, (double*)(ctx->ws + ctx->L.status), ctx->step, ctx->stream);
+}
+
+lbrs_status reset_status(lbrs_ctx* ctx)
+{
+    LBRS_CUDA(ctx, launch_status_reset((double*)(ctx->ws + ctx->L.status), ctx->stream));
+    ctx->launches += 1;
+    return LBRS_OK;
+}
 
 // The adjoint covers the periodic D2Q4 step.
 lbrs_status adjoint_supported(lbrs_ctx* ctx)
@@ -426,17 +452,37 @@ lbrs_status lbrs_set_state(lbrs_ctx* ctx, const void* W, int on_device, int dtyp
                                         ctx->cfg.gamma, ctx->c, ctx->stream));
     }
     ctx->launches += 1;
+    lbrs_status rs = reset_status(ctx);
+    if (rs != LBRS_OK) return rs;
     if (!on_device) LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));   // host W is consumed on return
     ctx->has_state = true;
     ctx->step = 0;
     return LBRS_OK;
 }
 
+static lbrs_status step_plain(lbrs_ctx* ctx, int64_t n);
+
 lbrs_status lbrs_step(lbrs_ctx* ctx, int64_t n)
 {
     if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
     if (n < 0) return fail(ctx, LBRS_EINVAL, "negative step count");
     if (!ctx->has_state) return fail(ctx, LBRS_ESTATE, "no state set");
+    const int64_t every = ctx->cfg.diag_every;
+    if (every <= 0) return step_plain(ctx, n);
+    // run to each multiple of diag_every, check there
+    while (n > 0) {
+        const int64_t to_check = every - ctx->step % every;
+        const int64_t m = to_check < n ? to_check : n;
+        lbrs_status st = step_plain(ctx, m);
+        if (st != LBRS_OK) return st;
+        n -= m;
+        if (ctx->step % every == 0) LBRS_CUDA(ctx, periodic_check(ctx));
+    }
+    return LBRS_OK;
+}
+
+static lbrs_status step_plain(lbrs_ctx* ctx, int64_t n)
+{
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     LBRS_CUDA(ctx, cudaStreamIsCapturing(ctx->stream, &cap));
     int64_t left = n;
@@ -463,6 +509,29 @@ lbrs_status lbrs_sync(lbrs_ctx* ctx)
 {
     if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
     LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->cfg.diag_every > 0 && ctx->has_state) {
+        double st[4];
+        LBRS_CUDA(ctx, cudaMemcpyAsync(st, ctx->ws + ctx->L.status, sizeof st, cudaMemcpyDeviceToHost, ctx->stream));
+        LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        if (st[0] >= 0.0) {
+            if (st[1] > 0.0)
+                return fail(ctx, LBRS_ENONPHYS, "%lld non-physical cells at step %lld", (long long)st[1], (long long)st[0]);
+            return fail(ctx, LBRS_ESUBCHAR, "%lld cells exceed lambda at step %lld (max local bound %.6g)",
+                        (long long)st[2], (long long)st[0], st[3]);
+        }
+    }
+    return LBRS_OK;
+}
+
+lbrs_status lbrs_first_bad_step(lbrs_ctx* ctx, int64_t* step)
+{
+    if (!ctx || !step) return fail(ctx, LBRS_EINVAL, "NULL argument");
+    *step = -1;
+    if (!ctx->has_state) return LBRS_OK;
+    double st[4];
+    LBRS_CUDA(ctx, cudaMemcpyAsync(st, ctx->ws + ctx->L.status, sizeof st, cudaMemcpyDeviceToHost, ctx->stream));
+    LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    *step = (int64_t)st[0];
     return LBRS_OK;
 }
 
@@ -530,6 +599,8 @@ lbrs_status lbrs_set_distributions(lbrs_ctx* ctx, const void* src, int on_device
     if (step < 0) return fail(ctx, LBRS_EINVAL, "negative step");
     LBRS_CUDA(ctx, cudaMemcpyAsync(ctx->f[ctx->cur], src, ctx->L.f_bytes,
                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+    lbrs_status rs = reset_status(ctx);
+    if (rs != LBRS_OK) return rs;
     if (!on_device) LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     ctx->has_state = true;
     ctx->step = step;

@@ -19,11 +19,12 @@ _PRECISION = {"f64": abi.LBRS_F64, "f32": abi.LBRS_F32, "f16neq": abi.LBRS_F16NE
 
 
 def make_config(lattice: str, nx: int, ny: int, *, gamma: float, lam: float, omega: float, dx: float,
-                bc, precision: str, stream_handle: int) -> abi.lbrs_config:
+                bc, precision: str, stream_handle: int, diag_every: int = 0) -> abi.lbrs_config:
     cfg = abi.lbrs_config()
     cfg.struct_size = ctypes.sizeof(abi.lbrs_config)
     cfg.lattice = abi.LBRS_D2Q4 if lattice == "d2q4" else abi.LBRS_D1Q2
     cfg.precision = _PRECISION[precision]
+    cfg.diag_every = int(diag_every)
     cfg.nx, cfg.ny = int(nx), int(ny)
     cfg.gamma, cfg.lam, cfg.omega, cfg.dx = float(gamma), float(lam), float(omega), float(dx)
     for s, (kind, state) in enumerate(bc):
@@ -47,7 +48,7 @@ class Solver:
 
     def __init__(self, lattice: str, nx: int, ny: int = 1, *, lam: float, dx: float, bc, gamma: float = 1.4,
                  omega: float = 1.0, precision: str = "f32", stream: torch.cuda.Stream | None = None,
-                 device: torch.device | str | None = None):
+                 device: torch.device | str | None = None, diag_every: int = 0):
         self.lib = abi.load()
         self.lattice = lattice
         self.Q, self.K = (4, 4) if lattice == "d2q4" else (2, 3)
@@ -61,7 +62,7 @@ class Solver:
             raise ValueError(f"need {sides} boundary conditions")
         bc = bc + [("periodic", None)] * (4 - len(bc))
         self.cfg = make_config(lattice, nx, ny, gamma=gamma, lam=lam, omega=omega, dx=dx, bc=bc,
-                               precision=precision, stream_handle=self.stream.cuda_stream)
+                               precision=precision, stream_handle=self.stream.cuda_stream, diag_every=diag_every)
         size = ctypes.c_size_t()
         abi.check(self.lib.lbrs_workspace_size(ctypes.byref(self.cfg), ctypes.byref(size)))
         self.workspace = torch.empty(size.value, dtype=torch.uint8, device=self.device)
@@ -72,12 +73,14 @@ class Solver:
         self.ctx = ctx
 
     @classmethod
-    def from_workload(cls, wl, precision: str = "f32", stream=None, omega=None):
+    def from_workload(cls, wl, precision: str = "f32", stream=None, omega=None, diag_every: int = 0):
         if hasattr(wl, "ny"):
             return cls("d2q4", wl.nx, wl.ny, lam=wl.lam, dx=wl.dx, bc=wl.bc, gamma=wl.gamma,
-                       omega=wl.omega if omega is None else omega, precision=precision, stream=stream)
+                       omega=wl.omega if omega is None else omega, precision=precision, stream=stream,
+                       diag_every=diag_every)
         return cls("d1q2", wl.nx, 1, lam=wl.lam, dx=wl.dx, bc=wl.bc, gamma=wl.gamma,
-                   omega=wl.omega if omega is None else omega, precision=precision, stream=stream)
+                   omega=wl.omega if omega is None else omega, precision=precision, stream=stream,
+                   diag_every=diag_every)
 
     # ------------------------------------------------------------------ helpers
     @property
@@ -131,6 +134,11 @@ class Solver:
 
     def sync(self):
         self._check(self.lib.lbrs_sync(self.ctx))
+
+    def first_bad_step(self) -> int:
+        v = ctypes.c_int64()
+        self._check(self.lib.lbrs_first_bad_step(self.ctx, ctypes.byref(v)))
+        return v.value
 
     def moments(self, dtype=torch.float64, out: torch.Tensor | None = None) -> torch.Tensor:
         """Conserved fields U (K, *grid); on the GPU unless `out` is a CPU tensor."""

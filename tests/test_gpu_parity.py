@@ -359,3 +359,39 @@ def test_f32_kernel_variants_agree(tmp_path):
     scale = np.abs(res["0"]).max()
     for v in ("2", "4", "12", "14"):
         assert np.max(np.abs(res[v] - res["0"])) <= 1e-5 * scale, v
+
+
+# ------------------------------------------------------------------- periodic device checks
+
+@pytest.mark.parametrize("every", [1, 5])
+def test_periodic_checks_report_first_bad_step(every):
+    from paper_1504_07034_gb300 import abi
+    from paper_1504_07034_gb300.solver import Solver
+    wl = W.sod(400)
+    wl.lam = 1.5                                       # below the post-shock u + a of about 2.19
+    o = oracle.Oracle.from_workload(wl)
+    _, chk = o.run(o.init(o.prim_to_cons(wl.prim)), 60)
+    first = chk["first_bad_step"]
+    assert first >= 1
+    s = Solver.from_workload(wl, precision="f64", diag_every=every)
+    s.set_state(torch.from_numpy(wl.prim).cuda())
+    s.step(60)
+    with pytest.raises(abi.LbrsError) as e:
+        s.sync()
+    assert e.value.status in (abi.LBRS_ESUBCHAR, abi.LBRS_ENONPHYS)
+    expected = -(-first // every) * every              # first multiple of `every` at or after it
+    assert s.first_bad_step() == expected
+    s.set_state(torch.from_numpy(wl.prim).cuda())     # a new state clears the record
+    assert s.first_bad_step() == -1
+    s.close()
+
+
+def test_periodic_checks_quiet_on_a_healthy_run():
+    from paper_1504_07034_gb300.solver import Solver
+    wl = W.quadrant_riemann(0, 256, steps=300)
+    s = Solver.from_workload(wl, precision="f32", diag_every=10)
+    s.set_state(torch.from_numpy(wl.prim).cuda())
+    s.step(wl.steps)
+    s.sync()
+    assert s.first_bad_step() == -1
+    s.close()
