@@ -9,8 +9,8 @@ numpy arrays through ctypes.
 
 Array layout: distributions ``fs[q, k, j, i]`` (2-D) or ``fs[q, k, i]`` (1-D),
 conserved fields ``U[k, j, i]`` / ``U[k, i]``.  Lattice velocity order
-follows the paper: D1Q2 (-lambda, +lambda); D2Q4 f1..f4 with signs
-(-,-), (+,-), (+,+), (-,+).
+follows the paper: D1Q2 (-lambda, +lambda); D1Q3 (-lambda, 0, +lambda);
+D2Q4 f1..f4 with signs (-,-), (+,-), (+,+), (-,+).
 
 Every function is pinned by ``tests/test_oracle_pins.py`` against what the
 paper and the mathematics fix (moment identities, the exact Lax-Friedrichs
@@ -33,7 +33,7 @@ SRC = HERE / "lbrs_oracle.c"
 LIB = HERE / "_build" / "liblbrs_oracle.so"
 
 BC_KINDS = {"periodic": 0, "transmissive": 1, "dirichlet": 2, "wall": 3}
-D1Q2, D2Q4 = 2, 4
+D1Q2, D1Q3, D2Q4 = 2, 3, 4
 
 
 def build(force: bool = False) -> Path:
@@ -126,7 +126,7 @@ class Oracle:
     def __init__(self, lattice: int, nx: int, ny: int = 1, *, gamma: float = 1.4, lam: float,
                  omega: float = 1.0, bc=None, nthreads: int = 0):
         self.lattice = lattice
-        self.Q, self.K = (4, 4) if lattice == D2Q4 else (2, 3)
+        self.Q, self.K = {D2Q4: (4, 4), D1Q3: (3, 3), D1Q2: (2, 3)}[lattice]
         self.nx, self.ny = int(nx), int(ny)
         sides = 4 if lattice == D2Q4 else 2
         bc = list(bc) if bc is not None else [("periodic", None)] * sides
@@ -147,11 +147,11 @@ class Oracle:
             raise ValueError(f"invalid oracle parameters (code {err})")
 
     @classmethod
-    def from_workload(cls, wl, nthreads: int = 0, omega=None):
+    def from_workload(cls, wl, nthreads: int = 0, omega=None, lattice=None):
         if hasattr(wl, "ny"):
             return cls(D2Q4, wl.nx, wl.ny, gamma=wl.gamma, lam=wl.lam,
                        omega=wl.omega if omega is None else omega, bc=wl.bc, nthreads=nthreads)
-        return cls(D1Q2, wl.nx, 1, gamma=wl.gamma, lam=wl.lam,
+        return cls(lattice or D1Q2, wl.nx, 1, gamma=wl.gamma, lam=wl.lam,
                    omega=wl.omega if omega is None else omega, bc=wl.bc, nthreads=nthreads)
 
     # shapes -------------------------------------------------------------

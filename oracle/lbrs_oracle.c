@@ -22,6 +22,8 @@
  * Lattices (q is 0-based; the paper numbers them from 1):
  *   D1Q2 : c = (-1, +1) lattice units, K = 3 fields (rho, rho u, rho E).
  *          f^eq_{1,2} = U/2 -/+ G/(2 lambda)                  (Section II.C)
+ *   D1Q3 : c = (-1, 0, +1), K = 3 (rest particle added, Section II.C):
+ *          f^eq = (U/3 - G/(2 lambda), U/3, U/3 + G/(2 lambda))
  *   D2Q4 : c = (-1,-1), (+1,-1), (+1,+1), (-1,+1), K = 4 fields
  *          (rho, rho u, rho v, rho E);
  *          f^eq_q = U/4 + sx_q F/(4 lambda) + sy_q G/(4 lambda) (Section II.D)
@@ -52,10 +54,10 @@
 #include <omp.h>
 
 enum { ORC_PERIODIC = 0, ORC_TRANSMISSIVE = 1, ORC_DIRICHLET = 2, ORC_WALL = 3 };
-enum { ORC_D1Q2 = 2, ORC_D2Q4 = 4 };
+enum { ORC_D1Q2 = 2, ORC_D1Q3 = 3, ORC_D2Q4 = 4 };
 
 typedef struct {
-    int32_t lattice;      /* ORC_D1Q2 or ORC_D2Q4 */
+    int32_t lattice;      /* ORC_D1Q2, ORC_D1Q3 or ORC_D2Q4 */
     int32_t nthreads;     /* OpenMP threads, 0 = library default */
     int64_t nx, ny;       /* ny = 1 for D1Q2 */
     double gamma, lambda, omega;
@@ -74,9 +76,10 @@ typedef struct {
 static const int SX2[4] = {-1, +1, +1, -1};
 static const int SY2[4] = {-1, -1, +1, +1};
 static const int SX1[2] = {-1, +1};
+static const int SX13[3] = {-1, 0, +1};
 
 static int threads_of(const orc_params* P) { return P->nthreads > 0 ? P->nthreads : omp_get_max_threads(); }
-static int nq(const orc_params* P) { return P->lattice == ORC_D2Q4 ? 4 : 2; }
+static int nq(const orc_params* P) { return P->lattice == ORC_D2Q4 ? 4 : (P->lattice == ORC_D1Q3 ? 3 : 2); }
 static int nk(const orc_params* P) { return P->lattice == ORC_D2Q4 ? 4 : 3; }
 
 /* ---------------------------------------------------------------- state */
@@ -143,16 +146,29 @@ static void feq_cell(const orc_params* P, const double* U, double* feq)
         double p = (g - 1.0) * (en - 0.5 * (m * u));
         double G[3] = {m, m * u + p, u * (en + p)};
         double c = 1.0 / (2.0 * P->lambda);
-        for (int k = 0; k < 3; ++k) {
-            double a = 0.5 * U[k];
-            double b = c * G[k];
-            feq[0 * 3 + k] = a - b;   /* velocity -lambda */
-            feq[1 * 3 + k] = a + b;   /* velocity +lambda */
+        if (P->lattice == ORC_D1Q3) {
+            for (int k = 0; k < 3; ++k) {
+                double a = U[k] / 3.0;
+                double b = c * G[k];
+                feq[0 * 3 + k] = a - b;   /* velocity -lambda */
+                feq[1 * 3 + k] = a;       /* rest particle */
+                feq[2 * 3 + k] = a + b;   /* velocity +lambda */
+            }
+        } else {
+            for (int k = 0; k < 3; ++k) {
+                double a = 0.5 * U[k];
+                double b = c * G[k];
+                feq[0 * 3 + k] = a - b;   /* velocity -lambda */
+                feq[1 * 3 + k] = a + b;   /* velocity +lambda */
+            }
         }
     }
 }
 
-/* Local wave-speed bound: |u| + a in 1-D (Section II.C), max(|u+v|,|u-v|) + sqrt(2) a in 2-D (Section II.D). */
+/* Local wave-speed bound: |u| + a for D1Q2 (Section II.C), max(|u+v|,|u-v|) + sqrt(2) a
+ * for D2Q4 (Section II.D).  For D1Q3 the Chapman-Enskog analysis of Section II.B
+ * with sum_q lambda_q^2 f^eq_q = (2/3) lambda^2 U gives a positive diffusion for a
+ * wave of speed c only if c^2 < (2/3) lambda^2, hence the bound sqrt(3/2)(|u| + a). */
 static double lambda_local(const orc_params* P, const double* U, double p)
 {
     double a = sqrt(P->gamma * p / U[0]);
@@ -161,6 +177,7 @@ static double lambda_local(const orc_params* P, const double* U, double p)
         double s1 = fabs(u + v), s2 = fabs(u - v);
         return (s1 > s2 ? s1 : s2) + sqrt(2.0) * a;
     }
+    if (P->lattice == ORC_D1Q3) return sqrt(1.5) * (fabs(U[1] / U[0]) + a);
     return fabs(U[1] / U[0]) + a;
 }
 
@@ -227,9 +244,9 @@ void orc_moments(const orc_params* P, const double* fs, double* U)
 
 int orc_validate(const orc_params* P)
 {
-    if (P->lattice != ORC_D1Q2 && P->lattice != ORC_D2Q4) return 1;
+    if (P->lattice != ORC_D1Q2 && P->lattice != ORC_D1Q3 && P->lattice != ORC_D2Q4) return 1;
     if (P->nx < 1 || P->ny < 1) return 2;
-    if (P->lattice == ORC_D1Q2 && P->ny != 1) return 3;
+    if (P->lattice != ORC_D2Q4 && P->ny != 1) return 3;
     if (!(P->lambda > 0.0) || !(P->omega > 0.0 && P->omega < 2.0) || !(P->gamma > 1.0)) return 4;
     int sides = P->lattice == ORC_D2Q4 ? 4 : 2;
     for (int s = 0; s < sides; ++s) {
@@ -275,7 +292,7 @@ int orc_stream(const orc_params* P, const double* fs, double* f)
             const int64_t c = j * nx + i;
             int wall_pop[4] = {0, 0, 0, 0};
             for (int q = 0; q < Q; ++q) {
-                int sx = two_d ? SX2[q] : SX1[q];
+                int sx = two_d ? SX2[q] : (Q == 3 ? SX13[q] : SX1[q]);
                 int sy = two_d ? SY2[q] : 0;
                 int64_t si = i - sx, sj = j - sy;
                 int side_y = sj < 0 ? 2 : (sj >= ny ? 3 : -1);

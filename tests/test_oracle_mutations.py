@@ -33,6 +33,11 @@ MUTANTS = {
                                         "return g * (U[3] - 0.5 * (U[1] * u + U[2] * v));"),
     "ghost_uses_wrong_side": ("if (kind == ORC_DIRICHLET) g = ghost[side_x];",
                               "if (kind == ORC_DIRICHLET) g = ghost[side_x ^ 1];"),
+    # D1Q3
+    "d1q3_rest_fraction_quarter": ("double a = U[k] / 3.0;", "double a = U[k] / 4.0;"),
+    "d1q3_rest_particle_moves": ("static const int SX13[3] = {-1, 0, +1};", "static const int SX13[3] = {-1, +1, +1};"),
+    "d1q3_bound_without_factor": ("if (P->lattice == ORC_D1Q3) return sqrt(1.5) * (fabs(U[1] / U[0]) + a);",
+                                  "if (P->lattice == ORC_D1Q3) return (fabs(U[1] / U[0]) + a);"),
     # adjoint
     "adjoint_drops_y_flux_jacobian": ("ubar[k] = 0.25 * a[k] + c * sf + c * sg;", "ubar[k] = 0.25 * a[k] + c * sf;"),
     "adjoint_wrong_momentum_jacobian": ("{q2h - u * u, (3.0 - g) * u, -gm1 * v, gm1},",
@@ -57,6 +62,7 @@ def test_pins_catch_mutant(name, tmp_path):
     env = dict(os.environ, LBRS_ORACLE_LIB=str(so), OMP_NUM_THREADS="2")
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_pins_d1q3.py"),
                         os.path.join(ROOT, "tests", "test_oracle_adjoint.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"pins did not catch mutant {name}:\n{r.stdout[-2000:]}"

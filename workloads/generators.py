@@ -154,7 +154,12 @@ def lambda_2d_quadrants(gamma, q, safety=1.1) -> float:
 
 # --------------------------------------------------------------------------- 1-D
 
-def sod(nx: int = 1000, omega: float = 1.0, t_final: float = 0.2) -> Workload1D:
+# D1Q3 carries (2/3) lambda^2 U in its second moment, so its lattice speed must
+# exceed sqrt(3/2) times the wave speeds (positive Chapman-Enskog diffusion).
+LAMBDA_FACTOR = {"d1q2": 1.0, "d1q3": math.sqrt(1.5)}
+
+
+def sod(nx: int = 1000, omega: float = 1.0, t_final: float = 0.2, lattice: str = "d1q2") -> Workload1D:
     """Sod's shock tube in nondimensional form on [0, 1], diaphragm at 0.5 (Section III).
 
     The paper runs the dimensional version (1 kg/m^3, 0, 1e5 Pa | 0.125, 0,
@@ -166,12 +171,12 @@ def sod(nx: int = 1000, omega: float = 1.0, t_final: float = 0.2) -> Workload1D:
     prim = np.empty((3, nx))
     for k in range(3):
         prim[k] = np.where(x < 0.5, wl[k], wr[k])
-    lam, steps = _round_lambda(lambda_1d_riemann(GAMMA, wl, wr), dx, t_final)
+    lam, steps = _round_lambda(LAMBDA_FACTOR[lattice] * lambda_1d_riemann(GAMMA, wl, wr), dx, t_final)
     return Workload1D("sod", nx, dx, 0.0, prim, [("transmissive", None)] * 2, lam, omega, steps,
                       t_final=t_final, meta={"left": wl, "right": wr, "x_interface": 0.5})
 
 
-def steady_contact(nx: int = 100, omega: float = 1.0, t_final: float = 2.0) -> Workload1D:
+def steady_contact(nx: int = 100, omega: float = 1.0, t_final: float = 2.0, lattice: str = "d1q2") -> Workload1D:
     """Stationary contact (rho 1.4 | 1.0, u = 0, p = 1) on [0, 1] (Section III)."""
     wl, wr = (1.4, 0.0, 1.0), (1.0, 0.0, 1.0)
     dx = 1.0 / nx
@@ -179,13 +184,14 @@ def steady_contact(nx: int = 100, omega: float = 1.0, t_final: float = 2.0) -> W
     prim = np.empty((3, nx))
     for k in range(3):
         prim[k] = np.where(x < 0.5, wl[k], wr[k])
-    lam0 = 1.05 * max(sound(GAMMA, 1.0, 1.0), sound(GAMMA, 1.4, 1.0))
+    lam0 = 1.05 * LAMBDA_FACTOR[lattice] * max(sound(GAMMA, 1.0, 1.0), sound(GAMMA, 1.4, 1.0))
     lam, steps = _round_lambda(lam0, dx, t_final)
     return Workload1D("steady_contact", nx, dx, 0.0, prim, [("transmissive", None)] * 2, lam, omega,
                       steps, t_final=t_final, meta={"left": wl, "right": wr})
 
 
-def steady_shock(nx: int = 400, mach: float = 2.0, omega: float = 1.0, steps: int = 1000) -> Workload1D:
+def steady_shock(nx: int = 400, mach: float = 2.0, omega: float = 1.0, steps: int = 1000,
+                 lattice: str = "d1q2") -> Workload1D:
     """Stationary Mach-2 normal shock at x = 0 on [-1, 1] (Section III, steady shock).
 
     Pre-shock state (1, M a, 1/gamma) so that a = 1; the post-shock state
@@ -201,7 +207,7 @@ def steady_shock(nx: int = 400, mach: float = 2.0, omega: float = 1.0, steps: in
     prim = np.empty((3, nx))
     for k, (a, b) in enumerate(zip((r1, u1, p1), (r2, u2, p2))):
         prim[k] = np.where(x < 0.0, a, b)
-    lam = 1.1 * max(abs(u1) + sound(GAMMA, r1, p1), abs(u2) + sound(GAMMA, r2, p2))
+    lam = 1.1 * LAMBDA_FACTOR[lattice] * max(abs(u1) + sound(GAMMA, r1, p1), abs(u2) + sound(GAMMA, r2, p2))
     bc = [("dirichlet", (r1, u1, p1)), ("dirichlet", (r2, u2, p2))]
     return Workload1D("steady_shock", nx, dx, -1.0, prim, bc, lam, omega, steps,
                       meta={"pre": (r1, u1, p1), "post": (r2, u2, p2)})
