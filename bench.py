@@ -212,6 +212,16 @@ def sod_measurement(Solver, stream, barrier):
         out[precision] = {"ms": a.elapsed_time(b), "mlups": wl.nx * wl.steps / (a.elapsed_time(b) / 1e3) / 1e6,
                           "l1_rho_vs_exact_riemann": float(np.mean(np.abs(rho - exact)))}
         s.close()
+    # the rest-particle model (D1Q3), which the paper reports removes the D1Q2 staircase
+    wl3 = workloads.sod(1000, lattice="d1q3")
+    s = Solver.from_workload(wl3, precision="f64", stream=stream, lattice="d1q3")
+    with torch.cuda.stream(stream):
+        s.set_state(torch.from_numpy(wl3.prim).cuda())
+        s.step(wl3.steps)
+        rho = s.moments(torch.float64)[0].cpu().numpy()
+    s.close()
+    out["d1q3_f64"] = {"steps": wl3.steps, "lambda": wl3.lam,
+                       "l1_rho_vs_exact_riemann": float(np.mean(np.abs(rho - exact)))}
     return out
 
 

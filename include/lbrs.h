@@ -22,7 +22,7 @@
  *
  * Conventions
  *   Layout.    Distributions are structure-of-arrays f[q][k][j][i] (i fastest),
- *              q in the paper's order, Q = 2 or 4, K = 3 or 4, N = nx * ny.
+ *              q in the paper's order, Q = 2, 3 or 4, K = 3 or 4, N = nx * ny.
  *              Field arrays are [k][j][i].  1-D problems have ny = 1.
  *              Cells are cell-centred; dx = dy (exact hopping on the diagonals).
  *   Memory.    The caller owns every buffer.  Device memory for the solver
@@ -66,7 +66,12 @@ typedef enum {
     LBRS_ESTATE = 7     /* call out of order (e.g. stepping before a state was set) */
 } lbrs_status;
 
-typedef enum { LBRS_D1Q2 = 0, LBRS_D2Q4 = 1 } lbrs_lattice;
+/* LBRS_D1Q3 adds a rest particle (Section II.C): velocities (-lambda, 0, +lambda),
+ * f^eq = (U/3 - G/(2 lambda), U/3, U/3 + G/(2 lambda)).  Its Chapman-Enskog
+ * diffusion dt (1/omega - 1/2)(2 lambda^2/3 - c^2) stays positive only for
+ * wave speeds c below sqrt(2/3) lambda: the diagnostics' local bound for D1Q3 is
+ * sqrt(3/2)(|u| + a). */
+typedef enum { LBRS_D1Q2 = 0, LBRS_D2Q4 = 1, LBRS_D1Q3 = 2 } lbrs_lattice;
 
 /* Storage and arithmetic precision of the distributions.
  *   LBRS_F64     FP64 storage and arithmetic (the parity path);

@@ -33,7 +33,7 @@ enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_DIRICHLET = 2, BC_WALL = 3 };
 // LAT_U2D: a D2Q4 state stored as its moments U directly (the FP16
 // non-equilibrium form keeps U in FP32): read-outs treat it as one
 // "population" per field.
-enum { LAT_D1Q2 = 0, LAT_D2Q4 = 1, LAT_U2D = 2 };
+enum { LAT_D1Q2 = 0, LAT_D2Q4 = 1, LAT_U2D = 2, LAT_D1Q3 = 3 };
 enum { KIND_CONSERVED = 0, KIND_PRIMITIVE = 1 };
 
 // Ghost-table stride: one Dirichlet side holds Q*K <= 16 values.
@@ -120,6 +120,24 @@ __device__ __forceinline__ void equilibria1d(const T U[3], T gm1, T c, T e[2][3]
         const T b = c * G[k];
         e[0][k] = a - b;
         e[1][k] = a + b;
+    }
+}
+
+// D1Q3 equilibria (Section II.C, rest particle): f^eq = (U/3 - c G, U/3, U/3 + c G),
+// c = 1/(2 lambda), G the 1-D Euler flux.
+template <typename T>
+__device__ __forceinline__ void equilibria1d3(const T U[3], T gm1, T c, T e[3][3])
+{
+    const T u = velocity1<T>(U[0], U[1]);
+    const T p = gm1 * (U[2] - T(0.5) * (U[1] * u));
+    const T G[3] = {U[1], U[1] * u + p, u * (U[2] + p)};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const T a = U[k] / T(3);
+        const T b = c * G[k];
+        e[0][k] = a - b;
+        e[1][k] = a;
+        e[2][k] = a + b;
     }
 }
 
@@ -269,6 +287,42 @@ __global__ void __launch_bounds__(256) step1d_kernel(const StepArgs<T> a)
     equilibria1d<T>(U, a.gm1, a.c, e);
 #pragma unroll
     for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) a.dst[(q * 3 + k) * a.N + i] = a.om1 * f[q][k] + a.om * e[q][k];
+}
+
+// ---------------------------------------------------------------- D1Q3 step
+
+// Velocity -lambda pulls from i + 1, the rest particle stays, +lambda pulls from i - 1.
+template <typename T>
+__global__ void __launch_bounds__(256) step1d_q3_kernel(const StepArgs<T> a)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.nx) return;
+    T f[3][3];
+#pragma unroll
+    for (int q = 0; q < 3; q += 2) {
+        int si = q == 0 ? i + 1 : i - 1;
+        const T* g = nullptr;
+        if (si < 0 || si >= a.nx) {
+            const int side = si < 0 ? 0 : 1;
+            const int kind = side == 0 ? a.bc[0] : a.bc[1];
+            if (kind == BC_DIRICHLET) g = a.ghost + side * GHOST_STRIDE + q * 3;
+            else if (kind == BC_PERIODIC) si = si < 0 ? si + a.nx : si - a.nx;
+            else si = si < 0 ? 0 : a.nx - 1;
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) f[q][k] = g ? g[k] : a.src[(q * 3 + k) * a.N + si];
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) f[1][k] = a.src[(3 + k) * a.N + i];
+    T U[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) U[k] = (f[0][k] + f[1][k]) + f[2][k];
+    T e[3][3];
+    equilibria1d3<T>(U, a.gm1, a.c, e);
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
 #pragma unroll
         for (int k = 0; k < 3; ++k) a.dst[(q * 3 + k) * a.N + i] = a.om1 * f[q][k] + a.om * e[q][k];
 }

@@ -39,6 +39,10 @@ template <>
 struct Dims<LAT_U2D> {
     static constexpr int Q = 1, K = 4;
 };
+template <>
+struct Dims<LAT_D1Q3> {
+    static constexpr int Q = 3, K = 3;
+};
 
 // f^eq in FP64 for either lattice, e[q*K + k]
 template <int LAT>
@@ -51,6 +55,13 @@ __device__ __forceinline__ void equilibria_flat(const double* U, double gm1, dou
         for (int q = 0; q < 4; ++q)
 #pragma unroll
             for (int k = 0; k < 4; ++k) e[q * 4 + k] = t[q][k];
+    } else if constexpr (LAT == LAT_D1Q3) {
+        double t[3][3];
+        equilibria1d3<double>(U, gm1, c, t);
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) e[q * 3 + k] = t[q][k];
     } else {
         double t[2][3];
         equilibria1d<double>(U, gm1, c, t);
@@ -75,6 +86,7 @@ __global__ void ghost_kernel(GhostSpec g, double gamma, double c, Ts* ghost)
     const int side = threadIdx.x;
     if (side >= 4) return;
     double e[16];
+    static_assert(Q * K <= GHOST_STRIDE, "ghost table stride");
     for (int n = 0; n < GHOST_STRIDE; ++n) e[n] = 0.0;
     if (g.kind[side] == BC_DIRICHLET) {
         double U[4];
@@ -193,6 +205,7 @@ __global__ void __launch_bounds__(kThreads) diag_partial_kernel(const Ts* __rest
             const R u = U[1] * inv;
             p = gm1 * (U[2] - (R)0.5 * (U[1] * u));
             lam = fabs(u) + sqrt(g * p * inv);
+            if constexpr (LAT == LAT_D1Q3) lam *= (R)1.224744871391589;   // sqrt(3/2)
         }
         if (finite) {
             mn_rho = fmin(mn_rho, U[0]);
@@ -447,6 +460,8 @@ cudaError_t launch_step_f64(int lattice, const StepArgs<double>& a, cudaStream_t
         unsigned gy = (unsigned)((a.ny + block.y - 1) / block.y);
         const dim3 grid((unsigned)((a.nx + block.x - 1) / block.x), gy);
         step2d_kernel<double><<<grid, block, 0, s>>>(a);
+    } else if (lattice == LAT_D1Q3) {
+        step1d_q3_kernel<double><<<(unsigned)((a.nx + 255) / 256), 256, 0, s>>>(a);
     } else {
         step1d_kernel<double><<<(unsigned)((a.nx + 255) / 256), 256, 0, s>>>(a);
     }
@@ -459,6 +474,9 @@ cudaError_t launch_ghost(int lattice, int storage_f64, const GhostSpec& g, doubl
     if (lattice == LAT_D2Q4) {
         if (storage_f64) ghost_kernel<double, LAT_D2Q4><<<1, 32, 0, s>>>(g, gamma, c, (double*)ghost);
         else ghost_kernel<float, LAT_D2Q4><<<1, 32, 0, s>>>(g, gamma, c, (float*)ghost);
+    } else if (lattice == LAT_D1Q3) {
+        if (storage_f64) ghost_kernel<double, LAT_D1Q3><<<1, 32, 0, s>>>(g, gamma, c, (double*)ghost);
+        else ghost_kernel<float, LAT_D1Q3><<<1, 32, 0, s>>>(g, gamma, c, (float*)ghost);
     } else {
         if (storage_f64) ghost_kernel<double, LAT_D1Q2><<<1, 32, 0, s>>>(g, gamma, c, (double*)ghost);
         else ghost_kernel<float, LAT_D1Q2><<<1, 32, 0, s>>>(g, gamma, c, (float*)ghost);
@@ -484,6 +502,7 @@ cudaError_t launch_set_state(int lattice, int storage_f64, const void* W, int w_
                              int64_t N, double gamma, double c, cudaStream_t s)
 {
     if (lattice == LAT_D2Q4) set_state_dispatch<LAT_D2Q4>(storage_f64, W, w_dtype, kind, fs, N, gamma, c, s);
+    else if (lattice == LAT_D1Q3) set_state_dispatch<LAT_D1Q3>(storage_f64, W, w_dtype, kind, fs, N, gamma, c, s);
     else set_state_dispatch<LAT_D1Q2>(storage_f64, W, w_dtype, kind, fs, N, gamma, c, s);
     return cudaGetLastError();
 }
@@ -506,6 +525,7 @@ cudaError_t launch_moments(int lattice, int storage_f64, const void* fs, void* U
 {
     if (lattice == LAT_U2D) moments_dispatch<LAT_U2D>(0, fs, U, out_dtype, N, s);
     else if (lattice == LAT_D2Q4) moments_dispatch<LAT_D2Q4>(storage_f64, fs, U, out_dtype, N, s);
+    else if (lattice == LAT_D1Q3) moments_dispatch<LAT_D1Q3>(storage_f64, fs, U, out_dtype, N, s);
     else moments_dispatch<LAT_D1Q2>(storage_f64, fs, U, out_dtype, N, s);
     return cudaGetLastError();
 }
@@ -517,6 +537,9 @@ cudaError_t launch_diag(int lattice, int storage_f64, const void* fs, int64_t N,
 {
     if (lattice == LAT_U2D) {
         diag_partial_kernel<float, LAT_U2D><<<kDiagBlocks, kThreads, 0, s>>>((const float*)fs, N, gamma, lambda, partials);
+    } else if (lattice == LAT_D1Q3) {
+        if (storage_f64) diag_partial_kernel<double, LAT_D1Q3><<<kDiagBlocks, kThreads, 0, s>>>((const double*)fs, N, gamma, lambda, partials);
+        else diag_partial_kernel<float, LAT_D1Q3><<<kDiagBlocks, kThreads, 0, s>>>((const float*)fs, N, gamma, lambda, partials);
     } else if (lattice == LAT_D2Q4) {
         if (storage_f64) diag_partial_kernel<double, LAT_D2Q4><<<kDiagBlocks, kThreads, 0, s>>>((const double*)fs, N, gamma, lambda, partials);
         else diag_partial_kernel<float, LAT_D2Q4><<<kDiagBlocks, kThreads, 0, s>>>((const float*)fs, N, gamma, lambda, partials);

@@ -125,6 +125,7 @@ __global__ void __launch_bounds__(kThreads) noalloc_partial_kernel(const Ts* __r
             const R u = U[1] * inv;
             p = gm1 * (U[2] - (R)0.5 * (U[1] * u));
             lam = fabs(u) + sqrt(g * p * inv);
+            if (Q == 3) lam *= (R)1.224744871391589;   // D1Q3 bound: sqrt(3/2)(|u| + a)
         }
         if (finite) {
             mn_rho = fmin(mn_rho, U[0]);
@@ -241,6 +242,11 @@ extern "C" lbrs_status lbrs_diagnostics_noalloc(const lbrs_config* cfg, const vo
             noalloc_partial_kernel<double, 4, 4><<<nblocks, kThreads, 0, stream>>>((const double*)d_fs, N, cfg->gamma, cfg->lambda, scratch);
         else
             noalloc_partial_kernel<float, 4, 4><<<nblocks, kThreads, 0, stream>>>((const float*)d_fs, N, cfg->gamma, cfg->lambda, scratch);
+    } else if (cfg->lattice == LBRS_D1Q3) {
+        if (cfg->precision == LBRS_F64)
+            noalloc_partial_kernel<double, 3, 3><<<nblocks, kThreads, 0, stream>>>((const double*)d_fs, N, cfg->gamma, cfg->lambda, scratch);
+        else
+            noalloc_partial_kernel<float, 3, 3><<<nblocks, kThreads, 0, stream>>>((const float*)d_fs, N, cfg->gamma, cfg->lambda, scratch);
     } else {
         if (cfg->precision == LBRS_F64)
             noalloc_partial_kernel<double, 2, 3><<<nblocks, kThreads, 0, stream>>>((const double*)d_fs, N, cfg->gamma, cfg->lambda, scratch);

@@ -32,8 +32,10 @@ struct Layout {
     size_t f_bytes, f0, f1, ghost, partials, diag_out, scale, status, total;
 };
 
-int lattice_q(int lat) { return lat == LBRS_D2Q4 ? 4 : 2; }
+int lattice_q(int lat) { return lat == LBRS_D2Q4 ? 4 : (lat == LBRS_D1Q3 ? 3 : 2); }
 int lattice_k(int lat) { return lat == LBRS_D2Q4 ? 4 : 3; }
+// kernel lattice code of a public lattice
+int lat_code(int lat) { return lat == LBRS_D2Q4 ? LAT_D2Q4 : (lat == LBRS_D1Q3 ? LAT_D1Q3 : LAT_D1Q2); }
 
 Layout layout_of(const lbrs_config* c)
 {
@@ -117,7 +119,7 @@ lbrs_status validate(const lbrs_config* c)
     if (c->struct_size != sizeof(lbrs_config))
         return fail(nullptr, LBRS_EINVAL, "config.struct_size %u != sizeof(lbrs_config) %zu", c->struct_size,
                     sizeof(lbrs_config));
-    if (c->lattice != LBRS_D1Q2 && c->lattice != LBRS_D2Q4)
+    if (c->lattice != LBRS_D1Q2 && c->lattice != LBRS_D2Q4 && c->lattice != LBRS_D1Q3)
         return fail(nullptr, LBRS_EINVAL, "unknown lattice %d", c->lattice);
     if (c->precision != LBRS_F64 && c->precision != LBRS_F32 && c->precision != LBRS_F16NEQ)
         return fail(nullptr, LBRS_EINVAL, "unknown precision %d", c->precision);
@@ -125,7 +127,7 @@ lbrs_status validate(const lbrs_config* c)
         return fail(nullptr, LBRS_EINVAL, "LBRS_F16NEQ is a D2Q4 storage form");
     if (c->nx < 1 || c->ny < 1) return fail(nullptr, LBRS_EINVAL, "grid must have nx, ny >= 1");
     if (c->nx > (1LL << 30)) return fail(nullptr, LBRS_EINVAL, "nx too large (max 2^30)");
-    if (c->lattice == LBRS_D1Q2 && c->ny != 1) return fail(nullptr, LBRS_EINVAL, "D1Q2 needs ny == 1");
+    if (c->lattice != LBRS_D2Q4 && c->ny != 1) return fail(nullptr, LBRS_EINVAL, "1-D lattices (D1Q2, D1Q3) need ny == 1");
     if (c->lattice == LBRS_D2Q4 && c->ny > 2LL * 65535) return fail(nullptr, LBRS_EINVAL, "ny too large (max 131070)");
     if (!(c->gamma > 1.0) || !isfinite(c->gamma)) return fail(nullptr, LBRS_EINVAL, "gamma must be > 1");
     if (!finite_pos(c->lambda)) return fail(nullptr, LBRS_EINVAL, "lambda must be positive");
@@ -176,7 +178,7 @@ StepArgs<T> step_args(const lbrs_ctx* ctx, int from)
 
 cudaError_t launch_one_step(lbrs_ctx* ctx, int from, cudaStream_t s)
 {
-    const int lat = ctx->lattice == LBRS_D2Q4 ? LAT_D2Q4 : LAT_D1Q2;
+    const int lat = lat_code(ctx->lattice);
     if (ctx->f64) return launch_step_f64(lat, step_args<double>(ctx, from), s);
     if (ctx->f16) {
         F16StepArgs a;
@@ -200,7 +202,7 @@ cudaError_t launch_one_step(lbrs_ctx* ctx, int from, cudaStream_t s)
 int readout_lattice(const lbrs_ctx* ctx)
 {
     if (ctx->f16) return LAT_U2D;
-    return ctx->lattice == LBRS_D2Q4 ? LAT_D2Q4 : LAT_D1Q2;
+    return lat_code(ctx->lattice);
 }
 
 // Capture kGraphSteps step kernels starting from buffer `from` into graph[from].
@@ -400,7 +402,7 @@ lbrs_status lbrs_create(const lbrs_config* cfg, void* d_workspace, size_t bytes,
     ctx->f[0] = ctx->ws + L.f0;
     ctx->f[1] = ctx->ws + L.f1;
     ctx->stream = (cudaStream_t)cfg->cuda_stream;
-    ctx->c = cfg->lattice == LBRS_D2Q4 ? 1.0 / (4.0 * cfg->lambda) : 1.0 / (2.0 * cfg->lambda);
+    ctx->c = cfg->lattice == LBRS_D2Q4 ? 1.0 / (4.0 * cfg->lambda) : 1.0 / (2.0 * cfg->lambda);   // both 1-D lattices: 1/(2 lambda)
 
     GhostSpec g;
     memset(&g, 0, sizeof g);
@@ -408,7 +410,7 @@ lbrs_status lbrs_create(const lbrs_config* cfg, void* d_workspace, size_t bytes,
         g.kind[s] = cfg->bc[s].kind;
         for (int k = 0; k < 4; ++k) g.prim[s][k] = cfg->bc[s].prim[k];
     }
-    const int lat = cfg->lattice == LBRS_D2Q4 ? LAT_D2Q4 : LAT_D1Q2;
+    const int lat = lat_code(cfg->lattice);
     cudaError_t e = launch_ghost(lat, ctx->f64, g, cfg->gamma, ctx->c, ctx->ws + L.ghost, ctx->stream);
     if (e != cudaSuccess) {
         lbrs_status s = cuda_fail(nullptr, e, "ghost-table kernel");
@@ -442,7 +444,7 @@ lbrs_status lbrs_set_state(lbrs_ctx* ctx, const void* W, int on_device, int dtyp
         LBRS_CUDA(ctx, cudaMemcpyAsync(stage, W, field_bytes(ctx, dtype), cudaMemcpyHostToDevice, ctx->stream));
         src = stage;
     }
-    const int lat = ctx->lattice == LBRS_D2Q4 ? LAT_D2Q4 : LAT_D1Q2;
+    const int lat = lat_code(ctx->lattice);
     if (ctx->f16) {
         LBRS_CUDA(ctx, launch_set_state_f16neq(src, dtype == LBRS_F32, kind, ctx->f[ctx->cur], ctx->N, ctx->cfg.gamma,
                                                (unsigned int*)(ctx->ws + ctx->L.scale), ctx->stream));

@@ -22,7 +22,7 @@ def make_config(lattice: str, nx: int, ny: int, *, gamma: float, lam: float, ome
                 bc, precision: str, stream_handle: int, diag_every: int = 0) -> abi.lbrs_config:
     cfg = abi.lbrs_config()
     cfg.struct_size = ctypes.sizeof(abi.lbrs_config)
-    cfg.lattice = abi.LBRS_D2Q4 if lattice == "d2q4" else abi.LBRS_D1Q2
+    cfg.lattice = {"d2q4": abi.LBRS_D2Q4, "d1q2": abi.LBRS_D1Q2, "d1q3": abi.LBRS_D1Q3}[lattice]
     cfg.precision = _PRECISION[precision]
     cfg.diag_every = int(diag_every)
     cfg.nx, cfg.ny = int(nx), int(ny)
@@ -39,7 +39,7 @@ def make_config(lattice: str, nx: int, ny: int, *, gamma: float, lam: float, ome
 class Solver:
     """One LBRS problem on one GPU.
 
-    lattice   "d1q2" or "d2q4"
+    lattice   "d1q2", "d1q3" or "d2q4"
     bc        per side (x-lo, x-hi[, y-lo, y-hi]): (kind, primitive_state_or_None)
     precision "f64" (plain FP64 path), "f32" (FP32 distributions) or "f16neq" (D2Q4: FP32
               moments plus FP16 non-equilibrium parts)
@@ -51,7 +51,7 @@ class Solver:
                  device: torch.device | str | None = None, diag_every: int = 0):
         self.lib = abi.load()
         self.lattice = lattice
-        self.Q, self.K = (4, 4) if lattice == "d2q4" else (2, 3)
+        self.Q, self.K = {"d2q4": (4, 4), "d1q2": (2, 3), "d1q3": (3, 3)}[lattice]
         self.nx, self.ny = int(nx), int(ny)
         self.precision = precision
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
@@ -73,12 +73,13 @@ class Solver:
         self.ctx = ctx
 
     @classmethod
-    def from_workload(cls, wl, precision: str = "f32", stream=None, omega=None, diag_every: int = 0):
+    def from_workload(cls, wl, precision: str = "f32", stream=None, omega=None, diag_every: int = 0,
+                      lattice: str = "d1q2"):
         if hasattr(wl, "ny"):
             return cls("d2q4", wl.nx, wl.ny, lam=wl.lam, dx=wl.dx, bc=wl.bc, gamma=wl.gamma,
                        omega=wl.omega if omega is None else omega, precision=precision, stream=stream,
                        diag_every=diag_every)
-        return cls("d1q2", wl.nx, 1, lam=wl.lam, dx=wl.dx, bc=wl.bc, gamma=wl.gamma,
+        return cls(lattice, wl.nx, 1, lam=wl.lam, dx=wl.dx, bc=wl.bc, gamma=wl.gamma,
                    omega=wl.omega if omega is None else omega, precision=precision, stream=stream,
                    diag_every=diag_every)
 
@@ -86,6 +87,7 @@ class Solver:
     @property
     def grid(self):
         return (self.ny, self.nx) if self.lattice == "d2q4" else (self.nx,)
+
 
     @property
     def storage_dtype(self):
