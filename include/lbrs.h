@@ -83,8 +83,13 @@ typedef enum { LBRS_D1Q2 = 0, LBRS_D2Q4 = 1, LBRS_D1Q3 = 2 } lbrs_lattice;
  *                40 instead of 64 bytes per cell.  Not differentiable (the
  *                adjoint calls reject it); lbrs_get/set_distributions move the
  *                raw buffer: U [4][N] FP32, g [3][4][N] FP16, 4 FP32 scales
- *                (40 N + 16 bytes). */
-typedef enum { LBRS_F64 = 0, LBRS_F32 = 1, LBRS_F16NEQ = 2 } lbrs_precision;
+ *                (40 N + 16 bytes);
+ *   LBRS_F32U    D2Q4 with omega = 1 exactly: the post-collision state is then
+ *                f^eq(U) (Section II.A with omega = 1), so only the moments U
+ *                are stored (FP32, 16 bytes per cell) and each step rebuilds
+ *                the pulled populations from the neighbours' moments.  Same
+ *                restrictions as LBRS_F16NEQ; raw buffer U [4][N] FP32. */
+typedef enum { LBRS_F64 = 0, LBRS_F32 = 1, LBRS_F16NEQ = 2, LBRS_F32U = 3 } lbrs_precision;
 
 /* Boundary kinds.  The paper defines only the free-slip wall (Section II.E);
  * the others are this library's readings:

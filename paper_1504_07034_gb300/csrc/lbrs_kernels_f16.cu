@@ -1,20 +1,26 @@
-// D2Q4 step with FP16 storage of the non-equilibrium part (precision LBRS_F16NEQ).
+// Reduced-state D2Q4 steps: the FP16 non-equilibrium form (LBRS_F16NEQ) and
+// the omega = 1 moments-only form (LBRS_F32U).
 //
-// State per cell: the moments U (4 x FP32) and, per field k, the post-collision
-// non-equilibrium parts g_q = f*_q - f^eq_q(U) of populations q = 0, 1, 2 in
-// FP16, scaled by a per-field power of two s_k (stored value g / s_k).  A state
-// buffer is U [4][N] FP32, g [3][4][N] FP16, then the four scales (FP32), so a
-// copy of the buffer is a complete checkpoint; every step carries the scales
-// over to its output buffer.  The
-// fourth follows from sum_q g_q = 0: the collision leaves the moments
-// unchanged, sum_q f*_q = U = sum_q f^eq_q(U).  40 bytes per cell instead of
-// 64, so a step moves 80 B instead of 128 B per lattice update.
+// LBRS_F16NEQ.  State per cell: the moments U (4 x FP32) and, per field k, the
+// post-collision non-equilibrium parts g_q = f*_q - f^eq_q(U) of populations
+// q = 0, 1, 2 in FP16, scaled by a per-field power of two s_k (stored value
+// g / s_k).  A state buffer is U [4][N] FP32, g [3][4][N] FP16, then the four
+// scales (FP32), so a copy of the buffer is a complete checkpoint; every step
+// carries the scales over to its output buffer.  The fourth part follows from
+// sum_q g_q = 0: the collision leaves the moments unchanged, sum_q f*_q = U =
+// sum_q f^eq_q(U).  40 bytes per cell instead of 64: 80 B per lattice update.
 //
-// Streaming pulls f*_q(x - c_q) = f^eq_q(U(x - c_q)) + s_k g_q(x - c_q): the
-// equilibrium of the source cell is re-evaluated from its stored moments
-// (Sections II.C/II.D), then the step is the FP32 step: moments, fluxes,
-// equilibria, relaxation; the new g = (1 - omega)(f - f^eq(U)) (the
-// relaxation written on the non-equilibrium part) is rounded to FP16.
+// LBRS_F32U.  At omega = 1 the relaxation returns f* = f^eq(U) exactly (Section
+// II.A with omega = 1), so the state is the moments U alone: 16 bytes per
+// cell, 32 B per lattice update.
+//
+// Both stream by reconstruction: f*_q(x - c_q) = f^eq_q(U(x - c_q)) [+ s_k g_q].
+// One CTA owns a 32 x 8 tile; it first rebuilds f* of the 34 x 10 window (tile
+// plus one cell of halo, sources outside the domain resolved by the boundary
+// kind exactly as the pull of the distribution-storing kernel does) in shared
+// memory, each window cell once, then every tile cell gathers its four pulled
+// populations, applies the wall relations, forms U and -- for the FP16 form --
+// the new non-equilibrium parts g = (1 - omega)(f - f^eq(U)).
 #include <cuda_fp16.h>
 
 #include "lbrs_kernels.cuh"
@@ -38,62 +44,87 @@ struct F16Args {
     float om, om1, c, gm1;
 };
 
-// f*_q of one source cell, all four fields.
-__device__ __forceinline__ void load_pop(const F16Args& a, int q, int64_t s, const float sc[4], float f[4])
-{
-    float U[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) U[k] = a.Uin[k * a.N + s];
-    float g[4];
-    if (q < 3) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) g[k] = __half2float(a.gin[(q * 4 + k) * a.N + s]);
-    } else {
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            g[k] = -((__half2float(a.gin[k * a.N + s]) + __half2float(a.gin[(4 + k) * a.N + s])) +
-                     __half2float(a.gin[(8 + k) * a.N + s]));
-    }
-    float e[4][4];
-    equilibria2d<float>(U, a.gm1, a.c, e);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) f[k] = e[q][k] + sc[k] * g[k];
-}
+constexpr int kTX = 32, kTY = 8, kWX = kTX + 2, kWY = kTY + 2, kWN = kWX * kWY;
 
-__device__ __forceinline__ void pull_edge_f16(const F16Args& a, int i, int j, const float sc[4], float f[4][4])
+template <bool F16>
+__global__ void __launch_bounds__(kTX * kTY) step2d_tile_kernel(const F16Args a)
 {
-    const int SX[4] = {-1, 1, 1, -1};
-    const int SY[4] = {-1, -1, 1, 1};
-    bool wall_top = false, wall_bottom = false;
+    __shared__ float s_f[16 * kWN];      // f*_{q,k} of every window slot: [q * 4 + k][slot]
+    const int i0 = blockIdx.x * kTX - 1, j0 = blockIdx.y * kTY - 1;
+    float sc[4] = {1.f, 1.f, 1.f, 1.f}, inv[4] = {1.f, 1.f, 1.f, 1.f};
+    if constexpr (F16) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        int si = i - SX[q], sj = j - SY[q];
-        const int side_y = sj < 0 ? 2 : (sj >= a.ny ? 3 : -1);
-        const int side_x = si < 0 ? 0 : (si >= a.nx ? 1 : -1);
-        const int kind_y = side_y == 2 ? a.bc[2] : a.bc[3];
-        const int kind_x = side_x == 0 ? a.bc[0] : a.bc[1];
-        if (side_y >= 0 && kind_y == BC_WALL) {
-            if (side_y == 3) wall_top = true; else wall_bottom = true;
-            continue;
+        for (int k = 0; k < 4; ++k) {
+            sc[k] = a.scale[k];
+            inv[k] = 1.f / sc[k];          // exact: the scales are powers of two
         }
+        if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x < 4) a.scale_out[threadIdx.x] = a.scale[threadIdx.x];
+    }
+
+    // phase 1: f* of each window slot, its source resolved like the pull does
+    for (int w = threadIdx.x; w < kWN; w += kTX * kTY) {
+        int i = i0 + w % kWX, j = j0 + w / kWX;
+        const int side_x = i < 0 ? 0 : (i >= a.nx ? 1 : -1);
+        const int side_y = j < 0 ? 2 : (j >= a.ny ? 3 : -1);
+        const int kind_x = side_x == 0 ? a.bc[0] : a.bc[1];
+        const int kind_y = side_y == 2 ? a.bc[2] : a.bc[3];
         const float* g = nullptr;
         if (side_x >= 0) {
-            if (kind_x == BC_DIRICHLET) g = a.ghost + side_x * GHOST_STRIDE + q * 4;
-            else if (kind_x == BC_PERIODIC) si = si < 0 ? si + a.nx : si - a.nx;
-            else si = si < 0 ? 0 : a.nx - 1;
+            if (kind_x == BC_DIRICHLET) g = a.ghost + side_x * GHOST_STRIDE;
+            else if (kind_x == BC_PERIODIC) i = i < 0 ? i + a.nx : i - a.nx;
+            else i = i < 0 ? 0 : a.nx - 1;
         }
         if (!g && side_y >= 0) {
-            if (kind_y == BC_DIRICHLET) g = a.ghost + side_y * GHOST_STRIDE + q * 4;
-            else if (kind_y == BC_PERIODIC) sj = sj < 0 ? sj + a.ny : sj - a.ny;
-            else sj = sj < 0 ? 0 : a.ny - 1;
+            // a wall side's slot is never used (the wall relation replaces those
+            // populations); clamp it like a transmissive side
+            if (kind_y == BC_DIRICHLET) g = a.ghost + side_y * GHOST_STRIDE;
+            else if (kind_y == BC_PERIODIC) j = j < 0 ? j + a.ny : j - a.ny;
+            else j = j < 0 ? 0 : a.ny - 1;
         }
         if (g) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) f[q][k] = g[k];
-        } else {
-            load_pop(a, q, (int64_t)sj * a.nx + si, sc, f[q]);
+            for (int n = 0; n < 16; ++n) s_f[n * kWN + w] = g[n];
+            continue;
         }
+        const int64_t c = (int64_t)j * a.nx + i;
+        float U[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) U[k] = a.Uin[k * a.N + c];
+        float e[4][4];
+        equilibria2d<float>(U, a.gm1, a.c, e);
+        if constexpr (F16) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float g0 = __half2float(a.gin[k * a.N + c]);
+                const float g1 = __half2float(a.gin[(4 + k) * a.N + c]);
+                const float g2 = __half2float(a.gin[(8 + k) * a.N + c]);
+                e[0][k] += sc[k] * g0;
+                e[1][k] += sc[k] * g1;
+                e[2][k] += sc[k] * g2;
+                e[3][k] += sc[k] * -((g0 + g1) + g2);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) s_f[(q * 4 + k) * kWN + w] = e[q][k];
     }
+    __syncthreads();
+
+    // phase 2: pull, wall relations, moments [, non-equilibrium parts]
+    const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
+    const int i = blockIdx.x * kTX + tx, j = blockIdx.y * kTY + ty;
+    if (i >= a.nx || j >= a.ny) return;
+    const int slot = (ty + 1) * kWX + (tx + 1);
+    // sources x - c_q: q0 (-,-) <- (+1,+1); q1 (+,-) <- (-1,+1); q2 (+,+) <- (-1,-1); q3 (-,+) <- (+1,-1)
+    const int src[4] = {slot + kWX + 1, slot + kWX - 1, slot - kWX - 1, slot - kWX + 1};
+    float f[4][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) f[q][k] = s_f[(q * 4 + k) * kWN + src[q]];
+    const bool wall_bottom = j == 0 && a.bc[2] == BC_WALL;
+    const bool wall_top = j == a.ny - 1 && a.bc[3] == BC_WALL;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const float sgn = k == 2 ? -1.f : 1.f;
@@ -106,41 +137,22 @@ __device__ __forceinline__ void pull_edge_f16(const F16Args& a, int i, int j, co
             f[2][k] = sgn * f[1][k];
         }
     }
-}
-
-__global__ void __launch_bounds__(256) step2d_f16neq_kernel(const F16Args a)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= a.nx || j >= a.ny) return;
     const int64_t c = (int64_t)j * a.nx + i;
-    if (c < 4) a.scale_out[c] = a.scale[c];
-    float sc[4], inv[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        sc[k] = a.scale[k];
-        inv[k] = 1.f / sc[k];          // exact: the scales are powers of two
-    }
-    float f[4][4];
-    if (i > 0 && i < a.nx - 1 && j > 0 && j < a.ny - 1) {
-        const int64_t s[4] = {c + a.nx + 1, c + a.nx - 1, c - a.nx - 1, c - a.nx + 1};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) load_pop(a, q, s[q], sc, f[q]);
-    } else {
-        pull_edge_f16(a, i, j, sc, f);
-    }
     float U[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) U[k] = ((f[0][k] + f[1][k]) + f[2][k]) + f[3][k];
-    float e[4][4];
-    equilibria2d<float>(U, a.gm1, a.c, e);
+    for (int k = 0; k < 4; ++k) {
+        U[k] = ((f[0][k] + f[1][k]) + f[2][k]) + f[3][k];
+        a.Uout[k * a.N + c] = U[k];
+    }
+    if constexpr (F16) {
+        float e[4][4];
+        equilibria2d<float>(U, a.gm1, a.c, e);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) a.Uout[k * a.N + c] = U[k];
+        for (int q = 0; q < 3; ++q)
 #pragma unroll
-    for (int q = 0; q < 3; ++q)
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            a.gout[(q * 4 + k) * a.N + c] = __float2half_rn(a.om1 * (f[q][k] - e[q][k]) * inv[k]);
+            for (int k = 0; k < 4; ++k)
+                a.gout[(q * 4 + k) * a.N + c] = __float2half_rn(a.om1 * (f[q][k] - e[q][k]) * inv[k]);
+    }
 }
 
 // Initial state: U from W (conserved or primitive, FP64 arithmetic), g = 0.
@@ -161,8 +173,10 @@ __global__ void __launch_bounds__(256) set_state_f16neq_kernel(const Tin* __rest
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) U[k * N + i] = (float)u[k];
+        if (g) {
 #pragma unroll
-        for (int n = 0; n < 12; ++n) g[n * N + i] = __float2half_rn(0.f);
+            for (int n = 0; n < 12; ++n) g[n * N + i] = __float2half_rn(0.f);
+        }
     }
 }
 
@@ -193,16 +207,16 @@ __global__ void field_scale_kernel(const unsigned int* __restrict__ absmax_bits,
 
 }  // namespace
 
-cudaError_t launch_step_f16neq(const F16StepArgs& s, cudaStream_t st)
+static F16Args tile_args(const F16StepArgs& s, bool f16)
 {
     F16Args a;
     a.Uin = (const float*)s.src;
-    a.gin = (const __half*)((const char*)s.src + 16 * s.N);
+    a.gin = f16 ? (const __half*)((const char*)s.src + 16 * s.N) : nullptr;
     a.Uout = (float*)s.dst;
-    a.gout = (__half*)((char*)s.dst + 16 * s.N);
+    a.gout = f16 ? (__half*)((char*)s.dst + 16 * s.N) : nullptr;
     a.ghost = s.ghost;
-    a.scale = (const float*)((const char*)s.src + 40 * s.N);
-    a.scale_out = (float*)((char*)s.dst + 40 * s.N);
+    a.scale = f16 ? (const float*)((const char*)s.src + 40 * s.N) : nullptr;
+    a.scale_out = f16 ? (float*)((char*)s.dst + 40 * s.N) : nullptr;
     a.N = s.N;
     a.nx = s.nx;
     a.ny = s.ny;
@@ -211,9 +225,31 @@ cudaError_t launch_step_f16neq(const F16StepArgs& s, cudaStream_t st)
     a.om1 = s.om1;
     a.c = s.c;
     a.gm1 = s.gm1;
-    const dim3 block(128, 2);
-    const dim3 grid((unsigned)((s.nx + block.x - 1) / block.x), (unsigned)((s.ny + block.y - 1) / block.y));
-    step2d_f16neq_kernel<<<grid, block, 0, st>>>(a);
+    return a;
+}
+
+cudaError_t launch_step_f16neq(const F16StepArgs& s, cudaStream_t st)
+{
+    const dim3 grid((unsigned)((s.nx + kTX - 1) / kTX), (unsigned)((s.ny + kTY - 1) / kTY));
+    step2d_tile_kernel<true><<<grid, kTX * kTY, 0, st>>>(tile_args(s, true));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_f32u(const F16StepArgs& s, cudaStream_t st)
+{
+    const dim3 grid((unsigned)((s.nx + kTX - 1) / kTX), (unsigned)((s.ny + kTY - 1) / kTY));
+    step2d_tile_kernel<false><<<grid, kTX * kTY, 0, st>>>(tile_args(s, false));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_state_f32u(const void* W, int w_dtype, int kind, void* fs, int64_t N, double gamma,
+                                  cudaStream_t st)
+{
+    int64_t b = (N + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    const int g = (int)(b < 1 ? 1 : b);
+    if (w_dtype == 0) set_state_f16neq_kernel<double><<<g, 256, 0, st>>>((const double*)W, (float*)fs, nullptr, N, kind, gamma);
+    else set_state_f16neq_kernel<float><<<g, 256, 0, st>>>((const float*)W, (float*)fs, nullptr, N, kind, gamma);
     return cudaGetLastError();
 }
 

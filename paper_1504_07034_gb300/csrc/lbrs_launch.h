@@ -101,6 +101,10 @@ struct F16StepArgs {
     float om, om1, c, gm1;
 };
 cudaError_t launch_step_f16neq(const F16StepArgs& a, cudaStream_t s);
+// Moments-only form (omega = 1): a state buffer is U [4][N] FP32.
+cudaError_t launch_step_f32u(const F16StepArgs& a, cudaStream_t s);
+cudaError_t launch_set_state_f32u(const void* W, int w_dtype, int kind, void* fs, int64_t N, double gamma,
+                                  cudaStream_t s);
 // U = U(W) in FP32, g = 0, then the per-field scales from max |U_k| (absmax_bits: 4 words of scratch).
 cudaError_t launch_set_state_f16neq(const void* W, int w_dtype, int kind, void* fs, int64_t N, double gamma,
                                     unsigned int* absmax_bits, cudaStream_t s);

@@ -217,7 +217,7 @@ extern "C" lbrs_status lbrs_diagnostics_noalloc(const lbrs_config* cfg, const vo
 {
     lbrs_status st = validate_config(cfg);
     if (st != LBRS_OK) return st;
-    if (cfg->precision == LBRS_F16NEQ)
+    if (cfg->precision == LBRS_F16NEQ || cfg->precision == LBRS_F32U)
         return set_error(LBRS_EINVAL, "the no-allocation diagnostics read the F64 and F32 forms only");
     if (!d_fs) return set_error(LBRS_EINVAL, "d_fs is NULL");
     if (!out) return set_error(LBRS_EINVAL, "out is NULL");

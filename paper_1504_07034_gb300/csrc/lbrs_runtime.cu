@@ -43,7 +43,8 @@ Layout layout_of(const lbrs_config* c)
     const size_t elem = c->precision == LBRS_F64 ? 8 : 4;
     const size_t N = (size_t)c->nx * (size_t)c->ny;
     L.f_bytes = c->precision == LBRS_F16NEQ ? N * (4 * 4 + 12 * 2) + 4 * sizeof(float)
-                                            : N * (size_t)(lattice_q(c->lattice) * lattice_k(c->lattice)) * elem;
+              : c->precision == LBRS_F32U ? N * 4 * sizeof(float)
+                                          : N * (size_t)(lattice_q(c->lattice) * lattice_k(c->lattice)) * elem;
     size_t off = 0;
     L.f0 = off;
     off += align_up(L.f_bytes);
@@ -68,7 +69,7 @@ Layout layout_of(const lbrs_config* c)
 struct lbrs_ctx {
     lbrs_config cfg;
     Layout L;
-    int lattice, f64, f16, Q, K;
+    int lattice, f64, f16, f32u, Q, K;
     int64_t N;
     char* ws;
     char* f[2];
@@ -121,10 +122,12 @@ lbrs_status validate(const lbrs_config* c)
                     sizeof(lbrs_config));
     if (c->lattice != LBRS_D1Q2 && c->lattice != LBRS_D2Q4 && c->lattice != LBRS_D1Q3)
         return fail(nullptr, LBRS_EINVAL, "unknown lattice %d", c->lattice);
-    if (c->precision != LBRS_F64 && c->precision != LBRS_F32 && c->precision != LBRS_F16NEQ)
+    if (c->precision < LBRS_F64 || c->precision > LBRS_F32U)
         return fail(nullptr, LBRS_EINVAL, "unknown precision %d", c->precision);
-    if (c->precision == LBRS_F16NEQ && c->lattice != LBRS_D2Q4)
-        return fail(nullptr, LBRS_EINVAL, "LBRS_F16NEQ is a D2Q4 storage form");
+    if ((c->precision == LBRS_F16NEQ || c->precision == LBRS_F32U) && c->lattice != LBRS_D2Q4)
+        return fail(nullptr, LBRS_EINVAL, "LBRS_F16NEQ and LBRS_F32U are D2Q4 storage forms");
+    if (c->precision == LBRS_F32U && c->omega != 1.0)
+        return fail(nullptr, LBRS_EINVAL, "LBRS_F32U stores only the moments and needs omega == 1");
     if (c->nx < 1 || c->ny < 1) return fail(nullptr, LBRS_EINVAL, "grid must have nx, ny >= 1");
     if (c->nx > (1LL << 30)) return fail(nullptr, LBRS_EINVAL, "nx too large (max 2^30)");
     if (c->lattice != LBRS_D2Q4 && c->ny != 1) return fail(nullptr, LBRS_EINVAL, "1-D lattices (D1Q2, D1Q3) need ny == 1");
@@ -180,7 +183,7 @@ cudaError_t launch_one_step(lbrs_ctx* ctx, int from, cudaStream_t s)
 {
     const int lat = lat_code(ctx->lattice);
     if (ctx->f64) return launch_step_f64(lat, step_args<double>(ctx, from), s);
-    if (ctx->f16) {
+    if (ctx->f16 || ctx->f32u) {
         F16StepArgs a;
         a.src = ctx->f[from];
         a.dst = ctx->f[from ^ 1];
@@ -193,7 +196,7 @@ cudaError_t launch_one_step(lbrs_ctx* ctx, int from, cudaStream_t s)
         a.om1 = (float)(1.0 - ctx->cfg.omega);
         a.c = (float)ctx->c;
         a.gm1 = (float)(ctx->cfg.gamma - 1.0);
-        return launch_step_f16neq(a, s);
+        return ctx->f16 ? launch_step_f16neq(a, s) : launch_step_f32u(a, s);
     }
     return launch_step_f32(lat, step_args<float>(ctx, from), s);
 }
@@ -201,7 +204,7 @@ cudaError_t launch_one_step(lbrs_ctx* ctx, int from, cudaStream_t s)
 // Lattice code of the read-out kernels (moments, diagnostics) for this storage.
 int readout_lattice(const lbrs_ctx* ctx)
 {
-    if (ctx->f16) return LAT_U2D;
+    if (ctx->f16 || ctx->f32u) return LAT_U2D;
     return lat_code(ctx->lattice);
 }
 
@@ -264,7 +267,7 @@ lbrs_status reset_status(lbrs_ctx* ctx)
 lbrs_status adjoint_supported(lbrs_ctx* ctx)
 {
     if (ctx->lattice != LBRS_D2Q4) return fail(ctx, LBRS_EINVAL, "the adjoint covers D2Q4 only");
-    if (ctx->f16) return fail(ctx, LBRS_EINVAL, "the adjoint covers the F64 and F32 forms only");
+    if (ctx->f16 || ctx->f32u) return fail(ctx, LBRS_EINVAL, "the adjoint covers the F64 and F32 forms only");
     for (int s = 0; s < 4; ++s)
         if (ctx->cfg.bc[s].kind != LBRS_BC_PERIODIC)
             return fail(ctx, LBRS_EINVAL, "the adjoint covers fully periodic domains only");
@@ -395,6 +398,7 @@ lbrs_status lbrs_create(const lbrs_config* cfg, void* d_workspace, size_t bytes,
     ctx->lattice = cfg->lattice;
     ctx->f64 = cfg->precision == LBRS_F64;
     ctx->f16 = cfg->precision == LBRS_F16NEQ;
+    ctx->f32u = cfg->precision == LBRS_F32U;
     ctx->Q = lattice_q(cfg->lattice);
     ctx->K = lattice_k(cfg->lattice);
     ctx->N = cfg->nx * cfg->ny;
@@ -445,7 +449,10 @@ lbrs_status lbrs_set_state(lbrs_ctx* ctx, const void* W, int on_device, int dtyp
         src = stage;
     }
     const int lat = lat_code(ctx->lattice);
-    if (ctx->f16) {
+    if (ctx->f32u) {
+        LBRS_CUDA(ctx, launch_set_state_f32u(src, dtype == LBRS_F32, kind, ctx->f[ctx->cur], ctx->N, ctx->cfg.gamma,
+                                             ctx->stream));
+    } else if (ctx->f16) {
         LBRS_CUDA(ctx, launch_set_state_f16neq(src, dtype == LBRS_F32, kind, ctx->f[ctx->cur], ctx->N, ctx->cfg.gamma,
                                                (unsigned int*)(ctx->ws + ctx->L.scale), ctx->stream));
         ctx->launches += 3;
@@ -628,7 +635,7 @@ lbrs_status lbrs_step_record(lbrs_ctx* ctx, int64_t n, void* d_U_hist)
     if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
     if (n < 0) return fail(ctx, LBRS_EINVAL, "negative step count");
     if (n > 0 && !d_U_hist) return fail(ctx, LBRS_EINVAL, "d_U_hist is NULL");
-    if (ctx->lattice != LBRS_D2Q4 || ctx->f16)
+    if (ctx->lattice != LBRS_D2Q4 || ctx->f16 || ctx->f32u)
         return fail(ctx, LBRS_EINVAL, "recording steps cover the F64 and F32 D2Q4 forms only");
     if (!ctx->has_state) return fail(ctx, LBRS_ESTATE, "no state set");
     const size_t stride = (size_t)ctx->K * ctx->N * elem_bytes(ctx);
@@ -657,7 +664,7 @@ lbrs_status lbrs_vjp_loss(lbrs_ctx* ctx, const void* d_rho_target, int dtype, vo
     if (!d_rho_target || !d_gbar) return fail(ctx, LBRS_EINVAL, "NULL buffer");
     if (dtype != LBRS_F64 && dtype != LBRS_F32) return fail(ctx, LBRS_EINVAL, "dtype must be LBRS_F64 or LBRS_F32");
     if (!ctx->has_state) return fail(ctx, LBRS_ESTATE, "no state set");
-    if (ctx->f16) return fail(ctx, LBRS_EINVAL, "the adjoint covers the F64 and F32 forms only");
+    if (ctx->f16 || ctx->f32u) return fail(ctx, LBRS_EINVAL, "the adjoint covers the F64 and F32 forms only");
     const double vol = ctx->lattice == LBRS_D2Q4 ? ctx->cfg.dx * ctx->cfg.dx : ctx->cfg.dx;
     double* partials = (double*)(ctx->ws + ctx->L.partials);
     double* dout = (double*)(ctx->ws + ctx->L.diag_out);

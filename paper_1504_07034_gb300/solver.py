@@ -15,7 +15,7 @@ from . import abi
 
 _DTYPE_CODE = {torch.float64: abi.LBRS_F64, torch.float32: abi.LBRS_F32,
                np.dtype(np.float64): abi.LBRS_F64, np.dtype(np.float32): abi.LBRS_F32}
-_PRECISION = {"f64": abi.LBRS_F64, "f32": abi.LBRS_F32, "f16neq": abi.LBRS_F16NEQ}
+_PRECISION = {"f64": abi.LBRS_F64, "f32": abi.LBRS_F32, "f16neq": abi.LBRS_F16NEQ, "f32u": abi.LBRS_F32U}
 
 
 def make_config(lattice: str, nx: int, ny: int, *, gamma: float, lam: float, omega: float, dx: float,
@@ -41,8 +41,8 @@ class Solver:
 
     lattice   "d1q2", "d1q3" or "d2q4"
     bc        per side (x-lo, x-hi[, y-lo, y-hi]): (kind, primitive_state_or_None)
-    precision "f64" (plain FP64 path), "f32" (FP32 distributions) or "f16neq" (D2Q4: FP32
-              moments plus FP16 non-equilibrium parts)
+    precision "f64" (plain FP64 path), "f32" (FP32 distributions), "f16neq" (D2Q4: FP32
+              moments plus FP16 non-equilibrium parts) or "f32u" (D2Q4 at omega = 1: FP32 moments only)
     stream    a torch.cuda.Stream (default: the current stream)
     """
 
@@ -99,7 +99,8 @@ class Solver:
     def raw_state(self) -> torch.Tensor:
         """The storage buffer as bytes (any precision): lbrs_get_distributions into a uint8 tensor."""
         n = self.nx * self.ny
-        nbytes = n * 40 + 16 if self.precision == "f16neq" else self.Q * self.K * n * (8 if self.precision == "f64" else 4)
+        nbytes = {"f16neq": n * 40 + 16, "f32u": n * 16}.get(
+            self.precision, self.Q * self.K * n * (8 if self.precision == "f64" else 4))
         out = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         self._check(self.lib.lbrs_get_distributions(self.ctx, ctypes.c_void_p(out.data_ptr()), 1))
         return out
