@@ -62,7 +62,7 @@ typedef enum {
     LBRS_ECUDA = 3,     /* a CUDA runtime call failed (see lbrs_last_error) */
     LBRS_ENONPHYS = 4,  /* a cell has rho <= 0, p <= 0 or a non-finite value */
     LBRS_ESUBCHAR = 5,  /* a cell violates lambda >= local wave-speed bound (Sections II.A, II.D) */
-    LBRS_ETIMEOUT = 6,  /* reserved: a bounded device wait gave up */
+    LBRS_ETIMEOUT = 6,  /* a bounded device wait gave up (lbrs_sync; the state is then not valid) */
     LBRS_ESTATE = 7     /* call out of order (e.g. stepping before a state was set) */
 } lbrs_status;
 
@@ -164,10 +164,17 @@ lbrs_status lbrs_set_state(lbrs_ctx* ctx, const void* W, int on_device, int dtyp
 
 /* Enqueue n >= 0 time steps (stream, boundary conditions, moments, fluxes,
  * equilibria, relaxation; discrete LBRS update, Sections II.A and II.D).
- * Asynchronous.  ESTATE if no state was set. */
+ * Asynchronous.  ESTATE if no state was set.  D2Q4 in LBRS_F32 advances pairs of
+ * steps in one launch (two steps per read and write of the state; the result is
+ * bit-identical to single steps); an odd remainder takes one single step.  Where
+ * nx % 4 == 0 that kernel fetches its tiles by tensor copies with bounded waits
+ * (see LBRS_ETIMEOUT). */
 lbrs_status lbrs_step(lbrs_ctx* ctx, int64_t n);
 
-/* Wait for the context's stream; reports a CUDA error raised by earlier work.
+/* Wait for the context's stream; reports a CUDA error raised by earlier work,
+ * and LBRS_ETIMEOUT if a tile copy of the two-step kernel did not arrive within
+ * its bounded wait (the blocks concerned left their tiles unwritten; setting a
+ * state clears the flag).
  * With cfg.diag_every > 0, lbrs_step runs the FP64 diagnostics reduction of
  * lbrs_diagnostics on the device after every diag_every-th step and records
  * the first step at which a cell was non-physical or exceeded the lattice

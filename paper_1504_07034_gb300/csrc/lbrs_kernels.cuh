@@ -216,22 +216,42 @@ __device__ __forceinline__ void pull_edge_2d(const StepArgs<T>& a, int i, int j,
     }
 }
 
-template <typename T, bool STORE_U = false>
-__device__ __forceinline__ void collide_store_2d(const StepArgs<T>& a, int64_t c, const T f[4][4])
+// Collision of one cell (Eq. 9 with the equilibria of Eq. 12): moments U of the
+// pulled populations f, then out = (1 - omega) f + omega f^eq(U).
+// In FP32 at omega = 1 (a block-uniform branch) the result is f^eq itself, which
+// is what the general expression gives there for any finite f.
+template <typename T>
+__device__ __forceinline__ void collide_2d(const StepArgs<T>& a, const T f[4][4], T U[4], T out[4][4])
 {
-    T U[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) U[k] = ((f[0][k] + f[1][k]) + f[2][k]) + f[3][k];
-    if constexpr (STORE_U) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) a.Uout[k * a.N + c] = U[k];
+    if constexpr (std::is_same<T, float>::value) {
+        if (a.om1 == 0.f) {
+            equilibria2d<T>(U, a.gm1, a.c, out);
+            return;
+        }
     }
     T e[4][4];
     equilibria2d<T>(U, a.gm1, a.c, e);
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) a.dst[(q * 4 + k) * a.N + c] = a.om1 * f[q][k] + a.om * e[q][k];
+        for (int k = 0; k < 4; ++k) out[q][k] = a.om1 * f[q][k] + a.om * e[q][k];
+}
+
+template <typename T, bool STORE_U = false>
+__device__ __forceinline__ void collide_store_2d(const StepArgs<T>& a, int64_t c, const T f[4][4])
+{
+    T U[4], out[4][4];
+    collide_2d<T>(a, f, U, out);
+    if constexpr (STORE_U) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a.Uout[k * a.N + c] = U[k];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a.dst[(q * 4 + k) * a.N + c] = out[q][k];
 }
 
 // One thread per cell; blockDim.x along i (coalesced), blockDim.y along j.

@@ -13,6 +13,9 @@
 // cross the y boundaries (walls, ghosts, wrap), take the scalar path.
 #include <stdlib.h>
 #include <string.h>
+#include <mutex>
+
+#include <cuda.h>
 
 #include "lbrs_kernels.cuh"
 #include "lbrs_batch.cuh"
@@ -208,6 +211,289 @@ __global__ void __launch_bounds__(128) step2d_f32_ilp_kernel(const StepArgs<floa
     }
 }
 
+// ---------------------------------------------------------------- two steps per launch
+//
+// Temporal blocking by two: one CTA owns a 32 x 8 tile.  Phase 1 performs step
+// n -> n+1 (the same pull, boundary resolution and collision as step2d_kernel)
+// for the 34 x 10 window of the tile plus one cell of halo and keeps the result
+// in shared memory; window slots beyond a periodic side hold the wrapped cells,
+// slots beyond any other side are not computed.  Phase 2 performs step
+// n+1 -> n+2 for the tile, pulling from shared memory: a source outside the
+// domain is resolved exactly as in pull_edge_2d (Dirichlet ghost, clamp into
+// the domain, whose cell is then in the window, or the wall relations); a
+// periodic source keeps its unwrapped coordinate, whose slot holds the wrapped
+// cell.  The state is read and written once per two steps.
+constexpr int kFTX = 32, kFTY = 8, kFWX = kFTX + 2, kFWY = kFTY + 2, kFWN = kFWX * kFWY;
+
+__device__ __forceinline__ int wrap_index(int x, int n)
+{
+    x %= n;
+    return x < 0 ? x + n : x;
+}
+
+// Phase 2 of the two-step kernels: step n+1 -> n+2 for the tile (i0, j0), pulling
+// from the window of post-collision populations in shared memory.
+// STORE_U: a.Uout receives the moments of this (second) step.
+template <bool STORE_U>
+__device__ __forceinline__ void step2_phase2(const StepArgs<float>& a, const float* s_f, int i0, int j0)
+{
+    const int ti = threadIdx.x % kFTX, tj = threadIdx.x / kFTX;
+    const int i = i0 + ti, j = j0 + tj;
+    if (i >= a.nx || j >= a.ny) return;
+    float f[4][4];
+    if (i > 0 && i < a.nx - 1 && j > 0 && j < a.ny - 1) {
+        // the cell's own slot s0; sources (i + 1, j + 1), (i - 1, j + 1), (i - 1, j - 1), (i + 1, j - 1)
+        const int s0 = (tj + 1) * kFWX + ti + 1;
+        const int sl[4] = {s0 + kFWX + 1, s0 + kFWX - 1, s0 - kFWX - 1, s0 - kFWX + 1};
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) f[q][k] = s_f[(q * 4 + k) * kFWN + sl[q]];
+        collide_store_2d<float, STORE_U>(a, (int64_t)j * a.nx + i, f);
+        return;
+    }
+    const int SX[4] = {-1, 1, 1, -1};
+    const int SY[4] = {-1, -1, 1, 1};
+    bool wall_top = false, wall_bottom = false;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        int si = i - SX[q], sj = j - SY[q];
+        const int side_y = sj < 0 ? 2 : (sj >= a.ny ? 3 : -1);
+        const int side_x = si < 0 ? 0 : (si >= a.nx ? 1 : -1);
+        const int kind_y = side_y == 2 ? a.bc[2] : a.bc[3];
+        const int kind_x = side_x == 0 ? a.bc[0] : a.bc[1];
+        if (side_y >= 0 && kind_y == BC_WALL) {
+            if (side_y == 3) wall_top = true; else wall_bottom = true;
+            continue;
+        }
+        const float* g = nullptr;
+        if (side_x >= 0) {
+            if (kind_x == BC_DIRICHLET) g = a.ghost + side_x * GHOST_STRIDE + q * 4;
+            else if (kind_x != BC_PERIODIC) si = si < 0 ? 0 : a.nx - 1;
+        }
+        if (!g && side_y >= 0) {
+            if (kind_y == BC_DIRICHLET) g = a.ghost + side_y * GHOST_STRIDE + q * 4;
+            else if (kind_y != BC_PERIODIC) sj = sj < 0 ? 0 : a.ny - 1;
+        }
+        if (g) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) f[q][k] = g[k];
+        } else {
+            const int slot = (sj - (j0 - 1)) * kFWX + (si - (i0 - 1));
+#pragma unroll
+            for (int k = 0; k < 4; ++k) f[q][k] = s_f[(q * 4 + k) * kFWN + slot];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float sgn = k == 2 ? -1.f : 1.f;
+        if (wall_top) {
+            f[0][k] = sgn * f[3][k];
+            f[1][k] = sgn * f[2][k];
+        }
+        if (wall_bottom) {
+            f[3][k] = sgn * f[0][k];
+            f[2][k] = sgn * f[1][k];
+        }
+    }
+    collide_store_2d<float, STORE_U>(a, (int64_t)j * a.nx + i, f);
+}
+
+// Phase-1 output of window slot w = (wi, wj): the post-collision populations into
+// shared memory and, with STORE_U, the moments of a tile cell (the first step's)
+// into a.Uout.
+template <bool STORE_U>
+__device__ __forceinline__ void step2_store_slot(const StepArgs<float>& a, float* s_f, int w, int wi, int wj, int i0,
+                                                 int j0, const float U[4], const float out[4][4])
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) s_f[(q * 4 + k) * kFWN + w] = out[q][k];
+    if constexpr (STORE_U) {
+        const int i = i0 - 1 + wi, j = j0 - 1 + wj;
+        if (wi >= 1 && wi <= kFTX && wj >= 1 && wj <= kFTY && i < a.nx && j < a.ny) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) a.Uout[k * a.N + (int64_t)j * a.nx + i] = U[k];
+        }
+    }
+}
+
+// The arguments of the second step: with STORE_U its moments go to the next
+// record of the history, K * N values after the first step's.
+__device__ __forceinline__ StepArgs<float> second_step_args(const StepArgs<float>& a, bool store_u)
+{
+    StepArgs<float> b = a;
+    if (store_u) b.Uout = a.Uout + 4 * a.N;
+    return b;
+}
+
+template <bool STORE_U>
+__global__ void __launch_bounds__(kFTX * kFTY, 4) step2d_f32_fused2_kernel(const StepArgs<float> a)
+{
+    __shared__ float s_f[16 * kFWN];
+    const int i0 = blockIdx.x * kFTX, j0 = blockIdx.y * kFTY;
+    const bool px = a.bc[0] == BC_PERIODIC, py = a.bc[2] == BC_PERIODIC;
+
+    // phase 1: step n -> n+1 on the window
+    for (int w = threadIdx.x; w < kFWN; w += kFTX * kFTY) {
+        int i = i0 - 1 + w % kFWX, j = j0 - 1 + w / kFWX;
+        if (i < 0 || i >= a.nx) {
+            if (!px) continue;
+            i = wrap_index(i, a.nx);
+        }
+        if (j < 0 || j >= a.ny) {
+            if (!py) continue;
+            j = wrap_index(j, a.ny);
+        }
+        const int64_t c = (int64_t)j * a.nx + i;
+        float f[4][4];
+        if (i > 0 && i < a.nx - 1 && j > 0 && j < a.ny - 1) {
+            const int64_t src[4] = {c + a.nx + 1, c + a.nx - 1, c - a.nx - 1, c - a.nx + 1};
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) f[q][k] = a.src[(q * 4 + k) * a.N + src[q]];
+        } else {
+            pull_edge_2d<float>(a, i, j, f);
+        }
+        float U[4], out[4][4];
+        collide_2d<float>(a, f, U, out);
+        step2_store_slot<STORE_U>(a, s_f, w, w % kFWX, w / kFWX, i0, j0, U, out);
+    }
+    __syncthreads();
+
+    step2_phase2<STORE_U>(second_step_args(a, STORE_U), s_f, i0, j0);
+}
+
+// ---------------------------------------------------------------- two steps per launch, TMA-fed
+//
+// The same two steps, with the state the tile needs fetched by tensor copies
+// (cp.async.bulk.tensor) into shared memory.  Population q of a window slot
+// (i, j) is pulled from (i - sx_q, j - sy_q), so each population needs the window
+// shifted by its own velocity: one copy per population of its 4 fields over a
+// 36 x 10 box, x from i0 (q = 1, 4: sources right of the slot) or i0 - 4 (q = 2, 3),
+// y from j0 (sources above) or j0 - 2 (below).  x starts on a 16-byte boundary.
+// 22.5 KB in all, so that five blocks fit on an SM.  Cells outside the grid
+// arrive as zeros and are never read, because a window slot whose pull leaves the
+// grid interior takes the general path (global loads through pull_edge_2d)
+// instead.  One elected thread arms an mbarrier with the byte count and issues
+// the copies; every thread waits on the barrier's phase with a bounded number of
+// polls.  A wait that gives up sets *wait_flag, and the whole block leaves
+// without touching the destination.
+constexpr int kPX = 36, kPY = kFTY + 2, kPN = kPX * kPY;          // one field of one population's box
+constexpr uint32_t kRawBytes = 16u * kPN * sizeof(float);
+constexpr size_t kTmaSmemBytes = 128 + kRawBytes + 16 * kFWN * sizeof(float) + 16;
+constexpr int kWaitPolls = 1 << 22;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, int polls)
+{
+    for (int it = 0; it < polls; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// Phase 1 of the TMA-fed kernel: step n -> n+1 on the window of tile (i0, j0),
+// interior slots from the raw window in shared memory.
+template <bool STORE_U>
+__device__ __forceinline__ void step2_phase1_raw(const StepArgs<float>& a, const float* s_raw, float* s_f, int i0,
+                                                 int j0)
+{
+    const bool px = a.bc[0] == BC_PERIODIC, py = a.bc[2] == BC_PERIODIC;
+    for (int w = threadIdx.x; w < kFWN; w += kFTX * kFTY) {
+        const int wi = w % kFWX, wj = w / kFWX;
+        int i = i0 - 1 + wi, j = j0 - 1 + wj;
+        if (i < 0 || i >= a.nx) {
+            if (!px) continue;
+            i = wrap_index(i, a.nx);
+        }
+        if (j < 0 || j >= a.ny) {
+            if (!py) continue;
+            j = wrap_index(j, a.ny);
+        }
+        float f[4][4];
+        if (i > 0 && i < a.nx - 1 && j > 0 && j < a.ny - 1) {
+            // source of population q in its box: row wj, column wi (+2 where the box starts at i0 - 4)
+            const int b = wj * kPX + wi;
+            const int r[4] = {b, b + 2, b + 2, b};
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) f[q][k] = s_raw[(q * 4 + k) * kPN + r[q]];
+        } else {
+            pull_edge_2d<float>(a, i, j, f);
+        }
+        float U[4], out[4][4];
+        collide_2d<float>(a, f, U, out);
+        step2_store_slot<STORE_U>(a, s_f, w, wi, wj, i0, j0, U, out);
+    }
+}
+
+__device__ __forceinline__ void issue_tile_copy(const CUtensorMap* tmap, float* s_raw, uint32_t bar, int i0, int j0)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kRawBytes) : "memory");
+    const int x0[4] = {i0, i0 - 4, i0 - 4, i0};
+    const int y0[4] = {j0, j0, j0 - 2, j0 - 2};
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(s_raw + q * 4 * kPN)),
+            "l"((uint64_t)tmap), "r"(x0[q]), "r"(y0[q]), "r"(q * 4), "r"(bar)
+            : "memory");
+}
+
+// One block per tile, five resident blocks per SM (48 registers, 44.9 KB of shared
+// memory each).  Forms that reuse a block for further tiles, issuing the next
+// copy as soon as phase 1 has read the raw buffer, measured slower: persistent
+// blocks fall into step and wait for their copies together, and a loop over
+// tiles raises the register count past the five-block budget (spills).
+template <bool STORE_U>
+__global__ void __launch_bounds__(kFTX * kFTY, 5)
+    step2d_f32_fused2_tma_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs<float> a, unsigned* wait_flag)
+{
+    extern __shared__ unsigned char smem_dyn[];
+    float* s_raw = (float*)(((uintptr_t)smem_dyn + 127) & ~(uintptr_t)127);
+    float* s_f = s_raw + 16 * kPN;
+    uint64_t* bar_p = (uint64_t*)(s_f + 16 * kFWN);
+    const uint32_t bar = smem_addr(bar_p);
+    const int i0 = blockIdx.x * kFTX, j0 = blockIdx.y * kFTY;
+
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue_tile_copy(&tmap, s_raw, bar, i0, j0);
+    }
+    __syncthreads();
+    const bool arrived = mbar_wait_bounded(bar, 0, kWaitPolls);
+    if (!__syncthreads_and(arrived)) {
+        if (threadIdx.x == 0) {
+            atomicExch(wait_flag, 1u);
+            mbar_wait_bounded(bar, 0, kWaitPolls);   // give the copy in flight a last chance to land
+        }
+        return;
+    }
+    step2_phase1_raw<STORE_U>(a, s_raw, s_f, i0, j0);
+    __syncthreads();
+    step2_phase2<STORE_U>(second_step_args(a, STORE_U), s_f, i0, j0);
+}
+
 // Kernel variant for D2Q4 FP32: 0 = scalar one cell per thread, 2 or 4 =
 // vector width, 12 / 14 = 2 / 4 strided cells per thread.  The default can be
 // overridden for tuning sweeps with the environment variable LBRS_F32_STEP_VARIANT.
@@ -249,6 +535,92 @@ cudaError_t launch_step_f32(int lattice, const StepArgs<float>& a, cudaStream_t 
         step1d_q3_kernel<float><<<(unsigned)((a.nx + 255) / 256), 256, 0, s>>>(a);
     } else {
         step1d_kernel<float><<<(unsigned)((a.nx + 255) / 256), 256, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+// Two steps per launch (temporal blocking by two); on by default, LBRS_F32_FUSE=0 turns it off.
+bool step2_f32_enabled()
+{
+    static int v = [] {
+        const char* s = getenv("LBRS_F32_FUSE");
+        return (s && !strcmp(s, "0")) ? 0 : 1;
+    }();
+    return v != 0;
+}
+
+// Tensor copies for the two-step kernel; on by default, LBRS_F32_TMA=0 turns them off.
+static bool tma_enabled()
+{
+    static int v = [] {
+        const char* s = getenv("LBRS_F32_TMA");
+        return (s && !strcmp(s, "0")) ? 0 : 1;
+    }();
+    return v != 0;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled()
+{
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    });
+    return fn;
+}
+
+bool encode_f32_tile_map(TileMap* map, const float* f, int64_t nx, int64_t ny)
+{
+    static_assert(sizeof(map->bytes) == sizeof(CUtensorMap), "TileMap holds one CUtensorMap");
+    map->valid = 0;
+    if (!tma_enabled() || nx % 4 != 0 || ((uintptr_t)f & 15)) return false;   // row and field strides: 16-byte multiples
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return false;
+    static std::once_flag attr_once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr_once, [] {
+        attr_err = cudaFuncSetAttribute(step2d_f32_fused2_tma_kernel<false>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmemBytes);
+        if (attr_err == cudaSuccess)
+            attr_err = cudaFuncSetAttribute(step2d_f32_fused2_tma_kernel<true>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmemBytes);
+    });
+    if (attr_err != cudaSuccess) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, 16};
+    const cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)(nx * ny) * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)kPX, (cuuint32_t)kPY, 4};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUtensorMap m;
+    if (enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)f, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+        return false;
+    memcpy(map->bytes, &m, sizeof m);
+    map->valid = 1;
+    return true;
+}
+
+cudaError_t launch_step2_f32(const StepArgs<float>& a, const TileMap* map, unsigned* wait_flag, cudaStream_t s)
+{
+    const dim3 grid((unsigned)((a.nx + kFTX - 1) / kFTX), (unsigned)((a.ny + kFTY - 1) / kFTY));
+    const bool rec = a.Uout != nullptr;
+    if (map && map->valid && wait_flag) {
+        CUtensorMap m;
+        memcpy(&m, map->bytes, sizeof m);
+        if (rec) step2d_f32_fused2_tma_kernel<true><<<grid, kFTX * kFTY, kTmaSmemBytes, s>>>(m, a, wait_flag);
+        else step2d_f32_fused2_tma_kernel<false><<<grid, kFTX * kFTY, kTmaSmemBytes, s>>>(m, a, wait_flag);
+    } else {
+        if (rec) step2d_f32_fused2_kernel<true><<<grid, kFTX * kFTY, 0, s>>>(a);
+        else step2d_f32_fused2_kernel<false><<<grid, kFTX * kFTY, 0, s>>>(a);
     }
     return cudaGetLastError();
 }

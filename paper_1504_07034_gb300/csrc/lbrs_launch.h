@@ -21,6 +21,17 @@ struct BatchTile;
 // One time step src -> dst.  lattice: LAT_D1Q2 / LAT_D2Q4.
 cudaError_t launch_step_f64(int lattice, const StepArgs<double>& a, cudaStream_t s);
 cudaError_t launch_step_f32(int lattice, const StepArgs<float>& a, cudaStream_t s);
+// D2Q4 FP32: two time steps in one launch, src -> dst (temporal blocking by two).
+// With a valid tile map of src the kernel fetches its window by tensor copies and
+// reports a bounded wait that gave up in *wait_flag; otherwise it loads directly.
+// A non-null a.Uout records the moments of both steps: [2][4][N] from a.Uout.
+struct alignas(64) TileMap {
+    unsigned char bytes[128];   // an encoded CUtensorMap
+    int valid;
+};
+bool step2_f32_enabled();
+bool encode_f32_tile_map(TileMap* map, const float* f, int64_t nx, int64_t ny);
+cudaError_t launch_step2_f32(const StepArgs<float>& a, const TileMap* map, unsigned* wait_flag, cudaStream_t s);
 
 // Dirichlet ghost tables: ghost[side][q*K + k] = f^eq(U(prim[side])) for every
 // side whose kind is DIRICHLET, computed in FP64 and rounded to the storage type.

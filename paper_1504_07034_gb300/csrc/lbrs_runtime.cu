@@ -29,7 +29,7 @@ thread_local char g_err[512] = "";
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t f_bytes, f0, f1, ghost, partials, diag_out, scale, status, total;
+    size_t f_bytes, f0, f1, ghost, partials, diag_out, scale, status, wait_flag, total;
 };
 
 int lattice_q(int lat) { return lat == LBRS_D2Q4 ? 4 : (lat == LBRS_D1Q3 ? 3 : 2); }
@@ -60,6 +60,8 @@ Layout layout_of(const lbrs_config* c)
     off += align_up(4 * sizeof(float));
     L.status = off;                                  // record of the periodic device checks
     off += align_up(4 * sizeof(double));
+    L.wait_flag = off;                               // set by a bounded device wait that gave up
+    off += align_up(sizeof(unsigned));
     L.total = off;
     return L;
 }
@@ -81,6 +83,7 @@ struct lbrs_ctx {
     double c;                // 1/(4 lambda) in 2-D, 1/(2 lambda) in 1-D
     cudaStream_t cap_stream;
     cudaGraphExec_t graph[2];
+    TileMap tmap[2];         // tensor maps of the two state buffers (FP32 D2Q4 two-step kernel)
     // checkpointed adjoint: the run recorded by lbrs_forward_checkpointed
     char* adj_ws;
     size_t adj_bytes;
@@ -201,6 +204,20 @@ cudaError_t launch_one_step(lbrs_ctx* ctx, int from, cudaStream_t s)
     return launch_step_f32(lat, step_args<float>(ctx, from), s);
 }
 
+// Two-steps-per-launch kernel available for this context?
+bool fused2(const lbrs_ctx* ctx)
+{
+    return !ctx->f64 && !ctx->f16 && !ctx->f32u && ctx->lattice == LBRS_D2Q4 && step2_f32_enabled();
+}
+
+unsigned* wait_flag(const lbrs_ctx* ctx) { return (unsigned*)(ctx->ws + ctx->L.wait_flag); }
+
+// Two steps from buffer b into buffer b ^ 1.
+cudaError_t launch_step2(const lbrs_ctx* ctx, int b, cudaStream_t s)
+{
+    return launch_step2_f32(step_args<float>(ctx, b), &ctx->tmap[b], wait_flag(ctx), s);
+}
+
 // Lattice code of the read-out kernels (moments, diagnostics) for this storage.
 int readout_lattice(const lbrs_ctx* ctx)
 {
@@ -216,8 +233,14 @@ lbrs_status ensure_graph(lbrs_ctx* ctx, int from)
     LBRS_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t le = cudaSuccess;
     int b = from;
-    for (int n = 0; n < kGraphSteps && le == cudaSuccess; ++n) {
-        le = launch_one_step(ctx, b, ctx->cap_stream);
+    for (int n = 0; n < kGraphSteps && le == cudaSuccess;) {
+        if (fused2(ctx)) {
+            le = launch_step2(ctx, b, ctx->cap_stream);
+            n += 2;
+        } else {
+            le = launch_one_step(ctx, b, ctx->cap_stream);
+            n += 1;
+        }
         b ^= 1;
     }
     cudaGraph_t g = nullptr;
@@ -256,9 +279,11 @@ cudaError_t periodic_check(lbrs_ctx* ctx)
     return launch_status_update(dout, (double*)(ctx->ws + ctx->L.status), ctx->step, ctx->stream);
 }
 
+// A new state clears the record of the periodic checks and the wait flag.
 lbrs_status reset_status(lbrs_ctx* ctx)
 {
     LBRS_CUDA(ctx, launch_status_reset((double*)(ctx->ws + ctx->L.status), ctx->stream));
+    LBRS_CUDA(ctx, cudaMemsetAsync(wait_flag(ctx), 0, sizeof(unsigned), ctx->stream));
     ctx->launches += 1;
     return LBRS_OK;
 }
@@ -303,6 +328,34 @@ cudaError_t launch_record_step(lbrs_ctx* ctx, void* Uout)
     StepArgs<float> a = step_args<float>(ctx, ctx->cur);
     a.Uout = (float*)Uout;
     return launch_step_record_f32(a, ctx->stream);
+}
+
+// Two recording steps in one launch (FP32 D2Q4): the moments of both steps go to
+// Uout and Uout + K N.
+cudaError_t launch_record_step2(lbrs_ctx* ctx, void* Uout)
+{
+    StepArgs<float> a = step_args<float>(ctx, ctx->cur);
+    a.Uout = (float*)Uout;
+    return launch_step2_f32(a, &ctx->tmap[ctx->cur], wait_flag(ctx), ctx->stream);
+}
+
+// n recording steps from the current buffer into U_hist (stride: one step's moments),
+// in pairs where the two-step kernel applies.
+lbrs_status record_steps(lbrs_ctx* ctx, int64_t n, char* U_hist)
+{
+    const size_t stride = (size_t)ctx->K * ctx->N * elem_bytes(ctx);
+    int64_t m = 0;
+    for (; m + 2 <= n && fused2(ctx); m += 2) {
+        LBRS_CUDA(ctx, launch_record_step2(ctx, U_hist + m * stride));
+        ctx->cur ^= 1;
+        ctx->launches += 1;
+    }
+    for (; m < n; ++m) {
+        LBRS_CUDA(ctx, launch_record_step(ctx, U_hist + m * stride));
+        ctx->cur ^= 1;
+        ctx->launches += 1;
+    }
+    return LBRS_OK;
 }
 
 cudaError_t launch_adjoint_step_raw(lbrs_ctx* ctx, const void* U_next, const void* gin, void* gout)
@@ -422,6 +475,14 @@ lbrs_status lbrs_create(const lbrs_config* cfg, void* d_workspace, size_t bytes,
         return s;
     }
     ctx->launches = 1;
+    e = cudaMemsetAsync(wait_flag(ctx), 0, sizeof(unsigned), ctx->stream);
+    if (e != cudaSuccess) {
+        lbrs_status s = cuda_fail(nullptr, e, "clearing the wait flag");
+        free(ctx);
+        return s;
+    }
+    if (fused2(ctx))
+        for (int b = 0; b < 2; ++b) encode_f32_tile_map(&ctx->tmap[b], (const float*)ctx->f[b], cfg->nx, cfg->ny);
     *out = ctx;
     return LBRS_OK;
 }
@@ -498,12 +559,19 @@ static lbrs_status step_plain(lbrs_ctx* ctx, int64_t n)
     if (cap == cudaStreamCaptureStatusNone && n >= 2 * kGraphSteps) {
         lbrs_status st = ensure_graph(ctx, ctx->cur);
         if (st != LBRS_OK) return st;
+        const int per_graph = fused2(ctx) ? kGraphSteps / 2 : kGraphSteps;
         while (left >= kGraphSteps) {
             LBRS_CUDA(ctx, cudaGraphLaunch(ctx->graph[ctx->cur], ctx->stream));
             left -= kGraphSteps;
             ctx->step += kGraphSteps;
-            ctx->launches += kGraphSteps;
+            ctx->launches += per_graph;
         }
+    }
+    for (; left >= 2 && fused2(ctx); left -= 2) {
+        LBRS_CUDA(ctx, launch_step2(ctx, ctx->cur, ctx->stream));
+        ctx->cur ^= 1;
+        ctx->step += 2;
+        ctx->launches += 1;
     }
     for (; left > 0; --left) {
         LBRS_CUDA(ctx, launch_one_step(ctx, ctx->cur, ctx->stream));
@@ -518,6 +586,12 @@ lbrs_status lbrs_sync(lbrs_ctx* ctx)
 {
     if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
     LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->tmap[0].valid || ctx->tmap[1].valid) {
+        unsigned flag = 0;
+        LBRS_CUDA(ctx, cudaMemcpyAsync(&flag, wait_flag(ctx), sizeof flag, cudaMemcpyDeviceToHost, ctx->stream));
+        LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        if (flag) return fail(ctx, LBRS_ETIMEOUT, "a bounded wait for a tile copy gave up; the state is not valid");
+    }
     if (ctx->cfg.diag_every > 0 && ctx->has_state) {
         double st[4];
         LBRS_CUDA(ctx, cudaMemcpyAsync(st, ctx->ws + ctx->L.status, sizeof st, cudaMemcpyDeviceToHost, ctx->stream));
@@ -638,13 +712,9 @@ lbrs_status lbrs_step_record(lbrs_ctx* ctx, int64_t n, void* d_U_hist)
     if (ctx->lattice != LBRS_D2Q4 || ctx->f16 || ctx->f32u)
         return fail(ctx, LBRS_EINVAL, "recording steps cover the F64 and F32 D2Q4 forms only");
     if (!ctx->has_state) return fail(ctx, LBRS_ESTATE, "no state set");
-    const size_t stride = (size_t)ctx->K * ctx->N * elem_bytes(ctx);
-    for (int64_t m = 0; m < n; ++m) {
-        LBRS_CUDA(ctx, launch_record_step(ctx, (char*)d_U_hist + m * stride));
-        ctx->cur ^= 1;
-        ctx->step += 1;
-        ctx->launches += 1;
-    }
+    lbrs_status st = record_steps(ctx, n, (char*)d_U_hist);
+    if (st != LBRS_OK) return st;
+    ctx->step += n;
     return LBRS_OK;
 }
 
@@ -757,11 +827,8 @@ lbrs_status lbrs_backward_checkpointed(lbrs_ctx* ctx, void* d_adj_ws, const void
         // recompute the segment from its checkpoint, recording U^{start+1 .. start+len}
         LBRS_CUDA(ctx, cudaMemcpyAsync(ctx->f[ctx->cur], ws + A.ckpt0 + s * A.ckpt_stride, ctx->L.f_bytes,
                                        cudaMemcpyDeviceToDevice, ctx->stream));
-        for (int64_t m = 0; m < len; ++m) {
-            LBRS_CUDA(ctx, launch_record_step(ctx, uhist + m * ustride));
-            ctx->cur ^= 1;
-            ctx->launches += 1;
-        }
+        lbrs_status rs = record_steps(ctx, len, uhist);
+        if (rs != LBRS_OK) return rs;
         for (int64_t m = len - 1; m >= 0; --m) {
             LBRS_CUDA(ctx, launch_adjoint_step_raw(ctx, uhist + m * ustride, g[gc], g[gc ^ 1]));
             gc ^= 1;

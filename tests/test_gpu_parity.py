@@ -138,7 +138,8 @@ def test_zero_steps_is_initial_equilibrium():
 
 
 def test_graph_path_equals_single_steps():
-    """lbrs_step(n) replays a captured graph for long runs; it must equal n single steps bitwise."""
+    """lbrs_step(n) replays a captured graph for long runs and, in FP32, advances two steps per
+    launch; it must equal n single steps bitwise."""
     wl = small_case(100, 64, "dirichlet_wall", 1.2, steps=0)
     a = solver(wl, "f32")
     b = solver(wl, "f32")
@@ -329,13 +330,27 @@ from paper_1504_07034_gb300.solver import Solver
 out = []
 D = [("dirichlet", (1.0, 0.5, 0.1, 1.0)), ("dirichlet", (0.8, -0.2, 0.0, 0.9))]
 T = ("transmissive", None)
-for bc in ([T] * 4, [("periodic", None)] * 4, D + [T, T], [T, D[1], ("wall", None), D[0]]):
+P = ("periodic", None)
+Wl = ("wall", None)
+for bc in ([T] * 4, [P] * 4, D + [T, T], [T, D[1], Wl, D[0]], [P, P, Wl, Wl], [D[0], T, D[1], Wl]):
     wl = W.quadrant_riemann(1, 64, steps=50)
-    for nx in (256, 64, 12):
-        prim = np.ascontiguousarray(np.tile(wl.prim, (1, 1, 4))[:, :48, :nx])
-        s = Solver("d2q4", nx, 48, lam=1.6 * wl.lam, dx=1.0 / 64, bc=bc, precision="f32")
+    for nx, ny in ((256, 48), (64, 48), (12, 48), (37, 29), (66, 17), (5, 3), (1, 9), (33, 1)):
+        if bc[0] == P and nx % 2:
+            nx += 1
+        if bc[2] == P and ny % 2:
+            ny += 1
+        if Wl in (bc[2], bc[3]):
+            ny = max(ny, 2)
+        prim = np.ascontiguousarray(np.tile(wl.prim, (1, 1, 4))[:, :ny, :nx])
+        if bc[2] == Wl:
+            prim[2, 0, :] = 0.0
+        if bc[3] == Wl:
+            prim[2, -1, :] = 0.0
+        s = Solver("d2q4", nx, ny, lam=1.6 * wl.lam, dx=1.0 / 64, bc=bc, precision="f32")
         s.set_state(torch.from_numpy(prim).cuda())
-        s.step(50)
+        s.step(51)
+        out.append(s.get_distributions().cpu().numpy().ravel())
+        out.append(s.step_record(7).cpu().numpy().ravel())      # recording steps: 3 pairs and a single
         out.append(s.get_distributions().cpu().numpy().ravel())
         s.close()
 np.save(sys.argv[2], np.concatenate(out))
@@ -343,7 +358,13 @@ np.save(sys.argv[2], np.concatenate(out))
 
 
 def test_f32_kernel_variants_agree(tmp_path):
-    """Scalar, vector-width and strided kernels compute the same step (up to FMA contraction)."""
+    """Scalar, vector-width and strided one-step kernels and the two-steps-per-launch kernel
+    compute the same steps.  The two-step kernel runs the scalar kernel's per-cell code (same
+    loads, boundary resolution and collision helper), so it must agree bit for bit; the other
+    variants up to FMA contraction.  The two-step kernel is fed by tensor copies where
+    nx % 4 == 0 and by direct loads otherwise (and everywhere with LBRS_F32_TMA=0).  51 steps:
+    a 32-step graph, then 9 two-step launches and one single step; then 7 recording steps
+    (moments of every step, as the adjoint recompute takes them)."""
     import os
     import subprocess
     import sys
@@ -351,14 +372,18 @@ def test_f32_kernel_variants_agree(tmp_path):
     script = tmp_path / "variant.py"
     script.write_text(_VARIANT_SCRIPT)
     res = {}
-    for v in ("0", "2", "4", "12", "14"):
+    for v in ("0", "2", "4", "12", "14", "fused", "fused_direct"):
         out = tmp_path / f"v{v}.npy"
-        env = dict(os.environ, LBRS_F32_STEP_VARIANT=v)
+        fused = v.startswith("fused")
+        env = dict(os.environ, LBRS_F32_STEP_VARIANT="0" if fused else v, LBRS_F32_FUSE="1" if fused else "0",
+                   LBRS_F32_TMA="0" if v == "fused_direct" else "1")
         subprocess.run([sys.executable, str(script), root, str(out)], check=True, env=env, timeout=300)
         res[v] = np.load(out)
     scale = np.abs(res["0"]).max()
     for v in ("2", "4", "12", "14"):
         assert np.max(np.abs(res[v] - res["0"])) <= 1e-5 * scale, v
+    for v in ("fused", "fused_direct"):
+        assert np.array_equal(res[v], res["0"]), (v, np.max(np.abs(res[v] - res["0"])) / scale)
 
 
 # ------------------------------------------------------------------- periodic device checks
