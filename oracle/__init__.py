@@ -68,6 +68,7 @@ class _Params(ctypes.Structure):
         ("omega", ctypes.c_double),
         ("bc_kind", ctypes.c_int32 * 4),
         ("bc_prim", (ctypes.c_double * 4) * 4),
+        ("solid", ctypes.POINTER(ctypes.c_uint8)),
     ]
 
 
@@ -107,6 +108,8 @@ def lib():
         L.orc_adjoint_step.restype = ctypes.c_int
         L.orc_vjp_equilibrium.argtypes = [P, dp, dp, dp]
         L.orc_vjp_equilibrium.restype = ctypes.c_int
+        L.orc_obstacle_check.argtypes = [P]
+        L.orc_obstacle_check.restype = ctypes.c_int64
         _lib = L
     return _lib
 
@@ -124,7 +127,7 @@ class Oracle:
     """One LBRS problem: lattice, grid, gamma, lambda, omega, boundary conditions."""
 
     def __init__(self, lattice: int, nx: int, ny: int = 1, *, gamma: float = 1.4, lam: float,
-                 omega: float = 1.0, bc=None, nthreads: int = 0):
+                 omega: float = 1.0, bc=None, nthreads: int = 0, solid=None):
         self.lattice = lattice
         self.Q, self.K = {D2Q4: (4, 4), D1Q3: (3, 3), D1Q2: (2, 3)}[lattice]
         self.nx, self.ny = int(nx), int(ny)
@@ -141,16 +144,25 @@ class Oracle:
             if state is not None:
                 for k, val in enumerate(state):
                     p.bc_prim[s][k] = float(val)
+        self.solid = None
+        if solid is not None:
+            self.solid = np.ascontiguousarray(solid, dtype=np.uint8)
+            if self.solid.shape != (self.ny, self.nx):
+                raise ValueError(f"solid mask must have shape {(self.ny, self.nx)}")
+            p.solid = self.solid.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
         self.p = p
         err = lib().orc_validate(ctypes.byref(p))
         if err:
             raise ValueError(f"invalid oracle parameters (code {err})")
+        if lib().orc_obstacle_check(ctypes.byref(p)):
+            raise ValueError("obstacle geometry leaves a fluid cell without a known mirror population")
 
     @classmethod
     def from_workload(cls, wl, nthreads: int = 0, omega=None, lattice=None):
         if hasattr(wl, "ny"):
             return cls(D2Q4, wl.nx, wl.ny, gamma=wl.gamma, lam=wl.lam,
-                       omega=wl.omega if omega is None else omega, bc=wl.bc, nthreads=nthreads)
+                       omega=wl.omega if omega is None else omega, bc=wl.bc, nthreads=nthreads,
+                       solid=getattr(wl, "solid", None))
         return cls(lattice or D1Q2, wl.nx, 1, gamma=wl.gamma, lam=wl.lam,
                    omega=wl.omega if omega is None else omega, bc=wl.bc, nthreads=nthreads)
 

@@ -63,6 +63,7 @@ typedef struct {
     double gamma, lambda, omega;
     int32_t bc_kind[4];   /* x-lo, x-hi, y-lo, y-hi */
     double bc_prim[4][4]; /* Dirichlet primitive state per side: (rho,u,p) in 1-D, (rho,u,v,p) in 2-D */
+    const uint8_t* solid; /* D2Q4 only, nullable: [ny][nx], nonzero = solid (internal wall) cell */
 } orc_params;
 
 typedef struct {
@@ -257,7 +258,101 @@ int orc_validate(const orc_params* P)
     }
     if (P->lattice == ORC_D2Q4 && (P->bc_kind[2] == ORC_WALL || P->bc_kind[3] == ORC_WALL) && P->ny < 2)
         return 8;
+    if (P->solid && P->lattice != ORC_D2Q4) return 9;
     return 0;
+}
+
+/*
+ * Internal walls (lattice-aligned obstacles), extending the free-slip wall of
+ * Section II.E to solid cells.  Readings (the paper gives the rule for a
+ * straight upper wall only):
+ *   - solid cells are inert: their distributions are carried unchanged;
+ *   - in a fluid cell, a population whose pull source (after the domain
+ *     boundaries) is a solid cell is unknown after streaming.  It takes the
+ *     value of a known population of the same cell, chosen by which of the two
+ *     axis neighbours towards the source, (i - sx, j) and (i, j - sy), is solid:
+ *       only the x neighbour: a wall normal to x -> the population mirrored in x,
+ *                             (-sx, sy), with rho u negated;
+ *       only the y neighbour: a wall normal to y -> mirrored in y, (sx, -sy),
+ *                             with rho v negated (the paper's upper-wall rule);
+ *       both or neither (a concave or a convex corner): the opposite population
+ *                             (-sx, -sy), with rho u and rho v negated;
+ *   - the axis neighbours are mapped through the domain boundaries like a
+ *     pull source (wrap, clamp); a Dirichlet or wall side counts as fluid;
+ *   - a geometry where the chosen population is itself unknown (a fluid
+ *     channel one cell wide, say) is rejected;
+ *   - obstacle populations are resolved before the domain-wall relations.
+ */
+static int is_solid(const orc_params* P, int64_t i, int64_t j)
+{
+    const int64_t nx = P->nx, ny = P->ny;
+    if (i < 0 || i >= nx) {
+        int kind = P->bc_kind[i < 0 ? 0 : 1];
+        if (kind == ORC_PERIODIC) i = (i + nx) % nx;
+        else if (kind == ORC_TRANSMISSIVE) i = i < 0 ? 0 : nx - 1;
+        else return 0;
+    }
+    if (j < 0 || j >= ny) {
+        int kind = P->bc_kind[j < 0 ? 2 : 3];
+        if (kind == ORC_PERIODIC) j = (j + ny) % ny;
+        else if (kind == ORC_TRANSMISSIVE) j = j < 0 ? 0 : ny - 1;
+        else return 0;
+    }
+    return P->solid[j * nx + i] != 0;
+}
+
+/* The population that replaces q (unknown at cell (i, j)) and the signs of rho u, rho v. */
+static int obstacle_mirror(const orc_params* P, int64_t i, int64_t j, int q, double* sgn_u, double* sgn_v)
+{
+    int sx = SX2[q], sy = SY2[q];
+    int xn = is_solid(P, i - sx, j), yn = is_solid(P, i, j - sy);
+    int mx = sx, my = sy;
+    if (xn && !yn) {
+        mx = -sx;
+    } else if (!xn && yn) {
+        my = -sy;
+    } else {
+        mx = -sx;
+        my = -sy;
+    }
+    *sgn_u = mx != sx ? -1.0 : 1.0;
+    *sgn_v = my != sy ? -1.0 : 1.0;
+    for (int m = 0; m < 4; ++m)
+        if (SX2[m] == mx && SY2[m] == my) return m;
+    return -1;
+}
+
+/* How the pull of population q into (i, j) resolves: 0 a grid cell that is fluid,
+ * 1 a Dirichlet ghost, 2 a wall side, 3 a solid cell. */
+static int pull_kind(const orc_params* P, int64_t i, int64_t j, int q)
+{
+    const int64_t nx = P->nx, ny = P->ny;
+    int64_t si = i - SX2[q], sj = j - SY2[q];
+    int side_y = sj < 0 ? 2 : (sj >= ny ? 3 : -1);
+    int side_x = si < 0 ? 0 : (si >= nx ? 1 : -1);
+    if (side_y >= 0 && P->bc_kind[side_y] == ORC_WALL) return 2;
+    if (side_x >= 0 && P->bc_kind[side_x] == ORC_DIRICHLET) return 1;
+    if (side_y >= 0 && P->bc_kind[side_y] == ORC_DIRICHLET) return 1;
+    return is_solid(P, si, sj) ? 3 : 0;
+}
+
+/* Number of (cell, population) pairs whose replacement is itself unknown (0 = valid geometry). */
+int64_t orc_obstacle_check(const orc_params* P)
+{
+    if (!P->solid || P->lattice != ORC_D2Q4) return 0;
+    int64_t bad = 0;
+    for (int64_t j = 0; j < P->ny; ++j)
+        for (int64_t i = 0; i < P->nx; ++i) {
+            if (P->solid[j * P->nx + i]) continue;
+            for (int q = 0; q < 4; ++q) {
+                if (pull_kind(P, i, j, q) != 3) continue;
+                double su, sv;
+                int m = obstacle_mirror(P, i, j, q, &su, &sv);
+                int km = pull_kind(P, i, j, m);
+                if (km == 2 || km == 3) ++bad;
+            }
+        }
+    return bad;
 }
 
 /* Ghost distributions of each Dirichlet side: f^eq of the boundary state. */
@@ -280,6 +375,7 @@ int orc_stream(const orc_params* P, const double* fs, double* f)
 {
     int err = orc_validate(P);
     if (err) return err;
+    if (orc_obstacle_check(P)) return 10;
     const int64_t nx = P->nx, ny = P->ny, N = nx * ny;
     const int Q = nq(P), K = nk(P);
     double ghost[4][16];
@@ -290,7 +386,13 @@ int orc_stream(const orc_params* P, const double* fs, double* f)
     for (int64_t j = 0; j < ny; ++j) {
         for (int64_t i = 0; i < nx; ++i) {
             const int64_t c = j * nx + i;
+            if (P->solid && P->solid[c]) {                    /* inert solid cell */
+                for (int q = 0; q < Q; ++q)
+                    for (int k = 0; k < K; ++k) f[(q * K + k) * N + c] = fs[(q * K + k) * N + c];
+                continue;
+            }
             int wall_pop[4] = {0, 0, 0, 0};
+            int solid_pop[4] = {0, 0, 0, 0};
             for (int q = 0; q < Q; ++q) {
                 int sx = two_d ? SX2[q] : (Q == 3 ? SX13[q] : SX1[q]);
                 int sy = two_d ? SY2[q] : 0;
@@ -314,8 +416,22 @@ int orc_stream(const orc_params* P, const double* fs, double* f)
                     else if (kind == ORC_PERIODIC) sj = (sj + ny) % ny;
                     else sj = sj < 0 ? 0 : ny - 1;              /* transmissive */
                 }
+                if (!g && P->solid && P->solid[sj * nx + si]) {
+                    solid_pop[q] = 1;         /* set below from the internal-wall relation */
+                    continue;
+                }
                 for (int k = 0; k < K; ++k)
                     f[(q * K + k) * N + c] = g ? g[q * K + k] : fs[(q * K + k) * N + sj * nx + si];
+            }
+            /* Internal walls: an unknown population takes a known one of this cell. */
+            for (int q = 0; q < Q; ++q) {
+                if (!solid_pop[q]) continue;
+                double sgn_u, sgn_v;
+                int m = obstacle_mirror(P, i, j, q, &sgn_u, &sgn_v);
+                for (int k = 0; k < K; ++k) {
+                    double sgn = k == 1 ? sgn_u : (k == 2 ? sgn_v : 1.0);
+                    f[(q * K + k) * N + c] = sgn * f[(m * K + k) * N + c];
+                }
             }
             /* Free-slip wall (Section II.E).  Top wall: the incoming downward
              * populations f1, f2 (q = 0, 1) take f1 = f4, f2 = f3, negated for
@@ -363,10 +479,11 @@ void orc_collide(const orc_params* P, const double* f, double* fs, double* U, or
             if (U) U[k * N + c] = s;
         }
         feq_cell(P, u, feq);
+        const int inert = P->solid && P->solid[c];          /* solid cells are carried unchanged */
         for (int q = 0; q < Q; ++q)
             for (int k = 0; k < K; ++k) {
                 int64_t idx = (q * K + k) * N + c;
-                fs[idx] = om1 * f[idx] + om * feq[q * K + k];
+                fs[idx] = inert ? f[idx] : om1 * f[idx] + om * feq[q * K + k];
             }
         double p = pressure(P, u);
         int finite = 1;

@@ -494,6 +494,135 @@ __global__ void __launch_bounds__(kFTX * kFTY, 5)
     step2_phase2<STORE_U>(second_step_args(a, STORE_U), s_f, i0, j0);
 }
 
+// ---------------------------------------------------------------- adjoint, two steps per launch
+//
+// The adjoint step pushes fbar(x) = (1 - w) g(x) + w J_E(U(x))^T g(x) to x - c_q.
+// Read as a pull, g^{s-1}(y)_q = k^s_q(y + c_q) with k^s = fbar computed at its own
+// cell.  Storing k instead of g makes the adjoint sweep the same shape as the
+// forward step -- gather, then a local operator -- so two steps fuse like the
+// forward's: phase 1 forms k^{s-1} on the tile's 34 x 10 window (periodic wrap)
+// into shared memory, phase 2 forms k^{s-2} on the tile.  Every value is the push
+// kernel's expression at the same cell, so the sweep is bit-identical to it.
+
+__device__ __forceinline__ void adj_local(const AdjArgs<float>& a, const float U[4], const float g[4][4],
+                                          float out[4][4])
+{
+    float ubar[4];
+    equilibrium_vjp2d<float>(U, g, a.gamma, a.gm1, a.c, ubar);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) out[q][k] = a.om1 * g[q][k] + a.om * ubar[k];
+}
+
+// g(x)_q = k_q(x + c_q) for a cell (i, j) of the periodic grid.
+__device__ __forceinline__ void adj_gather(const AdjArgs<float>& a, int i, int j, float g[4][4])
+{
+    const int SX[4] = {-1, 1, 1, -1};
+    const int SY[4] = {-1, -1, 1, 1};
+    if (i > 0 && i < a.nx - 1 && j > 0 && j < a.ny - 1) {
+        const int64_t c = (int64_t)j * a.nx + i;
+        const int64_t src[4] = {c - a.nx - 1, c - a.nx + 1, c + a.nx + 1, c + a.nx - 1};
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) g[q][k] = a.gin[(q * 4 + k) * a.N + src[q]];
+        return;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int64_t s = (int64_t)wrap_index(j + SY[q], a.ny) * a.nx + wrap_index(i + SX[q], a.nx);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) g[q][k] = a.gin[(q * 4 + k) * a.N + s];
+    }
+}
+
+// k(x) = (1 - w) g(x) + w J_E(U(x))^T g(x), pointwise (the start of a sweep).
+__global__ void __launch_bounds__(256) adj_local_kernel(const AdjArgs<float> a)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < a.N; c += (int64_t)gridDim.x * blockDim.x) {
+        float g[4][4], U[4], out[4][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) g[q][k] = a.gin[(q * 4 + k) * a.N + c];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) U[k] = a.U[k * a.N + c];
+        adj_local(a, U, g, out);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) a.gout[(q * 4 + k) * a.N + c] = out[q][k];
+    }
+}
+
+// One step: g = gathered k; with a.U, out = the local operator of g, else out = g
+// (the last step of a segment, which hands g to the earlier segment).
+__global__ void __launch_bounds__(256) adj_pull_kernel(const AdjArgs<float> a)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= a.nx || j >= a.ny) return;
+    const int64_t c = (int64_t)j * a.nx + i;
+    float g[4][4], out[4][4];
+    adj_gather(a, i, j, g);
+    if (a.U) {
+        float U[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) U[k] = a.U[k * a.N + c];
+        adj_local(a, U, g, out);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) out[q][k] = g[q][k];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a.gout[(q * 4 + k) * a.N + c] = out[q][k];
+}
+
+// Two steps: k^s (a.gin) -> k^{s-2} (a.gout); a.U = U_{s-1}, U2 = U_{s-2}.
+__global__ void __launch_bounds__(kFTX * kFTY, 4) adj_fused2_kernel(const AdjArgs<float> a, const float* __restrict__ U2)
+{
+    __shared__ float s_k[16 * kFWN];
+    const int i0 = blockIdx.x * kFTX, j0 = blockIdx.y * kFTY;
+    for (int w = threadIdx.x; w < kFWN; w += kFTX * kFTY) {
+        const int i = wrap_index(i0 - 1 + w % kFWX, a.nx), j = wrap_index(j0 - 1 + w / kFWX, a.ny);
+        float g[4][4], U[4], out[4][4];
+        adj_gather(a, i, j, g);
+        const int64_t c = (int64_t)j * a.nx + i;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) U[k] = a.U[k * a.N + c];
+        adj_local(a, U, g, out);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) s_k[(q * 4 + k) * kFWN + w] = out[q][k];
+    }
+    __syncthreads();
+    const int ti = threadIdx.x % kFTX, tj = threadIdx.x / kFTX;
+    const int i = i0 + ti, j = j0 + tj;
+    if (i >= a.nx || j >= a.ny) return;
+    // sources y + c_q: slots (ti + 1 + sx_q, tj + 1 + sy_q)
+    const int s0 = (tj + 1) * kFWX + ti + 1;
+    const int sl[4] = {s0 - kFWX - 1, s0 - kFWX + 1, s0 + kFWX + 1, s0 + kFWX - 1};
+    float g[4][4], U[4], out[4][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) g[q][k] = s_k[(q * 4 + k) * kFWN + sl[q]];
+    const int64_t c = (int64_t)j * a.nx + i;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) U[k] = U2[k * a.N + c];
+    adj_local(a, U, g, out);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a.gout[(q * 4 + k) * a.N + c] = out[q][k];
+}
+
 // Kernel variant for D2Q4 FP32: 0 = scalar one cell per thread, 2 or 4 =
 // vector width, 12 / 14 = 2 / 4 strided cells per thread.  The default can be
 // overridden for tuning sweeps with the environment variable LBRS_F32_STEP_VARIANT.
@@ -638,6 +767,29 @@ cudaError_t launch_adjoint_f32(const AdjArgs<float>& a, cudaStream_t s)
     const dim3 block(128, 2);
     const dim3 grid((unsigned)((a.nx + block.x - 1) / block.x), (unsigned)((a.ny + block.y - 1) / block.y));
     adjoint2d_kernel<float><<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_local_f32(const AdjArgs<float>& a, cudaStream_t s)
+{
+    int64_t b = (a.N + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    adj_local_kernel<<<(unsigned)(b < 1 ? 1 : b), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_pull_f32(const AdjArgs<float>& a, cudaStream_t s)
+{
+    const dim3 block(128, 2);
+    const dim3 grid((unsigned)((a.nx + block.x - 1) / block.x), (unsigned)((a.ny + block.y - 1) / block.y));
+    adj_pull_kernel<<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_fused2_f32(const AdjArgs<float>& a, const float* U2, cudaStream_t s)
+{
+    const dim3 grid((unsigned)((a.nx + kFTX - 1) / kFTX), (unsigned)((a.ny + kFTY - 1) / kFTY));
+    adj_fused2_kernel<<<grid, kFTX * kFTY, 0, s>>>(a, U2);
     return cudaGetLastError();
 }
 

@@ -68,6 +68,12 @@ cudaError_t launch_step_record_f32(const StepArgs<float>& a, cudaStream_t s);
 // Adjoint of one periodic D2Q4 step, and the equilibrium VJP dL/dU0 (see lbrs_kernels.cuh).
 cudaError_t launch_adjoint_f64(const AdjArgs<double>& a, cudaStream_t s);
 cudaError_t launch_adjoint_f32(const AdjArgs<float>& a, cudaStream_t s);
+// FP32 adjoint sweep on k = (1 - w) g + w J_E^T g (periodic D2Q4): pointwise k from
+// g (a.U, a.gin -> a.gout); one pull step (with a.U: k, without: g); two fused steps
+// k^s -> k^{s-2} with a.U = U_{s-1} and U2 = U_{s-2}.
+cudaError_t launch_adj_local_f32(const AdjArgs<float>& a, cudaStream_t s);
+cudaError_t launch_adj_pull_f32(const AdjArgs<float>& a, cudaStream_t s);
+cudaError_t launch_adj_fused2_f32(const AdjArgs<float>& a, const float* U2, cudaStream_t s);
 cudaError_t launch_vjp_equilibrium_f64(const AdjArgs<double>& a, cudaStream_t s);
 cudaError_t launch_vjp_equilibrium_f32(const AdjArgs<float>& a, cudaStream_t s);
 

@@ -829,10 +829,34 @@ lbrs_status lbrs_backward_checkpointed(lbrs_ctx* ctx, void* d_adj_ws, const void
                                        cudaMemcpyDeviceToDevice, ctx->stream));
         lbrs_status rs = record_steps(ctx, len, uhist);
         if (rs != LBRS_OK) return rs;
-        for (int64_t m = len - 1; m >= 0; --m) {
-            LBRS_CUDA(ctx, launch_adjoint_step_raw(ctx, uhist + m * ustride, g[gc], g[gc ^ 1]));
+        if (fused2(ctx)) {
+            // sweep on k = fbar: k^{end} from g^{end}, two steps per launch while U_{s-1} and
+            // U_{s-2} lie in this segment, one more step if needed, then the pull that hands
+            // g^{start} to the earlier segment.  uhist[m] holds U_{start+m+1}.
+            AdjArgs<float> aa = adj_args<float>(ctx, uhist + (len - 1) * ustride, g[gc], g[gc ^ 1]);
+            LBRS_CUDA(ctx, launch_adj_local_f32(aa, ctx->stream));
             gc ^= 1;
-            ctx->launches += 1;
+            int64_t t = len;                                   // g[gc] holds k^{start+t}
+            for (; t >= 3; t -= 2) {
+                aa = adj_args<float>(ctx, uhist + (t - 2) * ustride, g[gc], g[gc ^ 1]);
+                LBRS_CUDA(ctx, launch_adj_fused2_f32(aa, (const float*)(uhist + (t - 3) * ustride), ctx->stream));
+                gc ^= 1;
+            }
+            if (t == 2) {
+                aa = adj_args<float>(ctx, uhist, g[gc], g[gc ^ 1]);
+                LBRS_CUDA(ctx, launch_adj_pull_f32(aa, ctx->stream));
+                gc ^= 1;
+            }
+            aa = adj_args<float>(ctx, nullptr, g[gc], g[gc ^ 1]);
+            LBRS_CUDA(ctx, launch_adj_pull_f32(aa, ctx->stream));
+            gc ^= 1;
+            ctx->launches += 2 + (len - 1) / 2 + ((len - 1) % 2);
+        } else {
+            for (int64_t m = len - 1; m >= 0; --m) {
+                LBRS_CUDA(ctx, launch_adjoint_step_raw(ctx, uhist + m * ustride, g[gc], g[gc ^ 1]));
+                gc ^= 1;
+                ctx->launches += 1;
+            }
         }
     }
     // dL/dU0 = J_E(U0)^T gbar^0 with U0 the moments of the first checkpoint

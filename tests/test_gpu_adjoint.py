@@ -92,6 +92,47 @@ def test_segmentations_give_identical_gradients():
     assert torch.equal(results[0], results[1]) and torch.equal(results[0], results[2])
 
 
+_SWEEP_SCRIPT = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+import workloads as W
+from paper_1504_07034_gb300.solver import Solver
+out = []
+for (nx, ny), steps, seg in (((64, 48), 23, 5), ((66, 18), 20, 4), ((34, 10), 9, 9), ((130, 50), 12, 1),
+                             ((2, 2), 7, 3), ((40, 8), 30, 6)):
+    wl, target = W.adjoint_pulses(seed=2, n=max(nx, ny), steps=0, width=0.1, pulses=3, omega=1.3)
+    prim = np.ascontiguousarray(wl.prim[:, :ny, :nx])
+    s = Solver("d2q4", nx, ny, lam=wl.lam, dx=wl.dx, bc=[("periodic", None)] * 4, omega=1.3, precision="f32")
+    s.set_state(torch.from_numpy(prim).cuda())
+    s.forward_checkpointed(steps, seg)
+    _, gT = s.vjp_loss(torch.from_numpy(np.ascontiguousarray(target[:ny, :nx])).cuda())
+    out.append(s.backward_checkpointed(gT).cpu().numpy().ravel())
+    s.close()
+np.save(sys.argv[2], np.concatenate(out))
+"""
+
+
+def test_f32_fused_sweep_equals_push_sweep(tmp_path):
+    """The FP32 backward sweep stores k = (1 - w) g + w J_E^T g and advances two steps per launch;
+    it computes every value with the push kernel's expression at the same cell, so the gradient
+    must equal the one-step push sweep's bit for bit (odd and even segment lengths, ragged tiles,
+    segment 1, a 2 x 2 grid)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = tmp_path / "sweep.py"
+    script.write_text(_SWEEP_SCRIPT)
+    res = {}
+    for fuse in ("0", "1"):
+        out = tmp_path / f"g{fuse}.npy"
+        env = dict(os.environ, LBRS_F32_FUSE=fuse)
+        subprocess.run([sys.executable, str(script), root, str(out)], check=True, env=env, timeout=300)
+        res[fuse] = np.load(out)
+    assert np.all(np.isfinite(res["0"]))
+    assert np.array_equal(res["0"], res["1"]), np.max(np.abs(res["0"] - res["1"])) / np.max(np.abs(res["0"]))
+
+
 def _fd_errors(s_grad, wl, target, U0, steps, ndir, seed=5):
     """Relative errors of <grad, d> against FP64 central differences of the FP64 GPU path."""
     from paper_1504_07034_gb300.solver import Solver

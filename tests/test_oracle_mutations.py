@@ -14,8 +14,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "lbrs_oracle.c")
 
 MUTANTS = {
-    "relaxation_weights_swapped": ("fs[idx] = om1 * f[idx] + om * feq[q * K + k];",
-                                   "fs[idx] = om * f[idx] + om1 * feq[q * K + k];"),
+    "relaxation_weights_swapped": ("fs[idx] = inert ? f[idx] : om1 * f[idx] + om * feq[q * K + k];",
+                                   "fs[idx] = inert ? f[idx] : om * f[idx] + om1 * feq[q * K + k];"),
     "energy_flux_drops_pressure": ("F[3] = u * (en + p);", "F[3] = u * en;"),
     "momentum_flux_drops_pressure": ("F[1] = mx * u + p;", "F[1] = mx * u;"),
     "pressure_drops_v_term": ("double p = (g - 1.0) * (en - 0.5 * (mx * u + my * v));",
@@ -44,6 +44,14 @@ MUTANTS = {
                                         "{q2h - u * u, (2.0 - g) * u, -gm1 * v, gm1},"),
     "adjoint_pushes_the_wrong_way": ("const int64_t ti = (i - SX2[q] + nx) % nx, tj = (j - SY2[q] + ny) % ny;",
                                      "const int64_t ti = (i + SX2[q] + nx) % nx, tj = (j + SY2[q] + ny) % ny;"),
+    # internal walls
+    "obstacle_x_wall_keeps_rho_u_sign": ("*sgn_u = mx != sx ? -1.0 : 1.0;", "*sgn_u = 1.0;"),
+    "obstacle_walls_classified_crosswise": ("    if (xn && !yn) {\n        mx = -sx;\n    } else if (!xn && yn) {\n        my = -sy;",
+                                            "    if (xn && !yn) {\n        my = -sy;\n    } else if (!xn && yn) {\n        mx = -sx;"),
+    "obstacle_corner_reflects_in_y": ("    } else {\n        mx = -sx;\n        my = -sy;\n    }",
+                                      "    } else {\n        my = -sy;\n    }"),
+    "obstacle_solid_cells_relax": ("fs[idx] = inert ? f[idx] : om1 * f[idx] + om * feq[q * K + k];",
+                                   "fs[idx] = om1 * f[idx] + om * feq[q * K + k];"),
     "adjoint_relaxation_weights_swapped": ("gout[(q * 4 + k) * N + tj * nx + ti] = om1 * gq[q * 4 + k] + om * ubar[k];",
                                            "gout[(q * 4 + k) * N + tj * nx + ti] = om * gq[q * 4 + k] + om1 * ubar[k];"),
 }
@@ -63,6 +71,7 @@ def test_pins_catch_mutant(name, tmp_path):
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", "test_oracle_pins.py"),
                         os.path.join(ROOT, "tests", "test_oracle_pins_d1q3.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_adjoint.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_adjoint.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_obstacles.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"pins did not catch mutant {name}:\n{r.stdout[-2000:]}"

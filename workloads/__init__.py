@@ -15,6 +15,9 @@ from .generators import (  # noqa: F401
     batched_tubes,
     bouchut_speed,
     explosion,
+    forward_facing_step,
+    normal_shock_state,
+    shock_diffraction,
     lambda_1d_riemann,
     lambda_2d_quadrants,
     oblique_shock_reflection,

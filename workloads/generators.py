@@ -65,6 +65,7 @@ class Workload2D:
     steps: int
     gamma: float = GAMMA
     meta: dict = field(default_factory=dict)
+    solid: np.ndarray | None = None   # (ny, nx) uint8, 1 = solid cell of an internal wall
 
     @property
     def cells(self) -> int:
@@ -379,3 +380,84 @@ def adjoint_pulses(seed: int = 0, n: int = 2048, pulses: int = 8, amp: float = 0
     wl = Workload2D(f"adjoint_pulses_s{seed}", n, n, 1.0 / n, 0.0, 0.0, prim, [("periodic", None)] * 4,
                     lam, omega, steps)
     return wl, target
+
+
+# ---------------------------------------------------------------- internal walls
+
+FFS_INFLOW = (1.4, 3.0, 0.0, 1.0)          # Mach 3: a = sqrt(1.4 * 1 / 1.4) = 1
+
+
+def normal_shock_state(gamma, rho1, u1, p1, mach):
+    """State behind a normal shock of Mach number `mach` relative to a gas (rho1, u1, p1)
+    moving along +x; the shock moves along +x (Rankine-Hugoniot, ideal gas).
+    Returns (rho2, u2, p2) in the frame of the input state."""
+    a1 = sound(gamma, rho1, p1)
+    m2 = mach * mach
+    p2 = p1 * (1.0 + 2.0 * gamma / (gamma + 1.0) * (m2 - 1.0))
+    rho2 = rho1 * (gamma + 1.0) * m2 / ((gamma - 1.0) * m2 + 2.0)
+    w = u1 + mach * a1                      # shock speed
+    u2 = w - (w - u1) * rho1 / rho2         # mass flux continuity in the shock frame
+    return rho2, u2, p2
+
+
+def forward_facing_step(nx: int = 240, ny: int = 80, omega: float = 1.0, t_final: float = 4.0,
+                        steps: int | None = None, lam_factor: float = 1.5) -> Workload2D:
+    """Mach 3 flow over a forward-facing step in the channel [0, 3] x [0, 1] (Section III).
+
+    The step is the block x >= 0.6, y < 0.2 (solid cells).  Inflow (1.4, 3, 0, 1) on the
+    left, transmissive outflow on the right, free-slip walls at the bottom and the top;
+    the interior starts at the inflow state.  lambda = lam_factor times the D2Q4 bound of the
+    stagnation state behind the bow shock (the largest bound the run meets, checked by the
+    oracle), raised so that t_final is a whole number of steps.
+    """
+    dx = 3.0 / nx
+    if abs(dx - 1.0 / ny) > 1e-15:
+        raise ValueError("D2Q4 needs dx == dy: use nx = 3 ny")
+    x = _cell_centres(nx, 0.0, dx)[None, :]
+    y = _cell_centres(ny, 0.0, dx)[:, None]
+    solid = ((x >= 0.6) & (y < 0.2)).astype(np.uint8)
+    prim = np.empty((4, ny, nx))
+    for k in range(4):
+        prim[k] = FFS_INFLOW[k]
+    rho, u, v, p = FFS_INFLOW
+    mach = u / sound(GAMMA, rho, p)
+    r2, u2_lab, p2 = normal_shock_state(GAMMA, rho, 0.0, p, mach)
+    u2 = mach * sound(GAMMA, rho, p) - u2_lab                   # behind a standing normal shock
+    lam0 = max(bouchut_speed(GAMMA, rho, u, v, p), bouchut_speed(GAMMA, r2, u2, 0.0, p2),
+               bouchut_speed(GAMMA, r2, 0.0, u2, p2))
+    lam = lam_factor * lam0
+    if steps is None:
+        lam, steps = _round_lambda(lam, dx, t_final)
+    bc = [("dirichlet", FFS_INFLOW), ("transmissive", None), ("wall", None), ("wall", None)]
+    return Workload2D("forward_facing_step", nx, ny, dx, 0.0, 0.0, prim, bc, lam, omega, int(steps),
+                      meta={"step": (0.6, 0.2), "t_final": t_final}, solid=solid)
+
+
+def shock_diffraction(n: int = 400, omega: float = 1.0, t_final: float = 0.1561, steps: int | None = None,
+                      corner=(0.1, 0.6), mach: float = 5.09, lam_factor: float = 2.0) -> Workload2D:
+    """A Mach 5.09 normal shock diffracting over a backward-facing step in [0, 1]^2 (Section III).
+
+    The step is the block x < corner[0], y < corner[1] (solid cells).  The shock starts at
+    x = corner[0] above the step, moving along +x into gas at rest (1.4, 0, 0, 1); behind it
+    the Rankine-Hugoniot state.  Left side: that state (inflow); right and top transmissive;
+    bottom a free-slip wall.  lambda = lam_factor times the D2Q4 bound of the post-shock
+    state (the corner expansion accelerates the flow; checked by the oracle).
+    """
+    dx = 1.0 / n
+    xs, ys = corner
+    x = _cell_centres(n, 0.0, dx)[None, :]
+    y = _cell_centres(n, 0.0, dx)[:, None]
+    solid = ((x < xs) & (y < ys)).astype(np.uint8)
+    pre = (1.4, 0.0, 0.0, 1.0)
+    r2, u2, p2 = normal_shock_state(GAMMA, pre[0], pre[1], pre[3], mach)
+    post = (r2, u2, 0.0, p2)
+    prim = np.empty((4, n, n))
+    behind = np.broadcast_to(x < xs, (n, n))
+    for k in range(4):
+        prim[k] = np.where(behind, post[k], pre[k])
+    lam = lam_factor * bouchut_speed(GAMMA, *post)
+    if steps is None:
+        lam, steps = _round_lambda(lam, dx, t_final)
+    bc = [("dirichlet", post), ("transmissive", None), ("wall", None), ("transmissive", None)]
+    return Workload2D("shock_diffraction", n, n, dx, 0.0, 0.0, prim, bc, lam, omega, int(steps),
+                      meta={"corner": corner, "mach": mach, "post": post, "t_final": t_final}, solid=solid)
