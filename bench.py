@@ -276,6 +276,53 @@ def oblique_measurement(Solver, stream, barrier, peak):
     return out
 
 
+def obstacle_measurement(Solver, stream, barrier, peak):
+    """Internal walls: the Mach 3 forward-facing step at the paper's 240 x 80 to t = 4 and the
+    shock diffraction at 400 x 400 to t = 0.1561 (FP32 density L1 against FP64 over the fluid
+    cells), and steady FP32 stepping of the step problem on a 6144 x 2048 grid (805 MB of
+    state, larger than L2) for MLUPS and the roofline of the obstacle step kernel."""
+    import torch
+    out = {}
+    for name, wl in (("forward_facing_step_240x80_t4", workloads.forward_facing_step()),
+                     ("shock_diffraction_400x400", workloads.shock_diffraction(n=400))):
+        rho = {}
+        with torch.cuda.stream(stream):
+            for precision in ("f64", "f32"):
+                s = Solver.from_workload(wl, precision=precision, stream=stream)
+                s.set_state(torch.from_numpy(wl.prim).cuda())
+                s.step(wl.steps)
+                rho[precision] = s.moments(torch.float64)[0].clone()
+                if precision == "f64":
+                    diag = s.diagnostics()
+                s.close()
+        stream.synchronize()
+        fluid = torch.from_numpy(wl.solid == 0).cuda()
+        out[name] = {"steps": wl.steps, "lambda": wl.lam,
+                     "l1_rho_f32_vs_f64": float((rho["f32"] - rho["f64"])[fluid].abs().mean().item()),
+                     "fp64_status": diag["status"], "fp64_min_rho": diag["min_rho"], "fp64_min_p": diag["min_p"]}
+    big = workloads.forward_facing_step(nx=6144, ny=2048, steps=200)
+    s = Solver.from_workload(big, precision="f32", stream=stream)
+    with torch.cuda.stream(stream):
+        s.set_state(torch.from_numpy(big.prim).cuda())
+        s.step(64)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        a.record(stream)
+        s.step(big.steps)
+        b.record(stream)
+        barrier()
+    s.close()
+    t = a.elapsed_time(b) / 1e3
+    mlups = big.cells * big.steps / t / 1e6
+    bpl = BYTES_PER_LUP_F32 + 1
+    out["steady_6144x2048_f32"] = {"value": mlups, "unit": UNIT, "kernel": "step2d_obstacle_kernel<float>",
+                                   "algorithmic_bytes_per_lup": bpl, "achieved_gbs": bpl * mlups / 1e3,
+                                   "frac": bpl * mlups / 1e3 / peak,
+                                   "note": "one step per launch (the two-step kernel has no internal walls); "
+                                           "128 B of distributions plus the 1 B mask per update"}
+    return out
+
+
 def batch_measurement(stream, barrier):
     """4096 shock tubes, N log-uniform in [200, 20000], to t = 0.15 in FP32 (temporal blocking)."""
     import torch
@@ -505,6 +552,9 @@ def run_ours(args):
     # --- Sod shock tube (1-D, latency-bound) ------------------------------------------
     sod = sod_measurement(Solver, stream, barrier)
 
+    # --- internal walls: forward-facing step and shock diffraction ------------------
+    obstacles = obstacle_measurement(Solver, stream, barrier, peak)
+
     # --- batched 1-D tubes ---------------------------------------------------------
     batched = batch_measurement(stream, barrier)
 
@@ -546,6 +596,7 @@ def run_ours(args):
             "moments_only_omega1": moments_only,
             "adjoint": adjoint,
             "sod_1d": sod,
+            "internal_walls": obstacles,
             "batched_tubes": batched,
             "fp64": {"value": mlups64, "unit": UNIT, "achieved_gbs": BYTES_PER_LUP_F64 * mlups64 / 1e3,
                      "diag_after_1000_steps": {k: d64[k] for k in ("status", "min_rho", "min_p", "max_lambda_local")}},

@@ -224,6 +224,22 @@ lbrs_status lbrs_diagnostics_noalloc(const lbrs_config* cfg, const void* d_fs, l
 lbrs_status lbrs_get_distributions(lbrs_ctx* ctx, void* dst, int on_device);
 lbrs_status lbrs_set_distributions(lbrs_ctx* ctx, const void* src, int on_device, int64_t step);
 
+/* Lattice-aligned internal walls (obstacles such as the forward-facing step and the
+ * backward-facing step of the shock-diffraction problem, Section III), D2Q4 in
+ * LBRS_F64 or LBRS_F32.  d_solid: device mask [ny][nx] of uint8, nonzero = solid
+ * cell; owned by the caller, read at every step until replaced, so it must outlive
+ * the context or a later call with NULL (which removes the walls).  Solid cells are
+ * inert (their distributions are carried unchanged).  In a fluid cell, a population
+ * pulled from a solid cell takes the free-slip reflection of Section II.E, applied
+ * to the obstacle face: the population mirrored in x (rho u negated) when only the
+ * axis neighbour (i - sx, j) is solid, mirrored in y (rho v negated) when only
+ * (i, j - sy) is, the opposite one (both negated) at corners.  The mask is checked
+ * on the host (one synchronous copy): EINVAL if a replacement would itself be
+ * unknown (fluid channels one cell wide), for other lattices or storage forms.
+ * With walls set, FP32 steps run one per launch and the adjoint calls return
+ * EINVAL. */
+lbrs_status lbrs_set_obstacles(lbrs_ctx* ctx, const uint8_t* d_solid);
+
 /* ---------------------------------------------------------------- adjoint
  *
  * Discrete adjoint of the D2Q4 step on a fully periodic domain.  The paper

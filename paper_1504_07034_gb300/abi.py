@@ -97,6 +97,7 @@ SIGNATURES = {
     "lbrs_diagnostics_noalloc": (ctypes.c_int, [ctypes.POINTER(lbrs_config), _P, ctypes.POINTER(lbrs_diag)]),
     "lbrs_get_distributions": (ctypes.c_int, [_CTX, _P, ctypes.c_int]),
     "lbrs_set_distributions": (ctypes.c_int, [_CTX, _P, ctypes.c_int, ctypes.c_int64]),
+    "lbrs_set_obstacles": (ctypes.c_int, [_CTX, _P]),
     "lbrs_step_count": (ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_int64)]),
     "lbrs_launch_count": (ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_int64)]),
     "lbrs_last_error": (ctypes.c_char_p, [_CTX]),

@@ -53,6 +53,7 @@ struct StepArgs {
     T c;                          // 1/(4 lambda) in 2-D, 1/(2 lambda) in 1-D
     T gm1;                        // gamma - 1
     T* __restrict__ Uout;         // recording steps only: moments U_k of the step, [K][ny][nx]
+    const uint8_t* __restrict__ solid;  // D2Q4, nullable: [ny][nx], nonzero = solid cell of an internal wall
 };
 
 // ---------------------------------------------------------------- arithmetic
@@ -216,6 +217,110 @@ __device__ __forceinline__ void pull_edge_2d(const StepArgs<T>& a, int i, int j,
     }
 }
 
+// ---------------------------------------------------------------- internal walls
+//
+// Lattice-aligned obstacles: solid cells are inert (their distributions are
+// carried unchanged).  In a fluid cell, a population whose pull source (after the
+// domain boundaries) is a solid cell is replaced by a known population of the same
+// cell -- the free-slip reflection of Section II.E generalised to obstacle faces:
+// with only the axis neighbour (i - sx, j) solid, the wall is normal to x and the
+// population mirrored in x, (-sx, sy), is taken with rho u negated; with only
+// (i, j - sy) solid, mirrored in y with rho v negated (the paper's upper-wall
+// relations); with both or neither (a concave or a convex corner), the opposite
+// population with both negated.  Axis neighbours map through the domain sides
+// like pull sources (wrap, clamp; Dirichlet and wall sides count as fluid).  The
+// host rejects geometries where the chosen population is itself unknown, so the
+// replacement is always a pulled or ghost value.  Obstacle populations are
+// resolved before the domain-wall relations.
+
+template <typename T>
+__device__ __forceinline__ bool solid_at(const StepArgs<T>& a, int i, int j)
+{
+    if (i < 0 || i >= a.nx) {
+        const int kind = i < 0 ? a.bc[0] : a.bc[1];
+        if (kind == BC_PERIODIC) i = i < 0 ? i + a.nx : i - a.nx;
+        else if (kind == BC_TRANSMISSIVE) i = i < 0 ? 0 : a.nx - 1;
+        else return false;
+    }
+    if (j < 0 || j >= a.ny) {
+        const int kind = j < 0 ? a.bc[2] : a.bc[3];
+        if (kind == BC_PERIODIC) j = j < 0 ? j + a.ny : j - a.ny;
+        else if (kind == BC_TRANSMISSIVE) j = j < 0 ? 0 : a.ny - 1;
+        else return false;
+    }
+    return a.solid[(int64_t)j * a.nx + i] != 0;
+}
+
+// The pull of pull_edge_2d for a fluid cell next to obstacles.
+template <typename T>
+__device__ __forceinline__ void pull_obstacle_2d(const StepArgs<T>& a, int i, int j, T f[4][4])
+{
+    const int SX[4] = {-1, 1, 1, -1};
+    const int SY[4] = {-1, -1, 1, 1};
+    bool wall_top = false, wall_bottom = false;
+    bool unknown[4] = {false, false, false, false};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        int si = i - SX[q], sj = j - SY[q];
+        const int side_y = sj < 0 ? 2 : (sj >= a.ny ? 3 : -1);
+        const int side_x = si < 0 ? 0 : (si >= a.nx ? 1 : -1);
+        const int kind_y = side_y == 2 ? a.bc[2] : a.bc[3];
+        const int kind_x = side_x == 0 ? a.bc[0] : a.bc[1];
+        if (side_y >= 0 && kind_y == BC_WALL) {
+            if (side_y == 3) wall_top = true; else wall_bottom = true;
+            continue;
+        }
+        const T* g = nullptr;
+        if (side_x >= 0) {
+            if (kind_x == BC_DIRICHLET) g = a.ghost + side_x * GHOST_STRIDE + q * 4;
+            else if (kind_x == BC_PERIODIC) si = si < 0 ? si + a.nx : si - a.nx;
+            else si = si < 0 ? 0 : a.nx - 1;
+        }
+        if (!g && side_y >= 0) {
+            if (kind_y == BC_DIRICHLET) g = a.ghost + side_y * GHOST_STRIDE + q * 4;
+            else if (kind_y == BC_PERIODIC) sj = sj < 0 ? sj + a.ny : sj - a.ny;
+            else sj = sj < 0 ? 0 : a.ny - 1;
+        }
+        const int64_t s = (int64_t)sj * a.nx + si;
+        if (!g && a.solid[s]) {
+            unknown[q] = true;
+            continue;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) f[q][k] = g ? g[k] : a.src[(q * 4 + k) * a.N + s];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (!unknown[q]) continue;
+        const bool xn = solid_at(a, i - SX[q], j), yn = solid_at(a, i, j - SY[q]);
+        const bool flip_x = !(yn && !xn), flip_y = !(xn && !yn);   // x wall: flip x only; y wall: y only
+        const int mx = flip_x ? -SX[q] : SX[q], my = flip_y ? -SY[q] : SY[q];
+        const int m = my < 0 ? (mx < 0 ? 0 : 1) : (mx > 0 ? 2 : 3);
+        const T su = flip_x ? T(-1) : T(1), sv = flip_y ? T(-1) : T(1);
+#pragma unroll
+        for (int mm = 0; mm < 4; ++mm) {
+            if (mm != m) continue;
+            f[q][0] = f[mm][0];
+            f[q][1] = su * f[mm][1];
+            f[q][2] = sv * f[mm][2];
+            f[q][3] = f[mm][3];
+        }
+    }
+    // domain walls: top f1 = f4, f2 = f3; bottom f4 = f1, f3 = f2; rho v negated
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const T sgn = k == 2 ? T(-1) : T(1);
+        if (wall_top) {
+            f[0][k] = sgn * f[3][k];
+            f[1][k] = sgn * f[2][k];
+        }
+        if (wall_bottom) {
+            f[3][k] = sgn * f[0][k];
+            f[2][k] = sgn * f[1][k];
+        }
+    }
+}
+
 // Collision of one cell (Eq. 9 with the equilibria of Eq. 12): moments U of the
 // pulled populations f, then out = (1 - omega) f + omega f^eq(U).
 // In FP32 at omega = 1 (a block-uniform branch) the result is f^eq itself, which
@@ -275,6 +380,48 @@ __global__ void __launch_bounds__(256) step2d_kernel(const StepArgs<T> a)
     } else {
         pull_edge_2d<T>(a, i, j, f);
     }
+    collide_store_2d<T, STORE_U>(a, c, f);
+}
+
+// The D2Q4 step on a grid with internal walls: solid cells carried unchanged,
+// fluid cells pulled through pull_obstacle_2d (which also resolves the domain
+// sides), then the same collision.
+template <typename T, bool STORE_U = false>
+__global__ void __launch_bounds__(256) step2d_obstacle_kernel(const StepArgs<T> a)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= a.nx || j >= a.ny) return;
+    const int64_t c = (int64_t)j * a.nx + i;
+    if (a.solid[c]) {
+        T f[4][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                f[q][k] = a.src[(q * 4 + k) * a.N + c];
+                a.dst[(q * 4 + k) * a.N + c] = f[q][k];
+            }
+        if constexpr (STORE_U) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) a.Uout[k * a.N + c] = ((f[0][k] + f[1][k]) + f[2][k]) + f[3][k];
+        }
+        return;
+    }
+    T f[4][4];
+    if (i > 0 && i < a.nx - 1 && j > 0 && j < a.ny - 1) {
+        // away from the domain sides and from solid sources: the plain interior pull
+        const int64_t s[4] = {c + a.nx + 1, c + a.nx - 1, c - a.nx - 1, c - a.nx + 1};
+        if (!(a.solid[s[0]] | a.solid[s[1]] | a.solid[s[2]] | a.solid[s[3]])) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) f[q][k] = a.src[(q * 4 + k) * a.N + s[q]];
+            collide_store_2d<T, STORE_U>(a, c, f);
+            return;
+        }
+    }
+    pull_obstacle_2d<T>(a, i, j, f);
     collide_store_2d<T, STORE_U>(a, c, f);
 }
 

@@ -643,7 +643,11 @@ int step2d_f32_variant()
 
 cudaError_t launch_step_f32(int lattice, const StepArgs<float>& a, cudaStream_t s)
 {
-    if (lattice == LAT_D2Q4) {
+    if (lattice == LAT_D2Q4 && a.solid) {
+        const dim3 block(128, 2);
+        const dim3 grid((unsigned)((a.nx + block.x - 1) / block.x), (unsigned)((a.ny + block.y - 1) / block.y));
+        step2d_obstacle_kernel<float><<<grid, block, 0, s>>>(a);
+    } else if (lattice == LAT_D2Q4) {
         const int var = step2d_f32_variant();
         if ((var == 2 || var == 4) && a.nx % var == 0 && a.ny <= 65535) {
             const unsigned per_block = 128u * var;
@@ -758,7 +762,8 @@ cudaError_t launch_step_record_f32(const StepArgs<float>& a, cudaStream_t s)
 {
     const dim3 block(128, 2);
     const dim3 grid((unsigned)((a.nx + block.x - 1) / block.x), (unsigned)((a.ny + block.y - 1) / block.y));
-    step2d_kernel<float, true><<<grid, block, 0, s>>>(a);
+    if (a.solid) step2d_obstacle_kernel<float, true><<<grid, block, 0, s>>>(a);
+    else step2d_kernel<float, true><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -404,7 +404,8 @@ static dim3 grid2d(int nx, int ny, dim3 block)
 cudaError_t launch_step_record_f64(const StepArgs<double>& a, cudaStream_t s)
 {
     const dim3 block(128, 2);
-    step2d_kernel<double, true><<<grid2d(a.nx, a.ny, block), block, 0, s>>>(a);
+    if (a.solid) step2d_obstacle_kernel<double, true><<<grid2d(a.nx, a.ny, block), block, 0, s>>>(a);
+    else step2d_kernel<double, true><<<grid2d(a.nx, a.ny, block), block, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -459,7 +460,8 @@ cudaError_t launch_step_f64(int lattice, const StepArgs<double>& a, cudaStream_t
         const dim3 block(128, 2);
         unsigned gy = (unsigned)((a.ny + block.y - 1) / block.y);
         const dim3 grid((unsigned)((a.nx + block.x - 1) / block.x), gy);
-        step2d_kernel<double><<<grid, block, 0, s>>>(a);
+        if (a.solid) step2d_obstacle_kernel<double><<<grid, block, 0, s>>>(a);
+        else step2d_kernel<double><<<grid, block, 0, s>>>(a);
     } else if (lattice == LAT_D1Q3) {
         step1d_q3_kernel<double><<<(unsigned)((a.nx + 255) / 256), 256, 0, s>>>(a);
     } else {

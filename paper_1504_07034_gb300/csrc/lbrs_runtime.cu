@@ -11,6 +11,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <vector>
+
 #include <cuda_runtime.h>
 
 #include "lbrs.h"
@@ -84,6 +86,7 @@ struct lbrs_ctx {
     cudaStream_t cap_stream;
     cudaGraphExec_t graph[2];
     TileMap tmap[2];         // tensor maps of the two state buffers (FP32 D2Q4 two-step kernel)
+    const uint8_t* solid;    // caller-owned obstacle mask [ny][nx] (lbrs_set_obstacles), or NULL
     // checkpointed adjoint: the run recorded by lbrs_forward_checkpointed
     char* adj_ws;
     size_t adj_bytes;
@@ -179,6 +182,7 @@ StepArgs<T> step_args(const lbrs_ctx* ctx, int from)
     a.c = (T)ctx->c;
     a.gm1 = (T)(ctx->cfg.gamma - 1.0);
     a.Uout = nullptr;
+    a.solid = ctx->solid;
     return a;
 }
 
@@ -207,7 +211,8 @@ cudaError_t launch_one_step(lbrs_ctx* ctx, int from, cudaStream_t s)
 // Two-steps-per-launch kernel available for this context?
 bool fused2(const lbrs_ctx* ctx)
 {
-    return !ctx->f64 && !ctx->f16 && !ctx->f32u && ctx->lattice == LBRS_D2Q4 && step2_f32_enabled();
+    return !ctx->f64 && !ctx->f16 && !ctx->f32u && ctx->lattice == LBRS_D2Q4 && !ctx->solid &&
+           step2_f32_enabled();
 }
 
 unsigned* wait_flag(const lbrs_ctx* ctx) { return (unsigned*)(ctx->ws + ctx->L.wait_flag); }
@@ -296,7 +301,61 @@ lbrs_status adjoint_supported(lbrs_ctx* ctx)
     for (int s = 0; s < 4; ++s)
         if (ctx->cfg.bc[s].kind != LBRS_BC_PERIODIC)
             return fail(ctx, LBRS_EINVAL, "the adjoint covers fully periodic domains only");
+    if (ctx->solid) return fail(ctx, LBRS_EINVAL, "the adjoint does not cover internal walls");
     return LBRS_OK;
+}
+
+// Host check of an obstacle mask: every population of a fluid cell whose pull comes
+// from a solid cell must be replaced by one that is pulled from a fluid cell or a
+// Dirichlet ghost (not itself unknown, not behind a domain wall).  Returns the
+// number of (cell, population) pairs that break this.
+int64_t obstacle_violations(const lbrs_config* c, const uint8_t* m)
+{
+    const int64_t nx = c->nx, ny = c->ny;
+    static const int SX[4] = {-1, 1, 1, -1}, SY[4] = {-1, -1, 1, 1};
+    // solidity of a cell index after the domain mapping; Dirichlet and wall sides are fluid
+    auto solid = [&](int64_t i, int64_t j) -> bool {
+        if (i < 0 || i >= nx) {
+            const int kind = c->bc[i < 0 ? 0 : 1].kind;
+            if (kind == LBRS_BC_PERIODIC) i = i < 0 ? i + nx : i - nx;
+            else if (kind == LBRS_BC_TRANSMISSIVE) i = i < 0 ? 0 : nx - 1;
+            else return false;
+        }
+        if (j < 0 || j >= ny) {
+            const int kind = c->bc[j < 0 ? 2 : 3].kind;
+            if (kind == LBRS_BC_PERIODIC) j = j < 0 ? j + ny : j - ny;
+            else if (kind == LBRS_BC_TRANSMISSIVE) j = j < 0 ? 0 : ny - 1;
+            else return false;
+        }
+        return m[j * nx + i] != 0;
+    };
+    // is population q of cell (i, j) unknown after streaming (wall side or solid source)?
+    auto unknown = [&](int64_t i, int64_t j, int q) -> bool {
+        const int64_t si = i - SX[q], sj = j - SY[q];
+        const bool out_y = sj < 0 || sj >= ny, out_x = si < 0 || si >= nx;
+        if (out_y && c->bc[sj < 0 ? 2 : 3].kind == LBRS_BC_WALL) return true;
+        if (out_x && c->bc[si < 0 ? 0 : 1].kind == LBRS_BC_DIRICHLET) return false;
+        if (out_y && c->bc[sj < 0 ? 2 : 3].kind == LBRS_BC_DIRICHLET) return false;
+        return solid(si, sj);
+    };
+    int64_t bad = 0;
+    for (int64_t j = 0; j < ny; ++j)
+        for (int64_t i = 0; i < nx; ++i) {
+            if (m[j * nx + i]) continue;
+            for (int q = 0; q < 4; ++q) {
+                const int64_t si = i - SX[q], sj = j - SY[q];
+                const bool out_y = sj < 0 || sj >= ny;
+                if (out_y && c->bc[sj < 0 ? 2 : 3].kind == LBRS_BC_WALL) continue;   // a domain wall's population
+                if (!unknown(i, j, q)) continue;
+                const bool xn = solid(i - SX[q], j), yn = solid(i, j - SY[q]);
+                const int mx = (xn && !yn) || xn == yn ? -SX[q] : SX[q];
+                const int my = (!xn && yn) || xn == yn ? -SY[q] : SY[q];
+                int mq = 0;
+                while (SX[mq] != mx || SY[mq] != my) ++mq;
+                if (unknown(i, j, mq)) ++bad;
+            }
+        }
+    return bad;
 }
 
 template <typename T>
@@ -672,6 +731,31 @@ lbrs_status lbrs_get_distributions(lbrs_ctx* ctx, void* dst, int on_device)
     LBRS_CUDA(ctx, cudaMemcpyAsync(dst, ctx->f[ctx->cur], ctx->L.f_bytes,
                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
     if (!on_device) LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return LBRS_OK;
+}
+
+lbrs_status lbrs_set_obstacles(lbrs_ctx* ctx, const uint8_t* d_solid)
+{
+    if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
+    if (d_solid) {
+        if (ctx->lattice != LBRS_D2Q4 || ctx->f16 || ctx->f32u)
+            return fail(ctx, LBRS_EINVAL, "internal walls cover the F64 and F32 D2Q4 forms");
+        std::vector<uint8_t> m((size_t)ctx->N);
+        LBRS_CUDA(ctx, cudaMemcpyAsync(m.data(), d_solid, m.size(), cudaMemcpyDeviceToHost, ctx->stream));
+        LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        const int64_t bad = obstacle_violations(&ctx->cfg, m.data());
+        if (bad)
+            return fail(ctx, LBRS_EINVAL,
+                        "obstacle geometry: %lld populations of fluid cells have no known mirror "
+                        "(fluid channels must be at least two cells wide)", (long long)bad);
+    }
+    // the captured step graphs hold the previous mask
+    for (int b = 0; b < 2; ++b)
+        if (ctx->graph[b]) {
+            cudaGraphExecDestroy(ctx->graph[b]);
+            ctx->graph[b] = nullptr;
+        }
+    ctx->solid = d_solid;
     return LBRS_OK;
 }
 

@@ -2,8 +2,8 @@
 
     python -m paper_1504_07034_gb300.profile_kernels CASE
 
-CASE: step2d_f32 | step2d_f32_flushed | step2d_f16neq | adjoint | batch |
-diagnostics.  Each case
+CASE: step2d_f32 | step2d_f32_flushed | step2d_f16neq | obstacles | adjoint |
+batch | diagnostics.  Each case
 holds at most about 1.5 GB on the device and launches its kernels a handful
 of times after a warm-up, so that a profiler capture (`ncu -k ... -c ...`)
 stays small.  It prints one line per case with the wall time of its kernels.
@@ -59,6 +59,15 @@ def step2d_f16neq():
     return _timed(lambda: [s.step(1) for _ in range(wl.steps)])
 
 
+def obstacles():
+    """The forward-facing step on 3072 x 1024 in FP32 (the obstacle step kernel), 10 steps."""
+    from .solver import Solver
+    wl = workloads.forward_facing_step(nx=3072, ny=1024, steps=10)
+    s = Solver.from_workload(wl, precision="f32")
+    s.set_state(torch.from_numpy(wl.prim).cuda())
+    return _timed(lambda: [s.step(1) for _ in range(wl.steps)])
+
+
 def adjoint():
     from .solver import Solver
     wl, target = workloads.adjoint_pulses(seed=0, n=1024, steps=0)
@@ -91,7 +100,8 @@ def diagnostics():
     return _timed(lambda: [s.diagnostics() for _ in range(3)])
 
 
-CASES = {f.__name__: f for f in (step2d_f32, step2d_f32_flushed, step2d_f16neq, adjoint, batch, diagnostics)}
+CASES = {f.__name__: f for f in (step2d_f32, step2d_f32_flushed, step2d_f16neq, obstacles, adjoint, batch,
+                                 diagnostics)}
 
 
 def main(argv):

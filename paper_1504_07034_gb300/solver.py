@@ -50,6 +50,7 @@ class Solver:
                  omega: float = 1.0, precision: str = "f32", stream: torch.cuda.Stream | None = None,
                  device: torch.device | str | None = None, diag_every: int = 0):
         self.lib = abi.load()
+        self.solid = None
         self.lattice = lattice
         self.Q, self.K = {"d2q4": (4, 4), "d1q2": (2, 3), "d1q3": (3, 3)}[lattice]
         self.nx, self.ny = int(nx), int(ny)
@@ -76,9 +77,12 @@ class Solver:
     def from_workload(cls, wl, precision: str = "f32", stream=None, omega=None, diag_every: int = 0,
                       lattice: str = "d1q2"):
         if hasattr(wl, "ny"):
-            return cls("d2q4", wl.nx, wl.ny, lam=wl.lam, dx=wl.dx, bc=wl.bc, gamma=wl.gamma,
-                       omega=wl.omega if omega is None else omega, precision=precision, stream=stream,
-                       diag_every=diag_every)
+            s = cls("d2q4", wl.nx, wl.ny, lam=wl.lam, dx=wl.dx, bc=wl.bc, gamma=wl.gamma,
+                    omega=wl.omega if omega is None else omega, precision=precision, stream=stream,
+                    diag_every=diag_every)
+            if getattr(wl, "solid", None) is not None:
+                s.set_obstacles(torch.from_numpy(wl.solid))
+            return s
         return cls(lattice, wl.nx, 1, lam=wl.lam, dx=wl.dx, bc=wl.bc, gamma=wl.gamma,
                    omega=wl.omega if omega is None else omega, precision=precision, stream=stream,
                    diag_every=diag_every)
@@ -175,6 +179,20 @@ class Solver:
             raise ValueError("f must be a contiguous (Q, K, *grid) tensor of the storage dtype")
         self._check(self.lib.lbrs_set_distributions(self.ctx, ctypes.c_void_p(f.data_ptr()), 1 if f.is_cuda else 0,
                                                     int(step)))
+
+    def set_obstacles(self, solid):
+        """Internal walls from a (ny, nx) mask (nonzero = solid cell); None removes them.
+        The mask is kept on the device for the solver's lifetime (the library reads it
+        at every step)."""
+        if solid is None:
+            self._check(self.lib.lbrs_set_obstacles(self.ctx, None))
+            self.solid = None
+            return
+        m = torch.as_tensor(solid).to(device=self.device, dtype=torch.uint8).contiguous()
+        if tuple(m.shape) != (self.ny, self.nx):
+            raise ValueError(f"obstacle mask must have shape {(self.ny, self.nx)}")
+        self._check(self.lib.lbrs_set_obstacles(self.ctx, ctypes.c_void_p(m.data_ptr())))
+        self.solid = m
 
     # ------------------------------------------------------------------ adjoint (periodic D2Q4)
     def _fields_tensor(self, n=None):
