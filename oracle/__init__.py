@@ -33,7 +33,7 @@ SRC = HERE / "lbrs_oracle.c"
 LIB = HERE / "_build" / "liblbrs_oracle.so"
 
 BC_KINDS = {"periodic": 0, "transmissive": 1, "dirichlet": 2, "wall": 3}
-D1Q2, D1Q3, D2Q4 = 2, 3, 4
+D1Q2, D1Q3, D2Q4, D2Q4S = 2, 3, 4, 5      # D2Q4S: the scalar 2-D inviscid Burgers law
 
 
 def build(force: bool = False) -> Path:
@@ -69,6 +69,7 @@ class _Params(ctypes.Structure):
         ("bc_kind", ctypes.c_int32 * 4),
         ("bc_prim", (ctypes.c_double * 4) * 4),
         ("solid", ctypes.POINTER(ctypes.c_uint8)),
+        ("dx", ctypes.c_double),
     ]
 
 
@@ -127,11 +128,11 @@ class Oracle:
     """One LBRS problem: lattice, grid, gamma, lambda, omega, boundary conditions."""
 
     def __init__(self, lattice: int, nx: int, ny: int = 1, *, gamma: float = 1.4, lam: float,
-                 omega: float = 1.0, bc=None, nthreads: int = 0, solid=None):
+                 omega: float = 1.0, bc=None, nthreads: int = 0, solid=None, dx: float = 1.0):
         self.lattice = lattice
-        self.Q, self.K = {D2Q4: (4, 4), D1Q3: (3, 3), D1Q2: (2, 3)}[lattice]
+        self.Q, self.K = {D2Q4: (4, 4), D2Q4S: (4, 1), D1Q3: (3, 3), D1Q2: (2, 3)}[lattice]
         self.nx, self.ny = int(nx), int(ny)
-        sides = 4 if lattice == D2Q4 else 2
+        sides = 4 if lattice in (D2Q4, D2Q4S) else 2
         bc = list(bc) if bc is not None else [("periodic", None)] * sides
         if len(bc) != sides:
             raise ValueError(f"need {sides} boundary conditions")
@@ -139,6 +140,7 @@ class Oracle:
         p.lattice, p.nthreads = lattice, nthreads
         p.nx, p.ny = self.nx, self.ny
         p.gamma, p.lam, p.omega = gamma, lam, omega
+        p.dx = dx
         for s, (kind, state) in enumerate(bc):
             p.bc_kind[s] = BC_KINDS[kind]
             if state is not None:
@@ -160,16 +162,17 @@ class Oracle:
     @classmethod
     def from_workload(cls, wl, nthreads: int = 0, omega=None, lattice=None):
         if hasattr(wl, "ny"):
-            return cls(D2Q4, wl.nx, wl.ny, gamma=wl.gamma, lam=wl.lam,
+            law = D2Q4S if getattr(wl, "law", "euler") == "burgers" else D2Q4
+            return cls(lattice or law, wl.nx, wl.ny, gamma=wl.gamma, lam=wl.lam,
                        omega=wl.omega if omega is None else omega, bc=wl.bc, nthreads=nthreads,
-                       solid=getattr(wl, "solid", None))
+                       solid=getattr(wl, "solid", None), dx=wl.dx)
         return cls(lattice or D1Q2, wl.nx, 1, gamma=wl.gamma, lam=wl.lam,
                    omega=wl.omega if omega is None else omega, bc=wl.bc, nthreads=nthreads)
 
     # shapes -------------------------------------------------------------
     @property
     def grid(self):
-        return (self.ny, self.nx) if self.lattice == D2Q4 else (self.nx,)
+        return (self.ny, self.nx) if self.lattice in (D2Q4, D2Q4S) else (self.nx,)
 
     def _fields(self, a) -> np.ndarray:
         a = np.ascontiguousarray(a, dtype=np.float64)

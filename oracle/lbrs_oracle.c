@@ -54,16 +54,17 @@
 #include <omp.h>
 
 enum { ORC_PERIODIC = 0, ORC_TRANSMISSIVE = 1, ORC_DIRICHLET = 2, ORC_WALL = 3 };
-enum { ORC_D1Q2 = 2, ORC_D1Q3 = 3, ORC_D2Q4 = 4 };
+enum { ORC_D1Q2 = 2, ORC_D1Q3 = 3, ORC_D2Q4 = 4, ORC_D2Q4S = 5 };
 
 typedef struct {
-    int32_t lattice;      /* ORC_D1Q2, ORC_D1Q3 or ORC_D2Q4 */
+    int32_t lattice;      /* ORC_D1Q2, ORC_D1Q3, ORC_D2Q4 or ORC_D2Q4S (scalar Burgers) */
     int32_t nthreads;     /* OpenMP threads, 0 = library default */
     int64_t nx, ny;       /* ny = 1 for D1Q2 */
     double gamma, lambda, omega;
     int32_t bc_kind[4];   /* x-lo, x-hi, y-lo, y-hi */
     double bc_prim[4][4]; /* Dirichlet primitive state per side: (rho,u,p) in 1-D, (rho,u,v,p) in 2-D */
     const uint8_t* solid; /* D2Q4 only, nullable: [ny][nx], nonzero = solid (internal wall) cell */
+    double dx;            /* lattice spacing (the scalar lattice's boundary profiles) */
 } orc_params;
 
 typedef struct {
@@ -80,8 +81,9 @@ static const int SX1[2] = {-1, +1};
 static const int SX13[3] = {-1, 0, +1};
 
 static int threads_of(const orc_params* P) { return P->nthreads > 0 ? P->nthreads : omp_get_max_threads(); }
-static int nq(const orc_params* P) { return P->lattice == ORC_D2Q4 ? 4 : (P->lattice == ORC_D1Q3 ? 3 : 2); }
-static int nk(const orc_params* P) { return P->lattice == ORC_D2Q4 ? 4 : 3; }
+static int two_d(const orc_params* P) { return P->lattice == ORC_D2Q4 || P->lattice == ORC_D2Q4S; }
+static int nq(const orc_params* P) { return two_d(P) ? 4 : (P->lattice == ORC_D1Q3 ? 3 : 2); }
+static int nk(const orc_params* P) { return P->lattice == ORC_D2Q4 ? 4 : (P->lattice == ORC_D2Q4S ? 1 : 3); }
 
 /* ---------------------------------------------------------------- state */
 
@@ -89,6 +91,10 @@ static int nk(const orc_params* P) { return P->lattice == ORC_D2Q4 ? 4 : 3; }
 static void prim_to_cons_cell(const orc_params* P, const double* w, double* U)
 {
     double g = P->gamma;
+    if (P->lattice == ORC_D2Q4S) {
+        U[0] = w[0];                 /* the scalar is its own conserved variable */
+        return;
+    }
     if (P->lattice == ORC_D2Q4) {
         double rho = w[0], u = w[1], v = w[2], p = w[3];
         U[0] = rho;
@@ -119,6 +125,22 @@ static double pressure(const orc_params* P, const double* U)
 static void feq_cell(const orc_params* P, const double* U, double* feq)
 {
     double g = P->gamma;
+    if (P->lattice == ORC_D2Q4S) {
+        /* scalar law u_t + g1(u)_x + g2(u)_y = 0 with the inviscid Burgers fluxes of
+         * Section III, g1 = u^2/2, g2 = u; f^eq_q = u/4 + sx g1/(4 lambda) + sy g2/(4 lambda)
+         * (Section II.D) */
+        double u = U[0];
+        double g1 = 0.5 * u * u, g2 = u;
+        double c = 1.0 / (4.0 * P->lambda);
+        for (int q = 0; q < 4; ++q) {
+            double a = 0.25 * u;
+            double b = c * g1;
+            double d = c * g2;
+            double t = SX2[q] < 0 ? a - b : a + b;
+            feq[q] = SY2[q] < 0 ? t - d : t + d;
+        }
+        return;
+    }
     if (P->lattice == ORC_D2Q4) {
         /* 2-D Euler fluxes: F = (rho u, rho u^2 + p, rho u v, u(rho E + p)),
          *                   G = (rho v, rho v u, rho v^2 + p, v(rho E + p)). */
@@ -172,6 +194,8 @@ static void feq_cell(const orc_params* P, const double* U, double* feq)
  * wave of speed c only if c^2 < (2/3) lambda^2, hence the bound sqrt(3/2)(|u| + a). */
 static double lambda_local(const orc_params* P, const double* U, double p)
 {
+    /* scalar D2Q4: f^eq_q is non-decreasing in u for every q iff lambda >= |g1'| + |g2'| = |u| + 1 */
+    if (P->lattice == ORC_D2Q4S) return fabs(U[0]) + 1.0;
     double a = sqrt(P->gamma * p / U[0]);
     if (P->lattice == ORC_D2Q4) {
         double u = U[1] / U[0], v = U[2] / U[0];
@@ -205,6 +229,7 @@ void orc_cons_to_prim(const orc_params* P, const double* U, double* W)
         double u[4];
         for (int k = 0; k < K; ++k) u[k] = U[k * N + c];
         W[0 * N + c] = u[0];
+        if (K == 1) continue;
         W[1 * N + c] = u[1] / u[0];
         if (K == 4) W[2 * N + c] = u[2] / u[0];
         W[(K - 1) * N + c] = pressure(P, u);
@@ -245,20 +270,23 @@ void orc_moments(const orc_params* P, const double* fs, double* U)
 
 int orc_validate(const orc_params* P)
 {
-    if (P->lattice != ORC_D1Q2 && P->lattice != ORC_D1Q3 && P->lattice != ORC_D2Q4) return 1;
+    if (P->lattice != ORC_D1Q2 && P->lattice != ORC_D1Q3 && P->lattice != ORC_D2Q4 && P->lattice != ORC_D2Q4S)
+        return 1;
     if (P->nx < 1 || P->ny < 1) return 2;
-    if (P->lattice != ORC_D2Q4 && P->ny != 1) return 3;
+    if (!two_d(P) && P->ny != 1) return 3;
     if (!(P->lambda > 0.0) || !(P->omega > 0.0 && P->omega < 2.0) || !(P->gamma > 1.0)) return 4;
-    int sides = P->lattice == ORC_D2Q4 ? 4 : 2;
+    int sides = two_d(P) ? 4 : 2;
     for (int s = 0; s < sides; ++s) {
         int kind = P->bc_kind[s];
         if (kind < ORC_PERIODIC || kind > ORC_WALL) return 5;
+        if (kind == ORC_WALL && P->lattice == ORC_D2Q4S) return 11;   /* no wall rule for a scalar */
         if (kind == ORC_WALL && s < 2) return 6;              /* walls on the y sides only */
         if (kind == ORC_PERIODIC && P->bc_kind[s ^ 1] != ORC_PERIODIC) return 7;
     }
     if (P->lattice == ORC_D2Q4 && (P->bc_kind[2] == ORC_WALL || P->bc_kind[3] == ORC_WALL) && P->ny < 2)
         return 8;
     if (P->solid && P->lattice != ORC_D2Q4) return 9;
+    if (P->lattice == ORC_D2Q4S && !(P->dx > 0.0)) return 12;
     return 0;
 }
 
@@ -358,12 +386,22 @@ int64_t orc_obstacle_check(const orc_params* P)
 /* Ghost distributions of each Dirichlet side: f^eq of the boundary state. */
 static void ghost_tables(const orc_params* P, double ghost[4][16])
 {
-    int sides = P->lattice == ORC_D2Q4 ? 4 : 2;
+    int sides = P->lattice == ORC_D2Q4 ? 4 : (P->lattice == ORC_D2Q4S ? 0 : 2);
     for (int s = 0; s < sides; ++s) {
         double U[4];
         prim_to_cons_cell(P, P->bc_prim[s], U);
         feq_cell(P, U, ghost[s]);
     }
+}
+
+/* Scalar lattice: a Dirichlet side holds the linear profile u_b = prim[0] + prim[1] s,
+ * s the centre coordinate (m + 1/2) dx of the ghost cell along that side (m may lie
+ * outside the side at a corner: the profile is extended); the ghost is f^eq(u_b). */
+static const double* profile_ghost(const orc_params* P, int side, int64_t m, double* buf)
+{
+    double ub = P->bc_prim[side][0] + P->bc_prim[side][1] * (((double)m + 0.5) * P->dx);
+    feq_cell(P, &ub, buf);
+    return buf;
 }
 
 /*
@@ -380,7 +418,7 @@ int orc_stream(const orc_params* P, const double* fs, double* f)
     const int Q = nq(P), K = nk(P);
     double ghost[4][16];
     ghost_tables(P, ghost);
-    const int two_d = P->lattice == ORC_D2Q4;
+    const int is2d = two_d(P), scalar = P->lattice == ORC_D2Q4S;
 
 #pragma omp parallel for schedule(static) num_threads(threads_of(P))
     for (int64_t j = 0; j < ny; ++j) {
@@ -394,8 +432,9 @@ int orc_stream(const orc_params* P, const double* fs, double* f)
             int wall_pop[4] = {0, 0, 0, 0};
             int solid_pop[4] = {0, 0, 0, 0};
             for (int q = 0; q < Q; ++q) {
-                int sx = two_d ? SX2[q] : (Q == 3 ? SX13[q] : SX1[q]);
-                int sy = two_d ? SY2[q] : 0;
+                int sx = is2d ? SX2[q] : (Q == 3 ? SX13[q] : SX1[q]);
+                int sy = is2d ? SY2[q] : 0;
+                double gbuf[4];
                 int64_t si = i - sx, sj = j - sy;
                 int side_y = sj < 0 ? 2 : (sj >= ny ? 3 : -1);
                 int side_x = si < 0 ? 0 : (si >= nx ? 1 : -1);
@@ -406,13 +445,13 @@ int orc_stream(const orc_params* P, const double* fs, double* f)
                 }
                 if (side_x >= 0) {
                     int kind = P->bc_kind[side_x];
-                    if (kind == ORC_DIRICHLET) g = ghost[side_x];
+                    if (kind == ORC_DIRICHLET) g = scalar ? profile_ghost(P, side_x, sj, gbuf) : ghost[side_x];
                     else if (kind == ORC_PERIODIC) si = (si + nx) % nx;
                     else si = si < 0 ? 0 : nx - 1;              /* transmissive */
                 }
                 if (!g && side_y >= 0) {
                     int kind = P->bc_kind[side_y];
-                    if (kind == ORC_DIRICHLET) g = ghost[side_y];
+                    if (kind == ORC_DIRICHLET) g = scalar ? profile_ghost(P, side_y, si, gbuf) : ghost[side_y];
                     else if (kind == ORC_PERIODIC) sj = (sj + ny) % ny;
                     else sj = sj < 0 ? 0 : ny - 1;              /* transmissive */
                 }
@@ -485,10 +524,11 @@ void orc_collide(const orc_params* P, const double* f, double* fs, double* U, or
                 int64_t idx = (q * K + k) * N + c;
                 fs[idx] = inert ? f[idx] : om1 * f[idx] + om * feq[q * K + k];
             }
-        double p = pressure(P, u);
+        const int scalar = P->lattice == ORC_D2Q4S;          /* a scalar has no density or pressure */
+        double p = scalar ? 1.0 : pressure(P, u);
         int finite = 1;
         for (int k = 0; k < K; ++k) finite &= isfinite(u[k]);
-        if (!finite || !(u[0] > 0.0) || !(p > 0.0)) {
+        if (!finite || (!scalar && (!(u[0] > 0.0) || !(p > 0.0)))) {
             ++bad;
         } else {
             double l = lambda_local(P, u, p);

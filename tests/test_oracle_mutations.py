@@ -31,8 +31,8 @@ MUTANTS = {
                                  "double G[3] = {m, m * u, u * (en + p)};"),
     "gamma_in_place_of_gamma_minus_1": ("return (g - 1.0) * (U[3] - 0.5 * (U[1] * u + U[2] * v));",
                                         "return g * (U[3] - 0.5 * (U[1] * u + U[2] * v));"),
-    "ghost_uses_wrong_side": ("if (kind == ORC_DIRICHLET) g = ghost[side_x];",
-                              "if (kind == ORC_DIRICHLET) g = ghost[side_x ^ 1];"),
+    "ghost_uses_wrong_side": ("profile_ghost(P, side_x, sj, gbuf) : ghost[side_x];",
+                              "profile_ghost(P, side_x, sj, gbuf) : ghost[side_x ^ 1];"),
     # D1Q3
     "d1q3_rest_fraction_quarter": ("double a = U[k] / 3.0;", "double a = U[k] / 4.0;"),
     "d1q3_rest_particle_moves": ("static const int SX13[3] = {-1, 0, +1};", "static const int SX13[3] = {-1, +1, +1};"),
@@ -52,6 +52,11 @@ MUTANTS = {
                                       "    } else {\n        my = -sy;\n    }"),
     "obstacle_solid_cells_relax": ("fs[idx] = inert ? f[idx] : om1 * f[idx] + om * feq[q * K + k];",
                                    "fs[idx] = om1 * f[idx] + om * feq[q * K + k];"),
+    # scalar D2Q4 (2-D Burgers)
+    "burgers_flux_drops_half": ("double g1 = 0.5 * u * u, g2 = u;", "double g1 = u * u, g2 = u;"),
+    "burgers_drops_y_flux": ("double g1 = 0.5 * u * u, g2 = u;", "double g1 = 0.5 * u * u, g2 = 0.0 * u;"),
+    "profile_at_cell_edge": ("(((double)m + 0.5) * P->dx)", "(((double)m) * P->dx)"),
+    "profile_ghost_wrong_side": ("profile_ghost(P, side_x, sj, gbuf)", "profile_ghost(P, side_x ^ 1, sj, gbuf)"),
     "adjoint_relaxation_weights_swapped": ("gout[(q * 4 + k) * N + tj * nx + ti] = om1 * gq[q * 4 + k] + om * ubar[k];",
                                            "gout[(q * 4 + k) * N + tj * nx + ti] = om * gq[q * 4 + k] + om1 * ubar[k];"),
 }
@@ -72,6 +77,7 @@ def test_pins_catch_mutant(name, tmp_path):
                         os.path.join(ROOT, "tests", "test_oracle_pins.py"),
                         os.path.join(ROOT, "tests", "test_oracle_pins_d1q3.py"),
                         os.path.join(ROOT, "tests", "test_oracle_adjoint.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_obstacles.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_obstacles.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_burgers.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"pins did not catch mutant {name}:\n{r.stdout[-2000:]}"

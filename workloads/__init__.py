@@ -13,6 +13,8 @@ from .generators import (  # noqa: F401
     TubeBatch,
     adjoint_pulses,
     batched_tubes,
+    burgers_2d,
+    burgers_steady_exact,
     bouchut_speed,
     explosion,
     forward_facing_step,

@@ -66,6 +66,7 @@ class Workload2D:
     gamma: float = GAMMA
     meta: dict = field(default_factory=dict)
     solid: np.ndarray | None = None   # (ny, nx) uint8, 1 = solid cell of an internal wall
+    law: str = "euler"                 # "euler" (4 fields) or "burgers" (the scalar law, 1 field)
 
     @property
     def cells(self) -> int:
@@ -461,3 +462,56 @@ def shock_diffraction(n: int = 400, omega: float = 1.0, t_final: float = 0.1561,
     bc = [("dirichlet", post), ("transmissive", None), ("wall", None), ("transmissive", None)]
     return Workload2D("shock_diffraction", n, n, dx, 0.0, 0.0, prim, bc, lam, omega, int(steps),
                       meta={"corner": corner, "mach": mach, "post": post, "t_final": t_final}, solid=solid)
+
+
+# ---------------------------------------------------------------- scalar 2-D Burgers
+
+BURGERS_CASES = {
+    # (u at x = 0, u at x = 1, bottom profile u(x, 0) = b0 + b1 x)        (Section III)
+    1: (1.0, -1.0, (1.0, -2.0)),
+    2: (1.5, -0.5, (1.5, -2.0)),
+}
+
+
+def burgers_2d(case: int = 1, n: int = 64, omega: float = 1.0, t_final: float = 3.0, steps: int | None = None,
+               safety: float = 1.1) -> Workload2D:
+    """The 2-D inviscid Burgers problems of Section III on [0, 1]^2, u_t + (u^2/2)_x + u_y = 0.
+
+    Dirichlet u = left / right values on x = 0, 1 and the linear profile on y = 0; the top
+    is an outflow (transmissive; the y-speed g2' = 1 carries everything out).  The interior
+    starts at the bottom profile extended in y.  lambda = safety * max(|u| + 1) over the
+    boundary data (the scalar D2Q4 bound |g1'| + |g2'|), rounded so that t_final is a whole
+    number of steps.  The steady state is reached after a few crossing times (t = 3).
+    """
+    left, right, (b0, b1) = BURGERS_CASES[case]
+    dx = 1.0 / n
+    x = _cell_centres(n, 0.0, dx)[None, :]
+    prim = np.broadcast_to(b0 + b1 * x, (n, n))[None].copy()
+    umax = max(abs(left), abs(right), abs(b0), abs(b0 + b1))
+    lam = safety * (umax + 1.0)
+    if steps is None:
+        lam, steps = _round_lambda(lam, dx, t_final)
+    bc = [("dirichlet", (left, 0.0, 0.0, 0.0)), ("dirichlet", (right, 0.0, 0.0, 0.0)),
+          ("dirichlet", (b0, b1, 0.0, 0.0)), ("transmissive", None)]
+    return Workload2D(f"burgers_case{case}", n, n, dx, 0.0, 0.0, prim, bc, lam, omega, int(steps),
+                      meta={"case": case, "t_final": t_final}, law="burgers")
+
+
+def burgers_steady_exact(case: int, x, y):
+    """Exact steady solution of the Section III Burgers problems (characteristics dx/dy = u).
+
+    Below y = 1/2 the bottom characteristics fan in towards the focus: u = (b0 + b1 x) along
+    x = x0 + u y gives u = (b0 + b1 x) / (1 + b1 y) between the lines carrying the left and
+    right boundary values; above it a shock moves with slope (u_l + u_r) / 2 from the focus.
+    """
+    left, right, (b0, b1) = BURGERS_CASES[case]
+    x, y = np.broadcast_arrays(np.asarray(x, float), np.asarray(y, float))
+    below = y < 0.5
+    fan = (b0 + b1 * x) / (1.0 + b1 * y)
+    xl = left * y                          # the characteristic from (0, 0) carrying u = left
+    xr = 1.0 + right * y                   # the one from (1, 0) carrying u = right
+    u_below = np.where(x <= xl, left, np.where(x >= xr, right, fan))
+    xf = left * 0.5                        # the focus (the fan's lines all meet at y = 1/2)
+    xs = xf + 0.5 * (left + right) * (y - 0.5)
+    u_above = np.where(x < xs, left, right)
+    return np.where(below, u_below, u_above)
