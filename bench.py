@@ -323,6 +323,50 @@ def obstacle_measurement(Solver, stream, barrier, peak):
     return out
 
 
+def burgers_measurement(Solver, stream, barrier, peak):
+    """The scalar D2Q4 lattice on the 2-D inviscid Burgers problems of Section III: density-free
+    L1 distance of the FP64 and FP32 steady states (t = 3) to the exact steady solutions on the
+    paper's 64 x 64 grid, and steady FP32 stepping of case 1 on 8192 x 8192 (537 MB of state,
+    larger than L2) for MLUPS and the roofline (4 x 4 B read + written per update)."""
+    import torch
+    out = {}
+    n = 64
+    x = (np.arange(n) + 0.5) / n
+    X, Y = np.meshgrid(x, x)
+    for case in (1, 2):
+        wl = workloads.burgers_2d(case, n)
+        exact = workloads.burgers_steady_exact(case, X, Y)
+        res = {"steps": wl.steps, "lambda": wl.lam}
+        for precision in ("f64", "f32"):
+            s = Solver.from_workload(wl, precision=precision, stream=stream)
+            with torch.cuda.stream(stream):
+                s.set_state(torch.from_numpy(wl.prim).cuda())
+                s.step(wl.steps)
+                u = s.moments(torch.float64)[0].cpu().numpy()
+            s.close()
+            res[f"l1_vs_exact_steady_{precision}"] = float(np.mean(np.abs(u - exact)))
+        out[f"case{case}_64x64_t3"] = res
+    big = workloads.burgers_2d(1, 8192, steps=200)
+    s = Solver.from_workload(big, precision="f32", stream=stream)
+    with torch.cuda.stream(stream):
+        s.set_state(torch.from_numpy(big.prim).cuda())
+        s.step(64)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        a.record(stream)
+        s.step(big.steps)
+        b.record(stream)
+        barrier()
+    s.close()
+    t = a.elapsed_time(b) / 1e3
+    mlups = big.cells * big.steps / t / 1e6
+    bpl = 32
+    out["steady_8192x8192_f32"] = {"value": mlups, "unit": UNIT, "kernel": "step2ds_kernel<float>",
+                                   "algorithmic_bytes_per_lup": bpl, "achieved_gbs": bpl * mlups / 1e3,
+                                   "frac": bpl * mlups / 1e3 / peak}
+    return out
+
+
 def batch_measurement(stream, barrier):
     """4096 shock tubes, N log-uniform in [200, 20000], to t = 0.15 in FP32 (temporal blocking)."""
     import torch
@@ -555,6 +599,9 @@ def run_ours(args):
     # --- internal walls: forward-facing step and shock diffraction ------------------
     obstacles = obstacle_measurement(Solver, stream, barrier, peak)
 
+    # --- scalar D2Q4: the 2-D Burgers problems -------------------------------------
+    burgers = burgers_measurement(Solver, stream, barrier, peak)
+
     # --- batched 1-D tubes ---------------------------------------------------------
     batched = batch_measurement(stream, barrier)
 
@@ -597,6 +644,7 @@ def run_ours(args):
             "adjoint": adjoint,
             "sod_1d": sod,
             "internal_walls": obstacles,
+            "burgers_2d": burgers,
             "batched_tubes": batched,
             "fp64": {"value": mlups64, "unit": UNIT, "achieved_gbs": BYTES_PER_LUP_F64 * mlups64 / 1e3,
                      "diag_after_1000_steps": {k: d64[k] for k in ("status", "min_rho", "min_p", "max_lambda_local")}},

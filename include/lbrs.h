@@ -71,7 +71,16 @@ typedef enum {
  * diffusion dt (1/omega - 1/2)(2 lambda^2/3 - c^2) stays positive only for
  * wave speeds c below sqrt(2/3) lambda: the diagnostics' local bound for D1Q3 is
  * sqrt(3/2)(|u| + a). */
-typedef enum { LBRS_D1Q2 = 0, LBRS_D2Q4 = 1, LBRS_D1Q3 = 2 } lbrs_lattice;
+/* LBRS_D2Q4S is the D2Q4 lattice for one scalar conserved variable u with the
+ * fluxes of the 2-D inviscid Burgers law of Section III, g1 = u^2/2, g2 = u:
+ * f^eq_q = u/4 + sx_q g1/(4 lambda) + sy_q g2/(4 lambda) (Section II.D).  Fields
+ * are [1][ny][nx]; LBRS_F64 or LBRS_F32 only; no walls, obstacles or adjoint.  A
+ * Dirichlet side holds the linear profile u_b = prim[0] + prim[1] s, s = (m + 1/2) dx
+ * the centre coordinate of the ghost cell along that side (m its index, extended
+ * past the side's ends at corners).  The diagnostics report min u as min_rho, 1 as
+ * min_p, and the local bound |u| + 1 (f^eq_q non-decreasing in u for every q iff
+ * lambda >= |g1'| + |g2'|); only non-finite values count as non-physical. */
+typedef enum { LBRS_D1Q2 = 0, LBRS_D2Q4 = 1, LBRS_D1Q3 = 2, LBRS_D2Q4S = 3 } lbrs_lattice;
 
 /* Storage and arithmetic precision of the distributions.
  *   LBRS_F64     FP64 storage and arithmetic (the parity path);

@@ -16,7 +16,7 @@ LIB_PATH = PKG / "liblbrs.so"
 
 # enums (include/lbrs.h)
 LBRS_OK, LBRS_EINVAL, LBRS_ENOMEM, LBRS_ECUDA, LBRS_ENONPHYS, LBRS_ESUBCHAR, LBRS_ETIMEOUT, LBRS_ESTATE = range(8)
-LBRS_D1Q2, LBRS_D2Q4, LBRS_D1Q3 = 0, 1, 2
+LBRS_D1Q2, LBRS_D2Q4, LBRS_D1Q3, LBRS_D2Q4S = 0, 1, 2, 3
 LBRS_F64, LBRS_F32, LBRS_F16NEQ, LBRS_F32U = 0, 1, 2, 3
 LBRS_BC_PERIODIC, LBRS_BC_TRANSMISSIVE, LBRS_BC_DIRICHLET, LBRS_BC_WALL = 0, 1, 2, 3
 LBRS_CONSERVED, LBRS_PRIMITIVE = 0, 1

@@ -33,7 +33,7 @@ enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_DIRICHLET = 2, BC_WALL = 3 };
 // LAT_U2D: a D2Q4 state stored as its moments U directly (the FP16
 // non-equilibrium form keeps U in FP32): read-outs treat it as one
 // "population" per field.
-enum { LAT_D1Q2 = 0, LAT_D2Q4 = 1, LAT_U2D = 2, LAT_D1Q3 = 3 };
+enum { LAT_D1Q2 = 0, LAT_D2Q4 = 1, LAT_U2D = 2, LAT_D1Q3 = 3, LAT_D2Q4S = 4 };
 enum { KIND_CONSERVED = 0, KIND_PRIMITIVE = 1 };
 
 // Ghost-table stride: one Dirichlet side holds Q*K <= 16 values.
@@ -105,6 +105,28 @@ __device__ __forceinline__ void equilibria2d(const T U[4], T gm1, T c, T e[4][4]
         e[2][k] = (a + b) + d;
         e[3][k] = (a - b) + d;
     }
+}
+
+// Scalar D2Q4 equilibria for the 2-D inviscid Burgers law of Section III,
+// g1 = u^2/2, g2 = u: f^eq_q = u/4 + sx_q c g1 + sy_q c g2, c = 1/(4 lambda) (Section II.D).
+template <typename T>
+__device__ __forceinline__ void equilibria2ds(T u, T c, T e[4])
+{
+    const T g1 = T(0.5) * u * u, g2 = u;
+    const T a = T(0.25) * u, b = c * g1, d = c * g2;
+    e[0] = (a - b) - d;
+    e[1] = (a + b) - d;
+    e[2] = (a + b) + d;
+    e[3] = (a - b) + d;
+}
+
+// Scalar lattice Dirichlet side: the linear profile u0 + slope * s at the centre
+// coordinate s = (m + 1/2) dx of the ghost cell along the side; the ghost table of
+// the side holds (u0, slope, dx).
+template <typename T>
+__device__ __forceinline__ T profile_value(const T* g, int m)
+{
+    return g[0] + g[1] * ((T(m) + T(0.5)) * g[2]);
 }
 
 // D1Q2 equilibria (Section II.C): G = (rho u, rho u^2 + p, u (rho E + p)),
@@ -423,6 +445,74 @@ __global__ void __launch_bounds__(256) step2d_obstacle_kernel(const StepArgs<T> 
     }
     pull_obstacle_2d<T>(a, i, j, f);
     collide_store_2d<T, STORE_U>(a, c, f);
+}
+
+// ---------------------------------------------------------------- scalar D2Q4 step
+//
+// One thread per cell: pull the four populations (periodic wrap, transmissive
+// clamp, Dirichlet ghost f^eq of the side's profile value; x side first), then the
+// moment u, the equilibria and the relaxation.
+template <typename T>
+__global__ void __launch_bounds__(256) step2ds_kernel(const StepArgs<T> a)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= a.nx || j >= a.ny) return;
+    const int64_t c = (int64_t)j * a.nx + i;
+    const int SX[4] = {-1, 1, 1, -1};
+    const int SY[4] = {-1, -1, 1, 1};
+    T f[4];
+    if (i > 0 && i < a.nx - 1 && j > 0 && j < a.ny - 1) {
+        const int64_t s[4] = {c + a.nx + 1, c + a.nx - 1, c - a.nx - 1, c - a.nx + 1};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) f[q] = a.src[q * a.N + s[q]];
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int si = i - SX[q], sj = j - SY[q];
+            const int side_y = sj < 0 ? 2 : (sj >= a.ny ? 3 : -1);
+            const int side_x = si < 0 ? 0 : (si >= a.nx ? 1 : -1);
+            const int kind_y = side_y == 2 ? a.bc[2] : a.bc[3];
+            const int kind_x = side_x == 0 ? a.bc[0] : a.bc[1];
+            const T* g = nullptr;
+            int m = 0;
+            if (side_x >= 0) {
+                if (kind_x == BC_DIRICHLET) {
+                    g = a.ghost + side_x * GHOST_STRIDE;
+                    m = sj;
+                } else if (kind_x == BC_PERIODIC) {
+                    si = si < 0 ? si + a.nx : si - a.nx;
+                } else {
+                    si = si < 0 ? 0 : a.nx - 1;
+                }
+            }
+            if (!g && side_y >= 0) {
+                if (kind_y == BC_DIRICHLET) {
+                    g = a.ghost + side_y * GHOST_STRIDE;
+                    m = si;
+                } else if (kind_y == BC_PERIODIC) {
+                    sj = sj < 0 ? sj + a.ny : sj - a.ny;
+                } else {
+                    sj = sj < 0 ? 0 : a.ny - 1;
+                }
+            }
+            if (g) {
+                T e[4];
+                equilibria2ds<T>(profile_value<T>(g, m), a.c, e);
+                f[q] = e[0];
+#pragma unroll
+                for (int r = 1; r < 4; ++r)
+                    if (r == q) f[q] = e[r];
+            } else {
+                f[q] = a.src[q * a.N + (int64_t)sj * a.nx + si];
+            }
+        }
+    }
+    const T u = ((f[0] + f[1]) + f[2]) + f[3];
+    T e[4];
+    equilibria2ds<T>(u, a.c, e);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) a.dst[q * a.N + c] = a.om1 * f[q] + a.om * e[q];
 }
 
 // ---------------------------------------------------------------- D1Q2 step

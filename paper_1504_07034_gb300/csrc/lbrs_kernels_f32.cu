@@ -664,6 +664,10 @@ cudaError_t launch_step_f32(int lattice, const StepArgs<float>& a, cudaStream_t 
             const dim3 grid((unsigned)((a.nx + block.x - 1) / block.x), (unsigned)((a.ny + block.y - 1) / block.y));
             step2d_kernel<float><<<grid, block, 0, s>>>(a);
         }
+    } else if (lattice == LAT_D2Q4S) {
+        const dim3 block(128, 2);
+        const dim3 grid((unsigned)((a.nx + block.x - 1) / block.x), (unsigned)((a.ny + block.y - 1) / block.y));
+        step2ds_kernel<float><<<grid, block, 0, s>>>(a);
     } else if (lattice == LAT_D1Q3) {
         step1d_q3_kernel<float><<<(unsigned)((a.nx + 255) / 256), 256, 0, s>>>(a);
     } else {

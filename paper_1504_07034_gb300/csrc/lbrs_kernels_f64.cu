@@ -43,12 +43,18 @@ template <>
 struct Dims<LAT_D1Q3> {
     static constexpr int Q = 3, K = 3;
 };
+template <>
+struct Dims<LAT_D2Q4S> {
+    static constexpr int Q = 4, K = 1;
+};
 
 // f^eq in FP64 for either lattice, e[q*K + k]
 template <int LAT>
 __device__ __forceinline__ void equilibria_flat(const double* U, double gm1, double c, double* e)
 {
-    if constexpr (LAT == LAT_D2Q4) {
+    if constexpr (LAT == LAT_D2Q4S) {
+        equilibria2ds<double>(U[0], c, e);
+    } else if constexpr (LAT == LAT_D2Q4) {
         double t[4][4];
         equilibria2d<double>(U, gm1, c, t);
 #pragma unroll
@@ -75,7 +81,8 @@ __device__ __forceinline__ void equilibria_flat(const double* U, double gm1, dou
 template <int LAT>
 __device__ __forceinline__ void prim_to_cons(const double* w, double gamma, double* U)
 {
-    if constexpr (LAT == LAT_D2Q4) prim_to_cons2d(w, gamma, U);
+    if constexpr (LAT == LAT_D2Q4S) U[0] = w[0];
+    else if constexpr (LAT == LAT_D2Q4) prim_to_cons2d(w, gamma, U);
     else prim_to_cons1d(w, gamma, U);
 }
 
@@ -89,12 +96,17 @@ __global__ void ghost_kernel(GhostSpec g, double gamma, double c, Ts* ghost)
     static_assert(Q * K <= GHOST_STRIDE, "ghost table stride");
     for (int n = 0; n < GHOST_STRIDE; ++n) e[n] = 0.0;
     if (g.kind[side] == BC_DIRICHLET) {
-        double U[4];
-        prim_to_cons<LAT>(g.prim[side], gamma, U);
-        equilibria_flat<LAT>(U, gamma - 1.0, c, e);
+        if constexpr (LAT == LAT_D2Q4S) {
+            e[0] = g.prim[side][0];            // the profile: u0, slope, dx
+            e[1] = g.prim[side][1];
+            e[2] = g.dx;
+        } else {
+            double U[4];
+            prim_to_cons<LAT>(g.prim[side], gamma, U);
+            equilibria_flat<LAT>(U, gamma - 1.0, c, e);
+        }
     }
-    for (int n = 0; n < Q * K; ++n) ghost[side * GHOST_STRIDE + n] = (Ts)e[n];
-    for (int n = Q * K; n < GHOST_STRIDE; ++n) ghost[side * GHOST_STRIDE + n] = (Ts)0;
+    for (int n = 0; n < GHOST_STRIDE; ++n) ghost[side * GHOST_STRIDE + n] = (Ts)e[n];
 }
 
 template <typename Tin, typename Ts, int LAT>
@@ -194,14 +206,19 @@ __global__ void __launch_bounds__(kThreads) diag_partial_kernel(const Ts* __rest
             acc.tot[k] += (double)s;
             finite = finite && isfinite(s);
         }
-        const R inv = (R)1 / U[0];
         R p, lam;
-        if constexpr (K == 4) {
+        if constexpr (K == 1) {
+            // the scalar law: no density or pressure; f^eq is monotone in u iff lambda >= |u| + 1
+            p = (R)1;
+            lam = fabs(U[0]) + (R)1;
+        } else if constexpr (K == 4) {
+            const R inv = (R)1 / U[0];
             const R u = U[1] * inv, v = U[2] * inv;
             p = gm1 * (U[3] - (R)0.5 * (U[1] * u + U[2] * v));
             const R s1 = fabs(u + v), s2 = fabs(u - v);
             lam = (s1 > s2 ? s1 : s2) + sqrt((R)2 * g * p * inv);
         } else {
+            const R inv = (R)1 / U[0];
             const R u = U[1] * inv;
             p = gm1 * (U[2] - (R)0.5 * (U[1] * u));
             lam = fabs(u) + sqrt(g * p * inv);
@@ -211,7 +228,7 @@ __global__ void __launch_bounds__(kThreads) diag_partial_kernel(const Ts* __rest
             mn_rho = fmin(mn_rho, U[0]);
             mn_p = fmin(mn_p, p);
         }
-        if (!finite || !(U[0] > (R)0) || !(p > (R)0)) {
+        if (!finite || (K > 1 && (!(U[0] > (R)0) || !(p > (R)0)))) {
             acc.nbad += 1.0;
         } else {
             mx_lam = fmax(mx_lam, lam);
@@ -462,6 +479,9 @@ cudaError_t launch_step_f64(int lattice, const StepArgs<double>& a, cudaStream_t
         const dim3 grid((unsigned)((a.nx + block.x - 1) / block.x), gy);
         if (a.solid) step2d_obstacle_kernel<double><<<grid, block, 0, s>>>(a);
         else step2d_kernel<double><<<grid, block, 0, s>>>(a);
+    } else if (lattice == LAT_D2Q4S) {
+        const dim3 block(128, 2);
+        step2ds_kernel<double><<<grid2d(a.nx, a.ny, block), block, 0, s>>>(a);
     } else if (lattice == LAT_D1Q3) {
         step1d_q3_kernel<double><<<(unsigned)((a.nx + 255) / 256), 256, 0, s>>>(a);
     } else {
@@ -473,7 +493,10 @@ cudaError_t launch_step_f64(int lattice, const StepArgs<double>& a, cudaStream_t
 cudaError_t launch_ghost(int lattice, int storage_f64, const GhostSpec& g, double gamma, double c, void* ghost,
                          cudaStream_t s)
 {
-    if (lattice == LAT_D2Q4) {
+    if (lattice == LAT_D2Q4S) {
+        if (storage_f64) ghost_kernel<double, LAT_D2Q4S><<<1, 32, 0, s>>>(g, gamma, c, (double*)ghost);
+        else ghost_kernel<float, LAT_D2Q4S><<<1, 32, 0, s>>>(g, gamma, c, (float*)ghost);
+    } else if (lattice == LAT_D2Q4) {
         if (storage_f64) ghost_kernel<double, LAT_D2Q4><<<1, 32, 0, s>>>(g, gamma, c, (double*)ghost);
         else ghost_kernel<float, LAT_D2Q4><<<1, 32, 0, s>>>(g, gamma, c, (float*)ghost);
     } else if (lattice == LAT_D1Q3) {
@@ -503,7 +526,8 @@ static void set_state_dispatch(int storage_f64, const void* W, int w_dtype, int 
 cudaError_t launch_set_state(int lattice, int storage_f64, const void* W, int w_dtype, int kind, void* fs,
                              int64_t N, double gamma, double c, cudaStream_t s)
 {
-    if (lattice == LAT_D2Q4) set_state_dispatch<LAT_D2Q4>(storage_f64, W, w_dtype, kind, fs, N, gamma, c, s);
+    if (lattice == LAT_D2Q4S) set_state_dispatch<LAT_D2Q4S>(storage_f64, W, w_dtype, kind, fs, N, gamma, c, s);
+    else if (lattice == LAT_D2Q4) set_state_dispatch<LAT_D2Q4>(storage_f64, W, w_dtype, kind, fs, N, gamma, c, s);
     else if (lattice == LAT_D1Q3) set_state_dispatch<LAT_D1Q3>(storage_f64, W, w_dtype, kind, fs, N, gamma, c, s);
     else set_state_dispatch<LAT_D1Q2>(storage_f64, W, w_dtype, kind, fs, N, gamma, c, s);
     return cudaGetLastError();
@@ -526,6 +550,7 @@ cudaError_t launch_moments(int lattice, int storage_f64, const void* fs, void* U
                            cudaStream_t s)
 {
     if (lattice == LAT_U2D) moments_dispatch<LAT_U2D>(0, fs, U, out_dtype, N, s);
+    else if (lattice == LAT_D2Q4S) moments_dispatch<LAT_D2Q4S>(storage_f64, fs, U, out_dtype, N, s);
     else if (lattice == LAT_D2Q4) moments_dispatch<LAT_D2Q4>(storage_f64, fs, U, out_dtype, N, s);
     else if (lattice == LAT_D1Q3) moments_dispatch<LAT_D1Q3>(storage_f64, fs, U, out_dtype, N, s);
     else moments_dispatch<LAT_D1Q2>(storage_f64, fs, U, out_dtype, N, s);
@@ -542,6 +567,9 @@ cudaError_t launch_diag(int lattice, int storage_f64, const void* fs, int64_t N,
     } else if (lattice == LAT_D1Q3) {
         if (storage_f64) diag_partial_kernel<double, LAT_D1Q3><<<kDiagBlocks, kThreads, 0, s>>>((const double*)fs, N, gamma, lambda, partials);
         else diag_partial_kernel<float, LAT_D1Q3><<<kDiagBlocks, kThreads, 0, s>>>((const float*)fs, N, gamma, lambda, partials);
+    } else if (lattice == LAT_D2Q4S) {
+        if (storage_f64) diag_partial_kernel<double, LAT_D2Q4S><<<kDiagBlocks, kThreads, 0, s>>>((const double*)fs, N, gamma, lambda, partials);
+        else diag_partial_kernel<float, LAT_D2Q4S><<<kDiagBlocks, kThreads, 0, s>>>((const float*)fs, N, gamma, lambda, partials);
     } else if (lattice == LAT_D2Q4) {
         if (storage_f64) diag_partial_kernel<double, LAT_D2Q4><<<kDiagBlocks, kThreads, 0, s>>>((const double*)fs, N, gamma, lambda, partials);
         else diag_partial_kernel<float, LAT_D2Q4><<<kDiagBlocks, kThreads, 0, s>>>((const float*)fs, N, gamma, lambda, partials);

@@ -38,6 +38,7 @@ cudaError_t launch_step2_f32(const StepArgs<float>& a, const TileMap* map, unsig
 struct GhostSpec {
     double prim[4][4];
     int kind[4];
+    double dx;       // the scalar lattice's boundary profiles are functions of the coordinate
 };
 cudaError_t launch_ghost(int lattice, int storage_f64, const GhostSpec& g, double gamma, double c, void* ghost,
                          cudaStream_t s);

@@ -230,6 +230,7 @@ extern "C" lbrs_status lbrs_diagnostics_noalloc(const lbrs_config* cfg, const vo
                  (long long)N, (long long)kMaxCells, kMaxBlocks);
         return set_error(LBRS_EINVAL, msg);
     }
+    if (cfg->lattice == LBRS_D2Q4S) return set_error(LBRS_EINVAL, "the scalar lattice is not covered here; use lbrs_diagnostics");
     double* scratch = nullptr;
     st = scratch_address(&scratch);
     if (st != LBRS_OK) return st;

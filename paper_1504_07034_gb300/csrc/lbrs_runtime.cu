@@ -34,10 +34,14 @@ struct Layout {
     size_t f_bytes, f0, f1, ghost, partials, diag_out, scale, status, wait_flag, total;
 };
 
-int lattice_q(int lat) { return lat == LBRS_D2Q4 ? 4 : (lat == LBRS_D1Q3 ? 3 : 2); }
-int lattice_k(int lat) { return lat == LBRS_D2Q4 ? 4 : 3; }
+bool two_d(int lat) { return lat == LBRS_D2Q4 || lat == LBRS_D2Q4S; }
+int lattice_q(int lat) { return two_d(lat) ? 4 : (lat == LBRS_D1Q3 ? 3 : 2); }
+int lattice_k(int lat) { return lat == LBRS_D2Q4 ? 4 : (lat == LBRS_D2Q4S ? 1 : 3); }
 // kernel lattice code of a public lattice
-int lat_code(int lat) { return lat == LBRS_D2Q4 ? LAT_D2Q4 : (lat == LBRS_D1Q3 ? LAT_D1Q3 : LAT_D1Q2); }
+int lat_code(int lat)
+{
+    return lat == LBRS_D2Q4 ? LAT_D2Q4 : (lat == LBRS_D2Q4S ? LAT_D2Q4S : (lat == LBRS_D1Q3 ? LAT_D1Q3 : LAT_D1Q2));
+}
 
 Layout layout_of(const lbrs_config* c)
 {
@@ -126,7 +130,7 @@ lbrs_status validate(const lbrs_config* c)
     if (c->struct_size != sizeof(lbrs_config))
         return fail(nullptr, LBRS_EINVAL, "config.struct_size %u != sizeof(lbrs_config) %zu", c->struct_size,
                     sizeof(lbrs_config));
-    if (c->lattice != LBRS_D1Q2 && c->lattice != LBRS_D2Q4 && c->lattice != LBRS_D1Q3)
+    if (c->lattice != LBRS_D1Q2 && c->lattice != LBRS_D2Q4 && c->lattice != LBRS_D1Q3 && c->lattice != LBRS_D2Q4S)
         return fail(nullptr, LBRS_EINVAL, "unknown lattice %d", c->lattice);
     if (c->precision < LBRS_F64 || c->precision > LBRS_F32U)
         return fail(nullptr, LBRS_EINVAL, "unknown precision %d", c->precision);
@@ -136,14 +140,14 @@ lbrs_status validate(const lbrs_config* c)
         return fail(nullptr, LBRS_EINVAL, "LBRS_F32U stores only the moments and needs omega == 1");
     if (c->nx < 1 || c->ny < 1) return fail(nullptr, LBRS_EINVAL, "grid must have nx, ny >= 1");
     if (c->nx > (1LL << 30)) return fail(nullptr, LBRS_EINVAL, "nx too large (max 2^30)");
-    if (c->lattice != LBRS_D2Q4 && c->ny != 1) return fail(nullptr, LBRS_EINVAL, "1-D lattices (D1Q2, D1Q3) need ny == 1");
-    if (c->lattice == LBRS_D2Q4 && c->ny > 2LL * 65535) return fail(nullptr, LBRS_EINVAL, "ny too large (max 131070)");
+    if (!two_d(c->lattice) && c->ny != 1) return fail(nullptr, LBRS_EINVAL, "1-D lattices (D1Q2, D1Q3) need ny == 1");
+    if (two_d(c->lattice) && c->ny > 2LL * 65535) return fail(nullptr, LBRS_EINVAL, "ny too large (max 131070)");
     if (!(c->gamma > 1.0) || !isfinite(c->gamma)) return fail(nullptr, LBRS_EINVAL, "gamma must be > 1");
     if (!finite_pos(c->lambda)) return fail(nullptr, LBRS_EINVAL, "lambda must be positive");
     if (!(c->omega > 0.0 && c->omega < 2.0)) return fail(nullptr, LBRS_EINVAL, "omega must lie in (0, 2)");
     if (!finite_pos(c->dx)) return fail(nullptr, LBRS_EINVAL, "dx must be positive");
     if (c->diag_every < 0) return fail(nullptr, LBRS_EINVAL, "diag_every must be >= 0");
-    const int sides = c->lattice == LBRS_D2Q4 ? 4 : 2;
+    const int sides = two_d(c->lattice) ? 4 : 2;
     for (int s = 0; s < sides; ++s) {
         const int kind = c->bc[s].kind;
         if (kind < LBRS_BC_PERIODIC || kind > LBRS_BC_WALL)
@@ -155,6 +159,11 @@ lbrs_status validate(const lbrs_config* c)
         if (kind == LBRS_BC_DIRICHLET) {
             const double* w = c->bc[s].prim;
             const int K = lattice_k(c->lattice);
+            if (c->lattice == LBRS_D2Q4S) {       // the scalar's linear profile (value, slope)
+                if (!isfinite(w[0]) || !isfinite(w[1]))
+                    return fail(nullptr, LBRS_EINVAL, "side %d: non-finite Dirichlet profile", s);
+                continue;
+            }
             for (int k = 0; k < K; ++k)
                 if (!isfinite(w[k])) return fail(nullptr, LBRS_EINVAL, "side %d: non-finite Dirichlet state", s);
             if (!(w[0] > 0.0) || !(w[K - 1] > 0.0))
@@ -274,7 +283,7 @@ int readout_lattice(const lbrs_ctx* ctx);
 // folded into the device status record under the current step number.
 cudaError_t periodic_check(lbrs_ctx* ctx)
 {
-    const double vol = ctx->lattice == LBRS_D2Q4 ? ctx->cfg.dx * ctx->cfg.dx : ctx->cfg.dx;
+    const double vol = two_d(ctx->lattice) ? ctx->cfg.dx * ctx->cfg.dx : ctx->cfg.dx;
     double* partials = (double*)(ctx->ws + ctx->L.partials);
     double* dout = (double*)(ctx->ws + ctx->L.diag_out);
     cudaError_t e = launch_diag(readout_lattice(ctx), ctx->f64, ctx->f[ctx->cur], ctx->N, ctx->cfg.gamma,
@@ -518,10 +527,11 @@ lbrs_status lbrs_create(const lbrs_config* cfg, void* d_workspace, size_t bytes,
     ctx->f[0] = ctx->ws + L.f0;
     ctx->f[1] = ctx->ws + L.f1;
     ctx->stream = (cudaStream_t)cfg->cuda_stream;
-    ctx->c = cfg->lattice == LBRS_D2Q4 ? 1.0 / (4.0 * cfg->lambda) : 1.0 / (2.0 * cfg->lambda);   // both 1-D lattices: 1/(2 lambda)
+    ctx->c = two_d(cfg->lattice) ? 1.0 / (4.0 * cfg->lambda) : 1.0 / (2.0 * cfg->lambda);   // both 1-D lattices: 1/(2 lambda)
 
     GhostSpec g;
     memset(&g, 0, sizeof g);
+    g.dx = cfg->dx;
     for (int s = 0; s < 4; ++s) {
         g.kind[s] = cfg->bc[s].kind;
         for (int k = 0; k < 4; ++k) g.prim[s][k] = cfg->bc[s].prim[k];
@@ -700,7 +710,7 @@ lbrs_status lbrs_diagnostics(lbrs_ctx* ctx, lbrs_diag* out)
     if (!out) return fail(ctx, LBRS_EINVAL, "out is NULL");
     if (!ctx->has_state) return fail(ctx, LBRS_ESTATE, "no state set");
     const int lat = readout_lattice(ctx);
-    const double vol = ctx->lattice == LBRS_D2Q4 ? ctx->cfg.dx * ctx->cfg.dx : ctx->cfg.dx;
+    const double vol = two_d(ctx->lattice) ? ctx->cfg.dx * ctx->cfg.dx : ctx->cfg.dx;
     double* partials = (double*)(ctx->ws + ctx->L.partials);
     double* dout = (double*)(ctx->ws + ctx->L.diag_out);
     LBRS_CUDA(ctx, launch_diag(lat, ctx->f64, ctx->f[ctx->cur], ctx->N, ctx->cfg.gamma, ctx->cfg.lambda, vol,
@@ -819,7 +829,7 @@ lbrs_status lbrs_vjp_loss(lbrs_ctx* ctx, const void* d_rho_target, int dtype, vo
     if (dtype != LBRS_F64 && dtype != LBRS_F32) return fail(ctx, LBRS_EINVAL, "dtype must be LBRS_F64 or LBRS_F32");
     if (!ctx->has_state) return fail(ctx, LBRS_ESTATE, "no state set");
     if (ctx->f16 || ctx->f32u) return fail(ctx, LBRS_EINVAL, "the adjoint covers the F64 and F32 forms only");
-    const double vol = ctx->lattice == LBRS_D2Q4 ? ctx->cfg.dx * ctx->cfg.dx : ctx->cfg.dx;
+    const double vol = two_d(ctx->lattice) ? ctx->cfg.dx * ctx->cfg.dx : ctx->cfg.dx;
     double* partials = (double*)(ctx->ws + ctx->L.partials);
     double* dout = (double*)(ctx->ws + ctx->L.diag_out);
     LBRS_CUDA(ctx, launch_density_loss(ctx->Q, ctx->K, ctx->f64, ctx->f[ctx->cur], d_rho_target, dtype == LBRS_F32,

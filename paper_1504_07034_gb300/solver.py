@@ -22,7 +22,8 @@ def make_config(lattice: str, nx: int, ny: int, *, gamma: float, lam: float, ome
                 bc, precision: str, stream_handle: int, diag_every: int = 0) -> abi.lbrs_config:
     cfg = abi.lbrs_config()
     cfg.struct_size = ctypes.sizeof(abi.lbrs_config)
-    cfg.lattice = {"d2q4": abi.LBRS_D2Q4, "d1q2": abi.LBRS_D1Q2, "d1q3": abi.LBRS_D1Q3}[lattice]
+    cfg.lattice = {"d2q4": abi.LBRS_D2Q4, "d2q4s": abi.LBRS_D2Q4S, "d1q2": abi.LBRS_D1Q2,
+                   "d1q3": abi.LBRS_D1Q3}[lattice]
     cfg.precision = _PRECISION[precision]
     cfg.diag_every = int(diag_every)
     cfg.nx, cfg.ny = int(nx), int(ny)
@@ -39,7 +40,8 @@ def make_config(lattice: str, nx: int, ny: int, *, gamma: float, lam: float, ome
 class Solver:
     """One LBRS problem on one GPU.
 
-    lattice   "d1q2", "d1q3" or "d2q4"
+    lattice   "d1q2", "d1q3", "d2q4" or "d2q4s" (the scalar 2-D Burgers law; one field u; a
+              Dirichlet side's state is the linear profile (value, slope) along it)
     bc        per side (x-lo, x-hi[, y-lo, y-hi]): (kind, primitive_state_or_None)
     precision "f64" (plain FP64 path), "f32" (FP32 distributions), "f16neq" (D2Q4: FP32
               moments plus FP16 non-equilibrium parts) or "f32u" (D2Q4 at omega = 1: FP32 moments only)
@@ -52,12 +54,12 @@ class Solver:
         self.lib = abi.load()
         self.solid = None
         self.lattice = lattice
-        self.Q, self.K = {"d2q4": (4, 4), "d1q2": (2, 3), "d1q3": (3, 3)}[lattice]
+        self.Q, self.K = {"d2q4": (4, 4), "d2q4s": (4, 1), "d1q2": (2, 3), "d1q3": (3, 3)}[lattice]
         self.nx, self.ny = int(nx), int(ny)
         self.precision = precision
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        sides = 4 if lattice == "d2q4" else 2
+        sides = 4 if lattice in ("d2q4", "d2q4s") else 2
         bc = list(bc)
         if len(bc) < sides:
             raise ValueError(f"need {sides} boundary conditions")
@@ -77,7 +79,8 @@ class Solver:
     def from_workload(cls, wl, precision: str = "f32", stream=None, omega=None, diag_every: int = 0,
                       lattice: str = "d1q2"):
         if hasattr(wl, "ny"):
-            s = cls("d2q4", wl.nx, wl.ny, lam=wl.lam, dx=wl.dx, bc=wl.bc, gamma=wl.gamma,
+            lat = "d2q4s" if getattr(wl, "law", "euler") == "burgers" else "d2q4"
+            s = cls(lat, wl.nx, wl.ny, lam=wl.lam, dx=wl.dx, bc=wl.bc, gamma=wl.gamma,
                     omega=wl.omega if omega is None else omega, precision=precision, stream=stream,
                     diag_every=diag_every)
             if getattr(wl, "solid", None) is not None:
@@ -90,7 +93,7 @@ class Solver:
     # ------------------------------------------------------------------ helpers
     @property
     def grid(self):
-        return (self.ny, self.nx) if self.lattice == "d2q4" else (self.nx,)
+        return (self.ny, self.nx) if self.lattice in ("d2q4", "d2q4s") else (self.nx,)
 
 
     @property

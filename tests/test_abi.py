@@ -94,6 +94,9 @@ def test_workspace_size_formula(lib):
     (dict(bc=[("periodic", None), ("transmissive", None), ("transmissive", None), ("transmissive", None)]), "periodic"),
     (dict(bc=[("dirichlet", (-1.0, 0, 0, 1)), ("transmissive", None), ("transmissive", None), ("transmissive", None)]), "Dirichlet"),
     (dict(ny=1, bc=[("transmissive", None), ("transmissive", None), ("wall", None), ("transmissive", None)]), "ny >= 2"),
+    (dict(lattice="d2q4s", bc=[("transmissive", None)] * 2 + [("wall", None)] * 2), "wall"),
+    (dict(lattice="d2q4s", bc=[("dirichlet", (float("nan"), 0.0))] + [("transmissive", None)] * 3), "profile"),
+    (dict(lattice="d2q4s", precision="f16neq"), "D2Q4 storage forms"),
 ])
 def test_invalid_config_rejected(lib, bad, needle):
     from paper_1504_07034_gb300 import abi
@@ -132,3 +135,14 @@ def test_null_context_calls(lib):
     lib.lbrs_destroy(None)
     assert lib.lbrs_status_string(abi.LBRS_ESUBCHAR) == b"LBRS_ESUBCHAR"
     assert lib.lbrs_abi_version() == abi.ABI_VERSION
+
+
+def test_scalar_lattice_workspace(lib):
+    """The scalar D2Q4 lattice stores 4 populations of one field per cell; Dirichlet profiles may
+    take any finite value and slope (a negative u is a valid state of the scalar law)."""
+    from paper_1504_07034_gb300 import abi
+    bc = [("dirichlet", (-1.0, 2.0)), ("dirichlet", (1.5, -0.5)), ("transmissive", None), ("transmissive", None)]
+    cfg = _cfg(lattice="d2q4s", nx=100, ny=30, bc=bc, precision="f64")
+    size = ctypes.c_size_t()
+    assert lib.lbrs_workspace_size(ctypes.byref(cfg), ctypes.byref(size)) == abi.LBRS_OK
+    assert 2 * 4 * 100 * 30 * 8 <= size.value < 2 * 4 * 100 * 30 * 8 + 64 * 1024
