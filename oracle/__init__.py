@@ -109,6 +109,9 @@ def lib():
         L.orc_adjoint_step.restype = ctypes.c_int
         L.orc_vjp_equilibrium.argtypes = [P, dp, dp, dp]
         L.orc_vjp_equilibrium.restype = ctypes.c_int
+        L.orc_run_adaptive.argtypes = [P, dp, dp, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       dp, dp, dp]
+        L.orc_run_adaptive.restype = ctypes.c_int64
         L.orc_obstacle_check.argtypes = [P]
         L.orc_obstacle_check.restype = ctypes.c_int64
         _lib = L
@@ -242,6 +245,22 @@ class Oracle:
         if err:
             raise ValueError(f"oracle run error {err}")
         return fs, _check_dict(chk)
+
+    def run_adaptive(self, fs, nsteps: int, dx: float, safety: float, t_final: float = 0.0):
+        """Advance a copy of fs (whose equilibria were built with this problem's lambda) with
+        the lambda chosen anew every step: each step streams with the current state's lambda
+        (advancing dx / lambda) and collides with safety times the largest local bound of the
+        state before it and of the Dirichlet states; stop at t_final exactly if positive.
+        Returns (fs, the stream lambda of every step, time reached, lambda of the final state)."""
+        fs = self._dists(fs).copy()
+        work = np.empty_like(fs)
+        lam = np.empty(max(int(nsteps), 1))
+        t, lam_next = ctypes.c_double(), ctypes.c_double()
+        n = lib().orc_run_adaptive(ctypes.byref(self.p), _ptr(fs), _ptr(work), int(nsteps), float(dx),
+                                   float(safety), float(t_final), _ptr(lam), ctypes.byref(t), ctypes.byref(lam_next))
+        if n < 0:
+            raise ValueError(f"oracle adaptive run error {n}")
+        return fs, lam[:n].copy(), t.value, lam_next.value
 
     def moments(self, fs) -> np.ndarray:
         fs = self._dists(fs)

@@ -561,6 +561,89 @@ int orc_run(const orc_params* P, double* fs, double* work, int64_t nsteps, int64
     return 0;
 }
 
+/* Largest local bound over the cells' moments U (physical cells only) and the
+ * Dirichlet states of the sides. */
+static double max_bound(const orc_params* P, const double* U)
+{
+    const int64_t N = P->nx * P->ny;
+    const int K = nk(P);
+    double m = 0.0;
+    for (int64_t c = 0; c < N; ++c) {
+        double u[4];
+        for (int k = 0; k < K; ++k) u[k] = U[k * N + c];
+        double p = pressure(P, u);
+        if (!(u[0] > 0.0) || !(p > 0.0) || !isfinite(p)) continue;
+        double l = lambda_local(P, u, p);
+        if (l > m) m = l;
+    }
+    int sides = two_d(P) ? 4 : 2;
+    for (int s = 0; s < sides; ++s) {
+        if (P->bc_kind[s] != ORC_DIRICHLET) continue;
+        double u[4];
+        prim_to_cons_cell(P, P->bc_prim[s], u);
+        double l = lambda_local(P, u, pressure(P, u));
+        if (l > m) m = l;
+    }
+    return m;
+}
+
+/*
+ * Adaptive lattice speed: the sub-characteristic choice of Section II.C (the bound
+ * of Section II.D in 2-D) taken anew every step.  The post-collision distributions
+ * carry the lambda of their equilibria, and streaming them one cell advances the
+ * solution by dt = dx / (that lambda) (at omega = 1 the update is Lax-Friedrichs
+ * with that lambda).  So each step streams with the lambda of the current state
+ * (P->lambda for the first; Dirichlet ghosts built with it too), advancing the time
+ * by dx / lambda, and its collision builds the equilibria with the next lambda:
+ * safety times the largest local bound over the moments of the state before the
+ * step and the Dirichlet states (one step behind, so that the GPU can take the max
+ * in the same pass).  With t_final > 0 the collision whose state would stream past
+ * t_final takes lambda = dx / (t_final - t) instead (larger, hence admissible), and
+ * the run stops after that stream, at t_final exactly.  lam_out (nullable, nsteps
+ * entries) receives each step's stream lambda; *lam_next the lambda of the final
+ * state.  Returns the number of steps taken (negative on invalid parameters, or if
+ * the first stream alone passes t_final); *t is the time reached.  Euler lattices,
+ * no obstacles.
+ */
+int64_t orc_run_adaptive(const orc_params* P, double* fs, double* work, int64_t nsteps, double dx, double safety,
+                         double t_final, double* lam_out, double* t, double* lam_next)
+{
+    if (orc_validate(P) || P->lattice == ORC_D2Q4S || P->solid || !(dx > 0.0) || !(safety >= 1.0)) return -1;
+    if (t_final > 0.0 && dx / P->lambda > t_final) return -3;
+    const int64_t N = P->nx * P->ny;
+    double* U = (double*)malloc((size_t)nk(P) * (size_t)N * sizeof(double));
+    if (!U) return -2;
+    orc_params Qs = *P, Qc = *P;
+    orc_moments(P, fs, U);
+    double bound = max_bound(P, U), tt = 0.0, lam_cur = P->lambda;
+    int last = 0;
+    int64_t n = 0;
+    while (n < nsteps) {
+        double t_next = last ? t_final : tt + dx / lam_cur;
+        double lam_new = safety * bound;
+        int next_last = 0;
+        if (!last && t_final > 0.0 && t_next + dx / lam_new >= t_final) {
+            lam_new = dx / (t_final - t_next);
+            next_last = 1;
+        }
+        Qs.lambda = lam_cur;
+        Qc.lambda = lam_new;
+        orc_stream(&Qs, fs, work);
+        orc_collide(&Qc, work, fs, U, NULL, n + 1);
+        if (lam_out) lam_out[n] = lam_cur;
+        tt = t_next;
+        lam_cur = lam_new;
+        bound = max_bound(P, U);
+        ++n;
+        if (last) break;
+        last = next_last;
+    }
+    free(U);
+    *t = tt;
+    *lam_next = lam_cur;
+    return n;
+}
+
 /* FP64 totals sum_cells U_k * cell volume (cell volume = dx for 1-D, dx^2 for 2-D). */
 void orc_totals(const orc_params* P, const double* fs, double cell_volume, double* totals)
 {
