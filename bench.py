@@ -367,6 +367,35 @@ def burgers_measurement(Solver, stream, barrier, peak):
     return out
 
 
+def adaptive_measurement(Solver, stream, barrier, wl, t_final):
+    """The bench workload (1024^2 quadrant Riemann) run to the configuration's final time
+    with the lattice speed chosen anew every step (safety 1.05): steps taken against the
+    fixed-lambda configuration, MLUPS (each step: one prep launch and one step launch with
+    the fused max reduction), and the FP32 density L1 against the FP64 adaptive run."""
+    import torch
+    out = {"t_final": t_final, "safety": 1.05, "fixed_lambda_steps": wl.steps, "fixed_lambda": wl.lam}
+    rho = {}
+    for precision in ("f64", "f32"):
+        s = Solver.from_workload(wl, precision=precision, stream=stream)
+        with torch.cuda.stream(stream):
+            s.set_state(torch.from_numpy(wl.prim).cuda())
+            s.run_to_time(t_final, 1.05)                      # warm-up run
+            s.set_state(torch.from_numpy(wl.prim).cuda())
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            barrier()
+            a.record(stream)
+            st = s.run_to_time(t_final, 1.05, chunk=128)
+            b.record(stream)
+            barrier()
+            rho[precision] = s.moments(torch.float64)[0].clone()
+        s.close()
+        sec = a.elapsed_time(b) / 1e3
+        out[precision] = {"steps": st["steps"], "t_reached": st["t"], "final_lambda": st["lambda"],
+                          "seconds_incl_chunk_syncs": sec, "mlups": wl.cells * st["steps"] / sec / 1e6}
+    out["l1_rho_f32_vs_f64"] = float((rho["f32"] - rho["f64"]).abs().mean().item())
+    return out
+
+
 def batch_measurement(stream, barrier):
     """4096 shock tubes, N log-uniform in [200, 20000], to t = 0.15 in FP32 (temporal blocking)."""
     import torch
@@ -599,6 +628,9 @@ def run_ours(args):
     # --- internal walls: forward-facing step and shock diffraction ------------------
     obstacles = obstacle_measurement(Solver, stream, barrier, peak)
 
+    # --- adaptive lambda on the bench workload, to the configuration's final time ----
+    adaptive = adaptive_measurement(Solver, stream, barrier, wl, CONFIG_STEPS * wl.dx / wl.lam)
+
     # --- scalar D2Q4: the 2-D Burgers problems -------------------------------------
     burgers = burgers_measurement(Solver, stream, barrier, peak)
 
@@ -645,6 +677,7 @@ def run_ours(args):
             "sod_1d": sod,
             "internal_walls": obstacles,
             "burgers_2d": burgers,
+            "adaptive_lambda": adaptive,
             "batched_tubes": batched,
             "fp64": {"value": mlups64, "unit": UNIT, "achieved_gbs": BYTES_PER_LUP_F64 * mlups64 / 1e3,
                      "diag_after_1000_steps": {k: d64[k] for k in ("status", "min_rho", "min_p", "max_lambda_local")}},

@@ -180,6 +180,29 @@ lbrs_status lbrs_set_state(lbrs_ctx* ctx, const void* W, int on_device, int dtyp
  * (see LBRS_ETIMEOUT). */
 lbrs_status lbrs_step(lbrs_ctx* ctx, int64_t n);
 
+/* Adaptive lattice speed (D2Q4, LBRS_F64 or LBRS_F32, no internal walls): the
+ * sub-characteristic choice of Section II.C with the bound of Section II.D, taken
+ * anew every step.  Distributions carry the lambda of their equilibria and streaming
+ * them one cell advances the solution by dt = dx / that lambda; so each step streams
+ * with the current state's lambda (Dirichlet ghosts rebuilt with it) and collides
+ * with the next one, safety times the largest local bound max(|u+v|, |u-v|) +
+ * sqrt(2) a over the moments of the state before the step and the Dirichlet states.
+ * The maximum over the cells is taken inside the step kernel (for the step after);
+ * one small kernel per step turns it into lambda and the clock.  The first call after
+ * a state was set starts a run at t = 0 with the configured lambda (whose first step
+ * must not pass t_final: EINVAL).  With t_final > 0, the collision whose state would
+ * stream past t_final takes lambda = dx / (t_final - t), so the run ends exactly at
+ * t_final; steps enqueued after that keep the state unchanged (keep t_final fixed
+ * over one run).  n steps are enqueued asynchronously (2 launches each).  After an
+ * adaptive step, lbrs_step returns ESTATE until a state is set again (the ghosts
+ * return to the configured lambda); lbrs_diagnostics compares the bounds with the
+ * configured lambda.  safety >= 1, t_final >= 0 (0: no end). */
+lbrs_status lbrs_step_adaptive(lbrs_ctx* ctx, int64_t n, double safety, double t_final);
+
+/* The adaptive run's time reached, the lambda of the current distributions, the
+ * adaptive steps taken and whether t_final was reached; synchronises. */
+lbrs_status lbrs_adaptive_state(lbrs_ctx* ctx, double* t, double* lambda, int64_t* steps, int* done);
+
 /* Wait for the context's stream; reports a CUDA error raised by earlier work,
  * and LBRS_ETIMEOUT if a tile copy of the two-step kernel did not arrive within
  * its bounded wait (the blocks concerned left their tiles unwritten; setting a

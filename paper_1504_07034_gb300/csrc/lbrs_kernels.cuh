@@ -447,6 +447,117 @@ __global__ void __launch_bounds__(256) step2d_obstacle_kernel(const StepArgs<T> 
     collide_store_2d<T, STORE_U>(a, c, f);
 }
 
+// ---------------------------------------------------------------- adaptive lambda (D2Q4)
+//
+// The lattice speed taken anew every step (the sub-characteristic choice of
+// Section II.C with the bound of Section II.D): distributions carry the lambda of
+// their equilibria, so a step streams with the current state's lambda (the
+// Dirichlet ghosts are rebuilt with it; the step advances the time by dx / lambda)
+// and collides with the next one, safety times the largest local bound of the
+// state before the step and of the Dirichlet states.  The maximum over the cells
+// is taken by the step kernel itself for the following step (one block max and one
+// 64-bit atomic max per block, of the bits of a non-negative double); a one-thread
+// prep kernel before each step turns it into the next lambda, the clock and the
+// ghosts.  Three rotating accumulator slots keep reads and resets apart.
+struct AdaptState {
+    unsigned long long bound_bits[3];   // largest bound of a state, as the bits of a non-negative double
+    double t;                           // time reached
+    double lam_cur;                     // lambda of the current distributions
+    double c_new;                       // 1/(4 lambda) of the running step's collision
+    long long steps;                    // adaptive steps taken
+    int last;                           // the next step ends the run
+    int done;                           // the run reached t_final: further steps keep the state
+    int slot_cur;                       // slot with the bound of the current state
+    int skip;                           // the running step keeps the state
+};
+
+// The local bound max(|u+v|, |u-v|) + sqrt(2) a of a state (Section II.D), in T;
+// -1 for a state with rho <= 0, p <= 0 or a non-finite pressure (left out).
+template <typename T>
+__device__ __forceinline__ double bound2d(const T U[4], double gamma)
+{
+    const T g = (T)gamma, gm1 = (T)(gamma - 1.0);
+    const T u = U[1] / U[0], v = U[2] / U[0];
+    const T p = gm1 * (U[3] - T(0.5) * (U[1] * u + U[2] * v));
+    if (!(U[0] > T(0)) || !(p > T(0)) || !isfinite(p)) return -1.0;
+    const T a = sqrt(g * p / U[0]);
+    const T s1 = fabs(u + v), s2 = fabs(u - v);
+    return (double)((s1 > s2 ? s1 : s2) + sqrt(T(2)) * a);
+}
+
+// Block maximum of v (threads of a 1-D or 2-D block of NT threads), folded into *dst.
+template <int NT>
+__device__ __forceinline__ void block_max_into(double v, unsigned long long* dst)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, off));
+    __shared__ double wmax[NT / 32];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    if ((tid & 31) == 0) wmax[tid >> 5] = v;
+    __syncthreads();
+    if (tid == 0) {
+        double m = wmax[0];
+        for (int w = 1; w < NT / 32; ++w) m = fmax(m, wmax[w]);
+        if (m > 0.0) atomicMax(dst, (unsigned long long)__double_as_longlong(m));
+    }
+}
+
+// One adaptive step (stream with the ghosts the prep kernel built, collide with
+// c_new), accumulating the bound of the new state into the prep's slot.
+template <typename T>
+__global__ void __launch_bounds__(256) step2d_adapt_kernel(const StepArgs<T> a, AdaptState* st, double gamma)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const bool in = i < a.nx && j < a.ny;
+    const int64_t c = (int64_t)j * a.nx + i;
+    if (st->skip) {            // the same for every thread of the grid
+        if (in) {
+#pragma unroll
+            for (int n = 0; n < 16; ++n) a.dst[n * a.N + c] = a.src[n * a.N + c];
+        }
+        return;
+    }
+    double bnd = -1.0;
+    if (in) {
+        StepArgs<T> b = a;
+        b.c = (T)st->c_new;
+        T f[4][4];
+        if (i > 0 && i < a.nx - 1 && j > 0 && j < a.ny - 1) {
+            const int64_t s[4] = {c + a.nx + 1, c + a.nx - 1, c - a.nx - 1, c - a.nx + 1};
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) f[q][k] = a.src[(q * 4 + k) * a.N + s[q]];
+        } else {
+            pull_edge_2d<T>(b, i, j, f);
+        }
+        T U[4], out[4][4];
+        collide_2d<T>(b, f, U, out);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) a.dst[(q * 4 + k) * a.N + c] = out[q][k];
+        bnd = bound2d<T>(U, gamma);
+    }
+    block_max_into<256>(bnd, &st->bound_bits[st->slot_cur]);
+}
+
+// The bound of the current state (its moments summed in q order), into slot_cur.
+template <typename T>
+__global__ void __launch_bounds__(256) adapt_init_bound_kernel(const T* __restrict__ fs, int64_t N, double gamma,
+                                                              AdaptState* st)
+{
+    double bnd = -1.0;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += (int64_t)gridDim.x * blockDim.x) {
+        T U[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) U[k] = ((fs[k * N + c] + fs[(4 + k) * N + c]) + fs[(8 + k) * N + c]) + fs[(12 + k) * N + c];
+        bnd = fmax(bnd, bound2d<T>(U, gamma));
+    }
+    block_max_into<256>(bnd, &st->bound_bits[st->slot_cur]);
+}
+
 // ---------------------------------------------------------------- scalar D2Q4 step
 //
 // One thread per cell: pull the four populations (periodic wrap, transmissive

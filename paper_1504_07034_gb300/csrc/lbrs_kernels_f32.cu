@@ -762,6 +762,22 @@ cudaError_t launch_step2_f32(const StepArgs<float>& a, const TileMap* map, unsig
     return cudaGetLastError();
 }
 
+cudaError_t launch_adapt_step_f32(const StepArgs<float>& a, void* st, double gamma, cudaStream_t s)
+{
+    const dim3 block(128, 2);
+    const dim3 grid((unsigned)((a.nx + block.x - 1) / block.x), (unsigned)((a.ny + block.y - 1) / block.y));
+    step2d_adapt_kernel<float><<<grid, block, 0, s>>>(a, (AdaptState*)st, gamma);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adapt_init_bound_f32(const void* fs, int64_t N, double gamma, void* st, cudaStream_t s)
+{
+    int64_t b = (N + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    adapt_init_bound_kernel<float><<<(unsigned)(b < 1 ? 1 : b), 256, 0, s>>>((const float*)fs, N, gamma, (AdaptState*)st);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_step_record_f32(const StepArgs<float>& a, cudaStream_t s)
 {
     const dim3 block(128, 2);

@@ -382,6 +382,65 @@ __global__ void status_update_kernel(const double* __restrict__ diag, double* __
     }
 }
 
+// Adaptive lambda: reset the run's record (time 0, the configured lambda).
+__global__ void adapt_reset_kernel(AdaptState* st, double lambda)
+{
+    if (threadIdx.x != 0) return;
+    for (int n = 0; n < 3; ++n) st->bound_bits[n] = 0ull;
+    st->t = 0.0;
+    st->lam_cur = lambda;
+    st->c_new = 1.0 / (4.0 * lambda);
+    st->steps = 0;
+    st->last = st->done = st->slot_cur = st->skip = 0;
+}
+
+// Adaptive lambda, before each step (one thread; FP64 without contraction, the
+// oracle's expressions): the next lambda from the bound of the current state and of
+// the Dirichlet states, the stop at t_final, the clock, the ghosts of this step's
+// stream (with the current lambda) and a cleared slot for the step's bound.
+template <typename Ts>
+__global__ void adapt_prep_kernel(AdaptState* st, Ts* ghost, GhostSpec g, double gamma, double dx, double safety,
+                                  double t_final)
+{
+    if (threadIdx.x != 0) return;
+    if (st->done) {
+        st->skip = 1;
+        return;
+    }
+    st->skip = 0;
+    double bound = __longlong_as_double((long long)st->bound_bits[st->slot_cur]);
+    double Ub[4][4];
+    for (int s = 0; s < 4; ++s) {
+        if (g.kind[s] != BC_DIRICHLET) continue;
+        prim_to_cons2d(g.prim[s], gamma, Ub[s]);
+        bound = fmax(bound, bound2d<double>(Ub[s], gamma));
+    }
+    const double t_next = st->last ? t_final : st->t + dx / st->lam_cur;
+    double lam_new = safety * bound;
+    int next_last = 0;
+    if (!st->last && t_final > 0.0 && t_next + dx / lam_new >= t_final) {
+        lam_new = dx / (t_final - t_next);
+        next_last = 1;
+    }
+    const double c_cur = 1.0 / (4.0 * st->lam_cur);
+    for (int s = 0; s < 4; ++s) {
+        if (g.kind[s] != BC_DIRICHLET) continue;
+        double e[4][4];
+        equilibria2d<double>(Ub[s], gamma - 1.0, c_cur, e);
+        for (int q = 0; q < 4; ++q)
+            for (int k = 0; k < 4; ++k) ghost[s * GHOST_STRIDE + q * 4 + k] = (Ts)e[q][k];
+    }
+    st->c_new = 1.0 / (4.0 * lam_new);
+    const int acc = (st->slot_cur + 1) % 3;
+    st->bound_bits[acc] = 0ull;
+    st->slot_cur = acc;
+    st->t = t_next;
+    st->lam_cur = lam_new;
+    st->steps += 1;
+    if (st->last) st->done = 1;
+    st->last = next_last;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
@@ -625,6 +684,39 @@ cudaError_t launch_batch_copy_f64(const double* src, double* dst, int64_t N, con
 {
     if (ntiles <= 0) return cudaSuccess;
     batch_copy_kernel<double><<<ntiles, 256, 0, s>>>(src, dst, N, tiles, tube_off);
+    return cudaGetLastError();
+}
+
+}  // namespace lbrs
+
+namespace lbrs {
+
+cudaError_t launch_adapt_reset(void* st, double lambda, cudaStream_t s)
+{
+    adapt_reset_kernel<<<1, 32, 0, s>>>((AdaptState*)st, lambda);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adapt_prep(int storage_f64, void* st, void* ghost, const GhostSpec& g, double gamma, double dx,
+                              double safety, double t_final, cudaStream_t s)
+{
+    if (storage_f64)
+        adapt_prep_kernel<double><<<1, 32, 0, s>>>((AdaptState*)st, (double*)ghost, g, gamma, dx, safety, t_final);
+    else
+        adapt_prep_kernel<float><<<1, 32, 0, s>>>((AdaptState*)st, (float*)ghost, g, gamma, dx, safety, t_final);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adapt_step_f64(const StepArgs<double>& a, void* st, double gamma, cudaStream_t s)
+{
+    const dim3 block(128, 2);
+    step2d_adapt_kernel<double><<<grid2d(a.nx, a.ny, block), block, 0, s>>>(a, (AdaptState*)st, gamma);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adapt_init_bound_f64(const void* fs, int64_t N, double gamma, void* st, cudaStream_t s)
+{
+    adapt_init_bound_kernel<double><<<grid_for(N), 256, 0, s>>>((const double*)fs, N, gamma, (AdaptState*)st);
     return cudaGetLastError();
 }
 

@@ -42,6 +42,15 @@ struct GhostSpec {
 };
 cudaError_t launch_ghost(int lattice, int storage_f64, const GhostSpec& g, double gamma, double c, void* ghost,
                          cudaStream_t s);
+// Adaptive lambda (D2Q4): st is an AdaptState in the workspace.
+cudaError_t launch_adapt_reset(void* st, double lambda, cudaStream_t s);
+cudaError_t launch_adapt_prep(int storage_f64, void* st, void* ghost, const GhostSpec& g, double gamma, double dx,
+                              double safety, double t_final, cudaStream_t s);
+cudaError_t launch_adapt_step_f64(const StepArgs<double>& a, void* st, double gamma, cudaStream_t s);
+cudaError_t launch_adapt_step_f32(const StepArgs<float>& a, void* st, double gamma, cudaStream_t s);
+cudaError_t launch_adapt_init_bound_f64(const void* fs, int64_t N, double gamma, void* st, cudaStream_t s);
+cudaError_t launch_adapt_init_bound_f32(const void* fs, int64_t N, double gamma, void* st, cudaStream_t s);
+
 
 // f = f^eq(U(W)) for every cell; W is [K][N] of w_dtype (0 f64, 1 f32), conserved or primitive.
 cudaError_t launch_set_state(int lattice, int storage_f64, const void* W, int w_dtype, int kind, void* fs,

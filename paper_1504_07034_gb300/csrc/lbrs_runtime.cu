@@ -31,7 +31,7 @@ thread_local char g_err[512] = "";
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t f_bytes, f0, f1, ghost, partials, diag_out, scale, status, wait_flag, total;
+    size_t f_bytes, f0, f1, ghost, partials, diag_out, scale, status, wait_flag, adapt, total;
 };
 
 bool two_d(int lat) { return lat == LBRS_D2Q4 || lat == LBRS_D2Q4S; }
@@ -68,6 +68,8 @@ Layout layout_of(const lbrs_config* c)
     off += align_up(4 * sizeof(double));
     L.wait_flag = off;                               // set by a bounded device wait that gave up
     off += align_up(sizeof(unsigned));
+    L.adapt = off;                                   // the adaptive-lambda run's record
+    off += align_up(sizeof(AdaptState));
     L.total = off;
     return L;
 }
@@ -91,6 +93,9 @@ struct lbrs_ctx {
     cudaGraphExec_t graph[2];
     TileMap tmap[2];         // tensor maps of the two state buffers (FP32 D2Q4 two-step kernel)
     const uint8_t* solid;    // caller-owned obstacle mask [ny][nx] (lbrs_set_obstacles), or NULL
+    GhostSpec gspec;         // the sides' kinds and states (the adaptive run rebuilds the ghosts)
+    bool adapt_ready;        // the adaptive record holds the current state's run
+    bool adapt_used;         // the distributions carry an adaptive lambda
     // checkpointed adjoint: the run recorded by lbrs_forward_checkpointed
     char* adj_ws;
     size_t adj_bytes;
@@ -293,9 +298,16 @@ cudaError_t periodic_check(lbrs_ctx* ctx)
     return launch_status_update(dout, (double*)(ctx->ws + ctx->L.status), ctx->step, ctx->stream);
 }
 
-// A new state clears the record of the periodic checks and the wait flag.
+// A new state clears the record of the periodic checks and the wait flag, and ends an
+// adaptive-lambda run (the ghosts return to the configured lambda).
 lbrs_status reset_status(lbrs_ctx* ctx)
 {
+    if (ctx->adapt_used) {
+        LBRS_CUDA(ctx, launch_ghost(lat_code(ctx->lattice), ctx->f64, ctx->gspec, ctx->cfg.gamma, ctx->c,
+                                    ctx->ws + ctx->L.ghost, ctx->stream));
+        ctx->launches += 1;
+    }
+    ctx->adapt_ready = ctx->adapt_used = false;
     LBRS_CUDA(ctx, launch_status_reset((double*)(ctx->ws + ctx->L.status), ctx->stream));
     LBRS_CUDA(ctx, cudaMemsetAsync(wait_flag(ctx), 0, sizeof(unsigned), ctx->stream));
     ctx->launches += 1;
@@ -536,6 +548,7 @@ lbrs_status lbrs_create(const lbrs_config* cfg, void* d_workspace, size_t bytes,
         g.kind[s] = cfg->bc[s].kind;
         for (int k = 0; k < 4; ++k) g.prim[s][k] = cfg->bc[s].prim[k];
     }
+    ctx->gspec = g;
     const int lat = lat_code(cfg->lattice);
     cudaError_t e = launch_ghost(lat, ctx->f64, g, cfg->gamma, ctx->c, ctx->ws + L.ghost, ctx->stream);
     if (e != cudaSuccess) {
@@ -606,6 +619,9 @@ lbrs_status lbrs_step(lbrs_ctx* ctx, int64_t n)
     if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
     if (n < 0) return fail(ctx, LBRS_EINVAL, "negative step count");
     if (!ctx->has_state) return fail(ctx, LBRS_ESTATE, "no state set");
+    if (ctx->adapt_used)
+        return fail(ctx, LBRS_ESTATE, "the distributions carry an adaptive lambda: continue with "
+                                      "lbrs_step_adaptive or set a state");
     const int64_t every = ctx->cfg.diag_every;
     if (every <= 0) return step_plain(ctx, n);
     // run to each multiple of diag_every, check there
@@ -766,6 +782,62 @@ lbrs_status lbrs_set_obstacles(lbrs_ctx* ctx, const uint8_t* d_solid)
             ctx->graph[b] = nullptr;
         }
     ctx->solid = d_solid;
+    return LBRS_OK;
+}
+
+lbrs_status lbrs_step_adaptive(lbrs_ctx* ctx, int64_t n, double safety, double t_final)
+{
+    if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
+    if (n < 0) return fail(ctx, LBRS_EINVAL, "negative step count");
+    if (ctx->lattice != LBRS_D2Q4 || ctx->f16 || ctx->f32u || ctx->solid)
+        return fail(ctx, LBRS_EINVAL, "the adaptive lambda covers the F64 and F32 D2Q4 forms without internal walls");
+    if (!(safety >= 1.0) || !isfinite(safety)) return fail(ctx, LBRS_EINVAL, "safety must be >= 1");
+    if (!(t_final >= 0.0) || !isfinite(t_final)) return fail(ctx, LBRS_EINVAL, "t_final must be >= 0");
+    if (!ctx->has_state) return fail(ctx, LBRS_ESTATE, "no state set");
+    void* st = ctx->ws + ctx->L.adapt;
+    if (!ctx->adapt_ready) {
+        if (t_final > 0.0 && ctx->cfg.dx / ctx->cfg.lambda > t_final)
+            return fail(ctx, LBRS_EINVAL, "the first step alone (dx / lambda) passes t_final");
+        LBRS_CUDA(ctx, launch_adapt_reset(st, ctx->cfg.lambda, ctx->stream));
+        if (ctx->f64)
+            LBRS_CUDA(ctx, launch_adapt_init_bound_f64(ctx->f[ctx->cur], ctx->N, ctx->cfg.gamma, st, ctx->stream));
+        else
+            LBRS_CUDA(ctx, launch_adapt_init_bound_f32(ctx->f[ctx->cur], ctx->N, ctx->cfg.gamma, st, ctx->stream));
+        ctx->launches += 2;
+        ctx->adapt_ready = true;
+    }
+    ctx->adapt_used = true;
+    for (int64_t m = 0; m < n; ++m) {
+        LBRS_CUDA(ctx, launch_adapt_prep(ctx->f64, st, ctx->ws + ctx->L.ghost, ctx->gspec, ctx->cfg.gamma,
+                                         ctx->cfg.dx, safety, t_final, ctx->stream));
+        if (ctx->f64)
+            LBRS_CUDA(ctx, launch_adapt_step_f64(step_args<double>(ctx, ctx->cur), st, ctx->cfg.gamma, ctx->stream));
+        else
+            LBRS_CUDA(ctx, launch_adapt_step_f32(step_args<float>(ctx, ctx->cur), st, ctx->cfg.gamma, ctx->stream));
+        ctx->cur ^= 1;
+        ctx->step += 1;
+        ctx->launches += 2;
+    }
+    return LBRS_OK;
+}
+
+lbrs_status lbrs_adaptive_state(lbrs_ctx* ctx, double* t, double* lambda, int64_t* steps, int* done)
+{
+    if (!ctx || !t || !lambda || !steps || !done) return fail(ctx, LBRS_EINVAL, "NULL argument");
+    if (!ctx->adapt_ready) {
+        *t = 0.0;
+        *lambda = ctx->cfg.lambda;
+        *steps = 0;
+        *done = 0;
+        return LBRS_OK;
+    }
+    AdaptState h;
+    LBRS_CUDA(ctx, cudaMemcpyAsync(&h, ctx->ws + ctx->L.adapt, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+    LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    *t = h.t;
+    *lambda = h.lam_cur;
+    *steps = h.steps;
+    *done = h.done;
     return LBRS_OK;
 }
 

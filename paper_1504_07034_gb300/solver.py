@@ -183,6 +183,25 @@ class Solver:
         self._check(self.lib.lbrs_set_distributions(self.ctx, ctypes.c_void_p(f.data_ptr()), 1 if f.is_cuda else 0,
                                                     int(step)))
 
+    def step_adaptive(self, n: int, safety: float = 1.0, t_final: float = 0.0):
+        """n steps with the lattice speed chosen anew every step (see lbrs_step_adaptive)."""
+        self._check(self.lib.lbrs_step_adaptive(self.ctx, int(n), float(safety), float(t_final)))
+
+    def adaptive_state(self) -> dict:
+        t, lam, steps, done = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64(), ctypes.c_int()
+        self._check(self.lib.lbrs_adaptive_state(self.ctx, ctypes.byref(t), ctypes.byref(lam), ctypes.byref(steps),
+                                                 ctypes.byref(done)))
+        return {"t": t.value, "lambda": lam.value, "steps": steps.value, "done": bool(done.value)}
+
+    def run_to_time(self, t_final: float, safety: float = 1.0, chunk: int = 64, max_steps: int = 10 ** 8) -> dict:
+        """Adaptive steps until t_final is reached exactly, enqueued `chunk` at a time (one
+        synchronisation per chunk); returns the adaptive state at the end."""
+        st = self.adaptive_state()
+        while not st["done"] and st["steps"] < max_steps:
+            self.step_adaptive(chunk, safety, t_final)
+            st = self.adaptive_state()
+        return st
+
     def set_obstacles(self, solid):
         """Internal walls from a (ny, nx) mask (nonzero = solid cell); None removes them.
         The mask is kept on the device for the solver's lifetime (the library reads it
