@@ -159,9 +159,17 @@ def oracle_sample(wl, seconds=12.0):
     fs, t1 = o.timed_run(fs, 2)
     n = max(2, min(wl.steps, int(seconds / max(t1 / 2, 1e-6))))
     _, t = o.timed_run(fs, n)
-    return {"value": wl.cells * n / t / 1e6, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": f"FP64 C oracle, full {wl.nx}x{wl.ny} grid, steps 3..{n + 2} of the 1000-step run "
-                      f"({t:.1f} s, OpenMP over rows)"}
+    out = {"value": wl.cells * n / t / 1e6, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+           "sample": f"FP64 C oracle, full {wl.nx}x{wl.ny} grid, steps 3..{n + 2} of the 1000-step run "
+                     f"({t:.1f} s, OpenMP over rows)"}
+    # the same oracle on one thread, a few steps of the same run
+    o1 = oracle.Oracle.from_workload(wl, nthreads=1)
+    _, t1 = o1.timed_run(fs, 1)
+    n1 = max(1, min(wl.steps, int(0.4 * seconds / max(t1, 1e-6))))
+    _, t1 = o1.timed_run(fs, n1)
+    out["single_thread"] = {"value": wl.cells * n1 / t1 / 1e6, "unit": UNIT, "cores": 1,
+                            "sample": f"{n1} steps of the same grid ({t1:.1f} s)"}
+    return out
 
 
 def run_reference(args):

@@ -96,6 +96,8 @@ struct lbrs_ctx {
     GhostSpec gspec;         // the sides' kinds and states (the adaptive run rebuilds the ghosts)
     bool adapt_ready;        // the adaptive record holds the current state's run
     bool adapt_used;         // the distributions carry an adaptive lambda
+    cudaGraphExec_t agraph[2];   // kAdaptGraphSteps adaptive steps from buffer b
+    double agraph_key[2];        // (safety, t_final) the adaptive graphs were captured with
     // checkpointed adjoint: the run recorded by lbrs_forward_checkpointed
     char* adj_ws;
     size_t adj_bytes;
@@ -572,8 +574,10 @@ lbrs_status lbrs_create(const lbrs_config* cfg, void* d_workspace, size_t bytes,
 void lbrs_destroy(lbrs_ctx* ctx)
 {
     if (!ctx) return;
-    for (int b = 0; b < 2; ++b)
+    for (int b = 0; b < 2; ++b) {
         if (ctx->graph[b]) cudaGraphExecDestroy(ctx->graph[b]);
+        if (ctx->agraph[b]) cudaGraphExecDestroy(ctx->agraph[b]);
+    }
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     free(ctx);
 }
@@ -785,6 +789,56 @@ lbrs_status lbrs_set_obstacles(lbrs_ctx* ctx, const uint8_t* d_solid)
     return LBRS_OK;
 }
 
+// One adaptive step from the current buffer on stream s (a prep launch and a step launch).
+static cudaError_t launch_adapt_pair(lbrs_ctx* ctx, int from, double safety, double t_final, cudaStream_t s)
+{
+    void* st = ctx->ws + ctx->L.adapt;
+    cudaError_t e = launch_adapt_prep(ctx->f64, st, ctx->ws + ctx->L.ghost, ctx->gspec, ctx->cfg.gamma, ctx->cfg.dx,
+                                      safety, t_final, s);
+    if (e != cudaSuccess) return e;
+    if (ctx->f64) return launch_adapt_step_f64(step_args<double>(ctx, from), st, ctx->cfg.gamma, s);
+    return launch_adapt_step_f32(step_args<float>(ctx, from), st, ctx->cfg.gamma, s);
+}
+
+constexpr int kAdaptGraphSteps = 32;   // even: a graph returns the buffers to their parity
+
+// The graph of kAdaptGraphSteps adaptive steps from buffer `from` for (safety, t_final).
+static lbrs_status ensure_adapt_graph(lbrs_ctx* ctx, int from, double safety, double t_final)
+{
+    if (ctx->agraph[from] && ctx->agraph_key[0] == safety && ctx->agraph_key[1] == t_final) return LBRS_OK;
+    if (ctx->agraph_key[0] != safety || ctx->agraph_key[1] != t_final) {
+        for (int b = 0; b < 2; ++b)
+            if (ctx->agraph[b]) {
+                cudaGraphExecDestroy(ctx->agraph[b]);
+                ctx->agraph[b] = nullptr;
+            }
+        ctx->agraph_key[0] = safety;
+        ctx->agraph_key[1] = t_final;
+    }
+    if (!ctx->cap_stream) LBRS_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    LBRS_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t le = cudaSuccess;
+    int b = from;
+    for (int m = 0; m < kAdaptGraphSteps && le == cudaSuccess; ++m) {
+        le = launch_adapt_pair(ctx, b, safety, t_final, ctx->cap_stream);
+        b ^= 1;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(ctx->cap_stream, &g);
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(ctx, le, "adaptive step launch during graph capture");
+    }
+    if (ee != cudaSuccess) return cuda_fail(ctx, ee, "cudaStreamEndCapture");
+    cudaError_t ie = cudaGraphInstantiate(&ctx->agraph[from], g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+        ctx->agraph[from] = nullptr;
+        return cuda_fail(ctx, ie, "cudaGraphInstantiate");
+    }
+    return LBRS_OK;
+}
+
 lbrs_status lbrs_step_adaptive(lbrs_ctx* ctx, int64_t n, double safety, double t_final)
 {
     if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
@@ -807,13 +861,20 @@ lbrs_status lbrs_step_adaptive(lbrs_ctx* ctx, int64_t n, double safety, double t
         ctx->adapt_ready = true;
     }
     ctx->adapt_used = true;
-    for (int64_t m = 0; m < n; ++m) {
-        LBRS_CUDA(ctx, launch_adapt_prep(ctx->f64, st, ctx->ws + ctx->L.ghost, ctx->gspec, ctx->cfg.gamma,
-                                         ctx->cfg.dx, safety, t_final, ctx->stream));
-        if (ctx->f64)
-            LBRS_CUDA(ctx, launch_adapt_step_f64(step_args<double>(ctx, ctx->cur), st, ctx->cfg.gamma, ctx->stream));
-        else
-            LBRS_CUDA(ctx, launch_adapt_step_f32(step_args<float>(ctx, ctx->cur), st, ctx->cfg.gamma, ctx->stream));
+    int64_t left = n;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    LBRS_CUDA(ctx, cudaStreamIsCapturing(ctx->stream, &cap));
+    if (cap == cudaStreamCaptureStatusNone && n >= kAdaptGraphSteps) {
+        lbrs_status gs = ensure_adapt_graph(ctx, ctx->cur, safety, t_final);
+        if (gs != LBRS_OK) return gs;
+        for (; left >= kAdaptGraphSteps; left -= kAdaptGraphSteps) {
+            LBRS_CUDA(ctx, cudaGraphLaunch(ctx->agraph[ctx->cur], ctx->stream));
+            ctx->step += kAdaptGraphSteps;
+            ctx->launches += 2 * kAdaptGraphSteps;
+        }
+    }
+    for (; left > 0; --left) {
+        LBRS_CUDA(ctx, launch_adapt_pair(ctx, ctx->cur, safety, t_final, ctx->stream));
         ctx->cur ^= 1;
         ctx->step += 1;
         ctx->launches += 2;

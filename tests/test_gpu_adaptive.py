@@ -43,7 +43,7 @@ def gpu_adaptive(wl, precision, safety, t_final, nsteps):
     s = Solver.from_workload(wl, precision=precision)
     s.set_state(torch.from_numpy(wl.prim).cuda())
     if t_final > 0:
-        st = s.run_to_time(t_final, safety, chunk=16)
+        st = s.run_to_time(t_final, safety, chunk=40)   # a 32-step graph and 8 single steps per chunk
     else:
         s.step_adaptive(nsteps, safety)
         st = s.adaptive_state()
