@@ -414,6 +414,24 @@ template <bool STORE_U>
 __device__ __forceinline__ void step2_phase1_raw(const StepArgs<float>& a, const float* s_raw, float* s_f, int i0,
                                                  int j0)
 {
+    if (i0 >= 2 && j0 >= 2 && i0 + kFTX + 2 <= a.nx && j0 + kFTY + 2 <= a.ny) {
+        // every window slot is an interior cell (the whole block takes this branch):
+        // all pulls come from the copied boxes
+        for (int w = threadIdx.x; w < kFWN; w += kFTX * kFTY) {
+            const int wi = w % kFWX, wj = w / kFWX;
+            const int b = wj * kPX + wi;
+            const int r[4] = {b, b + 2, b + 2, b};
+            float f[4][4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) f[q][k] = s_raw[(q * 4 + k) * kPN + r[q]];
+            float U[4], out[4][4];
+            collide_2d<float>(a, f, U, out);
+            step2_store_slot<STORE_U>(a, s_f, w, wi, wj, i0, j0, U, out);
+        }
+        return;
+    }
     const bool px = a.bc[0] == BC_PERIODIC, py = a.bc[2] == BC_PERIODIC;
     for (int w = threadIdx.x; w < kFWN; w += kFTX * kFTY) {
         const int wi = w % kFWX, wj = w / kFWX;

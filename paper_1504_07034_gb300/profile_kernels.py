@@ -68,6 +68,24 @@ def obstacles():
     return _timed(lambda: [s.step(1) for _ in range(wl.steps)])
 
 
+def burgers():
+    """The scalar D2Q4 lattice on case 1 of the 2-D Burgers problems, 4096 x 4096 FP32, 10 steps."""
+    from .solver import Solver
+    wl = workloads.burgers_2d(1, 4096, steps=10)
+    s = Solver.from_workload(wl, precision="f32")
+    s.set_state(torch.from_numpy(wl.prim).cuda())
+    return _timed(lambda: [s.step(1) for _ in range(wl.steps)])
+
+
+def adaptive():
+    """Adaptive lambda on the 1024 x 1024 quadrant problem in FP32, 10 single adaptive steps."""
+    from .solver import Solver
+    wl = workloads.quadrant_riemann(0, 1024, steps=0)
+    s = Solver.from_workload(wl, precision="f32")
+    s.set_state(torch.from_numpy(wl.prim).cuda())
+    return _timed(lambda: [s.step_adaptive(1, 1.05) for _ in range(10)])
+
+
 def adjoint():
     from .solver import Solver
     wl, target = workloads.adjoint_pulses(seed=0, n=1024, steps=0)
@@ -100,8 +118,8 @@ def diagnostics():
     return _timed(lambda: [s.diagnostics() for _ in range(3)])
 
 
-CASES = {f.__name__: f for f in (step2d_f32, step2d_f32_flushed, step2d_f16neq, obstacles, adjoint, batch,
-                                 diagnostics)}
+CASES = {f.__name__: f for f in (step2d_f32, step2d_f32_flushed, step2d_f16neq, obstacles, burgers, adaptive,
+                                 adjoint, batch, diagnostics)}
 
 
 def main(argv):
