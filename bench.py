@@ -424,18 +424,57 @@ def batch_measurement(stream, barrier):
         b.record(stream)
         barrier()
         launches = s.launch_count - l0
+        rho32 = s.moments()[0].double()
+    stream.synchronize()
     t = a.elapsed_time(b) / 1e3
     lups = tb.total_updates
     s.close()
+    # per-tube density L1 of FP32 against the FP64 batch (which equals the FP64 oracle per tube)
+    s64 = BatchSolver.from_tubes(tb, precision="f64", stream=stream)
+    with torch.cuda.stream(stream):
+        s64.set_state(W0)
+        s64.run(tb.steps)
+        rho64 = s64.moments()[0].double()
+    stream.synchronize()
+    s64.close()
+    diff = (rho32 - rho64).abs().cpu().numpy()
+    off = np.concatenate([[0], np.cumsum(tb.lengths)])
+    l1 = np.array([diff[off[b]:off[b + 1]].mean() for b in range(len(tb.lengths))])
     return {"workload": "4096 D1Q2 shock tubes, N log-uniform in [200, 20000] (sum N = %d), seeded states, "
                         "t = 0.15, FP32" % tb.total_cells,
+            "l1_rho_f32_vs_f64_per_tube": {"max": float(l1.max()), "mean": float(l1.mean())},
             "lattice_updates": lups, "seconds": t, "value": lups / t / 1e6, "unit": UNIT,
             "effective_gbs_at_48_b_per_lup": 48 * lups / t / 1e9,
             "tuning": {"block": tuning[0], "cells_per_thread": tuning[1], "halo": tuning[2],
                        "autotune_ns_per_update": ns},
             "kernel_launches": launches,
+            "d1q3": batch_d1q3_measurement(stream, barrier),
             "note": "temporal blocking in shared memory: up to `halo` steps per launch, so the effective "
                     "48 B/LUP bandwidth can exceed the HBM peak"}
+
+
+def batch_d1q3_measurement(stream, barrier):
+    """The same 4096 tubes with the rest-particle model (lambda scaled by sqrt(3/2)), FP32."""
+    import torch
+    from paper_1504_07034_gb300.solver import BatchSolver
+    tb = workloads.batched_tubes(seed=0, count=4096, lattice="d1q3")
+    s = BatchSolver.from_tubes(tb, precision="f32", stream=stream)
+    W0 = torch.from_numpy(tb.prim()).cuda()
+    with torch.cuda.stream(stream):
+        s.set_state(W0)
+        tuning, _ = s.autotune(tb.steps)
+        s.run(tb.steps)
+        s.set_state(W0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        a.record(stream)
+        s.run(tb.steps)
+        b.record(stream)
+        barrier()
+    s.close()
+    t = a.elapsed_time(b) / 1e3
+    return {"lattice_updates": tb.total_updates, "seconds": t, "value": tb.total_updates / t / 1e6, "unit": UNIT,
+            "tuning": list(tuning), "effective_gbs_at_72_b_per_lup": 72 * tb.total_updates / t / 1e9}
 
 
 def adjoint_measurement(Solver, stream, barrier, n=2048, steps=2000):

@@ -321,15 +321,15 @@ lbrs_status lbrs_forward_checkpointed(lbrs_ctx* ctx, int64_t n_steps, int64_t se
  * context's state is the final forward state again on return. */
 lbrs_status lbrs_backward_checkpointed(lbrs_ctx* ctx, void* d_adj_ws, const void* d_gbar_T, void* d_gradU0);
 
-/* ---------------------------------------------------------------- batched D1Q2 tubes
+/* ---------------------------------------------------------------- batched D1Q2 / D1Q3 tubes
  *
  * Many independent 1-D problems (shock tubes) of uneven length advanced
  * together, each with its own lattice speed lambda_b and number of steps.
  * All tubes share gamma, omega and the end condition (transmissive or
  * periodic at both ends).  Distributions are stored concatenated:
  * f[q][k][off_b + x], off_b = sum of the lengths of the tubes before b;
- * field arrays are [3][sum N_b].  The step per cell is the D1Q2 step of
- * Section II.C, identical in arithmetic to the single-tube path; the
+ * field arrays are [3][sum N_b].  The step per cell is the D1Q2 (or D1Q3,
+ * cfg.lattice) step of Section II.C, identical in arithmetic to the single-tube path; the
  * kernels advance a tile of a tube by up to `halo` steps in shared memory per
  * launch (temporal blocking, see lbrs_batch_tuning). */
 typedef struct lbrs_batch lbrs_batch;
@@ -338,7 +338,7 @@ typedef struct {
     uint32_t struct_size;    /* = sizeof(lbrs_batch_config) */
     int32_t precision;       /* LBRS_F64 or LBRS_F32 */
     int32_t boundary;        /* LBRS_BC_TRANSMISSIVE or LBRS_BC_PERIODIC, both ends of every tube */
-    int32_t reserved0;
+    int32_t lattice;         /* LBRS_D1Q2 (0) or LBRS_D1Q3 (the rest particle; lambda per tube accordingly) */
     int64_t batch;           /* number of tubes, >= 1 */
     const int64_t* lengths;  /* host [batch]: cells per tube (>= 1); copied at create */
     const double* lambda;    /* host [batch]: lattice speed per tube (> 0); copied at create */

@@ -64,7 +64,7 @@ class lbrs_batch_config(ctypes.Structure):
         ("struct_size", ctypes.c_uint32),
         ("precision", ctypes.c_int32),
         ("boundary", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32),
+        ("lattice", ctypes.c_int32),
         ("batch", ctypes.c_int64),
         ("lengths", ctypes.POINTER(ctypes.c_int64)),
         ("lam", ctypes.POINTER(ctypes.c_double)),

@@ -1,9 +1,10 @@
-// Batched D1Q2 time steps for many independent shock tubes (device code).
+// Batched D1Q2 or D1Q3 time steps for many independent shock tubes (device code).
 //
 // Each tube b has its own length N_b, lattice speed lambda_b (c_b = 1/(2 lambda_b))
 // and number of steps; all share gamma, omega and the boundary kind
 // (transmissive or periodic at both ends).  The tubes are concatenated:
-// f[q][k][off_b + x], x in [0, N_b), plane stride N = sum N_b.
+// f[q][k][off_b + x], x in [0, N_b), plane stride N = sum N_b; Q = 2 (D1Q2) or 3
+// (D1Q3, the rest particle of Section II.C).
 //
 // Temporal blocking.  A launch advances every active tube by up to H steps.
 // One CTA owns a tile of TILE cells of one tube and stages the window
@@ -43,14 +44,16 @@ struct BatchArgs {
     int halo;                               // H
     int periodic;                           // 1: periodic tubes, 0: transmissive ends
     int launch;                             // index of this launch within the run
+    int q;                                  // 2 (D1Q2) or 3 (D1Q3)
     T om, om1, gm1;
 };
 
 // Window of W = TILE + 2H cells: W slots per (q, k) plane in shared memory, two
-// buffers of 6 planes.  BLOCK threads, each owning slots i = tid, tid + BLOCK, ...
-template <typename T, int BLOCK>
+// buffers of 3Q planes.  BLOCK threads, each owning slots i = tid, tid + BLOCK, ...
+template <typename T, int BLOCK, int Q>
 __global__ void __launch_bounds__(BLOCK) batch1d_kernel(const BatchArgs<T> a)
 {
+    constexpr int P = 3 * Q;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
     const int4 tile = __ldg(reinterpret_cast<const int4*>(a.tiles) + blockIdx.x);   // {tube, t0, len, pad}
@@ -73,7 +76,7 @@ __global__ void __launch_bounds__(BLOCK) batch1d_kernel(const BatchArgs<T> a)
         }
         if (x >= 0 && x < len) {
 #pragma unroll
-            for (int n = 0; n < 6; ++n) sm[n * W + i] = a.src[n * a.N + off + x];
+            for (int n = 0; n < P; ++n) sm[n * W + i] = a.src[n * a.N + off + x];
         }
     }
     __syncthreads();
@@ -84,27 +87,39 @@ __global__ void __launch_bounds__(BLOCK) batch1d_kernel(const BatchArgs<T> a)
     const int hi = a.periodic ? W : min(W, len - x0);
     int cur = 0;
     for (int s = 0; s < ns; ++s) {
-        const T* in = sm + cur * 6 * W;
-        T* out = sm + (cur ^ 1) * 6 * W;
+        const T* in = sm + cur * P * W;
+        T* out = sm + (cur ^ 1) * P * W;
         for (int i = lo + threadIdx.x; i < hi; i += BLOCK) {
             // velocity -1 pulls from i + 1, +1 from i - 1; at a tube end the
             // transmissive clamp returns the cell itself; at a window cut the
             // slot is stale anyway (outside the valid cone), clamp to stay in bounds
             const int ip = i + 1 < hi ? i + 1 : hi - 1;
             const int im = i - 1 >= lo ? i - 1 : lo;
-            T f[2][3];
+            // D1Q3: the rest population stays in its cell
+            T f[Q][3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 f[0][k] = in[k * W + ip];
-                f[1][k] = in[(3 + k) * W + im];
+                if constexpr (Q == 3) {
+                    f[1][k] = in[(3 + k) * W + i];
+                    f[2][k] = in[(6 + k) * W + im];
+                } else {
+                    f[1][k] = in[(3 + k) * W + im];
+                }
             }
             T U[3];
+            T e[Q][3];
+            if constexpr (Q == 3) {
 #pragma unroll
-            for (int k = 0; k < 3; ++k) U[k] = f[0][k] + f[1][k];
-            T e[2][3];
-            equilibria1d<T>(U, a.gm1, c, e);
+                for (int k = 0; k < 3; ++k) U[k] = (f[0][k] + f[1][k]) + f[2][k];
+                equilibria1d3<T>(U, a.gm1, c, e);
+            } else {
 #pragma unroll
-            for (int q = 0; q < 2; ++q)
+                for (int k = 0; k < 3; ++k) U[k] = f[0][k] + f[1][k];
+                equilibria1d<T>(U, a.gm1, c, e);
+            }
+#pragma unroll
+            for (int q = 0; q < Q; ++q)
 #pragma unroll
                 for (int k = 0; k < 3; ++k) out[(q * 3 + k) * W + i] = a.om1 * f[q][k] + a.om * e[q][k];
         }
@@ -112,12 +127,12 @@ __global__ void __launch_bounds__(BLOCK) batch1d_kernel(const BatchArgs<T> a)
         cur ^= 1;
     }
 
-    const T* fin = sm + cur * 6 * W;
+    const T* fin = sm + cur * P * W;
     for (int i = threadIdx.x; i < tlen; i += BLOCK) {
         const int slot = H + i;
         const int64_t g = off + t0 + i;
 #pragma unroll
-        for (int n = 0; n < 6; ++n) a.dst[n * a.N + g] = fin[n * W + slot];
+        for (int n = 0; n < P; ++n) a.dst[n * a.N + g] = fin[n * W + slot];
     }
 }
 
@@ -125,13 +140,12 @@ __global__ void __launch_bounds__(BLOCK) batch1d_kernel(const BatchArgs<T> a)
 // ended in the other ping-pong buffer).
 template <typename T>
 __global__ void batch_copy_kernel(const T* __restrict__ src, T* __restrict__ dst, int64_t N,
-                                  const BatchTile* __restrict__ tiles, const int64_t* __restrict__ tube_off)
+                                  const BatchTile* __restrict__ tiles, const int64_t* __restrict__ tube_off, int planes)
 {
     const int4 tile = __ldg(reinterpret_cast<const int4*>(tiles) + blockIdx.x);   // {tube, t0, len, pad}
     const int64_t base = tube_off[tile.x] + tile.y;
     for (int i = threadIdx.x; i < tile.z; i += blockDim.x)
-#pragma unroll
-        for (int n = 0; n < 6; ++n) dst[n * N + base + i] = src[n * N + base + i];
+        for (int n = 0; n < planes; ++n) dst[n * N + base + i] = src[n * N + base + i];
 }
 
 }  // namespace lbrs

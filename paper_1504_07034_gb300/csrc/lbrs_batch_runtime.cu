@@ -59,7 +59,7 @@ BLayout layout_of(const lbrs_batch_config* c)
     const size_t elem = c->precision == LBRS_F64 ? 8 : 4;
     const int64_t N = total_cells(c);
     L.max_tiles = N / kMinTile + c->batch + 1;
-    L.f_bytes = (size_t)N * 6 * elem;
+    L.f_bytes = (size_t)N * 3 * (c->lattice == LBRS_D1Q3 ? 3 : 2) * elem;
     size_t off = 0;
     L.f0 = off;
     off += align_up(L.f_bytes);
@@ -92,6 +92,7 @@ struct lbrs_batch {
     BLayout L;
     int64_t N;
     int f64;
+    int q;                   // populations per field: 2 (D1Q2) or 3 (D1Q3)
     char* ws;
     char* f[2];
     int cur;
@@ -135,6 +136,8 @@ lbrs_status validate(const lbrs_batch_config* c)
         return bfail(nullptr, LBRS_EINVAL, "config.struct_size %u != sizeof(lbrs_batch_config) %zu", c->struct_size,
                      sizeof(lbrs_batch_config));
     if (c->precision != LBRS_F64 && c->precision != LBRS_F32) return bfail(nullptr, LBRS_EINVAL, "unknown precision");
+    if (c->lattice != LBRS_D1Q2 && c->lattice != LBRS_D1Q3)
+        return bfail(nullptr, LBRS_EINVAL, "batched tubes are D1Q2 or D1Q3");
     if (c->boundary != LBRS_BC_TRANSMISSIVE && c->boundary != LBRS_BC_PERIODIC)
         return bfail(nullptr, LBRS_EINVAL, "batched tubes support transmissive or periodic ends");
     if (c->batch < 1 || c->batch > (1 << 30)) return bfail(nullptr, LBRS_EINVAL, "batch must be in [1, 2^30]");
@@ -166,12 +169,12 @@ constexpr size_t kMaxSmem = 227 * 1024;
 
 size_t smem_of(const lbrs_batch* B, const lbrs_batch_tuning& t)
 {
-    return 2 * 6 * (size_t)(tile_of(t) + 2 * t.halo) * (B->f64 ? 8 : 4);
+    return 2 * 3 * (size_t)B->q * (size_t)(tile_of(t) + 2 * t.halo) * (B->f64 ? 8 : 4);
 }
 
 cudaError_t prepare(const lbrs_batch* B, const lbrs_batch_tuning& t)
 {
-    return B->f64 ? prepare_batch_f64(t.block, smem_of(B, t)) : prepare_batch_f32(t.block, smem_of(B, t));
+    return B->f64 ? prepare_batch_f64(t.block, smem_of(B, t), B->q) : prepare_batch_f32(t.block, smem_of(B, t), B->q);
 }
 
 // Tubes ordered by decreasing steps (stable) and their tiles in that order.
@@ -220,6 +223,7 @@ BatchArgs<T> batch_args(const lbrs_batch* B, int from, const lbrs_batch_tuning& 
     a.halo = t.halo;
     a.periodic = B->cfg.boundary == LBRS_BC_PERIODIC;
     a.launch = launch;
+    a.q = B->q;
     a.om = (T)B->cfg.omega;
     a.om1 = (T)(1.0 - B->cfg.omega);
     a.gm1 = (T)(B->cfg.gamma - 1.0);
@@ -278,8 +282,8 @@ cudaError_t enqueue_run(lbrs_batch* B, const lbrs_batch_tuning& t, const std::ve
         void* dst = B->f[final_parity];
         const BatchTile* ct = (const BatchTile*)(B->ws + B->L.copy_tiles);
         const int64_t* off = (const int64_t*)(B->ws + B->L.tube_off);
-        return B->f64 ? launch_batch_copy_f64((const double*)src, (double*)dst, B->N, ct, ncopy, off, s)
-                      : launch_batch_copy_f32((const float*)src, (float*)dst, B->N, ct, ncopy, off, s);
+        return B->f64 ? launch_batch_copy_f64((const double*)src, (double*)dst, B->N, ct, ncopy, off, 3 * B->q, s)
+                      : launch_batch_copy_f32((const float*)src, (float*)dst, B->N, ct, ncopy, off, 3 * B->q, s);
     }
     return cudaSuccess;
 }
@@ -319,6 +323,7 @@ lbrs_status lbrs_batch_create(const lbrs_batch_config* cfg, void* d_workspace, s
     B->L = L;
     B->N = total_cells(cfg);
     B->f64 = cfg->precision == LBRS_F64;
+    B->q = cfg->lattice == LBRS_D1Q3 ? 3 : 2;
     B->ws = (char*)d_workspace;
     B->f[0] = B->ws + L.f0;
     B->f[1] = B->ws + L.f1;
@@ -386,7 +391,7 @@ lbrs_status lbrs_batch_set_state(lbrs_batch* B, const void* W, int on_device, in
     }
     BCUDA(B, launch_batch_set_state(B->f64, src, dtype == LBRS_F32, kind, B->f[B->cur], B->N,
                                     (const int64_t*)(B->ws + B->L.tube_off), B->cfg.batch,
-                                    (const double*)(B->ws + B->L.tube_lam), B->cfg.gamma, B->stream));
+                                    (const double*)(B->ws + B->L.tube_lam), B->cfg.gamma, B->q, B->stream));
     B->launches += 1;
     if (!on_device) BCUDA(B, cudaStreamSynchronize(B->stream));
     B->has_state = true;
@@ -535,7 +540,8 @@ lbrs_status lbrs_batch_moments(lbrs_batch* B, void* U_out, int on_device, int dt
     if (dtype != LBRS_F64 && dtype != LBRS_F32) return bfail(B, LBRS_EINVAL, "dtype must be LBRS_F64 or LBRS_F32");
     if (!B->has_state) return bfail(B, LBRS_ESTATE, "no state set");
     void* dst = on_device ? U_out : (void*)B->f[B->cur ^ 1];
-    BCUDA(B, launch_moments(LAT_D1Q2, B->f64, B->f[B->cur], dst, dtype == LBRS_F32, B->N, B->stream));
+    BCUDA(B, launch_moments(B->q == 3 ? LAT_D1Q3 : LAT_D1Q2, B->f64, B->f[B->cur], dst, dtype == LBRS_F32, B->N,
+                            B->stream));
     B->launches += 1;
     if (!on_device) {
         BCUDA(B, cudaMemcpyAsync(U_out, dst, (size_t)3 * B->N * (dtype == LBRS_F64 ? 8 : 4), cudaMemcpyDeviceToHost,

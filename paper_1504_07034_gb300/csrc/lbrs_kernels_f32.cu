@@ -846,19 +846,19 @@ cudaError_t launch_vjp_equilibrium_f32(const AdjArgs<float>& a, cudaStream_t s)
 
 // ---------------------------------------------------------------- batched tubes
 
-cudaError_t launch_batch_f32(const BatchArgs<float>& a, int ntiles, int block, cudaStream_t s)
+template <int Q>
+static cudaError_t launch_batch_q_f32(const BatchArgs<float>& a, int ntiles, int block, cudaStream_t s)
 {
-    if (ntiles <= 0) return cudaSuccess;
-    const size_t smem = 2 * 6 * (size_t)(a.tile_cells + 2 * a.halo) * sizeof(float);
+    const size_t smem = 2 * 3 * Q * (size_t)(a.tile_cells + 2 * a.halo) * sizeof(float);
     switch (block) {
         case 128:
-            batch1d_kernel<float, 128><<<ntiles, 128, smem, s>>>(a);
+            batch1d_kernel<float, 128, Q><<<ntiles, 128, smem, s>>>(a);
             break;
         case 256:
-            batch1d_kernel<float, 256><<<ntiles, 256, smem, s>>>(a);
+            batch1d_kernel<float, 256, Q><<<ntiles, 256, smem, s>>>(a);
             break;
         case 512:
-            batch1d_kernel<float, 512><<<ntiles, 512, smem, s>>>(a);
+            batch1d_kernel<float, 512, Q><<<ntiles, 512, smem, s>>>(a);
             break;
         default:
             return cudaErrorInvalidValue;
@@ -866,26 +866,38 @@ cudaError_t launch_batch_f32(const BatchArgs<float>& a, int ntiles, int block, c
     return cudaGetLastError();
 }
 
-cudaError_t prepare_batch_f32(int block, size_t smem)
+cudaError_t launch_batch_f32(const BatchArgs<float>& a, int ntiles, int block, cudaStream_t s)
+{
+    if (ntiles <= 0) return cudaSuccess;
+    return a.q == 3 ? launch_batch_q_f32<3>(a, ntiles, block, s) : launch_batch_q_f32<2>(a, ntiles, block, s);
+}
+
+template <int Q>
+static cudaError_t prepare_batch_q_f32(int block, size_t smem)
 {
     // opt in to more than the default 48 KiB of dynamic shared memory
     switch (block) {
         case 128:
-            return cudaFuncSetAttribute(batch1d_kernel<float, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            return cudaFuncSetAttribute(batch1d_kernel<float, 128, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         case 256:
-            return cudaFuncSetAttribute(batch1d_kernel<float, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            return cudaFuncSetAttribute(batch1d_kernel<float, 256, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         case 512:
-            return cudaFuncSetAttribute(batch1d_kernel<float, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            return cudaFuncSetAttribute(batch1d_kernel<float, 512, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         default:
             return cudaErrorInvalidValue;
     }
 }
 
+cudaError_t prepare_batch_f32(int block, size_t smem, int q)
+{
+    return q == 3 ? prepare_batch_q_f32<3>(block, smem) : prepare_batch_q_f32<2>(block, smem);
+}
+
 cudaError_t launch_batch_copy_f32(const float* src, float* dst, int64_t N, const BatchTile* tiles, int ntiles,
-                                     const int64_t* tube_off, cudaStream_t s)
+                                     const int64_t* tube_off, int planes, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
-    batch_copy_kernel<float><<<ntiles, 256, 0, s>>>(src, dst, N, tiles, tube_off);
+    batch_copy_kernel<float><<<ntiles, 256, 0, s>>>(src, dst, N, tiles, tube_off, planes);
     return cudaGetLastError();
 }
 

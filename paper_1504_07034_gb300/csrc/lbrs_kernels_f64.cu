@@ -337,7 +337,7 @@ template <typename Tin, typename Ts>
 __global__ void __launch_bounds__(kThreads) batch_set_state_kernel(const Tin* __restrict__ W, Ts* __restrict__ fs,
                                                                    int64_t N, int kind, double gamma,
                                                                    const int64_t* __restrict__ tube_off, int64_t nb,
-                                                                   const double* __restrict__ tube_lam)
+                                                                   const double* __restrict__ tube_lam, int q)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         int64_t lo = 0, hi = nb - 1;             // last tube with off <= i
@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(kThreads) batch_set_state_kernel(const Tin* __
             if (tube_off[mid] <= i) lo = mid; else hi = mid - 1;
         }
         const double c = 1.0 / (2.0 * tube_lam[lo]);
-        double w[3], U[3], e[6];
+        double w[3], U[3], e[9];
 #pragma unroll
         for (int k = 0; k < 3; ++k) w[k] = (double)W[k * N + i];
         if (kind == KIND_PRIMITIVE) {
@@ -355,9 +355,9 @@ __global__ void __launch_bounds__(kThreads) batch_set_state_kernel(const Tin* __
 #pragma unroll
             for (int k = 0; k < 3; ++k) U[k] = w[k];
         }
-        equilibria_flat<LAT_D1Q2>(U, gamma - 1.0, c, e);
-#pragma unroll
-        for (int n = 0; n < 6; ++n) fs[n * N + i] = (Ts)e[n];
+        if (q == 3) equilibria_flat<LAT_D1Q3>(U, gamma - 1.0, c, e);
+        else equilibria_flat<LAT_D1Q2>(U, gamma - 1.0, c, e);
+        for (int n = 0; n < 3 * q; ++n) fs[n * N + i] = (Ts)e[n];
     }
 }
 
@@ -458,16 +458,16 @@ cudaError_t launch_status_update(const double* diag_out, double* status, int64_t
 }
 
 cudaError_t launch_batch_set_state(int storage_f64, const void* W, int w_dtype, int kind, void* fs, int64_t N,
-                                   const int64_t* tube_off, int64_t nb, const double* tube_lam, double gamma,
+                                   const int64_t* tube_off, int64_t nb, const double* tube_lam, double gamma, int q,
                                    cudaStream_t s)
 {
     const int g = grid_for(N);
     if (storage_f64) {
-        if (w_dtype == 0) batch_set_state_kernel<double, double><<<g, kThreads, 0, s>>>((const double*)W, (double*)fs, N, kind, gamma, tube_off, nb, tube_lam);
-        else batch_set_state_kernel<float, double><<<g, kThreads, 0, s>>>((const float*)W, (double*)fs, N, kind, gamma, tube_off, nb, tube_lam);
+        if (w_dtype == 0) batch_set_state_kernel<double, double><<<g, kThreads, 0, s>>>((const double*)W, (double*)fs, N, kind, gamma, tube_off, nb, tube_lam, q);
+        else batch_set_state_kernel<float, double><<<g, kThreads, 0, s>>>((const float*)W, (double*)fs, N, kind, gamma, tube_off, nb, tube_lam, q);
     } else {
-        if (w_dtype == 0) batch_set_state_kernel<double, float><<<g, kThreads, 0, s>>>((const double*)W, (float*)fs, N, kind, gamma, tube_off, nb, tube_lam);
-        else batch_set_state_kernel<float, float><<<g, kThreads, 0, s>>>((const float*)W, (float*)fs, N, kind, gamma, tube_off, nb, tube_lam);
+        if (w_dtype == 0) batch_set_state_kernel<double, float><<<g, kThreads, 0, s>>>((const double*)W, (float*)fs, N, kind, gamma, tube_off, nb, tube_lam, q);
+        else batch_set_state_kernel<float, float><<<g, kThreads, 0, s>>>((const float*)W, (float*)fs, N, kind, gamma, tube_off, nb, tube_lam, q);
     }
     return cudaGetLastError();
 }
@@ -644,19 +644,19 @@ cudaError_t launch_diag(int lattice, int storage_f64, const void* fs, int64_t N,
 
 // ---------------------------------------------------------------- batched tubes
 
-cudaError_t launch_batch_f64(const BatchArgs<double>& a, int ntiles, int block, cudaStream_t s)
+template <int Q>
+static cudaError_t launch_batch_q_f64(const BatchArgs<double>& a, int ntiles, int block, cudaStream_t s)
 {
-    if (ntiles <= 0) return cudaSuccess;
-    const size_t smem = 2 * 6 * (size_t)(a.tile_cells + 2 * a.halo) * sizeof(double);
+    const size_t smem = 2 * 3 * Q * (size_t)(a.tile_cells + 2 * a.halo) * sizeof(double);
     switch (block) {
         case 128:
-            batch1d_kernel<double, 128><<<ntiles, 128, smem, s>>>(a);
+            batch1d_kernel<double, 128, Q><<<ntiles, 128, smem, s>>>(a);
             break;
         case 256:
-            batch1d_kernel<double, 256><<<ntiles, 256, smem, s>>>(a);
+            batch1d_kernel<double, 256, Q><<<ntiles, 256, smem, s>>>(a);
             break;
         case 512:
-            batch1d_kernel<double, 512><<<ntiles, 512, smem, s>>>(a);
+            batch1d_kernel<double, 512, Q><<<ntiles, 512, smem, s>>>(a);
             break;
         default:
             return cudaErrorInvalidValue;
@@ -664,26 +664,38 @@ cudaError_t launch_batch_f64(const BatchArgs<double>& a, int ntiles, int block, 
     return cudaGetLastError();
 }
 
-cudaError_t prepare_batch_f64(int block, size_t smem)
+cudaError_t launch_batch_f64(const BatchArgs<double>& a, int ntiles, int block, cudaStream_t s)
+{
+    if (ntiles <= 0) return cudaSuccess;
+    return a.q == 3 ? launch_batch_q_f64<3>(a, ntiles, block, s) : launch_batch_q_f64<2>(a, ntiles, block, s);
+}
+
+template <int Q>
+static cudaError_t prepare_batch_q_f64(int block, size_t smem)
 {
     // opt in to more than the default 48 KiB of dynamic shared memory
     switch (block) {
         case 128:
-            return cudaFuncSetAttribute(batch1d_kernel<double, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            return cudaFuncSetAttribute(batch1d_kernel<double, 128, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         case 256:
-            return cudaFuncSetAttribute(batch1d_kernel<double, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            return cudaFuncSetAttribute(batch1d_kernel<double, 256, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         case 512:
-            return cudaFuncSetAttribute(batch1d_kernel<double, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            return cudaFuncSetAttribute(batch1d_kernel<double, 512, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         default:
             return cudaErrorInvalidValue;
     }
 }
 
+cudaError_t prepare_batch_f64(int block, size_t smem, int q)
+{
+    return q == 3 ? prepare_batch_q_f64<3>(block, smem) : prepare_batch_q_f64<2>(block, smem);
+}
+
 cudaError_t launch_batch_copy_f64(const double* src, double* dst, int64_t N, const BatchTile* tiles, int ntiles,
-                                     const int64_t* tube_off, cudaStream_t s)
+                                     const int64_t* tube_off, int planes, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
-    batch_copy_kernel<double><<<ntiles, 256, 0, s>>>(src, dst, N, tiles, tube_off);
+    batch_copy_kernel<double><<<ntiles, 256, 0, s>>>(src, dst, N, tiles, tube_off, planes);
     return cudaGetLastError();
 }
 

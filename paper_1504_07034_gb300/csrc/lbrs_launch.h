@@ -98,21 +98,21 @@ cudaError_t launch_density_loss(int Q, int K, int storage_f64, const void* fs, c
                                 void* gbar, int64_t N, double cell_volume, double* partials, double* out,
                                 cudaStream_t s);
 
-// Batched D1Q2 tubes with temporal blocking (lbrs_batch.cuh): one CTA of
-// `block` threads per active tile; dynamic shared memory 2*6*(TILE+2H) elements.
+// Batched D1Q2 / D1Q3 tubes with temporal blocking (lbrs_batch.cuh): one CTA of
+// `block` threads per active tile; dynamic shared memory 2*3Q*(TILE+2H) elements.
 cudaError_t launch_batch_f64(const BatchArgs<double>& a, int ntiles, int block, cudaStream_t s);
 cudaError_t launch_batch_f32(const BatchArgs<float>& a, int ntiles, int block, cudaStream_t s);
 // Raise the kernel's dynamic shared-memory limit to smem bytes (call before launching or capturing).
-cudaError_t prepare_batch_f64(int block, size_t smem);
-cudaError_t prepare_batch_f32(int block, size_t smem);
+cudaError_t prepare_batch_f64(int block, size_t smem, int q);
+cudaError_t prepare_batch_f32(int block, size_t smem, int q);
 cudaError_t launch_batch_copy_f64(const double* src, double* dst, int64_t N, const BatchTile* tiles, int ntiles,
-                                  const int64_t* tube_off, cudaStream_t s);
+                                  const int64_t* tube_off, int planes, cudaStream_t s);
 cudaError_t launch_batch_copy_f32(const float* src, float* dst, int64_t N, const BatchTile* tiles, int ntiles,
-                                  const int64_t* tube_off, cudaStream_t s);
+                                  const int64_t* tube_off, int planes, cudaStream_t s);
 
 // Batched tubes: f = f^eq(U(W)) with each cell's tube lambda (bisection in tube_off).
 cudaError_t launch_batch_set_state(int storage_f64, const void* W, int w_dtype, int kind, void* fs, int64_t N,
-                                   const int64_t* tube_off, int64_t nb, const double* tube_lam, double gamma,
+                                   const int64_t* tube_off, int64_t nb, const double* tube_lam, double gamma, int q,
                                    cudaStream_t s);
 
 // FP16 non-equilibrium form (lbrs_kernels_f16.cu).  A state buffer holds U as

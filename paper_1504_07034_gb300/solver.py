@@ -311,8 +311,10 @@ class BatchSolver:
     """
 
     def __init__(self, lengths, lam, *, gamma: float = 1.4, omega: float = 1.0, boundary: str = "transmissive",
-                 precision: str = "f32", stream: torch.cuda.Stream | None = None):
+                 precision: str = "f32", stream: torch.cuda.Stream | None = None, lattice: str = "d1q2"):
         self.lib = abi.load()
+        self.lattice = lattice
+        self.Q = {"d1q2": 2, "d1q3": 3}[lattice]
         self.lengths = np.ascontiguousarray(lengths, dtype=np.int64)
         self.lam = np.ascontiguousarray(lam, dtype=np.float64)
         self.batch = len(self.lengths)
@@ -325,6 +327,7 @@ class BatchSolver:
         cfg.struct_size = ctypes.sizeof(abi.lbrs_batch_config)
         cfg.precision = _PRECISION[precision]
         cfg.boundary = abi.BC_KINDS[boundary]
+        cfg.lattice = abi.LBRS_D1Q3 if lattice == "d1q3" else abi.LBRS_D1Q2
         cfg.batch = self.batch
         cfg.lengths = self.lengths.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
         cfg.lam = self.lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
@@ -340,9 +343,9 @@ class BatchSolver:
         self.ctx = ctx
 
     @classmethod
-    def from_tubes(cls, tubes, precision: str = "f32", stream=None):
+    def from_tubes(cls, tubes, precision: str = "f32", stream=None, lattice: str | None = None):
         return cls(tubes.lengths, tubes.lam, gamma=tubes.gamma, omega=tubes.omega, precision=precision,
-                   stream=stream)
+                   stream=stream, lattice=lattice or getattr(tubes, "lattice", "d1q2"))
 
     @property
     def storage_dtype(self):
@@ -378,7 +381,7 @@ class BatchSolver:
         return out
 
     def get_distributions(self) -> torch.Tensor:
-        out = torch.empty((2, 3, self.N), dtype=self.storage_dtype, device=self.device)
+        out = torch.empty((self.Q, 3, self.N), dtype=self.storage_dtype, device=self.device)
         self._check(self.lib.lbrs_batch_get_distributions(self.ctx, ctypes.c_void_p(out.data_ptr()), 1))
         return out
 

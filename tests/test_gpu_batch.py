@@ -148,3 +148,58 @@ def test_full_size_batch_sampled_against_oracle():
         worst = max(worst, l1)
         assert l1 <= 1e-5, (b, l1)
     print(f"4096 tubes: worst sampled density L1 vs FP64 oracle {worst:.2e}")
+
+
+# ------------------------------------------------------------------- batched D1Q3
+
+def run_batch_q3(tb, steps, precision, tuning=None, boundary="transmissive", prim=None):
+    from paper_1504_07034_gb300.solver import BatchSolver
+    s = BatchSolver(tb.lengths, tb.lam, gamma=tb.gamma, omega=tb.omega, boundary=boundary, precision=precision,
+                    lattice="d1q3")
+    if tuning:
+        s.tuning = tuning
+    s.set_state(torch.from_numpy(tb.prim() if prim is None else prim).cuda())
+    s.run(steps)
+    U = s.moments().cpu().numpy()
+    f = s.get_distributions()
+    assert tuple(f.shape) == (3, 3, tb.total_cells)
+    s.close()
+    return U
+
+
+def oracle_tube_q3(tb, b, steps, prim_all, offsets, boundary="transmissive"):
+    n = int(tb.lengths[b])
+    o = oracle.Oracle(oracle.D1Q3, n, lam=float(tb.lam[b]), omega=tb.omega, gamma=tb.gamma,
+                      bc=[(boundary, None)] * 2)
+    fs, _ = o.run(o.init(o.prim_to_cons(prim_all[:, offsets[b]:offsets[b] + n])), int(steps))
+    return o.moments(fs)
+
+
+@pytest.mark.parametrize("tuning", [None, (128, 1, 8), (512, 2, 64)])
+@pytest.mark.parametrize("boundary", ["transmissive", "periodic"])
+def test_f64_batched_d1q3_matches_oracle_per_tube(tuning, boundary):
+    """The rest-particle model (Section II.C) in the batched kernel: each tube as a lone D1Q3 tube."""
+    tb = W.batched_tubes(seed=4, count=17, n_min=1, n_max=500, t_final=0.1, omega=0.9, lattice="d1q3")
+    rng = np.random.default_rng(4)
+    steps = rng.integers(0, 250, size=17)
+    prim = tb.prim()
+    if boundary == "periodic":
+        tb.lam = tb.lam * 1.5
+    U = run_batch_q3(tb, steps, "f64", tuning, boundary, prim)
+    off = np.concatenate([[0], np.cumsum(tb.lengths)[:-1]])
+    for b in range(len(tb.lengths)):
+        ref = oracle_tube_q3(tb, b, steps[b], prim, off, boundary)
+        got = U[:, off[b]:off[b] + tb.lengths[b]]
+        err = np.max(np.abs(got - ref), axis=1) / np.max(np.abs(ref))
+        assert np.all(err <= 1e-12), (b, tb.lengths[b], steps[b], err)
+
+
+def test_f32_batched_d1q3_close_to_oracle():
+    tb = W.batched_tubes(seed=5, count=9, n_min=50, n_max=2000, t_final=0.15, lattice="d1q3")
+    U = run_batch_q3(tb, tb.steps, "f32", (256, 2, 16))
+    off = np.concatenate([[0], np.cumsum(tb.lengths)[:-1]])
+    prim = tb.prim()
+    for b in range(len(tb.lengths)):
+        ref = oracle_tube_q3(tb, b, tb.steps[b], prim, off)
+        got = U[:, off[b]:off[b] + tb.lengths[b]]
+        assert np.mean(np.abs(got[0] - ref[0])) <= 1e-6

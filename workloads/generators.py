@@ -85,6 +85,7 @@ class TubeBatch:
     t_final: float
     omega: float
     gamma: float = GAMMA
+    lattice: str = "d1q2"       # "d1q2" or "d1q3" (lambda scaled by LAMBDA_FACTOR)
 
     @property
     def total_cells(self) -> int:
@@ -216,12 +217,13 @@ def steady_shock(nx: int = 400, mach: float = 2.0, omega: float = 1.0, steps: in
 
 
 def batched_tubes(seed: int = 0, count: int = 4096, n_min: int = 200, n_max: int = 20000,
-                  t_final: float = 0.15, omega: float = 1.0) -> TubeBatch:
+                  t_final: float = 0.15, omega: float = 1.0, lattice: str = "d1q2") -> TubeBatch:
     """Seeded shock tubes on [0, 1] with log-uniform lengths.
 
     Left/right rho, p ~ U[0.05, 2], u ~ U[-1, 1]; a draw whose Riemann problem
     generates vacuum is replaced by the next draw.  Lambda per tube from its
-    exact solution, rounded so t_final is reached in a whole number of steps.
+    exact solution (times the lattice's factor), rounded so t_final is reached in
+    a whole number of steps.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     lengths = np.rint(np.exp(rng.uniform(math.log(n_min), math.log(n_max), size=count))).astype(np.int64)
@@ -238,8 +240,8 @@ def batched_tubes(seed: int = 0, count: int = 4096, n_min: int = 200, n_max: int
                 break
         left[b], right[b] = wl, wr
         dx = 1.0 / lengths[b]
-        lam[b], steps[b] = _round_lambda(lambda_1d_riemann(GAMMA, wl, wr), dx, t_final)
-    return TubeBatch(lengths, left, right, lam, steps, t_final, omega)
+        lam[b], steps[b] = _round_lambda(LAMBDA_FACTOR[lattice] * lambda_1d_riemann(GAMMA, wl, wr), dx, t_final)
+    return TubeBatch(lengths, left, right, lam, steps, t_final, omega, lattice=lattice)
 
 
 # --------------------------------------------------------------------------- 2-D
