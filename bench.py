@@ -492,10 +492,12 @@ def adjoint_measurement(Solver, stream, barrier, n=2048, steps=2000):
         _, g = s.vjp_loss(tgt)
         s.backward_checkpointed(g)
         s.set_state(W0)
+        tot0 = s.diagnostics()["totals"]
         barrier()
         ev[0].record(stream)
         s.forward_checkpointed(steps)
         ev[1].record(stream)
+        tot1 = s.diagnostics()["totals"]
         loss, g = s.vjp_loss(tgt)
         ev2 = torch.cuda.Event(enable_timing=True)
         ev2.record(stream)
@@ -543,8 +545,11 @@ def adjoint_measurement(Solver, stream, barrier, n=2048, steps=2000):
     stream.synchronize()
     s32.close()
     s64.close()
+    drift = [abs(b - a) / abs(a) for a, b in zip(tot0, tot1)]
     return {"workload": f"{n}x{n} periodic, uniform (1, 0.5, 0.3, 1) + 8 Gaussian pulses, {steps} FP32 steps, "
                         f"density L2 loss, sqrt(T) checkpointing (segment {math.ceil(math.sqrt(steps))})",
+            "conservation_drift_fp32_2000_steps": {"relative_change_of_totals": drift,
+                                                    "note": "periodic grid: mass, momentum and energy totals in FP64"},
             "forward_s": t_fwd, "backward_s": t_bwd, "backward_over_forward": t_bwd / t_fwd,
             "forward_mlups": n * n * steps / t_fwd / 1e6, "loss": loss, "grad_norm": gnorm,
             "fd_check_64x64": {"steps": fd_steps, "directions": 4,

@@ -256,6 +256,20 @@ lbrs_status lbrs_diagnostics_noalloc(const lbrs_config* cfg, const void* d_fs, l
 lbrs_status lbrs_get_distributions(lbrs_ctx* ctx, void* dst, int on_device);
 lbrs_status lbrs_set_distributions(lbrs_ctx* ctx, const void* src, int on_device, int64_t step);
 
+/* Checkpoints: a self-describing copy of the state, a 256-byte header (magic
+ * "LBRSCKP1", version 1; lattice, precision, grid, step, lambda, omega, gamma, dx,
+ * boundary kinds and states; the size of the distributions) followed by the raw
+ * distributions (the FP16 form's scales included).  lbrs_checkpoint_size gives the
+ * blob's bytes; save writes it to host or device memory and synchronises; load
+ * checks the header against the context's configuration (EINVAL on any difference
+ * or a foreign blob), restores the distributions and the step counter, and clears
+ * the record of the periodic checks (as setting a state does).  Resuming from a
+ * checkpoint is bit-identical to an uninterrupted run.  The state of an adaptive-
+ * lambda run is not covered (EINVAL). */
+lbrs_status lbrs_checkpoint_size(const lbrs_ctx* ctx, size_t* bytes);
+lbrs_status lbrs_checkpoint_save(lbrs_ctx* ctx, void* dst, int on_device);
+lbrs_status lbrs_checkpoint_load(lbrs_ctx* ctx, const void* src, int on_device);
+
 /* Lattice-aligned internal walls (obstacles such as the forward-facing step and the
  * backward-facing step of the shock-diffraction problem, Section III), D2Q4 in
  * LBRS_F64 or LBRS_F32.  d_solid: device mask [ny][nx] of uint8, nonzero = solid

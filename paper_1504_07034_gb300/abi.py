@@ -98,6 +98,9 @@ SIGNATURES = {
     "lbrs_get_distributions": (ctypes.c_int, [_CTX, _P, ctypes.c_int]),
     "lbrs_set_distributions": (ctypes.c_int, [_CTX, _P, ctypes.c_int, ctypes.c_int64]),
     "lbrs_set_obstacles": (ctypes.c_int, [_CTX, _P]),
+    "lbrs_checkpoint_size": (ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_size_t)]),
+    "lbrs_checkpoint_save": (ctypes.c_int, [_CTX, _P, ctypes.c_int]),
+    "lbrs_checkpoint_load": (ctypes.c_int, [_CTX, _P, ctypes.c_int]),
     "lbrs_step_adaptive": (ctypes.c_int, [_CTX, ctypes.c_int64, ctypes.c_double, ctypes.c_double]),
     "lbrs_adaptive_state": (ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int)]),

@@ -417,6 +417,7 @@ lbrs_status lbrs_batch_set_tuning(lbrs_batch* B, const lbrs_batch_tuning* t)
 
 lbrs_status lbrs_batch_run(lbrs_batch* B, const int64_t* steps)
 {
+    NvtxRange range("lbrs_batch_run");
     if (!B) return bfail(nullptr, LBRS_EINVAL, "batch is NULL");
     if (!steps) return bfail(B, LBRS_EINVAL, "steps is NULL");
     if (!B->has_state) return bfail(B, LBRS_ESTATE, "no state set");

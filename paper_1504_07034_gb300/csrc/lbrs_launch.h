@@ -8,6 +8,19 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <nvtx3/nvToolsExt.h>
+
+namespace lbrs {
+// A named range on the profiler's host timeline for the enclosing scope (header-only
+// NVTX: without an attached tool the calls do nothing).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+}  // namespace lbrs
+
 namespace lbrs {
 
 template <typename T>

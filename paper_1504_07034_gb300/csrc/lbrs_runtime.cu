@@ -620,6 +620,7 @@ static lbrs_status step_plain(lbrs_ctx* ctx, int64_t n);
 
 lbrs_status lbrs_step(lbrs_ctx* ctx, int64_t n)
 {
+    NvtxRange range("lbrs_step");
     if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
     if (n < 0) return fail(ctx, LBRS_EINVAL, "negative step count");
     if (!ctx->has_state) return fail(ctx, LBRS_ESTATE, "no state set");
@@ -841,6 +842,7 @@ static lbrs_status ensure_adapt_graph(lbrs_ctx* ctx, int from, double safety, do
 
 lbrs_status lbrs_step_adaptive(lbrs_ctx* ctx, int64_t n, double safety, double t_final)
 {
+    NvtxRange range("lbrs_step_adaptive");
     if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
     if (n < 0) return fail(ctx, LBRS_EINVAL, "negative step count");
     if (ctx->lattice != LBRS_D2Q4 || ctx->f16 || ctx->f32u || ctx->solid)
@@ -899,6 +901,113 @@ lbrs_status lbrs_adaptive_state(lbrs_ctx* ctx, double* t, double* lambda, int64_
     *lambda = h.lam_cur;
     *steps = h.steps;
     *done = h.done;
+    return LBRS_OK;
+}
+
+// ---------------------------------------------------------------- checkpoints
+
+namespace {
+// Header of a checkpoint blob; the raw distributions follow at kCkptHeader bytes.
+struct CkptHeader {
+    char magic[8];
+    uint32_t version;
+    int32_t lattice, precision;
+    int32_t bc_kind[4];
+    int32_t reserved;
+    int64_t nx, ny, step;
+    double lambda, omega, gamma, dx;
+    double bc_prim[4][4];
+    uint64_t f_bytes;
+};
+constexpr size_t kCkptHeader = 256;
+static_assert(sizeof(CkptHeader) <= kCkptHeader, "checkpoint header size");
+constexpr char kCkptMagic[8] = {'L', 'B', 'R', 'S', 'C', 'K', 'P', '1'};
+
+CkptHeader header_of(const lbrs_ctx* ctx)
+{
+    CkptHeader h;
+    memset(&h, 0, sizeof h);
+    memcpy(h.magic, kCkptMagic, sizeof h.magic);
+    h.version = 1;
+    h.lattice = ctx->cfg.lattice;
+    h.precision = ctx->cfg.precision;
+    for (int s = 0; s < 4; ++s) {
+        h.bc_kind[s] = ctx->cfg.bc[s].kind;
+        for (int k = 0; k < 4; ++k) h.bc_prim[s][k] = ctx->cfg.bc[s].prim[k];
+    }
+    h.nx = ctx->cfg.nx;
+    h.ny = ctx->cfg.ny;
+    h.step = ctx->step;
+    h.lambda = ctx->cfg.lambda;
+    h.omega = ctx->cfg.omega;
+    h.gamma = ctx->cfg.gamma;
+    h.dx = ctx->cfg.dx;
+    h.f_bytes = ctx->L.f_bytes;
+    return h;
+}
+}  // namespace
+
+lbrs_status lbrs_checkpoint_size(const lbrs_ctx* ctx, size_t* bytes)
+{
+    if (!ctx || !bytes) return fail(nullptr, LBRS_EINVAL, "NULL argument");
+    *bytes = kCkptHeader + ctx->L.f_bytes;
+    return LBRS_OK;
+}
+
+lbrs_status lbrs_checkpoint_save(lbrs_ctx* ctx, void* dst, int on_device)
+{
+    if (!ctx || !dst) return fail(ctx, LBRS_EINVAL, "NULL argument");
+    if (!ctx->has_state) return fail(ctx, LBRS_ESTATE, "no state set");
+    if (ctx->adapt_used) return fail(ctx, LBRS_EINVAL, "an adaptive run's state is not covered by checkpoints");
+    unsigned char head[kCkptHeader];
+    memset(head, 0, sizeof head);
+    const CkptHeader h = header_of(ctx);
+    memcpy(head, &h, sizeof h);
+    char* d = (char*)dst;
+    if (on_device) {
+        LBRS_CUDA(ctx, cudaMemcpyAsync(d, head, kCkptHeader, cudaMemcpyHostToDevice, ctx->stream));
+        LBRS_CUDA(ctx, cudaMemcpyAsync(d + kCkptHeader, ctx->f[ctx->cur], ctx->L.f_bytes, cudaMemcpyDeviceToDevice,
+                                       ctx->stream));
+        LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));   // the header's host copy goes out of scope
+    } else {
+        memcpy(d, head, kCkptHeader);
+        LBRS_CUDA(ctx, cudaMemcpyAsync(d + kCkptHeader, ctx->f[ctx->cur], ctx->L.f_bytes, cudaMemcpyDeviceToHost,
+                                       ctx->stream));
+        LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    return LBRS_OK;
+}
+
+lbrs_status lbrs_checkpoint_load(lbrs_ctx* ctx, const void* src, int on_device)
+{
+    if (!ctx || !src) return fail(ctx, LBRS_EINVAL, "NULL argument");
+    CkptHeader h;
+    const char* s = (const char*)src;
+    if (on_device) {
+        LBRS_CUDA(ctx, cudaMemcpyAsync(&h, s, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+        LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    } else {
+        memcpy(&h, s, sizeof h);
+    }
+    if (memcmp(h.magic, kCkptMagic, sizeof h.magic) != 0 || h.version != 1)
+        return fail(ctx, LBRS_EINVAL, "not a checkpoint of this library (magic or version)");
+    const CkptHeader want = header_of(ctx);
+    bool same = h.lattice == want.lattice && h.precision == want.precision && h.nx == want.nx && h.ny == want.ny &&
+                h.lambda == want.lambda && h.omega == want.omega && h.gamma == want.gamma && h.dx == want.dx &&
+                h.f_bytes == want.f_bytes;
+    for (int q = 0; q < 4 && same; ++q) {
+        same = h.bc_kind[q] == want.bc_kind[q];
+        for (int k = 0; k < 4 && same; ++k) same = h.bc_prim[q][k] == want.bc_prim[q][k];
+    }
+    if (!same) return fail(ctx, LBRS_EINVAL, "checkpoint of another configuration (grid, lattice, precision, "
+                                             "lambda, omega, gamma, dx or boundaries differ)");
+    LBRS_CUDA(ctx, cudaMemcpyAsync(ctx->f[ctx->cur], s + kCkptHeader, ctx->L.f_bytes,
+                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+    if (!on_device) LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->has_state = true;
+    ctx->step = h.step;
+    lbrs_status rs = reset_status(ctx);
+    if (rs != LBRS_OK) return rs;
     return LBRS_OK;
 }
 
@@ -1008,6 +1117,7 @@ lbrs_status lbrs_adjoint_workspace_size(const lbrs_ctx* ctx, int64_t n_steps, in
 
 lbrs_status lbrs_forward_checkpointed(lbrs_ctx* ctx, int64_t n_steps, int64_t segment, void* d_adj_ws, size_t bytes)
 {
+    NvtxRange range("lbrs_forward_checkpointed");
     if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
     lbrs_status st = adjoint_supported(ctx);
     if (st != LBRS_OK) return st;
@@ -1037,6 +1147,7 @@ lbrs_status lbrs_forward_checkpointed(lbrs_ctx* ctx, int64_t n_steps, int64_t se
 
 lbrs_status lbrs_backward_checkpointed(lbrs_ctx* ctx, void* d_adj_ws, const void* d_gbar_T, void* d_gradU0)
 {
+    NvtxRange range("lbrs_backward_checkpointed");
     if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
     if (!ctx->adj_ws || d_adj_ws != ctx->adj_ws)
         return fail(ctx, LBRS_ESTATE, "no checkpointed forward run recorded on this adjoint workspace");
@@ -1049,6 +1160,7 @@ lbrs_status lbrs_backward_checkpointed(lbrs_ctx* ctx, void* d_adj_ws, const void
     LBRS_CUDA(ctx, cudaMemcpyAsync(g[0], d_gbar_T, ctx->L.f_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
     int gc = 0;
     for (int64_t s = A.nseg - 1; s >= 0; --s) {
+        NvtxRange seg_range("adjoint segment");
         const int64_t start = s * ctx->adj_seg;
         const int64_t len = start + ctx->adj_seg <= ctx->adj_n ? ctx->adj_seg : ctx->adj_n - start;
         // recompute the segment from its checkpoint, recording U^{start+1 .. start+len}

@@ -183,6 +183,19 @@ class Solver:
         self._check(self.lib.lbrs_set_distributions(self.ctx, ctypes.c_void_p(f.data_ptr()), 1 if f.is_cuda else 0,
                                                     int(step)))
 
+    def checkpoint(self, device: bool = True) -> torch.Tensor:
+        """The state as a self-describing blob (uint8 tensor on the GPU, or in pinned host memory)."""
+        size = ctypes.c_size_t()
+        self._check(self.lib.lbrs_checkpoint_size(self.ctx, ctypes.byref(size)))
+        blob = torch.empty(size.value, dtype=torch.uint8, device=self.device if device else "cpu")
+        self._check(self.lib.lbrs_checkpoint_save(self.ctx, ctypes.c_void_p(blob.data_ptr()), 1 if device else 0))
+        return blob
+
+    def restore(self, blob: torch.Tensor):
+        """Resume from a blob of checkpoint(); the configuration must match."""
+        blob = blob.contiguous()
+        self._check(self.lib.lbrs_checkpoint_load(self.ctx, ctypes.c_void_p(blob.data_ptr()), 1 if blob.is_cuda else 0))
+
     def step_adaptive(self, n: int, safety: float = 1.0, t_final: float = 0.0):
         """n steps with the lattice speed chosen anew every step (see lbrs_step_adaptive)."""
         self._check(self.lib.lbrs_step_adaptive(self.ctx, int(n), float(safety), float(t_final)))
