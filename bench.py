@@ -322,12 +322,14 @@ def obstacle_measurement(Solver, stream, barrier, peak):
     s.close()
     t = a.elapsed_time(b) / 1e3
     mlups = big.cells * big.steps / t / 1e6
-    bpl = BYTES_PER_LUP_F32 + 1
-    out["steady_6144x2048_f32"] = {"value": mlups, "unit": UNIT, "kernel": "step2d_obstacle_kernel<float>",
+    bpl = BYTES_PER_LUP_F32_FUSED2 + 0.5
+    out["steady_6144x2048_f32"] = {"value": mlups, "unit": UNIT,
+                                   "kernel": "step2d_f32_fused2_tma_kernel<false, true>",
                                    "algorithmic_bytes_per_lup": bpl, "achieved_gbs": bpl * mlups / 1e3,
                                    "frac": bpl * mlups / 1e3 / peak,
-                                   "note": "one step per launch (the two-step kernel has no internal walls); "
-                                           "128 B of distributions plus the 1 B mask per update"}
+                                   "note": "two steps per launch with the obstacle mask of each tile's pull "
+                                           "range in shared memory: 128 B of distributions and the 1 B mask "
+                                           "per cell and launch"}
     return out
 
 

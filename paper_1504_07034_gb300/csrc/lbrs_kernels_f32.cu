@@ -462,6 +462,173 @@ __device__ __forceinline__ void step2_phase1_raw(const StepArgs<float>& a, const
     }
 }
 
+// Internal walls in the two-step kernel.  The block keeps the solidity of the
+// tile's pull range, the 36 x 12 cells from (i0 - 2, j0 - 2), in shared memory:
+// every cell whose solidity the two steps consult lies there (window slots, their
+// sources and the x and y neighbours of the mirror rule).  A coordinate outside
+// the domain takes solid_at's value (wrapped, clamped, or fluid beyond a Dirichlet
+// or wall side), wrapped as often as needed: the sources of a periodic window slot
+// lie two cells out, and a solid one among them must send the tile down the
+// obstacle path even though the slot's own pull reads the global mask.
+constexpr int kMX = kFTX + 4, kMY = kFTY + 4, kMN = kMX * kMY;
+constexpr size_t kTmaObstSmemBytes = kTmaSmemBytes + kMN;
+
+// Fill the mask window; true when any of its cells is solid (for the whole block).
+__device__ __forceinline__ bool load_mask_window(const StepArgs<float>& a, uint8_t* s_m, int i0, int j0)
+{
+    int any = 0;
+    for (int m = threadIdx.x; m < kMN; m += kFTX * kFTY) {
+        int i = i0 - 2 + m % kMX, j = j0 - 2 + m / kMX;
+        bool fluid = false;
+        if (i < 0 || i >= a.nx) {
+            const int kind = i < 0 ? a.bc[0] : a.bc[1];
+            if (kind == BC_PERIODIC) i = wrap_index(i, a.nx);
+            else if (kind == BC_TRANSMISSIVE) i = i < 0 ? 0 : a.nx - 1;
+            else fluid = true;
+        }
+        if (j < 0 || j >= a.ny) {
+            const int kind = j < 0 ? a.bc[2] : a.bc[3];
+            if (kind == BC_PERIODIC) j = wrap_index(j, a.ny);
+            else if (kind == BC_TRANSMISSIVE) j = j < 0 ? 0 : a.ny - 1;
+            else fluid = true;
+        }
+        const uint8_t v = !fluid && a.solid[(int64_t)j * a.nx + i] ? 1 : 0;
+        s_m[m] = v;
+        any |= v;
+    }
+    return __syncthreads_or(any) != 0;
+}
+
+__device__ __forceinline__ bool msolid(const uint8_t* s_m, int i, int j, int i0, int j0)
+{
+    return s_m[(j - j0 + 2) * kMX + (i - i0 + 2)] != 0;
+}
+
+// Phase 1 with internal walls: solid window slots are skipped (phase 2 never
+// reads them: a population pulled from a solid cell is replaced by the mirror
+// rule); a fluid slot with a solid source, or on a domain side, takes the
+// single-step kernel's obstacle pull from global memory.
+__device__ __forceinline__ void step2_phase1_obst(const StepArgs<float>& a, const float* s_raw, float* s_f,
+                                                  const uint8_t* s_m, int i0, int j0)
+{
+    const bool px = a.bc[0] == BC_PERIODIC, py = a.bc[2] == BC_PERIODIC;
+    for (int w = threadIdx.x; w < kFWN; w += kFTX * kFTY) {
+        const int wi = w % kFWX, wj = w / kFWX;
+        const int ui = i0 - 1 + wi, uj = j0 - 1 + wj;
+        int i = ui, j = uj;
+        if (i < 0 || i >= a.nx) {
+            if (!px) continue;
+            i = wrap_index(i, a.nx);
+        }
+        if (j < 0 || j >= a.ny) {
+            if (!py) continue;
+            j = wrap_index(j, a.ny);
+        }
+        if (msolid(s_m, ui, uj, i0, j0)) continue;
+        float f[4][4];
+        if (i > 0 && i < a.nx - 1 && j > 0 && j < a.ny - 1 && !msolid(s_m, ui + 1, uj + 1, i0, j0) &&
+            !msolid(s_m, ui - 1, uj + 1, i0, j0) && !msolid(s_m, ui - 1, uj - 1, i0, j0) &&
+            !msolid(s_m, ui + 1, uj - 1, i0, j0)) {
+            const int b = wj * kPX + wi;
+            const int r[4] = {b, b + 2, b + 2, b};
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) f[q][k] = s_raw[(q * 4 + k) * kPN + r[q]];
+        } else {
+            pull_obstacle_2d<float>(a, i, j, f);
+        }
+        float U[4], out[4][4];
+        collide_2d<float>(a, f, U, out);
+        step2_store_slot<false>(a, s_f, w, wi, wj, i0, j0, U, out);
+    }
+}
+
+// Phase 2 with internal walls: a solid tile cell is carried unchanged (its two
+// steps copy it); a fluid cell pulls from the window and resolves solid sources
+// and domain sides in pull_obstacle_2d's order.
+__device__ __forceinline__ void step2_phase2_obst(const StepArgs<float>& a, const float* s_f, const uint8_t* s_m,
+                                                  int i0, int j0)
+{
+    const int ti = threadIdx.x % kFTX, tj = threadIdx.x / kFTX;
+    const int i = i0 + ti, j = j0 + tj;
+    if (i >= a.nx || j >= a.ny) return;
+    const int64_t c = (int64_t)j * a.nx + i;
+    if (msolid(s_m, i, j, i0, j0)) {
+#pragma unroll
+        for (int n = 0; n < 16; ++n) a.dst[n * a.N + c] = a.src[n * a.N + c];
+        return;
+    }
+    const int SX[4] = {-1, 1, 1, -1};
+    const int SY[4] = {-1, -1, 1, 1};
+    float f[4][4];
+    bool wall_top = false, wall_bottom = false;
+    bool unknown[4] = {false, false, false, false};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        int si = i - SX[q], sj = j - SY[q];
+        const int side_y = sj < 0 ? 2 : (sj >= a.ny ? 3 : -1);
+        const int side_x = si < 0 ? 0 : (si >= a.nx ? 1 : -1);
+        const int kind_y = side_y == 2 ? a.bc[2] : a.bc[3];
+        const int kind_x = side_x == 0 ? a.bc[0] : a.bc[1];
+        if (side_y >= 0 && kind_y == BC_WALL) {
+            if (side_y == 3) wall_top = true; else wall_bottom = true;
+            continue;
+        }
+        const float* g = nullptr;
+        if (side_x >= 0) {
+            if (kind_x == BC_DIRICHLET) g = a.ghost + side_x * GHOST_STRIDE + q * 4;
+            else if (kind_x != BC_PERIODIC) si = si < 0 ? 0 : a.nx - 1;
+        }
+        if (!g && side_y >= 0) {
+            if (kind_y == BC_DIRICHLET) g = a.ghost + side_y * GHOST_STRIDE + q * 4;
+            else if (kind_y != BC_PERIODIC) sj = sj < 0 ? 0 : a.ny - 1;
+        }
+        if (!g && msolid(s_m, si, sj, i0, j0)) {
+            unknown[q] = true;
+            continue;
+        }
+        if (g) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) f[q][k] = g[k];
+        } else {
+            const int slot = (sj - (j0 - 1)) * kFWX + (si - (i0 - 1));
+#pragma unroll
+            for (int k = 0; k < 4; ++k) f[q][k] = s_f[(q * 4 + k) * kFWN + slot];
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (!unknown[q]) continue;
+        const bool xn = msolid(s_m, i - SX[q], j, i0, j0), yn = msolid(s_m, i, j - SY[q], i0, j0);
+        const bool flip_x = !(yn && !xn), flip_y = !(xn && !yn);
+        const int mx = flip_x ? -SX[q] : SX[q], my = flip_y ? -SY[q] : SY[q];
+        const int m = my < 0 ? (mx < 0 ? 0 : 1) : (mx > 0 ? 2 : 3);
+        const float su = flip_x ? -1.f : 1.f, sv = flip_y ? -1.f : 1.f;
+#pragma unroll
+        for (int mm = 0; mm < 4; ++mm) {
+            if (mm != m) continue;
+            f[q][0] = f[mm][0];
+            f[q][1] = su * f[mm][1];
+            f[q][2] = sv * f[mm][2];
+            f[q][3] = f[mm][3];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float sgn = k == 2 ? -1.f : 1.f;
+        if (wall_top) {
+            f[0][k] = sgn * f[3][k];
+            f[1][k] = sgn * f[2][k];
+        }
+        if (wall_bottom) {
+            f[3][k] = sgn * f[0][k];
+            f[2][k] = sgn * f[1][k];
+        }
+    }
+    collide_store_2d<float>(a, c, f);
+}
+
 __device__ __forceinline__ void issue_tile_copy(const CUtensorMap* tmap, float* s_raw, uint32_t bar, int i0, int j0)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kRawBytes) : "memory");
@@ -477,14 +644,15 @@ __device__ __forceinline__ void issue_tile_copy(const CUtensorMap* tmap, float* 
 }
 
 // One block per tile, five resident blocks per SM (48 registers, 44.9 KB of shared
-// memory each).  Forms that reuse a block for further tiles, issuing the next
+// memory each; 45.3 KB with the obstacle mask window of OBST).  Forms that reuse a block for further tiles, issuing the next
 // copy as soon as phase 1 has read the raw buffer, measured slower: persistent
 // blocks fall into step and wait for their copies together, and a loop over
 // tiles raises the register count past the five-block budget (spills).
-template <bool STORE_U>
+template <bool STORE_U, bool OBST = false>
 __global__ void __launch_bounds__(kFTX * kFTY, 5)
     step2d_f32_fused2_tma_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs<float> a, unsigned* wait_flag)
 {
+    static_assert(!(STORE_U && OBST), "the recording form has no internal walls");
     extern __shared__ unsigned char smem_dyn[];
     float* s_raw = (float*)(((uintptr_t)smem_dyn + 127) & ~(uintptr_t)127);
     float* s_f = s_raw + 16 * kPN;
@@ -499,12 +667,21 @@ __global__ void __launch_bounds__(kFTX * kFTY, 5)
         issue_tile_copy(&tmap, s_raw, bar, i0, j0);
     }
     __syncthreads();
+    bool obst = false;
+    uint8_t* s_m = (uint8_t*)(bar_p + 2);
+    if constexpr (OBST) obst = load_mask_window(a, s_m, i0, j0);   // while the copies are in flight
     const bool arrived = mbar_wait_bounded(bar, 0, kWaitPolls);
     if (!__syncthreads_and(arrived)) {
         if (threadIdx.x == 0) {
             atomicExch(wait_flag, 1u);
             mbar_wait_bounded(bar, 0, kWaitPolls);   // give the copy in flight a last chance to land
         }
+        return;
+    }
+    if (OBST && obst) {
+        step2_phase1_obst(a, s_raw, s_f, s_m, i0, j0);
+        __syncthreads();
+        step2_phase2_obst(a, s_f, s_m, i0, j0);
         return;
     }
     step2_phase1_raw<STORE_U>(a, s_raw, s_f, i0, j0);
@@ -748,6 +925,9 @@ bool encode_f32_tile_map(TileMap* map, const float* f, int64_t nx, int64_t ny)
         if (attr_err == cudaSuccess)
             attr_err = cudaFuncSetAttribute(step2d_f32_fused2_tma_kernel<true>,
                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmemBytes);
+        if (attr_err == cudaSuccess)
+            attr_err = cudaFuncSetAttribute(step2d_f32_fused2_tma_kernel<false, true>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaObstSmemBytes);
     });
     if (attr_err != cudaSuccess) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, 16};
@@ -771,8 +951,16 @@ cudaError_t launch_step2_f32(const StepArgs<float>& a, const TileMap* map, unsig
     if (map && map->valid && wait_flag) {
         CUtensorMap m;
         memcpy(&m, map->bytes, sizeof m);
-        if (rec) step2d_f32_fused2_tma_kernel<true><<<grid, kFTX * kFTY, kTmaSmemBytes, s>>>(m, a, wait_flag);
-        else step2d_f32_fused2_tma_kernel<false><<<grid, kFTX * kFTY, kTmaSmemBytes, s>>>(m, a, wait_flag);
+        if (a.solid) {
+            if (rec) return cudaErrorInvalidValue;   // the recording form has no internal walls
+            step2d_f32_fused2_tma_kernel<false, true><<<grid, kFTX * kFTY, kTmaObstSmemBytes, s>>>(m, a, wait_flag);
+        } else if (rec) {
+            step2d_f32_fused2_tma_kernel<true><<<grid, kFTX * kFTY, kTmaSmemBytes, s>>>(m, a, wait_flag);
+        } else {
+            step2d_f32_fused2_tma_kernel<false><<<grid, kFTX * kFTY, kTmaSmemBytes, s>>>(m, a, wait_flag);
+        }
+    } else if (a.solid) {
+        return cudaErrorInvalidValue;                // internal walls need the tensor-copy form
     } else {
         if (rec) step2d_f32_fused2_kernel<true><<<grid, kFTX * kFTY, 0, s>>>(a);
         else step2d_f32_fused2_kernel<false><<<grid, kFTX * kFTY, 0, s>>>(a);

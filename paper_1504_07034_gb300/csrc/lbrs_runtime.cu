@@ -224,11 +224,12 @@ cudaError_t launch_one_step(lbrs_ctx* ctx, int from, cudaStream_t s)
     return launch_step_f32(lat, step_args<float>(ctx, from), s);
 }
 
-// Two-steps-per-launch kernel available for this context?
+// Two-steps-per-launch kernel available for this context?  With internal walls
+// only in its tensor-copy form.
 bool fused2(const lbrs_ctx* ctx)
 {
-    return !ctx->f64 && !ctx->f16 && !ctx->f32u && ctx->lattice == LBRS_D2Q4 && !ctx->solid &&
-           step2_f32_enabled();
+    if (ctx->f64 || ctx->f16 || ctx->f32u || ctx->lattice != LBRS_D2Q4 || !step2_f32_enabled()) return false;
+    return !ctx->solid || (ctx->tmap[0].valid && ctx->tmap[1].valid);
 }
 
 unsigned* wait_flag(const lbrs_ctx* ctx) { return (unsigned*)(ctx->ws + ctx->L.wait_flag); }
@@ -427,7 +428,7 @@ lbrs_status record_steps(lbrs_ctx* ctx, int64_t n, char* U_hist)
 {
     const size_t stride = (size_t)ctx->K * ctx->N * elem_bytes(ctx);
     int64_t m = 0;
-    for (; m + 2 <= n && fused2(ctx); m += 2) {
+    for (; m + 2 <= n && fused2(ctx) && !ctx->solid; m += 2) {
         LBRS_CUDA(ctx, launch_record_step2(ctx, U_hist + m * stride));
         ctx->cur ^= 1;
         ctx->launches += 1;

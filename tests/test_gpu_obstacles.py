@@ -137,6 +137,53 @@ def test_f32_forward_facing_step_close_to_oracle():
     assert l1 <= 1e-5, l1
 
 
+_FUSE_SCRIPT = r"""
+import sys
+import numpy as np
+import torch
+sys.path.insert(0, sys.argv[1])
+sys.path.insert(0, sys.argv[1] + "/tests")
+import workloads as W
+from test_gpu_obstacles import random_obstacle_case
+from paper_1504_07034_gb300.solver import Solver
+cases = [W.forward_facing_step(), W.shock_diffraction(n=200)]
+for k, (nx, ny) in enumerate(((64, 40), (132, 18), (36, 29), (96, 48), (37, 29))):
+    for bcname in ("periodic", "walls_periodic_x", "transmissive", "mixed"):
+        cases.append(random_obstacle_case(nx, ny, bcname, (1.0, 1.6)[k % 2], seed=11 * k + len(bcname), steps=0))
+out = []
+for wl in cases:
+    s = Solver.from_workload(wl, precision="f32")
+    s.set_state(torch.from_numpy(wl.prim).cuda())
+    s.step(51)
+    out.append(s.get_distributions().cpu().numpy().ravel())
+    out.append(s.step_record(5).cpu().numpy().ravel())
+    out.append(s.get_distributions().cpu().numpy().ravel())
+    s.close()
+np.save(sys.argv[2], np.concatenate(out))
+"""
+
+
+def test_f32_two_step_kernel_with_walls_equals_single_steps(tmp_path):
+    """The two-steps-per-launch kernel with internal walls (tensor copies where nx % 4 == 0;
+    the mask of each tile's pull range in shared memory) against one-step launches, bit for
+    bit: both run the same per-cell code (pull, mirror rule, collision).  Random rectangles
+    under every boundary set, ragged tiles, the forward-facing step and the shock
+    diffraction; 51 steps (a graph, pairs and a single step), then 5 recording steps."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = tmp_path / "fuse_walls.py"
+    script.write_text(_FUSE_SCRIPT)
+    res = {}
+    for fuse in ("0", "1"):
+        out = tmp_path / f"f{fuse}.npy"
+        subprocess.run([sys.executable, str(script), root, str(out)], check=True,
+                       env=dict(os.environ, LBRS_F32_FUSE=fuse), timeout=600)
+        res[fuse] = np.load(out)
+    assert np.array_equal(res["1"], res["0"]), np.max(np.abs(res["1"] - res["0"]))
+
+
 @pytest.mark.parametrize("precision", ["f64", "f32"])
 def test_all_fluid_mask_equals_no_obstacles(precision):
     wl = random_obstacle_case(70, 40, "mixed", 1.2, seed=3, steps=70)
