@@ -485,20 +485,40 @@ __device__ __forceinline__ double bound2d(const T U[4], double gamma)
     return (double)((s1 > s2 ? s1 : s2) + sqrt(T(2)) * a);
 }
 
-// Block maximum of v (threads of a 1-D or 2-D block of NT threads), folded into *dst.
-template <int NT>
-__device__ __forceinline__ void block_max_into(double v, unsigned long long* dst)
+// The local bound in the storage precision: bound2d for FP64 (the oracle's
+// expressions); in FP32 one correctly rounded reciprocal of rho (the one the
+// collision's velocities use) and one square root, sqrt(2 gamma p / rho) for
+// sqrt(2) a.
+template <typename T>
+__device__ __forceinline__ T bound_local(const T U[4], double gamma)
+{
+    if constexpr (std::is_same<T, float>::value) {
+        const float g = (float)gamma, gm1 = (float)(gamma - 1.0);
+        const float inv = __frcp_rn(U[0]);
+        const float u = U[1] * inv, v = U[2] * inv;
+        const float p = gm1 * (U[3] - 0.5f * (U[1] * u + U[2] * v));
+        if (!(U[0] > 0.f) || !(p > 0.f) || !isfinite(p)) return -1.f;
+        return fmaxf(fabsf(u + v), fabsf(u - v)) + sqrtf(2.f * (g * p * inv));
+    } else {
+        return bound2d<double>(U, gamma);
+    }
+}
+
+// Block maximum of v (threads of a 1-D or 2-D block of NT threads), folded into *dst
+// as the bits of a non-negative double.
+template <int NT, typename V>
+__device__ __forceinline__ void block_max_into(V v, unsigned long long* dst)
 {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, off));
-    __shared__ double wmax[NT / 32];
+    __shared__ V wmax[NT / 32];
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     if ((tid & 31) == 0) wmax[tid >> 5] = v;
     __syncthreads();
     if (tid == 0) {
-        double m = wmax[0];
+        V m = wmax[0];
         for (int w = 1; w < NT / 32; ++w) m = fmax(m, wmax[w]);
-        if (m > 0.0) atomicMax(dst, (unsigned long long)__double_as_longlong(m));
+        if (m > V(0)) atomicMax(dst, (unsigned long long)__double_as_longlong((double)m));
     }
 }
 
@@ -511,18 +531,9 @@ __global__ void __launch_bounds__(256) step2d_adapt_kernel(const StepArgs<T> a, 
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const bool in = i < a.nx && j < a.ny;
     const int64_t c = (int64_t)j * a.nx + i;
-    if (st->skip) {            // the same for every thread of the grid
-        if (in) {
-#pragma unroll
-            for (int n = 0; n < 16; ++n) a.dst[n * a.N + c] = a.src[n * a.N + c];
-        }
-        return;
-    }
-    double bnd = -1.0;
+    // the pull does not depend on the prep's results: its loads go out before the state is read
+    T f[4][4];
     if (in) {
-        StepArgs<T> b = a;
-        b.c = (T)st->c_new;
-        T f[4][4];
         if (i > 0 && i < a.nx - 1 && j > 0 && j < a.ny - 1) {
             const int64_t s[4] = {c + a.nx + 1, c + a.nx - 1, c - a.nx - 1, c - a.nx + 1};
 #pragma unroll
@@ -530,15 +541,27 @@ __global__ void __launch_bounds__(256) step2d_adapt_kernel(const StepArgs<T> a, 
 #pragma unroll
                 for (int k = 0; k < 4; ++k) f[q][k] = a.src[(q * 4 + k) * a.N + s[q]];
         } else {
-            pull_edge_2d<T>(b, i, j, f);
+            pull_edge_2d<T>(a, i, j, f);
         }
+    }
+    if (st->skip) {            // the same for every thread of the grid
+        if (in) {
+#pragma unroll
+            for (int n = 0; n < 16; ++n) a.dst[n * a.N + c] = a.src[n * a.N + c];
+        }
+        return;
+    }
+    T bnd = T(-1);
+    if (in) {
+        StepArgs<T> b = a;
+        b.c = (T)st->c_new;
         T U[4], out[4][4];
         collide_2d<T>(b, f, U, out);
 #pragma unroll
         for (int q = 0; q < 4; ++q)
 #pragma unroll
             for (int k = 0; k < 4; ++k) a.dst[(q * 4 + k) * a.N + c] = out[q][k];
-        bnd = bound2d<T>(U, gamma);
+        bnd = bound_local<T>(U, gamma);
     }
     block_max_into<256>(bnd, &st->bound_bits[st->slot_cur]);
 }
@@ -548,12 +571,12 @@ template <typename T>
 __global__ void __launch_bounds__(256) adapt_init_bound_kernel(const T* __restrict__ fs, int64_t N, double gamma,
                                                               AdaptState* st)
 {
-    double bnd = -1.0;
+    T bnd = T(-1);
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += (int64_t)gridDim.x * blockDim.x) {
         T U[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) U[k] = ((fs[k * N + c] + fs[(4 + k) * N + c]) + fs[(8 + k) * N + c]) + fs[(12 + k) * N + c];
-        bnd = fmax(bnd, bound2d<T>(U, gamma));
+        bnd = fmax(bnd, bound_local<T>(U, gamma));
     }
     block_max_into<256>(bnd, &st->bound_bits[st->slot_cur]);
 }
