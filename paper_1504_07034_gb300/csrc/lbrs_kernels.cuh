@@ -345,18 +345,17 @@ __device__ __forceinline__ void pull_obstacle_2d(const StepArgs<T>& a, int i, in
 
 // Collision of one cell (Eq. 9 with the equilibria of Eq. 12): moments U of the
 // pulled populations f, then out = (1 - omega) f + omega f^eq(U).
-// In FP32 at omega = 1 (a block-uniform branch) the result is f^eq itself, which
-// is what the general expression gives there for any finite f.
+// At omega = 1 (a grid-uniform branch) the result is f^eq itself, which is what
+// the general expression gives there for any finite f (0 f + 1 f^eq rounds to
+// f^eq; only the sign of a zero may differ).
 template <typename T>
 __device__ __forceinline__ void collide_2d(const StepArgs<T>& a, const T f[4][4], T U[4], T out[4][4])
 {
 #pragma unroll
     for (int k = 0; k < 4; ++k) U[k] = ((f[0][k] + f[1][k]) + f[2][k]) + f[3][k];
-    if constexpr (std::is_same<T, float>::value) {
-        if (a.om1 == 0.f) {
-            equilibria2d<T>(U, a.gm1, a.c, out);
-            return;
-        }
+    if (a.om1 == T(0)) {
+        equilibria2d<T>(U, a.gm1, a.c, out);
+        return;
     }
     T e[4][4];
     equilibria2d<T>(U, a.gm1, a.c, e);
