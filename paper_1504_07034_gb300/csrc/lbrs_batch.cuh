@@ -118,10 +118,19 @@ __global__ void __launch_bounds__(BLOCK) batch1d_kernel(const BatchArgs<T> a)
                 for (int k = 0; k < 3; ++k) U[k] = f[0][k] + f[1][k];
                 equilibria1d<T>(U, a.gm1, c, e);
             }
+            if (a.om1 == T(0)) {
+                // omega = 1 (uniform over the launch): the relaxation returns f^eq, which is
+                // what the general expression rounds to for any finite f
 #pragma unroll
-            for (int q = 0; q < Q; ++q)
+                for (int q = 0; q < Q; ++q)
 #pragma unroll
-                for (int k = 0; k < 3; ++k) out[(q * 3 + k) * W + i] = a.om1 * f[q][k] + a.om * e[q][k];
+                    for (int k = 0; k < 3; ++k) out[(q * 3 + k) * W + i] = e[q][k];
+            } else {
+#pragma unroll
+                for (int q = 0; q < Q; ++q)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) out[(q * 3 + k) * W + i] = a.om1 * f[q][k] + a.om * e[q][k];
+            }
         }
         __syncthreads();
         cur ^= 1;
