@@ -800,10 +800,13 @@ __global__ void __launch_bounds__(256) adjoint2d_kernel(const AdjArgs<T> a)
     const int jp = j + 1 == a.ny ? 0 : j + 1, jm = j == 0 ? a.ny - 1 : j - 1;
     const int64_t t[4] = {(int64_t)jp * a.nx + ip, (int64_t)jp * a.nx + im, (int64_t)jm * a.nx + im,
                           (int64_t)jm * a.nx + ip};
+    // omega = 1: fbar = J_E^T g alone (what the general expression rounds to for finite g)
+    const bool eq_only = a.om1 == T(0);
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) a.gout[(q * 4 + k) * a.N + t[q]] = a.om1 * g[q][k] + a.om * ubar[k];
+        for (int k = 0; k < 4; ++k)
+            a.gout[(q * 4 + k) * a.N + t[q]] = eq_only ? ubar[k] : a.om1 * g[q][k] + a.om * ubar[k];
 }
 
 // dL/dU0 = J_E(U0)^T dL/df*^0, per cell.

@@ -704,10 +704,11 @@ __device__ __forceinline__ void adj_local(const AdjArgs<float>& a, const float U
 {
     float ubar[4];
     equilibrium_vjp2d<float>(U, g, a.gamma, a.gm1, a.c, ubar);
+    const bool eq_only = a.om1 == 0.f;   // omega = 1: as in the push kernel
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) out[q][k] = a.om1 * g[q][k] + a.om * ubar[k];
+        for (int k = 0; k < 4; ++k) out[q][k] = eq_only ? ubar[k] : a.om1 * g[q][k] + a.om * ubar[k];
 }
 
 // g(x)_q = k_q(x + c_q) for a cell (i, j) of the periodic grid.
