@@ -282,8 +282,8 @@ lbrs_status lbrs_checkpoint_load(lbrs_ctx* ctx, const void* src, int on_device);
  * (i, j - sy) is, the opposite one (both negated) at corners.  The mask is checked
  * on the host (one synchronous copy): EINVAL if a replacement would itself be
  * unknown (fluid channels one cell wide), for other lattices or storage forms.
- * With walls set, FP32 steps run one per launch and the adjoint calls return
- * EINVAL. */
+ * With walls set, FP32 steps keep running two per launch where nx % 4 == 0 (the
+ * tensor-copy form), one per launch otherwise; the adjoint calls return EINVAL. */
 lbrs_status lbrs_set_obstacles(lbrs_ctx* ctx, const uint8_t* d_solid);
 
 /* ---------------------------------------------------------------- adjoint
