@@ -146,6 +146,21 @@ typedef struct {
 /* Library ABI version (LBRS_ABI_VERSION of the build). */
 int lbrs_abi_version(void);
 
+/* Bounds-checked build (not a method of the paper: the library's own check of its
+ * index arithmetic, where no memory sanitizer can run).  The library built with
+ * -DLBRS_DEBUG (liblbrs_debug.so, `python -m paper_1504_07034_gb300.build --debug`)
+ * checks the indices of its kernels' global and shared-memory accesses; an index
+ * outside its buffer is replaced by 0 (the access stays inside the buffer, its value
+ * is wrong) and the first such event of each kernel unit is recorded.
+ * lbrs_debug_build: 1 for that build, 0 for the release build (which records
+ * nothing).  lbrs_debug_check: after the caller has synchronised the device, writes
+ * the first record, (site << 40) | index, to *first (0 if none), clears the records
+ * and returns LBRS_ECUDA if there was one (LBRS_EINVAL for a NULL pointer); in
+ * that build lbrs_sync also reports a record as LBRS_ECUDA.  Device-wide, not per
+ * context: records of concurrent contexts are not told apart. */
+int lbrs_debug_build(void);
+lbrs_status lbrs_debug_check(uint64_t* first);
+
 /* Human-readable name of a status code. Never NULL. */
 const char* lbrs_status_string(lbrs_status s);
 

@@ -84,6 +84,8 @@ _P = ctypes.c_void_p
 _CTX = ctypes.c_void_p
 SIGNATURES = {
     "lbrs_abi_version": (ctypes.c_int, []),
+    "lbrs_debug_build": (ctypes.c_int, []),
+    "lbrs_debug_check": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64)]),
     "lbrs_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "lbrs_workspace_size": (ctypes.c_int, [ctypes.POINTER(lbrs_config), ctypes.POINTER(ctypes.c_size_t)]),
     "lbrs_create": (ctypes.c_int, [ctypes.POINTER(lbrs_config), _P, ctypes.c_size_t, ctypes.POINTER(_CTX)]),

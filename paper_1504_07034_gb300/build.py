@@ -10,7 +10,11 @@ shared library with the CUDA runtime linked statically:
   csrc/lbrs_noalloc.cu      diagnostics variant with static scratch, -fmad=false
   csrc/lbrs_batch_runtime.cu host runtime of the batched tubes
 
-Usage: python -m paper_1504_07034_gb300.build [--force]
+The bounds-checked variant (-DLBRS_DEBUG: every checked kernel index that leaves
+its buffer is recorded and replaced by 0, see lbrs_debug_check in include/lbrs.h)
+builds into _build_debug/ as liblbrs_debug.so; load it with LBRS_LIBRARY.
+
+Usage: python -m paper_1504_07034_gb300.build [--force] [--debug]
 """
 from __future__ import annotations
 
@@ -27,6 +31,8 @@ CSRC = PKG / "csrc"
 INCLUDE = ROOT / "include"
 BUILD = PKG / "_build"
 LIB = PKG / "liblbrs.so"
+BUILD_DEBUG = PKG / "_build_debug"
+LIB_DEBUG = PKG / "liblbrs_debug.so"
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
@@ -56,10 +62,10 @@ def _stale(target: Path, deps) -> bool:
     return any(Path(d).stat().st_mtime > t for d in deps)
 
 
-def _compile(unit: str, extra) -> Path:
+def _compile(unit: str, extra, bdir: Path = BUILD) -> Path:
     src = CSRC / unit
-    obj = BUILD / (unit + ".o")
-    log = BUILD / (unit + ".ptxas.log")
+    obj = bdir / (unit + ".o")
+    log = bdir / (unit + ".ptxas.log")
     cmd = [nvcc(), *ARCH, *COMMON, *extra, "-c", str(src), "-o", str(obj)]
     r = subprocess.run(cmd, capture_output=True, text=True)
     log.write_text(" ".join(cmd) + "\n" + r.stdout + r.stderr)
@@ -68,22 +74,24 @@ def _compile(unit: str, extra) -> Path:
     return obj
 
 
-def build(force: bool = False) -> Path:
-    BUILD.mkdir(parents=True, exist_ok=True)
+def build(force: bool = False, debug: bool = False) -> Path:
+    bdir, lib = (BUILD_DEBUG, LIB_DEBUG) if debug else (BUILD, LIB)
+    flags = ["-DLBRS_DEBUG"] if debug else []
+    bdir.mkdir(parents=True, exist_ok=True)
     todo = [(u, x) for u, x in UNITS.items()
-            if force or _stale(BUILD / (u + ".o"), [CSRC / u, *HEADERS])]
+            if force or _stale(bdir / (u + ".o"), [CSRC / u, *HEADERS])]
     with ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
-        list(ex.map(lambda ux: _compile(*ux), todo))
-    objs = [BUILD / (u + ".o") for u in UNITS]
-    if force or todo or _stale(LIB, objs):
-        tmp = LIB.with_name(f"liblbrs.{os.getpid()}.tmp.so")
+        list(ex.map(lambda ux: _compile(ux[0], [*ux[1], *flags], bdir), todo))
+    objs = [bdir / (u + ".o") for u in UNITS]
+    if force or todo or _stale(lib, objs):
+        tmp = lib.with_name(f"{lib.stem}.{os.getpid()}.tmp.so")
         cmd = [nvcc(), *ARCH, "-shared", "-o", str(tmp), *map(str, objs)]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr[-4000:]}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv))
+    print(build(force="--force" in sys.argv, debug="--debug" in sys.argv))

@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(BLOCK) batch1d_kernel(const BatchArgs<T> a)
         }
         if (x >= 0 && x < len) {
 #pragma unroll
-            for (int n = 0; n < P; ++n) sm[n * W + i] = a.src[n * a.N + off + x];
+            for (int n = 0; n < P; ++n) sm[LBRS_IX(n * W + i, P * W, 20)] = a.src[LBRS_IX(n * a.N + off + x, P * a.N, 21)];
         }
     }
     __syncthreads();
@@ -99,12 +99,12 @@ __global__ void __launch_bounds__(BLOCK) batch1d_kernel(const BatchArgs<T> a)
             T f[Q][3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                f[0][k] = in[k * W + ip];
+                f[0][k] = in[LBRS_IX(k * W + ip, P * W, 20)];
                 if constexpr (Q == 3) {
-                    f[1][k] = in[(3 + k) * W + i];
-                    f[2][k] = in[(6 + k) * W + im];
+                    f[1][k] = in[LBRS_IX((3 + k) * W + i, P * W, 20)];
+                    f[2][k] = in[LBRS_IX((6 + k) * W + im, P * W, 20)];
                 } else {
-                    f[1][k] = in[(3 + k) * W + im];
+                    f[1][k] = in[LBRS_IX((3 + k) * W + im, P * W, 20)];
                 }
             }
             T U[3];
@@ -124,12 +124,12 @@ __global__ void __launch_bounds__(BLOCK) batch1d_kernel(const BatchArgs<T> a)
 #pragma unroll
                 for (int q = 0; q < Q; ++q)
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) out[(q * 3 + k) * W + i] = e[q][k];
+                    for (int k = 0; k < 3; ++k) out[LBRS_IX((q * 3 + k) * W + i, P * W, 20)] = e[q][k];
             } else {
 #pragma unroll
                 for (int q = 0; q < Q; ++q)
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) out[(q * 3 + k) * W + i] = a.om1 * f[q][k] + a.om * e[q][k];
+                    for (int k = 0; k < 3; ++k) out[LBRS_IX((q * 3 + k) * W + i, P * W, 20)] = a.om1 * f[q][k] + a.om * e[q][k];
             }
         }
         __syncthreads();
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(BLOCK) batch1d_kernel(const BatchArgs<T> a)
         const int slot = H + i;
         const int64_t g = off + t0 + i;
 #pragma unroll
-        for (int n = 0; n < P; ++n) a.dst[n * a.N + g] = fin[n * W + slot];
+        for (int n = 0; n < P; ++n) a.dst[LBRS_IX(n * a.N + g, P * a.N, 21)] = fin[LBRS_IX(n * W + slot, P * W, 20)];
     }
 }
 

@@ -29,6 +29,39 @@
 
 namespace lbrs {
 
+// Index check of the LBRS_DEBUG build, the library's bounds and race check where no
+// sanitizer runs: an index outside [0, n) is replaced by 0, so that the access stays
+// inside its buffer, and the first such event of the translation unit is recorded
+// as (site << 40) | (index mod 2^40) in its debug word, which lbrs_sync reports.  In
+// the release build LBRS_IX is the index itself.
+#ifdef LBRS_DEBUG
+static __device__ unsigned long long g_debug_first = 0ull;   // one per translation unit
+static __device__ __forceinline__ int64_t debug_index(int64_t i, int64_t n, int site)
+{
+    if (i >= 0 && i < n) return i;
+    atomicCAS(&g_debug_first, 0ull,
+              ((unsigned long long)site << 40) | ((unsigned long long)i & ((1ull << 40) - 1)));
+    return 0;
+}
+#define LBRS_IX(i, n, site) ::lbrs::debug_index((int64_t)(i), (int64_t)(n), (site))
+// A host function of the translation unit returning (and with clear, zeroing) its word.
+#define LBRS_DEBUG_WORD(name)                                                           \
+    unsigned long long name(int clear)                                                  \
+    {                                                                                   \
+        unsigned long long w = 0ull;                                                    \
+        if (cudaMemcpyFromSymbol(&w, g_debug_first, sizeof w) != cudaSuccess) return 0; \
+        if (clear && w) {                                                               \
+            const unsigned long long z = 0ull;                                          \
+            cudaMemcpyToSymbol(g_debug_first, &z, sizeof z);                            \
+        }                                                                               \
+        return w;                                                                       \
+    }
+#else
+#define LBRS_IX(i, n, site) (i)
+#define LBRS_DEBUG_WORD(name) \
+    unsigned long long name(int) { return 0ull; }
+#endif
+
 enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_DIRICHLET = 2, BC_WALL = 3 };
 // LAT_U2D: a D2Q4 state stored as its moments U directly (the FP16
 // non-equilibrium form keeps U in FP32): read-outs treat it as one
@@ -222,7 +255,7 @@ __device__ __forceinline__ void pull_edge_2d(const StepArgs<T>& a, int i, int j,
         }
         const int64_t s = (int64_t)sj * a.nx + si;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) f[q][k] = g ? g[k] : a.src[(q * 4 + k) * a.N + s];
+        for (int k = 0; k < 4; ++k) f[q][k] = g ? g[k] : a.src[LBRS_IX((q * 4 + k) * a.N + s, 16 * a.N, 1)];
     }
     // top wall: f1 = f4, f2 = f3; bottom wall: f4 = f1, f3 = f2; rho v negated
 #pragma unroll
@@ -270,7 +303,7 @@ __device__ __forceinline__ bool solid_at(const StepArgs<T>& a, int i, int j)
         else if (kind == BC_TRANSMISSIVE) j = j < 0 ? 0 : a.ny - 1;
         else return false;
     }
-    return a.solid[(int64_t)j * a.nx + i] != 0;
+    return a.solid[LBRS_IX((int64_t)j * a.nx + i, a.N, 2)] != 0;
 }
 
 // The pull of pull_edge_2d for a fluid cell next to obstacles.
@@ -304,12 +337,12 @@ __device__ __forceinline__ void pull_obstacle_2d(const StepArgs<T>& a, int i, in
             else sj = sj < 0 ? 0 : a.ny - 1;
         }
         const int64_t s = (int64_t)sj * a.nx + si;
-        if (!g && a.solid[s]) {
+        if (!g && a.solid[LBRS_IX(s, a.N, 3)]) {
             unknown[q] = true;
             continue;
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k) f[q][k] = g ? g[k] : a.src[(q * 4 + k) * a.N + s];
+        for (int k = 0; k < 4; ++k) f[q][k] = g ? g[k] : a.src[LBRS_IX((q * 4 + k) * a.N + s, 16 * a.N, 3)];
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -372,12 +405,12 @@ __device__ __forceinline__ void collide_store_2d(const StepArgs<T>& a, int64_t c
     collide_2d<T>(a, f, U, out);
     if constexpr (STORE_U) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) a.Uout[k * a.N + c] = U[k];
+        for (int k = 0; k < 4; ++k) a.Uout[LBRS_IX(k * a.N + c, 4 * a.N, 4)] = U[k];
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) a.dst[(q * 4 + k) * a.N + c] = out[q][k];
+        for (int k = 0; k < 4; ++k) a.dst[LBRS_IX((q * 4 + k) * a.N + c, 16 * a.N, 4)] = out[q][k];
 }
 
 // One thread per cell; blockDim.x along i (coalesced), blockDim.y along j.
@@ -397,7 +430,7 @@ __global__ void __launch_bounds__(256) step2d_kernel(const StepArgs<T> a)
 #pragma unroll
         for (int q = 0; q < 4; ++q)
 #pragma unroll
-            for (int k = 0; k < 4; ++k) f[q][k] = a.src[(q * 4 + k) * a.N + s[q]];
+            for (int k = 0; k < 4; ++k) f[q][k] = a.src[LBRS_IX((q * 4 + k) * a.N + s[q], 16 * a.N, 5)];
     } else {
         pull_edge_2d<T>(a, i, j, f);
     }
@@ -414,18 +447,18 @@ __global__ void __launch_bounds__(256) step2d_obstacle_kernel(const StepArgs<T> 
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= a.nx || j >= a.ny) return;
     const int64_t c = (int64_t)j * a.nx + i;
-    if (a.solid[c]) {
+    if (a.solid[LBRS_IX(c, a.N, 6)]) {
         T f[4][4];
 #pragma unroll
         for (int q = 0; q < 4; ++q)
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                f[q][k] = a.src[(q * 4 + k) * a.N + c];
-                a.dst[(q * 4 + k) * a.N + c] = f[q][k];
+                f[q][k] = a.src[LBRS_IX((q * 4 + k) * a.N + c, 16 * a.N, 6)];
+                a.dst[LBRS_IX((q * 4 + k) * a.N + c, 16 * a.N, 6)] = f[q][k];
             }
         if constexpr (STORE_U) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) a.Uout[k * a.N + c] = ((f[0][k] + f[1][k]) + f[2][k]) + f[3][k];
+            for (int k = 0; k < 4; ++k) a.Uout[LBRS_IX(k * a.N + c, 4 * a.N, 6)] = ((f[0][k] + f[1][k]) + f[2][k]) + f[3][k];
         }
         return;
     }
@@ -433,11 +466,11 @@ __global__ void __launch_bounds__(256) step2d_obstacle_kernel(const StepArgs<T> 
     if (i > 0 && i < a.nx - 1 && j > 0 && j < a.ny - 1) {
         // away from the domain sides and from solid sources: the plain interior pull
         const int64_t s[4] = {c + a.nx + 1, c + a.nx - 1, c - a.nx - 1, c - a.nx + 1};
-        if (!(a.solid[s[0]] | a.solid[s[1]] | a.solid[s[2]] | a.solid[s[3]])) {
+        if (!(a.solid[LBRS_IX(s[0], a.N, 6)] | a.solid[LBRS_IX(s[1], a.N, 6)] | a.solid[LBRS_IX(s[2], a.N, 6)] | a.solid[LBRS_IX(s[3], a.N, 6)])) {
 #pragma unroll
             for (int q = 0; q < 4; ++q)
 #pragma unroll
-                for (int k = 0; k < 4; ++k) f[q][k] = a.src[(q * 4 + k) * a.N + s[q]];
+                for (int k = 0; k < 4; ++k) f[q][k] = a.src[LBRS_IX((q * 4 + k) * a.N + s[q], 16 * a.N, 6)];
             collide_store_2d<T, STORE_U>(a, c, f);
             return;
         }
@@ -538,7 +571,7 @@ __global__ void __launch_bounds__(256) step2d_adapt_kernel(const StepArgs<T> a, 
 #pragma unroll
             for (int q = 0; q < 4; ++q)
 #pragma unroll
-                for (int k = 0; k < 4; ++k) f[q][k] = a.src[(q * 4 + k) * a.N + s[q]];
+                for (int k = 0; k < 4; ++k) f[q][k] = a.src[LBRS_IX((q * 4 + k) * a.N + s[q], 16 * a.N, 7)];
         } else {
             pull_edge_2d<T>(a, i, j, f);
         }
@@ -546,7 +579,7 @@ __global__ void __launch_bounds__(256) step2d_adapt_kernel(const StepArgs<T> a, 
     if (st->skip) {            // the same for every thread of the grid
         if (in) {
 #pragma unroll
-            for (int n = 0; n < 16; ++n) a.dst[n * a.N + c] = a.src[n * a.N + c];
+            for (int n = 0; n < 16; ++n) a.dst[LBRS_IX(n * a.N + c, 16 * a.N, 7)] = a.src[LBRS_IX(n * a.N + c, 16 * a.N, 7)];
         }
         return;
     }
@@ -559,7 +592,7 @@ __global__ void __launch_bounds__(256) step2d_adapt_kernel(const StepArgs<T> a, 
 #pragma unroll
         for (int q = 0; q < 4; ++q)
 #pragma unroll
-            for (int k = 0; k < 4; ++k) a.dst[(q * 4 + k) * a.N + c] = out[q][k];
+            for (int k = 0; k < 4; ++k) a.dst[LBRS_IX((q * 4 + k) * a.N + c, 16 * a.N, 7)] = out[q][k];
         bnd = bound_local<T>(U, gamma);
     }
     block_max_into<256>(bnd, &st->bound_bits[st->slot_cur]);
@@ -598,7 +631,7 @@ __global__ void __launch_bounds__(256) step2ds_kernel(const StepArgs<T> a)
     if (i > 0 && i < a.nx - 1 && j > 0 && j < a.ny - 1) {
         const int64_t s[4] = {c + a.nx + 1, c + a.nx - 1, c - a.nx - 1, c - a.nx + 1};
 #pragma unroll
-        for (int q = 0; q < 4; ++q) f[q] = a.src[q * a.N + s[q]];
+        for (int q = 0; q < 4; ++q) f[q] = a.src[LBRS_IX(q * a.N + s[q], 4 * a.N, 8)];
     } else {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -637,7 +670,7 @@ __global__ void __launch_bounds__(256) step2ds_kernel(const StepArgs<T> a)
                 for (int r = 1; r < 4; ++r)
                     if (r == q) f[q] = e[r];
             } else {
-                f[q] = a.src[q * a.N + (int64_t)sj * a.nx + si];
+                f[q] = a.src[LBRS_IX(q * a.N + (int64_t)sj * a.nx + si, 4 * a.N, 8)];
             }
         }
     }
@@ -645,7 +678,7 @@ __global__ void __launch_bounds__(256) step2ds_kernel(const StepArgs<T> a)
     T e[4];
     equilibria2ds<T>(u, a.c, e);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) a.dst[q * a.N + c] = a.om1 * f[q] + a.om * e[q];
+    for (int q = 0; q < 4; ++q) a.dst[LBRS_IX(q * a.N + c, 4 * a.N, 8)] = a.om1 * f[q] + a.om * e[q];
 }
 
 // ---------------------------------------------------------------- D1Q2 step
@@ -668,7 +701,7 @@ __global__ void __launch_bounds__(256) step1d_kernel(const StepArgs<T> a)
             else si = si < 0 ? 0 : a.nx - 1;
         }
 #pragma unroll
-        for (int k = 0; k < 3; ++k) f[q][k] = g ? g[k] : a.src[(q * 3 + k) * a.N + si];
+        for (int k = 0; k < 3; ++k) f[q][k] = g ? g[k] : a.src[LBRS_IX((q * 3 + k) * a.N + si, 6 * a.N, 9)];
     }
     T U[3];
 #pragma unroll
@@ -678,7 +711,7 @@ __global__ void __launch_bounds__(256) step1d_kernel(const StepArgs<T> a)
 #pragma unroll
     for (int q = 0; q < 2; ++q)
 #pragma unroll
-        for (int k = 0; k < 3; ++k) a.dst[(q * 3 + k) * a.N + i] = a.om1 * f[q][k] + a.om * e[q][k];
+        for (int k = 0; k < 3; ++k) a.dst[LBRS_IX((q * 3 + k) * a.N + i, 6 * a.N, 9)] = a.om1 * f[q][k] + a.om * e[q][k];
 }
 
 // ---------------------------------------------------------------- D1Q3 step
@@ -702,10 +735,10 @@ __global__ void __launch_bounds__(256) step1d_q3_kernel(const StepArgs<T> a)
             else si = si < 0 ? 0 : a.nx - 1;
         }
 #pragma unroll
-        for (int k = 0; k < 3; ++k) f[q][k] = g ? g[k] : a.src[(q * 3 + k) * a.N + si];
+        for (int k = 0; k < 3; ++k) f[q][k] = g ? g[k] : a.src[LBRS_IX((q * 3 + k) * a.N + si, 9 * a.N, 9)];
     }
 #pragma unroll
-    for (int k = 0; k < 3; ++k) f[1][k] = a.src[(3 + k) * a.N + i];
+    for (int k = 0; k < 3; ++k) f[1][k] = a.src[LBRS_IX((3 + k) * a.N + i, 9 * a.N, 9)];
     T U[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) U[k] = (f[0][k] + f[1][k]) + f[2][k];
@@ -714,7 +747,7 @@ __global__ void __launch_bounds__(256) step1d_q3_kernel(const StepArgs<T> a)
 #pragma unroll
     for (int q = 0; q < 3; ++q)
 #pragma unroll
-        for (int k = 0; k < 3; ++k) a.dst[(q * 3 + k) * a.N + i] = a.om1 * f[q][k] + a.om * e[q][k];
+        for (int k = 0; k < 3; ++k) a.dst[LBRS_IX((q * 3 + k) * a.N + i, 9 * a.N, 9)] = a.om1 * f[q][k] + a.om * e[q][k];
 }
 
 // ---------------------------------------------------------------- adjoint (periodic D2Q4)
@@ -791,9 +824,9 @@ __global__ void __launch_bounds__(256) adjoint2d_kernel(const AdjArgs<T> a)
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) g[q][k] = a.gin[(q * 4 + k) * a.N + c];
+        for (int k = 0; k < 4; ++k) g[q][k] = a.gin[LBRS_IX((q * 4 + k) * a.N + c, 16 * a.N, 30)];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) U[k] = a.U[k * a.N + c];
+    for (int k = 0; k < 4; ++k) U[k] = a.U[LBRS_IX(k * a.N + c, 4 * a.N, 30)];
     equilibrium_vjp2d<T>(U, g, a.gamma, a.gm1, a.c, ubar);
     // targets x - c_q: q0 (-,-) -> (i+1, j+1); q1 (+,-) -> (i-1, j+1); q2 (+,+) -> (i-1, j-1); q3 (-,+) -> (i+1, j-1)
     const int ip = i + 1 == a.nx ? 0 : i + 1, im = i == 0 ? a.nx - 1 : i - 1;
@@ -806,7 +839,7 @@ __global__ void __launch_bounds__(256) adjoint2d_kernel(const AdjArgs<T> a)
     for (int q = 0; q < 4; ++q)
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            a.gout[(q * 4 + k) * a.N + t[q]] = eq_only ? ubar[k] : a.om1 * g[q][k] + a.om * ubar[k];
+            a.gout[LBRS_IX((q * 4 + k) * a.N + t[q], 16 * a.N, 30)] = eq_only ? ubar[k] : a.om1 * g[q][k] + a.om * ubar[k];
 }
 
 // dL/dU0 = J_E(U0)^T dL/df*^0, per cell.
@@ -818,12 +851,12 @@ __global__ void __launch_bounds__(256) vjp_equilibrium2d_kernel(const AdjArgs<T>
 #pragma unroll
         for (int q = 0; q < 4; ++q)
 #pragma unroll
-            for (int k = 0; k < 4; ++k) g[q][k] = a.gin[(q * 4 + k) * a.N + c];
+            for (int k = 0; k < 4; ++k) g[q][k] = a.gin[LBRS_IX((q * 4 + k) * a.N + c, 16 * a.N, 31)];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) U[k] = a.U[k * a.N + c];
+        for (int k = 0; k < 4; ++k) U[k] = a.U[LBRS_IX(k * a.N + c, 4 * a.N, 31)];
         equilibrium_vjp2d<T>(U, g, a.gamma, a.gm1, a.c, ubar);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) a.gout[k * a.N + c] = ubar[k];
+        for (int k = 0; k < 4; ++k) a.gout[LBRS_IX(k * a.N + c, 4 * a.N, 31)] = ubar[k];
     }
 }
 

@@ -64,6 +64,9 @@ __global__ void __launch_bounds__(kTX * kTY) step2d_tile_kernel(const F16Args a)
     // phase 1: f* of each window slot, its source resolved like the pull does
     for (int w = threadIdx.x; w < kWN; w += kTX * kTY) {
         int i = i0 + w % kWX, j = j0 + w / kWX;
+        // a slot more than one cell outside the grid is no tile cell's source (and one
+        // wrap would not bring it inside a periodic grid narrower than the tile)
+        if (i < -1 || i > a.nx || j < -1 || j > a.ny) continue;
         const int side_x = i < 0 ? 0 : (i >= a.nx ? 1 : -1);
         const int side_y = j < 0 ? 2 : (j >= a.ny ? 3 : -1);
         const int kind_x = side_x == 0 ? a.bc[0] : a.bc[1];
@@ -83,21 +86,21 @@ __global__ void __launch_bounds__(kTX * kTY) step2d_tile_kernel(const F16Args a)
         }
         if (g) {
 #pragma unroll
-            for (int n = 0; n < 16; ++n) s_f[n * kWN + w] = g[n];
+            for (int n = 0; n < 16; ++n) s_f[LBRS_IX(n * kWN + w, 16 * kWN, 40)] = g[n];
             continue;
         }
         const int64_t c = (int64_t)j * a.nx + i;
         float U[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) U[k] = a.Uin[k * a.N + c];
+        for (int k = 0; k < 4; ++k) U[k] = a.Uin[LBRS_IX(k * a.N + c, 4 * a.N, 41)];
         float e[4][4];
         equilibria2d<float>(U, a.gm1, a.c, e);
         if constexpr (F16) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const float g0 = __half2float(a.gin[k * a.N + c]);
-                const float g1 = __half2float(a.gin[(4 + k) * a.N + c]);
-                const float g2 = __half2float(a.gin[(8 + k) * a.N + c]);
+                const float g0 = __half2float(a.gin[LBRS_IX(k * a.N + c, 12 * a.N, 41)]);
+                const float g1 = __half2float(a.gin[LBRS_IX((4 + k) * a.N + c, 12 * a.N, 41)]);
+                const float g2 = __half2float(a.gin[LBRS_IX((8 + k) * a.N + c, 12 * a.N, 41)]);
                 e[0][k] += sc[k] * g0;
                 e[1][k] += sc[k] * g1;
                 e[2][k] += sc[k] * g2;
@@ -107,7 +110,7 @@ __global__ void __launch_bounds__(kTX * kTY) step2d_tile_kernel(const F16Args a)
 #pragma unroll
         for (int q = 0; q < 4; ++q)
 #pragma unroll
-            for (int k = 0; k < 4; ++k) s_f[(q * 4 + k) * kWN + w] = e[q][k];
+            for (int k = 0; k < 4; ++k) s_f[LBRS_IX((q * 4 + k) * kWN + w, 16 * kWN, 40)] = e[q][k];
     }
     __syncthreads();
 
@@ -122,7 +125,7 @@ __global__ void __launch_bounds__(kTX * kTY) step2d_tile_kernel(const F16Args a)
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) f[q][k] = s_f[(q * 4 + k) * kWN + src[q]];
+        for (int k = 0; k < 4; ++k) f[q][k] = s_f[LBRS_IX((q * 4 + k) * kWN + src[q], 16 * kWN, 40)];
     const bool wall_bottom = j == 0 && a.bc[2] == BC_WALL;
     const bool wall_top = j == a.ny - 1 && a.bc[3] == BC_WALL;
 #pragma unroll
@@ -142,7 +145,7 @@ __global__ void __launch_bounds__(kTX * kTY) step2d_tile_kernel(const F16Args a)
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         U[k] = ((f[0][k] + f[1][k]) + f[2][k]) + f[3][k];
-        a.Uout[k * a.N + c] = U[k];
+        a.Uout[LBRS_IX(k * a.N + c, 4 * a.N, 41)] = U[k];
     }
     if constexpr (F16) {
         float e[4][4];
@@ -151,7 +154,7 @@ __global__ void __launch_bounds__(kTX * kTY) step2d_tile_kernel(const F16Args a)
         for (int q = 0; q < 3; ++q)
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                a.gout[(q * 4 + k) * a.N + c] = __float2half_rn(a.om1 * (f[q][k] - e[q][k]) * inv[k]);
+                a.gout[LBRS_IX((q * 4 + k) * a.N + c, 12 * a.N, 41)] = __float2half_rn(a.om1 * (f[q][k] - e[q][k]) * inv[k]);
     }
 }
 
@@ -274,5 +277,8 @@ cudaError_t launch_set_state_f16neq(const void* W, int w_dtype, int kind, void* 
     field_scale_kernel<<<1, 32, 0, st>>>(absmax_bits, scale);
     return cudaGetLastError();
 }
+
+// First out-of-bounds index recorded by this unit's kernels (LBRS_DEBUG builds; 0 otherwise).
+LBRS_DEBUG_WORD(debug_word_f16)
 
 }  // namespace lbrs

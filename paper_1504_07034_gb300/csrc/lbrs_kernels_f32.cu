@@ -248,7 +248,7 @@ __device__ __forceinline__ void step2_phase2(const StepArgs<float>& a, const flo
 #pragma unroll
         for (int q = 0; q < 4; ++q)
 #pragma unroll
-            for (int k = 0; k < 4; ++k) f[q][k] = s_f[(q * 4 + k) * kFWN + sl[q]];
+            for (int k = 0; k < 4; ++k) f[q][k] = s_f[LBRS_IX((q * 4 + k) * kFWN + sl[q], 16 * kFWN, 12)];
         collide_store_2d<float, STORE_U>(a, (int64_t)j * a.nx + i, f);
         return;
     }
@@ -281,7 +281,7 @@ __device__ __forceinline__ void step2_phase2(const StepArgs<float>& a, const flo
         } else {
             const int slot = (sj - (j0 - 1)) * kFWX + (si - (i0 - 1));
 #pragma unroll
-            for (int k = 0; k < 4; ++k) f[q][k] = s_f[(q * 4 + k) * kFWN + slot];
+            for (int k = 0; k < 4; ++k) f[q][k] = s_f[LBRS_IX((q * 4 + k) * kFWN + slot, 16 * kFWN, 12)];
         }
     }
 #pragma unroll
@@ -309,12 +309,12 @@ __device__ __forceinline__ void step2_store_slot(const StepArgs<float>& a, float
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) s_f[(q * 4 + k) * kFWN + w] = out[q][k];
+        for (int k = 0; k < 4; ++k) s_f[LBRS_IX((q * 4 + k) * kFWN + w, 16 * kFWN, 11)] = out[q][k];
     if constexpr (STORE_U) {
         const int i = i0 - 1 + wi, j = j0 - 1 + wj;
         if (wi >= 1 && wi <= kFTX && wj >= 1 && wj <= kFTY && i < a.nx && j < a.ny) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) a.Uout[k * a.N + (int64_t)j * a.nx + i] = U[k];
+            for (int k = 0; k < 4; ++k) a.Uout[LBRS_IX(k * a.N + (int64_t)j * a.nx + i, 4 * a.N, 11)] = U[k];
         }
     }
 }
@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(kFTX * kFTY, 4) step2d_f32_fused2_kernel(const
 #pragma unroll
             for (int q = 0; q < 4; ++q)
 #pragma unroll
-                for (int k = 0; k < 4; ++k) f[q][k] = a.src[(q * 4 + k) * a.N + src[q]];
+                for (int k = 0; k < 4; ++k) f[q][k] = a.src[LBRS_IX((q * 4 + k) * a.N + src[q], 16 * a.N, 10)];
         } else {
             pull_edge_2d<float>(a, i, j, f);
         }
@@ -425,7 +425,7 @@ __device__ __forceinline__ void step2_phase1_raw(const StepArgs<float>& a, const
 #pragma unroll
             for (int q = 0; q < 4; ++q)
 #pragma unroll
-                for (int k = 0; k < 4; ++k) f[q][k] = s_raw[(q * 4 + k) * kPN + r[q]];
+                for (int k = 0; k < 4; ++k) f[q][k] = s_raw[LBRS_IX((q * 4 + k) * kPN + r[q], 16 * kPN, 13)];
             float U[4], out[4][4];
             collide_2d<float>(a, f, U, out);
             step2_store_slot<STORE_U>(a, s_f, w, wi, wj, i0, j0, U, out);
@@ -452,7 +452,7 @@ __device__ __forceinline__ void step2_phase1_raw(const StepArgs<float>& a, const
 #pragma unroll
             for (int q = 0; q < 4; ++q)
 #pragma unroll
-                for (int k = 0; k < 4; ++k) f[q][k] = s_raw[(q * 4 + k) * kPN + r[q]];
+                for (int k = 0; k < 4; ++k) f[q][k] = s_raw[LBRS_IX((q * 4 + k) * kPN + r[q], 16 * kPN, 13)];
         } else {
             pull_edge_2d<float>(a, i, j, f);
         }
@@ -492,7 +492,7 @@ __device__ __forceinline__ bool load_mask_window(const StepArgs<float>& a, uint8
             else if (kind == BC_TRANSMISSIVE) j = j < 0 ? 0 : a.ny - 1;
             else fluid = true;
         }
-        const uint8_t v = !fluid && a.solid[(int64_t)j * a.nx + i] ? 1 : 0;
+        const uint8_t v = !fluid && a.solid[LBRS_IX((int64_t)j * a.nx + i, a.N, 14)] ? 1 : 0;
         s_m[m] = v;
         any |= v;
     }
@@ -501,7 +501,7 @@ __device__ __forceinline__ bool load_mask_window(const StepArgs<float>& a, uint8
 
 __device__ __forceinline__ bool msolid(const uint8_t* s_m, int i, int j, int i0, int j0)
 {
-    return s_m[(j - j0 + 2) * kMX + (i - i0 + 2)] != 0;
+    return s_m[LBRS_IX((j - j0 + 2) * kMX + (i - i0 + 2), kMN, 14)] != 0;
 }
 
 // Phase 1 with internal walls: solid window slots are skipped (phase 2 never
@@ -534,7 +534,7 @@ __device__ __forceinline__ void step2_phase1_obst(const StepArgs<float>& a, cons
 #pragma unroll
             for (int q = 0; q < 4; ++q)
 #pragma unroll
-                for (int k = 0; k < 4; ++k) f[q][k] = s_raw[(q * 4 + k) * kPN + r[q]];
+                for (int k = 0; k < 4; ++k) f[q][k] = s_raw[LBRS_IX((q * 4 + k) * kPN + r[q], 16 * kPN, 13)];
         } else {
             pull_obstacle_2d<float>(a, i, j, f);
         }
@@ -556,7 +556,7 @@ __device__ __forceinline__ void step2_phase2_obst(const StepArgs<float>& a, cons
     const int64_t c = (int64_t)j * a.nx + i;
     if (msolid(s_m, i, j, i0, j0)) {
 #pragma unroll
-        for (int n = 0; n < 16; ++n) a.dst[n * a.N + c] = a.src[n * a.N + c];
+        for (int n = 0; n < 16; ++n) a.dst[LBRS_IX(n * a.N + c, 16 * a.N, 15)] = a.src[LBRS_IX(n * a.N + c, 16 * a.N, 15)];
         return;
     }
     const int SX[4] = {-1, 1, 1, -1};
@@ -594,7 +594,7 @@ __device__ __forceinline__ void step2_phase2_obst(const StepArgs<float>& a, cons
         } else {
             const int slot = (sj - (j0 - 1)) * kFWX + (si - (i0 - 1));
 #pragma unroll
-            for (int k = 0; k < 4; ++k) f[q][k] = s_f[(q * 4 + k) * kFWN + slot];
+            for (int k = 0; k < 4; ++k) f[q][k] = s_f[LBRS_IX((q * 4 + k) * kFWN + slot, 16 * kFWN, 12)];
         }
     }
 #pragma unroll
@@ -722,14 +722,14 @@ __device__ __forceinline__ void adj_gather(const AdjArgs<float>& a, int i, int j
 #pragma unroll
         for (int q = 0; q < 4; ++q)
 #pragma unroll
-            for (int k = 0; k < 4; ++k) g[q][k] = a.gin[(q * 4 + k) * a.N + src[q]];
+            for (int k = 0; k < 4; ++k) g[q][k] = a.gin[LBRS_IX((q * 4 + k) * a.N + src[q], 16 * a.N, 32)];
         return;
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int64_t s = (int64_t)wrap_index(j + SY[q], a.ny) * a.nx + wrap_index(i + SX[q], a.nx);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) g[q][k] = a.gin[(q * 4 + k) * a.N + s];
+        for (int k = 0; k < 4; ++k) g[q][k] = a.gin[LBRS_IX((q * 4 + k) * a.N + s, 16 * a.N, 32)];
     }
 }
 
@@ -741,14 +741,14 @@ __global__ void __launch_bounds__(256) adj_local_kernel(const AdjArgs<float> a)
 #pragma unroll
         for (int q = 0; q < 4; ++q)
 #pragma unroll
-            for (int k = 0; k < 4; ++k) g[q][k] = a.gin[(q * 4 + k) * a.N + c];
+            for (int k = 0; k < 4; ++k) g[q][k] = a.gin[LBRS_IX((q * 4 + k) * a.N + c, 16 * a.N, 32)];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) U[k] = a.U[k * a.N + c];
+        for (int k = 0; k < 4; ++k) U[k] = a.U[LBRS_IX(k * a.N + c, 4 * a.N, 32)];
         adj_local(a, U, g, out);
 #pragma unroll
         for (int q = 0; q < 4; ++q)
 #pragma unroll
-            for (int k = 0; k < 4; ++k) a.gout[(q * 4 + k) * a.N + c] = out[q][k];
+            for (int k = 0; k < 4; ++k) a.gout[LBRS_IX((q * 4 + k) * a.N + c, 16 * a.N, 32)] = out[q][k];
     }
 }
 
@@ -765,7 +765,7 @@ __global__ void __launch_bounds__(256) adj_pull_kernel(const AdjArgs<float> a)
     if (a.U) {
         float U[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) U[k] = a.U[k * a.N + c];
+        for (int k = 0; k < 4; ++k) U[k] = a.U[LBRS_IX(k * a.N + c, 4 * a.N, 32)];
         adj_local(a, U, g, out);
     } else {
 #pragma unroll
@@ -776,7 +776,7 @@ __global__ void __launch_bounds__(256) adj_pull_kernel(const AdjArgs<float> a)
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) a.gout[(q * 4 + k) * a.N + c] = out[q][k];
+        for (int k = 0; k < 4; ++k) a.gout[LBRS_IX((q * 4 + k) * a.N + c, 16 * a.N, 32)] = out[q][k];
 }
 
 // Two steps: k^s (a.gin) -> k^{s-2} (a.gout); a.U = U_{s-1}, U2 = U_{s-2}.
@@ -790,12 +790,12 @@ __global__ void __launch_bounds__(kFTX * kFTY, 4) adj_fused2_kernel(const AdjArg
         adj_gather(a, i, j, g);
         const int64_t c = (int64_t)j * a.nx + i;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) U[k] = a.U[k * a.N + c];
+        for (int k = 0; k < 4; ++k) U[k] = a.U[LBRS_IX(k * a.N + c, 4 * a.N, 33)];
         adj_local(a, U, g, out);
 #pragma unroll
         for (int q = 0; q < 4; ++q)
 #pragma unroll
-            for (int k = 0; k < 4; ++k) s_k[(q * 4 + k) * kFWN + w] = out[q][k];
+            for (int k = 0; k < 4; ++k) s_k[LBRS_IX((q * 4 + k) * kFWN + w, 16 * kFWN, 33)] = out[q][k];
     }
     __syncthreads();
     const int ti = threadIdx.x % kFTX, tj = threadIdx.x / kFTX;
@@ -808,15 +808,15 @@ __global__ void __launch_bounds__(kFTX * kFTY, 4) adj_fused2_kernel(const AdjArg
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) g[q][k] = s_k[(q * 4 + k) * kFWN + sl[q]];
+        for (int k = 0; k < 4; ++k) g[q][k] = s_k[LBRS_IX((q * 4 + k) * kFWN + sl[q], 16 * kFWN, 33)];
     const int64_t c = (int64_t)j * a.nx + i;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) U[k] = U2[k * a.N + c];
+    for (int k = 0; k < 4; ++k) U[k] = U2[LBRS_IX(k * a.N + c, 4 * a.N, 33)];
     adj_local(a, U, g, out);
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) a.gout[(q * 4 + k) * a.N + c] = out[q][k];
+        for (int k = 0; k < 4; ++k) a.gout[LBRS_IX((q * 4 + k) * a.N + c, 16 * a.N, 33)] = out[q][k];
 }
 
 // Kernel variant for D2Q4 FP32: 0 = scalar one cell per thread, 2 or 4 =
@@ -1089,5 +1089,8 @@ cudaError_t launch_batch_copy_f32(const float* src, float* dst, int64_t N, const
     batch_copy_kernel<float><<<ntiles, 256, 0, s>>>(src, dst, N, tiles, tube_off, planes);
     return cudaGetLastError();
 }
+
+// First out-of-bounds index recorded by this unit's kernels (LBRS_DEBUG builds; 0 otherwise).
+LBRS_DEBUG_WORD(debug_word_f32)
 
 }  // namespace lbrs

@@ -732,4 +732,7 @@ cudaError_t launch_adapt_init_bound_f64(const void* fs, int64_t N, double gamma,
     return cudaGetLastError();
 }
 
+// First out-of-bounds index recorded by this unit's kernels (LBRS_DEBUG builds; 0 otherwise).
+LBRS_DEBUG_WORD(debug_word_f64)
+
 }  // namespace lbrs

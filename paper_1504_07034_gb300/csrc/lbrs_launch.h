@@ -31,6 +31,12 @@ template <typename T>
 struct BatchArgs;
 struct BatchTile;
 
+// The LBRS_DEBUG build's first out-of-bounds record of each kernel unit
+// ((site << 40) | index, 0 if none; clear != 0 zeroes it); 0 in release builds.
+unsigned long long debug_word_f32(int clear);
+unsigned long long debug_word_f64(int clear);
+unsigned long long debug_word_f16(int clear);
+
 // One time step src -> dst.  lattice: LAT_D1Q2 / LAT_D2Q4.
 cudaError_t launch_step_f64(int lattice, const StepArgs<double>& a, cudaStream_t s);
 cudaError_t launch_step_f32(int lattice, const StepArgs<float>& a, cudaStream_t s);

@@ -491,6 +491,28 @@ extern "C" {
 
 int lbrs_abi_version(void) { return LBRS_ABI_VERSION; }
 
+int lbrs_debug_build(void)
+{
+#ifdef LBRS_DEBUG
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+lbrs_status lbrs_debug_check(uint64_t* first)
+{
+    if (!first) return fail(nullptr, LBRS_EINVAL, "first is NULL");
+    unsigned long long w = 0ull;
+    for (unsigned long long v : {debug_word_f32(1), debug_word_f64(1), debug_word_f16(1)})
+        if (!w) w = v;
+    *first = (uint64_t)w;
+    if (w)
+        return fail(nullptr, LBRS_ECUDA, "index out of bounds (bounds-checked build): site %llu, index %llu",
+                    w >> 40, w & ((1ull << 40) - 1));
+    return LBRS_OK;
+}
+
 const char* lbrs_status_string(lbrs_status s)
 {
     switch (s) {
@@ -683,6 +705,14 @@ lbrs_status lbrs_sync(lbrs_ctx* ctx)
         LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
         if (flag) return fail(ctx, LBRS_ETIMEOUT, "a bounded wait for a tile copy gave up; the state is not valid");
     }
+#ifdef LBRS_DEBUG
+    {
+        uint64_t w = 0;
+        if (lbrs_debug_check(&w) != LBRS_OK)
+            return fail(ctx, LBRS_ECUDA, "index out of bounds (bounds-checked build): site %llu, index %llu",
+                        (unsigned long long)(w >> 40), (unsigned long long)(w & ((1ull << 40) - 1)));
+    }
+#endif
     if (ctx->cfg.diag_every > 0 && ctx->has_state) {
         double st[4];
         LBRS_CUDA(ctx, cudaMemcpyAsync(st, ctx->ws + ctx->L.status, sizeof st, cudaMemcpyDeviceToHost, ctx->stream));

@@ -170,8 +170,12 @@ class Solver:
                 "n_nonphysical": d.n_nonphysical, "n_subchar": d.n_subchar}
 
     def get_distributions(self, out: torch.Tensor | None = None) -> torch.Tensor:
+        """The raw state.  For the reduced storage forms (f16neq: U and the FP16
+        non-equilibrium parts; f32u: U) it fills only the leading bytes of the
+        (Q, K, *grid) tensor; a tensor allocated here is zero beyond them."""
         if out is None:
-            out = torch.empty((self.Q, self.K) + self.grid, dtype=self.storage_dtype, device=self.device)
+            alloc = torch.empty if self.precision in ("f64", "f32") else torch.zeros
+            out = alloc((self.Q, self.K) + self.grid, dtype=self.storage_dtype, device=self.device)
         if out.dtype != self.storage_dtype or not out.is_contiguous() or out.numel() != self.Q * self.K * self.nx * self.ny:
             raise ValueError("out must be a contiguous (Q, K, *grid) tensor of the storage dtype")
         self._check(self.lib.lbrs_get_distributions(self.ctx, ctypes.c_void_p(out.data_ptr()), 1 if out.is_cuda else 0))
