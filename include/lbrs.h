@@ -161,6 +161,15 @@ int lbrs_abi_version(void);
 int lbrs_debug_build(void);
 lbrs_status lbrs_debug_check(uint64_t* first);
 
+/* Failure-detection self-test (not a method of the paper).  Every device wait of the
+ * library is bounded: the tile kernels' waits for their tensor copies give up after a
+ * fixed number of polls, raise a flag in the workspace and leave their tile unwritten,
+ * and lbrs_sync reports the flag as LBRS_ETIMEOUT; setting a state clears it.  This call
+ * enqueues on the context's stream one block whose bounded wait, on an mbarrier that
+ * nothing completes, runs out and raises the same flag, so that the reporting path can
+ * be exercised without a fault.  The distributions are not touched. */
+lbrs_status lbrs_selftest_wait_timeout(lbrs_ctx* ctx);
+
 /* Human-readable name of a status code. Never NULL. */
 const char* lbrs_status_string(lbrs_status s);
 

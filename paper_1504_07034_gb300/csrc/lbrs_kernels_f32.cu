@@ -689,6 +689,23 @@ __global__ void __launch_bounds__(kFTX * kFTY, 5)
     step2_phase2<STORE_U>(second_step_args(a, STORE_U), s_f, i0, j0);
 }
 
+// Failure-detection self-test: one block waits, with the tile kernels' bounded wait,
+// on an mbarrier that nothing completes (no copy, no arrival); the wait gives up after
+// `polls` polls and the block raises *wait_flag as the tile kernels do.  Nothing is in
+// flight when it returns.
+__global__ void __launch_bounds__(32) wait_timeout_selftest_kernel(unsigned* wait_flag, int polls)
+{
+    __shared__ uint64_t bar;
+    const uint32_t b = smem_addr(&bar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool arrived = mbar_wait_bounded(b, 0, polls);
+    if (!__syncthreads_and(arrived) && threadIdx.x == 0) atomicExch(wait_flag, 1u);
+}
+
 // ---------------------------------------------------------------- adjoint, two steps per launch
 //
 // The adjoint step pushes fbar(x) = (1 - w) g(x) + w J_E(U(x))^T g(x) to x - c_q.
@@ -966,6 +983,12 @@ cudaError_t launch_step2_f32(const StepArgs<float>& a, const TileMap* map, unsig
         if (rec) step2d_f32_fused2_kernel<true><<<grid, kFTX * kFTY, 0, s>>>(a);
         else step2d_f32_fused2_kernel<false><<<grid, kFTX * kFTY, 0, s>>>(a);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wait_timeout_selftest(unsigned* wait_flag, cudaStream_t s)
+{
+    wait_timeout_selftest_kernel<<<1, 32, 0, s>>>(wait_flag, 1 << 12);
     return cudaGetLastError();
 }
 

@@ -491,6 +491,14 @@ extern "C" {
 
 int lbrs_abi_version(void) { return LBRS_ABI_VERSION; }
 
+lbrs_status lbrs_selftest_wait_timeout(lbrs_ctx* ctx)
+{
+    if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
+    LBRS_CUDA(ctx, launch_wait_timeout_selftest(wait_flag(ctx), ctx->stream));
+    ctx->launches += 1;
+    return LBRS_OK;
+}
+
 int lbrs_debug_build(void)
 {
 #ifdef LBRS_DEBUG
@@ -699,7 +707,7 @@ lbrs_status lbrs_sync(lbrs_ctx* ctx)
 {
     if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
     LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    if (ctx->tmap[0].valid || ctx->tmap[1].valid) {
+    {
         unsigned flag = 0;
         LBRS_CUDA(ctx, cudaMemcpyAsync(&flag, wait_flag(ctx), sizeof flag, cudaMemcpyDeviceToHost, ctx->stream));
         LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
