@@ -735,7 +735,7 @@ def run_ours(args):
             "gpu_launches": launches,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "step2d_f32_fused2_tma_kernel<false, false>", "peak_kind": f"{peak_kind} hbm_gbs",
+                         "kernel": "step2d_f32_fused2_tall_kernel<false>", "peak_kind": f"{peak_kind} hbm_gbs",
                          "algorithmic_bytes_per_launch": 2 * BYTES_PER_LUP_F32_FUSED2 * wl.cells,
                          "algorithmic_bytes_per_lup": BYTES_PER_LUP_F32_FUSED2,
                          "timed_call": "lbrs_step(2): one launch of the two-steps-per-launch kernel"},

@@ -629,16 +629,19 @@ __device__ __forceinline__ void step2_phase2_obst(const StepArgs<float>& a, cons
     collide_store_2d<float>(a, c, f);
 }
 
+// The four population boxes of tile (i0, j0), each PN floats per field (36 columns
+// and PN / 36 rows), onto one mbarrier.
+template <int PN = kPN>
 __device__ __forceinline__ void issue_tile_copy(const CUtensorMap* tmap, float* s_raw, uint32_t bar, int i0, int j0)
 {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kRawBytes) : "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(16u * PN * 4u) : "memory");
     const int x0[4] = {i0, i0 - 4, i0 - 4, i0};
     const int y0[4] = {j0, j0, j0 - 2, j0 - 2};
 #pragma unroll
     for (int q = 0; q < 4; ++q)
         asm volatile(
             "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-            " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(s_raw + q * 4 * kPN)),
+            " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(s_raw + q * 4 * PN)),
             "l"((uint64_t)tmap), "r"(x0[q]), "r"(y0[q]), "r"(q * 4), "r"(bar)
             : "memory");
 }
@@ -687,6 +690,186 @@ __global__ void __launch_bounds__(kFTX * kFTY, 5)
     step2_phase1_raw<STORE_U>(a, s_raw, s_f, i0, j0);
     __syncthreads();
     step2_phase2<STORE_U>(second_step_args(a, STORE_U), s_f, i0, j0);
+}
+
+// ---------------------------------------------------------------- two steps per launch, 32 x 16 tiles
+//
+// The same two steps on tiles of 32 x 16 cells (two cells per thread in phase 2),
+// the window's post-collision populations written over the copied boxes: population
+// q of window slot w is pulled from exactly one box position, which no other slot
+// reads, so each thread overwrites the 16 values it has just read (no hazard between
+// threads) and phase 2 reads population q of a slot where it was pulled from.  The
+// boxes (36 x 18 per field) are the only shared-memory buffer: 40.5 KB, five blocks
+// per SM.  Against the 32 x 8 tile this recomputes 612 window slots per 512 cells
+// instead of 340 per 256 and re-reads fewer halo rows.
+constexpr int kTY = 16, kTWY = kTY + 2, kTWN = kFWX * kTWY, kTPY = kTY + 2, kTPN = kPX * kTPY;
+constexpr size_t kTallSmemBytes = 128 + 16u * kTPN * sizeof(float) + 16;
+
+// Position of population q, field k of window slot (wi, wj) in the tall boxes.
+__device__ __forceinline__ int tall_pos(int q, int k, int wi, int wj)
+{
+    return (q * 4 + k) * kTPN + wj * kPX + wi + ((q == 1 || q == 2) ? 2 : 0);
+}
+
+template <bool STORE_U>
+__device__ __forceinline__ void tall_store_slot(const StepArgs<float>& a, float* s_raw, int wi, int wj, int i0, int j0,
+                                                const float U[4], const float out[4][4])
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) s_raw[LBRS_IX(tall_pos(q, k, wi, wj), 16 * kTPN, 16)] = out[q][k];
+    if constexpr (STORE_U) {
+        const int i = i0 - 1 + wi, j = j0 - 1 + wj;
+        if (wi >= 1 && wi <= kFTX && wj >= 1 && wj <= kTY && i < a.nx && j < a.ny) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) a.Uout[LBRS_IX(k * a.N + (int64_t)j * a.nx + i, 4 * a.N, 16)] = U[k];
+        }
+    }
+}
+
+// Phase 1 on the 34 x 18 window, in place.
+template <bool STORE_U>
+__device__ __forceinline__ void tall_phase1(const StepArgs<float>& a, float* s_raw, int i0, int j0)
+{
+    if (i0 >= 2 && j0 >= 2 && i0 + kFTX + 2 <= a.nx && j0 + kTY + 2 <= a.ny) {
+        for (int w = threadIdx.x; w < kTWN; w += kFTX * kFTY) {
+            const int wi = w % kFWX, wj = w / kFWX;
+            float f[4][4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) f[q][k] = s_raw[LBRS_IX(tall_pos(q, k, wi, wj), 16 * kTPN, 16)];
+            float U[4], out[4][4];
+            collide_2d<float>(a, f, U, out);
+            tall_store_slot<STORE_U>(a, s_raw, wi, wj, i0, j0, U, out);
+        }
+        return;
+    }
+    const bool px = a.bc[0] == BC_PERIODIC, py = a.bc[2] == BC_PERIODIC;
+    for (int w = threadIdx.x; w < kTWN; w += kFTX * kFTY) {
+        const int wi = w % kFWX, wj = w / kFWX;
+        int i = i0 - 1 + wi, j = j0 - 1 + wj;
+        if (i < 0 || i >= a.nx) {
+            if (!px) continue;
+            i = wrap_index(i, a.nx);
+        }
+        if (j < 0 || j >= a.ny) {
+            if (!py) continue;
+            j = wrap_index(j, a.ny);
+        }
+        float f[4][4];
+        if (i > 0 && i < a.nx - 1 && j > 0 && j < a.ny - 1) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) f[q][k] = s_raw[LBRS_IX(tall_pos(q, k, wi, wj), 16 * kTPN, 16)];
+        } else {
+            pull_edge_2d<float>(a, i, j, f);
+        }
+        float U[4], out[4][4];
+        collide_2d<float>(a, f, U, out);
+        tall_store_slot<STORE_U>(a, s_raw, wi, wj, i0, j0, U, out);
+    }
+}
+
+// Phase 2 for tile cell (ti, tj), pulling from the window in the boxes.
+template <bool STORE_U>
+__device__ __forceinline__ void tall_phase2(const StepArgs<float>& a, const float* s_f, int i0, int j0, int ti, int tj)
+{
+    const int i = i0 + ti, j = j0 + tj;
+    if (i >= a.nx || j >= a.ny) return;
+    float f[4][4];
+    if (i > 0 && i < a.nx - 1 && j > 0 && j < a.ny - 1) {
+        // sources (i + 1, j + 1), (i - 1, j + 1), (i - 1, j - 1), (i + 1, j - 1): window slots
+        const int swi[4] = {ti + 2, ti, ti, ti + 2};
+        const int swj[4] = {tj + 2, tj + 2, tj, tj};
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) f[q][k] = s_f[LBRS_IX(tall_pos(q, k, swi[q], swj[q]), 16 * kTPN, 17)];
+        collide_store_2d<float, STORE_U>(a, (int64_t)j * a.nx + i, f);
+        return;
+    }
+    const int SX[4] = {-1, 1, 1, -1};
+    const int SY[4] = {-1, -1, 1, 1};
+    bool wall_top = false, wall_bottom = false;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        int si = i - SX[q], sj = j - SY[q];
+        const int side_y = sj < 0 ? 2 : (sj >= a.ny ? 3 : -1);
+        const int side_x = si < 0 ? 0 : (si >= a.nx ? 1 : -1);
+        const int kind_y = side_y == 2 ? a.bc[2] : a.bc[3];
+        const int kind_x = side_x == 0 ? a.bc[0] : a.bc[1];
+        if (side_y >= 0 && kind_y == BC_WALL) {
+            if (side_y == 3) wall_top = true; else wall_bottom = true;
+            continue;
+        }
+        const float* g = nullptr;
+        if (side_x >= 0) {
+            if (kind_x == BC_DIRICHLET) g = a.ghost + side_x * GHOST_STRIDE + q * 4;
+            else if (kind_x != BC_PERIODIC) si = si < 0 ? 0 : a.nx - 1;
+        }
+        if (!g && side_y >= 0) {
+            if (kind_y == BC_DIRICHLET) g = a.ghost + side_y * GHOST_STRIDE + q * 4;
+            else if (kind_y != BC_PERIODIC) sj = sj < 0 ? 0 : a.ny - 1;
+        }
+        if (g) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) f[q][k] = g[k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                f[q][k] = s_f[LBRS_IX(tall_pos(q, k, si - (i0 - 1), sj - (j0 - 1)), 16 * kTPN, 17)];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float sgn = k == 2 ? -1.f : 1.f;
+        if (wall_top) {
+            f[0][k] = sgn * f[3][k];
+            f[1][k] = sgn * f[2][k];
+        }
+        if (wall_bottom) {
+            f[3][k] = sgn * f[0][k];
+            f[2][k] = sgn * f[1][k];
+        }
+    }
+    collide_store_2d<float, STORE_U>(a, (int64_t)j * a.nx + i, f);
+}
+
+// Copies and waits as step2d_f32_fused2_tma_kernel; 256 threads per 32 x 16 tile.
+template <bool STORE_U>
+__global__ void __launch_bounds__(kFTX * kFTY, 5)
+    step2d_f32_fused2_tall_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs<float> a,
+                                  unsigned* wait_flag)
+{
+    extern __shared__ unsigned char smem_dyn[];
+    float* s_raw = (float*)(((uintptr_t)smem_dyn + 127) & ~(uintptr_t)127);
+    uint64_t* bar_p = (uint64_t*)(s_raw + 16 * kTPN);
+    const uint32_t bar = smem_addr(bar_p);
+    const int i0 = blockIdx.x * kFTX, j0 = blockIdx.y * kTY;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue_tile_copy<kTPN>(&tmap, s_raw, bar, i0, j0);
+    }
+    __syncthreads();
+    const bool arrived = mbar_wait_bounded(bar, 0, kWaitPolls);
+    if (!__syncthreads_and(arrived)) {
+        if (threadIdx.x == 0) {
+            atomicExch(wait_flag, 1u);
+            mbar_wait_bounded(bar, 0, kWaitPolls);   // give the copy in flight a last chance to land
+        }
+        return;
+    }
+    tall_phase1<STORE_U>(a, s_raw, i0, j0);
+    __syncthreads();
+    const StepArgs<float> b = second_step_args(a, STORE_U);
+    const int ti = threadIdx.x % kFTX, tj = threadIdx.x / kFTX;
+    tall_phase2<STORE_U>(b, s_raw, i0, j0, ti, tj);
+    tall_phase2<STORE_U>(b, s_raw, i0, j0, ti, tj + kFTY);
 }
 
 // Failure-detection self-test: one block waits, with the tile kernels' bounded wait,
@@ -930,7 +1113,8 @@ static EncodeTiledFn encode_tiled()
 
 bool encode_f32_tile_map(TileMap* map, const float* f, int64_t nx, int64_t ny)
 {
-    static_assert(sizeof(map->bytes) == sizeof(CUtensorMap), "TileMap holds one CUtensorMap");
+    static_assert(sizeof(map->bytes) == sizeof(CUtensorMap) && sizeof(map->bytes_tall) == sizeof(CUtensorMap),
+                  "TileMap holds two CUtensorMaps");
     map->valid = 0;
     if (!tma_enabled() || nx % 4 != 0 || ((uintptr_t)f & 15)) return false;   // row and field strides: 16-byte multiples
     EncodeTiledFn enc = encode_tiled();
@@ -946,18 +1130,29 @@ bool encode_f32_tile_map(TileMap* map, const float* f, int64_t nx, int64_t ny)
         if (attr_err == cudaSuccess)
             attr_err = cudaFuncSetAttribute(step2d_f32_fused2_tma_kernel<false, true>,
                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaObstSmemBytes);
+        if (attr_err == cudaSuccess)
+            attr_err = cudaFuncSetAttribute(step2d_f32_fused2_tall_kernel<false>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTallSmemBytes);
+        if (attr_err == cudaSuccess)
+            attr_err = cudaFuncSetAttribute(step2d_f32_fused2_tall_kernel<true>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTallSmemBytes);
     });
     if (attr_err != cudaSuccess) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, 16};
     const cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)(nx * ny) * 4};
-    const cuuint32_t box[3] = {(cuuint32_t)kPX, (cuuint32_t)kPY, 4};
     const cuuint32_t estr[3] = {1, 1, 1};
-    CUtensorMap m;
-    if (enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)f, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
-        CUDA_SUCCESS)
-        return false;
-    memcpy(map->bytes, &m, sizeof m);
+    // boxes of 10 rows (32 x 8 tiles: the walls' form) and of 18 rows (32 x 16 tiles)
+    const cuuint32_t rows[2] = {(cuuint32_t)kPY, (cuuint32_t)kTPY};
+    unsigned char* dst[2] = {map->bytes, map->bytes_tall};
+    for (int n = 0; n < 2; ++n) {
+        const cuuint32_t box[3] = {(cuuint32_t)kPX, rows[n], 4};
+        CUtensorMap m;
+        if (enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)f, dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+        memcpy(dst[n], &m, sizeof m);
+    }
     map->valid = 1;
     return true;
 }
@@ -972,10 +1167,12 @@ cudaError_t launch_step2_f32(const StepArgs<float>& a, const TileMap* map, unsig
         if (a.solid) {
             if (rec) return cudaErrorInvalidValue;   // the recording form has no internal walls
             step2d_f32_fused2_tma_kernel<false, true><<<grid, kFTX * kFTY, kTmaObstSmemBytes, s>>>(m, a, wait_flag);
-        } else if (rec) {
-            step2d_f32_fused2_tma_kernel<true><<<grid, kFTX * kFTY, kTmaSmemBytes, s>>>(m, a, wait_flag);
         } else {
-            step2d_f32_fused2_tma_kernel<false><<<grid, kFTX * kFTY, kTmaSmemBytes, s>>>(m, a, wait_flag);
+            CUtensorMap mt;
+            memcpy(&mt, map->bytes_tall, sizeof mt);
+            const dim3 gt((unsigned)((a.nx + kFTX - 1) / kFTX), (unsigned)((a.ny + kTY - 1) / kTY));
+            if (rec) step2d_f32_fused2_tall_kernel<true><<<gt, kFTX * kFTY, kTallSmemBytes, s>>>(mt, a, wait_flag);
+            else step2d_f32_fused2_tall_kernel<false><<<gt, kFTX * kFTY, kTallSmemBytes, s>>>(mt, a, wait_flag);
         }
     } else if (a.solid) {
         return cudaErrorInvalidValue;                // internal walls need the tensor-copy form
