@@ -324,7 +324,7 @@ def obstacle_measurement(Solver, stream, barrier, peak):
     mlups = big.cells * big.steps / t / 1e6
     bpl = BYTES_PER_LUP_F32_FUSED2 + 0.5
     out["steady_6144x2048_f32"] = {"value": mlups, "unit": UNIT,
-                                   "kernel": "step2d_f32_fused2_tma_kernel<false, true>",
+                                   "kernel": "step2d_f32_fused2_tall_kernel<false, true>",
                                    "algorithmic_bytes_per_lup": bpl, "achieved_gbs": bpl * mlups / 1e3,
                                    "frac": bpl * mlups / 1e3 / peak,
                                    "note": "two steps per launch with the obstacle mask of each tile's pull "

@@ -368,22 +368,27 @@ __global__ void __launch_bounds__(kFTX * kFTY, 4) step2d_f32_fused2_kernel(const
 
 // ---------------------------------------------------------------- two steps per launch, TMA-fed
 //
-// The same two steps, with the state the tile needs fetched by tensor copies
-// (cp.async.bulk.tensor) into shared memory.  Population q of a window slot
-// (i, j) is pulled from (i - sx_q, j - sy_q), so each population needs the window
-// shifted by its own velocity: one copy per population of its 4 fields over a
-// 36 x 10 box, x from i0 (q = 1, 4: sources right of the slot) or i0 - 4 (q = 2, 3),
-// y from j0 (sources above) or j0 - 2 (below).  x starts on a 16-byte boundary.
-// 22.5 KB in all, so that five blocks fit on an SM.  Cells outside the grid
-// arrive as zeros and are never read, because a window slot whose pull leaves the
-// grid interior takes the general path (global loads through pull_edge_2d)
-// instead.  One elected thread arms an mbarrier with the byte count and issues
-// the copies; every thread waits on the barrier's phase with a bounded number of
-// polls.  A wait that gives up sets *wait_flag, and the whole block leaves
-// without touching the destination.
-constexpr int kPX = 36, kPY = kFTY + 2, kPN = kPX * kPY;          // one field of one population's box
-constexpr uint32_t kRawBytes = 16u * kPN * sizeof(float);
-constexpr size_t kTmaSmemBytes = 128 + kRawBytes + 16 * kFWN * sizeof(float) + 16;
+// The same two steps on tiles of 32 x 16 cells, with the state the tile needs
+// fetched by tensor copies (cp.async.bulk.tensor) into shared memory.  Population q
+// of a window slot (i, j) is pulled from (i - sx_q, j - sy_q), so each population
+// needs the window shifted by its own velocity: one copy per population of its 4
+// fields over a 36 x 18 box, x from i0 (q = 1, 4: sources right of the slot) or
+// i0 - 4 (q = 2, 3), y from j0 (sources above) or j0 - 2 (below); x starts on a
+// 16-byte boundary.  Phase 1 computes the 34 x 18 window and writes each slot's
+// post-collision populations over the box positions it pulled them from:
+// population q of a slot is pulled from exactly one position, which no other slot
+// reads, so each thread overwrites the 16 values it has just read (no hazard
+// between threads) and the boxes are the only buffer (40.5 KB, five blocks per SM).
+// Phase 2 computes the tile's second step, two cells per thread, reading population
+// q of a source slot where it was pulled from.  Cells outside the grid arrive as
+// zeros and are never read: a window slot whose pull leaves the grid interior takes
+// the general path (global loads through pull_edge_2d).  One elected thread arms an
+// mbarrier with the byte count and issues the copies; every thread waits on the
+// barrier's phase with a bounded number of polls.  A wait that gives up sets
+// *wait_flag, and the whole block leaves without touching the destination.
+constexpr int kPX = 36;                                   // box columns (the 34-slot window, 16-byte aligned)
+constexpr int kTY = 16, kTWY = kTY + 2, kTWN = kFWX * kTWY, kTPY = kTY + 2, kTPN = kPX * kTPY;
+constexpr size_t kTallSmemBytes = 128 + 16u * kTPN * sizeof(float) + 16;
 constexpr int kWaitPolls = 1 << 22;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -408,230 +413,9 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
     return false;
 }
 
-// Phase 1 of the TMA-fed kernel: step n -> n+1 on the window of tile (i0, j0),
-// interior slots from the raw window in shared memory.
-template <bool STORE_U>
-__device__ __forceinline__ void step2_phase1_raw(const StepArgs<float>& a, const float* s_raw, float* s_f, int i0,
-                                                 int j0)
-{
-    if (i0 >= 2 && j0 >= 2 && i0 + kFTX + 2 <= a.nx && j0 + kFTY + 2 <= a.ny) {
-        // every window slot is an interior cell (the whole block takes this branch):
-        // all pulls come from the copied boxes
-        for (int w = threadIdx.x; w < kFWN; w += kFTX * kFTY) {
-            const int wi = w % kFWX, wj = w / kFWX;
-            const int b = wj * kPX + wi;
-            const int r[4] = {b, b + 2, b + 2, b};
-            float f[4][4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) f[q][k] = s_raw[LBRS_IX((q * 4 + k) * kPN + r[q], 16 * kPN, 13)];
-            float U[4], out[4][4];
-            collide_2d<float>(a, f, U, out);
-            step2_store_slot<STORE_U>(a, s_f, w, wi, wj, i0, j0, U, out);
-        }
-        return;
-    }
-    const bool px = a.bc[0] == BC_PERIODIC, py = a.bc[2] == BC_PERIODIC;
-    for (int w = threadIdx.x; w < kFWN; w += kFTX * kFTY) {
-        const int wi = w % kFWX, wj = w / kFWX;
-        int i = i0 - 1 + wi, j = j0 - 1 + wj;
-        if (i < 0 || i >= a.nx) {
-            if (!px) continue;
-            i = wrap_index(i, a.nx);
-        }
-        if (j < 0 || j >= a.ny) {
-            if (!py) continue;
-            j = wrap_index(j, a.ny);
-        }
-        float f[4][4];
-        if (i > 0 && i < a.nx - 1 && j > 0 && j < a.ny - 1) {
-            // source of population q in its box: row wj, column wi (+2 where the box starts at i0 - 4)
-            const int b = wj * kPX + wi;
-            const int r[4] = {b, b + 2, b + 2, b};
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) f[q][k] = s_raw[LBRS_IX((q * 4 + k) * kPN + r[q], 16 * kPN, 13)];
-        } else {
-            pull_edge_2d<float>(a, i, j, f);
-        }
-        float U[4], out[4][4];
-        collide_2d<float>(a, f, U, out);
-        step2_store_slot<STORE_U>(a, s_f, w, wi, wj, i0, j0, U, out);
-    }
-}
-
-// Internal walls in the two-step kernel.  The block keeps the solidity of the
-// tile's pull range, the 36 x 12 cells from (i0 - 2, j0 - 2), in shared memory:
-// every cell whose solidity the two steps consult lies there (window slots, their
-// sources and the x and y neighbours of the mirror rule).  A coordinate outside
-// the domain takes solid_at's value (wrapped, clamped, or fluid beyond a Dirichlet
-// or wall side), wrapped as often as needed: the sources of a periodic window slot
-// lie two cells out, and a solid one among them must send the tile down the
-// obstacle path even though the slot's own pull reads the global mask.
-constexpr int kMX = kFTX + 4, kMY = kFTY + 4, kMN = kMX * kMY;
-constexpr size_t kTmaObstSmemBytes = kTmaSmemBytes + kMN;
-
-// Fill the mask window; true when any of its cells is solid (for the whole block).
-__device__ __forceinline__ bool load_mask_window(const StepArgs<float>& a, uint8_t* s_m, int i0, int j0)
-{
-    int any = 0;
-    for (int m = threadIdx.x; m < kMN; m += kFTX * kFTY) {
-        int i = i0 - 2 + m % kMX, j = j0 - 2 + m / kMX;
-        bool fluid = false;
-        if (i < 0 || i >= a.nx) {
-            const int kind = i < 0 ? a.bc[0] : a.bc[1];
-            if (kind == BC_PERIODIC) i = wrap_index(i, a.nx);
-            else if (kind == BC_TRANSMISSIVE) i = i < 0 ? 0 : a.nx - 1;
-            else fluid = true;
-        }
-        if (j < 0 || j >= a.ny) {
-            const int kind = j < 0 ? a.bc[2] : a.bc[3];
-            if (kind == BC_PERIODIC) j = wrap_index(j, a.ny);
-            else if (kind == BC_TRANSMISSIVE) j = j < 0 ? 0 : a.ny - 1;
-            else fluid = true;
-        }
-        const uint8_t v = !fluid && a.solid[LBRS_IX((int64_t)j * a.nx + i, a.N, 14)] ? 1 : 0;
-        s_m[m] = v;
-        any |= v;
-    }
-    return __syncthreads_or(any) != 0;
-}
-
-__device__ __forceinline__ bool msolid(const uint8_t* s_m, int i, int j, int i0, int j0)
-{
-    return s_m[LBRS_IX((j - j0 + 2) * kMX + (i - i0 + 2), kMN, 14)] != 0;
-}
-
-// Phase 1 with internal walls: solid window slots are skipped (phase 2 never
-// reads them: a population pulled from a solid cell is replaced by the mirror
-// rule); a fluid slot with a solid source, or on a domain side, takes the
-// single-step kernel's obstacle pull from global memory.
-__device__ __forceinline__ void step2_phase1_obst(const StepArgs<float>& a, const float* s_raw, float* s_f,
-                                                  const uint8_t* s_m, int i0, int j0)
-{
-    const bool px = a.bc[0] == BC_PERIODIC, py = a.bc[2] == BC_PERIODIC;
-    for (int w = threadIdx.x; w < kFWN; w += kFTX * kFTY) {
-        const int wi = w % kFWX, wj = w / kFWX;
-        const int ui = i0 - 1 + wi, uj = j0 - 1 + wj;
-        int i = ui, j = uj;
-        if (i < 0 || i >= a.nx) {
-            if (!px) continue;
-            i = wrap_index(i, a.nx);
-        }
-        if (j < 0 || j >= a.ny) {
-            if (!py) continue;
-            j = wrap_index(j, a.ny);
-        }
-        if (msolid(s_m, ui, uj, i0, j0)) continue;
-        float f[4][4];
-        if (i > 0 && i < a.nx - 1 && j > 0 && j < a.ny - 1 && !msolid(s_m, ui + 1, uj + 1, i0, j0) &&
-            !msolid(s_m, ui - 1, uj + 1, i0, j0) && !msolid(s_m, ui - 1, uj - 1, i0, j0) &&
-            !msolid(s_m, ui + 1, uj - 1, i0, j0)) {
-            const int b = wj * kPX + wi;
-            const int r[4] = {b, b + 2, b + 2, b};
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) f[q][k] = s_raw[LBRS_IX((q * 4 + k) * kPN + r[q], 16 * kPN, 13)];
-        } else {
-            pull_obstacle_2d<float>(a, i, j, f);
-        }
-        float U[4], out[4][4];
-        collide_2d<float>(a, f, U, out);
-        step2_store_slot<false>(a, s_f, w, wi, wj, i0, j0, U, out);
-    }
-}
-
-// Phase 2 with internal walls: a solid tile cell is carried unchanged (its two
-// steps copy it); a fluid cell pulls from the window and resolves solid sources
-// and domain sides in pull_obstacle_2d's order.
-__device__ __forceinline__ void step2_phase2_obst(const StepArgs<float>& a, const float* s_f, const uint8_t* s_m,
-                                                  int i0, int j0)
-{
-    const int ti = threadIdx.x % kFTX, tj = threadIdx.x / kFTX;
-    const int i = i0 + ti, j = j0 + tj;
-    if (i >= a.nx || j >= a.ny) return;
-    const int64_t c = (int64_t)j * a.nx + i;
-    if (msolid(s_m, i, j, i0, j0)) {
-#pragma unroll
-        for (int n = 0; n < 16; ++n) a.dst[LBRS_IX(n * a.N + c, 16 * a.N, 15)] = a.src[LBRS_IX(n * a.N + c, 16 * a.N, 15)];
-        return;
-    }
-    const int SX[4] = {-1, 1, 1, -1};
-    const int SY[4] = {-1, -1, 1, 1};
-    float f[4][4];
-    bool wall_top = false, wall_bottom = false;
-    bool unknown[4] = {false, false, false, false};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        int si = i - SX[q], sj = j - SY[q];
-        const int side_y = sj < 0 ? 2 : (sj >= a.ny ? 3 : -1);
-        const int side_x = si < 0 ? 0 : (si >= a.nx ? 1 : -1);
-        const int kind_y = side_y == 2 ? a.bc[2] : a.bc[3];
-        const int kind_x = side_x == 0 ? a.bc[0] : a.bc[1];
-        if (side_y >= 0 && kind_y == BC_WALL) {
-            if (side_y == 3) wall_top = true; else wall_bottom = true;
-            continue;
-        }
-        const float* g = nullptr;
-        if (side_x >= 0) {
-            if (kind_x == BC_DIRICHLET) g = a.ghost + side_x * GHOST_STRIDE + q * 4;
-            else if (kind_x != BC_PERIODIC) si = si < 0 ? 0 : a.nx - 1;
-        }
-        if (!g && side_y >= 0) {
-            if (kind_y == BC_DIRICHLET) g = a.ghost + side_y * GHOST_STRIDE + q * 4;
-            else if (kind_y != BC_PERIODIC) sj = sj < 0 ? 0 : a.ny - 1;
-        }
-        if (!g && msolid(s_m, si, sj, i0, j0)) {
-            unknown[q] = true;
-            continue;
-        }
-        if (g) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) f[q][k] = g[k];
-        } else {
-            const int slot = (sj - (j0 - 1)) * kFWX + (si - (i0 - 1));
-#pragma unroll
-            for (int k = 0; k < 4; ++k) f[q][k] = s_f[LBRS_IX((q * 4 + k) * kFWN + slot, 16 * kFWN, 12)];
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        if (!unknown[q]) continue;
-        const bool xn = msolid(s_m, i - SX[q], j, i0, j0), yn = msolid(s_m, i, j - SY[q], i0, j0);
-        const bool flip_x = !(yn && !xn), flip_y = !(xn && !yn);
-        const int mx = flip_x ? -SX[q] : SX[q], my = flip_y ? -SY[q] : SY[q];
-        const int m = my < 0 ? (mx < 0 ? 0 : 1) : (mx > 0 ? 2 : 3);
-        const float su = flip_x ? -1.f : 1.f, sv = flip_y ? -1.f : 1.f;
-#pragma unroll
-        for (int mm = 0; mm < 4; ++mm) {
-            if (mm != m) continue;
-            f[q][0] = f[mm][0];
-            f[q][1] = su * f[mm][1];
-            f[q][2] = sv * f[mm][2];
-            f[q][3] = f[mm][3];
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const float sgn = k == 2 ? -1.f : 1.f;
-        if (wall_top) {
-            f[0][k] = sgn * f[3][k];
-            f[1][k] = sgn * f[2][k];
-        }
-        if (wall_bottom) {
-            f[3][k] = sgn * f[0][k];
-            f[2][k] = sgn * f[1][k];
-        }
-    }
-    collide_store_2d<float>(a, c, f);
-}
-
 // The four population boxes of tile (i0, j0), each PN floats per field (36 columns
 // and PN / 36 rows), onto one mbarrier.
-template <int PN = kPN>
+template <int PN>
 __device__ __forceinline__ void issue_tile_copy(const CUtensorMap* tmap, float* s_raw, uint32_t bar, int i0, int j0)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(16u * PN * 4u) : "memory");
@@ -646,66 +430,7 @@ __device__ __forceinline__ void issue_tile_copy(const CUtensorMap* tmap, float* 
             : "memory");
 }
 
-// One block per tile, five resident blocks per SM (48 registers, 44.9 KB of shared
-// memory each; 45.3 KB with the obstacle mask window of OBST).  Forms that reuse a block for further tiles, issuing the next
-// copy as soon as phase 1 has read the raw buffer, measured slower: persistent
-// blocks fall into step and wait for their copies together, and a loop over
-// tiles raises the register count past the five-block budget (spills).
-template <bool STORE_U, bool OBST = false>
-__global__ void __launch_bounds__(kFTX * kFTY, 5)
-    step2d_f32_fused2_tma_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs<float> a, unsigned* wait_flag)
-{
-    static_assert(!(STORE_U && OBST), "the recording form has no internal walls");
-    extern __shared__ unsigned char smem_dyn[];
-    float* s_raw = (float*)(((uintptr_t)smem_dyn + 127) & ~(uintptr_t)127);
-    float* s_f = s_raw + 16 * kPN;
-    uint64_t* bar_p = (uint64_t*)(s_f + 16 * kFWN);
-    const uint32_t bar = smem_addr(bar_p);
-    const int i0 = blockIdx.x * kFTX, j0 = blockIdx.y * kFTY;
-
-    if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        issue_tile_copy(&tmap, s_raw, bar, i0, j0);
-    }
-    __syncthreads();
-    bool obst = false;
-    uint8_t* s_m = (uint8_t*)(bar_p + 2);
-    if constexpr (OBST) obst = load_mask_window(a, s_m, i0, j0);   // while the copies are in flight
-    const bool arrived = mbar_wait_bounded(bar, 0, kWaitPolls);
-    if (!__syncthreads_and(arrived)) {
-        if (threadIdx.x == 0) {
-            atomicExch(wait_flag, 1u);
-            mbar_wait_bounded(bar, 0, kWaitPolls);   // give the copy in flight a last chance to land
-        }
-        return;
-    }
-    if (OBST && obst) {
-        step2_phase1_obst(a, s_raw, s_f, s_m, i0, j0);
-        __syncthreads();
-        step2_phase2_obst(a, s_f, s_m, i0, j0);
-        return;
-    }
-    step2_phase1_raw<STORE_U>(a, s_raw, s_f, i0, j0);
-    __syncthreads();
-    step2_phase2<STORE_U>(second_step_args(a, STORE_U), s_f, i0, j0);
-}
-
-// ---------------------------------------------------------------- two steps per launch, 32 x 16 tiles
-//
-// The same two steps on tiles of 32 x 16 cells (two cells per thread in phase 2),
-// the window's post-collision populations written over the copied boxes: population
-// q of window slot w is pulled from exactly one box position, which no other slot
-// reads, so each thread overwrites the 16 values it has just read (no hazard between
-// threads) and phase 2 reads population q of a slot where it was pulled from.  The
-// boxes (36 x 18 per field) are the only shared-memory buffer: 40.5 KB, five blocks
-// per SM.  Against the 32 x 8 tile this recomputes 612 window slots per 512 cells
-// instead of 340 per 256 and re-reads fewer halo rows.
-constexpr int kTY = 16, kTWY = kTY + 2, kTWN = kFWX * kTWY, kTPY = kTY + 2, kTPN = kPX * kTPY;
-constexpr size_t kTallSmemBytes = 128 + 16u * kTPN * sizeof(float) + 16;
-
-// Position of population q, field k of window slot (wi, wj) in the tall boxes.
+// Position of population q, field k of window slot (wi, wj) in the boxes.
 __device__ __forceinline__ int tall_pos(int q, int k, int wi, int wj)
 {
     return (q * 4 + k) * kTPN + wj * kPX + wi + ((q == 1 || q == 2) ? 2 : 0);
@@ -733,6 +458,8 @@ template <bool STORE_U>
 __device__ __forceinline__ void tall_phase1(const StepArgs<float>& a, float* s_raw, int i0, int j0)
 {
     if (i0 >= 2 && j0 >= 2 && i0 + kFTX + 2 <= a.nx && j0 + kTY + 2 <= a.ny) {
+        // every window slot is an interior cell (the whole block takes this branch):
+        // all pulls come from the copied boxes
         for (int w = threadIdx.x; w < kTWN; w += kFTX * kFTY) {
             const int wi = w % kFWX, wj = w / kFWX;
             float f[4][4];
@@ -838,12 +565,182 @@ __device__ __forceinline__ void tall_phase2(const StepArgs<float>& a, const floa
     collide_store_2d<float, STORE_U>(a, (int64_t)j * a.nx + i, f);
 }
 
-// Copies and waits as step2d_f32_fused2_tma_kernel; 256 threads per 32 x 16 tile.
-template <bool STORE_U>
+// Internal walls in the two-step kernel.  The block keeps the solidity of the
+// tile's pull range, the 36 x 20 cells from (i0 - 2, j0 - 2), in shared memory:
+// every cell whose solidity the two steps consult lies there (window slots, their
+// sources and the x and y neighbours of the mirror rule).  A coordinate outside
+// the domain takes solid_at's value (wrapped, clamped, or fluid beyond a Dirichlet
+// or wall side), wrapped as often as needed: the sources of a periodic window slot
+// lie two cells out, and a solid one among them must send the tile down the
+// obstacle path even though the slot's own pull reads the global mask.
+constexpr int kMX = kFTX + 4, kMY = kTY + 4, kMN = kMX * kMY;
+constexpr size_t kTallObstSmemBytes = kTallSmemBytes + kMN;
+
+// Fill the mask window; true when any of its cells is solid (for the whole block).
+__device__ __forceinline__ bool load_mask_window(const StepArgs<float>& a, uint8_t* s_m, int i0, int j0)
+{
+    int any = 0;
+    for (int m = threadIdx.x; m < kMN; m += kFTX * kFTY) {
+        int i = i0 - 2 + m % kMX, j = j0 - 2 + m / kMX;
+        bool fluid = false;
+        if (i < 0 || i >= a.nx) {
+            const int kind = i < 0 ? a.bc[0] : a.bc[1];
+            if (kind == BC_PERIODIC) i = wrap_index(i, a.nx);
+            else if (kind == BC_TRANSMISSIVE) i = i < 0 ? 0 : a.nx - 1;
+            else fluid = true;
+        }
+        if (j < 0 || j >= a.ny) {
+            const int kind = j < 0 ? a.bc[2] : a.bc[3];
+            if (kind == BC_PERIODIC) j = wrap_index(j, a.ny);
+            else if (kind == BC_TRANSMISSIVE) j = j < 0 ? 0 : a.ny - 1;
+            else fluid = true;
+        }
+        const uint8_t v = !fluid && a.solid[LBRS_IX((int64_t)j * a.nx + i, a.N, 14)] ? 1 : 0;
+        s_m[m] = v;
+        any |= v;
+    }
+    return __syncthreads_or(any) != 0;
+}
+
+__device__ __forceinline__ bool msolid(const uint8_t* s_m, int i, int j, int i0, int j0)
+{
+    return s_m[LBRS_IX((j - j0 + 2) * kMX + (i - i0 + 2), kMN, 14)] != 0;
+}
+
+// Phase 1 with internal walls: solid window slots are skipped (phase 2 never
+// reads them: a population pulled from a solid cell is replaced by the mirror
+// rule); a fluid slot with a solid source, or on a domain side, takes the
+// single-step kernel's obstacle pull from global memory.
+__device__ __forceinline__ void tall_phase1_obst(const StepArgs<float>& a, float* s_raw, const uint8_t* s_m, int i0,
+                                                 int j0)
+{
+    const bool px = a.bc[0] == BC_PERIODIC, py = a.bc[2] == BC_PERIODIC;
+    for (int w = threadIdx.x; w < kTWN; w += kFTX * kFTY) {
+        const int wi = w % kFWX, wj = w / kFWX;
+        const int ui = i0 - 1 + wi, uj = j0 - 1 + wj;
+        int i = ui, j = uj;
+        if (i < 0 || i >= a.nx) {
+            if (!px) continue;
+            i = wrap_index(i, a.nx);
+        }
+        if (j < 0 || j >= a.ny) {
+            if (!py) continue;
+            j = wrap_index(j, a.ny);
+        }
+        if (msolid(s_m, ui, uj, i0, j0)) continue;
+        float f[4][4];
+        if (i > 0 && i < a.nx - 1 && j > 0 && j < a.ny - 1 && !msolid(s_m, ui + 1, uj + 1, i0, j0) &&
+            !msolid(s_m, ui - 1, uj + 1, i0, j0) && !msolid(s_m, ui - 1, uj - 1, i0, j0) &&
+            !msolid(s_m, ui + 1, uj - 1, i0, j0)) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) f[q][k] = s_raw[LBRS_IX(tall_pos(q, k, wi, wj), 16 * kTPN, 13)];
+        } else {
+            pull_obstacle_2d<float>(a, i, j, f);
+        }
+        float U[4], out[4][4];
+        collide_2d<float>(a, f, U, out);
+        tall_store_slot<false>(a, s_raw, wi, wj, i0, j0, U, out);
+    }
+}
+
+// Phase 2 with internal walls: a solid tile cell is carried unchanged (its two
+// steps copy it); a fluid cell pulls from the window and resolves solid sources
+// and domain sides in pull_obstacle_2d's order.
+__device__ __forceinline__ void tall_phase2_obst(const StepArgs<float>& a, const float* s_f, const uint8_t* s_m, int i0,
+                                                 int j0, int ti, int tj)
+{
+    const int i = i0 + ti, j = j0 + tj;
+    if (i >= a.nx || j >= a.ny) return;
+    const int64_t c = (int64_t)j * a.nx + i;
+    if (msolid(s_m, i, j, i0, j0)) {
+#pragma unroll
+        for (int n = 0; n < 16; ++n) a.dst[LBRS_IX(n * a.N + c, 16 * a.N, 15)] = a.src[LBRS_IX(n * a.N + c, 16 * a.N, 15)];
+        return;
+    }
+    const int SX[4] = {-1, 1, 1, -1};
+    const int SY[4] = {-1, -1, 1, 1};
+    float f[4][4];
+    bool wall_top = false, wall_bottom = false;
+    bool unknown[4] = {false, false, false, false};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        int si = i - SX[q], sj = j - SY[q];
+        const int side_y = sj < 0 ? 2 : (sj >= a.ny ? 3 : -1);
+        const int side_x = si < 0 ? 0 : (si >= a.nx ? 1 : -1);
+        const int kind_y = side_y == 2 ? a.bc[2] : a.bc[3];
+        const int kind_x = side_x == 0 ? a.bc[0] : a.bc[1];
+        if (side_y >= 0 && kind_y == BC_WALL) {
+            if (side_y == 3) wall_top = true; else wall_bottom = true;
+            continue;
+        }
+        const float* g = nullptr;
+        if (side_x >= 0) {
+            if (kind_x == BC_DIRICHLET) g = a.ghost + side_x * GHOST_STRIDE + q * 4;
+            else if (kind_x != BC_PERIODIC) si = si < 0 ? 0 : a.nx - 1;
+        }
+        if (!g && side_y >= 0) {
+            if (kind_y == BC_DIRICHLET) g = a.ghost + side_y * GHOST_STRIDE + q * 4;
+            else if (kind_y != BC_PERIODIC) sj = sj < 0 ? 0 : a.ny - 1;
+        }
+        if (!g && msolid(s_m, si, sj, i0, j0)) {
+            unknown[q] = true;
+            continue;
+        }
+        if (g) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) f[q][k] = g[k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                f[q][k] = s_f[LBRS_IX(tall_pos(q, k, si - (i0 - 1), sj - (j0 - 1)), 16 * kTPN, 12)];
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (!unknown[q]) continue;
+        const bool xn = msolid(s_m, i - SX[q], j, i0, j0), yn = msolid(s_m, i, j - SY[q], i0, j0);
+        const bool flip_x = !(yn && !xn), flip_y = !(xn && !yn);
+        const int mx = flip_x ? -SX[q] : SX[q], my = flip_y ? -SY[q] : SY[q];
+        const int m = my < 0 ? (mx < 0 ? 0 : 1) : (mx > 0 ? 2 : 3);
+        const float su = flip_x ? -1.f : 1.f, sv = flip_y ? -1.f : 1.f;
+#pragma unroll
+        for (int mm = 0; mm < 4; ++mm) {
+            if (mm != m) continue;
+            f[q][0] = f[mm][0];
+            f[q][1] = su * f[mm][1];
+            f[q][2] = sv * f[mm][2];
+            f[q][3] = f[mm][3];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float sgn = k == 2 ? -1.f : 1.f;
+        if (wall_top) {
+            f[0][k] = sgn * f[3][k];
+            f[1][k] = sgn * f[2][k];
+        }
+        if (wall_bottom) {
+            f[3][k] = sgn * f[0][k];
+            f[2][k] = sgn * f[1][k];
+        }
+    }
+    collide_store_2d<float>(a, c, f);
+}
+
+// One block per 32 x 16 tile, five resident blocks per SM (48 registers, 40.5 KB of
+// shared memory; 41.2 KB with the obstacle mask window of OBST).  Forms measured
+// slower: 32 x 8 tiles with a separate window buffer (the same time on a flushed
+// 1024^2 grid, 10 % less throughput on large grids); blocks reused for further
+// tiles with the next copy issued early (fewer resident warps); L2 prefetch of
+// later tiles (evicts halo rows still to be read).
+template <bool STORE_U, bool OBST = false>
 __global__ void __launch_bounds__(kFTX * kFTY, 5)
     step2d_f32_fused2_tall_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs<float> a,
                                   unsigned* wait_flag)
 {
+    static_assert(!(STORE_U && OBST), "the recording form has no internal walls");
     extern __shared__ unsigned char smem_dyn[];
     float* s_raw = (float*)(((uintptr_t)smem_dyn + 127) & ~(uintptr_t)127);
     uint64_t* bar_p = (uint64_t*)(s_raw + 16 * kTPN);
@@ -856,6 +753,9 @@ __global__ void __launch_bounds__(kFTX * kFTY, 5)
         issue_tile_copy<kTPN>(&tmap, s_raw, bar, i0, j0);
     }
     __syncthreads();
+    bool obst = false;
+    uint8_t* s_m = (uint8_t*)(bar_p + 2);
+    if constexpr (OBST) obst = load_mask_window(a, s_m, i0, j0);   // while the copies are in flight
     const bool arrived = mbar_wait_bounded(bar, 0, kWaitPolls);
     if (!__syncthreads_and(arrived)) {
         if (threadIdx.x == 0) {
@@ -864,10 +764,17 @@ __global__ void __launch_bounds__(kFTX * kFTY, 5)
         }
         return;
     }
+    const int ti = threadIdx.x % kFTX, tj = threadIdx.x / kFTX;
+    if (OBST && obst) {
+        tall_phase1_obst(a, s_raw, s_m, i0, j0);
+        __syncthreads();
+        tall_phase2_obst(a, s_raw, s_m, i0, j0, ti, tj);
+        tall_phase2_obst(a, s_raw, s_m, i0, j0, ti, tj + kFTY);
+        return;
+    }
     tall_phase1<STORE_U>(a, s_raw, i0, j0);
     __syncthreads();
     const StepArgs<float> b = second_step_args(a, STORE_U);
-    const int ti = threadIdx.x % kFTX, tj = threadIdx.x / kFTX;
     tall_phase2<STORE_U>(b, s_raw, i0, j0, ti, tj);
     tall_phase2<STORE_U>(b, s_raw, i0, j0, ti, tj + kFTY);
 }
@@ -1113,8 +1020,7 @@ static EncodeTiledFn encode_tiled()
 
 bool encode_f32_tile_map(TileMap* map, const float* f, int64_t nx, int64_t ny)
 {
-    static_assert(sizeof(map->bytes) == sizeof(CUtensorMap) && sizeof(map->bytes_tall) == sizeof(CUtensorMap),
-                  "TileMap holds two CUtensorMaps");
+    static_assert(sizeof(map->bytes) == sizeof(CUtensorMap), "TileMap holds one CUtensorMap");
     map->valid = 0;
     if (!tma_enabled() || nx % 4 != 0 || ((uintptr_t)f & 15)) return false;   // row and field strides: 16-byte multiples
     EncodeTiledFn enc = encode_tiled();
@@ -1122,61 +1028,49 @@ bool encode_f32_tile_map(TileMap* map, const float* f, int64_t nx, int64_t ny)
     static std::once_flag attr_once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(attr_once, [] {
-        attr_err = cudaFuncSetAttribute(step2d_f32_fused2_tma_kernel<false>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmemBytes);
-        if (attr_err == cudaSuccess)
-            attr_err = cudaFuncSetAttribute(step2d_f32_fused2_tma_kernel<true>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmemBytes);
-        if (attr_err == cudaSuccess)
-            attr_err = cudaFuncSetAttribute(step2d_f32_fused2_tma_kernel<false, true>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaObstSmemBytes);
-        if (attr_err == cudaSuccess)
-            attr_err = cudaFuncSetAttribute(step2d_f32_fused2_tall_kernel<false>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTallSmemBytes);
+        attr_err = cudaFuncSetAttribute(step2d_f32_fused2_tall_kernel<false>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTallSmemBytes);
         if (attr_err == cudaSuccess)
             attr_err = cudaFuncSetAttribute(step2d_f32_fused2_tall_kernel<true>,
                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTallSmemBytes);
+        if (attr_err == cudaSuccess)
+            attr_err = cudaFuncSetAttribute(step2d_f32_fused2_tall_kernel<false, true>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTallObstSmemBytes);
     });
     if (attr_err != cudaSuccess) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, 16};
     const cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)(nx * ny) * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)kPX, (cuuint32_t)kTPY, 4};
     const cuuint32_t estr[3] = {1, 1, 1};
-    // boxes of 10 rows (32 x 8 tiles: the walls' form) and of 18 rows (32 x 16 tiles)
-    const cuuint32_t rows[2] = {(cuuint32_t)kPY, (cuuint32_t)kTPY};
-    unsigned char* dst[2] = {map->bytes, map->bytes_tall};
-    for (int n = 0; n < 2; ++n) {
-        const cuuint32_t box[3] = {(cuuint32_t)kPX, rows[n], 4};
-        CUtensorMap m;
-        if (enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)f, dims, strides, box, estr,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-            return false;
-        memcpy(dst[n], &m, sizeof m);
-    }
+    CUtensorMap m;
+    if (enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)f, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+        return false;
+    memcpy(map->bytes, &m, sizeof m);
     map->valid = 1;
     return true;
 }
 
 cudaError_t launch_step2_f32(const StepArgs<float>& a, const TileMap* map, unsigned* wait_flag, cudaStream_t s)
 {
-    const dim3 grid((unsigned)((a.nx + kFTX - 1) / kFTX), (unsigned)((a.ny + kFTY - 1) / kFTY));
     const bool rec = a.Uout != nullptr;
     if (map && map->valid && wait_flag) {
         CUtensorMap m;
         memcpy(&m, map->bytes, sizeof m);
+        const dim3 grid((unsigned)((a.nx + kFTX - 1) / kFTX), (unsigned)((a.ny + kTY - 1) / kTY));
         if (a.solid) {
             if (rec) return cudaErrorInvalidValue;   // the recording form has no internal walls
-            step2d_f32_fused2_tma_kernel<false, true><<<grid, kFTX * kFTY, kTmaObstSmemBytes, s>>>(m, a, wait_flag);
+            step2d_f32_fused2_tall_kernel<false, true><<<grid, kFTX * kFTY, kTallObstSmemBytes, s>>>(m, a, wait_flag);
+        } else if (rec) {
+            step2d_f32_fused2_tall_kernel<true><<<grid, kFTX * kFTY, kTallSmemBytes, s>>>(m, a, wait_flag);
         } else {
-            CUtensorMap mt;
-            memcpy(&mt, map->bytes_tall, sizeof mt);
-            const dim3 gt((unsigned)((a.nx + kFTX - 1) / kFTX), (unsigned)((a.ny + kTY - 1) / kTY));
-            if (rec) step2d_f32_fused2_tall_kernel<true><<<gt, kFTX * kFTY, kTallSmemBytes, s>>>(mt, a, wait_flag);
-            else step2d_f32_fused2_tall_kernel<false><<<gt, kFTX * kFTY, kTallSmemBytes, s>>>(mt, a, wait_flag);
+            step2d_f32_fused2_tall_kernel<false><<<grid, kFTX * kFTY, kTallSmemBytes, s>>>(m, a, wait_flag);
         }
     } else if (a.solid) {
         return cudaErrorInvalidValue;                // internal walls need the tensor-copy form
     } else {
+        const dim3 grid((unsigned)((a.nx + kFTX - 1) / kFTX), (unsigned)((a.ny + kFTY - 1) / kFTY));
         if (rec) step2d_f32_fused2_kernel<true><<<grid, kFTX * kFTY, 0, s>>>(a);
         else step2d_f32_fused2_kernel<false><<<grid, kFTX * kFTY, 0, s>>>(a);
     }

@@ -49,8 +49,7 @@ cudaError_t launch_step_f32(int lattice, const StepArgs<float>& a, cudaStream_t 
 // reports a bounded wait that gave up in *wait_flag; otherwise it loads directly.
 // A non-null a.Uout records the moments of both steps: [2][4][N] from a.Uout.
 struct alignas(64) TileMap {
-    unsigned char bytes[128];        // an encoded CUtensorMap: boxes for 32 x 8 tiles
-    unsigned char bytes_tall[128];   // the same state, boxes for 32 x 16 tiles
+    unsigned char bytes[128];   // an encoded CUtensorMap (36 x 18 x 4-field boxes of the state)
     int valid;
 };
 bool step2_f32_enabled();
