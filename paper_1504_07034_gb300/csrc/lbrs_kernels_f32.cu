@@ -926,6 +926,105 @@ __global__ void __launch_bounds__(kFTX * kFTY, 4) adj_fused2_kernel(const AdjArg
         for (int k = 0; k < 4; ++k) a.gout[LBRS_IX((q * 4 + k) * a.N + c, 16 * a.N, 33)] = out[q][k];
 }
 
+// The two adjoint steps on 32 x 16 tiles, fed like the forward's tall kernel: the
+// gather g(x)_q = k_q(x + c_q) pulls population q from the cell one step along
+// +c_q, so its box starts at x = i0 - 4 (sx_q = -1) or i0, y = j0 - 2 (sy_q = -1)
+// or j0 (the mirror of the forward's boxes), 36 x 18 per field.  Phase 1 forms
+// k^{s-1} on the 34 x 18 window in place over the boxes (each position is gathered
+// by one slot only); slots whose sources wrap around the periodic grid gather from
+// global memory.  Phase 2 forms k^{s-2} for the tile, two cells per thread.  The
+// same expressions in the same order as the push kernel: bit-identical.
+__device__ __forceinline__ int adj_pos(int q, int k, int wi, int wj)
+{
+    return (q * 4 + k) * kTPN + wj * kPX + wi + ((q == 0 || q == 3) ? 2 : 0);
+}
+
+__device__ __forceinline__ void issue_adj_copy(const CUtensorMap* tmap, float* s_raw, uint32_t bar, int i0, int j0)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(16u * kTPN * 4u) : "memory");
+    const int x0[4] = {i0 - 4, i0, i0, i0 - 4};
+    const int y0[4] = {j0 - 2, j0 - 2, j0, j0};
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(s_raw + q * 4 * kTPN)),
+            "l"((uint64_t)tmap), "r"(x0[q]), "r"(y0[q]), "r"(q * 4), "r"(bar)
+            : "memory");
+}
+
+// Two steps: k^s (a.gin, through tmap) -> k^{s-2} (a.gout); a.U = U_{s-1}, U2 = U_{s-2}.
+__global__ void __launch_bounds__(kFTX * kFTY, 5)
+    adj_fused2_tall_kernel(const __grid_constant__ CUtensorMap tmap, const AdjArgs<float> a,
+                           const float* __restrict__ U2, unsigned* wait_flag)
+{
+    extern __shared__ unsigned char smem_dyn[];
+    float* s_raw = (float*)(((uintptr_t)smem_dyn + 127) & ~(uintptr_t)127);
+    uint64_t* bar_p = (uint64_t*)(s_raw + 16 * kTPN);
+    const uint32_t bar = smem_addr(bar_p);
+    const int i0 = blockIdx.x * kFTX, j0 = blockIdx.y * kTY;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue_adj_copy(&tmap, s_raw, bar, i0, j0);
+    }
+    __syncthreads();
+    const bool arrived = mbar_wait_bounded(bar, 0, kWaitPolls);
+    if (!__syncthreads_and(arrived)) {
+        if (threadIdx.x == 0) {
+            atomicExch(wait_flag, 1u);
+            mbar_wait_bounded(bar, 0, kWaitPolls);   // give the copy in flight a last chance to land
+        }
+        return;
+    }
+    // phase 1: k^{s-1} on the window (periodic: every slot is a cell of the grid)
+    for (int w = threadIdx.x; w < kTWN; w += kFTX * kFTY) {
+        const int wi = w % kFWX, wj = w / kFWX;
+        const int ui = i0 - 1 + wi, uj = j0 - 1 + wj;
+        const int i = wrap_index(ui, a.nx), j = wrap_index(uj, a.ny);
+        float g[4][4], U[4], out[4][4];
+        if (ui > 0 && ui < a.nx - 1 && uj > 0 && uj < a.ny - 1) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) g[q][k] = s_raw[LBRS_IX(adj_pos(q, k, wi, wj), 16 * kTPN, 34)];
+        } else {
+            adj_gather(a, i, j, g);
+        }
+        const int64_t c = (int64_t)j * a.nx + i;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) U[k] = a.U[LBRS_IX(k * a.N + c, 4 * a.N, 34)];
+        adj_local(a, U, g, out);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) s_raw[LBRS_IX(adj_pos(q, k, wi, wj), 16 * kTPN, 34)] = out[q][k];
+    }
+    __syncthreads();
+    // phase 2: k^{s-2} on the tile; the source of population q is slot (ti + 1 + sx_q, tj + 1 + sy_q)
+    const int ti = threadIdx.x % kFTX;
+    for (int tj = threadIdx.x / kFTX; tj < kTY; tj += kFTY) {
+        const int i = i0 + ti, j = j0 + tj;
+        if (i >= a.nx || j >= a.ny) continue;
+        const int swi[4] = {ti, ti + 2, ti + 2, ti};
+        const int swj[4] = {tj, tj, tj + 2, tj + 2};
+        float g[4][4], U[4], out[4][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) g[q][k] = s_raw[LBRS_IX(adj_pos(q, k, swi[q], swj[q]), 16 * kTPN, 35)];
+        const int64_t c = (int64_t)j * a.nx + i;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) U[k] = U2[LBRS_IX(k * a.N + c, 4 * a.N, 35)];
+        adj_local(a, U, g, out);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) a.gout[LBRS_IX((q * 4 + k) * a.N + c, 16 * a.N, 35)] = out[q][k];
+    }
+}
+
 // Kernel variant for D2Q4 FP32: 0 = scalar one cell per thread, 2 or 4 =
 // vector width, 12 / 14 = 2 / 4 strided cells per thread.  The default can be
 // overridden for tuning sweeps with the environment variable LBRS_F32_STEP_VARIANT.
@@ -1132,8 +1231,19 @@ cudaError_t launch_adj_pull_f32(const AdjArgs<float>& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_fused2_f32(const AdjArgs<float>& a, const float* U2, cudaStream_t s)
+cudaError_t launch_adj_fused2_f32(const AdjArgs<float>& a, const float* U2, const TileMap* map, unsigned* wait_flag,
+                                  cudaStream_t s)
 {
+    if (map && map->valid && wait_flag) {
+        static const cudaError_t attr = cudaFuncSetAttribute(
+            adj_fused2_tall_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTallSmemBytes);
+        if (attr != cudaSuccess) return attr;
+        CUtensorMap m;
+        memcpy(&m, map->bytes, sizeof m);
+        const dim3 grid((unsigned)((a.nx + kFTX - 1) / kFTX), (unsigned)((a.ny + kTY - 1) / kTY));
+        adj_fused2_tall_kernel<<<grid, kFTX * kFTY, kTallSmemBytes, s>>>(m, a, U2, wait_flag);
+        return cudaGetLastError();
+    }
     const dim3 grid((unsigned)((a.nx + kFTX - 1) / kFTX), (unsigned)((a.ny + kFTY - 1) / kFTY));
     adj_fused2_kernel<<<grid, kFTX * kFTY, 0, s>>>(a, U2);
     return cudaGetLastError();

@@ -106,7 +106,10 @@ cudaError_t launch_adjoint_f32(const AdjArgs<float>& a, cudaStream_t s);
 // k^s -> k^{s-2} with a.U = U_{s-1} and U2 = U_{s-2}.
 cudaError_t launch_adj_local_f32(const AdjArgs<float>& a, cudaStream_t s);
 cudaError_t launch_adj_pull_f32(const AdjArgs<float>& a, cudaStream_t s);
-cudaError_t launch_adj_fused2_f32(const AdjArgs<float>& a, const float* U2, cudaStream_t s);
+// With a valid tile map of a.gin (the k buffer, encode_f32_tile_map) the tensor-copy form on 32 x 16
+// tiles, reporting a bounded wait that gave up in *wait_flag; otherwise direct loads.
+cudaError_t launch_adj_fused2_f32(const AdjArgs<float>& a, const float* U2, const TileMap* map, unsigned* wait_flag,
+                                  cudaStream_t s);
 cudaError_t launch_vjp_equilibrium_f64(const AdjArgs<double>& a, cudaStream_t s);
 cudaError_t launch_vjp_equilibrium_f32(const AdjArgs<float>& a, cudaStream_t s);
 

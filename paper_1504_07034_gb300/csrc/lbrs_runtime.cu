@@ -1194,6 +1194,9 @@ lbrs_status lbrs_backward_checkpointed(lbrs_ctx* ctx, void* d_adj_ws, const void
     const AdjLayout A = adj_layout(ctx, ctx->adj_n, ctx->adj_seg);
     char* ws = ctx->adj_ws;
     char* g[2] = {ws + A.gbar0, ws + A.gbar1};
+    TileMap gmap[2];                 // tensor maps of the two k buffers (FP32 fused sweep)
+    for (int b = 0; b < 2; ++b)
+        if (ctx->f64 || !encode_f32_tile_map(&gmap[b], (const float*)g[b], ctx->cfg.nx, ctx->cfg.ny)) gmap[b].valid = 0;
     char* uhist = ws + A.uhist;
     const size_t ustride = (size_t)ctx->K * ctx->N * elem_bytes(ctx);
     LBRS_CUDA(ctx, cudaMemcpyAsync(g[0], d_gbar_T, ctx->L.f_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -1217,7 +1220,8 @@ lbrs_status lbrs_backward_checkpointed(lbrs_ctx* ctx, void* d_adj_ws, const void
             int64_t t = len;                                   // g[gc] holds k^{start+t}
             for (; t >= 3; t -= 2) {
                 aa = adj_args<float>(ctx, uhist + (t - 2) * ustride, g[gc], g[gc ^ 1]);
-                LBRS_CUDA(ctx, launch_adj_fused2_f32(aa, (const float*)(uhist + (t - 3) * ustride), ctx->stream));
+                LBRS_CUDA(ctx, launch_adj_fused2_f32(aa, (const float*)(uhist + (t - 3) * ustride), &gmap[gc],
+                                                     wait_flag(ctx), ctx->stream));
                 gc ^= 1;
             }
             if (t == 2) {
