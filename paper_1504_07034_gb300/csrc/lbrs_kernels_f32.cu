@@ -1025,6 +1025,108 @@ __global__ void __launch_bounds__(kFTX * kFTY, 5)
     }
 }
 
+// ---------------------------------------------------------------- adjoint at omega = 1, moments form
+//
+// At omega = 1 the local operator returns k_q = J_E(U)^T g for every q: the sweep's
+// state is q-independent, so it is kept as its 4 fields kU (the adjoint's analogue of
+// the forward's moments-only form; exact, the same values as the 16-value sweep).
+// The gather becomes g_q(x) = kU(x + c_q): 4 fields of each of the 4 neighbours.
+
+// g_q(x) = kU(x + c_q) for cell (i, j) of the periodic grid (kU: 4 planes).
+__device__ __forceinline__ void adj_gather_u(const float* __restrict__ kU, int64_t N, int nx, int ny, int i, int j,
+                                             float g[4][4])
+{
+    const int SX[4] = {-1, 1, 1, -1};
+    const int SY[4] = {-1, -1, 1, 1};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int64_t s = (int64_t)wrap_index(j + SY[q], ny) * nx + wrap_index(i + SX[q], nx);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) g[q][k] = kU[LBRS_IX(k * N + s, 4 * N, 36)];
+    }
+}
+
+// kU = J_E(U)^T g from the full g (a.gin, 16 planes): the start of a sweep.
+__global__ void __launch_bounds__(256) adj_local_u_kernel(const AdjArgs<float> a)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < a.N; c += (int64_t)gridDim.x * blockDim.x) {
+        float g[4][4], U[4], ubar[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) g[q][k] = a.gin[LBRS_IX((q * 4 + k) * a.N + c, 16 * a.N, 36)];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) U[k] = a.U[LBRS_IX(k * a.N + c, 4 * a.N, 36)];
+        equilibrium_vjp2d<float>(U, g, a.gamma, a.gm1, a.c, ubar);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a.gout[LBRS_IX(k * a.N + c, 4 * a.N, 36)] = ubar[k];
+    }
+}
+
+// One step from kU (a.gin, 4 planes): with a.U, kU' = J_E(U)^T g; without, the full
+// g (16 planes) for the earlier segment.
+__global__ void __launch_bounds__(256) adj_pull_u_kernel(const AdjArgs<float> a)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= a.nx || j >= a.ny) return;
+    const int64_t c = (int64_t)j * a.nx + i;
+    float g[4][4];
+    adj_gather_u(a.gin, a.N, a.nx, a.ny, i, j, g);
+    if (a.U) {
+        float U[4], ubar[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) U[k] = a.U[LBRS_IX(k * a.N + c, 4 * a.N, 36)];
+        equilibrium_vjp2d<float>(U, g, a.gamma, a.gm1, a.c, ubar);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a.gout[LBRS_IX(k * a.N + c, 4 * a.N, 36)] = ubar[k];
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) a.gout[LBRS_IX((q * 4 + k) * a.N + c, 16 * a.N, 36)] = g[q][k];
+    }
+}
+
+// Two steps kU^s -> kU^{s-2} on a 32 x 16 tile: phase 1 forms kU^{s-1} on the 34 x 18
+// window (4 fields per slot in shared memory), phase 2 kU^{s-2} for the tile.
+__global__ void __launch_bounds__(kFTX * kFTY) adj_fused2_u_kernel(const AdjArgs<float> a, const float* __restrict__ U2)
+{
+    __shared__ float s_w[4 * kTWN];
+    const int i0 = blockIdx.x * kFTX, j0 = blockIdx.y * kTY;
+    for (int w = threadIdx.x; w < kTWN; w += kFTX * kFTY) {
+        const int i = wrap_index(i0 - 1 + w % kFWX, a.nx), j = wrap_index(j0 - 1 + w / kFWX, a.ny);
+        float g[4][4], U[4], ubar[4];
+        adj_gather_u(a.gin, a.N, a.nx, a.ny, i, j, g);
+        const int64_t c = (int64_t)j * a.nx + i;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) U[k] = a.U[LBRS_IX(k * a.N + c, 4 * a.N, 37)];
+        equilibrium_vjp2d<float>(U, g, a.gamma, a.gm1, a.c, ubar);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) s_w[LBRS_IX(k * kTWN + w, 4 * kTWN, 37)] = ubar[k];
+    }
+    __syncthreads();
+    const int ti = threadIdx.x % kFTX;
+    for (int tj = threadIdx.x / kFTX; tj < kTY; tj += kFTY) {
+        const int i = i0 + ti, j = j0 + tj;
+        if (i >= a.nx || j >= a.ny) continue;
+        // the source of population q, x + c_q, is window slot (ti + 1 + sx_q, tj + 1 + sy_q)
+        const int s0 = (tj + 1) * kFWX + ti + 1;
+        const int sl[4] = {s0 - kFWX - 1, s0 - kFWX + 1, s0 + kFWX + 1, s0 + kFWX - 1};
+        float g[4][4], U[4], ubar[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) g[q][k] = s_w[LBRS_IX(k * kTWN + sl[q], 4 * kTWN, 37)];
+        const int64_t c = (int64_t)j * a.nx + i;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) U[k] = U2[LBRS_IX(k * a.N + c, 4 * a.N, 37)];
+        equilibrium_vjp2d<float>(U, g, a.gamma, a.gm1, a.c, ubar);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a.gout[LBRS_IX(k * a.N + c, 4 * a.N, 37)] = ubar[k];
+    }
+}
+
 // Kernel variant for D2Q4 FP32: 0 = scalar one cell per thread, 2 or 4 =
 // vector width, 12 / 14 = 2 / 4 strided cells per thread.  The default can be
 // overridden for tuning sweeps with the environment variable LBRS_F32_STEP_VARIANT.
@@ -1246,6 +1348,39 @@ cudaError_t launch_adj_fused2_f32(const AdjArgs<float>& a, const float* U2, cons
     }
     const dim3 grid((unsigned)((a.nx + kFTX - 1) / kFTX), (unsigned)((a.ny + kFTY - 1) / kFTY));
     adj_fused2_kernel<<<grid, kFTX * kFTY, 0, s>>>(a, U2);
+    return cudaGetLastError();
+}
+
+// The omega = 1 sweep in its moments form; on by default, LBRS_ADJ_UFORM=0 turns it off.
+bool adj_uform_enabled()
+{
+    static int v = [] {
+        const char* e = getenv("LBRS_ADJ_UFORM");
+        return (e && !strcmp(e, "0")) ? 0 : 1;
+    }();
+    return v != 0;
+}
+
+cudaError_t launch_adj_local_u_f32(const AdjArgs<float>& a, cudaStream_t s)
+{
+    int64_t b = (a.N + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    adj_local_u_kernel<<<(unsigned)(b < 1 ? 1 : b), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_pull_u_f32(const AdjArgs<float>& a, cudaStream_t s)
+{
+    const dim3 block(128, 2);
+    const dim3 grid((unsigned)((a.nx + block.x - 1) / block.x), (unsigned)((a.ny + block.y - 1) / block.y));
+    adj_pull_u_kernel<<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_fused2_u_f32(const AdjArgs<float>& a, const float* U2, cudaStream_t s)
+{
+    const dim3 grid((unsigned)((a.nx + kFTX - 1) / kFTX), (unsigned)((a.ny + kTY - 1) / kTY));
+    adj_fused2_u_kernel<<<grid, kFTX * kFTY, 0, s>>>(a, U2);
     return cudaGetLastError();
 }
 

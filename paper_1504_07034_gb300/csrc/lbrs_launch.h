@@ -110,6 +110,13 @@ cudaError_t launch_adj_pull_f32(const AdjArgs<float>& a, cudaStream_t s);
 // tiles, reporting a bounded wait that gave up in *wait_flag; otherwise direct loads.
 cudaError_t launch_adj_fused2_f32(const AdjArgs<float>& a, const float* U2, const TileMap* map, unsigned* wait_flag,
                                   cudaStream_t s);
+// FP32 sweep at omega = 1 in its moments form: the state kU = J_E(U)^T g (4 planes, the
+// same for every population).  local: kU from a full g; pull: kU -> kU' (a.U set) or
+// -> the full g (a.U NULL); fused2: kU^s -> kU^{s-2} (a.U = U_{s-1}, U2 = U_{s-2}).
+bool adj_uform_enabled();
+cudaError_t launch_adj_local_u_f32(const AdjArgs<float>& a, cudaStream_t s);
+cudaError_t launch_adj_pull_u_f32(const AdjArgs<float>& a, cudaStream_t s);
+cudaError_t launch_adj_fused2_u_f32(const AdjArgs<float>& a, const float* U2, cudaStream_t s);
 cudaError_t launch_vjp_equilibrium_f64(const AdjArgs<double>& a, cudaStream_t s);
 cudaError_t launch_vjp_equilibrium_f32(const AdjArgs<float>& a, cudaStream_t s);
 

@@ -1214,23 +1214,26 @@ lbrs_status lbrs_backward_checkpointed(lbrs_ctx* ctx, void* d_adj_ws, const void
             // sweep on k = fbar: k^{end} from g^{end}, two steps per launch while U_{s-1} and
             // U_{s-2} lie in this segment, one more step if needed, then the pull that hands
             // g^{start} to the earlier segment.  uhist[m] holds U_{start+m+1}.
+            // at omega = 1 the sweep's state is the same for every population: kept as 4 fields
+            const bool uform = ctx->cfg.omega == 1.0 && adj_uform_enabled();
             AdjArgs<float> aa = adj_args<float>(ctx, uhist + (len - 1) * ustride, g[gc], g[gc ^ 1]);
-            LBRS_CUDA(ctx, launch_adj_local_f32(aa, ctx->stream));
+            LBRS_CUDA(ctx, uform ? launch_adj_local_u_f32(aa, ctx->stream) : launch_adj_local_f32(aa, ctx->stream));
             gc ^= 1;
             int64_t t = len;                                   // g[gc] holds k^{start+t}
             for (; t >= 3; t -= 2) {
                 aa = adj_args<float>(ctx, uhist + (t - 2) * ustride, g[gc], g[gc ^ 1]);
-                LBRS_CUDA(ctx, launch_adj_fused2_f32(aa, (const float*)(uhist + (t - 3) * ustride), &gmap[gc],
-                                                     wait_flag(ctx), ctx->stream));
+                const float* U2 = (const float*)(uhist + (t - 3) * ustride);
+                LBRS_CUDA(ctx, uform ? launch_adj_fused2_u_f32(aa, U2, ctx->stream)
+                                     : launch_adj_fused2_f32(aa, U2, &gmap[gc], wait_flag(ctx), ctx->stream));
                 gc ^= 1;
             }
             if (t == 2) {
                 aa = adj_args<float>(ctx, uhist, g[gc], g[gc ^ 1]);
-                LBRS_CUDA(ctx, launch_adj_pull_f32(aa, ctx->stream));
+                LBRS_CUDA(ctx, uform ? launch_adj_pull_u_f32(aa, ctx->stream) : launch_adj_pull_f32(aa, ctx->stream));
                 gc ^= 1;
             }
             aa = adj_args<float>(ctx, nullptr, g[gc], g[gc ^ 1]);
-            LBRS_CUDA(ctx, launch_adj_pull_f32(aa, ctx->stream));
+            LBRS_CUDA(ctx, uform ? launch_adj_pull_u_f32(aa, ctx->stream) : launch_adj_pull_f32(aa, ctx->stream));
             gc ^= 1;
             ctx->launches += 2 + (len - 1) / 2 + ((len - 1) % 2);
         } else {

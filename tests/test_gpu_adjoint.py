@@ -100,9 +100,10 @@ from paper_1504_07034_gb300.solver import Solver
 out = []
 for (nx, ny), steps, seg in (((64, 48), 23, 5), ((66, 18), 20, 4), ((34, 10), 9, 9), ((130, 50), 12, 1),
                              ((2, 2), 7, 3), ((40, 8), 30, 6)):
-    wl, target = W.adjoint_pulses(seed=2, n=max(nx, ny), steps=0, width=0.1, pulses=3, omega=1.3)
+    omega = float(sys.argv[3])
+    wl, target = W.adjoint_pulses(seed=2, n=max(nx, ny), steps=0, width=0.1, pulses=3, omega=omega)
     prim = np.ascontiguousarray(wl.prim[:, :ny, :nx])
-    s = Solver("d2q4", nx, ny, lam=wl.lam, dx=wl.dx, bc=[("periodic", None)] * 4, omega=1.3, precision="f32")
+    s = Solver("d2q4", nx, ny, lam=wl.lam, dx=wl.dx, bc=[("periodic", None)] * 4, omega=omega, precision="f32")
     s.set_state(torch.from_numpy(prim).cuda())
     s.forward_checkpointed(steps, seg)
     _, gT = s.vjp_loss(torch.from_numpy(np.ascontiguousarray(target[:ny, :nx])).cuda())
@@ -127,10 +128,31 @@ def test_f32_fused_sweep_equals_push_sweep(tmp_path):
     for fuse in ("0", "1"):
         out = tmp_path / f"g{fuse}.npy"
         env = dict(os.environ, LBRS_F32_FUSE=fuse)
-        subprocess.run([sys.executable, str(script), root, str(out)], check=True, env=env, timeout=300)
+        subprocess.run([sys.executable, str(script), root, str(out), "1.3"], check=True, env=env, timeout=300)
         res[fuse] = np.load(out)
     assert np.all(np.isfinite(res["0"]))
     assert np.array_equal(res["0"], res["1"]), np.max(np.abs(res["0"] - res["1"])) / np.max(np.abs(res["0"]))
+
+
+def test_f32_omega1_moments_sweep_equals_full_sweeps(tmp_path):
+    """At omega = 1 the FP32 sweep keeps its state as the 4 fields J_E^T g (the same for every
+    population): the gradient must equal the 16-value fused sweep's and the push sweep's bit for
+    bit, over the same segmentations and grids."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = tmp_path / "sweep.py"
+    script.write_text(_SWEEP_SCRIPT)
+    res = {}
+    for name, env_add in (("uform", {}), ("full", {"LBRS_ADJ_UFORM": "0"}), ("push", {"LBRS_F32_FUSE": "0"})):
+        out = tmp_path / f"{name}.npy"
+        env = dict(os.environ, **env_add)
+        subprocess.run([sys.executable, str(script), root, str(out), "1.0"], check=True, env=env, timeout=300)
+        res[name] = np.load(out)
+    assert np.all(np.isfinite(res["push"]))
+    for name in ("uform", "full"):
+        assert np.array_equal(res[name], res["push"]), (name, np.max(np.abs(res[name] - res["push"])))
 
 
 def _fd_errors(s_grad, wl, target, U0, steps, ndir, seed=5):
