@@ -8,6 +8,9 @@ forward map, which the other pin files tie to the paper:
   A2 one adjoint step: <w, (step(fs+h d) - step(fs-h d))/2h> == <adjoint_step(w), d>
   A3 whole gradient of the config-5 style density loss over many steps against
      central differences along random directions and single entries.
+  A4 at omega = 1 the adjoint of a step is the push of one 4-field quantity:
+     dL/dfs^n_q(y) = (J_E(U(x))^T g(x))(x = y + c_q) for every q (the basis of the
+     GPU sweep's 4-field form at omega = 1, as P2 is of the forward's moments-only form).
 """
 import numpy as np
 import pytest
@@ -101,3 +104,24 @@ def test_adjoint_rejects_non_periodic():
     o = oracle.Oracle(oracle.D2Q4, 4, 4, lam=3.0, bc=[("transmissive", None)] * 4)
     with pytest.raises(ValueError):
         o.adjoint_step(np.ones((4, 4, 4)), np.ones((4, 4, 4, 4)))
+
+
+def test_a4_omega1_adjoint_is_push_of_four_fields():
+    rng = np.random.default_rng(14)
+    n = 8
+    o = periodic(n, omega=1.0)
+    prim, _ = pulse_state(n, seed=2)
+    fs = o.init(o.prim_to_cons(prim)) * (1 + 0.05 * rng.uniform(-1, 1, (4, 4, n, n)))
+    _, U_next = step(o, fs)
+    g = rng.standard_normal(fs.shape)
+    out = o.adjoint_step(U_next, g)
+    ubar = o.vjp_equilibrium(U_next, g)                 # J_E(U)^T g per cell: 4 fields
+    SX, SY = [-1, 1, 1, -1], [-1, -1, 1, 1]
+    for q in range(4):
+        want = np.roll(ubar, shift=(-SY[q], -SX[q]), axis=(1, 2))   # ubar(y + c_q)
+        assert np.allclose(out[q], want, rtol=1e-14, atol=1e-14 * np.abs(ubar).max())
+    # and the 4-field form is not an identity of every omega
+    o13 = periodic(n, omega=1.3)
+    out13 = o13.adjoint_step(U_next, g)
+    assert not np.allclose(out13[0], np.roll(o13.vjp_equilibrium(U_next, g), shift=(1, 1), axis=(1, 2)))
+
