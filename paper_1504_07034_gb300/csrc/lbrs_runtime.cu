@@ -367,7 +367,7 @@ int64_t obstacle_violations(const lbrs_config* c, const uint8_t* m)
         for (int64_t i = 0; i < nx; ++i) {
             if (m[j * nx + i]) continue;
             for (int q = 0; q < 4; ++q) {
-                const int64_t si = i - SX[q], sj = j - SY[q];
+                const int64_t sj = j - SY[q];
                 const bool out_y = sj < 0 || sj >= ny;
                 if (out_y && c->bc[sj < 0 ? 2 : 3].kind == LBRS_BC_WALL) continue;   // a domain wall's population
                 if (!unknown(i, j, q)) continue;
