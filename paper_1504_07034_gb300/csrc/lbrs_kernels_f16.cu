@@ -15,12 +15,15 @@
 // cell, 32 B per lattice update.
 //
 // Both stream by reconstruction: f*_q(x - c_q) = f^eq_q(U(x - c_q)) [+ s_k g_q].
-// One CTA owns a 32 x 8 tile; it first rebuilds f* of the 34 x 10 window (tile
+// One CTA owns a 32 x 16 tile; it first rebuilds f* of the 34 x 18 window (tile
 // plus one cell of halo, sources outside the domain resolved by the boundary
 // kind exactly as the pull of the distribution-storing kernel does) in shared
 // memory, each window cell once, then every tile cell gathers its four pulled
 // populations, applies the wall relations, forms U and -- for the FP16 form --
-// the new non-equilibrium parts g = (1 - omega)(f - f^eq(U)).
+// the new non-equilibrium parts g = (1 - omega)(f - f^eq(U)).  The window keeps
+// the four fields of a population together (one 16-byte word per population and
+// slot), so a slot is written and a cell's pull is read in four vector accesses;
+// a tile whose window lies inside the domain skips the boundary resolution.
 #include <cuda_fp16.h>
 
 #include "lbrs_kernels.cuh"
@@ -44,12 +47,13 @@ struct F16Args {
     float om, om1, c, gm1;
 };
 
-constexpr int kTX = 32, kTY = 8, kWX = kTX + 2, kWY = kTY + 2, kWN = kWX * kWY;
+constexpr int kTX = 32, kTY = 16, kWX = kTX + 2, kWY = kTY + 2, kWN = kWX * kWY;
+constexpr int kThreads = kTX * kTY;
 
 template <bool F16>
-__global__ void __launch_bounds__(kTX * kTY) step2d_tile_kernel(const F16Args a)
+__global__ void __launch_bounds__(kThreads) step2d_tile_kernel(const F16Args a)
 {
-    __shared__ float s_f[16 * kWN];      // f*_{q,k} of every window slot: [q * 4 + k][slot]
+    __shared__ float4 s_f[4 * kWN];      // f*_{q,k} of every window slot: [q][slot].(k = x, y, z, w)
     const int i0 = blockIdx.x * kTX - 1, j0 = blockIdx.y * kTY - 1;
     float sc[4] = {1.f, 1.f, 1.f, 1.f}, inv[4] = {1.f, 1.f, 1.f, 1.f};
     if constexpr (F16) {
@@ -62,32 +66,36 @@ __global__ void __launch_bounds__(kTX * kTY) step2d_tile_kernel(const F16Args a)
     }
 
     // phase 1: f* of each window slot, its source resolved like the pull does
-    for (int w = threadIdx.x; w < kWN; w += kTX * kTY) {
+    const bool inside = i0 >= 0 && j0 >= 0 && i0 + kWX <= a.nx && j0 + kWY <= a.ny;
+    for (int w = threadIdx.x; w < kWN; w += kThreads) {
         int i = i0 + w % kWX, j = j0 + w / kWX;
-        // a slot more than one cell outside the grid is no tile cell's source (and one
-        // wrap would not bring it inside a periodic grid narrower than the tile)
-        if (i < -1 || i > a.nx || j < -1 || j > a.ny) continue;
-        const int side_x = i < 0 ? 0 : (i >= a.nx ? 1 : -1);
-        const int side_y = j < 0 ? 2 : (j >= a.ny ? 3 : -1);
-        const int kind_x = side_x == 0 ? a.bc[0] : a.bc[1];
-        const int kind_y = side_y == 2 ? a.bc[2] : a.bc[3];
-        const float* g = nullptr;
-        if (side_x >= 0) {
-            if (kind_x == BC_DIRICHLET) g = a.ghost + side_x * GHOST_STRIDE;
-            else if (kind_x == BC_PERIODIC) i = i < 0 ? i + a.nx : i - a.nx;
-            else i = i < 0 ? 0 : a.nx - 1;
-        }
-        if (!g && side_y >= 0) {
-            // a wall side's slot is never used (the wall relation replaces those
-            // populations); clamp it like a transmissive side
-            if (kind_y == BC_DIRICHLET) g = a.ghost + side_y * GHOST_STRIDE;
-            else if (kind_y == BC_PERIODIC) j = j < 0 ? j + a.ny : j - a.ny;
-            else j = j < 0 ? 0 : a.ny - 1;
-        }
-        if (g) {
+        if (!inside) {
+            // a slot more than one cell outside the grid is no tile cell's source (and one
+            // wrap would not bring it inside a periodic grid narrower than the tile)
+            if (i < -1 || i > a.nx || j < -1 || j > a.ny) continue;
+            const int side_x = i < 0 ? 0 : (i >= a.nx ? 1 : -1);
+            const int side_y = j < 0 ? 2 : (j >= a.ny ? 3 : -1);
+            const int kind_x = side_x == 0 ? a.bc[0] : a.bc[1];
+            const int kind_y = side_y == 2 ? a.bc[2] : a.bc[3];
+            const float* g = nullptr;
+            if (side_x >= 0) {
+                if (kind_x == BC_DIRICHLET) g = a.ghost + side_x * GHOST_STRIDE;
+                else if (kind_x == BC_PERIODIC) i = i < 0 ? i + a.nx : i - a.nx;
+                else i = i < 0 ? 0 : a.nx - 1;
+            }
+            if (!g && side_y >= 0) {
+                // a wall side's slot is never used (the wall relation replaces those
+                // populations); clamp it like a transmissive side
+                if (kind_y == BC_DIRICHLET) g = a.ghost + side_y * GHOST_STRIDE;
+                else if (kind_y == BC_PERIODIC) j = j < 0 ? j + a.ny : j - a.ny;
+                else j = j < 0 ? 0 : a.ny - 1;
+            }
+            if (g) {
 #pragma unroll
-            for (int n = 0; n < 16; ++n) s_f[LBRS_IX(n * kWN + w, 16 * kWN, 40)] = g[n];
-            continue;
+                for (int q = 0; q < 4; ++q)
+                    s_f[LBRS_IX(q * kWN + w, 4 * kWN, 40)] = make_float4(g[q * 4], g[q * 4 + 1], g[q * 4 + 2], g[q * 4 + 3]);
+                continue;
+            }
         }
         const int64_t c = (int64_t)j * a.nx + i;
         float U[4];
@@ -108,9 +116,7 @@ __global__ void __launch_bounds__(kTX * kTY) step2d_tile_kernel(const F16Args a)
             }
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) s_f[LBRS_IX((q * 4 + k) * kWN + w, 16 * kWN, 40)] = e[q][k];
+        for (int q = 0; q < 4; ++q) s_f[LBRS_IX(q * kWN + w, 4 * kWN, 40)] = make_float4(e[q][0], e[q][1], e[q][2], e[q][3]);
     }
     __syncthreads();
 
@@ -123,9 +129,13 @@ __global__ void __launch_bounds__(kTX * kTY) step2d_tile_kernel(const F16Args a)
     const int src[4] = {slot + kWX + 1, slot + kWX - 1, slot - kWX - 1, slot - kWX + 1};
     float f[4][4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) f[q][k] = s_f[LBRS_IX((q * 4 + k) * kWN + src[q], 16 * kWN, 40)];
+    for (int q = 0; q < 4; ++q) {
+        const float4 v = s_f[LBRS_IX(q * kWN + src[q], 4 * kWN, 40)];
+        f[q][0] = v.x;
+        f[q][1] = v.y;
+        f[q][2] = v.z;
+        f[q][3] = v.w;
+    }
     const bool wall_bottom = j == 0 && a.bc[2] == BC_WALL;
     const bool wall_top = j == a.ny - 1 && a.bc[3] == BC_WALL;
 #pragma unroll
@@ -234,14 +244,14 @@ static F16Args tile_args(const F16StepArgs& s, bool f16)
 cudaError_t launch_step_f16neq(const F16StepArgs& s, cudaStream_t st)
 {
     const dim3 grid((unsigned)((s.nx + kTX - 1) / kTX), (unsigned)((s.ny + kTY - 1) / kTY));
-    step2d_tile_kernel<true><<<grid, kTX * kTY, 0, st>>>(tile_args(s, true));
+    step2d_tile_kernel<true><<<grid, kThreads, 0, st>>>(tile_args(s, true));
     return cudaGetLastError();
 }
 
 cudaError_t launch_step_f32u(const F16StepArgs& s, cudaStream_t st)
 {
     const dim3 grid((unsigned)((s.nx + kTX - 1) / kTX), (unsigned)((s.ny + kTY - 1) / kTY));
-    step2d_tile_kernel<false><<<grid, kTX * kTY, 0, st>>>(tile_args(s, false));
+    step2d_tile_kernel<false><<<grid, kThreads, 0, st>>>(tile_args(s, false));
     return cudaGetLastError();
 }
 

@@ -61,7 +61,7 @@ BCS = {"transmissive": [T] * 4, "periodic": [P] * 4, "mixed": [D[0], T, WL, D[1]
 base = W.quadrant_riemann(1, 64, steps=0)
 for precision in ("f64", "f32", "f16neq", "f32u"):
     for bname, bc in BCS.items():
-        for nx, ny in ((1, 1), (1, 9), (33, 1), (5, 3), (37, 29), (36, 20), (66, 17), (132, 18)):
+        for nx, ny in ((1, 1), (1, 9), (33, 1), (5, 3), (37, 29), (36, 20), (66, 17), (132, 18), (98, 66)):
             if bc[0] == P and nx % 2:
                 nx += 1
             if bc[2] == P and ny % 2:

@@ -4,7 +4,7 @@ At omega = 1 the post-collision state is f^eq(U), so storing U alone is an exact
 reformulation: the form must agree with the FP32 distribution-storing path up
 to FP32 rounding, and with the FP64 oracle within the FP32 bar, on every
 boundary kind and on tiles cut by the domain edge (nx, ny not multiples of the
-32 x 8 tile).
+32 x 16 tile).
 """
 import numpy as np
 import pytest
