@@ -68,7 +68,7 @@ for precision in ("f64", "f32", "f16neq", "f32u"):
                 ny += 1
             if WL in (bc[2], bc[3]):
                 ny = max(ny, 2)
-            prim = np.ascontiguousarray(np.tile(base.prim, (1, 1, 4))[:, :ny, :nx])
+            prim = np.ascontiguousarray(np.tile(base.prim, (1, 2, 4))[:, :ny, :nx])
             if bc[2] == WL:
                 prim[2, 0, :] = 0.0
             if bc[3] == WL:
