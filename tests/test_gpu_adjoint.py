@@ -7,7 +7,6 @@ central finite differences to 1e-4 (relative, along random directions) on a
 64 x 64 copy of the adjoint workload run to the same final time, and at the
 workload's full 2048 x 2048 x 2000-step size.
 """
-import math
 
 import numpy as np
 import pytest

@@ -1,7 +1,6 @@
 """Checkpoint blobs through the C ABI: resuming is bit-identical to an uninterrupted run (device
 and host blobs, the FP32, FP64 and FP16 forms, the two-steps-per-launch path, the step counter);
 a blob of another configuration or a foreign buffer is refused."""
-import numpy as np
 import pytest
 import torch
 
