@@ -738,7 +738,13 @@ def run_ours(args):
                          "kernel": "step2d_f32_fused2_tall_kernel<false>", "peak_kind": f"{peak_kind} hbm_gbs",
                          "algorithmic_bytes_per_launch": 2 * BYTES_PER_LUP_F32_FUSED2 * wl.cells,
                          "algorithmic_bytes_per_lup": BYTES_PER_LUP_F32_FUSED2,
-                         "timed_call": "lbrs_step(2): one launch of the two-steps-per-launch kernel"},
+                         "timed_call": "lbrs_step(2): one launch of the two-steps-per-launch kernel",
+                         "per_step_roofline": {
+                             "mlups": peak * 1e3 / BYTES_PER_LUP_F32,
+                             "value_over_it": value / ws / (peak * 1e3 / BYTES_PER_LUP_F32),
+                             "note": "the MLUPS that the peak allows a step that reads and writes the state once "
+                                     "(128 B per update); two steps per launch move 64 B per update, so the "
+                                     "step rate can pass it"}},
             "single_step_kernel": single_step,
             "steady_large_grid": steady,
             "moments_only_omega1": moments_only,
