@@ -95,7 +95,6 @@ class Solver:
     def grid(self):
         return (self.ny, self.nx) if self.lattice in ("d2q4", "d2q4s") else (self.nx,)
 
-
     @property
     def storage_dtype(self):
         return torch.float64 if self.precision == "f64" else torch.float32
