@@ -63,6 +63,15 @@ MUTANTS = {
     "adaptive_collides_with_stream_lambda": ("Qc.lambda = lam_new;", "Qc.lambda = lam_cur;"),
     "adaptive_ignores_dirichlet_states": ("        if (P->bc_kind[s] != ORC_DIRICHLET) continue;\n        double u[4];",
                                           "        if (P->bc_kind[s] != ORC_DIRICHLET || 1) continue;\n        double u[4];"),
+    # local wave-speed bound and boundary resolution
+    "d2q4_bound_without_sqrt2": ("return (s1 > s2 ? s1 : s2) + sqrt(2.0) * a;", "return (s1 > s2 ? s1 : s2) + a;"),
+    "sound_speed_without_gamma": ("double a = sqrt(P->gamma * p / U[0]);", "double a = sqrt(p / U[0]);"),
+    "periodic_y_clamps": ("else if (kind == ORC_PERIODIC) sj = (sj + ny) % ny;",
+                          "else if (kind == ORC_PERIODIC) sj = sj < 0 ? 0 : ny - 1;"),
+    "corner_ghost_from_y_side": (
+        "if (kind == ORC_DIRICHLET) g = scalar ? profile_ghost(P, side_x, sj, gbuf) : ghost[side_x];",
+        "if (kind == ORC_DIRICHLET && !(side_y >= 0 && P->bc_kind[side_y] == ORC_DIRICHLET))"
+        " g = scalar ? profile_ghost(P, side_x, sj, gbuf) : ghost[side_x];"),
     "adjoint_relaxation_weights_swapped": ("gout[(q * 4 + k) * N + tj * nx + ti] = om1 * gq[q * 4 + k] + om * ubar[k];",
                                            "gout[(q * 4 + k) * N + tj * nx + ti] = om * gq[q * 4 + k] + om1 * ubar[k];"),
 }
