@@ -72,6 +72,11 @@ MUTANTS = {
         "if (kind == ORC_DIRICHLET) g = scalar ? profile_ghost(P, side_x, sj, gbuf) : ghost[side_x];",
         "if (kind == ORC_DIRICHLET && !(side_y >= 0 && P->bc_kind[side_y] == ORC_DIRICHLET))"
         " g = scalar ? profile_ghost(P, side_x, sj, gbuf) : ghost[side_x];"),
+    "top_wall_crossed_mapping": (
+        "f[(0 * K + k) * N + c] = sgn * f[(3 * K + k) * N + c];\n"
+        "                    f[(1 * K + k) * N + c] = sgn * f[(2 * K + k) * N + c];",
+        "f[(0 * K + k) * N + c] = sgn * f[(2 * K + k) * N + c];\n"
+        "                    f[(1 * K + k) * N + c] = sgn * f[(3 * K + k) * N + c];"),
     "adjoint_relaxation_weights_swapped": ("gout[(q * 4 + k) * N + tj * nx + ti] = om1 * gq[q * 4 + k] + om * ubar[k];",
                                            "gout[(q * 4 + k) * N + tj * nx + ti] = om * gq[q * 4 + k] + om1 * ubar[k];"),
 }
