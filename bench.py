@@ -52,7 +52,7 @@ def workload():
 def config_dict(wl, extra=None):
     d = {"workload": "2-D D2Q4 four-quadrant Riemann 1024x1024, seed 0, transmissive, 1000-step configuration",
          "nx": wl.nx, "ny": wl.ny, "lattice": "D2Q4", "gamma": wl.gamma, "omega": wl.omega,
-         "lambda": wl.lam, "precision": "f32",
+         "lambda": wl.lam,
          "l2": "flushed (256 MiB write) before every timed call of lbrs_step (two time steps for the "
                "FP32 headline, one for the others), outside the call's CUDA events"}
     if extra:
@@ -190,9 +190,10 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded quadrant states)", "config": config_dict(wl, {"precision": "f64"}),
+            "data": "synthetic (seeded quadrant states)", "config": config_dict(wl),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-                             "sample": f"full {wl.nx}x{wl.ny} grid, {args.steps} steps after {args.warmup} warm-up"},
+                             "sample": f"full {wl.nx}x{wl.ny} grid, {args.steps} steps after {args.warmup} warm-up, "
+                                       "FP64 on the host cores (no L2 flush: a CPU run)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
