@@ -105,15 +105,24 @@ typedef enum { LBRS_F64 = 0, LBRS_F32 = 1, LBRS_F16NEQ = 2, LBRS_F32U = 3 } lbrs
  *   PERIODIC     the pull source wraps around (both sides of an axis must be periodic);
  *   TRANSMISSIVE the pull source index is clamped into the domain (zero-order extrapolation);
  *   DIRICHLET    populations entering from outside are f^eq of the given state;
- *   WALL         free-slip wall on a y side (D2Q4 only), applied on the wall row. */
-typedef enum { LBRS_BC_PERIODIC = 0, LBRS_BC_TRANSMISSIVE = 1, LBRS_BC_DIRICHLET = 2, LBRS_BC_WALL = 3 } lbrs_bc_kind;
+ *   WALL         free-slip wall on a y side (D2Q4 only), applied on the wall row;
+ *   CUT          a y side (D2Q4; LBRS_F64, LBRS_F32 or LBRS_F32U) where this context's rows
+ *                meet a neighbouring context's rows: the context is one y-slab of a larger
+ *                grid (see lbrs_halo_export below). */
+typedef enum {
+    LBRS_BC_PERIODIC = 0,
+    LBRS_BC_TRANSMISSIVE = 1,
+    LBRS_BC_DIRICHLET = 2,
+    LBRS_BC_WALL = 3,
+    LBRS_BC_CUT = 4
+} lbrs_bc_kind;
 
 /* Kind of the fields passed to lbrs_set_state. */
 typedef enum { LBRS_CONSERVED = 0, LBRS_PRIMITIVE = 1 } lbrs_state_kind;
 
 typedef struct {
     int32_t kind;       /* lbrs_bc_kind */
-    int32_t reserved;
+    int32_t halo_rows;  /* CUT only: ghost rows H stored beyond the side, 1..64 (0: 2); ignored otherwise */
     double prim[4];     /* DIRICHLET state: (rho, u, v, p) in 2-D, (rho, u, p) in 1-D */
 } lbrs_bc;
 
@@ -309,6 +318,46 @@ lbrs_status lbrs_checkpoint_load(lbrs_ctx* ctx, const void* src, int on_device);
  * With walls set, FP32 steps keep running two per launch where nx % 4 == 0 (the
  * tensor-copy form), one per launch otherwise; the adjoint calls return EINVAL. */
 lbrs_status lbrs_set_obstacles(lbrs_ctx* ctx, const uint8_t* d_solid);
+
+/* ---------------------------------------------------------------- y-slabs
+ *
+ * One grid split into y-slabs, one context per slab (on one GPU or one per GPU).
+ * The pull of the multi-D update (Section II.D) reads, for the row j, the rows
+ * j - 1 and j + 1 only, so a step of a slab needs, at each cut, the neighbouring
+ * slab's row next to the cut.  A context whose y side is LBRS_BC_CUT stores H
+ * ghost rows beyond that side (lbrs_bc.halo_rows) and closes its stored grid
+ * there like a transmissive side.  After a rows' import, up to H steps leave the
+ * context's own rows exactly as in the unsplit grid: each step spoils one more
+ * ghost row from the outer edge inwards and never an own row.  Hence:
+ *   - nx, ny, the fields of lbrs_set_state and lbrs_moments, the distributions of
+ *     lbrs_get/set_distributions and checkpoints, and the diagnostics cover the
+ *     context's own rows only (ny of them);
+ *   - after lbrs_set_state, lbrs_set_distributions or lbrs_checkpoint_load, and
+ *     after every H steps, lbrs_step returns LBRS_ESTATE until each cut side has
+ *     been imported again; a step count larger than what the last imports cover
+ *     is refused the same way (no step is taken);
+ *   - a slab's own rows evolve bit for bit as the same rows of the unsplit grid
+ *     do (same kernels, same per-cell arithmetic), provided that every import
+ *     carries the neighbour's rows of the same step number.
+ * Not covered on cut grids (LBRS_EINVAL): internal walls, the adaptive lambda,
+ * recording steps and the adjoint.  The diagnostics totals of the slabs add up to
+ * the unsplit grid's up to the order of the FP64 additions.
+ *
+ * lbrs_halo_size: the rows H of a cut side (2 = y-lo, 3 = y-hi; 0 rows if the side is
+ *   not a cut) and the bytes of one exchanged block: P planes x H rows x nx cells in
+ *   the storage precision, P = Q K = 16 in the distribution forms, 4 in LBRS_F32U.
+ * lbrs_halo_export: copies the H own rows next to `side` (rows 0..H-1 for y-lo,
+ *   ny-H..ny-1 for y-hi), every plane, to dst as [P][H][nx] (rows in increasing y).
+ *   dst is caller-owned, host (on_device = 0; the call then synchronises) or device
+ *   memory of any GPU (a peer copy).  Enqueued on the context's stream.
+ * lbrs_halo_import: writes such a block, exported by the neighbour across `side` (its
+ *   y-hi block for our y-lo side, its y-lo block for our y-hi side), into the ghost
+ *   rows beyond `side`, and lets H more steps run.  src as dst above; the caller keeps
+ *   it unchanged until the stream has passed the call.
+ * Both return LBRS_EINVAL for a side that is not a cut and LBRS_ESTATE without a state. */
+lbrs_status lbrs_halo_size(const lbrs_ctx* ctx, int side, int64_t* rows, size_t* bytes);
+lbrs_status lbrs_halo_export(lbrs_ctx* ctx, int side, void* dst, int on_device);
+lbrs_status lbrs_halo_import(lbrs_ctx* ctx, int side, const void* src, int on_device);
 
 /* ---------------------------------------------------------------- adjoint
  *

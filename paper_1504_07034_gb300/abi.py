@@ -18,16 +18,16 @@ LIB_PATH = PKG / "liblbrs.so"
 LBRS_OK, LBRS_EINVAL, LBRS_ENOMEM, LBRS_ECUDA, LBRS_ENONPHYS, LBRS_ESUBCHAR, LBRS_ETIMEOUT, LBRS_ESTATE = range(8)
 LBRS_D1Q2, LBRS_D2Q4, LBRS_D1Q3, LBRS_D2Q4S = 0, 1, 2, 3
 LBRS_F64, LBRS_F32, LBRS_F16NEQ, LBRS_F32U = 0, 1, 2, 3
-LBRS_BC_PERIODIC, LBRS_BC_TRANSMISSIVE, LBRS_BC_DIRICHLET, LBRS_BC_WALL = 0, 1, 2, 3
+LBRS_BC_PERIODIC, LBRS_BC_TRANSMISSIVE, LBRS_BC_DIRICHLET, LBRS_BC_WALL, LBRS_BC_CUT = 0, 1, 2, 3, 4
 LBRS_CONSERVED, LBRS_PRIMITIVE = 0, 1
 ABI_VERSION = 1
 
 BC_KINDS = {"periodic": LBRS_BC_PERIODIC, "transmissive": LBRS_BC_TRANSMISSIVE,
-            "dirichlet": LBRS_BC_DIRICHLET, "wall": LBRS_BC_WALL}
+            "dirichlet": LBRS_BC_DIRICHLET, "wall": LBRS_BC_WALL, "cut": LBRS_BC_CUT}
 
 
 class lbrs_bc(ctypes.Structure):
-    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("prim", ctypes.c_double * 4)]
+    _fields_ = [("kind", ctypes.c_int32), ("halo_rows", ctypes.c_int32), ("prim", ctypes.c_double * 4)]
 
 
 class lbrs_config(ctypes.Structure):
@@ -107,6 +107,10 @@ SIGNATURES = {
     "lbrs_step_adaptive": (ctypes.c_int, [_CTX, ctypes.c_int64, ctypes.c_double, ctypes.c_double]),
     "lbrs_adaptive_state": (ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int)]),
+    "lbrs_halo_size": (ctypes.c_int, [_CTX, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                      ctypes.POINTER(ctypes.c_size_t)]),
+    "lbrs_halo_export": (ctypes.c_int, [_CTX, ctypes.c_int, _P, ctypes.c_int]),
+    "lbrs_halo_import": (ctypes.c_int, [_CTX, ctypes.c_int, _P, ctypes.c_int]),
     "lbrs_step_count": (ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_int64)]),
     "lbrs_launch_count": (ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_int64)]),
     "lbrs_last_error": (ctypes.c_char_p, [_CTX]),

@@ -542,7 +542,7 @@ lbrs_status lbrs_batch_moments(lbrs_batch* B, void* U_out, int on_device, int dt
     if (!B->has_state) return bfail(B, LBRS_ESTATE, "no state set");
     void* dst = on_device ? U_out : (void*)B->f[B->cur ^ 1];
     BCUDA(B, launch_moments(B->q == 3 ? LAT_D1Q3 : LAT_D1Q2, B->f64, B->f[B->cur], dst, dtype == LBRS_F32, B->N,
-                            B->stream));
+                            B->N, B->stream));
     B->launches += 1;
     if (!on_device) {
         BCUDA(B, cudaMemcpyAsync(U_out, dst, (size_t)3 * B->N * (dtype == LBRS_F64 ? 8 : 4), cudaMemcpyDeviceToHost,

@@ -171,8 +171,8 @@ __global__ void __launch_bounds__(kThreads) step2d_tile_kernel(const F16Args a)
 // Initial state: U from W (conserved or primitive, FP64 arithmetic), g = 0.
 template <typename Tin>
 __global__ void __launch_bounds__(256) set_state_f16neq_kernel(const Tin* __restrict__ W, float* __restrict__ U,
-                                                               __half* __restrict__ g, int64_t N, int kind,
-                                                               double gamma)
+                                                               __half* __restrict__ g, int64_t N, int64_t P,
+                                                               int kind, double gamma)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         double w[4], u[4];
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(256) set_state_f16neq_kernel(const Tin* __rest
             for (int k = 0; k < 4; ++k) u[k] = w[k];
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k) U[k * N + i] = (float)u[k];
+        for (int k = 0; k < 4; ++k) U[k * P + i] = (float)u[k];
         if (g) {
 #pragma unroll
             for (int n = 0; n < 12; ++n) g[n * N + i] = __float2half_rn(0.f);
@@ -255,14 +255,14 @@ cudaError_t launch_step_f32u(const F16StepArgs& s, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_set_state_f32u(const void* W, int w_dtype, int kind, void* fs, int64_t N, double gamma,
-                                  cudaStream_t st)
+cudaError_t launch_set_state_f32u(const void* W, int w_dtype, int kind, void* fs, int64_t N, int64_t plane,
+                                  double gamma, cudaStream_t st)
 {
     int64_t b = (N + 255) / 256;
     if (b > 152 * 16) b = 152 * 16;
     const int g = (int)(b < 1 ? 1 : b);
-    if (w_dtype == 0) set_state_f16neq_kernel<double><<<g, 256, 0, st>>>((const double*)W, (float*)fs, nullptr, N, kind, gamma);
-    else set_state_f16neq_kernel<float><<<g, 256, 0, st>>>((const float*)W, (float*)fs, nullptr, N, kind, gamma);
+    if (w_dtype == 0) set_state_f16neq_kernel<double><<<g, 256, 0, st>>>((const double*)W, (float*)fs, nullptr, N, plane, kind, gamma);
+    else set_state_f16neq_kernel<float><<<g, 256, 0, st>>>((const float*)W, (float*)fs, nullptr, N, plane, kind, gamma);
     return cudaGetLastError();
 }
 
@@ -275,8 +275,8 @@ cudaError_t launch_set_state_f16neq(const void* W, int w_dtype, int kind, void* 
     const int g = (int)(b < 1 ? 1 : b);
     float* U = (float*)fs;
     __half* gq = (__half*)((char*)fs + 16 * N);
-    if (w_dtype == 0) set_state_f16neq_kernel<double><<<g, 256, 0, st>>>((const double*)W, U, gq, N, kind, gamma);
-    else set_state_f16neq_kernel<float><<<g, 256, 0, st>>>((const float*)W, U, gq, N, kind, gamma);
+    if (w_dtype == 0) set_state_f16neq_kernel<double><<<g, 256, 0, st>>>((const double*)W, U, gq, N, N, kind, gamma);
+    else set_state_f16neq_kernel<float><<<g, 256, 0, st>>>((const float*)W, U, gq, N, N, kind, gamma);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(absmax_bits, 0, 4 * sizeof(unsigned int), st);

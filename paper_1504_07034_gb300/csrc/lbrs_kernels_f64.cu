@@ -111,7 +111,8 @@ __global__ void ghost_kernel(GhostSpec g, double gamma, double c, Ts* ghost)
 
 template <typename Tin, typename Ts, int LAT>
 __global__ void __launch_bounds__(kThreads) set_state_kernel(const Tin* __restrict__ W, Ts* __restrict__ fs,
-                                                             int64_t N, int kind, double gamma, double c)
+                                                             int64_t N, int64_t P, int kind, double gamma,
+                                                             double c)
 {
     constexpr int Q = Dims<LAT>::Q, K = Dims<LAT>::K;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
@@ -126,20 +127,21 @@ __global__ void __launch_bounds__(kThreads) set_state_kernel(const Tin* __restri
         }
         equilibria_flat<LAT>(U, gamma - 1.0, c, e);
 #pragma unroll
-        for (int n = 0; n < Q * K; ++n) fs[n * N + i] = (Ts)e[n];
+        for (int n = 0; n < Q * K; ++n) fs[n * P + i] = (Ts)e[n];
     }
 }
 
 template <typename Ts, typename To, int LAT>
-__global__ void __launch_bounds__(kThreads) moments_kernel(const Ts* __restrict__ fs, To* __restrict__ U, int64_t N)
+__global__ void __launch_bounds__(kThreads) moments_kernel(const Ts* __restrict__ fs, To* __restrict__ U, int64_t N,
+                                                          int64_t P)
 {
     constexpr int Q = Dims<LAT>::Q, K = Dims<LAT>::K;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            double s = (double)fs[(0 * K + k) * N + i];
+            double s = (double)fs[(0 * K + k) * P + i];
 #pragma unroll
-            for (int q = 1; q < Q; ++q) s += (double)fs[(q * K + k) * N + i];
+            for (int q = 1; q < Q; ++q) s += (double)fs[(q * K + k) * P + i];
             U[k * N + i] = (To)s;
         }
     }
@@ -181,8 +183,9 @@ __device__ __forceinline__ DiagAcc diag_shfl_down(const DiagAcc& a, int off)
 // The checks run in the storage precision R (FP64 arithmetic is slow on this
 // GPU and FP32 states gain nothing from it); the totals accumulate in FP64.
 template <typename Ts, int LAT>
-__global__ void __launch_bounds__(kThreads) diag_partial_kernel(const Ts* __restrict__ fs, int64_t N, double gamma,
-                                                                double lambda, double* __restrict__ partials)
+__global__ void __launch_bounds__(kThreads) diag_partial_kernel(const Ts* __restrict__ fs, int64_t N, int64_t P,
+                                                                double gamma, double lambda,
+                                                                double* __restrict__ partials)
 {
     constexpr int Q = Dims<LAT>::Q, K = Dims<LAT>::K;
     using R = Ts;
@@ -199,9 +202,9 @@ __global__ void __launch_bounds__(kThreads) diag_partial_kernel(const Ts* __rest
         bool finite = true;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            R s = fs[(0 * K + k) * N + i];
+            R s = fs[(0 * K + k) * P + i];
 #pragma unroll
-            for (int q = 1; q < Q; ++q) s += fs[(q * K + k) * N + i];
+            for (int q = 1; q < Q; ++q) s += fs[(q * K + k) * P + i];
             U[k] = s;
             acc.tot[k] += (double)s;
             finite = finite && isfinite(s);
@@ -570,71 +573,72 @@ cudaError_t launch_ghost(int lattice, int storage_f64, const GhostSpec& g, doubl
 
 template <int LAT>
 static void set_state_dispatch(int storage_f64, const void* W, int w_dtype, int kind, void* fs, int64_t N,
-                               double gamma, double c, cudaStream_t s)
+                               int64_t P, double gamma, double c, cudaStream_t s)
 {
     const int g = grid_for(N);
     if (storage_f64) {
-        if (w_dtype == 0) set_state_kernel<double, double, LAT><<<g, kThreads, 0, s>>>((const double*)W, (double*)fs, N, kind, gamma, c);
-        else set_state_kernel<float, double, LAT><<<g, kThreads, 0, s>>>((const float*)W, (double*)fs, N, kind, gamma, c);
+        if (w_dtype == 0) set_state_kernel<double, double, LAT><<<g, kThreads, 0, s>>>((const double*)W, (double*)fs, N, P, kind, gamma, c);
+        else set_state_kernel<float, double, LAT><<<g, kThreads, 0, s>>>((const float*)W, (double*)fs, N, P, kind, gamma, c);
     } else {
-        if (w_dtype == 0) set_state_kernel<double, float, LAT><<<g, kThreads, 0, s>>>((const double*)W, (float*)fs, N, kind, gamma, c);
-        else set_state_kernel<float, float, LAT><<<g, kThreads, 0, s>>>((const float*)W, (float*)fs, N, kind, gamma, c);
+        if (w_dtype == 0) set_state_kernel<double, float, LAT><<<g, kThreads, 0, s>>>((const double*)W, (float*)fs, N, P, kind, gamma, c);
+        else set_state_kernel<float, float, LAT><<<g, kThreads, 0, s>>>((const float*)W, (float*)fs, N, P, kind, gamma, c);
     }
 }
 
 cudaError_t launch_set_state(int lattice, int storage_f64, const void* W, int w_dtype, int kind, void* fs,
-                             int64_t N, double gamma, double c, cudaStream_t s)
+                             int64_t N, int64_t plane, double gamma, double c, cudaStream_t s)
 {
-    if (lattice == LAT_D2Q4S) set_state_dispatch<LAT_D2Q4S>(storage_f64, W, w_dtype, kind, fs, N, gamma, c, s);
-    else if (lattice == LAT_D2Q4) set_state_dispatch<LAT_D2Q4>(storage_f64, W, w_dtype, kind, fs, N, gamma, c, s);
-    else if (lattice == LAT_D1Q3) set_state_dispatch<LAT_D1Q3>(storage_f64, W, w_dtype, kind, fs, N, gamma, c, s);
-    else set_state_dispatch<LAT_D1Q2>(storage_f64, W, w_dtype, kind, fs, N, gamma, c, s);
+    if (lattice == LAT_D2Q4S) set_state_dispatch<LAT_D2Q4S>(storage_f64, W, w_dtype, kind, fs, N, plane, gamma, c, s);
+    else if (lattice == LAT_D2Q4) set_state_dispatch<LAT_D2Q4>(storage_f64, W, w_dtype, kind, fs, N, plane, gamma, c, s);
+    else if (lattice == LAT_D1Q3) set_state_dispatch<LAT_D1Q3>(storage_f64, W, w_dtype, kind, fs, N, plane, gamma, c, s);
+    else set_state_dispatch<LAT_D1Q2>(storage_f64, W, w_dtype, kind, fs, N, plane, gamma, c, s);
     return cudaGetLastError();
 }
 
 template <int LAT>
-static void moments_dispatch(int storage_f64, const void* fs, void* U, int out_dtype, int64_t N, cudaStream_t s)
+static void moments_dispatch(int storage_f64, const void* fs, void* U, int out_dtype, int64_t N, int64_t P,
+                             cudaStream_t s)
 {
     const int g = grid_for(N);
     if (storage_f64) {
-        if (out_dtype == 0) moments_kernel<double, double, LAT><<<g, kThreads, 0, s>>>((const double*)fs, (double*)U, N);
-        else moments_kernel<double, float, LAT><<<g, kThreads, 0, s>>>((const double*)fs, (float*)U, N);
+        if (out_dtype == 0) moments_kernel<double, double, LAT><<<g, kThreads, 0, s>>>((const double*)fs, (double*)U, N, P);
+        else moments_kernel<double, float, LAT><<<g, kThreads, 0, s>>>((const double*)fs, (float*)U, N, P);
     } else {
-        if (out_dtype == 0) moments_kernel<float, double, LAT><<<g, kThreads, 0, s>>>((const float*)fs, (double*)U, N);
-        else moments_kernel<float, float, LAT><<<g, kThreads, 0, s>>>((const float*)fs, (float*)U, N);
+        if (out_dtype == 0) moments_kernel<float, double, LAT><<<g, kThreads, 0, s>>>((const float*)fs, (double*)U, N, P);
+        else moments_kernel<float, float, LAT><<<g, kThreads, 0, s>>>((const float*)fs, (float*)U, N, P);
     }
 }
 
 cudaError_t launch_moments(int lattice, int storage_f64, const void* fs, void* U, int out_dtype, int64_t N,
-                           cudaStream_t s)
+                           int64_t plane, cudaStream_t s)
 {
-    if (lattice == LAT_U2D) moments_dispatch<LAT_U2D>(0, fs, U, out_dtype, N, s);
-    else if (lattice == LAT_D2Q4S) moments_dispatch<LAT_D2Q4S>(storage_f64, fs, U, out_dtype, N, s);
-    else if (lattice == LAT_D2Q4) moments_dispatch<LAT_D2Q4>(storage_f64, fs, U, out_dtype, N, s);
-    else if (lattice == LAT_D1Q3) moments_dispatch<LAT_D1Q3>(storage_f64, fs, U, out_dtype, N, s);
-    else moments_dispatch<LAT_D1Q2>(storage_f64, fs, U, out_dtype, N, s);
+    if (lattice == LAT_U2D) moments_dispatch<LAT_U2D>(0, fs, U, out_dtype, N, plane, s);
+    else if (lattice == LAT_D2Q4S) moments_dispatch<LAT_D2Q4S>(storage_f64, fs, U, out_dtype, N, plane, s);
+    else if (lattice == LAT_D2Q4) moments_dispatch<LAT_D2Q4>(storage_f64, fs, U, out_dtype, N, plane, s);
+    else if (lattice == LAT_D1Q3) moments_dispatch<LAT_D1Q3>(storage_f64, fs, U, out_dtype, N, plane, s);
+    else moments_dispatch<LAT_D1Q2>(storage_f64, fs, U, out_dtype, N, plane, s);
     return cudaGetLastError();
 }
 
 int diag_blocks() { return kDiagBlocks; }
 
-cudaError_t launch_diag(int lattice, int storage_f64, const void* fs, int64_t N, double gamma, double lambda,
-                        double cell_volume, double* partials, double* out, cudaStream_t s)
+cudaError_t launch_diag(int lattice, int storage_f64, const void* fs, int64_t N, int64_t plane, double gamma,
+                        double lambda, double cell_volume, double* partials, double* out, cudaStream_t s)
 {
     if (lattice == LAT_U2D) {
-        diag_partial_kernel<float, LAT_U2D><<<kDiagBlocks, kThreads, 0, s>>>((const float*)fs, N, gamma, lambda, partials);
+        diag_partial_kernel<float, LAT_U2D><<<kDiagBlocks, kThreads, 0, s>>>((const float*)fs, N, plane, gamma, lambda, partials);
     } else if (lattice == LAT_D1Q3) {
-        if (storage_f64) diag_partial_kernel<double, LAT_D1Q3><<<kDiagBlocks, kThreads, 0, s>>>((const double*)fs, N, gamma, lambda, partials);
-        else diag_partial_kernel<float, LAT_D1Q3><<<kDiagBlocks, kThreads, 0, s>>>((const float*)fs, N, gamma, lambda, partials);
+        if (storage_f64) diag_partial_kernel<double, LAT_D1Q3><<<kDiagBlocks, kThreads, 0, s>>>((const double*)fs, N, plane, gamma, lambda, partials);
+        else diag_partial_kernel<float, LAT_D1Q3><<<kDiagBlocks, kThreads, 0, s>>>((const float*)fs, N, plane, gamma, lambda, partials);
     } else if (lattice == LAT_D2Q4S) {
-        if (storage_f64) diag_partial_kernel<double, LAT_D2Q4S><<<kDiagBlocks, kThreads, 0, s>>>((const double*)fs, N, gamma, lambda, partials);
-        else diag_partial_kernel<float, LAT_D2Q4S><<<kDiagBlocks, kThreads, 0, s>>>((const float*)fs, N, gamma, lambda, partials);
+        if (storage_f64) diag_partial_kernel<double, LAT_D2Q4S><<<kDiagBlocks, kThreads, 0, s>>>((const double*)fs, N, plane, gamma, lambda, partials);
+        else diag_partial_kernel<float, LAT_D2Q4S><<<kDiagBlocks, kThreads, 0, s>>>((const float*)fs, N, plane, gamma, lambda, partials);
     } else if (lattice == LAT_D2Q4) {
-        if (storage_f64) diag_partial_kernel<double, LAT_D2Q4><<<kDiagBlocks, kThreads, 0, s>>>((const double*)fs, N, gamma, lambda, partials);
-        else diag_partial_kernel<float, LAT_D2Q4><<<kDiagBlocks, kThreads, 0, s>>>((const float*)fs, N, gamma, lambda, partials);
+        if (storage_f64) diag_partial_kernel<double, LAT_D2Q4><<<kDiagBlocks, kThreads, 0, s>>>((const double*)fs, N, plane, gamma, lambda, partials);
+        else diag_partial_kernel<float, LAT_D2Q4><<<kDiagBlocks, kThreads, 0, s>>>((const float*)fs, N, plane, gamma, lambda, partials);
     } else {
-        if (storage_f64) diag_partial_kernel<double, LAT_D1Q2><<<kDiagBlocks, kThreads, 0, s>>>((const double*)fs, N, gamma, lambda, partials);
-        else diag_partial_kernel<float, LAT_D1Q2><<<kDiagBlocks, kThreads, 0, s>>>((const float*)fs, N, gamma, lambda, partials);
+        if (storage_f64) diag_partial_kernel<double, LAT_D1Q2><<<kDiagBlocks, kThreads, 0, s>>>((const double*)fs, N, plane, gamma, lambda, partials);
+        else diag_partial_kernel<float, LAT_D1Q2><<<kDiagBlocks, kThreads, 0, s>>>((const float*)fs, N, plane, gamma, lambda, partials);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -75,20 +75,22 @@ cudaError_t launch_adapt_init_bound_f64(const void* fs, int64_t N, double gamma,
 cudaError_t launch_adapt_init_bound_f32(const void* fs, int64_t N, double gamma, void* st, cudaStream_t s);
 
 
-// f = f^eq(U(W)) for every cell; W is [K][N] of w_dtype (0 f64, 1 f32), conserved or primitive.
+// f = f^eq(U(W)) for every cell; W is [K][N] of w_dtype (0 f64, 1 f32), conserved or primitive;
+// fs has planes of `plane` >= N elements (cell c of plane n at fs[n * plane + c]).
 cudaError_t launch_set_state(int lattice, int storage_f64, const void* W, int w_dtype, int kind, void* fs,
-                             int64_t N, double gamma, double c, cudaStream_t s);
+                             int64_t N, int64_t plane, double gamma, double c, cudaStream_t s);
 
-// U[k][c] = sum_q fs[q][k][c] in FP64, written as out_dtype (0 f64, 1 f32).
+// U[k][c] = sum_q fs[q][k][c] in FP64, written as out_dtype (0 f64, 1 f32), for the N cells
+// c of planes `plane` elements apart (U is [K][N]).
 cudaError_t launch_moments(int lattice, int storage_f64, const void* fs, void* U, int out_dtype, int64_t N,
-                           cudaStream_t s);
+                           int64_t plane, cudaStream_t s);
 
 // Fixed-order FP64 diagnostics: nblocks partial records of DIAG_W doubles, then
 // one finalising pass into out[DIAG_W] = totals[4], min_rho, min_p,
 // max_lambda_local, n_nonphysical, n_subchar, (unused).
 int diag_blocks();
-cudaError_t launch_diag(int lattice, int storage_f64, const void* fs, int64_t N, double gamma, double lambda,
-                        double cell_volume, double* partials, double* out, cudaStream_t s);
+cudaError_t launch_diag(int lattice, int storage_f64, const void* fs, int64_t N, int64_t plane, double gamma,
+                        double lambda, double cell_volume, double* partials, double* out, cudaStream_t s);
 
 // Periodic device checks: reset the status record, fold one diagnostics result into it.
 cudaError_t launch_status_reset(double* status, cudaStream_t s);
@@ -163,8 +165,8 @@ struct F16StepArgs {
 cudaError_t launch_step_f16neq(const F16StepArgs& a, cudaStream_t s);
 // Moments-only form (omega = 1): a state buffer is U [4][N] FP32.
 cudaError_t launch_step_f32u(const F16StepArgs& a, cudaStream_t s);
-cudaError_t launch_set_state_f32u(const void* W, int w_dtype, int kind, void* fs, int64_t N, double gamma,
-                                  cudaStream_t s);
+cudaError_t launch_set_state_f32u(const void* W, int w_dtype, int kind, void* fs, int64_t N, int64_t plane,
+                                  double gamma, cudaStream_t s);
 // U = U(W) in FP32, g = 0, then the per-field scales from max |U_k| (absmax_bits: 4 words of scratch).
 cudaError_t launch_set_state_f16neq(const void* W, int w_dtype, int kind, void* fs, int64_t N, double gamma,
                                     unsigned int* absmax_bits, cudaStream_t s);

@@ -30,13 +30,32 @@ thread_local char g_err[512] = "";
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
+// f_bytes: the raw state of the context's own cells (what lbrs_get_distributions moves);
+// store_bytes: one stored buffer, which also holds the ghost rows of cut sides;
+// each of the two buffers takes a slot that can also stage K FP64 fields of host input.
 struct Layout {
-    size_t f_bytes, f0, f1, ghost, partials, diag_out, scale, status, wait_flag, adapt, total;
+    size_t f_bytes, store_bytes, slot, f0, f1, ghost, partials, diag_out, scale, status, wait_flag, adapt, total;
 };
 
 bool two_d(int lat) { return lat == LBRS_D2Q4 || lat == LBRS_D2Q4S; }
 int lattice_q(int lat) { return two_d(lat) ? 4 : (lat == LBRS_D1Q3 ? 3 : 2); }
 int lattice_k(int lat) { return lat == LBRS_D2Q4 ? 4 : (lat == LBRS_D2Q4S ? 1 : 3); }
+
+constexpr int kDefaultHaloRows = 2;   // the two-step kernel's depth
+constexpr int kMaxHaloRows = 64;
+
+// Ghost rows stored beyond y side s (2 = y-lo, 3 = y-hi): the side's halo depth if it is a cut.
+int64_t ghost_rows(const lbrs_config* c, int s)
+{
+    if (c->lattice != LBRS_D2Q4 || s < 2 || c->bc[s].kind != LBRS_BC_CUT) return 0;
+    return c->bc[s].halo_rows ? c->bc[s].halo_rows : kDefaultHaloRows;
+}
+int64_t stored_rows(const lbrs_config* c) { return c->ny + ghost_rows(c, 2) + ghost_rows(c, 3); }
+// Planes of one stored buffer in the distribution forms and the moments-only form.
+int state_planes(const lbrs_config* c)
+{
+    return c->precision == LBRS_F32U ? 4 : lattice_q(c->lattice) * lattice_k(c->lattice);
+}
 // kernel lattice code of a public lattice
 int lat_code(int lat)
 {
@@ -48,14 +67,21 @@ Layout layout_of(const lbrs_config* c)
     Layout L;
     const size_t elem = c->precision == LBRS_F64 ? 8 : 4;
     const size_t N = (size_t)c->nx * (size_t)c->ny;
-    L.f_bytes = c->precision == LBRS_F16NEQ ? N * (4 * 4 + 12 * 2) + 4 * sizeof(float)
-              : c->precision == LBRS_F32U ? N * 4 * sizeof(float)
-                                          : N * (size_t)(lattice_q(c->lattice) * lattice_k(c->lattice)) * elem;
+    const size_t Ns = (size_t)c->nx * (size_t)stored_rows(c);
+    if (c->precision == LBRS_F16NEQ) {
+        L.f_bytes = L.store_bytes = N * (4 * 4 + 12 * 2) + 4 * sizeof(float);
+    } else {
+        L.f_bytes = N * (size_t)state_planes(c) * elem;
+        L.store_bytes = Ns * (size_t)state_planes(c) * elem;
+    }
+    // host input and output are staged through the idle buffer: K FP64 fields of the own cells
+    const size_t stage = N * (size_t)lattice_k(c->lattice) * sizeof(double);
+    L.slot = align_up(L.store_bytes > stage ? L.store_bytes : stage);
     size_t off = 0;
     L.f0 = off;
-    off += align_up(L.f_bytes);
+    off += L.slot;
     L.f1 = off;
-    off += align_up(L.f_bytes);
+    off += L.slot;
     L.ghost = off;
     off += align_up(4 * GHOST_STRIDE * elem);
     L.partials = off;
@@ -80,7 +106,13 @@ struct lbrs_ctx {
     lbrs_config cfg;
     Layout L;
     int lattice, f64, f16, f32u, Q, K;
-    int64_t N;
+    int P;                   // planes of a stored buffer: Q * K, or 4 in the moments-only form
+    int64_t N;               // stored cells nx * ny_store: the plane stride of the state buffers
+    int64_t N_own;           // the context's own cells nx * ny
+    int64_t ny_store;        // stored rows: ny plus the ghost rows of cut y sides
+    int64_t row0;            // stored row of own row 0 (the ghost rows below it)
+    int64_t halo[2];         // ghost rows below (y-lo) and above (y-hi); 0 where the side is not a cut
+    int64_t halo_left[2];    // steps the last import of each cut side still covers
     char* ws;
     char* f[2];
     int cur;                 // index of the buffer holding the current state
@@ -148,7 +180,8 @@ lbrs_status validate(const lbrs_config* c)
     if (c->nx < 1 || c->ny < 1) return fail(nullptr, LBRS_EINVAL, "grid must have nx, ny >= 1");
     if (c->nx > (1LL << 30)) return fail(nullptr, LBRS_EINVAL, "nx too large (max 2^30)");
     if (!two_d(c->lattice) && c->ny != 1) return fail(nullptr, LBRS_EINVAL, "1-D lattices (D1Q2, D1Q3) need ny == 1");
-    if (two_d(c->lattice) && c->ny > 2LL * 65535) return fail(nullptr, LBRS_EINVAL, "ny too large (max 131070)");
+    if (two_d(c->lattice) && stored_rows(c) > 2LL * 65535)
+        return fail(nullptr, LBRS_EINVAL, "ny too large (max 131070 rows including the ghost rows of cuts)");
     if (!(c->gamma > 1.0) || !isfinite(c->gamma)) return fail(nullptr, LBRS_EINVAL, "gamma must be > 1");
     if (!finite_pos(c->lambda)) return fail(nullptr, LBRS_EINVAL, "lambda must be positive");
     if (!(c->omega > 0.0 && c->omega < 2.0)) return fail(nullptr, LBRS_EINVAL, "omega must lie in (0, 2)");
@@ -157,8 +190,20 @@ lbrs_status validate(const lbrs_config* c)
     const int sides = two_d(c->lattice) ? 4 : 2;
     for (int s = 0; s < sides; ++s) {
         const int kind = c->bc[s].kind;
-        if (kind < LBRS_BC_PERIODIC || kind > LBRS_BC_WALL)
+        if (kind < LBRS_BC_PERIODIC || kind > LBRS_BC_CUT)
             return fail(nullptr, LBRS_EINVAL, "side %d: unknown boundary kind %d", s, kind);
+        if (kind == LBRS_BC_CUT) {
+            if (c->lattice != LBRS_D2Q4 || s < 2)
+                return fail(nullptr, LBRS_EINVAL, "side %d: cuts are defined on the y sides of D2Q4 only", s);
+            if (c->precision == LBRS_F16NEQ)
+                return fail(nullptr, LBRS_EINVAL, "side %d: cuts cover the F64, F32 and F32U forms", s);
+            const int h = c->bc[s].halo_rows;
+            if (h < 0 || h > kMaxHaloRows)
+                return fail(nullptr, LBRS_EINVAL, "side %d: halo_rows must lie in [0, %d]", s, kMaxHaloRows);
+            if (c->ny < ghost_rows(c, s))
+                return fail(nullptr, LBRS_EINVAL, "side %d: a cut needs ny >= its halo rows", s);
+            continue;
+        }
         if (kind == LBRS_BC_WALL && (c->lattice != LBRS_D2Q4 || s < 2))
             return fail(nullptr, LBRS_EINVAL, "side %d: walls are defined on the y sides of D2Q4 only", s);
         if (kind == LBRS_BC_PERIODIC && c->bc[s ^ 1].kind != LBRS_BC_PERIODIC)
@@ -182,6 +227,16 @@ lbrs_status validate(const lbrs_config* c)
     return LBRS_OK;
 }
 
+// Boundary kind of side s as the kernels see it.  A cut side's stored grid ends in
+// its ghost rows, which the kernels close like a transmissive side: the rows next to
+// that edge go wrong one row per step, and within the halo depth they stay ghost rows
+// (the own rows never read them), until the next import replaces them.
+int kernel_bc(const lbrs_ctx* ctx, int s)
+{
+    const int kind = ctx->cfg.bc[s].kind;
+    return kind == LBRS_BC_CUT ? (int)LBRS_BC_TRANSMISSIVE : kind;
+}
+
 template <typename T>
 StepArgs<T> step_args(const lbrs_ctx* ctx, int from)
 {
@@ -191,8 +246,8 @@ StepArgs<T> step_args(const lbrs_ctx* ctx, int from)
     a.ghost = (const T*)(ctx->ws + ctx->L.ghost);
     a.N = ctx->N;
     a.nx = (int)ctx->cfg.nx;
-    a.ny = (int)ctx->cfg.ny;
-    for (int s = 0; s < 4; ++s) a.bc[s] = ctx->cfg.bc[s].kind;
+    a.ny = (int)ctx->ny_store;
+    for (int s = 0; s < 4; ++s) a.bc[s] = kernel_bc(ctx, s);
     a.om = (T)ctx->cfg.omega;
     a.om1 = (T)(1.0 - ctx->cfg.omega);
     a.c = (T)ctx->c;
@@ -213,8 +268,8 @@ cudaError_t launch_one_step(lbrs_ctx* ctx, int from, cudaStream_t s)
         a.ghost = (const float*)(ctx->ws + ctx->L.ghost);
         a.N = ctx->N;
         a.nx = (int)ctx->cfg.nx;
-        a.ny = (int)ctx->cfg.ny;
-        for (int k = 0; k < 4; ++k) a.bc[k] = ctx->cfg.bc[k].kind;
+        a.ny = (int)ctx->ny_store;
+        for (int k = 0; k < 4; ++k) a.bc[k] = kernel_bc(ctx, k);
         a.om = (float)ctx->cfg.omega;
         a.om1 = (float)(1.0 - ctx->cfg.omega);
         a.c = (float)ctx->c;
@@ -281,9 +336,30 @@ lbrs_status ensure_graph(lbrs_ctx* ctx, int from)
     return LBRS_OK;
 }
 
-size_t field_bytes(const lbrs_ctx* ctx, int dtype) { return (size_t)ctx->K * (size_t)ctx->N * (dtype == LBRS_F64 ? 8 : 4); }
+size_t field_bytes(const lbrs_ctx* ctx, int dtype)
+{
+    return (size_t)ctx->K * (size_t)ctx->N_own * (dtype == LBRS_F64 ? 8 : 4);
+}
 
 size_t elem_bytes(const lbrs_ctx* ctx) { return ctx->f64 ? 8 : 4; }
+
+// Cell 0 of the own rows in plane 0 of a stored buffer (the planes are ctx->N cells apart).
+char* own_ptr(const lbrs_ctx* ctx, char* buf) { return buf + (size_t)ctx->row0 * ctx->cfg.nx * elem_bytes(ctx); }
+
+// The raw state of the own cells between a stored buffer and contiguous planes elsewhere.
+cudaError_t copy_own_out(const lbrs_ctx* ctx, char* buf, void* dst, cudaMemcpyKind kind)
+{
+    if (ctx->N == ctx->N_own) return cudaMemcpyAsync(dst, buf, ctx->L.f_bytes, kind, ctx->stream);
+    const size_t e = elem_bytes(ctx), row = (size_t)ctx->N_own * e;
+    return cudaMemcpy2DAsync(dst, row, own_ptr(ctx, buf), (size_t)ctx->N * e, row, (size_t)ctx->P, kind, ctx->stream);
+}
+
+cudaError_t copy_own_in(const lbrs_ctx* ctx, char* buf, const void* src, cudaMemcpyKind kind)
+{
+    if (ctx->N == ctx->N_own) return cudaMemcpyAsync(buf, src, ctx->L.f_bytes, kind, ctx->stream);
+    const size_t e = elem_bytes(ctx), row = (size_t)ctx->N_own * e;
+    return cudaMemcpy2DAsync(own_ptr(ctx, buf), (size_t)ctx->N * e, src, row, row, (size_t)ctx->P, kind, ctx->stream);
+}
 
 int readout_lattice(const lbrs_ctx* ctx);
 
@@ -294,17 +370,19 @@ cudaError_t periodic_check(lbrs_ctx* ctx)
     const double vol = two_d(ctx->lattice) ? ctx->cfg.dx * ctx->cfg.dx : ctx->cfg.dx;
     double* partials = (double*)(ctx->ws + ctx->L.partials);
     double* dout = (double*)(ctx->ws + ctx->L.diag_out);
-    cudaError_t e = launch_diag(readout_lattice(ctx), ctx->f64, ctx->f[ctx->cur], ctx->N, ctx->cfg.gamma,
-                                ctx->cfg.lambda, vol, partials, dout, ctx->stream);
+    cudaError_t e = launch_diag(readout_lattice(ctx), ctx->f64, own_ptr(ctx, ctx->f[ctx->cur]), ctx->N_own, ctx->N,
+                                ctx->cfg.gamma, ctx->cfg.lambda, vol, partials, dout, ctx->stream);
     if (e != cudaSuccess) return e;
     ctx->launches += 3;
     return launch_status_update(dout, (double*)(ctx->ws + ctx->L.status), ctx->step, ctx->stream);
 }
 
-// A new state clears the record of the periodic checks and the wait flag, and ends an
-// adaptive-lambda run (the ghosts return to the configured lambda).
+// A new state clears the record of the periodic checks and the wait flag, ends an
+// adaptive-lambda run (the ghosts return to the configured lambda) and leaves the
+// ghost rows of cut sides stale until their next import.
 lbrs_status reset_status(lbrs_ctx* ctx)
 {
+    ctx->halo_left[0] = ctx->halo_left[1] = 0;
     if (ctx->adapt_used) {
         LBRS_CUDA(ctx, launch_ghost(lat_code(ctx->lattice), ctx->f64, ctx->gspec, ctx->cfg.gamma, ctx->c,
                                     ctx->ws + ctx->L.ghost, ctx->stream));
@@ -567,7 +645,13 @@ lbrs_status lbrs_create(const lbrs_config* cfg, void* d_workspace, size_t bytes,
     ctx->f32u = cfg->precision == LBRS_F32U;
     ctx->Q = lattice_q(cfg->lattice);
     ctx->K = lattice_k(cfg->lattice);
-    ctx->N = cfg->nx * cfg->ny;
+    ctx->P = state_planes(cfg);
+    ctx->halo[0] = ghost_rows(cfg, 2);
+    ctx->halo[1] = ghost_rows(cfg, 3);
+    ctx->row0 = ctx->halo[0];
+    ctx->ny_store = stored_rows(cfg);
+    ctx->N_own = cfg->nx * cfg->ny;
+    ctx->N = cfg->nx * ctx->ny_store;
     ctx->ws = (char*)d_workspace;
     ctx->f[0] = ctx->ws + L.f0;
     ctx->f[1] = ctx->ws + L.f1;
@@ -597,7 +681,7 @@ lbrs_status lbrs_create(const lbrs_config* cfg, void* d_workspace, size_t bytes,
         return s;
     }
     if (fused2(ctx))
-        for (int b = 0; b < 2; ++b) encode_f32_tile_map(&ctx->tmap[b], (const float*)ctx->f[b], cfg->nx, cfg->ny);
+        for (int b = 0; b < 2; ++b) encode_f32_tile_map(&ctx->tmap[b], (const float*)ctx->f[b], cfg->nx, ctx->ny_store);
     *out = ctx;
     return LBRS_OK;
 }
@@ -628,15 +712,15 @@ lbrs_status lbrs_set_state(lbrs_ctx* ctx, const void* W, int on_device, int dtyp
     }
     const int lat = lat_code(ctx->lattice);
     if (ctx->f32u) {
-        LBRS_CUDA(ctx, launch_set_state_f32u(src, dtype == LBRS_F32, kind, ctx->f[ctx->cur], ctx->N, ctx->cfg.gamma,
-                                             ctx->stream));
+        LBRS_CUDA(ctx, launch_set_state_f32u(src, dtype == LBRS_F32, kind, own_ptr(ctx, ctx->f[ctx->cur]), ctx->N_own,
+                                             ctx->N, ctx->cfg.gamma, ctx->stream));
     } else if (ctx->f16) {
         LBRS_CUDA(ctx, launch_set_state_f16neq(src, dtype == LBRS_F32, kind, ctx->f[ctx->cur], ctx->N, ctx->cfg.gamma,
                                                (unsigned int*)(ctx->ws + ctx->L.scale), ctx->stream));
         ctx->launches += 3;
     } else {
-        LBRS_CUDA(ctx, launch_set_state(lat, ctx->f64, src, dtype == LBRS_F32, kind, ctx->f[ctx->cur], ctx->N,
-                                        ctx->cfg.gamma, ctx->c, ctx->stream));
+        LBRS_CUDA(ctx, launch_set_state(lat, ctx->f64, src, dtype == LBRS_F32, kind, own_ptr(ctx, ctx->f[ctx->cur]),
+                                        ctx->N_own, ctx->N, ctx->cfg.gamma, ctx->c, ctx->stream));
     }
     ctx->launches += 1;
     lbrs_status rs = reset_status(ctx);
@@ -658,6 +742,13 @@ lbrs_status lbrs_step(lbrs_ctx* ctx, int64_t n)
     if (ctx->adapt_used)
         return fail(ctx, LBRS_ESTATE, "the distributions carry an adaptive lambda: continue with "
                                       "lbrs_step_adaptive or set a state");
+    for (int h = 0; h < 2; ++h)
+        if (ctx->halo[h] && n > ctx->halo_left[h])
+            return fail(ctx, LBRS_ESTATE, "%lld steps requested, but the ghost rows of the %s cut cover %lld more "
+                        "steps: import the neighbour's rows (lbrs_halo_import) first", (long long)n,
+                        h ? "y-hi" : "y-lo", (long long)ctx->halo_left[h]);
+    for (int h = 0; h < 2; ++h)
+        if (ctx->halo[h]) ctx->halo_left[h] -= n;
     const int64_t every = ctx->cfg.diag_every;
     if (every <= 0) return step_plain(ctx, n);
     // run to each multiple of diag_every, check there
@@ -754,8 +845,8 @@ lbrs_status lbrs_moments(lbrs_ctx* ctx, void* U_out, int on_device, int dtype)
     if (dtype != LBRS_F64 && dtype != LBRS_F32) return fail(ctx, LBRS_EINVAL, "dtype must be LBRS_F64 or LBRS_F32");
     if (!ctx->has_state) return fail(ctx, LBRS_ESTATE, "no state set");
     void* dst = on_device ? U_out : (void*)ctx->f[ctx->cur ^ 1];
-    LBRS_CUDA(ctx, launch_moments(readout_lattice(ctx), ctx->f64, ctx->f[ctx->cur], dst, dtype == LBRS_F32, ctx->N,
-                                  ctx->stream));
+    LBRS_CUDA(ctx, launch_moments(readout_lattice(ctx), ctx->f64, own_ptr(ctx, ctx->f[ctx->cur]), dst,
+                                  dtype == LBRS_F32, ctx->N_own, ctx->N, ctx->stream));
     ctx->launches += 1;
     if (!on_device) {
         LBRS_CUDA(ctx, cudaMemcpyAsync(U_out, dst, field_bytes(ctx, dtype), cudaMemcpyDeviceToHost, ctx->stream));
@@ -773,8 +864,8 @@ lbrs_status lbrs_diagnostics(lbrs_ctx* ctx, lbrs_diag* out)
     const double vol = two_d(ctx->lattice) ? ctx->cfg.dx * ctx->cfg.dx : ctx->cfg.dx;
     double* partials = (double*)(ctx->ws + ctx->L.partials);
     double* dout = (double*)(ctx->ws + ctx->L.diag_out);
-    LBRS_CUDA(ctx, launch_diag(lat, ctx->f64, ctx->f[ctx->cur], ctx->N, ctx->cfg.gamma, ctx->cfg.lambda, vol,
-                               partials, dout, ctx->stream));
+    LBRS_CUDA(ctx, launch_diag(lat, ctx->f64, own_ptr(ctx, ctx->f[ctx->cur]), ctx->N_own, ctx->N, ctx->cfg.gamma,
+                               ctx->cfg.lambda, vol, partials, dout, ctx->stream));
     ctx->launches += 2;
     double h[DIAG_W];
     LBRS_CUDA(ctx, cudaMemcpyAsync(h, dout, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
@@ -798,8 +889,7 @@ lbrs_status lbrs_get_distributions(lbrs_ctx* ctx, void* dst, int on_device)
     if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
     if (!dst) return fail(ctx, LBRS_EINVAL, "dst is NULL");
     if (!ctx->has_state) return fail(ctx, LBRS_ESTATE, "no state set");
-    LBRS_CUDA(ctx, cudaMemcpyAsync(dst, ctx->f[ctx->cur], ctx->L.f_bytes,
-                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+    LBRS_CUDA(ctx, copy_own_out(ctx, ctx->f[ctx->cur], dst, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
     if (!on_device) LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return LBRS_OK;
 }
@@ -810,6 +900,7 @@ lbrs_status lbrs_set_obstacles(lbrs_ctx* ctx, const uint8_t* d_solid)
     if (d_solid) {
         if (ctx->lattice != LBRS_D2Q4 || ctx->f16 || ctx->f32u)
             return fail(ctx, LBRS_EINVAL, "internal walls cover the F64 and F32 D2Q4 forms");
+        if (ctx->halo[0] || ctx->halo[1]) return fail(ctx, LBRS_EINVAL, "internal walls are not covered on cut grids");
         std::vector<uint8_t> m((size_t)ctx->N);
         LBRS_CUDA(ctx, cudaMemcpyAsync(m.data(), d_solid, m.size(), cudaMemcpyDeviceToHost, ctx->stream));
         LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -886,6 +977,8 @@ lbrs_status lbrs_step_adaptive(lbrs_ctx* ctx, int64_t n, double safety, double t
     if (n < 0) return fail(ctx, LBRS_EINVAL, "negative step count");
     if (ctx->lattice != LBRS_D2Q4 || ctx->f16 || ctx->f32u || ctx->solid)
         return fail(ctx, LBRS_EINVAL, "the adaptive lambda covers the F64 and F32 D2Q4 forms without internal walls");
+    if (ctx->halo[0] || ctx->halo[1])
+        return fail(ctx, LBRS_EINVAL, "the adaptive lambda is a global maximum: not covered on cut grids");
     if (!(safety >= 1.0) || !isfinite(safety)) return fail(ctx, LBRS_EINVAL, "safety must be >= 1");
     if (!(t_final >= 0.0) || !isfinite(t_final)) return fail(ctx, LBRS_EINVAL, "t_final must be >= 0");
     if (!ctx->has_state) return fail(ctx, LBRS_ESTATE, "no state set");
@@ -1005,13 +1098,11 @@ lbrs_status lbrs_checkpoint_save(lbrs_ctx* ctx, void* dst, int on_device)
     char* d = (char*)dst;
     if (on_device) {
         LBRS_CUDA(ctx, cudaMemcpyAsync(d, head, kCkptHeader, cudaMemcpyHostToDevice, ctx->stream));
-        LBRS_CUDA(ctx, cudaMemcpyAsync(d + kCkptHeader, ctx->f[ctx->cur], ctx->L.f_bytes, cudaMemcpyDeviceToDevice,
-                                       ctx->stream));
+        LBRS_CUDA(ctx, copy_own_out(ctx, ctx->f[ctx->cur], d + kCkptHeader, cudaMemcpyDeviceToDevice));
         LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));   // the header's host copy goes out of scope
     } else {
         memcpy(d, head, kCkptHeader);
-        LBRS_CUDA(ctx, cudaMemcpyAsync(d + kCkptHeader, ctx->f[ctx->cur], ctx->L.f_bytes, cudaMemcpyDeviceToHost,
-                                       ctx->stream));
+        LBRS_CUDA(ctx, copy_own_out(ctx, ctx->f[ctx->cur], d + kCkptHeader, cudaMemcpyDeviceToHost));
         LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     }
     return LBRS_OK;
@@ -1040,8 +1131,8 @@ lbrs_status lbrs_checkpoint_load(lbrs_ctx* ctx, const void* src, int on_device)
     }
     if (!same) return fail(ctx, LBRS_EINVAL, "checkpoint of another configuration (grid, lattice, precision, "
                                              "lambda, omega, gamma, dx or boundaries differ)");
-    LBRS_CUDA(ctx, cudaMemcpyAsync(ctx->f[ctx->cur], s + kCkptHeader, ctx->L.f_bytes,
-                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+    LBRS_CUDA(ctx, copy_own_in(ctx, ctx->f[ctx->cur], s + kCkptHeader,
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
     if (!on_device) LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     ctx->has_state = true;
     ctx->step = h.step;
@@ -1055,13 +1146,68 @@ lbrs_status lbrs_set_distributions(lbrs_ctx* ctx, const void* src, int on_device
     if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
     if (!src) return fail(ctx, LBRS_EINVAL, "src is NULL");
     if (step < 0) return fail(ctx, LBRS_EINVAL, "negative step");
-    LBRS_CUDA(ctx, cudaMemcpyAsync(ctx->f[ctx->cur], src, ctx->L.f_bytes,
-                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+    LBRS_CUDA(ctx, copy_own_in(ctx, ctx->f[ctx->cur], src, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
     lbrs_status rs = reset_status(ctx);
     if (rs != LBRS_OK) return rs;
     if (!on_device) LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     ctx->has_state = true;
     ctx->step = step;
+    return LBRS_OK;
+}
+
+// ---------------------------------------------------------------- cuts (y-slab decomposition)
+
+namespace {
+// First stored row of the H rows an export reads (the own rows next to the side) or an
+// import writes (the ghost rows beyond it); side 2 is y-lo, 3 is y-hi.
+int64_t halo_first_row(const lbrs_ctx* ctx, int side, bool import)
+{
+    if (side == 2) return import ? 0 : ctx->row0;
+    return import ? ctx->row0 + ctx->cfg.ny : ctx->row0 + ctx->cfg.ny - ctx->halo[1];
+}
+
+lbrs_status halo_args(lbrs_ctx* ctx, int side, const void* buf)
+{
+    if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
+    if (!buf) return fail(ctx, LBRS_EINVAL, "halo buffer is NULL");
+    if (side != 2 && side != 3) return fail(ctx, LBRS_EINVAL, "side must be 2 (y-lo) or 3 (y-hi), got %d", side);
+    if (!ctx->halo[side - 2]) return fail(ctx, LBRS_EINVAL, "side %d is not a cut", side);
+    if (!ctx->has_state) return fail(ctx, LBRS_ESTATE, "no state set");
+    return LBRS_OK;
+}
+}  // namespace
+
+lbrs_status lbrs_halo_size(const lbrs_ctx* ctx, int side, int64_t* rows, size_t* bytes)
+{
+    if (!ctx || !rows || !bytes) return fail(nullptr, LBRS_EINVAL, "NULL argument");
+    if (side != 2 && side != 3) return fail(nullptr, LBRS_EINVAL, "side must be 2 (y-lo) or 3 (y-hi)");
+    *rows = ctx->halo[side - 2];
+    *bytes = (size_t)ctx->P * (size_t)*rows * (size_t)ctx->cfg.nx * elem_bytes(ctx);
+    return LBRS_OK;
+}
+
+lbrs_status lbrs_halo_export(lbrs_ctx* ctx, int side, void* dst, int on_device)
+{
+    lbrs_status st = halo_args(ctx, side, dst);
+    if (st != LBRS_OK) return st;
+    const size_t e = elem_bytes(ctx), w = (size_t)ctx->halo[side - 2] * ctx->cfg.nx * e;
+    const char* src = ctx->f[ctx->cur] + (size_t)halo_first_row(ctx, side, false) * ctx->cfg.nx * e;
+    LBRS_CUDA(ctx, cudaMemcpy2DAsync(dst, w, src, (size_t)ctx->N * e, w, (size_t)ctx->P,
+                                     on_device ? cudaMemcpyDefault : cudaMemcpyDeviceToHost, ctx->stream));
+    if (!on_device) LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return LBRS_OK;
+}
+
+lbrs_status lbrs_halo_import(lbrs_ctx* ctx, int side, const void* src, int on_device)
+{
+    lbrs_status st = halo_args(ctx, side, src);
+    if (st != LBRS_OK) return st;
+    const size_t e = elem_bytes(ctx), w = (size_t)ctx->halo[side - 2] * ctx->cfg.nx * e;
+    char* dst = ctx->f[ctx->cur] + (size_t)halo_first_row(ctx, side, true) * ctx->cfg.nx * e;
+    LBRS_CUDA(ctx, cudaMemcpy2DAsync(dst, (size_t)ctx->N * e, src, w, w, (size_t)ctx->P,
+                                     on_device ? cudaMemcpyDefault : cudaMemcpyHostToDevice, ctx->stream));
+    if (!on_device) LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->halo_left[side - 2] = ctx->halo[side - 2];
     return LBRS_OK;
 }
 
@@ -1086,6 +1232,7 @@ lbrs_status lbrs_step_record(lbrs_ctx* ctx, int64_t n, void* d_U_hist)
     if (n > 0 && !d_U_hist) return fail(ctx, LBRS_EINVAL, "d_U_hist is NULL");
     if (ctx->lattice != LBRS_D2Q4 || ctx->f16 || ctx->f32u)
         return fail(ctx, LBRS_EINVAL, "recording steps cover the F64 and F32 D2Q4 forms only");
+    if (ctx->halo[0] || ctx->halo[1]) return fail(ctx, LBRS_EINVAL, "recording steps are not covered on cut grids");
     if (!ctx->has_state) return fail(ctx, LBRS_ESTATE, "no state set");
     lbrs_status st = record_steps(ctx, n, (char*)d_U_hist);
     if (st != LBRS_OK) return st;
@@ -1246,7 +1393,7 @@ lbrs_status lbrs_backward_checkpointed(lbrs_ctx* ctx, void* d_adj_ws, const void
     }
     // dL/dU0 = J_E(U0)^T gbar^0 with U0 the moments of the first checkpoint
     const int lat = LAT_D2Q4;
-    LBRS_CUDA(ctx, launch_moments(lat, ctx->f64, ws + A.ckpt0, uhist, ctx->f64 ? 0 : 1, ctx->N, ctx->stream));
+    LBRS_CUDA(ctx, launch_moments(lat, ctx->f64, ws + A.ckpt0, uhist, ctx->f64 ? 0 : 1, ctx->N, ctx->N, ctx->stream));
     LBRS_CUDA(ctx, launch_vjp_eq_raw(ctx, uhist, g[gc], d_gradU0));
     ctx->launches += 2;
     // restore the final forward state

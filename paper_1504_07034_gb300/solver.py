@@ -30,6 +30,9 @@ def make_config(lattice: str, nx: int, ny: int, *, gamma: float, lam: float, ome
     cfg.gamma, cfg.lam, cfg.omega, cfg.dx = float(gamma), float(lam), float(omega), float(dx)
     for s, (kind, state) in enumerate(bc):
         cfg.bc[s].kind = abi.BC_KINDS[kind]
+        if kind == "cut":                        # state: the ghost rows stored beyond the cut (None: 2)
+            cfg.bc[s].halo_rows = int(state or 0)
+            continue
         if state is not None:
             for k, v in enumerate(state):
                 cfg.bc[s].prim[k] = float(v)
@@ -42,7 +45,8 @@ class Solver:
 
     lattice   "d1q2", "d1q3", "d2q4" or "d2q4s" (the scalar 2-D Burgers law; one field u; a
               Dirichlet side's state is the linear profile (value, slope) along it)
-    bc        per side (x-lo, x-hi[, y-lo, y-hi]): (kind, primitive_state_or_None)
+    bc        per side (x-lo, x-hi[, y-lo, y-hi]): (kind, primitive_state_or_None); a y side
+              ("cut", rows_or_None) makes the solver one y-slab of a larger grid (halo_export/import)
     precision "f64" (plain FP64 path), "f32" (FP32 distributions), "f16neq" (D2Q4: FP32
               moments plus FP16 non-equilibrium parts) or "f32u" (D2Q4 at omega = 1: FP32 moments only)
     stream    a torch.cuda.Stream (default: the current stream)
@@ -185,6 +189,33 @@ class Solver:
             raise ValueError("f must be a contiguous (Q, K, *grid) tensor of the storage dtype")
         self._check(self.lib.lbrs_set_distributions(self.ctx, ctypes.c_void_p(f.data_ptr()), 1 if f.is_cuda else 0,
                                                     int(step)))
+
+    # ------------------------------------------------------------------ y-slabs (cut sides)
+    def halo_size(self, side: int) -> tuple[int, int]:
+        """(ghost rows, bytes of one exchanged block) of y side 2 (y-lo) or 3 (y-hi)."""
+        rows, nbytes = ctypes.c_int64(), ctypes.c_size_t()
+        self._check(self.lib.lbrs_halo_size(self.ctx, int(side), ctypes.byref(rows), ctypes.byref(nbytes)))
+        return rows.value, nbytes.value
+
+    def halo_buffer(self, side: int, device=None) -> torch.Tensor:
+        """An empty (P, rows, nx) tensor of the storage dtype for one exchanged block."""
+        rows, _ = self.halo_size(side)
+        planes = 4 if self.precision == "f32u" else self.Q * self.K
+        return torch.empty((planes, rows, self.nx), dtype=self.storage_dtype,
+                           device=self.device if device is None else device)
+
+    def halo_export(self, side: int, out: torch.Tensor) -> torch.Tensor:
+        """The own rows next to cut `side`, every plane, into `out` (from halo_buffer)."""
+        self._check(self.lib.lbrs_halo_export(self.ctx, int(side), ctypes.c_void_p(out.data_ptr()),
+                                              1 if out.is_cuda else 0))
+        return out
+
+    def halo_import(self, side: int, block: torch.Tensor):
+        """The neighbour's exported block into the ghost rows beyond cut `side`."""
+        self._keep_halo = getattr(self, "_keep_halo", {})
+        self._keep_halo[side] = block                       # referenced until the next import of this side
+        self._check(self.lib.lbrs_halo_import(self.ctx, int(side), ctypes.c_void_p(block.data_ptr()),
+                                              1 if block.is_cuda else 0))
 
     def checkpoint(self, device: bool = True) -> torch.Tensor:
         """The state as a self-describing blob (uint8 tensor on the GPU, or in pinned host memory)."""
