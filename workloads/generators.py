@@ -95,6 +95,12 @@ class TubeBatch:
     def total_updates(self) -> int:
         return int((self.lengths * self.steps).sum())
 
+    def subset(self, idx) -> "TubeBatch":
+        """The tubes idx (in that order) as a batch of their own."""
+        idx = np.asarray(idx, dtype=np.int64)
+        return TubeBatch(self.lengths[idx], self.left[idx], self.right[idx], self.lam[idx], self.steps[idx],
+                         self.t_final, self.omega, self.gamma, self.lattice)
+
     def prim(self) -> np.ndarray:
         """Concatenated primitive fields, shape (3, sum N), tube b at offset sum_{c<b} N_c."""
         out = np.empty((3, self.total_cells))
