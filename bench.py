@@ -202,6 +202,144 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ profiling cases
+#
+# `python bench.py --profile CASE` runs one kernel family on a representative case, for an
+# external profiler (ncu -k ... -c ...): each case holds at most about 1.5 GB on the device and
+# launches its kernels a handful of times after a warm-up, and prints the wall time of its calls.
+
+def _prof_timed(fn):
+    import torch
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    fn()
+    torch.cuda.synchronize()
+    return time.perf_counter() - t
+
+
+def prof_step2d_f32():
+    import torch
+    from paper_1504_07034_gb300.solver import Solver
+    wl = workloads.quadrant_riemann(0, 1024, steps=10)
+    s = Solver.from_workload(wl, precision="f32")
+    s.set_state(torch.from_numpy(wl.prim).cuda())
+    return _prof_timed(lambda: [s.step(1) for _ in range(wl.steps)])
+
+
+def prof_step2d_f32_flushed():
+    """The bench's cache state: a 256 MiB write before every call; 3 warm-up calls of two steps,
+    6 timed calls of two steps (one two-step launch each), then 6 calls of one step."""
+    import torch
+    from paper_1504_07034_gb300.solver import Solver
+    wl = workloads.quadrant_riemann(0, 1024, steps=0)
+    s = Solver.from_workload(wl, precision="f32")
+    s.set_state(torch.from_numpy(wl.prim).cuda())
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+
+    def run():
+        for n in [2] * 9 + [1] * 6:
+            flush.fill_(1.0)
+            s.step(n)
+    return _prof_timed(run)
+
+
+def prof_step2d_f16neq():
+    import torch
+    from paper_1504_07034_gb300.solver import Solver
+    wl = workloads.oblique_shock_reflection(nx=2048, ny=512, steps=10, omega=1.5)
+    s = Solver.from_workload(wl, precision="f16neq")
+    s.set_state(torch.from_numpy(wl.prim).cuda())
+    return _prof_timed(lambda: [s.step(1) for _ in range(wl.steps)])
+
+
+def prof_step2d_f32u_flushed():
+    """The moments-only form in the bench's cache state: a 256 MiB write before every call of two steps
+    (3 warm-up calls, then 6)."""
+    import torch
+    from paper_1504_07034_gb300.solver import Solver
+    wl = workloads.quadrant_riemann(0, 1024, steps=0)
+    s = Solver.from_workload(wl, precision="f32u")
+    s.set_state(torch.from_numpy(wl.prim).cuda())
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+
+    def run():
+        for _ in range(9):
+            flush.fill_(1.0)
+            s.step(2)
+    return _prof_timed(run)
+
+
+def prof_obstacles():
+    """The forward-facing step on 3072 x 1024 in FP32, 10 steps in calls of two (the two-step
+    kernel with the obstacle mask)."""
+    import torch
+    from paper_1504_07034_gb300.solver import Solver
+    wl = workloads.forward_facing_step(nx=3072, ny=1024, steps=10)
+    s = Solver.from_workload(wl, precision="f32")
+    s.set_state(torch.from_numpy(wl.prim).cuda())
+    return _prof_timed(lambda: [s.step(2) for _ in range(wl.steps // 2)])
+
+
+def prof_burgers():
+    """The scalar D2Q4 lattice on case 1 of the 2-D Burgers problems, 4096 x 4096 FP32, 10 steps."""
+    import torch
+    from paper_1504_07034_gb300.solver import Solver
+    wl = workloads.burgers_2d(1, 4096, steps=10)
+    s = Solver.from_workload(wl, precision="f32")
+    s.set_state(torch.from_numpy(wl.prim).cuda())
+    return _prof_timed(lambda: [s.step(1) for _ in range(wl.steps)])
+
+
+def prof_adaptive():
+    """Adaptive lambda on the 1024 x 1024 quadrant problem in FP32, 10 single adaptive steps."""
+    import torch
+    from paper_1504_07034_gb300.solver import Solver
+    wl = workloads.quadrant_riemann(0, 1024, steps=0)
+    s = Solver.from_workload(wl, precision="f32")
+    s.set_state(torch.from_numpy(wl.prim).cuda())
+    return _prof_timed(lambda: [s.step_adaptive(1, 1.05) for _ in range(10)])
+
+
+def prof_adjoint():
+    import torch
+    from paper_1504_07034_gb300.solver import Solver
+    wl, target = workloads.adjoint_pulses(seed=0, n=1024, steps=0)
+    s = Solver.from_workload(wl, precision="f32")
+    s.set_state(torch.from_numpy(wl.prim).cuda())
+    tgt = torch.from_numpy(target).float().cuda()
+
+    def run():
+        s.forward_checkpointed(12, 4)
+        _, g = s.vjp_loss(tgt)
+        s.backward_checkpointed(g)
+    return _prof_timed(run)
+
+
+def prof_batch():
+    import torch
+    from paper_1504_07034_gb300.solver import BatchSolver
+    tb = workloads.batched_tubes(seed=0, count=512)
+    steps = np.minimum(tb.steps, 96)
+    s = BatchSolver.from_tubes(tb, precision="f32")
+    s.tuning = (256, 4, 32)
+    s.set_state(torch.from_numpy(tb.prim()).cuda())
+    return _prof_timed(lambda: s.run(steps))
+
+
+def prof_diagnostics():
+    import torch
+    from paper_1504_07034_gb300.solver import Solver
+    wl = workloads.quadrant_riemann(0, 2048, steps=0)
+    s = Solver.from_workload(wl, precision="f32")
+    s.set_state(torch.from_numpy(wl.prim).cuda())
+    return _prof_timed(lambda: [s.diagnostics() for _ in range(3)])
+
+
+PROFILE_CASES = {f.__name__[len("prof_"):]: f for f in (
+    prof_step2d_f32, prof_step2d_f32_flushed, prof_step2d_f16neq, prof_step2d_f32u_flushed, prof_obstacles,
+    prof_burgers, prof_adaptive, prof_adjoint, prof_batch, prof_diagnostics)}
+
+
 # ------------------------------------------------------------------ GPU arm
 
 def sod_measurement(Solver, stream, barrier):
@@ -924,6 +1062,15 @@ def run_ours(args):
     return 0
 
 
+def run_profile(name):
+    from paper_1504_07034_gb300.build import build as build_lib
+    build_lib()
+    if name not in PROFILE_CASES:
+        raise SystemExit(f"unknown profiling case {name}; choose from {', '.join(PROFILE_CASES)}")
+    print(f"{name}: {PROFILE_CASES[name]() * 1e3:.2f} ms")
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -931,7 +1078,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", metavar="CASE", help="run one profiling case instead (see PROFILE_CASES)")
     args = ap.parse_args()
+    if args.profile:
+        return run_profile(args.profile)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

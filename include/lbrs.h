@@ -265,12 +265,13 @@ lbrs_status lbrs_diagnostics(lbrs_ctx* ctx, lbrs_diag* out);
 /* The same diagnostics for callers that cannot allocate device memory: no
  * context, no workspace, and no cudaMalloc/cudaFree or allocating library call.
  * The paper has no counterpart; it exists because some callers cannot provide
- * scratch memory -- code running while a CUDA graph is captured (allocation is
- * not allowed there), loops that must not stall on the implicit device
+ * scratch memory -- loops that must not stall on the implicit device
  * synchronisation of cudaMalloc/cudaFree, and processes whose device memory is
- * fully held by another allocator.
+ * fully held by another allocator (for instance a framework's caching pool).
  *   cfg   the configuration the distributions belong to (lattice, precision,
- *         nx, ny, gamma, lambda, dx are used; cuda_stream is the stream);
+ *         nx, ny, gamma, lambda, dx are used; cuda_stream is the stream).
+ *         Accepted: LBRS_D1Q2, LBRS_D1Q3 and LBRS_D2Q4 in LBRS_F64 or LBRS_F32;
+ *         LBRS_D2Q4S, LBRS_F16NEQ and LBRS_F32U get LBRS_EINVAL;
  *   d_fs  device distributions f[q][k][j][i] in cfg->precision, e.g. from
  *         lbrs_get_distributions;
  *   out   host struct, filled as by lbrs_diagnostics (same status rules).
@@ -278,9 +279,11 @@ lbrs_status lbrs_diagnostics(lbrs_ctx* ctx, lbrs_diag* out);
  * GPU that loads the library until the process exits.  Grids of more than
  * 33,554,432 cells are rejected with LBRS_EINVAL.  The first call on each
  * device (made while that device is current) looks up the array's device
- * address with cudaGetSymbolAddress; make that first call before any stream
- * capture.  All calls share the array: calls that overlap on the GPU race.
- * Synchronises cfg->cuda_stream. */
+ * address with cudaGetSymbolAddress and keeps it for the life of the process's
+ * context on that device (a cudaDeviceReset invalidates it); make that first
+ * call before any stream capture.  All calls share the array: calls that
+ * overlap on the GPU race.  The call reads the result back to host memory and
+ * synchronises cfg->cuda_stream before returning. */
 lbrs_status lbrs_diagnostics_noalloc(const lbrs_config* cfg, const void* d_fs, lbrs_diag* out);
 
 /* Copy the raw distributions f[q][k][j][i] (storage precision) out of / into

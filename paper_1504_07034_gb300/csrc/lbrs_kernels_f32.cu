@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(kFTX * kFTY, 4) step2d_f32_fused2_kernel(const
 // the general path (global loads through pull_edge_2d).  One elected thread arms an
 // mbarrier with the byte count and issues the copies; every thread waits on the
 // barrier's phase with a bounded number of polls.  A wait that gives up sets
-// *wait_flag, and the whole block leaves without touching the destination.
+// *wait_flag (see give_up_tile), and the block leaves without touching the destination.
 constexpr int kPX = 36;                                   // box columns (the 34-slot window, 16-byte aligned)
 constexpr int kTY = 16, kTWY = kTY + 2, kTWN = kFWX * kTWY, kTPY = kTY + 2, kTPN = kPX * kTPY;
 constexpr size_t kTallSmemBytes = 128 + 16u * kTPN * sizeof(float) + 16;
@@ -411,6 +411,22 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
     for (int it = 0; it < polls; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
+}
+
+// A block whose bounded wait for its tile copies gave up.  The thread that issued the
+// copies waits once more, again bounded, before the block leaves: while it waits the
+// block (and its shared memory) stays resident, so copies that land in that time land
+// in this block's own buffer.  The flag records the outcome: 1 if the copies landed
+// (nothing is in flight when the block leaves), 2 if they did not (a copy may still
+// complete into shared memory that a later block owns).  The host reports either as
+// LBRS_ETIMEOUT; the other threads leave at once (the block's shared memory is
+// released only when all of them have left).
+__device__ __forceinline__ void give_up_tile(uint32_t bar, unsigned* wait_flag)
+{
+    if (threadIdx.x == 0) {
+        const bool landed = mbar_wait_bounded(bar, 0, kWaitPolls);
+        atomicMax(wait_flag, landed ? 1u : 2u);
+    }
 }
 
 // The four population boxes of tile (i0, j0), each PN floats per field (36 columns
@@ -758,10 +774,7 @@ __global__ void __launch_bounds__(kFTX * kFTY, 5)
     if constexpr (OBST) obst = load_mask_window(a, s_m, i0, j0);   // while the copies are in flight
     const bool arrived = mbar_wait_bounded(bar, 0, kWaitPolls);
     if (!__syncthreads_and(arrived)) {
-        if (threadIdx.x == 0) {
-            atomicExch(wait_flag, 1u);
-            mbar_wait_bounded(bar, 0, kWaitPolls);   // give the copy in flight a last chance to land
-        }
+        give_up_tile(bar, wait_flag);
         return;
     }
     const int ti = threadIdx.x % kFTX, tj = threadIdx.x / kFTX;
@@ -972,10 +985,7 @@ __global__ void __launch_bounds__(kFTX * kFTY, 5)
     __syncthreads();
     const bool arrived = mbar_wait_bounded(bar, 0, kWaitPolls);
     if (!__syncthreads_and(arrived)) {
-        if (threadIdx.x == 0) {
-            atomicExch(wait_flag, 1u);
-            mbar_wait_bounded(bar, 0, kWaitPolls);   // give the copy in flight a last chance to land
-        }
+        give_up_tile(bar, wait_flag);
         return;
     }
     // phase 1: k^{s-1} on the window (periodic: every slot is a cell of the grid)

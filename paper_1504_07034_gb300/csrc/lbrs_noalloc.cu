@@ -2,11 +2,9 @@
 // workspace and without any device allocation.
 //
 // Some callers cannot hand this library a workspace for the reduction's
-// per-block partial sums: code that runs while a CUDA graph is being captured
-// (cudaMalloc is not allowed there), loops that must not stall on the
-// implicit device synchronisation of cudaMalloc/cudaFree, and processes whose
-// device memory is fully held by another allocator (for instance a
-// framework's caching pool).  For them this variant keeps its scratch in a
+// per-block partial sums: loops that must not stall on the implicit device
+// synchronisation of cudaMalloc/cudaFree, and processes whose device memory is
+// fully held by another allocator (for instance a framework's caching pool).  For them this variant keeps its scratch in a
 // file-scope static __device__ array of fixed size, which the CUDA runtime
 // places in device memory when the library's module is loaded and which stays
 // there, on every GPU that loads the library, until the process exits.
@@ -24,7 +22,10 @@
 // stand-in symbol, not a device address.  The device address is looked up
 // with cudaGetSymbolAddress once per device, with that device current, on the
 // first call made while it is current (that first call should therefore come
-// before any stream capture).  Device code here names the array directly.
+// before any stream capture), and kept for the life of the process's context
+// on that device: after a cudaDeviceReset the kept address is stale.  Device
+// code here names the array directly.  Each call ends by copying the result
+// to the caller's host struct and synchronising its stream.
 //
 // Compiled with -fmad=false, like the other FP64 kernels.
 #include <math.h>

@@ -802,7 +802,11 @@ lbrs_status lbrs_sync(lbrs_ctx* ctx)
         unsigned flag = 0;
         LBRS_CUDA(ctx, cudaMemcpyAsync(&flag, wait_flag(ctx), sizeof flag, cudaMemcpyDeviceToHost, ctx->stream));
         LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-        if (flag) return fail(ctx, LBRS_ETIMEOUT, "a bounded wait for a tile copy gave up; the state is not valid");
+        if (flag == 1) return fail(ctx, LBRS_ETIMEOUT, "a bounded wait for a tile copy gave up; the state is not valid");
+        if (flag)
+            return fail(ctx, LBRS_ETIMEOUT, "a bounded wait for a tile copy gave up and the copy had not landed when "
+                        "its block left: the state is not valid, and the copy may have completed into shared "
+                        "memory of a later block of the same launch or of a later kernel");
     }
 #ifdef LBRS_DEBUG
     {

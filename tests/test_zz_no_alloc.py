@@ -1,12 +1,12 @@
 """lbrs_diagnostics_noalloc: diagnostics for callers that cannot allocate device memory.
 
-Callers that run inside a CUDA graph capture, loops that must not stall on
-cudaMalloc's implicit synchronisation, and processes whose device memory is
-held by another allocator cannot hand the library a workspace.  The
-allocation-free entry point keeps its reduction scratch in a static device
-array instead.  These tests call it through the C ABI and check it against
-the workspace-based lbrs_diagnostics on the same distributions, twice in a
-row (the scratch is shared and keeps the previous call's contents).
+Loops that must not stall on cudaMalloc's implicit synchronisation and
+processes whose device memory is held by another allocator cannot hand the
+library a workspace.  The allocation-free entry point keeps its reduction
+scratch in a static device array instead.  These tests call it through the C
+ABI and check it against the workspace-based lbrs_diagnostics on the same
+distributions, for each accepted lattice, twice in a row (the scratch is
+shared and keeps the previous call's contents).
 
 This file is named so that pytest collects it last.
 """
@@ -38,10 +38,10 @@ def _solver(lattice, precision):
         wl.ny = 200
         s = Solver.from_workload(wl, precision=precision)
     else:
-        wl = W.sod(5000)
-        s = Solver.from_workload(wl, precision=precision)
+        wl = W.sod(5000, lattice=lattice)
+        s = Solver.from_workload(wl, precision=precision, lattice=lattice)
     s.set_state(torch.from_numpy(wl.prim).cuda())
-    s.step(wl.steps if lattice == "d1q2" else 60)
+    s.step(60 if lattice == "d2q4" else wl.steps)
     return s
 
 
@@ -61,7 +61,7 @@ def _same(ref, d, K):
 
 
 @pytest.mark.parametrize("precision", ["f64", "f32"])
-@pytest.mark.parametrize("lattice", ["d2q4", "d1q2"])
+@pytest.mark.parametrize("lattice", ["d2q4", "d1q2", "d1q3"])
 def test_noalloc_matches_workspace_diagnostics_twice(lattice, precision):
     from paper_1504_07034_gb300 import abi
     s = _solver(lattice, precision)
