@@ -24,6 +24,9 @@
 // the four fields of a population together (one 16-byte word per population and
 // slot), so a slot is written and a cell's pull is read in four vector accesses;
 // a tile whose window lies inside the domain skips the boundary resolution.
+#include <stdlib.h>
+#include <string.h>
+
 #include <cuda_fp16.h>
 
 #include "lbrs_kernels.cuh"
@@ -168,6 +171,214 @@ __global__ void __launch_bounds__(kThreads) step2d_tile_kernel(const F16Args a)
     }
 }
 
+// ---------------------------------------------------------------- moments-only form, two steps per launch
+//
+// At omega = 1 one step of the moments-only form is U'(x) = sum_q f^eq_q(U(x - c_q)) (with the
+// boundary resolution and the wall relations of the pull).  One CTA advances a 32 x 16 tile by two
+// steps and reads and writes the state once:
+//   phase A  f*^n = f^eq(U^n) of the 36 x 20 window (two cells of halo) into shared memory;
+//   phase B  U^{n+1} of the 34 x 18 inner window gathered from it; after a barrier the inner slots
+//            are overwritten in place with f*^{n+1} = f^eq(U^{n+1});
+//   phase C  U^{n+2} of the tile gathered from the inner window and stored.
+// Window slots beyond a periodic side hold the wrapped cells (their own pulls stay inside the
+// window).  A slot beyond another side stands for the source that the single-step pull would
+// resolve there: a Dirichlet side's ghost f, else the clamped cell (transmissive; a wall side's
+// slots are never read, the wall relations replace those populations), the x side taking
+// precedence at corners.  In phase A the clamped cell is loaded; in phase B the thread of such a
+// slot gathers U^{n+1} of the clamped slot itself, so every inner slot is written after one barrier.
+// Every value is formed by the arithmetic of the single-step kernel (step2d_tile_kernel<false>), so
+// the result is bit-identical to two single steps.  State traffic: 16 B read and 16 B written per
+// cell and launch, 16 B per lattice update.
+
+constexpr int kUX = 32, kUY = 16;                       // tile
+constexpr int kAX = kUX + 4, kAY = kUY + 4, kAN = kAX * kAY;   // phase-A window (two cells of halo)
+constexpr int kBX = kUX + 2, kBY = kUY + 2, kBN = kBX * kBY;   // phase-B inner window
+constexpr int kUThreads = kUX * kUY;
+constexpr int kBPer = (kBN + kUThreads - 1) / kUThreads;       // inner slots per thread
+
+// Cells beyond side s of an axis of n cells that a coordinate lies (0 inside).
+__device__ __forceinline__ int beyond(int i, int n) { return i < 0 ? -i : (i >= n ? i - n + 1 : 0); }
+
+__device__ __forceinline__ int wrap_mod(int i, int n)
+{
+    const int r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+// The two-step kernel.  a.Uin / a.Uout as in step2d_tile_kernel<false>.
+__global__ void __launch_bounds__(kUThreads) step2d_u2_kernel(const F16Args a)
+{
+    __shared__ float4 s_f[4 * kAN];      // [q][slot], slot = wy * kAX + wx
+    const int ti0 = blockIdx.x * kUX, tj0 = blockIdx.y * kUY;
+    const int i0 = ti0 - 2, j0 = tj0 - 2;                  // global cell of window slot (0, 0)
+    const bool inside = i0 >= 0 && j0 >= 0 && i0 + kAX <= a.nx && j0 + kAY <= a.ny;
+    const bool per_x = a.bc[0] == BC_PERIODIC, per_y = a.bc[2] == BC_PERIODIC;
+
+    // phase A: f*^n of every window slot that a later phase reads
+    for (int w = threadIdx.x; w < kAN; w += kUThreads) {
+        int i = i0 + w % kAX, j = j0 + w / kAX;
+        if (!inside) {
+            const int bx = beyond(i, a.nx), by = beyond(j, a.ny);
+            // two cells beyond a non-periodic side: only inner slots beyond that side would pull
+            // from here, and those are not gathered from their own position
+            if ((bx > 1 && !per_x) || (by > 1 && !per_y) || bx > 2 || by > 2) continue;
+            const float* g = nullptr;
+            if (bx) {
+                const int side = i < 0 ? 0 : 1;
+                const int kind = side == 0 ? a.bc[0] : a.bc[1];
+                if (kind == BC_DIRICHLET) g = a.ghost + side * GHOST_STRIDE;
+                else if (kind == BC_PERIODIC) i = wrap_mod(i, a.nx);
+                else i = i < 0 ? 0 : a.nx - 1;
+            }
+            if (!g && by) {
+                const int side = j < 0 ? 2 : 3;
+                const int kind = side == 2 ? a.bc[2] : a.bc[3];
+                if (kind == BC_DIRICHLET) g = a.ghost + side * GHOST_STRIDE;
+                else if (kind == BC_PERIODIC) j = wrap_mod(j, a.ny);
+                else j = j < 0 ? 0 : a.ny - 1;
+            }
+            if (g) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    s_f[LBRS_IX(q * kAN + w, 4 * kAN, 42)] = make_float4(g[q * 4], g[q * 4 + 1], g[q * 4 + 2], g[q * 4 + 3]);
+                continue;
+            }
+        }
+        const int64_t c = (int64_t)j * a.nx + i;
+        float U[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) U[k] = a.Uin[LBRS_IX(k * a.N + c, 4 * a.N, 43)];
+        float e[4][4];
+        equilibria2d<float>(U, a.gm1, a.c, e);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            s_f[LBRS_IX(q * kAN + w, 4 * kAN, 42)] = make_float4(e[q][0], e[q][1], e[q][2], e[q][3]);
+    }
+    __syncthreads();
+
+    // phase B: U^{n+1} of the inner slots (kind 0: skip, 1: gathered, 2: Dirichlet ghost of side gs)
+    float U1[kBPer][4];
+    int kind1[kBPer], gs1[kBPer];
+#pragma unroll
+    for (int r = 0; r < kBPer; ++r) {
+        kind1[r] = 0;
+        gs1[r] = 0;
+        const int b = threadIdx.x + r * kUThreads;
+        if (b >= kBN) continue;
+        int wx = 1 + b % kBX, wy = 1 + b / kBX;             // window position of the slot
+        if (!inside) {
+            const int i = i0 + wx, j = j0 + wy;
+            const int bx = beyond(i, a.nx), by = beyond(j, a.ny);
+            if (bx > 1 || by > 1) continue;                  // beyond a ragged tile's edge: no cell pulls it
+            bool ghost = false;
+            if (bx && !per_x) {
+                const int side = i < 0 ? 0 : 1;
+                if ((side == 0 ? a.bc[0] : a.bc[1]) == BC_DIRICHLET) {
+                    ghost = true;
+                    gs1[r] = side;
+                } else {
+                    wx += i < 0 ? -i : a.nx - 1 - i;        // the clamped cell's slot
+                }
+            }
+            if (!ghost && by && !per_y) {
+                const int side = j < 0 ? 2 : 3;
+                if ((side == 2 ? a.bc[2] : a.bc[3]) == BC_DIRICHLET) {
+                    ghost = true;
+                    gs1[r] = side;
+                } else {
+                    wy += j < 0 ? -j : a.ny - 1 - j;
+                }
+            }
+            if (ghost) {
+                kind1[r] = 2;
+                continue;
+            }
+        }
+        const int slot = wy * kAX + wx;
+        const int src[4] = {slot + kAX + 1, slot + kAX - 1, slot - kAX - 1, slot - kAX + 1};
+        float f[4][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 v = s_f[LBRS_IX(q * kAN + src[q], 4 * kAN, 44)];
+            f[q][0] = v.x;
+            f[q][1] = v.y;
+            f[q][2] = v.z;
+            f[q][3] = v.w;
+        }
+        const int j = j0 + wy;                               // the gathering cell's row (unwrapped)
+        const bool wall_bottom = j == 0 && a.bc[2] == BC_WALL;
+        const bool wall_top = j == a.ny - 1 && a.bc[3] == BC_WALL;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float sgn = k == 2 ? -1.f : 1.f;
+            if (wall_top) {
+                f[0][k] = sgn * f[3][k];
+                f[1][k] = sgn * f[2][k];
+            }
+            if (wall_bottom) {
+                f[3][k] = sgn * f[0][k];
+                f[2][k] = sgn * f[1][k];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) U1[r][k] = ((f[0][k] + f[1][k]) + f[2][k]) + f[3][k];
+        kind1[r] = 1;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kBPer; ++r) {
+        const int b = threadIdx.x + r * kUThreads;
+        if (b >= kBN || kind1[r] == 0) continue;
+        const int w = (1 + b / kBX) * kAX + 1 + b % kBX;
+        if (kind1[r] == 2) {
+            const float* g = a.ghost + gs1[r] * GHOST_STRIDE;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                s_f[LBRS_IX(q * kAN + w, 4 * kAN, 45)] = make_float4(g[q * 4], g[q * 4 + 1], g[q * 4 + 2], g[q * 4 + 3]);
+            continue;
+        }
+        float e[4][4];
+        equilibria2d<float>(U1[r], a.gm1, a.c, e);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            s_f[LBRS_IX(q * kAN + w, 4 * kAN, 45)] = make_float4(e[q][0], e[q][1], e[q][2], e[q][3]);
+    }
+    __syncthreads();
+
+    // phase C: U^{n+2} of the tile
+    const int tx = threadIdx.x % kUX, ty = threadIdx.x / kUX;
+    const int i = ti0 + tx, j = tj0 + ty;
+    if (i >= a.nx || j >= a.ny) return;
+    const int slot = (ty + 2) * kAX + (tx + 2);
+    const int src[4] = {slot + kAX + 1, slot + kAX - 1, slot - kAX - 1, slot - kAX + 1};
+    float f[4][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float4 v = s_f[LBRS_IX(q * kAN + src[q], 4 * kAN, 46)];
+        f[q][0] = v.x;
+        f[q][1] = v.y;
+        f[q][2] = v.z;
+        f[q][3] = v.w;
+    }
+    const bool wall_bottom = j == 0 && a.bc[2] == BC_WALL;
+    const bool wall_top = j == a.ny - 1 && a.bc[3] == BC_WALL;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float sgn = k == 2 ? -1.f : 1.f;
+        if (wall_top) {
+            f[0][k] = sgn * f[3][k];
+            f[1][k] = sgn * f[2][k];
+        }
+        if (wall_bottom) {
+            f[3][k] = sgn * f[0][k];
+            f[2][k] = sgn * f[1][k];
+        }
+    }
+    const int64_t c = (int64_t)j * a.nx + i;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a.Uout[LBRS_IX(k * a.N + c, 4 * a.N, 47)] = ((f[0][k] + f[1][k]) + f[2][k]) + f[3][k];
+}
+
 // Initial state: U from W (conserved or primitive, FP64 arithmetic), g = 0.
 template <typename Tin>
 __global__ void __launch_bounds__(256) set_state_f16neq_kernel(const Tin* __restrict__ W, float* __restrict__ U,
@@ -253,6 +464,22 @@ cudaError_t launch_step_f32u(const F16StepArgs& s, cudaStream_t st)
     const dim3 grid((unsigned)((s.nx + kTX - 1) / kTX), (unsigned)((s.ny + kTY - 1) / kTY));
     step2d_tile_kernel<false><<<grid, kThreads, 0, st>>>(tile_args(s, false));
     return cudaGetLastError();
+}
+
+cudaError_t launch_step2_f32u(const F16StepArgs& s, cudaStream_t st)
+{
+    const dim3 grid((unsigned)((s.nx + kUX - 1) / kUX), (unsigned)((s.ny + kUY - 1) / kUY));
+    step2d_u2_kernel<<<grid, kUThreads, 0, st>>>(tile_args(s, false));
+    return cudaGetLastError();
+}
+
+bool step2_f32u_enabled()
+{
+    static int v = [] {
+        const char* e = getenv("LBRS_F32U_FUSE");
+        return (e && !strcmp(e, "0")) ? 0 : 1;
+    }();
+    return v != 0;
 }
 
 cudaError_t launch_set_state_f32u(const void* W, int w_dtype, int kind, void* fs, int64_t N, int64_t plane,

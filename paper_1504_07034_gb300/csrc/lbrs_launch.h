@@ -165,6 +165,10 @@ struct F16StepArgs {
 cudaError_t launch_step_f16neq(const F16StepArgs& a, cudaStream_t s);
 // Moments-only form (omega = 1): a state buffer is U [4][N] FP32.
 cudaError_t launch_step_f32u(const F16StepArgs& a, cudaStream_t s);
+// The same, two steps per launch (bit-identical to two single steps); off when the
+// environment sets LBRS_F32U_FUSE=0.
+cudaError_t launch_step2_f32u(const F16StepArgs& a, cudaStream_t s);
+bool step2_f32u_enabled();
 cudaError_t launch_set_state_f32u(const void* W, int w_dtype, int kind, void* fs, int64_t N, int64_t plane,
                                   double gamma, cudaStream_t s);
 // U = U(W) in FP32, g = 0, then the per-field scales from max |U_k| (absmax_bits: 4 words of scratch).

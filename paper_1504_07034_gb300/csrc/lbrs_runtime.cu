@@ -257,41 +257,51 @@ StepArgs<T> step_args(const lbrs_ctx* ctx, int from)
     return a;
 }
 
+// Arguments of the reduced-state kernels (FP16 non-equilibrium and moments-only forms).
+F16StepArgs f16_args(const lbrs_ctx* ctx, int from)
+{
+    F16StepArgs a;
+    a.src = ctx->f[from];
+    a.dst = ctx->f[from ^ 1];
+    a.ghost = (const float*)(ctx->ws + ctx->L.ghost);
+    a.N = ctx->N;
+    a.nx = (int)ctx->cfg.nx;
+    a.ny = (int)ctx->ny_store;
+    for (int k = 0; k < 4; ++k) a.bc[k] = kernel_bc(ctx, k);
+    a.om = (float)ctx->cfg.omega;
+    a.om1 = (float)(1.0 - ctx->cfg.omega);
+    a.c = (float)ctx->c;
+    a.gm1 = (float)(ctx->cfg.gamma - 1.0);
+    return a;
+}
+
 cudaError_t launch_one_step(lbrs_ctx* ctx, int from, cudaStream_t s)
 {
     const int lat = lat_code(ctx->lattice);
     if (ctx->f64) return launch_step_f64(lat, step_args<double>(ctx, from), s);
-    if (ctx->f16 || ctx->f32u) {
-        F16StepArgs a;
-        a.src = ctx->f[from];
-        a.dst = ctx->f[from ^ 1];
-        a.ghost = (const float*)(ctx->ws + ctx->L.ghost);
-        a.N = ctx->N;
-        a.nx = (int)ctx->cfg.nx;
-        a.ny = (int)ctx->ny_store;
-        for (int k = 0; k < 4; ++k) a.bc[k] = kernel_bc(ctx, k);
-        a.om = (float)ctx->cfg.omega;
-        a.om1 = (float)(1.0 - ctx->cfg.omega);
-        a.c = (float)ctx->c;
-        a.gm1 = (float)(ctx->cfg.gamma - 1.0);
-        return ctx->f16 ? launch_step_f16neq(a, s) : launch_step_f32u(a, s);
-    }
+    if (ctx->f16) return launch_step_f16neq(f16_args(ctx, from), s);
+    if (ctx->f32u) return launch_step_f32u(f16_args(ctx, from), s);
     return launch_step_f32(lat, step_args<float>(ctx, from), s);
 }
 
-// Two-steps-per-launch kernel available for this context?  With internal walls
-// only in its tensor-copy form.
-bool fused2(const lbrs_ctx* ctx)
+// The FP32 distribution form's two-steps-per-launch kernel available for this context?
+// With internal walls only in its tensor-copy form.
+bool fused2_f32(const lbrs_ctx* ctx)
 {
     if (ctx->f64 || ctx->f16 || ctx->f32u || ctx->lattice != LBRS_D2Q4 || !step2_f32_enabled()) return false;
     return !ctx->solid || (ctx->tmap[0].valid && ctx->tmap[1].valid);
 }
+
+// Does lbrs_step advance this context two steps per launch (FP32 distributions, or the
+// moments-only form)?
+bool fused2(const lbrs_ctx* ctx) { return fused2_f32(ctx) || (ctx->f32u && step2_f32u_enabled()); }
 
 unsigned* wait_flag(const lbrs_ctx* ctx) { return (unsigned*)(ctx->ws + ctx->L.wait_flag); }
 
 // Two steps from buffer b into buffer b ^ 1.
 cudaError_t launch_step2(const lbrs_ctx* ctx, int b, cudaStream_t s)
 {
+    if (ctx->f32u) return launch_step2_f32u(f16_args(ctx, b), s);
     return launch_step2_f32(step_args<float>(ctx, b), &ctx->tmap[b], wait_flag(ctx), s);
 }
 
@@ -506,7 +516,7 @@ lbrs_status record_steps(lbrs_ctx* ctx, int64_t n, char* U_hist)
 {
     const size_t stride = (size_t)ctx->K * ctx->N * elem_bytes(ctx);
     int64_t m = 0;
-    for (; m + 2 <= n && fused2(ctx) && !ctx->solid; m += 2) {
+    for (; m + 2 <= n && fused2_f32(ctx) && !ctx->solid; m += 2) {
         LBRS_CUDA(ctx, launch_record_step2(ctx, U_hist + m * stride));
         ctx->cur ^= 1;
         ctx->launches += 1;
@@ -680,7 +690,7 @@ lbrs_status lbrs_create(const lbrs_config* cfg, void* d_workspace, size_t bytes,
         free(ctx);
         return s;
     }
-    if (fused2(ctx))
+    if (fused2_f32(ctx))
         for (int b = 0; b < 2; ++b) encode_f32_tile_map(&ctx->tmap[b], (const float*)ctx->f[b], cfg->nx, ctx->ny_store);
     *out = ctx;
     return LBRS_OK;
@@ -1361,7 +1371,7 @@ lbrs_status lbrs_backward_checkpointed(lbrs_ctx* ctx, void* d_adj_ws, const void
                                        cudaMemcpyDeviceToDevice, ctx->stream));
         lbrs_status rs = record_steps(ctx, len, uhist);
         if (rs != LBRS_OK) return rs;
-        if (fused2(ctx)) {
+        if (fused2_f32(ctx)) {
             // sweep on k = fbar: k^{end} from g^{end}, two steps per launch while U_{s-1} and
             // U_{s-2} lie in this segment, one more step if needed, then the pull that hands
             // g^{start} to the earlier segment.  uhist[m] holds U_{start+m+1}.
