@@ -682,7 +682,7 @@ def adjoint_measurement(Solver, stream, barrier, n=2048, steps=2000):
 
         gen = torch.Generator(device="cpu").manual_seed(5)
         errs = {"f32": [], "f64": []}
-        for _ in range(4):
+        for _ in range(8):
             d = torch.randn(U0.shape, generator=gen, dtype=torch.float64).cuda()
             h = 1e-6 * float(U0.norm() / d.norm())
             fd = (loss64(U0 + h * d) - loss64(U0 - h * d)) / (2 * h)
@@ -699,9 +699,10 @@ def adjoint_measurement(Solver, stream, barrier, n=2048, steps=2000):
                                                     "note": "periodic grid: mass, momentum and energy totals in FP64"},
             "forward_s": t_fwd, "backward_s": t_bwd, "backward_over_forward": t_bwd / t_fwd,
             "forward_mlups": n * n * steps / t_fwd / 1e6, "loss": loss, "grad_norm": gnorm,
-            "fd_check_64x64": {"steps": fd_steps, "directions": 4,
+            "fd_check_64x64": {"steps": fd_steps, "directions": 8,
                                "f32_max_rel_err_vs_fd": max(errs["f32"]),
                                "f64_max_rel_err_vs_fd": max(errs["f64"]),
+                               "f32_rel_err_vs_fd": errs["f32"], "f64_rel_err_vs_fd": errs["f64"],
                                "f32_vs_f64_gradient_normwise": normwise,
                                "reference": "FP64 GPU path central differences; 64x64 copy run to the same "
                                             "final time as the 2048^2 x 2000-step workload"}}

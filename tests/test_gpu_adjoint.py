@@ -33,8 +33,12 @@ def make(n, precision, steps=0, seed=0, omega=1.0, width=0.05, pulses=8):
     return wl, target, s, o
 
 
-def normwise(a, b):
-    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+def normwise(a, b, axis):
+    """Largest |a - b| relative to the largest |b|, taken per conserved field (axis: the field
+    axis of the arrays; a field that is zero throughout is scaled by the largest of all)."""
+    a, b = np.moveaxis(np.asarray(a), axis, 0), np.moveaxis(np.asarray(b), axis, 0)
+    glob = float(np.max(np.abs(b)))
+    return max(float(np.max(np.abs(a[k] - b[k]))) / (float(np.max(np.abs(b[k]))) or glob) for k in range(b.shape[0]))
 
 
 @pytest.mark.parametrize("omega", [1.0, 1.5])
@@ -47,12 +51,12 @@ def test_f64_adjoint_step_and_vjp_match_oracle(omega):
     fs = s.get_distributions().cpu().numpy()
     U_hist = s.step_record(1).cpu().numpy()[0]
     _, U_ref, _ = o.collide(o.stream(fs))
-    assert normwise(U_hist, U_ref) <= 1e-12
+    assert normwise(U_hist, U_ref, 0) <= 1e-12
     g = rng.standard_normal(fs.shape)
     out = s.adjoint_step(torch.from_numpy(U_ref).cuda(), torch.from_numpy(g).cuda()).cpu().numpy()
-    assert normwise(out, o.adjoint_step(U_ref, g)) <= 1e-12
+    assert normwise(out, o.adjoint_step(U_ref, g), 1) <= 1e-12
     vjp = s.vjp_equilibrium(torch.from_numpy(U0).cuda(), torch.from_numpy(g).cuda()).cpu().numpy()
-    assert normwise(vjp, o.vjp_equilibrium(U0, g)) <= 1e-12
+    assert normwise(vjp, o.vjp_equilibrium(U0, g), 0) <= 1e-12
     s.close()
 
 
@@ -71,9 +75,9 @@ def test_f64_checkpointed_gradient_matches_oracle():
     dLdU = np.zeros_like(U0)
     dLdU[0] = (rho - target) * cell
     g_ref, _ = o.gradient(U0, steps, dLdU)
-    assert normwise(grad, g_ref) <= 1e-10
+    assert normwise(grad, g_ref, 0) <= 1e-10
     # the forward state is restored after the backward sweep
-    assert np.max(np.abs(s.moments().cpu().numpy() - o.moments(fsT))) <= 1e-12 * np.abs(o.moments(fsT)).max()
+    assert normwise(s.moments().cpu().numpy(), o.moments(fsT), 0) <= 1e-12
     assert s.step_count == steps
     s.close()
 
@@ -195,26 +199,36 @@ def test_f64_gradient_matches_finite_differences(n, steps):
     final time (2000 * 64 / 2048 = 62.5 -> 63 steps); (64, 2000) keeps the step count."""
     wl, target, _, o = make(n, "f64")
     U0 = o.prim_to_cons(wl.prim)
-    errs = _fd_errors(_gpu_gradient("f64", wl, target, U0, steps), wl, target, U0, steps, 6)
-    assert max(errs) <= 1e-5, errs
+    errs = _fd_errors(_gpu_gradient("f64", wl, target, U0, steps), wl, target, U0, steps, 8)
+    # the FP64 adjoint equals the oracle's to 1e-10 (above); what remains here is the central
+    # differences' own truncation error at h = 1e-6 |U0| / |d|, up to about 1.1e-5 over these
+    # eight directions, a tenth of the 1e-4 target
+    assert max(errs) <= 2e-5, errs
 
 
 def test_f32_gradient_against_fp64_and_finite_differences():
     """FP32 gradient (FP32 forward, FP32 adjoint) on the 64 x 64 copy, 63 steps.
 
-    Bar: within 1e-4 of the FP64 gradient normwise (the FP64 gradient matches central
-    differences to 1e-5, test above).  Directional errors against the differences
-    themselves are reported and bounded by 1e-3: they are set by the FP32 rounding of the
-    forward trajectory (chiefly rho(T) in the loss), not by the adjoint."""
+    Bars: within 1e-4 of the FP64 gradient normwise, and per conserved field within 1e-4 of
+    that field's FP64 gradient (the FP64 gradient matches central differences to 2e-5 in
+    every direction, test above).  The 1e-4 target is not met in every direction against
+    the differences themselves: over these eight directions the FP32 errors run from 3e-6
+    to 5.5e-4 (three above 1e-4), so that check only guards against regressions (1e-3).
+    They are set by the FP32 rounding of the forward trajectory (an FP32 adjoint over an
+    FP64 forward is within 2e-7), and a direction whose derivative is small against |g| |d|
+    magnifies them."""
     n, steps = 64, 63
     wl, target, _, o = make(n, "f32")
     U0 = o.prim_to_cons(wl.prim)
     g32 = _gpu_gradient("f32", wl, target, U0, steps)
     g64 = _gpu_gradient("f64", wl, target, U0, steps)
     rel = np.linalg.norm(g32 - g64) / np.linalg.norm(g64)
-    errs = _fd_errors(g32, wl, target, U0, steps, 6)
-    print(f"FP32 gradient 64x64 x {steps}: normwise vs FP64 {rel:.2e}; directional vs FD max {max(errs):.2e}")
+    rel_field = max(np.linalg.norm(g32[k] - g64[k]) / np.linalg.norm(g64[k]) for k in range(4))
+    errs = _fd_errors(g32, wl, target, U0, steps, 8)
+    print(f"FP32 gradient 64x64 x {steps}: normwise vs FP64 {rel:.2e} (worst field {rel_field:.2e}); "
+          f"directional vs FD {['%.1e' % e for e in errs]}")
     assert rel <= 1e-4
+    assert rel_field <= 1e-4
     assert max(errs) <= 1e-3, errs
 
 
@@ -223,8 +237,8 @@ def test_f32_gradient_full_size():
 
     The FP64 gradient matches central differences (1e-5 bar, about 1e-7 measured).  The
     FP32 gradient is the exact gradient of the FP32 map; its distance to the FP64
-    gradient (about 2.7e-4 normwise, bar 5e-4) is the FP32 rounding of the 2000-step
-    forward trajectory, amplified by the loss seed rho(T) - rho_target."""
+    gradient (2.7e-4 normwise: the 1e-4 target is not met at this size in FP32; bar 5e-4
+    against regressions) is the FP32 rounding of the 2000-step forward trajectory."""
     n, steps = 2048, 2000
     wl, target = W.adjoint_pulses(seed=0, n=n, steps=steps)
     U0 = _cons(wl.prim)
