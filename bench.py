@@ -49,11 +49,33 @@ CONFIG_STEPS = 1000
 
 
 def workload():
-    return workloads.quadrant_riemann(seed=0, n=1024, steps=CONFIG_STEPS)
+    """The headline configuration (workloads/configs/quadrant_riemann_1024.json)."""
+    return workloads.from_config("quadrant_riemann_1024")[1]
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform string)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def config_dict(wl, extra=None):
     d = {"workload": "2-D D2Q4 four-quadrant Riemann 1024x1024, seed 0, transmissive, 1000-step configuration",
+         "config_file": "workloads/configs/quadrant_riemann_1024.json",
          "nx": wl.nx, "ny": wl.ny, "lattice": "D2Q4", "gamma": wl.gamma, "omega": wl.omega,
          "lambda": wl.lam,
          "l2": "flushed (256 MiB write) before every timed call of lbrs_step (two time steps for the "
@@ -61,6 +83,11 @@ def config_dict(wl, extra=None):
     if extra:
         d.update(extra)
     return d
+
+
+def parallelism(ws: int) -> str:
+    return "1 GPU" if ws == 1 else (f"{ws} y-slabs, one per GPU, 2 ghost rows per cut, NCCL send/recv of the "
+                                    "rows every two steps")
 
 
 def dist_env():
@@ -175,6 +202,87 @@ def oracle_sample(wl, seconds=12.0):
     return out
 
 
+def _oracle_rate(o, fs, cells, seconds, max_steps):
+    """MLUPS of the oracle `o` from fs over about `seconds` of steps (at most max_steps)."""
+    _, t1 = o.timed_run(fs, 1)
+    n = max(1, min(max_steps, int(seconds / max(t1, 1e-6))))
+    _, t = o.timed_run(fs, n)
+    return cells * n / t / 1e6, n, t
+
+
+def oracle_per_config(seconds=4.0):
+    """The FP64 oracle as it stands, on the host cores and on one thread, beside each seeded
+    configuration other than the headline: bounded samples of each (a few seconds of CPU
+    work apiece), with the full run's time extrapolated from the sample where the sample
+    is not the whole run."""
+    import oracle
+    out = {}
+    # 1: Sod, the whole run
+    cfg, wl = workloads.from_config("sod_d1q2_1000")
+    res = {"workload": cfg["name"], "steps": wl.steps}
+    for name, nth in (("all_cores", 0), ("one_thread", 1)):
+        o = oracle.Oracle.from_workload(wl, nthreads=nth)
+        fs = o.init(o.prim_to_cons(wl.prim))
+        _, t = o.timed_run(fs, wl.steps)
+        res[name] = {"value": wl.nx * wl.steps / t / 1e6, "unit": UNIT, "seconds": t,
+                     "cores": oracle.max_threads() if nth == 0 else 1, "sample": "the whole run"}
+    out["sod_d1q2_1000"] = res
+    # 3: oblique shock, the first steps of the run, the 20000-step time extrapolated
+    cfg, wl = workloads.from_config("oblique_shock_4096x1024", steps=0)
+    full_steps = cfg["kwargs"]["steps"]
+    res = {"workload": cfg["name"]}
+    for name, nth, sec in (("all_cores", 0, 2 * seconds), ("one_thread", 1, seconds)):
+        o = oracle.Oracle.from_workload(wl, nthreads=nth)
+        fs = o.init(o.prim_to_cons(wl.prim))
+        v, n, t = _oracle_rate(o, fs, wl.cells, sec, 2000)
+        res[name] = {"value": v, "unit": UNIT, "cores": oracle.max_threads() if nth == 0 else 1,
+                     "sample": f"steps 2..{n + 1} of the run on the full grid ({t:.1f} s)",
+                     "extrapolated_full_run_s": wl.cells * full_steps / (v * 1e6), "extrapolated": True}
+    out["oblique_shock_4096x1024"] = res
+    # 4: batched tubes, whole tubes from the front of the batch up to a bounded number of updates
+    cfg, tb = workloads.from_config("batched_tubes_4096")
+    budget, done, t = 2e8, 0, 0.0
+    b = 0
+    import time as _time
+    while b < len(tb.lengths) and done < budget:
+        n, steps = int(tb.lengths[b]), int(tb.steps[b])
+        o = oracle.Oracle(oracle.D1Q2, n, 1, gamma=tb.gamma, lam=float(tb.lam[b]), omega=tb.omega,
+                          bc=[("transmissive", None)] * 2, nthreads=1)
+        x = (np.arange(n) + 0.5) / n
+        prim = np.stack([np.where(x < 0.5, tb.left[b, k], tb.right[b, k]) for k in range(3)])
+        fs = o.init(o.prim_to_cons(prim))
+        _, dt = o.timed_run(fs, steps)
+        t += dt
+        done += n * steps
+        b += 1
+    v = done / t / 1e6
+    out["batched_tubes_4096"] = {"workload": cfg["name"], "one_thread": {
+        "value": v, "unit": UNIT, "cores": 1,
+        "sample": f"the batch's first {b} tubes, whole runs, {done:.3g} updates ({t:.1f} s); a tube is one "
+                  "row, which the oracle runs on one thread",
+        "extrapolated_full_run_s": tb.total_updates / (v * 1e6), "extrapolated": True}}
+    # 5: adjoint, forward with stored moments plus the backward sweep, at 64^2 and 512^2
+    res = {"workload": "adjoint_pulses_2048 at 64 x 64 (63 steps, the FD copy) and 512 x 512 (32 steps)"}
+    for n, steps in ((64, 63), (512, 32)):
+        wl5, tgt = workloads.adjoint_pulses(seed=0, n=n, steps=steps)
+        o = oracle.Oracle.from_workload(wl5)
+        U0 = o.prim_to_cons(wl5.prim)
+        t0 = _time.perf_counter()
+        fsT, _ = o.run(o.init(U0), steps)
+        t_fwd = _time.perf_counter() - t0
+        dLdU = np.zeros_like(U0)
+        dLdU[0] = (o.moments(fsT)[0] - tgt) * wl5.dx * wl5.dx
+        t0 = _time.perf_counter()
+        o.gradient(U0, steps, dLdU)
+        t_grad = _time.perf_counter() - t0
+        res[f"{n}x{n}"] = {"steps": steps, "forward_s": t_fwd, "forward_mlups": n * n * steps / t_fwd / 1e6,
+                           "gradient_s": t_grad, "gradient_over_forward": t_grad / t_fwd,
+                           "cores": oracle.max_threads(),
+                           "note": "gradient = a forward run storing every step's moments, then the adjoint sweep"}
+    out["adjoint_pulses_2048"] = res
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -193,8 +301,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded quadrant states)", "config": config_dict(wl),
+            "data": "synthetic (seeded quadrant states)", "config": config_dict(wl, {"parallelism": parallelism(ws)}),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                             "cpu_model": cpu_model(),
                              "sample": f"full {wl.nx}x{wl.ny} grid, {args.steps} steps after {args.warmup} warm-up, "
                                        "FP64 on the host cores (no L2 flush: a CPU run)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -347,7 +456,7 @@ def sod_measurement(Solver, stream, barrier):
     density L1 against the exact Riemann solution (a latency-bound case, not a roofline case)."""
     import torch
     from workloads import riemann
-    wl = workloads.sod(1000)
+    wl = workloads.from_config("sod_d1q2_1000")[1]
     exact = riemann.sample(wl.gamma, wl.meta["left"], wl.meta["right"], (wl.x - 0.5) / wl.t_final)[0]
     out = {"workload": "Sod D1Q2, 1000 cells on [0, 1], t = 0.2, %d steps, lambda %.4f" % (wl.steps, wl.lam)}
     for precision in ("f64", "f32"):
@@ -388,7 +497,7 @@ def oblique_measurement(Solver, stream, barrier, peak):
                        "working set larger than L2 (no flush needed)"}
     for precision, bpl in (("f32", BYTES_PER_LUP_F32_FUSED2), ("f16neq", BYTES_PER_LUP_F16NEQ),
                            ("f32u", BYTES_PER_LUP_F32U)):
-        big = workloads.oblique_shock_reflection(steps=200)
+        big = workloads.from_config("oblique_shock_4096x1024", steps=200)[1]
         s = Solver.from_workload(big, precision=precision, stream=stream)
         with torch.cuda.stream(stream):
             s.set_state(torch.from_numpy(big.prim).cuda())
@@ -408,7 +517,7 @@ def oblique_measurement(Solver, stream, barrier, peak):
             out[precision]["kernel_frac"] = 16 * mlups / 1e3 / peak
         s.close()
     for omega, steps in ((1.0, 20000), (1.5, 2000)):
-        wl = workloads.oblique_shock_reflection(steps=steps, omega=omega)
+        wl = workloads.from_config("oblique_shock_4096x1024", steps=steps, omega=omega)[1]
         rho = {}
         forms = ("f64", "f32", "f16neq", "f32u") if omega == 1.0 else ("f64", "f32", "f16neq")
         with torch.cuda.stream(stream):
@@ -555,7 +664,7 @@ def batch_measurement(stream, barrier):
     """4096 shock tubes, N log-uniform in [200, 20000], to t = 0.15 in FP32 (temporal blocking)."""
     import torch
     from paper_1504_07034_gb300.solver import BatchSolver
-    tb = workloads.batched_tubes(seed=0, count=4096)
+    tb = workloads.from_config("batched_tubes_4096")[1]
     s = BatchSolver.from_tubes(tb, precision="f32", stream=stream)
     W0 = torch.from_numpy(tb.prim()).cuda()
     with torch.cuda.stream(stream):
@@ -628,7 +737,7 @@ def adjoint_measurement(Solver, stream, barrier, n=2048, steps=2000):
     """Forward (checkpointed) vs backward (recompute + adjoint) time of the density-loss gradient,
     and the FP32 gradient's error against FP64 central differences on a 64 x 64 copy."""
     import torch
-    wl, target = workloads.adjoint_pulses(seed=0, n=n, steps=steps)
+    wl, target = workloads.from_config("adjoint_pulses_2048", n=n, steps=steps)[1]
     s = Solver.from_workload(wl, precision="f32", stream=stream)
     tgt = torch.from_numpy(target).float().cuda()
     W0 = torch.from_numpy(wl.prim).cuda()
@@ -828,8 +937,7 @@ def run_slabs(args, ws, rank, local):
             "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
             "scaling": "strong", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded four-quadrant Riemann states)",
-            "config": config_dict(wl, {"parallelism": f"{ws} y-slabs, one per GPU, 2 ghost rows per cut, "
-                                                      "NCCL send/recv of the rows every two steps"}),
+            "config": config_dict(wl, {"parallelism": parallelism(ws)}),
             "gpu_launches": launches,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
@@ -1031,10 +1139,14 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * t32 / args.steps, "higher_is_better": True,
             "scaling": "strong", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded four-quadrant Riemann states)",
-            "config": config_dict(wl, {"parallelism": "1 GPU"}),
+            "config": config_dict(wl, {"parallelism": parallelism(ws)}),
             "gpu_launches": launches,
+            "frac_kernel_bytes": achieved / peak,
+            "frac_per_step_128B": value / (peak * 1e3 / BYTES_PER_LUP_F32),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
+                         "frac_kernel_bytes": achieved / peak,
+                         "frac_per_step_128B": value / (peak * 1e3 / BYTES_PER_LUP_F32),
                          "kernel": "step2d_f32_fused2_tall_kernel<false>", "peak_kind": f"{peak_kind} hbm_gbs",
                          "algorithmic_bytes_per_launch": 2 * BYTES_PER_LUP_F32_FUSED2 * wl.cells,
                          "algorithmic_bytes_per_lup": BYTES_PER_LUP_F32_FUSED2,
@@ -1064,6 +1176,8 @@ def run_ours(args):
             "clocks": clocks}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(wl)
+        line["cpu_baseline"]["cpu_model"] = cpu_model()
+        line["cpu_baseline"]["per_config"] = oracle_per_config()
     if rank == 0:
         print(json.dumps(line))
     s32.close()

@@ -7,6 +7,7 @@ lattice Boltzmann relaxation scheme itself; both the CUDA path and the CPU
 oracle convert the primitive fields to conserved variables on their own.
 """
 from .generators import (  # noqa: F401
+    CONFIG_NAMES,
     GAMMA,
     Workload1D,
     Workload2D,
@@ -18,6 +19,8 @@ from .generators import (  # noqa: F401
     bouchut_speed,
     explosion,
     forward_facing_step,
+    from_config,
+    load_config,
     normal_shock_state,
     shock_diffraction,
     lambda_1d_riemann,

@@ -19,7 +19,9 @@ times a safety factor.
 """
 from __future__ import annotations
 
+import json
 import math
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -523,3 +525,25 @@ def burgers_steady_exact(case: int, x, y):
     xs = xf + 0.5 * (left + right) * (y - 0.5)
     u_above = np.where(x < xs, left, right)
     return np.where(below, u_below, u_above)
+
+
+# --------------------------------------------------------------------------- seeded configurations
+
+CONFIG_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "configs")
+CONFIG_NAMES = ("sod_d1q2_1000", "quadrant_riemann_1024", "oblique_shock_4096x1024", "batched_tubes_4096",
+                "adjoint_pulses_2048")
+
+
+def load_config(name: str) -> dict:
+    """The seeded configuration `name` (a JSON file under workloads/configs/)."""
+    with open(os.path.join(CONFIG_DIR, name + ".json")) as fh:
+        return json.load(fh)
+
+
+def from_config(name: str, **overrides):
+    """(configuration, workload) of a seeded configuration; keyword overrides replace its kwargs
+    (e.g. a shorter step count for a bounded sample)."""
+    cfg = load_config(name)
+    kwargs = dict(cfg["kwargs"], **overrides)
+    return cfg, globals()[cfg["generator"]](**kwargs)
+
