@@ -32,7 +32,7 @@ HERE = Path(__file__).resolve().parent
 SRC = HERE / "lbrs_oracle.c"
 LIB = HERE / "_build" / "liblbrs_oracle.so"
 
-BC_KINDS = {"periodic": 0, "transmissive": 1, "dirichlet": 2, "wall": 3}
+BC_KINDS = {"periodic": 0, "transmissive": 1, "dirichlet": 2, "wall": 3, "wall_halfway": 4}
 D1Q2, D1Q3, D2Q4, D2Q4S = 2, 3, 4, 5      # D2Q4S: the scalar 2-D inviscid Burgers law
 
 

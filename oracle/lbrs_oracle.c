@@ -37,6 +37,15 @@
  *     after streaming: at a top wall the unknown downward populations are
  *     f1 = f4, f2 = f3 (negated for the rho v field); a bottom wall mirrors
  *     it: f4 = f1, f3 = f2 (negated for rho v).  Walls exist on the y sides.
+ *   - the halfway alternative of that wall (a flag, ORC_WALL_HALFWAY): the
+ *     wall lies half a cell beyond the wall row, and a population that would
+ *     enter through it takes, by specular reflection there, the post-collision
+ *     value of its mirror image: at a bottom wall f3(i, 0) = f*2(i - 1, 0) and
+ *     f4(i, 0) = f*1(i + 1, 0), at a top wall f1(i, ny-1) = f*4(i + 1, ny-1)
+ *     and f2(i, ny-1) = f*3(i - 1, ny-1), negated for rho v; the horizontal
+ *     neighbour is resolved by the x sides like any pull source.  A domain
+ *     with such walls on both y sides is the lower half of a periodic domain
+ *     of twice the height whose upper half is its mirror image.
  *   - priority at a corner: a wall on the y side first, then a Dirichlet
  *     ghost on the x side, then a Dirichlet ghost on the y side, otherwise the
  *     source index is wrapped/clamped coordinate by coordinate.
@@ -53,7 +62,7 @@
 #include <string.h>
 #include <omp.h>
 
-enum { ORC_PERIODIC = 0, ORC_TRANSMISSIVE = 1, ORC_DIRICHLET = 2, ORC_WALL = 3 };
+enum { ORC_PERIODIC = 0, ORC_TRANSMISSIVE = 1, ORC_DIRICHLET = 2, ORC_WALL = 3, ORC_WALL_HALFWAY = 4 };
 enum { ORC_D1Q2 = 2, ORC_D1Q3 = 3, ORC_D2Q4 = 4, ORC_D2Q4S = 5 };
 
 typedef struct {
@@ -278,9 +287,10 @@ int orc_validate(const orc_params* P)
     int sides = two_d(P) ? 4 : 2;
     for (int s = 0; s < sides; ++s) {
         int kind = P->bc_kind[s];
-        if (kind < ORC_PERIODIC || kind > ORC_WALL) return 5;
-        if (kind == ORC_WALL && P->lattice == ORC_D2Q4S) return 11;   /* no wall rule for a scalar */
-        if (kind == ORC_WALL && s < 2) return 6;              /* walls on the y sides only */
+        if (kind < ORC_PERIODIC || kind > ORC_WALL_HALFWAY) return 5;
+        if ((kind == ORC_WALL || kind == ORC_WALL_HALFWAY) && P->lattice == ORC_D2Q4S) return 11;   /* no wall rule for a scalar */
+        if ((kind == ORC_WALL || kind == ORC_WALL_HALFWAY) && s < 2) return 6;   /* walls on the y sides only */
+        if (kind == ORC_WALL_HALFWAY && P->solid) return 13;  /* not combined with internal walls */
         if (kind == ORC_PERIODIC && P->bc_kind[s ^ 1] != ORC_PERIODIC) return 7;
     }
     if (P->lattice == ORC_D2Q4 && (P->bc_kind[2] == ORC_WALL || P->bc_kind[3] == ORC_WALL) && P->ny < 2)
@@ -441,6 +451,23 @@ int orc_stream(const orc_params* P, const double* fs, double* f)
                 const double* g = NULL;
                 if (side_y >= 0 && P->bc_kind[side_y] == ORC_WALL) {
                     wall_pop[q] = 1;          /* set below from the wall relation */
+                    continue;
+                }
+                if (side_y >= 0 && P->bc_kind[side_y] == ORC_WALL_HALFWAY) {
+                    /* the mirror image of this population (sy reversed) leaving the
+                     * horizontal neighbour on the wall row (x resolved as a pull source) */
+                    const int m = 3 - q;
+                    const double* gm = NULL;
+                    if (side_x >= 0) {
+                        int kind = P->bc_kind[side_x];
+                        if (kind == ORC_DIRICHLET) gm = ghost[side_x];
+                        else if (kind == ORC_PERIODIC) si = (si + nx) % nx;
+                        else si = si < 0 ? 0 : nx - 1;
+                    }
+                    for (int k = 0; k < K; ++k) {
+                        double sgn = (k == 2) ? -1.0 : 1.0;
+                        f[(q * K + k) * N + c] = sgn * (gm ? gm[m * K + k] : fs[(m * K + k) * N + j * nx + si]);
+                    }
                     continue;
                 }
                 if (side_x >= 0) {

@@ -77,6 +77,13 @@ MUTANTS = {
         "                    f[(1 * K + k) * N + c] = sgn * f[(2 * K + k) * N + c];",
         "f[(0 * K + k) * N + c] = sgn * f[(2 * K + k) * N + c];\n"
         "                    f[(1 * K + k) * N + c] = sgn * f[(3 * K + k) * N + c];"),
+    # halfway wall
+    "halfway_wall_wrong_neighbour": ("const int m = 3 - q;\n                    const double* gm = NULL;",
+                                     "const int m = 3 - q;\n                    const double* gm = NULL;\n"
+                                     "                    si = i + sx;"),
+    "halfway_wall_keeps_rho_v_sign": ("f[(q * K + k) * N + c] = sgn * (gm ? gm[m * K + k]",
+                                      "f[(q * K + k) * N + c] = 1.0 * (gm ? gm[m * K + k]"),
+    "halfway_wall_same_population": ("const int m = 3 - q;", "const int m = q ^ 1;"),
     "adjoint_relaxation_weights_swapped": ("gout[(q * 4 + k) * N + tj * nx + ti] = om1 * gq[q * 4 + k] + om * ubar[k];",
                                            "gout[(q * 4 + k) * N + tj * nx + ti] = om * gq[q * 4 + k] + om1 * ubar[k];"),
 }
@@ -99,6 +106,7 @@ def test_pins_catch_mutant(name, tmp_path):
                         os.path.join(ROOT, "tests", "test_oracle_adjoint.py"),
                         os.path.join(ROOT, "tests", "test_oracle_obstacles.py"),
                         os.path.join(ROOT, "tests", "test_oracle_burgers.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_adaptive.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_adaptive.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_halfway.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"pins did not catch mutant {name}:\n{r.stdout[-2000:]}"
