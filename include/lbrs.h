@@ -108,13 +108,23 @@ typedef enum { LBRS_F64 = 0, LBRS_F32 = 1, LBRS_F16NEQ = 2, LBRS_F32U = 3 } lbrs
  *   WALL         free-slip wall on a y side (D2Q4 only), applied on the wall row;
  *   CUT          a y side (D2Q4; LBRS_F64, LBRS_F32 or LBRS_F32U) where this context's rows
  *                meet a neighbouring context's rows: the context is one y-slab of a larger
- *                grid (see lbrs_halo_export below). */
+ *                grid (see lbrs_halo_export below);
+ *   WALL_HALFWAY the halfway alternative of the free-slip wall (a y side of D2Q4 in LBRS_F64
+ *                or LBRS_F32; not with internal walls): the wall lies half a cell beyond the
+ *                wall row, and a population that would enter through it takes, by specular
+ *                reflection there, the post-collision value of its mirror image leaving the
+ *                horizontal neighbour on the wall row, rho v negated -- bottom:
+ *                f3(i, 0) = f*2(i - 1, 0), f4(i, 0) = f*1(i + 1, 0); top:
+ *                f1(i, ny-1) = f*4(i + 1, ny-1), f2(i, ny-1) = f*3(i - 1, ny-1); the neighbour's
+ *                x is resolved like a pull source.  A grid with it on both y sides is the lower
+ *                half of a periodic grid of twice the height holding its mirror image. */
 typedef enum {
     LBRS_BC_PERIODIC = 0,
     LBRS_BC_TRANSMISSIVE = 1,
     LBRS_BC_DIRICHLET = 2,
     LBRS_BC_WALL = 3,
-    LBRS_BC_CUT = 4
+    LBRS_BC_CUT = 4,
+    LBRS_BC_WALL_HALFWAY = 5
 } lbrs_bc_kind;
 
 /* Kind of the fields passed to lbrs_set_state. */

@@ -18,12 +18,13 @@ LIB_PATH = PKG / "liblbrs.so"
 LBRS_OK, LBRS_EINVAL, LBRS_ENOMEM, LBRS_ECUDA, LBRS_ENONPHYS, LBRS_ESUBCHAR, LBRS_ETIMEOUT, LBRS_ESTATE = range(8)
 LBRS_D1Q2, LBRS_D2Q4, LBRS_D1Q3, LBRS_D2Q4S = 0, 1, 2, 3
 LBRS_F64, LBRS_F32, LBRS_F16NEQ, LBRS_F32U = 0, 1, 2, 3
-LBRS_BC_PERIODIC, LBRS_BC_TRANSMISSIVE, LBRS_BC_DIRICHLET, LBRS_BC_WALL, LBRS_BC_CUT = 0, 1, 2, 3, 4
+LBRS_BC_PERIODIC, LBRS_BC_TRANSMISSIVE, LBRS_BC_DIRICHLET, LBRS_BC_WALL, LBRS_BC_CUT, LBRS_BC_WALL_HALFWAY = range(6)
 LBRS_CONSERVED, LBRS_PRIMITIVE = 0, 1
 ABI_VERSION = 1
 
 BC_KINDS = {"periodic": LBRS_BC_PERIODIC, "transmissive": LBRS_BC_TRANSMISSIVE,
-            "dirichlet": LBRS_BC_DIRICHLET, "wall": LBRS_BC_WALL, "cut": LBRS_BC_CUT}
+            "dirichlet": LBRS_BC_DIRICHLET, "wall": LBRS_BC_WALL, "cut": LBRS_BC_CUT,
+            "wall_halfway": LBRS_BC_WALL_HALFWAY}
 
 
 class lbrs_bc(ctypes.Structure):

@@ -62,7 +62,9 @@ static __device__ __forceinline__ int64_t debug_index(int64_t i, int64_t n, int 
     unsigned long long name(int) { return 0ull; }
 #endif
 
-enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_DIRICHLET = 2, BC_WALL = 3 };
+// BC_WALL_HALFWAY has the code of LBRS_BC_WALL_HALFWAY (a cut side reaches the kernels as
+// BC_TRANSMISSIVE).
+enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_DIRICHLET = 2, BC_WALL = 3, BC_WALL_HALFWAY = 5 };
 // LAT_U2D: a D2Q4 state stored as its moments U directly (the FP16
 // non-equilibrium form keeps U in FP32): read-outs treat it as one
 // "population" per field.
@@ -221,6 +223,11 @@ __device__ __forceinline__ void prim_to_cons1d(const double w[3], double gamma, 
 // Priority: a wall on the y side; a Dirichlet ghost on the x side; a Dirichlet
 // ghost on the y side; otherwise wrap (periodic) / clamp (transmissive) each
 // coordinate.  Then the free-slip wall relations (Section II.E).
+// A halfway wall (the flag alternative of that wall, reflecting at the plane half a
+// cell beyond the wall row): a population that would enter through it takes the
+// mirror image (sy reversed, m = 3 - q) of the one leaving its horizontal neighbour
+// (i - sx, j) on the wall row, rho v negated; the neighbour's x is resolved like a
+// pull source (Dirichlet ghost, wrap, clamp).
 template <typename T>
 __device__ __forceinline__ void pull_edge_2d(const StepArgs<T>& a, int i, int j, T f[4][4])
 {
@@ -238,6 +245,22 @@ __device__ __forceinline__ void pull_edge_2d(const StepArgs<T>& a, int i, int j,
         const int kind_x = side_x == 0 ? a.bc[0] : a.bc[1];
         if (side_y >= 0 && kind_y == BC_WALL) {
             if (side_y == 3) wall_top = true; else wall_bottom = true;
+            continue;
+        }
+        if (side_y >= 0 && kind_y == BC_WALL_HALFWAY) {
+            const int m = 3 - q;
+            const T* gm = nullptr;
+            if (side_x >= 0) {
+                if (kind_x == BC_DIRICHLET) gm = a.ghost + side_x * GHOST_STRIDE + m * 4;
+                else if (kind_x == BC_PERIODIC) si = si < 0 ? si + a.nx : si - a.nx;
+                else si = si < 0 ? 0 : a.nx - 1;
+            }
+            const int64_t s = (int64_t)j * a.nx + si;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const T sgn = k == 2 ? T(-1) : T(1);
+                f[q][k] = sgn * (gm ? gm[k] : a.src[LBRS_IX((m * 4 + k) * a.N + s, 16 * a.N, 1)]);
+            }
             continue;
         }
         const T* g = nullptr;

@@ -266,6 +266,23 @@ __device__ __forceinline__ void step2_phase2(const StepArgs<float>& a, const flo
             if (side_y == 3) wall_top = true; else wall_bottom = true;
             continue;
         }
+        if (side_y >= 0 && kind_y == BC_WALL_HALFWAY) {
+            // the mirror image of this population leaving the horizontal neighbour on the wall
+            // row (a periodic neighbour keeps its unwrapped slot, which holds the wrapped cell)
+            const int m = 3 - q;
+            const float* gm = nullptr;
+            if (side_x >= 0) {
+                if (kind_x == BC_DIRICHLET) gm = a.ghost + side_x * GHOST_STRIDE + m * 4;
+                else if (kind_x != BC_PERIODIC) si = si < 0 ? 0 : a.nx - 1;
+            }
+            const int slot = (j - (j0 - 1)) * kFWX + (si - (i0 - 1));
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float sgn = k == 2 ? -1.f : 1.f;
+                f[q][k] = sgn * (gm ? gm[k] : s_f[LBRS_IX((m * 4 + k) * kFWN + slot, 16 * kFWN, 12)]);
+            }
+            continue;
+        }
         const float* g = nullptr;
         if (side_x >= 0) {
             if (kind_x == BC_DIRICHLET) g = a.ghost + side_x * GHOST_STRIDE + q * 4;
@@ -546,6 +563,22 @@ __device__ __forceinline__ void tall_phase2(const StepArgs<float>& a, const floa
         const int kind_x = side_x == 0 ? a.bc[0] : a.bc[1];
         if (side_y >= 0 && kind_y == BC_WALL) {
             if (side_y == 3) wall_top = true; else wall_bottom = true;
+            continue;
+        }
+        if (side_y >= 0 && kind_y == BC_WALL_HALFWAY) {
+            // the mirror image of this population leaving the horizontal neighbour on the wall
+            // row (a periodic neighbour keeps its unwrapped slot, which holds the wrapped cell)
+            const int m = 3 - q;
+            const float* gm = nullptr;
+            if (side_x >= 0) {
+                if (kind_x == BC_DIRICHLET) gm = a.ghost + side_x * GHOST_STRIDE + m * 4;
+                else if (kind_x != BC_PERIODIC) si = si < 0 ? 0 : a.nx - 1;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float sgn = k == 2 ? -1.f : 1.f;
+                f[q][k] = sgn * (gm ? gm[k] : s_f[LBRS_IX(tall_pos(m, k, si - (i0 - 1), j - (j0 - 1)), 16 * kTPN, 17)]);
+            }
             continue;
         }
         const float* g = nullptr;

@@ -190,8 +190,12 @@ lbrs_status validate(const lbrs_config* c)
     const int sides = two_d(c->lattice) ? 4 : 2;
     for (int s = 0; s < sides; ++s) {
         const int kind = c->bc[s].kind;
-        if (kind < LBRS_BC_PERIODIC || kind > LBRS_BC_CUT)
+        if (kind < LBRS_BC_PERIODIC || kind > LBRS_BC_WALL_HALFWAY)
             return fail(nullptr, LBRS_EINVAL, "side %d: unknown boundary kind %d", s, kind);
+        if (kind == LBRS_BC_WALL_HALFWAY &&
+            (c->lattice != LBRS_D2Q4 || s < 2 || (c->precision != LBRS_F64 && c->precision != LBRS_F32)))
+            return fail(nullptr, LBRS_EINVAL,
+                        "side %d: halfway walls are defined on the y sides of D2Q4 in LBRS_F64 or LBRS_F32", s);
         if (kind == LBRS_BC_CUT) {
             if (c->lattice != LBRS_D2Q4 || s < 2)
                 return fail(nullptr, LBRS_EINVAL, "side %d: cuts are defined on the y sides of D2Q4 only", s);
@@ -915,6 +919,8 @@ lbrs_status lbrs_set_obstacles(lbrs_ctx* ctx, const uint8_t* d_solid)
         if (ctx->lattice != LBRS_D2Q4 || ctx->f16 || ctx->f32u)
             return fail(ctx, LBRS_EINVAL, "internal walls cover the F64 and F32 D2Q4 forms");
         if (ctx->halo[0] || ctx->halo[1]) return fail(ctx, LBRS_EINVAL, "internal walls are not covered on cut grids");
+        if (ctx->cfg.bc[2].kind == LBRS_BC_WALL_HALFWAY || ctx->cfg.bc[3].kind == LBRS_BC_WALL_HALFWAY)
+            return fail(ctx, LBRS_EINVAL, "internal walls are not combined with halfway walls");
         std::vector<uint8_t> m((size_t)ctx->N);
         LBRS_CUDA(ctx, cudaMemcpyAsync(m.data(), d_solid, m.size(), cudaMemcpyDeviceToHost, ctx->stream));
         LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));

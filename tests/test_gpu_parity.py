@@ -72,6 +72,11 @@ BC_SETS = {
     "walls_periodic_x": [("periodic", None), ("periodic", None), ("wall", None), ("wall", None)],
     "mixed": [("transmissive", None), ("dirichlet", (1.0, -0.3, 0.2, 0.7)), ("dirichlet", (0.8, 0.1, 0.4, 0.9)),
               ("transmissive", None)],
+    # the halfway alternative of the free-slip wall, against a Dirichlet x side (corner resolution)
+    # and against the on-node wall on the other y side
+    "halfway_dirichlet": [("dirichlet", (1.2, 0.8, 0.1, 1.0)), ("transmissive", None), ("wall_halfway", None),
+                          ("wall", None)],
+    "halfway_periodic_x": [("periodic", None), ("periodic", None), ("wall_halfway", None), ("wall_halfway", None)],
 }
 
 
@@ -100,7 +105,7 @@ def small_case(nx, ny, bcname, omega, steps=60, seed=0):
 @pytest.mark.parametrize("omega", [1.0, 1.6])
 def test_f64_matches_oracle_small_2d(bcname, shape, omega):
     nx, ny = shape
-    if bcname in ("periodic", "walls_periodic_x") and (nx % 2 or ny % 2):
+    if bcname in ("periodic", "walls_periodic_x", "halfway_periodic_x") and (nx % 2 or ny % 2):
         nx += nx % 2
         ny += ny % 2
     wl = small_case(nx, ny, bcname, omega)
@@ -110,7 +115,7 @@ def test_f64_matches_oracle_small_2d(bcname, shape, omega):
     assert np.max(np.abs(fs - fs_ref)) <= F64_TOL * np.max(np.abs(fs_ref))
 
 
-@pytest.mark.parametrize("bcname", ["transmissive", "dirichlet_wall", "periodic"])
+@pytest.mark.parametrize("bcname", ["transmissive", "dirichlet_wall", "periodic", "halfway_dirichlet"])
 def test_f32_close_to_oracle_small_2d(bcname):
     wl = small_case(160, 96, bcname, 1.0, steps=100)
     U_ref, _, _ = run_oracle(wl)
@@ -311,7 +316,7 @@ def test_errors_state_and_arguments():
 def test_f32_matches_oracle_every_boundary(bcname, shape):
     """FP32 path (vectorised kernel where nx % 4 == 0, scalar otherwise) close to the FP64 oracle."""
     nx, ny = shape
-    if bcname in ("periodic", "walls_periodic_x") and (nx % 2 or ny % 2):
+    if bcname in ("periodic", "walls_periodic_x", "halfway_periodic_x") and (nx % 2 or ny % 2):
         ny += ny % 2
     wl = small_case(nx, ny, bcname, 1.3, steps=60)
     U_ref, _, _ = run_oracle(wl)
@@ -332,7 +337,9 @@ D = [("dirichlet", (1.0, 0.5, 0.1, 1.0)), ("dirichlet", (0.8, -0.2, 0.0, 0.9))]
 T = ("transmissive", None)
 P = ("periodic", None)
 Wl = ("wall", None)
-for bc in ([T] * 4, [P] * 4, D + [T, T], [T, D[1], Wl, D[0]], [P, P, Wl, Wl], [D[0], T, D[1], Wl]):
+Hw = ("wall_halfway", None)
+for bc in ([T] * 4, [P] * 4, D + [T, T], [T, D[1], Wl, D[0]], [P, P, Wl, Wl], [D[0], T, D[1], Wl], [P, P, Hw, Hw],
+           [D[0], T, Hw, Wl]):
     wl = W.quadrant_riemann(1, 64, steps=50)
     for nx, ny in ((256, 48), (64, 48), (12, 48), (37, 29), (66, 17), (5, 3), (1, 9), (33, 1)):
         if bc[0] == P and nx % 2:
