@@ -227,8 +227,9 @@ __device__ __forceinline__ void prim_to_cons1d(const double w[3], double gamma, 
 // cell beyond the wall row): a population that would enter through it takes the
 // mirror image (sy reversed, m = 3 - q) of the one leaving its horizontal neighbour
 // (i - sx, j) on the wall row, rho v negated; the neighbour's x is resolved like a
-// pull source (Dirichlet ghost, wrap, clamp).
-template <typename T>
+// pull source (Dirichlet ghost, wrap, clamp).  HALF = false compiles the pull without
+// that case, for kernels on a tight register budget that are not launched with it.
+template <typename T, bool HALF = true>
 __device__ __forceinline__ void pull_edge_2d(const StepArgs<T>& a, int i, int j, T f[4][4])
 {
     const int SX[4] = {-1, 1, 1, -1};
@@ -247,7 +248,7 @@ __device__ __forceinline__ void pull_edge_2d(const StepArgs<T>& a, int i, int j,
             if (side_y == 3) wall_top = true; else wall_bottom = true;
             continue;
         }
-        if (side_y >= 0 && kind_y == BC_WALL_HALFWAY) {
+        if (HALF && side_y >= 0 && kind_y == BC_WALL_HALFWAY) {
             const int m = 3 - q;
             const T* gm = nullptr;
             if (side_x >= 0) {

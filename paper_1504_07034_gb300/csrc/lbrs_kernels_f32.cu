@@ -234,7 +234,7 @@ __device__ __forceinline__ int wrap_index(int x, int n)
 // Phase 2 of the two-step kernels: step n+1 -> n+2 for the tile (i0, j0), pulling
 // from the window of post-collision populations in shared memory.
 // STORE_U: a.Uout receives the moments of this (second) step.
-template <bool STORE_U>
+template <bool STORE_U, bool HALF>
 __device__ __forceinline__ void step2_phase2(const StepArgs<float>& a, const float* s_f, int i0, int j0)
 {
     const int ti = threadIdx.x % kFTX, tj = threadIdx.x / kFTX;
@@ -266,7 +266,7 @@ __device__ __forceinline__ void step2_phase2(const StepArgs<float>& a, const flo
             if (side_y == 3) wall_top = true; else wall_bottom = true;
             continue;
         }
-        if (side_y >= 0 && kind_y == BC_WALL_HALFWAY) {
+        if (HALF && side_y >= 0 && kind_y == BC_WALL_HALFWAY) {
             // the mirror image of this population leaving the horizontal neighbour on the wall
             // row (a periodic neighbour keeps its unwrapped slot, which holds the wrapped cell)
             const int m = 3 - q;
@@ -345,7 +345,7 @@ __device__ __forceinline__ StepArgs<float> second_step_args(const StepArgs<float
     return b;
 }
 
-template <bool STORE_U>
+template <bool STORE_U, bool HALF>
 __global__ void __launch_bounds__(kFTX * kFTY, 4) step2d_f32_fused2_kernel(const StepArgs<float> a)
 {
     __shared__ float s_f[16 * kFWN];
@@ -372,7 +372,7 @@ __global__ void __launch_bounds__(kFTX * kFTY, 4) step2d_f32_fused2_kernel(const
 #pragma unroll
                 for (int k = 0; k < 4; ++k) f[q][k] = a.src[LBRS_IX((q * 4 + k) * a.N + src[q], 16 * a.N, 10)];
         } else {
-            pull_edge_2d<float>(a, i, j, f);
+            pull_edge_2d<float, HALF>(a, i, j, f);
         }
         float U[4], out[4][4];
         collide_2d<float>(a, f, U, out);
@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(kFTX * kFTY, 4) step2d_f32_fused2_kernel(const
     }
     __syncthreads();
 
-    step2_phase2<STORE_U>(second_step_args(a, STORE_U), s_f, i0, j0);
+    step2_phase2<STORE_U, HALF>(second_step_args(a, STORE_U), s_f, i0, j0);
 }
 
 // ---------------------------------------------------------------- two steps per launch, TMA-fed
@@ -487,7 +487,7 @@ __device__ __forceinline__ void tall_store_slot(const StepArgs<float>& a, float*
 }
 
 // Phase 1 on the 34 x 18 window, in place.
-template <bool STORE_U>
+template <bool STORE_U, bool HALF>
 __device__ __forceinline__ void tall_phase1(const StepArgs<float>& a, float* s_raw, int i0, int j0)
 {
     if (i0 >= 2 && j0 >= 2 && i0 + kFTX + 2 <= a.nx && j0 + kTY + 2 <= a.ny) {
@@ -525,7 +525,7 @@ __device__ __forceinline__ void tall_phase1(const StepArgs<float>& a, float* s_r
 #pragma unroll
                 for (int k = 0; k < 4; ++k) f[q][k] = s_raw[LBRS_IX(tall_pos(q, k, wi, wj), 16 * kTPN, 16)];
         } else {
-            pull_edge_2d<float>(a, i, j, f);
+            pull_edge_2d<float, HALF>(a, i, j, f);
         }
         float U[4], out[4][4];
         collide_2d<float>(a, f, U, out);
@@ -534,7 +534,7 @@ __device__ __forceinline__ void tall_phase1(const StepArgs<float>& a, float* s_r
 }
 
 // Phase 2 for tile cell (ti, tj), pulling from the window in the boxes.
-template <bool STORE_U>
+template <bool STORE_U, bool HALF>
 __device__ __forceinline__ void tall_phase2(const StepArgs<float>& a, const float* s_f, int i0, int j0, int ti, int tj)
 {
     const int i = i0 + ti, j = j0 + tj;
@@ -565,7 +565,7 @@ __device__ __forceinline__ void tall_phase2(const StepArgs<float>& a, const floa
             if (side_y == 3) wall_top = true; else wall_bottom = true;
             continue;
         }
-        if (side_y >= 0 && kind_y == BC_WALL_HALFWAY) {
+        if (HALF && side_y >= 0 && kind_y == BC_WALL_HALFWAY) {
             // the mirror image of this population leaving the horizontal neighbour on the wall
             // row (a periodic neighbour keeps its unwrapped slot, which holds the wrapped cell)
             const int m = 3 - q;
@@ -784,7 +784,7 @@ __device__ __forceinline__ void tall_phase2_obst(const StepArgs<float>& a, const
 // 1024^2 grid, 10 % less throughput on large grids); blocks reused for further
 // tiles with the next copy issued early (fewer resident warps); L2 prefetch of
 // later tiles (evicts halo rows still to be read).
-template <bool STORE_U, bool OBST = false>
+template <bool STORE_U, bool OBST = false, bool HALF = false>
 __global__ void __launch_bounds__(kFTX * kFTY, 5)
     step2d_f32_fused2_tall_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs<float> a,
                                   unsigned* wait_flag)
@@ -818,11 +818,11 @@ __global__ void __launch_bounds__(kFTX * kFTY, 5)
         tall_phase2_obst(a, s_raw, s_m, i0, j0, ti, tj + kFTY);
         return;
     }
-    tall_phase1<STORE_U>(a, s_raw, i0, j0);
+    tall_phase1<STORE_U, HALF>(a, s_raw, i0, j0);
     __syncthreads();
     const StepArgs<float> b = second_step_args(a, STORE_U);
-    tall_phase2<STORE_U>(b, s_raw, i0, j0, ti, tj);
-    tall_phase2<STORE_U>(b, s_raw, i0, j0, ti, tj + kFTY);
+    tall_phase2<STORE_U, HALF>(b, s_raw, i0, j0, ti, tj);
+    tall_phase2<STORE_U, HALF>(b, s_raw, i0, j0, ti, tj + kFTY);
 }
 
 // Failure-detection self-test: one block waits, with the tile kernels' bounded wait,
@@ -1280,6 +1280,12 @@ bool encode_f32_tile_map(TileMap* map, const float* f, int64_t nx, int64_t ny)
         if (attr_err == cudaSuccess)
             attr_err = cudaFuncSetAttribute(step2d_f32_fused2_tall_kernel<false, true>,
                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTallObstSmemBytes);
+        if (attr_err == cudaSuccess)
+            attr_err = cudaFuncSetAttribute(step2d_f32_fused2_tall_kernel<false, false, true>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTallSmemBytes);
+        if (attr_err == cudaSuccess)
+            attr_err = cudaFuncSetAttribute(step2d_f32_fused2_tall_kernel<true, false, true>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTallSmemBytes);
     });
     if (attr_err != cudaSuccess) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, 16};
@@ -1299,24 +1305,32 @@ bool encode_f32_tile_map(TileMap* map, const float* f, int64_t nx, int64_t ny)
 cudaError_t launch_step2_f32(const StepArgs<float>& a, const TileMap* map, unsigned* wait_flag, cudaStream_t s)
 {
     const bool rec = a.Uout != nullptr;
+    const bool half = a.bc[2] == BC_WALL_HALFWAY || a.bc[3] == BC_WALL_HALFWAY;   // the variants that resolve it
     if (map && map->valid && wait_flag) {
         CUtensorMap m;
         memcpy(&m, map->bytes, sizeof m);
         const dim3 grid((unsigned)((a.nx + kFTX - 1) / kFTX), (unsigned)((a.ny + kTY - 1) / kTY));
         if (a.solid) {
-            if (rec) return cudaErrorInvalidValue;   // the recording form has no internal walls
+            if (rec || half) return cudaErrorInvalidValue;   // no recording form or halfway walls with obstacles
             step2d_f32_fused2_tall_kernel<false, true><<<grid, kFTX * kFTY, kTallObstSmemBytes, s>>>(m, a, wait_flag);
         } else if (rec) {
-            step2d_f32_fused2_tall_kernel<true><<<grid, kFTX * kFTY, kTallSmemBytes, s>>>(m, a, wait_flag);
+            if (half) step2d_f32_fused2_tall_kernel<true, false, true><<<grid, kFTX * kFTY, kTallSmemBytes, s>>>(m, a, wait_flag);
+            else step2d_f32_fused2_tall_kernel<true><<<grid, kFTX * kFTY, kTallSmemBytes, s>>>(m, a, wait_flag);
         } else {
-            step2d_f32_fused2_tall_kernel<false><<<grid, kFTX * kFTY, kTallSmemBytes, s>>>(m, a, wait_flag);
+            if (half) step2d_f32_fused2_tall_kernel<false, false, true><<<grid, kFTX * kFTY, kTallSmemBytes, s>>>(m, a, wait_flag);
+            else step2d_f32_fused2_tall_kernel<false><<<grid, kFTX * kFTY, kTallSmemBytes, s>>>(m, a, wait_flag);
         }
     } else if (a.solid) {
         return cudaErrorInvalidValue;                // internal walls need the tensor-copy form
     } else {
         const dim3 grid((unsigned)((a.nx + kFTX - 1) / kFTX), (unsigned)((a.ny + kFTY - 1) / kFTY));
-        if (rec) step2d_f32_fused2_kernel<true><<<grid, kFTX * kFTY, 0, s>>>(a);
-        else step2d_f32_fused2_kernel<false><<<grid, kFTX * kFTY, 0, s>>>(a);
+        if (rec) {
+            if (half) step2d_f32_fused2_kernel<true, true><<<grid, kFTX * kFTY, 0, s>>>(a);
+            else step2d_f32_fused2_kernel<true, false><<<grid, kFTX * kFTY, 0, s>>>(a);
+        } else {
+            if (half) step2d_f32_fused2_kernel<false, true><<<grid, kFTX * kFTY, 0, s>>>(a);
+            else step2d_f32_fused2_kernel<false, false><<<grid, kFTX * kFTY, 0, s>>>(a);
+        }
     }
     return cudaGetLastError();
 }
