@@ -352,9 +352,10 @@ lbrs_status lbrs_set_obstacles(lbrs_ctx* ctx, const uint8_t* d_solid);
  *   - a slab's own rows evolve bit for bit as the same rows of the unsplit grid
  *     do (same kernels, same per-cell arithmetic), provided that every import
  *     carries the neighbour's rows of the same step number.
- * Not covered on cut grids (LBRS_EINVAL): internal walls, the adaptive lambda,
- * recording steps and the adjoint.  The diagnostics totals of the slabs add up to
- * the unsplit grid's up to the order of the FP64 additions.
+ * Not covered on cut grids (LBRS_EINVAL): internal walls, the adaptive lambda and
+ * the checkpointed adjoint driver; the adjoint steps themselves are (see
+ * lbrs_rows_export).  The diagnostics totals of the slabs add up to the unsplit grid's
+ * up to the order of the FP64 additions.
  *
  * lbrs_halo_size: the rows H of a cut side (2 = y-lo, 3 = y-hi; 0 rows if the side is
  *   not a cut) and the bytes of one exchanged block: P planes x H rows x nx cells in
@@ -372,6 +373,26 @@ lbrs_status lbrs_halo_size(const lbrs_ctx* ctx, int side, int64_t* rows, size_t*
 lbrs_status lbrs_halo_export(lbrs_ctx* ctx, int side, void* dst, int on_device);
 lbrs_status lbrs_halo_import(lbrs_ctx* ctx, int side, const void* src, int on_device);
 
+/* The adjoint on y-slabs of a periodic grid (x periodic, y sides cut): the reverse halo.
+ * On such a context the adjoint calls below (lbrs_step_record, lbrs_adjoint_seed,
+ * lbrs_vjp_loss, lbrs_adjoint_step, lbrs_vjp_equilibrium) take their buffers in the stored
+ * layout: [planes][ny_s][nx] with ny_s = ny plus the ghost rows of both cuts and own row 0 at
+ * stored row row0 (lbrs_store_rows).  The adjoint step pulls, for row j, from rows j - 1 and
+ * j + 1 (the transpose of the streaming moves the same rows the other way), and its kernels
+ * wrap the stored rows in y, which spoils ghost rows only; so H adjoint steps give exact own
+ * rows when the ghost rows of the adjoint state and of the H recorded moment fields they use
+ * hold the neighbours' rows.  lbrs_rows_export copies the H own rows next to cut `side` of a
+ * stored-layout buffer (planes planes in the storage precision, e.g. 16 for dL/df*, 4 T for T
+ * recorded steps of moments) to a block [planes][H][nx]; lbrs_rows_import writes such a block,
+ * exported by the neighbour across `side`, into the buffer's ghost rows.  Memory and stream
+ * rules as for lbrs_halo_export / lbrs_halo_import; no state needs to be set.  Recording steps follow the same import rule
+ * as lbrs_step (LBRS_ESTATE beyond what the imports cover); lbrs_vjp_loss sums the own rows
+ * only (the grid's loss is the sum over the slabs); the checkpointed driver below is not
+ * covered on cut grids (it would step without the neighbours' rows: LBRS_EINVAL). */
+lbrs_status lbrs_store_rows(const lbrs_ctx* ctx, int64_t* ny_store, int64_t* row0);
+lbrs_status lbrs_rows_export(lbrs_ctx* ctx, int side, const void* d_buf, int planes, void* dst, int on_device);
+lbrs_status lbrs_rows_import(lbrs_ctx* ctx, int side, void* d_buf, int planes, const void* src, int on_device);
+
 /* ---------------------------------------------------------------- adjoint
  *
  * Discrete adjoint of the D2Q4 step on a fully periodic domain.  The paper
@@ -383,8 +404,10 @@ lbrs_status lbrs_halo_import(lbrs_ctx* ctx, int side, const void* src, int on_de
  *             dL/df*^n_q(x - c_q) = fbar_q(x)       (gbar = dL/df*^{n+1})
  * with J_E the Jacobian of the equilibria (through the ideal-gas Euler flux
  * Jacobians).  Buffers are device memory in the storage precision unless a
- * dtype is given; distributions are [4][4][ny][nx], fields [4][ny][nx].
- * Non-periodic or D1Q2 contexts get LBRS_EINVAL. */
+ * dtype is given; distributions are [4][4][ny][nx], fields [4][ny][nx] (on a
+ * y-slab context, the stored layout: see lbrs_rows_export above).
+ * Contexts that are neither periodic nor a y-slab of a periodic grid, and D1Q2
+ * contexts, get LBRS_EINVAL. */
 
 /* Enqueue n steps like lbrs_step, also writing each step's moments U^{s+m+1}
  * (the U its collision used) to d_U_hist + m*K*N elements, m = 0..n-1. */

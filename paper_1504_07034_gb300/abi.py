@@ -112,6 +112,9 @@ SIGNATURES = {
                                       ctypes.POINTER(ctypes.c_size_t)]),
     "lbrs_halo_export": (ctypes.c_int, [_CTX, ctypes.c_int, _P, ctypes.c_int]),
     "lbrs_halo_import": (ctypes.c_int, [_CTX, ctypes.c_int, _P, ctypes.c_int]),
+    "lbrs_store_rows": (ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    "lbrs_rows_export": (ctypes.c_int, [_CTX, ctypes.c_int, _P, ctypes.c_int, _P, ctypes.c_int]),
+    "lbrs_rows_import": (ctypes.c_int, [_CTX, ctypes.c_int, _P, ctypes.c_int, _P, ctypes.c_int]),
     "lbrs_step_count": (ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_int64)]),
     "lbrs_launch_count": (ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_int64)]),
     "lbrs_last_error": (ctypes.c_char_p, [_CTX]),

@@ -301,18 +301,19 @@ __global__ void __launch_bounds__(kThreads) adjoint_seed_kernel(int Q, int K, co
 template <typename Ts, typename Tt>
 __global__ void __launch_bounds__(kThreads) density_loss_kernel(int Q, int K, const Ts* __restrict__ fs,
                                                                 const Tt* __restrict__ target, Ts* __restrict__ gbar,
-                                                                int64_t N, double cell, double* __restrict__ partials)
+                                                                int64_t N, int64_t P, double cell,
+                                                                double* __restrict__ partials)
 {
     double acc = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         double rho = (double)fs[i];
-        for (int q = 1; q < Q; ++q) rho += (double)fs[(q * K) * N + i];
+        for (int q = 1; q < Q; ++q) rho += (double)fs[(q * K) * P + i];
         const double r = rho - (double)target[i];
         acc += 0.5 * r * r;
         const Ts g = (Ts)(r * cell);
         for (int q = 0; q < Q; ++q) {
-            gbar[(q * K) * N + i] = g;
-            for (int k = 1; k < K; ++k) gbar[(q * K + k) * N + i] = (Ts)0;
+            gbar[(q * K) * P + i] = g;
+            for (int k = 1; k < K; ++k) gbar[(q * K + k) * P + i] = (Ts)0;
         }
     }
 #pragma unroll
@@ -516,16 +517,16 @@ cudaError_t launch_adjoint_seed(int Q, int K, int storage_f64, const void* dLdU,
 }
 
 cudaError_t launch_density_loss(int Q, int K, int storage_f64, const void* fs, const void* target, int t_dtype,
-                                void* gbar, int64_t N, double cell_volume, double* partials, double* out,
+                                void* gbar, int64_t N, int64_t plane, double cell_volume, double* partials, double* out,
                                 cudaStream_t s)
 {
     const int g = kDiagBlocks;
     if (storage_f64) {
-        if (t_dtype == 0) density_loss_kernel<double, double><<<g, kThreads, 0, s>>>(Q, K, (const double*)fs, (const double*)target, (double*)gbar, N, cell_volume, partials);
-        else density_loss_kernel<double, float><<<g, kThreads, 0, s>>>(Q, K, (const double*)fs, (const float*)target, (double*)gbar, N, cell_volume, partials);
+        if (t_dtype == 0) density_loss_kernel<double, double><<<g, kThreads, 0, s>>>(Q, K, (const double*)fs, (const double*)target, (double*)gbar, N, plane, cell_volume, partials);
+        else density_loss_kernel<double, float><<<g, kThreads, 0, s>>>(Q, K, (const double*)fs, (const float*)target, (double*)gbar, N, plane, cell_volume, partials);
     } else {
-        if (t_dtype == 0) density_loss_kernel<float, double><<<g, kThreads, 0, s>>>(Q, K, (const float*)fs, (const double*)target, (float*)gbar, N, cell_volume, partials);
-        else density_loss_kernel<float, float><<<g, kThreads, 0, s>>>(Q, K, (const float*)fs, (const float*)target, (float*)gbar, N, cell_volume, partials);
+        if (t_dtype == 0) density_loss_kernel<float, double><<<g, kThreads, 0, s>>>(Q, K, (const float*)fs, (const double*)target, (float*)gbar, N, plane, cell_volume, partials);
+        else density_loss_kernel<float, float><<<g, kThreads, 0, s>>>(Q, K, (const float*)fs, (const float*)target, (float*)gbar, N, plane, cell_volume, partials);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

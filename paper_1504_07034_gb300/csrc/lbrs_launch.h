@@ -130,7 +130,7 @@ cudaError_t launch_adjoint_seed(int Q, int K, int storage_f64, const void* dLdU,
 // reduced in FP64 in a fixed order into out[0], and its gradient seed
 // gbar[q][0] = (rho - target) * cell_volume, gbar[q][k>0] = 0.
 cudaError_t launch_density_loss(int Q, int K, int storage_f64, const void* fs, const void* target, int t_dtype,
-                                void* gbar, int64_t N, double cell_volume, double* partials, double* out,
+                                void* gbar, int64_t N, int64_t plane, double cell_volume, double* partials, double* out,
                                 cudaStream_t s);
 
 // Batched D1Q2 / D1Q3 tubes with temporal blocking (lbrs_batch.cuh): one CTA of

@@ -409,14 +409,17 @@ lbrs_status reset_status(lbrs_ctx* ctx)
     return LBRS_OK;
 }
 
-// The adjoint covers the periodic D2Q4 step.
+// The adjoint covers the periodic D2Q4 step, and y-slabs of a periodic grid (x periodic,
+// y sides cut): its kernels wrap the stored rows in y, which spoils only ghost rows.
 lbrs_status adjoint_supported(lbrs_ctx* ctx)
 {
     if (ctx->lattice != LBRS_D2Q4) return fail(ctx, LBRS_EINVAL, "the adjoint covers D2Q4 only");
     if (ctx->f16 || ctx->f32u) return fail(ctx, LBRS_EINVAL, "the adjoint covers the F64 and F32 forms only");
-    for (int s = 0; s < 4; ++s)
-        if (ctx->cfg.bc[s].kind != LBRS_BC_PERIODIC)
-            return fail(ctx, LBRS_EINVAL, "the adjoint covers fully periodic domains only");
+    for (int s = 0; s < 4; ++s) {
+        const int kind = ctx->cfg.bc[s].kind;
+        if (kind != LBRS_BC_PERIODIC && !(s >= 2 && kind == LBRS_BC_CUT))
+            return fail(ctx, LBRS_EINVAL, "the adjoint covers periodic domains and their y-slabs only");
+    }
     if (ctx->solid) return fail(ctx, LBRS_EINVAL, "the adjoint does not cover internal walls");
     return LBRS_OK;
 }
@@ -483,7 +486,7 @@ AdjArgs<T> adj_args(const lbrs_ctx* ctx, const void* U, const void* gin, void* g
     a.gout = (T*)gout;
     a.N = ctx->N;
     a.nx = (int)ctx->cfg.nx;
-    a.ny = (int)ctx->cfg.ny;
+    a.ny = (int)ctx->ny_store;
     a.om = (T)ctx->cfg.omega;
     a.om1 = (T)(1.0 - ctx->cfg.omega);
     a.c = (T)ctx->c;
@@ -1186,13 +1189,14 @@ int64_t halo_first_row(const lbrs_ctx* ctx, int side, bool import)
     return import ? ctx->row0 + ctx->cfg.ny : ctx->row0 + ctx->cfg.ny - ctx->halo[1];
 }
 
-lbrs_status halo_args(lbrs_ctx* ctx, int side, const void* buf)
+// Arguments of the row exchanges; the state's own exchanges also need a state.
+lbrs_status halo_args(lbrs_ctx* ctx, int side, const void* buf, bool need_state = true)
 {
     if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
     if (!buf) return fail(ctx, LBRS_EINVAL, "halo buffer is NULL");
     if (side != 2 && side != 3) return fail(ctx, LBRS_EINVAL, "side must be 2 (y-lo) or 3 (y-hi), got %d", side);
     if (!ctx->halo[side - 2]) return fail(ctx, LBRS_EINVAL, "side %d is not a cut", side);
-    if (!ctx->has_state) return fail(ctx, LBRS_ESTATE, "no state set");
+    if (need_state && !ctx->has_state) return fail(ctx, LBRS_ESTATE, "no state set");
     return LBRS_OK;
 }
 }  // namespace
@@ -1206,29 +1210,64 @@ lbrs_status lbrs_halo_size(const lbrs_ctx* ctx, int side, int64_t* rows, size_t*
     return LBRS_OK;
 }
 
+namespace {
+// The H rows next to cut `side` of a buffer in the stored layout ([planes][ny_store][nx], storage
+// precision) to or from a block [planes][H][nx] elsewhere: the own rows out (export), the ghost
+// rows in (import).
+lbrs_status copy_rows(lbrs_ctx* ctx, int side, char* buf, int planes, void* block, bool import, int on_device)
+{
+    const size_t e = elem_bytes(ctx), w = (size_t)ctx->halo[side - 2] * ctx->cfg.nx * e;
+    char* rows = buf + (size_t)halo_first_row(ctx, side, import) * ctx->cfg.nx * e;
+    if (import)
+        LBRS_CUDA(ctx, cudaMemcpy2DAsync(rows, (size_t)ctx->N * e, block, w, w, (size_t)planes,
+                                         on_device ? cudaMemcpyDefault : cudaMemcpyHostToDevice, ctx->stream));
+    else
+        LBRS_CUDA(ctx, cudaMemcpy2DAsync(block, w, rows, (size_t)ctx->N * e, w, (size_t)planes,
+                                         on_device ? cudaMemcpyDefault : cudaMemcpyDeviceToHost, ctx->stream));
+    if (!on_device) LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return LBRS_OK;
+}
+}  // namespace
+
 lbrs_status lbrs_halo_export(lbrs_ctx* ctx, int side, void* dst, int on_device)
 {
     lbrs_status st = halo_args(ctx, side, dst);
     if (st != LBRS_OK) return st;
-    const size_t e = elem_bytes(ctx), w = (size_t)ctx->halo[side - 2] * ctx->cfg.nx * e;
-    const char* src = ctx->f[ctx->cur] + (size_t)halo_first_row(ctx, side, false) * ctx->cfg.nx * e;
-    LBRS_CUDA(ctx, cudaMemcpy2DAsync(dst, w, src, (size_t)ctx->N * e, w, (size_t)ctx->P,
-                                     on_device ? cudaMemcpyDefault : cudaMemcpyDeviceToHost, ctx->stream));
-    if (!on_device) LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    return LBRS_OK;
+    return copy_rows(ctx, side, ctx->f[ctx->cur], ctx->P, dst, false, on_device);
 }
 
 lbrs_status lbrs_halo_import(lbrs_ctx* ctx, int side, const void* src, int on_device)
 {
     lbrs_status st = halo_args(ctx, side, src);
     if (st != LBRS_OK) return st;
-    const size_t e = elem_bytes(ctx), w = (size_t)ctx->halo[side - 2] * ctx->cfg.nx * e;
-    char* dst = ctx->f[ctx->cur] + (size_t)halo_first_row(ctx, side, true) * ctx->cfg.nx * e;
-    LBRS_CUDA(ctx, cudaMemcpy2DAsync(dst, (size_t)ctx->N * e, src, w, w, (size_t)ctx->P,
-                                     on_device ? cudaMemcpyDefault : cudaMemcpyHostToDevice, ctx->stream));
-    if (!on_device) LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    st = copy_rows(ctx, side, ctx->f[ctx->cur], ctx->P, (void*)src, true, on_device);
+    if (st != LBRS_OK) return st;
     ctx->halo_left[side - 2] = ctx->halo[side - 2];
     return LBRS_OK;
+}
+
+lbrs_status lbrs_store_rows(const lbrs_ctx* ctx, int64_t* ny_store, int64_t* row0)
+{
+    if (!ctx || !ny_store || !row0) return fail(nullptr, LBRS_EINVAL, "NULL argument");
+    *ny_store = ctx->ny_store;
+    *row0 = ctx->row0;
+    return LBRS_OK;
+}
+
+lbrs_status lbrs_rows_export(lbrs_ctx* ctx, int side, const void* d_buf, int planes, void* dst, int on_device)
+{
+    lbrs_status st = halo_args(ctx, side, dst, false);
+    if (st != LBRS_OK) return st;
+    if (!d_buf || planes < 1) return fail(ctx, LBRS_EINVAL, "buffer NULL or planes < 1");
+    return copy_rows(ctx, side, (char*)d_buf, planes, dst, false, on_device);
+}
+
+lbrs_status lbrs_rows_import(lbrs_ctx* ctx, int side, void* d_buf, int planes, const void* src, int on_device)
+{
+    lbrs_status st = halo_args(ctx, side, src, false);
+    if (st != LBRS_OK) return st;
+    if (!d_buf || planes < 1) return fail(ctx, LBRS_EINVAL, "buffer NULL or planes < 1");
+    return copy_rows(ctx, side, (char*)d_buf, planes, (void*)src, true, on_device);
 }
 
 lbrs_status lbrs_step_count(const lbrs_ctx* ctx, int64_t* steps)
@@ -1252,7 +1291,17 @@ lbrs_status lbrs_step_record(lbrs_ctx* ctx, int64_t n, void* d_U_hist)
     if (n > 0 && !d_U_hist) return fail(ctx, LBRS_EINVAL, "d_U_hist is NULL");
     if (ctx->lattice != LBRS_D2Q4 || ctx->f16 || ctx->f32u)
         return fail(ctx, LBRS_EINVAL, "recording steps cover the F64 and F32 D2Q4 forms only");
-    if (ctx->halo[0] || ctx->halo[1]) return fail(ctx, LBRS_EINVAL, "recording steps are not covered on cut grids");
+    if (ctx->halo[0] || ctx->halo[1]) {
+        lbrs_status hs = adjoint_supported(ctx);
+        if (hs != LBRS_OK) return hs;
+        for (int h = 0; h < 2; ++h)
+            if (ctx->halo[h] && n > ctx->halo_left[h])
+                return fail(ctx, LBRS_ESTATE, "%lld recording steps requested, but the ghost rows of the %s cut "
+                            "cover %lld more steps: import the neighbour's rows first", (long long)n,
+                            h ? "y-hi" : "y-lo", (long long)ctx->halo_left[h]);
+        for (int h = 0; h < 2; ++h)
+            if (ctx->halo[h]) ctx->halo_left[h] -= n;
+    }
     if (!ctx->has_state) return fail(ctx, LBRS_ESTATE, "no state set");
     lbrs_status st = record_steps(ctx, n, (char*)d_U_hist);
     if (st != LBRS_OK) return st;
@@ -1280,8 +1329,12 @@ lbrs_status lbrs_vjp_loss(lbrs_ctx* ctx, const void* d_rho_target, int dtype, vo
     const double vol = two_d(ctx->lattice) ? ctx->cfg.dx * ctx->cfg.dx : ctx->cfg.dx;
     double* partials = (double*)(ctx->ws + ctx->L.partials);
     double* dout = (double*)(ctx->ws + ctx->L.diag_out);
-    LBRS_CUDA(ctx, launch_density_loss(ctx->Q, ctx->K, ctx->f64, ctx->f[ctx->cur], d_rho_target, dtype == LBRS_F32,
-                                       d_gbar, ctx->N, vol, partials, dout, ctx->stream));
+    // own rows only (a cut context's buffers hold ghost rows, which the loss does not cover)
+    const size_t own = (size_t)ctx->row0 * ctx->cfg.nx;
+    LBRS_CUDA(ctx, launch_density_loss(ctx->Q, ctx->K, ctx->f64, own_ptr(ctx, ctx->f[ctx->cur]),
+                                       (const char*)d_rho_target + own * (dtype == LBRS_F64 ? 8 : 4),
+                                       dtype == LBRS_F32, (char*)d_gbar + own * elem_bytes(ctx), ctx->N_own, ctx->N,
+                                       vol, partials, dout, ctx->stream));
     ctx->launches += 2;
     if (loss) {
         LBRS_CUDA(ctx, cudaMemcpyAsync(loss, dout, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1327,6 +1380,9 @@ lbrs_status lbrs_forward_checkpointed(lbrs_ctx* ctx, int64_t n_steps, int64_t se
     if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
     lbrs_status st = adjoint_supported(ctx);
     if (st != LBRS_OK) return st;
+    if (ctx->halo[0] || ctx->halo[1])
+        return fail(ctx, LBRS_EINVAL, "the checkpointed driver steps without the neighbours' rows: on a cut grid, "
+                                      "drive recording and adjoint steps between row exchanges");
     if (n_steps < 1 || segment < 1) return fail(ctx, LBRS_EINVAL, "n_steps and segment must be >= 1");
     if (!ctx->has_state) return fail(ctx, LBRS_ESTATE, "no state set");
     if (!d_adj_ws || (uintptr_t)d_adj_ws % kAlign) return fail(ctx, LBRS_EINVAL, "adjoint workspace NULL or not 256-byte aligned");

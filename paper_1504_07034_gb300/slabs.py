@@ -15,7 +15,11 @@ This module
     with ``torch.distributed`` point-to-point calls (NCCL between GPUs; with gloo the blocks go
     through host memory);
   * reduces the slabs' diagnostics: FP64 sums of the totals and counts, minima of rho and p,
-    maximum of the local bound (``combine_diagnostics`` / ``DistSlab.diagnostics``).
+    maximum of the local bound (``combine_diagnostics`` / ``DistSlab.diagnostics``);
+  * runs the adjoint on slabs of a periodic grid (``gradient``): the transpose of the streaming
+    pulls, for row j, from rows j - 1 and j + 1 as the forward step does, so the same halo runs
+    the other way -- before every H adjoint steps each slab imports the neighbours' rows of the
+    adjoint state dL/df*, and once after the forward run those of every recorded moment field.
 
 A solver here is anything with ``halo_size``, ``halo_buffer``, ``halo_export``,
 ``halo_import``, ``step`` and ``diagnostics`` as ``paper_1504_07034_gb300.solver.Solver``
@@ -88,6 +92,10 @@ class _Stepping:
     halo_rows: int
     left: int
 
+    def _covered(self) -> int:
+        """Steps one exchange covers: the ghost rows of the cuts; without cuts, any number."""
+        return self.halo_rows if self.halo_rows else 1 << 62
+
     def exchange(self):
         raise NotImplementedError
 
@@ -104,8 +112,68 @@ class _Stepping:
             n -= m
 
     def invalidate(self):
-        """Call after a state was set on the solvers: the next step exchanges first."""
-        self.left = 0
+        """Call after a state was set on the solvers: the next step exchanges first (slabs
+        without cuts need no exchange)."""
+        self.left = 0 if self.halo_rows else self._covered()
+
+    # ------------------------------------------------------------ the adjoint (periodic grids)
+    def _locals(self) -> list:
+        raise NotImplementedError
+
+    def exchange_rows(self, bufs):
+        """The ghost rows of stored-layout tensors (one per local slab, any number of planes)
+        from the neighbours' own rows."""
+        raise NotImplementedError
+
+    def _sum(self, x: float) -> float:
+        return x
+
+    def gradient(self, U0s, targets, steps: int):
+        """Loss L = sum over the grid of 1/2 (rho(T) - target)^2 dx^2 after `steps` steps from the
+        conserved initial fields, and dL/dU0, on slabs of a periodic grid.  U0s, targets: per local
+        slab its own rows ((K, ny, nx) and (ny, nx) tensors on its device).  Returns (L, [dL/dU0 of
+        each local slab's own rows]).  The forward run records every step's moments (memory:
+        steps x K fields per slab); the backward sweeps them with the adjoint step."""
+        import torch
+        sv = self._locals()
+        H = self.halo_rows
+        U0st = []
+        for s, U0 in zip(sv, U0s):
+            t = s._fields_tensor()
+            t.zero_()
+            s.own_rows(t).copy_(U0)
+            U0st.append(t)
+        self.exchange_rows(U0st)
+        for s, U0 in zip(sv, U0s):
+            s.set_state(U0, primitive=False)
+        self.invalidate()
+        hists = [s._fields_tensor(steps) for s in sv]
+        t = 0
+        while t < steps:
+            if self.left == 0:
+                self.exchange()
+            m = min(self.left, steps - t)
+            for s, h in zip(sv, hists):
+                s.step_record(m, h[t:t + m])
+            self.left -= m
+            t += m
+        self.exchange_rows(hists)
+        losses, g = [], []
+        for s, tgt in zip(sv, targets):
+            tt = torch.zeros(s.store_grid, dtype=tgt.dtype, device=tgt.device)
+            s.own_rows(tt).copy_(tgt)
+            loss, gT = s.vjp_loss(tt)
+            losses.append(loss)
+            g.append(gT)
+        loss = self._sum(sum(losses))
+        t = steps
+        while t > 0:
+            self.exchange_rows(g)
+            m = min(H, t) if H else t
+            for _ in range(m):
+                t -= 1
+                g = [s.adjoint_step(h[t], gi) for s, h, gi in zip(sv, hists, g)]
+        return loss, [s.own_rows(s.vjp_equilibrium(u, gi)) for s, u, gi in zip(sv, U0st, g)]
 
 
 class LocalSlabs(_Stepping):
@@ -128,7 +196,7 @@ class LocalSlabs(_Stepping):
                 self.blocks[(r, Y_LO)] = self.solvers[r].halo_buffer(Y_LO)
             if up is not None:
                 self.blocks[(r, Y_HI)] = self.solvers[r].halo_buffer(Y_HI)
-        self.left = 0 if self.blocks else 1 << 62
+        self.left = 0 if self.halo_rows else self._covered()
 
     def exchange(self):
         for (r, side), buf in self.blocks.items():
@@ -138,11 +206,30 @@ class LocalSlabs(_Stepping):
                 self.solvers[r].halo_import(Y_LO, self.blocks[(lo, Y_HI)])
             if up is not None:
                 self.solvers[r].halo_import(Y_HI, self.blocks[(up, Y_LO)])
-        self.left = self.halo_rows
+        self.left = self._covered()
 
     def _step_all(self, n: int):
         for s in self.solvers:
             s.step(n)
+
+    def _locals(self) -> list:
+        return self.solvers
+
+    def exchange_rows(self, bufs):
+        import torch
+        blocks = {}
+        for r, (lo, up) in enumerate(self.nb):
+            s, b = self.solvers[r], bufs[r]
+            planes = b.numel() // (s.ny_store * s.nx)
+            for side, peer in ((Y_LO, lo), (Y_HI, up)):
+                if peer is not None:
+                    out = torch.empty((planes, s.halo_size(side)[0], s.nx), dtype=b.dtype, device=b.device)
+                    blocks[(r, side)] = s.rows_export(side, b, out)
+        for r, (lo, up) in enumerate(self.nb):
+            if lo is not None:
+                self.solvers[r].rows_import(Y_LO, bufs[r], blocks[(lo, Y_HI)])
+            if up is not None:
+                self.solvers[r].rows_import(Y_HI, bufs[r], blocks[(up, Y_LO)])
 
     def diagnostics(self) -> dict:
         return combine_diagnostics([s.diagnostics() for s in self.solvers])
@@ -176,34 +263,62 @@ class DistSlab(_Stepping):
             if peer is not None:
                 self.send[side] = solver.halo_buffer(side, device=dev)
                 self.recv[side] = solver.halo_buffer(side, device=dev)
-        self.left = 0 if self.send else 1 << 62
+        self.left = 0 if self.halo_rows else self._covered()
         self._torch = torch
-
-    def _ops(self):
-        dist, ops = self.dist, []
-        if self.upper is not None:
-            ops.append(dist.P2POp(dist.isend, self.send[Y_HI], self.upper, self.group, _TAG_UP))
-        if self.lower is not None:
-            ops.append(dist.P2POp(dist.isend, self.send[Y_LO], self.lower, self.group, _TAG_DOWN))
-        if self.lower is not None:
-            ops.append(dist.P2POp(dist.irecv, self.recv[Y_LO], self.lower, self.group, _TAG_UP))
-        if self.upper is not None:
-            ops.append(dist.P2POp(dist.irecv, self.recv[Y_HI], self.upper, self.group, _TAG_DOWN))
-        return ops
 
     def exchange(self):
         ctx = self._torch.cuda.stream(self.stream) if self.stream is not None else nullcontext()
         with ctx:
             for side, buf in self.send.items():
                 self.solver.halo_export(side, buf)
-            for work in self.dist.batch_isend_irecv(self._ops()):
-                work.wait()
+            self._p2p(self.send, self.recv)
             for side, buf in self.recv.items():
                 self.solver.halo_import(side, buf)
-        self.left = self.halo_rows
+        self.left = self._covered()
 
     def _step_all(self, n: int):
         self.solver.step(n)
+
+    def _locals(self) -> list:
+        return [self.solver]
+
+    def _p2p(self, send: dict, recv: dict):
+        """Blocks of the y-hi and y-lo sides out, the neighbours' in, in the order of _ops."""
+        dist, ops = self.dist, []
+        if self.upper is not None:
+            ops.append(dist.P2POp(dist.isend, send[Y_HI], self.upper, self.group, _TAG_UP))
+        if self.lower is not None:
+            ops.append(dist.P2POp(dist.isend, send[Y_LO], self.lower, self.group, _TAG_DOWN))
+        if self.lower is not None:
+            ops.append(dist.P2POp(dist.irecv, recv[Y_LO], self.lower, self.group, _TAG_UP))
+        if self.upper is not None:
+            ops.append(dist.P2POp(dist.irecv, recv[Y_HI], self.upper, self.group, _TAG_DOWN))
+        for work in dist.batch_isend_irecv(ops):
+            work.wait()
+
+    def exchange_rows(self, bufs):
+        torch, s = self._torch, self.solver
+        (b,) = bufs
+        planes = b.numel() // (s.ny_store * s.nx)
+        dev = b.device if self.dist.get_backend(self.group) == "nccl" else "cpu"
+        ctx = torch.cuda.stream(self.stream) if self.stream is not None else nullcontext()
+        with ctx:
+            send, recv = {}, {}
+            for side, peer in ((Y_LO, self.lower), (Y_HI, self.upper)):
+                if peer is not None:
+                    shape = (planes, s.halo_size(side)[0], s.nx)
+                    send[side] = s.rows_export(side, b, torch.empty(shape, dtype=b.dtype, device=dev))
+                    recv[side] = torch.empty(shape, dtype=b.dtype, device=dev)
+            self._p2p(send, recv)
+            for side, block in recv.items():
+                s.rows_import(side, b, block)
+
+    def _sum(self, x: float) -> float:
+        torch, dist = self._torch, self.dist
+        dev = "cuda" if dist.get_backend(self.group) == "nccl" else "cpu"
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=self.group)
+        return float(t.item())
 
     def diagnostics(self) -> dict:
         """The grid's diagnostics: this slab's, reduced over the group in FP64."""

@@ -78,6 +78,9 @@ class Solver:
             abi.check(self.lib.lbrs_create(ctypes.byref(self.cfg), ctypes.c_void_p(self.workspace.data_ptr()),
                                            size.value, ctypes.byref(ctx)))
         self.ctx = ctx
+        ny_s, row0 = ctypes.c_int64(), ctypes.c_int64()
+        abi.check(self.lib.lbrs_store_rows(ctx, ctypes.byref(ny_s), ctypes.byref(row0)))
+        self.ny_store, self.row0 = ny_s.value, row0.value   # stored rows (a cut context adds ghost rows)
 
     @classmethod
     def from_workload(cls, wl, precision: str = "f32", stream=None, omega=None, diag_every: int = 0,
@@ -264,12 +267,36 @@ class Solver:
         self.solid = m
 
     # ------------------------------------------------------------------ adjoint (periodic D2Q4)
+    @property
+    def store_grid(self):
+        """Grid of the adjoint buffers: the stored rows (own rows plus the ghost rows of cuts)."""
+        return (self.ny_store, self.nx) if self.lattice in ("d2q4", "d2q4s") else (self.nx,)
+
     def _fields_tensor(self, n=None):
-        shape = ((n,) if n is not None else ()) + (self.K,) + self.grid
+        shape = ((n,) if n is not None else ()) + (self.K,) + self.store_grid
         return torch.empty(shape, dtype=self.storage_dtype, device=self.device)
 
     def _dists_tensor(self):
-        return torch.empty((self.Q, self.K) + self.grid, dtype=self.storage_dtype, device=self.device)
+        return torch.empty((self.Q, self.K) + self.store_grid, dtype=self.storage_dtype, device=self.device)
+
+    def own_rows(self, t: torch.Tensor) -> torch.Tensor:
+        """The own rows of a stored-layout tensor (..., ny_store, nx)."""
+        return t[..., self.row0:self.row0 + self.ny, :]
+
+    def rows_export(self, side: int, buf: torch.Tensor, out: torch.Tensor) -> torch.Tensor:
+        """The own rows next to cut `side` of a stored-layout tensor, all its planes, into `out`
+        (planes x ghost rows x nx)."""
+        planes = buf.numel() // (self.ny_store * self.nx)
+        self._check(self.lib.lbrs_rows_export(self.ctx, int(side), self._ptr(buf), planes,
+                                              ctypes.c_void_p(out.data_ptr()), 1 if out.is_cuda else 0))
+        return out
+
+    def rows_import(self, side: int, buf: torch.Tensor, block: torch.Tensor):
+        """The neighbour's block into the ghost rows beyond cut `side` of a stored-layout tensor."""
+        planes = buf.numel() // (self.ny_store * self.nx)
+        self._keep_rows = block
+        self._check(self.lib.lbrs_rows_import(self.ctx, int(side), self._ptr(buf), planes,
+                                              ctypes.c_void_p(block.data_ptr()), 1 if block.is_cuda else 0))
 
     @staticmethod
     def _ptr(t: torch.Tensor):

@@ -26,7 +26,7 @@ import torch.multiprocessing as mp
 import oracle
 import workloads as W
 
-pytestmark = pytest.mark.gpu
+pytestmark = [pytest.mark.gpu, pytest.mark.timeout(600)]
 
 F64_TOL = 1e-12
 CHUNKS = (1, 4, 7, 2, 17, 9)          # 40 steps
@@ -201,6 +201,8 @@ def test_cut_configurations_refused_where_not_covered():
         s.set_obstacles(torch.zeros((32, 64), dtype=torch.uint8))
     with pytest.raises(abi.LbrsError):
         s.step_adaptive(1)
+    with pytest.raises(abi.LbrsError):
+        s.forward_checkpointed(4, 2)                              # steps without the neighbours' rows
     buf = s.halo_buffer(2)
     with pytest.raises(abi.LbrsError):
         s.halo_export(1, buf)                                     # not a y side
@@ -289,3 +291,42 @@ def test_two_gloo_ranks_on_one_gpu(tmp_path):
     assert np.array_equal(U, U_ref)
     t0, t1 = np.load(tmp_path / "tot0.npy"), np.load(tmp_path / "tot1.npy")
     assert np.array_equal(t0, t1)
+
+
+# ---------------------------------------------------------------- the adjoint on slabs (reverse halo)
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("parts,halo", [(2, 2), (3, 2), (3, 1)])
+def test_slab_gradient_equals_unsplit_gradient(precision, parts, halo):
+    """dL/dU0 on y-slabs of a periodic grid: forward recording with the state's rows exchanged every
+    H steps, the recorded moments' rows exchanged once, the adjoint state's rows before every H
+    adjoint steps.  The own rows equal the unsplit context's gradient bit for bit (same kernels,
+    same per-cell arithmetic); FP64 also the oracle's (1e-10 per field)."""
+    from paper_1504_07034_gb300 import slabs
+    wl, target = W.adjoint_pulses(seed=3, n=64, steps=0, width=0.1, pulses=3)
+    steps = 21
+    o = oracle.Oracle.from_workload(wl)
+    U0 = o.prim_to_cons(wl.prim)
+    dt = torch.float64 if precision == "f64" else torch.float32
+    one = _solver(wl, precision)
+    loss_ref, (g_ref,) = slabs.LocalSlabs([one], True).gradient(
+        [torch.from_numpy(U0).to("cuda", dt)], [torch.from_numpy(target).to("cuda", dt)], steps)
+    g_ref = g_ref.cpu().numpy()
+    one.close()
+    ss, U0s, tgts = [], [], []
+    for r, (j0, j1) in enumerate(slabs.slab_bounds(wl.ny, parts, halo)):
+        ss.append(_solver(wl, precision, ny=j1 - j0, bc=slabs.slab_bc(wl.bc, r, parts, halo)))
+        U0s.append(torch.from_numpy(np.ascontiguousarray(U0[:, j0:j1])).to("cuda", dt))
+        tgts.append(torch.from_numpy(np.ascontiguousarray(target[j0:j1])).to("cuda", dt))
+    loss, grads = slabs.LocalSlabs(ss, True).gradient(U0s, tgts, steps)
+    g = np.concatenate([x.cpu().numpy() for x in grads], axis=1)
+    assert np.array_equal(g, g_ref), np.max(np.abs(g - g_ref))
+    assert loss == pytest.approx(loss_ref, rel=1e-12)
+    if precision == "f64":
+        fsT, _ = o.run(o.init(U0), steps)
+        dLdU = np.zeros_like(U0)
+        dLdU[0] = (o.moments(fsT)[0] - target) * wl.dx * wl.dx
+        g_or, _ = o.gradient(U0, steps, dLdU)
+        assert _field_rel_err(g, g_or) <= 1e-10
+    for s in ss:
+        s.close()

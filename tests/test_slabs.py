@@ -7,7 +7,9 @@ semantics: H ghost rows stored beyond each cut, the stored grid closed
 transmissively there.  The ghost rows start as NaN, so any value of them that
 reached an own row before an import replaced it would show.  Every case must
 equal the unsplit oracle run bit for bit: within one process (LocalSlabs) and
-between gloo ranks (DistSlab, world sizes 2 and 3, 127.0.0.1).
+between gloo ranks (DistSlab, world sizes 2 and 3, 127.0.0.1).  The adjoint on
+slabs of a periodic grid (the reverse halo) must give the oracle's unsplit
+gradient bit for bit as well.
 """
 import os
 import socket
@@ -38,6 +40,11 @@ class OracleSlab:
         self.fs = np.full((4, 4, rows, wl.nx), np.nan)
         self.left = {2: 0, 3: 0}
         self.dx = wl.dx
+        # the adjoint interface: stored-layout buffers, the adjoint over the stored rows wrapped in y
+        self.K, self.ny_store, self.row0 = 4, rows, self.H[2]
+        self.store_grid = (rows, wl.nx)
+        self.oa = oracle.Oracle(oracle.D2Q4, wl.nx, rows, lam=wl.lam, omega=wl.omega, gamma=wl.gamma,
+                                bc=[("periodic", None)] * 4, dx=wl.dx)
 
     def set_own(self, fs_rows):
         self.fs[:, :, self.H[2]:self.H[2] + self.ny, :] = fs_rows
@@ -79,6 +86,52 @@ class OracleSlab:
                 self.left[side] -= n
         for _ in range(n):
             self.fs, _, _ = self.o.collide(self.o.stream(self.fs))
+
+    # adjoint interface (stored layout, torch CPU tensors)
+    def _fields_tensor(self, n=None):
+        return torch.zeros(((n,) if n is not None else ()) + (4,) + self.store_grid, dtype=torch.float64)
+
+    def own_rows(self, t):
+        return t[..., self.row0:self.row0 + self.ny, :]
+
+    def rows_export(self, side, buf, out):
+        b = buf.reshape(-1, self.ny_store, self.nx)
+        r0 = self.H[2] if side == 2 else self.H[2] + self.ny - self.H[3]
+        out.copy_(b[:, r0:r0 + self.H[side], :])
+        return out
+
+    def rows_import(self, side, buf, block):
+        b = buf.view(-1, self.ny_store, self.nx)
+        r0 = 0 if side == 2 else self.H[2] + self.ny
+        b[:, r0:r0 + self.H[side], :] = block
+
+    def set_state(self, U0, primitive=False):
+        assert not primitive
+        self.set_own(self.own_o.init(U0.numpy()))
+
+    def step_record(self, n, h):
+        for side in (2, 3):
+            if self.H[side]:
+                assert n <= self.left[side], "recording past what the last import covers"
+                self.left[side] -= n
+        for m in range(n):
+            self.fs, U, _ = self.o.collide(self.o.stream(self.fs))
+            h[m].copy_(torch.from_numpy(U))
+        return h
+
+    def vjp_loss(self, target):
+        own = np.ascontiguousarray(self.own())
+        r = self.own_o.moments(own)[0] - self.own_rows(target).numpy()
+        cell = self.dx * self.dx
+        g = torch.zeros((4, 4) + self.store_grid, dtype=torch.float64)
+        self.own_rows(g)[:, 0] = torch.from_numpy(r * cell)
+        return float(0.5 * np.sum(r * r) * cell), g
+
+    def adjoint_step(self, U_next, g):
+        return torch.from_numpy(self.oa.adjoint_step(U_next.numpy(), g.numpy()))
+
+    def vjp_equilibrium(self, U0, g):
+        return torch.from_numpy(self.oa.vjp_equilibrium(U0.numpy(), g.numpy()))
 
     def diagnostics(self):
         own = np.ascontiguousarray(self.own())
@@ -202,3 +255,84 @@ def test_gloo_ranks_equal_unsplit_run_bitwise(tmp_path, world, case):
     assert np.array_equal(diag[0][:4], local[:, :4].sum(axis=0)) or np.allclose(
         diag[0][:4], local[:, :4].sum(axis=0), rtol=1e-15, atol=0)
     assert diag[0][4] == local[:, 4].min() and diag[0][5] == local[:, 5].min()
+
+
+# ---------------------------------------------------------------- the adjoint on slabs
+
+def _gradient_case():
+    wl, target = W.adjoint_pulses(seed=2, n=40, steps=0, width=0.1, pulses=3)
+    o = oracle.Oracle.from_workload(wl)
+    U0 = o.prim_to_cons(wl.prim)
+    return wl, target, o, U0
+
+
+def _oracle_gradient(steps):
+    wl, target, o, U0 = _gradient_case()
+    fsT, _ = o.run(o.init(U0), steps)
+    cell = wl.dx * wl.dx
+    r = o.moments(fsT)[0] - target
+    dLdU = np.zeros_like(U0)
+    dLdU[0] = r * cell
+    grad, _ = o.gradient(U0, steps, dLdU)
+    return float(0.5 * np.sum(r * r) * cell), grad
+
+
+@pytest.mark.parametrize("parts,halo", [(2, 2), (3, 1), (4, 3)])
+def test_local_slab_gradient_equals_unsplit_oracle_gradient(parts, halo):
+    steps = 13
+    wl, target, _, U0 = _gradient_case()
+    ss, U0s, tgts = [], [], []
+    for r, (j0, j1) in enumerate(slabs.slab_bounds(wl.ny, parts, halo)):
+        ss.append(OracleSlab(wl, j0, j1, slabs.slab_bc(wl.bc, r, parts, halo)))
+        U0s.append(torch.from_numpy(np.ascontiguousarray(U0[:, j0:j1])))
+        tgts.append(torch.from_numpy(np.ascontiguousarray(target[j0:j1])))
+    loss, grads = slabs.LocalSlabs(ss, True).gradient(U0s, tgts, steps)
+    loss_ref, grad_ref = _oracle_gradient(steps)
+    assert loss == pytest.approx(loss_ref, rel=1e-13)
+    assert np.array_equal(np.concatenate([g.numpy() for g in grads], axis=1), grad_ref)
+
+
+def _grad_rank_main(rank, world, port, result_dir):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        wl, target, _, U0 = _gradient_case()
+        j0, j1 = slabs.slab_bounds(wl.ny, world)[rank]
+        s = OracleSlab(wl, j0, j1, slabs.slab_bc(wl.bc, rank, world))
+        run = slabs.DistSlab(s, rank, world, True)
+        loss, (g,) = run.gradient([torch.from_numpy(np.ascontiguousarray(U0[:, j0:j1]))],
+                                  [torch.from_numpy(np.ascontiguousarray(target[j0:j1]))], 11)
+        np.save(os.path.join(result_dir, f"grad{rank}.npy"), g.numpy())
+        np.save(os.path.join(result_dir, f"loss{rank}.npy"), np.array([loss]))
+    finally:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_gloo_ranks_gradient_equals_unsplit_oracle_gradient(tmp_path, world):
+    mp.start_processes(_grad_rank_main, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True,
+                       start_method="spawn")
+    loss_ref, grad_ref = _oracle_gradient(11)
+    got = np.concatenate([np.load(tmp_path / f"grad{r}.npy") for r in range(world)], axis=1)
+    assert np.array_equal(got, grad_ref)
+    for r in range(world):
+        assert float(np.load(tmp_path / f"loss{r}.npy")[0]) == pytest.approx(loss_ref, rel=1e-13)
+
+
+@pytest.mark.timeout(120)
+def test_a_single_uncut_slab_steps_and_differentiates():
+    """One slab of a periodic grid has no cuts: stepping and the gradient run without
+    exchanges (and terminate) and equal the plain run."""
+    steps = 9
+    wl, target, _, U0 = _gradient_case()
+    s = OracleSlab(wl, 0, wl.ny, slabs.slab_bc(wl.bc, 0, 1))
+    run = slabs.LocalSlabs([s], True)
+    loss, (g,) = run.gradient([torch.from_numpy(U0)], [torch.from_numpy(target)], steps)
+    loss_ref, grad_ref = _oracle_gradient(steps)
+    assert np.array_equal(g.numpy(), grad_ref)
+    assert loss == loss_ref
+    run.invalidate()
+    run.step(5)
+
