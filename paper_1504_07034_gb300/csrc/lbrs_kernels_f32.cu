@@ -825,6 +825,246 @@ __global__ void __launch_bounds__(kFTX * kFTY, 5)
     tall_phase2<STORE_U, HALF>(b, s_raw, i0, j0, ti, tj + kFTY);
 }
 
+// ---------------------------------------------------------------- three steps per launch, TMA-fed
+//
+// The state is read and written once per three steps (128 B per cell and launch, 42.7 B per
+// lattice update).  A block owns a 32 x 16 tile; window slot (wi, wj), wi < 36, wj < 20, is the
+// cell (i0 - 2 + wi, j0 - 2 + wj) (the tile and two cells of halo).  Four tensor copies bring,
+// per population q, the 40 x 20 x 4-field box of the values that the window's slots pull
+// (shifted by the velocity, x starting on a 16-byte boundary at i0 - 4): position f3_pos(q, k,
+// wi, wj) holds what slot (wi, wj) pulls.
+//   phase 1  step n -> n+1 on the window, each slot's results written over the positions it
+//            pulled them from (one reader per position);
+//   phase 2  step n+1 -> n+2 on the 34 x 18 inner slots: slot (u, v) pulls population q from
+//            slot (u - sx, v - sy), at f3_pos(q, ., u - sx, v - sy), and writes its own
+//            population q over that same position (again one reader per position);
+//   phase 3  step n+2 -> n+3 for the tile: cell (x, y) finds population q of its source slot
+//            (x - sx, y - sy) at f3_pos(q, ., x - 2 sx, y - 2 sy); the result goes to global memory.
+// Slots beyond a non-periodic side are not computed; on tiles at the grid's edge a fix-up pass
+// after phases 1 and 2 writes into them what the single-step pull resolves there (a Dirichlet
+// ghost, or the clamped cell's values, x side first), so phases 2 and 3 gather uniformly.  Slots
+// beyond a periodic side compute the wrapped cell (by the global pull of the single-step kernel:
+// the boxes hold the copy's fill there).  Every value is formed with the single-step kernel's
+// arithmetic, so three steps are bit-identical to single steps.  Not for internal walls, halfway
+// walls or recording steps (those take the two-step kernel).
+constexpr int kP3X = 40;                                    // box columns
+constexpr int kW3X = 36, kW3Y = kTY + 4, kW3N = kW3X * kW3Y;   // phase-1 window (tile + 2 halo)
+constexpr int kB3X = 34, kB3Y = kTY + 2, kB3N = kB3X * kB3Y;   // phase-2 slots (tile + 1 halo)
+constexpr int kP3N = kP3X * kW3Y;                           // floats per field plane of a box
+constexpr size_t kF3SmemBytes = 128 + 16u * kP3N * sizeof(float) + 16;
+
+// Position of population q, field k, as pulled by window slot (wi, wj).
+__device__ __forceinline__ int f3_pos(int q, int k, int wi, int wj)
+{
+    return (q * 4 + k) * kP3N + wj * kP3X + wi + ((q == 0 || q == 3) ? 3 : 1);
+}
+
+// The four population boxes of tile (i0, j0) onto one mbarrier.
+__device__ __forceinline__ void issue_tile_copy3(const CUtensorMap* tmap, float* s_raw, uint32_t bar, int i0, int j0)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(16u * kP3N * 4u) : "memory");
+    const int y0[4] = {j0 - 1, j0 - 1, j0 - 3, j0 - 3};
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(s_raw + q * 4 * kP3N)),
+            "l"((uint64_t)tmap), "r"(i0 - 4), "r"(y0[q]), "r"(q * 4), "r"(bar)
+            : "memory");
+}
+
+// How the window slot of unwrapped cell (ui, uj) gets its values: 0 computed there (inside the
+// grid, or beyond a periodic side: the wrapped cell); 1 the ghost of Dirichlet side *gs; 2 the
+// values of the slot of unwrapped cell (*ci, *cj) (a transmissive side's clamped cell); 3 none
+// (beyond a wall side, whose populations the wall relations replace, or farther beyond a side
+// than `reach` cells -- 2 for phase 1, 1 for phase 2 -- which no later phase pulls).
+__device__ __forceinline__ int f3_resolve(const StepArgs<float>& a, int ui, int uj, int& ci, int& cj, int& gs,
+                                          int reach)
+{
+    ci = ui;
+    cj = uj;
+    const int bx = ui < 0 ? -ui : (ui >= a.nx ? ui - a.nx + 1 : 0);
+    const int by = uj < 0 ? -uj : (uj >= a.ny ? uj - a.ny + 1 : 0);
+    const bool px = a.bc[0] == BC_PERIODIC, py = a.bc[2] == BC_PERIODIC;
+    if (bx > reach || by > reach || (bx > 1 && !px) || (by > 1 && !py)) return 3;
+    if (bx && !px) {
+        const int side = ui < 0 ? 0 : 1;
+        if ((side == 0 ? a.bc[0] : a.bc[1]) == BC_DIRICHLET) {
+            gs = side;
+            return 1;
+        }
+        ci = ui < 0 ? 0 : a.nx - 1;
+    }
+    if (by && !py) {
+        const int side = uj < 0 ? 2 : 3;
+        const int kind = side == 2 ? a.bc[2] : a.bc[3];
+        if (kind == BC_DIRICHLET) {
+            gs = side;
+            return 1;
+        }
+        if (kind == BC_WALL) return 3;
+        cj = uj < 0 ? 0 : a.ny - 1;
+    }
+    return (ci == ui && cj == uj) ? 0 : 2;
+}
+
+// The on-node wall relations (Section II.E) for a cell on row j.
+__device__ __forceinline__ void f3_walls(const StepArgs<float>& a, int j, float f[4][4])
+{
+    const bool wall_bottom = j == 0 && a.bc[2] == BC_WALL;
+    const bool wall_top = j == a.ny - 1 && a.bc[3] == BC_WALL;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float sgn = k == 2 ? -1.f : 1.f;
+        if (wall_top) {
+            f[0][k] = sgn * f[3][k];
+            f[1][k] = sgn * f[2][k];
+        }
+        if (wall_bottom) {
+            f[3][k] = sgn * f[0][k];
+            f[2][k] = sgn * f[1][k];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kFTX * kFTY, 4)
+    step2d_f32_fused3_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs<float> a, unsigned* wait_flag)
+{
+    extern __shared__ unsigned char smem_dyn[];
+    float* s = (float*)(((uintptr_t)smem_dyn + 127) & ~(uintptr_t)127);
+    uint64_t* bar_p = (uint64_t*)(s + 16 * kP3N);
+    const uint32_t bar = smem_addr(bar_p);
+    const int i0 = blockIdx.x * kFTX, j0 = blockIdx.y * kTY;
+    constexpr int kThr = kFTX * kFTY;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue_tile_copy3(&tmap, s, bar, i0, j0);
+    }
+    __syncthreads();
+    const bool arrived = mbar_wait_bounded(bar, 0, kWaitPolls);
+    if (!__syncthreads_and(arrived)) {
+        give_up_tile(bar, wait_flag);
+        return;
+    }
+    // every slot and every source of phase 1 inside the grid: no resolution anywhere
+    const bool inside = i0 >= 3 && j0 >= 3 && i0 + kFTX + 3 <= a.nx && j0 + kTY + 3 <= a.ny;
+
+    // phase 1: step n -> n+1 on the window, in place
+    for (int w = threadIdx.x; w < kW3N; w += kThr) {
+        const int wi = w % kW3X, wj = w / kW3X;
+        float f[4][4];
+        bool boxed = inside;
+        if (!inside) {
+            const int ui = i0 - 2 + wi, uj = j0 - 2 + wj;
+            int ci, cj, gs;
+            if (f3_resolve(a, ui, uj, ci, cj, gs, 2) != 0) continue;
+            boxed = ui >= 1 && ui <= a.nx - 2 && uj >= 1 && uj <= a.ny - 2;
+            if (!boxed) {
+                const int i = (ui < 0 || ui >= a.nx) ? wrap_index(ui, a.nx) : ui;
+                const int j = (uj < 0 || uj >= a.ny) ? wrap_index(uj, a.ny) : uj;
+                pull_edge_2d<float, false>(a, i, j, f);
+            }
+        }
+        if (boxed) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) f[q][k] = s[LBRS_IX(f3_pos(q, k, wi, wj), 16 * kP3N, 23)];
+        }
+        float U[4], out[4][4];
+        collide_2d<float>(a, f, U, out);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) s[LBRS_IX(f3_pos(q, k, wi, wj), 16 * kP3N, 23)] = out[q][k];
+    }
+    __syncthreads();
+    if (!inside) {
+        // window slots beyond a non-periodic side: what the single-step pull resolves there
+        for (int w = threadIdx.x; w < kW3N; w += kThr) {
+            const int wi = w % kW3X, wj = w / kW3X;
+            int ci, cj, gs;
+            const int r = f3_resolve(a, i0 - 2 + wi, j0 - 2 + wj, ci, cj, gs, 2);
+            if (r != 1 && r != 2) continue;
+            const int cwi = ci - (i0 - 2), cwj = cj - (j0 - 2);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    s[LBRS_IX(f3_pos(q, k, wi, wj), 16 * kP3N, 23)] =
+                        r == 1 ? a.ghost[gs * GHOST_STRIDE + q * 4 + k] : s[LBRS_IX(f3_pos(q, k, cwi, cwj), 16 * kP3N, 23)];
+        }
+        __syncthreads();
+    }
+
+    // phase 2: step n+1 -> n+2 on the inner slots, each written over the positions it pulled
+    for (int b = threadIdx.x; b < kB3N; b += kThr) {
+        const int u = 1 + b % kB3X, v = 1 + b / kB3X;
+        const int uj = j0 - 2 + v;
+        if (!inside) {
+            int ci, cj, gs;
+            if (f3_resolve(a, i0 - 2 + u, uj, ci, cj, gs, 1) != 0) continue;
+        }
+        // sources (u - sx, v - sy): q0 (u+1, v+1), q1 (u-1, v+1), q2 (u-1, v-1), q3 (u+1, v-1)
+        const int su[4] = {u + 1, u - 1, u - 1, u + 1};
+        const int sv[4] = {v + 1, v + 1, v - 1, v - 1};
+        float f[4][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) f[q][k] = s[LBRS_IX(f3_pos(q, k, su[q], sv[q]), 16 * kP3N, 24)];
+        if (!inside) f3_walls(a, uj, f);
+        float U[4], out[4][4];
+        collide_2d<float>(a, f, U, out);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) s[LBRS_IX(f3_pos(q, k, su[q], sv[q]), 16 * kP3N, 24)] = out[q][k];
+    }
+    __syncthreads();
+    if (!inside) {
+        // inner slots beyond a non-periodic side, stored where phase 3 looks for them
+        for (int b = threadIdx.x; b < kB3N; b += kThr) {
+            const int u = 1 + b % kB3X, v = 1 + b / kB3X;
+            int ci, cj, gs;
+            const int r = f3_resolve(a, i0 - 2 + u, j0 - 2 + v, ci, cj, gs, 1);
+            if (r != 1 && r != 2) continue;
+            const int cu = ci - (i0 - 2), cv = cj - (j0 - 2);
+            const int du[4] = {1, -1, -1, 1}, dv[4] = {1, 1, -1, -1};   // -sx, -sy
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    s[LBRS_IX(f3_pos(q, k, u + du[q], v + dv[q]), 16 * kP3N, 24)] =
+                        r == 1 ? a.ghost[gs * GHOST_STRIDE + q * 4 + k]
+                               : s[LBRS_IX(f3_pos(q, k, cu + du[q], cv + dv[q]), 16 * kP3N, 24)];
+        }
+        __syncthreads();
+    }
+
+    // phase 3: step n+2 -> n+3 for the tile, two cells per thread
+    const int ti = threadIdx.x % kFTX;
+#pragma unroll
+    for (int rep = 0; rep < kTY / kFTY; ++rep) {
+        const int ty = threadIdx.x / kFTX + rep * kFTY;
+        const int i = i0 + ti, j = j0 + ty;
+        if (i >= a.nx || j >= a.ny) continue;
+        const int x = ti + 2, y = ty + 2;
+        // population q of source slot (x - sx, y - sy) lies at (x - 2 sx, y - 2 sy)
+        const int px[4] = {x + 2, x - 2, x - 2, x + 2};
+        const int py[4] = {y + 2, y + 2, y - 2, y - 2};
+        float f[4][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) f[q][k] = s[LBRS_IX(f3_pos(q, k, px[q], py[q]), 16 * kP3N, 25)];
+        if (!inside) f3_walls(a, j, f);
+        collide_store_2d<float>(a, (int64_t)j * a.nx + i, f);
+    }
+}
+
 // Failure-detection self-test: one block waits, with the tile kernels' bounded wait,
 // on an mbarrier that nothing completes (no copy, no arrival); the wait gives up after
 // `polls` polls and the block raises *wait_flag as the tile kernels do.  Nothing is in
@@ -1300,6 +1540,53 @@ bool encode_f32_tile_map(TileMap* map, const float* f, int64_t nx, int64_t ny)
     memcpy(map->bytes, &m, sizeof m);
     map->valid = 1;
     return true;
+}
+
+// The tensor map of the three-step kernel: 40 x 20 x 4-field boxes of the state.
+bool encode_f32_tile_map3(TileMap* map, const float* f, int64_t nx, int64_t ny)
+{
+    map->valid = 0;
+    if (!tma_enabled() || nx % 4 != 0 || ((uintptr_t)f & 15)) return false;
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return false;
+    static std::once_flag attr_once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr_once, [] {
+        attr_err = cudaFuncSetAttribute(step2d_f32_fused3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kF3SmemBytes);
+    });
+    if (attr_err != cudaSuccess) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, 16};
+    const cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)(nx * ny) * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)kP3X, (cuuint32_t)kW3Y, 4};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUtensorMap m;
+    if (enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)f, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+        return false;
+    memcpy(map->bytes, &m, sizeof m);
+    map->valid = 1;
+    return true;
+}
+
+bool step3_f32_enabled()
+{
+    static int v = [] {
+        const char* e = getenv("LBRS_F32_FUSE3");
+        return (e && !strcmp(e, "0")) ? 0 : 1;
+    }();
+    return v != 0;
+}
+
+cudaError_t launch_step3_f32(const StepArgs<float>& a, const TileMap* map3, unsigned* wait_flag, cudaStream_t s)
+{
+    if (!map3 || !map3->valid || !wait_flag || a.solid || a.Uout) return cudaErrorInvalidValue;
+    CUtensorMap m;
+    memcpy(&m, map3->bytes, sizeof m);
+    const dim3 grid((unsigned)((a.nx + kFTX - 1) / kFTX), (unsigned)((a.ny + kTY - 1) / kTY));
+    step2d_f32_fused3_kernel<<<grid, kFTX * kFTY, kF3SmemBytes, s>>>(m, a, wait_flag);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_step2_f32(const StepArgs<float>& a, const TileMap* map, unsigned* wait_flag, cudaStream_t s)

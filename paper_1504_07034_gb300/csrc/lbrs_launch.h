@@ -55,6 +55,12 @@ struct alignas(64) TileMap {
 bool step2_f32_enabled();
 bool encode_f32_tile_map(TileMap* map, const float* f, int64_t nx, int64_t ny);
 cudaError_t launch_step2_f32(const StepArgs<float>& a, const TileMap* map, unsigned* wait_flag, cudaStream_t s);
+// D2Q4 FP32: three time steps in one launch, src -> dst (temporal blocking by three; tensor
+// copies of 40 x 20 boxes, so nx % 4 == 0), bit-identical to single steps.  Not for internal
+// walls, halfway walls or recording steps.  Off when the environment sets LBRS_F32_FUSE3=0.
+bool step3_f32_enabled();
+bool encode_f32_tile_map3(TileMap* map, const float* f, int64_t nx, int64_t ny);
+cudaError_t launch_step3_f32(const StepArgs<float>& a, const TileMap* map3, unsigned* wait_flag, cudaStream_t s);
 
 // Dirichlet ghost tables: ghost[side][q*K + k] = f^eq(U(prim[side])) for every
 // side whose kind is DIRICHLET, computed in FP64 and rounded to the storage type.

@@ -3,7 +3,7 @@
 // Owns nothing on the device: the caller's workspace is carved into two
 // ping-pong distribution buffers, the Dirichlet ghost tables and the
 // diagnostics scratch.  Steps are enqueued on the caller's stream; runs of
-// many steps replay a CUDA graph of kGraphSteps step kernels (captured once per
+// many steps replay a CUDA graph of graph_steps() steps (captured once per
 // context and buffer parity on a private stream).
 #include <math.h>
 #include <stdarg.h>
@@ -24,7 +24,7 @@ using namespace lbrs;
 namespace {
 
 constexpr size_t kAlign = 256;
-constexpr int kGraphSteps = 32;   // even: a graph returns the buffers to their parity
+constexpr int kGraphSteps = 32;   // 16 two-step or 32 one-step launches: an even number
 
 thread_local char g_err[512] = "";
 
@@ -124,6 +124,8 @@ struct lbrs_ctx {
     cudaStream_t cap_stream;
     cudaGraphExec_t graph[2];
     TileMap tmap[2];         // tensor maps of the two state buffers (FP32 D2Q4 two-step kernel)
+    TileMap tmap3[2];        // the same for the three-step kernel (larger boxes)
+    int graph_launches[2];   // kernels in graph[b]
     const uint8_t* solid;    // caller-owned obstacle mask [ny][nx] (lbrs_set_obstacles), or NULL
     GhostSpec gspec;         // the sides' kinds and states (the adaptive run rebuilds the ghosts)
     bool adapt_ready;        // the adaptive record holds the current state's run
@@ -302,6 +304,34 @@ bool fused2(const lbrs_ctx* ctx) { return fused2_f32(ctx) || (ctx->f32u && step2
 
 unsigned* wait_flag(const lbrs_ctx* ctx) { return (unsigned*)(ctx->ws + ctx->L.wait_flag); }
 
+// The FP32 three-steps-per-launch kernel available for this context?  Not with internal
+// walls or halfway walls (their populations break the one-reader rule of its in-place phases).
+bool fused3(const lbrs_ctx* ctx)
+{
+    if (!fused2_f32(ctx) || ctx->solid || !step3_f32_enabled()) return false;
+    if (ctx->cfg.bc[2].kind == LBRS_BC_WALL_HALFWAY || ctx->cfg.bc[3].kind == LBRS_BC_WALL_HALFWAY) return false;
+    return ctx->tmap3[0].valid && ctx->tmap3[1].valid;
+}
+
+// Steps the next launch takes out of `left`: three where the three-step kernel applies (but
+// 2 + 2 rather than 3 + 1), else two where the two-step kernel does, else one.
+int next_launch_steps(const lbrs_ctx* ctx, int64_t left)
+{
+    if (left >= 3 && left != 4 && fused3(ctx)) return 3;
+    if (left >= 2 && fused2(ctx)) return 2;
+    return 1;
+}
+
+// Steps per captured graph: 12 three-step launches, else kGraphSteps (an even number of
+// launches either way, so that a graph returns the buffers to their parity).
+int graph_steps(const lbrs_ctx* ctx) { return fused3(ctx) ? 36 : kGraphSteps; }
+
+// Three steps from buffer b into buffer b ^ 1.
+cudaError_t launch_step3(const lbrs_ctx* ctx, int b, cudaStream_t s)
+{
+    return launch_step3_f32(step_args<float>(ctx, b), &ctx->tmap3[b], wait_flag(ctx), s);
+}
+
 // Two steps from buffer b into buffer b ^ 1.
 cudaError_t launch_step2(const lbrs_ctx* ctx, int b, cudaStream_t s)
 {
@@ -316,24 +346,23 @@ int readout_lattice(const lbrs_ctx* ctx)
     return lat_code(ctx->lattice);
 }
 
-// Capture kGraphSteps step kernels starting from buffer `from` into graph[from].
+// Capture graph_steps() steps starting from buffer `from` into graph[from].
 lbrs_status ensure_graph(lbrs_ctx* ctx, int from)
 {
     if (ctx->graph[from]) return LBRS_OK;
     if (!ctx->cap_stream) LBRS_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
     LBRS_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t le = cudaSuccess;
-    int b = from;
-    for (int n = 0; n < kGraphSteps && le == cudaSuccess;) {
-        if (fused2(ctx)) {
-            le = launch_step2(ctx, b, ctx->cap_stream);
-            n += 2;
-        } else {
-            le = launch_one_step(ctx, b, ctx->cap_stream);
-            n += 1;
-        }
+    int b = from, launches = 0;
+    const int G = graph_steps(ctx);
+    for (int n = 0; n < G && le == cudaSuccess; ++launches) {
+        const int m = next_launch_steps(ctx, G - n);
+        le = m == 3 ? launch_step3(ctx, b, ctx->cap_stream)
+                    : (m == 2 ? launch_step2(ctx, b, ctx->cap_stream) : launch_one_step(ctx, b, ctx->cap_stream));
+        n += m;
         b ^= 1;
     }
+    ctx->graph_launches[from] = launches;
     cudaGraph_t g = nullptr;
     cudaError_t ee = cudaStreamEndCapture(ctx->cap_stream, &g);
     if (le != cudaSuccess) {
@@ -698,7 +727,10 @@ lbrs_status lbrs_create(const lbrs_config* cfg, void* d_workspace, size_t bytes,
         return s;
     }
     if (fused2_f32(ctx))
-        for (int b = 0; b < 2; ++b) encode_f32_tile_map(&ctx->tmap[b], (const float*)ctx->f[b], cfg->nx, ctx->ny_store);
+        for (int b = 0; b < 2; ++b) {
+            encode_f32_tile_map(&ctx->tmap[b], (const float*)ctx->f[b], cfg->nx, ctx->ny_store);
+            encode_f32_tile_map3(&ctx->tmap3[b], (const float*)ctx->f[b], cfg->nx, ctx->ny_store);
+        }
     *out = ctx;
     return LBRS_OK;
 }
@@ -785,28 +817,26 @@ static lbrs_status step_plain(lbrs_ctx* ctx, int64_t n)
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     LBRS_CUDA(ctx, cudaStreamIsCapturing(ctx->stream, &cap));
     int64_t left = n;
-    if (cap == cudaStreamCaptureStatusNone && n >= 2 * kGraphSteps) {
+    const int G = graph_steps(ctx);
+    if (cap == cudaStreamCaptureStatusNone && n >= 2 * G) {
         lbrs_status st = ensure_graph(ctx, ctx->cur);
         if (st != LBRS_OK) return st;
-        const int per_graph = fused2(ctx) ? kGraphSteps / 2 : kGraphSteps;
-        while (left >= kGraphSteps) {
+        while (left >= G) {
             LBRS_CUDA(ctx, cudaGraphLaunch(ctx->graph[ctx->cur], ctx->stream));
-            left -= kGraphSteps;
-            ctx->step += kGraphSteps;
-            ctx->launches += per_graph;
+            left -= G;
+            ctx->step += G;
+            ctx->launches += ctx->graph_launches[ctx->cur];
         }
     }
-    for (; left >= 2 && fused2(ctx); left -= 2) {
-        LBRS_CUDA(ctx, launch_step2(ctx, ctx->cur, ctx->stream));
+    while (left > 0) {
+        const int m = next_launch_steps(ctx, left);
+        LBRS_CUDA(ctx, m == 3 ? launch_step3(ctx, ctx->cur, ctx->stream)
+                              : (m == 2 ? launch_step2(ctx, ctx->cur, ctx->stream)
+                                        : launch_one_step(ctx, ctx->cur, ctx->stream)));
         ctx->cur ^= 1;
-        ctx->step += 2;
+        ctx->step += m;
         ctx->launches += 1;
-    }
-    for (; left > 0; --left) {
-        LBRS_CUDA(ctx, launch_one_step(ctx, ctx->cur, ctx->stream));
-        ctx->cur ^= 1;
-        ctx->step += 1;
-        ctx->launches += 1;
+        left -= m;
     }
     return LBRS_OK;
 }

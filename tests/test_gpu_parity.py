@@ -365,13 +365,14 @@ np.save(sys.argv[2], np.concatenate(out))
 
 
 def test_f32_kernel_variants_agree(tmp_path):
-    """Scalar, vector-width and strided one-step kernels and the two-steps-per-launch kernel
-    compute the same steps.  The two-step kernel runs the scalar kernel's per-cell code (same
-    loads, boundary resolution and collision helper), so it must agree bit for bit; the other
-    variants up to FMA contraction.  The two-step kernel is fed by tensor copies where
-    nx % 4 == 0 and by direct loads otherwise (and everywhere with LBRS_F32_TMA=0).  51 steps:
-    a 32-step graph, then 9 two-step launches and one single step; then 7 recording steps
-    (moments of every step, as the adjoint recompute takes them)."""
+    """Scalar, vector-width and strided one-step kernels and the multi-step kernels compute the
+    same steps.  The three- and two-steps-per-launch kernels run the scalar kernel's per-cell code
+    (same loads, boundary resolution and collision helper), so they must agree bit for bit; the
+    other variants up to FMA contraction.  Where nx % 4 == 0 lbrs_step takes three steps per
+    launch (tensor copies of 40 x 20 boxes; with LBRS_F32_FUSE3=0 the two-step kernel's 36 x 18
+    copies), elsewhere two (direct loads; everywhere with LBRS_F32_TMA=0).  51 steps: a graph
+    (36 steps in threes, or 32 in twos), then the rest; then 7 recording steps (moments of every
+    step, as the adjoint recompute takes them)."""
     import os
     import subprocess
     import sys
@@ -379,17 +380,17 @@ def test_f32_kernel_variants_agree(tmp_path):
     script = tmp_path / "variant.py"
     script.write_text(_VARIANT_SCRIPT)
     res = {}
-    for v in ("0", "2", "4", "12", "14", "fused", "fused_direct"):
+    for v in ("0", "2", "4", "12", "14", "fused", "fused2", "fused_direct"):
         out = tmp_path / f"v{v}.npy"
         fused = v.startswith("fused")
         env = dict(os.environ, LBRS_F32_STEP_VARIANT="0" if fused else v, LBRS_F32_FUSE="1" if fused else "0",
-                   LBRS_F32_TMA="0" if v == "fused_direct" else "1")
+                   LBRS_F32_TMA="0" if v == "fused_direct" else "1", LBRS_F32_FUSE3="1" if v == "fused" else "0")
         subprocess.run([sys.executable, str(script), root, str(out)], check=True, env=env, timeout=300)
         res[v] = np.load(out)
     scale = np.abs(res["0"]).max()
     for v in ("2", "4", "12", "14"):
         assert np.max(np.abs(res[v] - res["0"])) <= 1e-5 * scale, v
-    for v in ("fused", "fused_direct"):
+    for v in ("fused", "fused2", "fused_direct"):
         assert np.array_equal(res[v], res["0"]), (v, np.max(np.abs(res[v] - res["0"])) / scale)
 
 
