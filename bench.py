@@ -519,7 +519,7 @@ def oblique_measurement(Solver, stream, barrier, peak):
         s = Solver.from_workload(big, precision=precision, stream=stream)
         with torch.cuda.stream(stream):
             s.set_state(torch.from_numpy(big.prim).cuda())
-            s.step(72)                       # two 36-step graphs: both captured before the timing
+            s.step(72)                       # a 36-step graph, captured before the timing
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             barrier()
             a.record(stream)
