@@ -14,7 +14,7 @@ the HBM roofline of the step kernel, an end-to-end figure through the public
 API with host buffers, and the FP64 CPU oracle timed on the host cores.
 
 Under torchrun with N > 1 ranks the same grid is split into N y-slabs, one per GPU, whose
-cut rows are exchanged with NCCL send/recv every two steps (strong scaling; see run_slabs).
+cut rows are exchanged with NCCL send/recv every three steps (strong scaling; see run_slabs).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -42,6 +42,7 @@ UNIT = "MLUPS"
 BYTES_PER_LUP_F32 = 128      # 16 FP32 distributions read + 16 written per cell and step
 BYTES_PER_LUP_F32_FUSED2 = 64  # two steps per launch: the 128 B per cell are read and written once per two steps
 BYTES_PER_LUP_F32_FUSED3 = 128 / 3   # three steps per launch: once per three steps
+SLAB_HALO = 3                 # ghost rows per cut with N > 1 GPUs: one exchange per three-step launch
 BYTES_PER_LUP_F64 = 256
 BYTES_PER_LUP_F16NEQ = 80     # U (4 x FP32) + 12 FP16 non-equilibrium parts, read + written
 BYTES_PER_LUP_F32U = 32       # omega = 1 moments-only form: U (4 x FP32), read + written
@@ -87,8 +88,8 @@ def config_dict(wl, extra=None):
 
 
 def parallelism(ws: int) -> str:
-    return "1 GPU" if ws == 1 else (f"{ws} y-slabs, one per GPU, 2 ghost rows per cut, NCCL send/recv of the "
-                                    "rows every two steps")
+    return "1 GPU" if ws == 1 else (f"{ws} y-slabs, one per GPU, {SLAB_HALO} ghost rows per cut, NCCL send/recv "
+                                    f"of the rows every {SLAB_HALO} steps")
 
 
 def dist_env():
@@ -836,8 +837,8 @@ def adjoint_measurement(Solver, stream, barrier, n=2048, steps=2000):
 
 def run_slabs(args, ws, rank, local):
     """N > 1 GPUs: the headline grid split into N y-slabs, one per GPU (strong scaling).  Each rank
-    steps its slab with the same FP32 kernels; before every two steps the ranks swap the two rows
-    next to each cut (16 FP32 planes x 2 rows x 1024 cells = 128 KiB per cut and direction) with
+    steps its slab with the same FP32 kernels; before every three steps the ranks swap the three rows
+    next to each cut (16 FP32 planes x 3 rows x 1024 cells = 192 KiB per cut and direction) with
     NCCL send/recv on the solver's stream.  Timed like the single-GPU headline: calls of two time
     steps (exchange + one launch of the two-step kernel), the L2 flushed before every call."""
     import torch
@@ -846,10 +847,10 @@ def run_slabs(args, ws, rank, local):
     from paper_1504_07034_gb300.solver import Solver
 
     wl = workload()
-    j0, j1 = slabs.slab_bounds(wl.ny, ws)[rank]
+    j0, j1 = slabs.slab_bounds(wl.ny, ws, SLAB_HALO)[rank]
     stream = torch.cuda.Stream()
-    s = Solver("d2q4", wl.nx, j1 - j0, lam=wl.lam, dx=wl.dx, bc=slabs.slab_bc(wl.bc, rank, ws), gamma=wl.gamma,
-               omega=wl.omega, precision="f32", stream=stream)
+    s = Solver("d2q4", wl.nx, j1 - j0, lam=wl.lam, dx=wl.dx, bc=slabs.slab_bc(wl.bc, rank, ws, SLAB_HALO),
+               gamma=wl.gamma, omega=wl.omega, precision="f32", stream=stream)
     run = slabs.DistSlab(s, rank, ws, slabs.is_periodic_y(wl.bc))
     W0 = torch.from_numpy(np.ascontiguousarray(wl.prim[:, j0:j1, :])).cuda()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -869,8 +870,8 @@ def run_slabs(args, ws, rank, local):
         run.invalidate()
         for _ in range(args.warmup):
             flush.fill_(1.0)
-            run.step(2)
-    plan = [2] * (args.steps // 2) + ([args.steps % 2] if args.steps % 2 else [])
+            run.step(SLAB_HALO)
+    plan = [SLAB_HALO] * (args.steps // SLAB_HALO) + ([args.steps % SLAB_HALO] if args.steps % SLAB_HALO else [])
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in plan]
     props = torch.cuda.get_device_properties(local)
     gpu_id = f"GPU-{props.uuid}" if getattr(props, "uuid", None) else str(local)
@@ -890,10 +891,10 @@ def run_slabs(args, ws, rank, local):
     ms = [a.elapsed_time(b) for a, b in ev]
     t = tmax(sum(ms) / 1e3)
     value = wl.cells * args.steps / t / 1e6
-    pair_s = tmax(statistics.mean([m for m, n in zip(ms, plan) if n == 2] or ms) / 1e3)
+    call_s = tmax(statistics.mean([m for m, n in zip(ms, plan) if n == SLAB_HALO] or ms) / 1e3)
     peak, peak_kind = hbm_peak()
     own_cells = wl.nx * (j1 - j0)
-    achieved = 2 * BYTES_PER_LUP_F32_FUSED2 * own_cells / pair_s / 1e9
+    achieved = 3 * BYTES_PER_LUP_F32_FUSED3 * own_cells / call_s / 1e9
     halo_bytes = sum(s.halo_size(side)[1] for side in (2, 3))
 
     # FP32 density L1 of the split run against the FP64 unsplit run is that of the unsplit FP32
@@ -959,8 +960,8 @@ def run_slabs(args, ws, rank, local):
             "gpu_launches": launches,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": "step2d_f32_fused2_tall_kernel<false>", "peak_kind": f"{peak_kind} hbm_gbs",
-                         "algorithmic_bytes_per_launch": 2 * BYTES_PER_LUP_F32_FUSED2 * own_cells,
+                         "kernel": "step2d_f32_fused3_kernel", "peak_kind": f"{peak_kind} hbm_gbs",
+                         "algorithmic_bytes_per_launch": 3 * BYTES_PER_LUP_F32_FUSED3 * own_cells,
                          "note": "per rank: the slab's two-step launch plus its halo exchange per timed call "
                                  "(the slowest rank)"},
             "halo_bytes_per_exchange_per_rank": halo_bytes,
