@@ -108,7 +108,7 @@ def kernel_source_sha() -> str:
 
 
 def measured_traffic(cells: int):
-    """DRAM bytes per launch of the FP32 two-step kernel from the committed ncu summary, if it is current."""
+    """DRAM bytes per launch of the FP32 three-step kernel from the committed ncu summary, if it is current."""
     path = os.path.join(ROOT, "profiles", "step2d_f32_fused3_traffic.json")
     try:
         with open(path) as fh:

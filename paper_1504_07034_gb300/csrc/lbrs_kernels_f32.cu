@@ -927,33 +927,45 @@ __device__ __forceinline__ void f3_walls(const StepArgs<float>& a, int j, float 
     }
 }
 
-__global__ void __launch_bounds__(kFTX * kFTY, 4)
-    step2d_f32_fused3_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs<float> a, unsigned* wait_flag)
+// Window slots by warp: pass p < WY is window row p, one slot a lane (32 contiguous positions of a
+// box row, so no two lanes share a bank); the passes after it take the columns beyond 32.  Returns
+// false for the lanes of the last pass that have no slot.
+template <int WX, int WY>
+__host__ __device__ constexpr int window_passes()
 {
-    extern __shared__ unsigned char smem_dyn[];
-    float* s = (float*)(((uintptr_t)smem_dyn + 127) & ~(uintptr_t)127);
-    uint64_t* bar_p = (uint64_t*)(s + 16 * kP3N);
-    const uint32_t bar = smem_addr(bar_p);
-    const int i0 = blockIdx.x * kFTX, j0 = blockIdx.y * kTY;
-    constexpr int kThr = kFTX * kFTY;
-    if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        issue_tile_copy3(&tmap, s, bar, i0, j0);
+    return WY + ((WX - 32) * WY + 31) / 32;
+}
+
+template <int WX, int WY>
+__device__ __forceinline__ bool window_slot(int p, int lane, int& wi, int& wj)
+{
+    if (p < WY) {
+        wi = lane;
+        wj = p;
+        return true;
     }
-    __syncthreads();
-    const bool arrived = mbar_wait_bounded(bar, 0, kWaitPolls);
-    if (!__syncthreads_and(arrived)) {
-        give_up_tile(bar, wait_flag);
-        return;
-    }
+    const int L = (p - WY) * 32 + lane;
+    wi = 32 + L % (WX - 32);
+    wj = L / (WX - 32);
+    return L < (WX - 32) * WY;
+}
+
+// The three steps of tile (i0, j0) from its boxes at s (landed), by THR threads.
+template <int THR>
+__device__ __forceinline__ void f3_tile(const StepArgs<float>& a, float* s, int i0, int j0)
+{
+    constexpr int kThr = THR;
     // every slot and every source of phase 1 inside the grid: no resolution anywhere
     const bool inside = i0 >= 3 && j0 >= 3 && i0 + kFTX + 3 <= a.nx && j0 + kTY + 3 <= a.ny;
 
+    // slots go to warps by window row (window_slot)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int kNW = kThr / 32;
+
     // phase 1: step n -> n+1 on the window, in place
-    for (int w = threadIdx.x; w < kW3N; w += kThr) {
-        const int wi = w % kW3X, wj = w / kW3X;
+    for (int p = warp; p < window_passes<kW3X, kW3Y>(); p += kNW) {
+        int wi, wj;
+        if (!window_slot<kW3X, kW3Y>(p, lane, wi, wj)) continue;
         float f[4][4];
         bool boxed = inside;
         if (!inside) {
@@ -1000,8 +1012,11 @@ __global__ void __launch_bounds__(kFTX * kFTY, 4)
     }
 
     // phase 2: step n+1 -> n+2 on the inner slots, each written over the positions it pulled
-    for (int b = threadIdx.x; b < kB3N; b += kThr) {
-        const int u = 1 + b % kB3X, v = 1 + b / kB3X;
+    for (int p = warp; p < window_passes<kB3X, kB3Y>(); p += kNW) {
+        int u, v;
+        if (!window_slot<kB3X, kB3Y>(p, lane, u, v)) continue;
+        ++u;                                          // slot (u, v) of the window, u, v >= 1
+        ++v;
         const int uj = j0 - 2 + v;
         if (!inside) {
             int ci, cj, gs;
@@ -1044,14 +1059,13 @@ __global__ void __launch_bounds__(kFTX * kFTY, 4)
         __syncthreads();
     }
 
-    // phase 3: step n+2 -> n+3 for the tile, two cells per thread
-    const int ti = threadIdx.x % kFTX;
+    // phase 3: step n+2 -> n+3 for the tile, one tile row a warp (kFTX * kTY / THR rows a warp)
 #pragma unroll
-    for (int rep = 0; rep < kTY / kFTY; ++rep) {
-        const int ty = threadIdx.x / kFTX + rep * kFTY;
-        const int i = i0 + ti, j = j0 + ty;
+    for (int rep = 0; rep < kFTX * kTY / THR; ++rep) {
+        const int ty = warp + rep * kNW;
+        const int i = i0 + lane, j = j0 + ty;
         if (i >= a.nx || j >= a.ny) continue;
-        const int x = ti + 2, y = ty + 2;
+        const int x = lane + 2, y = ty + 2;
         // population q of source slot (x - sx, y - sy) lies at (x - 2 sx, y - 2 sy)
         const int px[4] = {x + 2, x - 2, x - 2, x + 2};
         const int py[4] = {y + 2, y + 2, y - 2, y - 2};
@@ -1063,6 +1077,29 @@ __global__ void __launch_bounds__(kFTX * kFTY, 4)
         if (!inside) f3_walls(a, j, f);
         collide_store_2d<float>(a, (int64_t)j * a.nx + i, f);
     }
+}
+
+__global__ void __launch_bounds__(kFTX * kFTY, 4)
+    step2d_f32_fused3_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs<float> a, unsigned* wait_flag)
+{
+    extern __shared__ unsigned char smem_dyn[];
+    float* s = (float*)(((uintptr_t)smem_dyn + 127) & ~(uintptr_t)127);
+    uint64_t* bar_p = (uint64_t*)(s + 16 * kP3N);
+    const uint32_t bar = smem_addr(bar_p);
+    const int i0 = blockIdx.x * kFTX, j0 = blockIdx.y * kTY;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue_tile_copy3(&tmap, s, bar, i0, j0);
+    }
+    __syncthreads();
+    const bool arrived = mbar_wait_bounded(bar, 0, kWaitPolls);
+    if (!__syncthreads_and(arrived)) {
+        give_up_tile(bar, wait_flag);
+        return;
+    }
+    f3_tile<kFTX * kFTY>(a, s, i0, j0);
 }
 
 // Failure-detection self-test: one block waits, with the tile kernels' bounded wait,
