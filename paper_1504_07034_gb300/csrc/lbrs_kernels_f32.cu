@@ -873,6 +873,17 @@ __device__ __forceinline__ void issue_tile_copy3(const CUtensorMap* tmap, float*
             : "memory");
 }
 
+// An L2 prefetch of the four population boxes of tile (i0, j0), the boxes issue_tile_copy3 copies.
+__device__ __forceinline__ void prefetch_tile_l2_3(const CUtensorMap* tmap, int i0, int j0)
+{
+    const int y0[4] = {j0 - 1, j0 - 1, j0 - 3, j0 - 3};
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"((uint64_t)tmap),
+                     "r"(i0 - 4), "r"(y0[q]), "r"(q * 4)
+                     : "memory");
+}
+
 // How the window slot of unwrapped cell (ui, uj) gets its values: 0 computed there (inside the
 // grid, or beyond a periodic side: the wrapped cell); 1 the ghost of Dirichlet side *gs; 2 the
 // values of the slot of unwrapped cell (*ci, *cj) (a transmissive side's clamped cell); 3 none
@@ -1079,8 +1090,14 @@ __device__ __forceinline__ void f3_tile(const StepArgs<float>& a, float* s, int 
     }
 }
 
+// One block a tile.  Once its own boxes have landed, the block asks the L2 for the boxes of the
+// block `ahead` places later in launch order (ahead = the resident blocks of the device, 0 for
+// none): that block starts about one wave later, and its copies then find their data in the L2
+// instead of queueing behind the wave's DRAM reads.  The prefetch moves no byte that the launch
+// would not read anyway; it only reads it earlier.
 __global__ void __launch_bounds__(kFTX * kFTY, 4)
-    step2d_f32_fused3_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs<float> a, unsigned* wait_flag)
+    step2d_f32_fused3_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs<float> a, unsigned* wait_flag,
+                             int ahead)
 {
     extern __shared__ unsigned char smem_dyn[];
     float* s = (float*)(((uintptr_t)smem_dyn + 127) & ~(uintptr_t)127);
@@ -1098,6 +1115,11 @@ __global__ void __launch_bounds__(kFTX * kFTY, 4)
     if (!__syncthreads_and(arrived)) {
         give_up_tile(bar, wait_flag);
         return;
+    }
+    if (threadIdx.x == 0 && ahead > 0) {
+        const int64_t later = (int64_t)blockIdx.y * gridDim.x + blockIdx.x + ahead;
+        if (later < (int64_t)gridDim.x * gridDim.y)
+            prefetch_tile_l2_3(&tmap, (int)(later % gridDim.x) * kFTX, (int)(later / gridDim.x) * kTY);
     }
     f3_tile<kFTX * kFTY>(a, s, i0, j0);
 }
@@ -1579,6 +1601,24 @@ bool encode_f32_tile_map(TileMap* map, const float* f, int64_t nx, int64_t ny)
     return true;
 }
 
+// Resident blocks of the three-step kernel on the current device (SMs x blocks per SM), the
+// distance of its L2 prefetch; 0 (no prefetch) with LBRS_F32_PREFETCH=0 or if the query fails.
+static int step3_prefetch_ahead()
+{
+    static int v = [] {
+        const char* e = getenv("LBRS_F32_PREFETCH");
+        if (e && !strcmp(e, "0")) return 0;
+        int dev = 0, sms = 0, per = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step2d_f32_fused3_kernel, kFTX * kFTY,
+                                                          kF3SmemBytes) != cudaSuccess)
+            return 0;
+        return sms * per;
+    }();
+    return v;
+}
+
 // The tensor map of the three-step kernel: 40 x 20 x 4-field boxes of the state.
 bool encode_f32_tile_map3(TileMap* map, const float* f, int64_t nx, int64_t ny)
 {
@@ -1593,6 +1633,7 @@ bool encode_f32_tile_map3(TileMap* map, const float* f, int64_t nx, int64_t ny)
                                         (int)kF3SmemBytes);
     });
     if (attr_err != cudaSuccess) return false;
+    step3_prefetch_ahead();   // its device queries now, not first inside a graph capture
     const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, 16};
     const cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)(nx * ny) * 4};
     const cuuint32_t box[3] = {(cuuint32_t)kP3X, (cuuint32_t)kW3Y, 4};
@@ -1622,7 +1663,8 @@ cudaError_t launch_step3_f32(const StepArgs<float>& a, const TileMap* map3, unsi
     CUtensorMap m;
     memcpy(&m, map3->bytes, sizeof m);
     const dim3 grid((unsigned)((a.nx + kFTX - 1) / kFTX), (unsigned)((a.ny + kTY - 1) / kTY));
-    step2d_f32_fused3_kernel<<<grid, kFTX * kFTY, kF3SmemBytes, s>>>(m, a, wait_flag);
+    const int ahead = step3_prefetch_ahead();
+    step2d_f32_fused3_kernel<<<grid, kFTX * kFTY, kF3SmemBytes, s>>>(m, a, wait_flag, ahead);
     return cudaGetLastError();
 }
 
