@@ -189,6 +189,16 @@ lbrs_status lbrs_debug_check(uint64_t* first);
  * be exercised without a fault.  The distributions are not touched. */
 lbrs_status lbrs_selftest_wait_timeout(lbrs_ctx* ctx);
 
+/* Arithmetic self-test (not a method of the paper).  The FP32 kernels form the
+ * velocities u = (rho u) / rho with one reciprocal of rho: the hardware's approximate
+ * reciprocal refined by one Newton-Raphson step for 1/x, r = r0 + r0 (1 - x r0).  This
+ * call writes that reciprocal of x[i] to r[i], i < n, so that its error can be checked
+ * against the exact quotient.  x and r: device buffers of n floats (caller-owned, not
+ * aliased); the work is enqueued on cuda_stream (a cudaStream_t, NULL for the legacy
+ * default stream) and not waited for.  LBRS_EINVAL for n < 0 or a NULL buffer with
+ * n > 0; LBRS_ECUDA if the launch fails. */
+lbrs_status lbrs_selftest_rcp_f32(const float* x, float* r, int64_t n, void* cuda_stream);
+
 /* Human-readable name of a status code. Never NULL. */
 const char* lbrs_status_string(lbrs_status s);
 

@@ -87,6 +87,7 @@ SIGNATURES = {
     "lbrs_abi_version": (ctypes.c_int, []),
     "lbrs_debug_build": (ctypes.c_int, []),
     "lbrs_selftest_wait_timeout": (ctypes.c_int, [_CTX]),
+    "lbrs_selftest_rcp_f32": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
     "lbrs_debug_check": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64)]),
     "lbrs_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "lbrs_workspace_size": (ctypes.c_int, [ctypes.POINTER(lbrs_config), ctypes.POINTER(ctypes.c_size_t)]),

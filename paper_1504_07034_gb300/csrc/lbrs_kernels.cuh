@@ -93,8 +93,20 @@ struct StepArgs {
 
 // ---------------------------------------------------------------- arithmetic
 
+// The FP32 reciprocal of a density: the hardware's approximate reciprocal r0
+// (within one unit in the last place; subnormal input or output flushed to zero,
+// which a density of a valid state never is), refined by one Newton-Raphson step
+// for 1/x, r = r0 + r0 (1 - x r0), both products fused.
+__device__ __forceinline__ float rcp_f32(float x)
+{
+    float r0;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(x));
+    const float e = __fmaf_rn(-x, r0, 1.f);
+    return __fmaf_rn(r0, e, r0);
+}
+
 // Velocities from momenta: IEEE divisions in FP64 (same rounding as the plain
-// expressions), one correctly rounded reciprocal in FP32.
+// expressions), one approximate reciprocal in FP32 (rcp_f32).
 template <typename T>
 __device__ __forceinline__ void velocity2(T rho, T mx, T my, T& u, T& v)
 {
@@ -102,7 +114,7 @@ __device__ __forceinline__ void velocity2(T rho, T mx, T my, T& u, T& v)
         u = mx / rho;
         v = my / rho;
     } else {
-        const float inv = __frcp_rn(rho);
+        const float inv = rcp_f32(rho);
         u = mx * inv;
         v = my * inv;
     }
@@ -114,7 +126,7 @@ __device__ __forceinline__ T velocity1(T rho, T m)
     if constexpr (std::is_same<T, double>::value) {
         return m / rho;
     } else {
-        return m * __frcp_rn(rho);
+        return m * rcp_f32(rho);
     }
 }
 
@@ -542,7 +554,7 @@ __device__ __forceinline__ double bound2d(const T U[4], double gamma)
 }
 
 // The local bound in the storage precision: bound2d for FP64 (the oracle's
-// expressions); in FP32 one correctly rounded reciprocal of rho (the one the
+// expressions); in FP32 one reciprocal of rho (rcp_f32, the one the
 // collision's velocities use) and one square root, sqrt(2 gamma p / rho) for
 // sqrt(2) a.
 template <typename T>
@@ -550,7 +562,7 @@ __device__ __forceinline__ T bound_local(const T U[4], double gamma)
 {
     if constexpr (std::is_same<T, float>::value) {
         const float g = (float)gamma, gm1 = (float)(gamma - 1.0);
-        const float inv = __frcp_rn(U[0]);
+        const float inv = rcp_f32(U[0]);
         const float u = U[1] * inv, v = U[2] * inv;
         const float p = gm1 * (U[3] - 0.5f * (U[1] * u + U[2] * v));
         if (!(U[0] > 0.f) || !(p > 0.f) || !isfinite(p)) return -1.f;

@@ -1,7 +1,7 @@
 // FP32 time step of the LBRS solver (distributions stored and updated in FP32).
 //
-// Compiled with FMA contraction allowed; velocities use one correctly rounded
-// reciprocal per cell.  The numerics differ from the FP64 path by rounding
+// Compiled with FMA contraction allowed; velocities use one reciprocal per cell
+// (rcp_f32: the hardware approximation refined by one Newton-Raphson step).  The numerics differ from the FP64 path by rounding
 // only; their distance to the FP64 oracle is measured, not assumed.
 //
 // D2Q4 uses a vectorised kernel when nx is a multiple of the vector width V:
@@ -1698,6 +1698,21 @@ cudaError_t launch_step2_f32(const StepArgs<float>& a, const TileMap* map, unsig
             else step2d_f32_fused2_kernel<false, false><<<grid, kFTX * kFTY, 0, s>>>(a);
         }
     }
+    return cudaGetLastError();
+}
+
+// rcp_f32 over n inputs, for its error-bound test.
+__global__ void rcp_selftest_kernel(const float* __restrict__ x, float* __restrict__ r, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        r[i] = rcp_f32(x[i]);
+}
+
+cudaError_t launch_rcp_selftest(const float* x, float* r, int64_t n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const int64_t blocks = (n + 255) / 256;
+    rcp_selftest_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(x, r, n);
     return cudaGetLastError();
 }
 

@@ -40,6 +40,7 @@ unsigned long long debug_word_f16(int clear);
 // Failure-detection self-test: a bounded wait on an mbarrier that nothing completes
 // gives up and raises *wait_flag (one block, 4096 polls).
 cudaError_t launch_wait_timeout_selftest(unsigned* wait_flag, cudaStream_t s);
+cudaError_t launch_rcp_selftest(const float* x, float* r, int64_t n, cudaStream_t s);
 
 // One time step src -> dst.  lattice: LAT_D1Q2 / LAT_D2Q4.
 cudaError_t launch_step_f64(int lattice, const StepArgs<double>& a, cudaStream_t s);

@@ -623,6 +623,14 @@ lbrs_status lbrs_selftest_wait_timeout(lbrs_ctx* ctx)
     return LBRS_OK;
 }
 
+lbrs_status lbrs_selftest_rcp_f32(const float* x, float* r, int64_t n, void* cuda_stream)
+{
+    if (n < 0 || (n > 0 && (!x || !r))) return fail(nullptr, LBRS_EINVAL, "x and r must be device buffers of n >= 0 floats");
+    const cudaError_t e = launch_rcp_selftest(x, r, n, (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) return fail(nullptr, LBRS_ECUDA, cudaGetErrorString(e));
+    return LBRS_OK;
+}
+
 int lbrs_debug_build(void)
 {
 #ifdef LBRS_DEBUG
