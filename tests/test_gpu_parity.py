@@ -394,6 +394,22 @@ def test_f32_kernel_variants_agree(tmp_path):
         assert np.array_equal(res[v], res["0"]), (v, np.max(np.abs(res[v] - res["0"])) / scale)
 
 
+def test_f32_three_steps_take_one_launch():
+    """Where nx % 4 == 0 the FP32 path advances three steps with one launch of the three-step kernel
+    (its tensor map accepted on this device); a grid it cannot tile takes more launches."""
+    from paper_1504_07034_gb300.solver import Solver
+    wl = W.quadrant_riemann(1, 64, steps=0)
+    for nx, launches in ((256, 1), (66, 2)):
+        prim = np.ascontiguousarray(np.tile(wl.prim, (1, 1, 5))[:, :, :nx])
+        s = Solver("d2q4", nx, 64, lam=wl.lam, dx=1.0 / 64, bc=[("transmissive", None)] * 4, precision="f32")
+        s.set_state(torch.from_numpy(prim).cuda())
+        l0 = s.launch_count
+        s.step(3)
+        torch.cuda.synchronize()
+        assert s.launch_count - l0 == launches, (nx, s.launch_count - l0)
+        s.close()
+
+
 # ------------------------------------------------------------------- periodic device checks
 
 @pytest.mark.parametrize("every", [1, 5])
