@@ -961,8 +961,10 @@ __device__ __forceinline__ bool window_slot(int p, int lane, int& wi, int& wj)
     return L < (WX - 32) * WY;
 }
 
-// The three steps of tile (i0, j0) from its boxes at s (landed), by THR threads.
-template <int THR>
+// The three steps of tile (i0, j0) from its boxes at s (landed), by THR threads.  STORE_U: a
+// recording launch, which also writes the moments of each step's collision for the tile's cells to
+// a.Uout (step n+1), a.Uout + 4N (n+2) and a.Uout + 8N (n+3), as three recording steps would.
+template <int THR, bool STORE_U>
 __device__ __forceinline__ void f3_tile(const StepArgs<float>& a, float* s, int i0, int j0)
 {
     constexpr int kThr = THR;
@@ -1002,6 +1004,13 @@ __device__ __forceinline__ void f3_tile(const StepArgs<float>& a, float* s, int 
         for (int q = 0; q < 4; ++q)
 #pragma unroll
             for (int k = 0; k < 4; ++k) s[LBRS_IX(f3_pos(q, k, wi, wj), 16 * kP3N, 23)] = out[q][k];
+        if constexpr (STORE_U) {
+            const int i = i0 - 2 + wi, j = j0 - 2 + wj;
+            if (wi >= 2 && wi < 2 + kFTX && wj >= 2 && wj < 2 + kTY && i < a.nx && j < a.ny) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) a.Uout[LBRS_IX(k * a.N + (int64_t)j * a.nx + i, 4 * a.N, 29)] = U[k];
+            }
+        }
     }
     __syncthreads();
     if (!inside) {
@@ -1048,6 +1057,14 @@ __device__ __forceinline__ void f3_tile(const StepArgs<float>& a, float* s, int 
         for (int q = 0; q < 4; ++q)
 #pragma unroll
             for (int k = 0; k < 4; ++k) s[LBRS_IX(f3_pos(q, k, su[q], sv[q]), 16 * kP3N, 24)] = out[q][k];
+        if constexpr (STORE_U) {
+            const int i = i0 - 2 + u;
+            if (u >= 2 && u < 2 + kFTX && v >= 2 && v < 2 + kTY && i < a.nx && uj < a.ny) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    a.Uout[LBRS_IX((4 + k) * a.N + (int64_t)uj * a.nx + i, 8 * a.N, 29)] = U[k];
+            }
+        }
     }
     __syncthreads();
     if (!inside) {
@@ -1086,7 +1103,13 @@ __device__ __forceinline__ void f3_tile(const StepArgs<float>& a, float* s, int 
 #pragma unroll
             for (int k = 0; k < 4; ++k) f[q][k] = s[LBRS_IX(f3_pos(q, k, px[q], py[q]), 16 * kP3N, 25)];
         if (!inside) f3_walls(a, j, f);
-        collide_store_2d<float>(a, (int64_t)j * a.nx + i, f);
+        if constexpr (STORE_U) {
+            StepArgs<float> c = a;
+            c.Uout = a.Uout + 8 * a.N;
+            collide_store_2d<float, true>(c, (int64_t)j * a.nx + i, f);
+        } else {
+            collide_store_2d<float>(a, (int64_t)j * a.nx + i, f);
+        }
     }
 }
 
@@ -1095,6 +1118,7 @@ __device__ __forceinline__ void f3_tile(const StepArgs<float>& a, float* s, int 
 // none): that block starts about one wave later, and its copies then find their data in the L2
 // instead of queueing behind the wave's DRAM reads.  The prefetch moves no byte that the launch
 // would not read anyway; it only reads it earlier.
+template <bool STORE_U>
 __global__ void __launch_bounds__(kFTX * kFTY, 4)
     step2d_f32_fused3_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs<float> a, unsigned* wait_flag,
                              int ahead)
@@ -1121,7 +1145,7 @@ __global__ void __launch_bounds__(kFTX * kFTY, 4)
         if (later < (int64_t)gridDim.x * gridDim.y)
             prefetch_tile_l2_3(&tmap, (int)(later % gridDim.x) * kFTX, (int)(later / gridDim.x) * kTY);
     }
-    f3_tile<kFTX * kFTY>(a, s, i0, j0);
+    f3_tile<kFTX * kFTY, STORE_U>(a, s, i0, j0);
 }
 
 // Failure-detection self-test: one block waits, with the tile kernels' bounded wait,
@@ -1611,7 +1635,7 @@ static int step3_prefetch_ahead()
         int dev = 0, sms = 0, per = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step2d_f32_fused3_kernel, kFTX * kFTY,
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step2d_f32_fused3_kernel<false>, kFTX * kFTY,
                                                           kF3SmemBytes) != cudaSuccess)
             return 0;
         return sms * per;
@@ -1629,8 +1653,11 @@ bool encode_f32_tile_map3(TileMap* map, const float* f, int64_t nx, int64_t ny)
     static std::once_flag attr_once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(attr_once, [] {
-        attr_err = cudaFuncSetAttribute(step2d_f32_fused3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        attr_err = cudaFuncSetAttribute(step2d_f32_fused3_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)kF3SmemBytes);
+        if (attr_err == cudaSuccess)
+            attr_err = cudaFuncSetAttribute(step2d_f32_fused3_kernel<true>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kF3SmemBytes);
     });
     if (attr_err != cudaSuccess) return false;
     step3_prefetch_ahead();   // its device queries now, not first inside a graph capture
@@ -1657,14 +1684,19 @@ bool step3_f32_enabled()
     return v != 0;
 }
 
+// Three steps; with a.Uout set, three recording steps (the moments of each step to a.Uout, one
+// step's 4 N values after another).
 cudaError_t launch_step3_f32(const StepArgs<float>& a, const TileMap* map3, unsigned* wait_flag, cudaStream_t s)
 {
-    if (!map3 || !map3->valid || !wait_flag || a.solid || a.Uout) return cudaErrorInvalidValue;
+    if (!map3 || !map3->valid || !wait_flag || a.solid) return cudaErrorInvalidValue;
     CUtensorMap m;
     memcpy(&m, map3->bytes, sizeof m);
     const dim3 grid((unsigned)((a.nx + kFTX - 1) / kFTX), (unsigned)((a.ny + kTY - 1) / kTY));
     const int ahead = step3_prefetch_ahead();
-    step2d_f32_fused3_kernel<<<grid, kFTX * kFTY, kF3SmemBytes, s>>>(m, a, wait_flag, ahead);
+    if (a.Uout)
+        step2d_f32_fused3_kernel<true><<<grid, kFTX * kFTY, kF3SmemBytes, s>>>(m, a, wait_flag, ahead);
+    else
+        step2d_f32_fused3_kernel<false><<<grid, kFTX * kFTY, kF3SmemBytes, s>>>(m, a, wait_flag, ahead);
     return cudaGetLastError();
 }
 

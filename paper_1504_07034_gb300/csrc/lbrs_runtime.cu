@@ -546,12 +546,26 @@ cudaError_t launch_record_step2(lbrs_ctx* ctx, void* Uout)
     return launch_step2_f32(a, &ctx->tmap[ctx->cur], wait_flag(ctx), ctx->stream);
 }
 
+// Three recording steps in one launch (FP32 D2Q4, where the three-step kernel applies).
+cudaError_t launch_record_step3(lbrs_ctx* ctx, void* Uout)
+{
+    StepArgs<float> a = step_args<float>(ctx, ctx->cur);
+    a.Uout = (float*)Uout;
+    return launch_step3_f32(a, &ctx->tmap3[ctx->cur], wait_flag(ctx), ctx->stream);
+}
+
 // n recording steps from the current buffer into U_hist (stride: one step's moments),
-// in pairs where the two-step kernel applies.
+// in threes where the three-step kernel applies (but 2 + 2 rather than 3 + 1), then in pairs
+// where the two-step kernel does.
 lbrs_status record_steps(lbrs_ctx* ctx, int64_t n, char* U_hist)
 {
     const size_t stride = (size_t)ctx->K * ctx->N * elem_bytes(ctx);
     int64_t m = 0;
+    for (; m + 3 <= n && n - m != 4 && fused3(ctx); m += 3) {
+        LBRS_CUDA(ctx, launch_record_step3(ctx, U_hist + m * stride));
+        ctx->cur ^= 1;
+        ctx->launches += 1;
+    }
     for (; m + 2 <= n && fused2_f32(ctx) && !ctx->solid; m += 2) {
         LBRS_CUDA(ctx, launch_record_step2(ctx, U_hist + m * stride));
         ctx->cur ^= 1;
