@@ -803,7 +803,11 @@ __device__ __forceinline__ void equilibrium_vjp2d(const T U[4], const T g[4][4],
     T u, v;
     velocity2<T>(rho, mx, my, u, v);
     const T p = gm1 * (en - T(0.5) * (mx * u + my * v));
-    const T H = (en + p) / rho;
+    T H;
+    if constexpr (std::is_same<T, double>::value)
+        H = (en + p) / rho;
+    else
+        H = (en + p) * rcp_f32(rho);   // the reciprocal the velocities used
     const T q2h = T(0.5) * gm1 * (u * u + v * v);
     const T dF[4][4] = {{T(0), T(1), T(0), T(0)},
                         {q2h - u * u, (T(3) - gamma) * u, -gm1 * v, gm1},

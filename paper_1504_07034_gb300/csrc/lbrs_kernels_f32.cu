@@ -225,8 +225,13 @@ __global__ void __launch_bounds__(128) step2d_f32_ilp_kernel(const StepArgs<floa
 // cell.  The state is read and written once per two steps.
 constexpr int kFTX = 32, kFTY = 8, kFWX = kFTX + 2, kFWY = kFTY + 2, kFWN = kFWX * kFWY;
 
+// x modulo n in [0, n): without a division for x within one period of the range, the case of
+// every neighbour and window offset on a grid at least as wide as the window.
 __device__ __forceinline__ int wrap_index(int x, int n)
 {
+    if (x >= 0 && x < n) return x;
+    if (x < 0 && x >= -n) return x + n;
+    if (x >= n && x - n < n) return x - n;
     x %= n;
     return x < 0 ? x + n : x;
 }
