@@ -833,14 +833,15 @@ __global__ void __launch_bounds__(kFTX * kFTY, 5)
 // ---------------------------------------------------------------- three steps per launch, TMA-fed
 //
 // The state is read and written once per three steps (128 B per cell and launch, 42.7 B per
-// lattice update).  A block owns a 32 x 16 tile; window slot (wi, wj), wi < 36, wj < 20, is the
+// lattice update).  A block of 192 threads owns a 32 x 12 tile (five blocks per SM: 41 KB of boxes and
+// 64 registers each); window slot (wi, wj), wi < 36, wj < 16, is the
 // cell (i0 - 2 + wi, j0 - 2 + wj) (the tile and two cells of halo).  Four tensor copies bring,
-// per population q, the 40 x 20 x 4-field box of the values that the window's slots pull
+// per population q, the 40 x 16 x 4-field box of the values that the window's slots pull
 // (shifted by the velocity, x starting on a 16-byte boundary at i0 - 4): position f3_pos(q, k,
 // wi, wj) holds what slot (wi, wj) pulls.
 //   phase 1  step n -> n+1 on the window, each slot's results written over the positions it
 //            pulled them from (one reader per position);
-//   phase 2  step n+1 -> n+2 on the 34 x 18 inner slots: slot (u, v) pulls population q from
+//   phase 2  step n+1 -> n+2 on the 34 x 14 inner slots: slot (u, v) pulls population q from
 //            slot (u - sx, v - sy), at f3_pos(q, ., u - sx, v - sy), and writes its own
 //            population q over that same position (again one reader per position);
 //   phase 3  step n+2 -> n+3 for the tile: cell (x, y) finds population q of its source slot
@@ -850,11 +851,12 @@ __global__ void __launch_bounds__(kFTX * kFTY, 5)
 // ghost, or the clamped cell's values, x side first), so phases 2 and 3 gather uniformly.  Slots
 // beyond a periodic side compute the wrapped cell (by the global pull of the single-step kernel:
 // the boxes hold the copy's fill there).  Every value is formed with the single-step kernel's
-// arithmetic, so three steps are bit-identical to single steps.  Not for internal walls, halfway
-// walls or recording steps (those take the two-step kernel).
+// arithmetic, so three steps are bit-identical to single steps.  Not for internal walls or halfway
+// walls (those take the two-step kernel).
+constexpr int kT3Y = 12, kT3T = 192, kT3B = 5;             // tile rows, threads and blocks per SM
 constexpr int kP3X = 40;                                    // box columns
-constexpr int kW3X = 36, kW3Y = kTY + 4, kW3N = kW3X * kW3Y;   // phase-1 window (tile + 2 halo)
-constexpr int kB3X = 34, kB3Y = kTY + 2, kB3N = kB3X * kB3Y;   // phase-2 slots (tile + 1 halo)
+constexpr int kW3X = 36, kW3Y = kT3Y + 4, kW3N = kW3X * kW3Y;  // phase-1 window (tile + 2 halo)
+constexpr int kB3X = 34, kB3Y = kT3Y + 2, kB3N = kB3X * kB3Y;  // phase-2 slots (tile + 1 halo)
 constexpr int kP3N = kP3X * kW3Y;                           // floats per field plane of a box
 constexpr size_t kF3SmemBytes = 128 + 16u * kP3N * sizeof(float) + 16;
 
@@ -974,7 +976,7 @@ __device__ __forceinline__ void f3_tile(const StepArgs<float>& a, float* s, int 
 {
     constexpr int kThr = THR;
     // every slot and every source of phase 1 inside the grid: no resolution anywhere
-    const bool inside = i0 >= 3 && j0 >= 3 && i0 + kFTX + 3 <= a.nx && j0 + kTY + 3 <= a.ny;
+    const bool inside = i0 >= 3 && j0 >= 3 && i0 + kFTX + 3 <= a.nx && j0 + kT3Y + 3 <= a.ny;
 
     // slots go to warps by window row (window_slot)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1011,7 +1013,7 @@ __device__ __forceinline__ void f3_tile(const StepArgs<float>& a, float* s, int 
             for (int k = 0; k < 4; ++k) s[LBRS_IX(f3_pos(q, k, wi, wj), 16 * kP3N, 23)] = out[q][k];
         if constexpr (STORE_U) {
             const int i = i0 - 2 + wi, j = j0 - 2 + wj;
-            if (wi >= 2 && wi < 2 + kFTX && wj >= 2 && wj < 2 + kTY && i < a.nx && j < a.ny) {
+            if (wi >= 2 && wi < 2 + kFTX && wj >= 2 && wj < 2 + kT3Y && i < a.nx && j < a.ny) {
 #pragma unroll
                 for (int k = 0; k < 4; ++k) a.Uout[LBRS_IX(k * a.N + (int64_t)j * a.nx + i, 4 * a.N, 29)] = U[k];
             }
@@ -1064,7 +1066,7 @@ __device__ __forceinline__ void f3_tile(const StepArgs<float>& a, float* s, int 
             for (int k = 0; k < 4; ++k) s[LBRS_IX(f3_pos(q, k, su[q], sv[q]), 16 * kP3N, 24)] = out[q][k];
         if constexpr (STORE_U) {
             const int i = i0 - 2 + u;
-            if (u >= 2 && u < 2 + kFTX && v >= 2 && v < 2 + kTY && i < a.nx && uj < a.ny) {
+            if (u >= 2 && u < 2 + kFTX && v >= 2 && v < 2 + kT3Y && i < a.nx && uj < a.ny) {
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
                     a.Uout[LBRS_IX((4 + k) * a.N + (int64_t)uj * a.nx + i, 8 * a.N, 29)] = U[k];
@@ -1092,9 +1094,9 @@ __device__ __forceinline__ void f3_tile(const StepArgs<float>& a, float* s, int 
         __syncthreads();
     }
 
-    // phase 3: step n+2 -> n+3 for the tile, one tile row a warp (kFTX * kTY / THR rows a warp)
+    // phase 3: step n+2 -> n+3 for the tile, one tile row a warp (kFTX * kT3Y / THR rows a warp)
 #pragma unroll
-    for (int rep = 0; rep < kFTX * kTY / THR; ++rep) {
+    for (int rep = 0; rep < kFTX * kT3Y / THR; ++rep) {
         const int ty = warp + rep * kNW;
         const int i = i0 + lane, j = j0 + ty;
         if (i >= a.nx || j >= a.ny) continue;
@@ -1124,7 +1126,7 @@ __device__ __forceinline__ void f3_tile(const StepArgs<float>& a, float* s, int 
 // instead of queueing behind the wave's DRAM reads.  The prefetch moves no byte that the launch
 // would not read anyway; it only reads it earlier.
 template <bool STORE_U>
-__global__ void __launch_bounds__(kFTX * kFTY, 4)
+__global__ void __launch_bounds__(kT3T, kT3B)
     step2d_f32_fused3_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs<float> a, unsigned* wait_flag,
                              int ahead)
 {
@@ -1132,7 +1134,7 @@ __global__ void __launch_bounds__(kFTX * kFTY, 4)
     float* s = (float*)(((uintptr_t)smem_dyn + 127) & ~(uintptr_t)127);
     uint64_t* bar_p = (uint64_t*)(s + 16 * kP3N);
     const uint32_t bar = smem_addr(bar_p);
-    const int i0 = blockIdx.x * kFTX, j0 = blockIdx.y * kTY;
+    const int i0 = blockIdx.x * kFTX, j0 = blockIdx.y * kT3Y;
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1148,9 +1150,9 @@ __global__ void __launch_bounds__(kFTX * kFTY, 4)
     if (threadIdx.x == 0 && ahead > 0) {
         const int64_t later = (int64_t)blockIdx.y * gridDim.x + blockIdx.x + ahead;
         if (later < (int64_t)gridDim.x * gridDim.y)
-            prefetch_tile_l2_3(&tmap, (int)(later % gridDim.x) * kFTX, (int)(later / gridDim.x) * kTY);
+            prefetch_tile_l2_3(&tmap, (int)(later % gridDim.x) * kFTX, (int)(later / gridDim.x) * kT3Y);
     }
-    f3_tile<kFTX * kFTY, STORE_U>(a, s, i0, j0);
+    f3_tile<kT3T, STORE_U>(a, s, i0, j0);
 }
 
 // Failure-detection self-test: one block waits, with the tile kernels' bounded wait,
@@ -1640,7 +1642,7 @@ static int step3_prefetch_ahead()
         int dev = 0, sms = 0, per = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step2d_f32_fused3_kernel<false>, kFTX * kFTY,
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step2d_f32_fused3_kernel<false>, kT3T,
                                                           kF3SmemBytes) != cudaSuccess)
             return 0;
         return sms * per;
@@ -1648,7 +1650,7 @@ static int step3_prefetch_ahead()
     return v;
 }
 
-// The tensor map of the three-step kernel: 40 x 20 x 4-field boxes of the state.
+// The tensor map of the three-step kernel: 40 x 16 x 4-field boxes of the state.
 bool encode_f32_tile_map3(TileMap* map, const float* f, int64_t nx, int64_t ny)
 {
     map->valid = 0;
@@ -1696,12 +1698,12 @@ cudaError_t launch_step3_f32(const StepArgs<float>& a, const TileMap* map3, unsi
     if (!map3 || !map3->valid || !wait_flag || a.solid) return cudaErrorInvalidValue;
     CUtensorMap m;
     memcpy(&m, map3->bytes, sizeof m);
-    const dim3 grid((unsigned)((a.nx + kFTX - 1) / kFTX), (unsigned)((a.ny + kTY - 1) / kTY));
+    const dim3 grid((unsigned)((a.nx + kFTX - 1) / kFTX), (unsigned)((a.ny + kT3Y - 1) / kT3Y));
     const int ahead = step3_prefetch_ahead();
     if (a.Uout)
-        step2d_f32_fused3_kernel<true><<<grid, kFTX * kFTY, kF3SmemBytes, s>>>(m, a, wait_flag, ahead);
+        step2d_f32_fused3_kernel<true><<<grid, kT3T, kF3SmemBytes, s>>>(m, a, wait_flag, ahead);
     else
-        step2d_f32_fused3_kernel<false><<<grid, kFTX * kFTY, kF3SmemBytes, s>>>(m, a, wait_flag, ahead);
+        step2d_f32_fused3_kernel<false><<<grid, kT3T, kF3SmemBytes, s>>>(m, a, wait_flag, ahead);
     return cudaGetLastError();
 }
 
