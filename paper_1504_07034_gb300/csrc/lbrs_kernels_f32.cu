@@ -1121,9 +1121,9 @@ __device__ __forceinline__ void f3_tile(const StepArgs<float>& a, float* s, int 
 }
 
 // One block a tile.  Once its own boxes have landed, the block asks the L2 for the boxes of the
-// block `ahead` places later in launch order (ahead = the resident blocks of the device, 0 for
-// none): that block starts about one wave later, and its copies then find their data in the L2
-// instead of queueing behind the wave's DRAM reads.  The prefetch moves no byte that the launch
+// block `ahead` places later in launch order (ahead = half the resident blocks of the device, 0
+// for none): that block starts about half a wave later, and its copies then find their data in the
+// L2 instead of queueing behind the wave's DRAM reads.  The prefetch moves no byte that the launch
 // would not read anyway; it only reads it earlier.
 template <bool STORE_U>
 __global__ void __launch_bounds__(kT3T, kT3B)
@@ -1632,20 +1632,23 @@ bool encode_f32_tile_map(TileMap* map, const float* f, int64_t nx, int64_t ny)
     return true;
 }
 
-// Resident blocks of the three-step kernel on the current device (SMs x blocks per SM), the
-// distance of its L2 prefetch; 0 (no prefetch) with LBRS_F32_PREFETCH=0 or if the query fails.
+// The distance of the three-step kernel's L2 prefetch: half its resident blocks on the current
+// device (SMs x blocks per SM / 2; measured on 1024^2 and 4096 x 1024 grids: a plateau from 0.5 to
+// 0.8 of a wave, below it at one wave or more); LBRS_F32_PREFETCH=n > 1 sets it, =0 turns the
+// prefetch off; 0 if the query fails.
 static int step3_prefetch_ahead()
 {
     static int v = [] {
         const char* e = getenv("LBRS_F32_PREFETCH");
         if (e && !strcmp(e, "0")) return 0;
+        if (e && atoi(e) > 1) return atoi(e);
         int dev = 0, sms = 0, per = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step2d_f32_fused3_kernel<false>, kT3T,
                                                           kF3SmemBytes) != cudaSuccess)
             return 0;
-        return sms * per;
+        return sms * per / 2;
     }();
     return v;
 }
