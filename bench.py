@@ -543,7 +543,27 @@ def oblique_measurement(Solver, stream, barrier, peak):
             for precision in forms:
                 s = Solver.from_workload(wl, precision=precision, stream=stream)
                 s.set_state(torch.from_numpy(wl.prim).cuda())
-                s.step(steps)
+                if precision == "f64" and omega == 1.0:
+                    # conservation against the sides' fluxes: at ten points of the run, the change of the
+                    # FP64 totals over one step against that step's boundary balance
+                    t_first = np.array(s.diagnostics()["totals"])
+                    drift, chunk = 0.0, steps // 10
+                    for _ in range(10):
+                        t0 = np.array(s.diagnostics()["totals"])
+                        fl = s.boundary_flux()
+                        s.step(1)
+                        t1 = np.array(s.diagnostics()["totals"])
+                        net = np.array(fl["inflow"]) - np.array(fl["outflow"])
+                        drift = max(drift, float(np.max(np.abs((t1 - t0) - net) / np.abs(t0))))
+                        s.step(chunk - 1)
+                    t_last = np.array(s.diagnostics()["totals"])
+                    out["fp64_flux_balance_omega1.0"] = {
+                        "samples": 10, "max_rel_drift_per_step": drift,
+                        "totals_change_over_run_rel": ((t_last - t_first) / np.abs(t_first)).tolist(),
+                        "note": "|change of the FP64 totals over one step - (inflow - outflow)| / |totals| "
+                                "(lbrs_boundary_flux), max over fields and ten points of the 20000-step FP64 run"}
+                else:
+                    s.step(steps)
                 rho[precision] = s.moments(torch.float64)[0].clone()
                 if precision == "f64":
                     out_diag = s.diagnostics()

@@ -282,6 +282,22 @@ lbrs_status lbrs_moments(lbrs_ctx* ctx, void* U_out, int on_device, int dtype);
  * violates the sub-characteristic bound, else OK; *out is filled in every case. */
 lbrs_status lbrs_diagnostics(lbrs_ctx* ctx, lbrs_diag* out);
 
+/* Boundary balance of the next step (D2Q4, F64 or F32 distributions; Section II.D's
+ * streaming with the side conditions of Section II.E and the readings for the other
+ * sides): FP64 sums, per conserved field and times the cell volume dx^2, of the
+ * populations the next step brings into the domain -- those of side cells whose pull
+ * source x - c_q lies beyond a non-periodic side, with the values the step gives them
+ * (a Dirichlet ghost, the clamped cell's population, a wall relation) -- (inflow) and
+ * of the current post-collision populations it takes out -- those of side cells whose
+ * destination x + c_q lies beyond a non-periodic side -- (outflow).  Every other
+ * population stays inside and the collision keeps the moments, so after one lbrs_step
+ * the totals of lbrs_diagnostics equal the current totals plus inflow minus outflow,
+ * up to rounding.  Bitwise reproducible (one block, fixed order).  Synchronises the
+ * stream.  inflow, outflow: host arrays of 4 doubles.  LBRS_EINVAL for NULL arrays,
+ * another lattice or form (F16NEQ, F32U), internal walls or cut sides; LBRS_ESTATE
+ * without a state or after adaptive steps. */
+lbrs_status lbrs_boundary_flux(lbrs_ctx* ctx, double inflow[4], double outflow[4]);
+
 /* The same diagnostics for callers that cannot allocate device memory: no
  * context, no workspace, and no cudaMalloc/cudaFree or allocating library call.
  * The paper has no counterpart; it exists because some callers cannot provide

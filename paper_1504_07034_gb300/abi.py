@@ -99,6 +99,7 @@ SIGNATURES = {
     "lbrs_first_bad_step": (ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_int64)]),
     "lbrs_moments": (ctypes.c_int, [_CTX, _P, ctypes.c_int, ctypes.c_int]),
     "lbrs_diagnostics": (ctypes.c_int, [_CTX, ctypes.POINTER(lbrs_diag)]),
+    "lbrs_boundary_flux": (ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "lbrs_diagnostics_noalloc": (ctypes.c_int, [ctypes.POINTER(lbrs_config), _P, ctypes.POINTER(lbrs_diag)]),
     "lbrs_get_distributions": (ctypes.c_int, [_CTX, _P, ctypes.c_int]),
     "lbrs_set_distributions": (ctypes.c_int, [_CTX, _P, ctypes.c_int, ctypes.c_int64]),

@@ -481,6 +481,83 @@ static dim3 grid2d(int nx, int ny, dim3 block)
     return dim3((unsigned)((nx + block.x - 1) / block.x), (unsigned)((ny + block.y - 1) / block.y));
 }
 
+// ---------------------------------------------------------------- boundary balance (D2Q4)
+//
+// The populations that the next step moves across the domain's sides, summed in FP64 per field:
+// inflow, the populations of side cells whose pull source lies beyond a non-periodic side, with
+// the values the step gives them (pull_edge_2d: a Dirichlet ghost, the clamped cell's population,
+// a wall relation); outflow, the current post-collision populations of side cells whose
+// destination x + c_q lies beyond a non-periodic side.  Every other population stays inside, so
+// the totals of the next state are the current ones plus inflow minus outflow (the collision
+// keeps the moments).  One block visits each side cell once in a fixed order and reduces in a
+// fixed tree: the sums are bitwise reproducible.  out[0..3] inflow, out[4..7] outflow, times vol.
+constexpr int kFluxThreads = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kFluxThreads) boundary_flux2d_kernel(const StepArgs<T> a, double vol, double* out)
+{
+    __shared__ double red[8][kFluxThreads];
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const int nx = a.nx, ny = a.ny;
+    const int64_t rows = ny > 1 ? 2 : 1;                       // the bottom row, and the top one
+    const int64_t inner = ny > 2 ? ny - 2 : 0;                 // rows between them
+    const int64_t cols = nx > 1 ? 2 : 1;                       // their first and last cells
+    const int64_t P = rows * nx + cols * inner;
+    const bool px = a.bc[0] == BC_PERIODIC, py = a.bc[2] == BC_PERIODIC;
+    const int SX[4] = {-1, 1, 1, -1};
+    const int SY[4] = {-1, -1, 1, 1};
+    for (int64_t p = threadIdx.x; p < P; p += kFluxThreads) {
+        int i, j;
+        if (p < nx) {
+            i = (int)p;
+            j = 0;
+        } else if (p < rows * nx) {
+            i = (int)(p - nx);
+            j = ny - 1;
+        } else {
+            const int64_t r = p - rows * nx;
+            j = 1 + (int)(r % inner);
+            i = r / inner ? nx - 1 : 0;
+        }
+        T f[4][4];
+        pull_edge_2d<T>(a, i, j, f);
+        const int64_t c = (int64_t)j * nx + i;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int si = i - SX[q], sj = j - SY[q], di = i + SX[q], dj = j + SY[q];
+            const bool in = (!px && (si < 0 || si >= nx)) || (!py && (sj < 0 || sj >= ny));
+            const bool leaves = (!px && (di < 0 || di >= nx)) || (!py && (dj < 0 || dj >= ny));
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (in) acc[k] += (double)f[q][k];
+                if (leaves) acc[4 + k] += (double)a.src[LBRS_IX((q * 4 + k) * a.N + c, 16 * a.N, 50)];
+            }
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < 8; ++m) red[m][threadIdx.x] = acc[m];
+    __syncthreads();
+    for (int h = kFluxThreads / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h)
+#pragma unroll
+            for (int m = 0; m < 8; ++m) red[m][threadIdx.x] += red[m][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x < 8) out[threadIdx.x] = red[threadIdx.x][0] * vol;
+}
+
+cudaError_t launch_boundary_flux_f64(const StepArgs<double>& a, double vol, double* out, cudaStream_t s)
+{
+    boundary_flux2d_kernel<double><<<1, kFluxThreads, 0, s>>>(a, vol, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_boundary_flux_f32(const StepArgs<float>& a, double vol, double* out, cudaStream_t s)
+{
+    boundary_flux2d_kernel<float><<<1, kFluxThreads, 0, s>>>(a, vol, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_step_record_f64(const StepArgs<double>& a, cudaStream_t s)
 {
     const dim3 block(128, 2);

@@ -105,6 +105,9 @@ cudaError_t launch_status_update(const double* diag_out, double* status, int64_t
 
 // Recording step (D2Q4): the step above that also writes its moments to a.Uout.
 cudaError_t launch_step_record_f64(const StepArgs<double>& a, cudaStream_t s);
+// D2Q4 boundary balance of the next step: out[0..3] inflow, out[4..7] outflow (FP64, times vol).
+cudaError_t launch_boundary_flux_f64(const StepArgs<double>& a, double vol, double* out, cudaStream_t s);
+cudaError_t launch_boundary_flux_f32(const StepArgs<float>& a, double vol, double* out, cudaStream_t s);
 cudaError_t launch_step_record_f32(const StepArgs<float>& a, cudaStream_t s);
 
 // Adjoint of one periodic D2Q4 step, and the equilibrium VJP dL/dU0 (see lbrs_kernels.cuh).

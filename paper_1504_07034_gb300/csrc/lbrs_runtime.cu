@@ -957,6 +957,32 @@ lbrs_status lbrs_diagnostics(lbrs_ctx* ctx, lbrs_diag* out)
     return LBRS_OK;
 }
 
+lbrs_status lbrs_boundary_flux(lbrs_ctx* ctx, double inflow[4], double outflow[4])
+{
+    if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");
+    if (!inflow || !outflow) return fail(ctx, LBRS_EINVAL, "inflow or outflow is NULL");
+    if (ctx->lattice != LBRS_D2Q4 || ctx->f16 || ctx->f32u)
+        return fail(ctx, LBRS_EINVAL, "the boundary balance covers D2Q4 with stored distributions (F64, F32)");
+    if (ctx->solid) return fail(ctx, LBRS_EINVAL, "the boundary balance covers the domain's sides, not internal walls");
+    if (ctx->halo[0] || ctx->halo[1]) return fail(ctx, LBRS_EINVAL, "the boundary balance is not defined on a cut grid");
+    if (!ctx->has_state) return fail(ctx, LBRS_ESTATE, "no state set");
+    if (ctx->adapt_used)
+        return fail(ctx, LBRS_ESTATE, "the distributions carry an adaptive lambda: the ghosts of the next step are not built");
+    const double vol = ctx->cfg.dx * ctx->cfg.dx;
+    double* dout = (double*)(ctx->ws + ctx->L.diag_out);
+    LBRS_CUDA(ctx, ctx->f64 ? launch_boundary_flux_f64(step_args<double>(ctx, ctx->cur), vol, dout, ctx->stream)
+                            : launch_boundary_flux_f32(step_args<float>(ctx, ctx->cur), vol, dout, ctx->stream));
+    ctx->launches += 1;
+    double h[8];
+    LBRS_CUDA(ctx, cudaMemcpyAsync(h, dout, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+    LBRS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int k = 0; k < 4; ++k) {
+        inflow[k] = h[k];
+        outflow[k] = h[4 + k];
+    }
+    return LBRS_OK;
+}
+
 lbrs_status lbrs_get_distributions(lbrs_ctx* ctx, void* dst, int on_device)
 {
     if (!ctx) return fail(nullptr, LBRS_EINVAL, "ctx is NULL");

@@ -175,6 +175,14 @@ class Solver:
                 "min_rho": d.min_rho, "min_p": d.min_p, "max_lambda_local": d.max_lambda_local,
                 "n_nonphysical": d.n_nonphysical, "n_subchar": d.n_subchar}
 
+    def boundary_flux(self) -> dict:
+        """FP64 per-field sums (times dx^2) of what the next step brings in across the domain's
+        sides and takes out (lbrs_boundary_flux): totals after one step = totals + inflow - outflow."""
+        fin = (ctypes.c_double * 4)()
+        fout = (ctypes.c_double * 4)()
+        self._check(self.lib.lbrs_boundary_flux(self.ctx, fin, fout))
+        return {"inflow": [fin[k] for k in range(self.K)], "outflow": [fout[k] for k in range(self.K)]}
+
     def get_distributions(self, out: torch.Tensor | None = None) -> torch.Tensor:
         """The raw state.  For the reduced storage forms (f16neq: U and the FP16
         non-equilibrium parts; f32u: U) it fills only the leading bytes of the
