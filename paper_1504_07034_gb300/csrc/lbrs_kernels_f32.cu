@@ -1462,16 +1462,30 @@ __global__ void __launch_bounds__(256) adj_pull_u_kernel(const AdjArgs<float> a)
 }
 
 // Two steps kU^s -> kU^{s-2} on a 32 x 16 tile: phase 1 forms kU^{s-1} on the 34 x 18
-// window (4 fields per slot in shared memory), phase 2 kU^{s-2} for the tile.
+// window (4 fields per slot in shared memory), phase 2 kU^{s-2} for the tile.  A tile whose
+// window and the window's neighbours lie inside the grid gathers without wrapping (the same
+// cells, so the same values).
 __global__ void __launch_bounds__(kFTX * kFTY) adj_fused2_u_kernel(const AdjArgs<float> a, const float* __restrict__ U2)
 {
     __shared__ float s_w[4 * kTWN];
     const int i0 = blockIdx.x * kFTX, j0 = blockIdx.y * kTY;
+    const bool inside = i0 >= 2 && j0 >= 2 && i0 + kFTX + 2 <= a.nx && j0 + kTY + 2 <= a.ny;
     for (int w = threadIdx.x; w < kTWN; w += kFTX * kFTY) {
-        const int i = wrap_index(i0 - 1 + w % kFWX, a.nx), j = wrap_index(j0 - 1 + w / kFWX, a.ny);
         float g[4][4], U[4], ubar[4];
-        adj_gather_u(a.gin, a.N, a.nx, a.ny, i, j, g);
-        const int64_t c = (int64_t)j * a.nx + i;
+        int64_t c;
+        if (inside) {
+            c = (int64_t)(j0 - 1 + w / kFWX) * a.nx + (i0 - 1 + w % kFWX);
+            // x + c_q: q0 (i-1, j-1), q1 (i+1, j-1), q2 (i+1, j+1), q3 (i-1, j+1)
+            const int64_t s[4] = {c - a.nx - 1, c - a.nx + 1, c + a.nx + 1, c + a.nx - 1};
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) g[q][k] = a.gin[LBRS_IX(k * a.N + s[q], 4 * a.N, 37)];
+        } else {
+            const int i = wrap_index(i0 - 1 + w % kFWX, a.nx), j = wrap_index(j0 - 1 + w / kFWX, a.ny);
+            adj_gather_u(a.gin, a.N, a.nx, a.ny, i, j, g);
+            c = (int64_t)j * a.nx + i;
+        }
 #pragma unroll
         for (int k = 0; k < 4; ++k) U[k] = a.U[LBRS_IX(k * a.N + c, 4 * a.N, 37)];
         equilibrium_vjp2d<float>(U, g, a.gamma, a.gm1, a.c, ubar);
