@@ -89,6 +89,18 @@ MUTANTS = {
 }
 
 
+PIN_FILES = ("test_oracle_pins.py", "test_oracle_pins_d1q3.py", "test_oracle_adjoint.py", "test_oracle_obstacles.py",
+             "test_oracle_burgers.py", "test_oracle_adaptive.py", "test_oracle_halfway.py")
+FEATURE_FILES = {"d1q3": "test_oracle_pins_d1q3.py", "adjoint": "test_oracle_adjoint.py",
+                 "obstacle": "test_oracle_obstacles.py", "burgers": "test_oracle_burgers.py",
+                 "profile": "test_oracle_burgers.py", "adaptive": "test_oracle_adaptive.py",
+                 "halfway": "test_oracle_halfway.py", "d2q4_bound": "test_oracle_adaptive.py"}
+
+
+def _first_file(name):
+    return next((f for prefix, f in FEATURE_FILES.items() if name.startswith(prefix)), PIN_FILES[0])
+
+
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_pins_catch_mutant(name, tmp_path):
     old, new = MUTANTS[name]
@@ -100,13 +112,8 @@ def test_pins_catch_mutant(name, tmp_path):
     subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-shared", "-fPIC",
                     str(mutated), "-o", str(so), "-lm"], check=True)
     env = dict(os.environ, LBRS_ORACLE_LIB=str(so), OMP_NUM_THREADS="2")
-    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_pins_d1q3.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_adjoint.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_obstacles.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_burgers.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_adaptive.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_halfway.py")],
+    # the whole pin suite, the pins of the mutant's own feature first (-x stops at the first catch)
+    files = [os.path.join(ROOT, "tests", f) for f in sorted(PIN_FILES, key=lambda f: f != _first_file(name))]
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *files],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"pins did not catch mutant {name}:\n{r.stdout[-2000:]}"
