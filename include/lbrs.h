@@ -226,11 +226,12 @@ lbrs_status lbrs_set_state(lbrs_ctx* ctx, const void* W, int on_device, int dtyp
 
 /* Enqueue n >= 0 time steps (stream, boundary conditions, moments, fluxes,
  * equilibria, relaxation; discrete LBRS update, Sections II.A and II.D).
- * Asynchronous.  ESTATE if no state was set.  D2Q4 in LBRS_F32 advances pairs of
- * steps in one launch (two steps per read and write of the state; the result is
- * bit-identical to single steps); an odd remainder takes one single step.  Where
- * nx % 4 == 0 that kernel fetches its tiles by tensor copies with bounded waits
- * (see LBRS_ETIMEOUT). */
+ * Asynchronous.  ESTATE if no state was set.  D2Q4 in LBRS_F32 advances several
+ * steps per read and write of the state, bit-identical to single steps: where
+ * nx % 4 == 0 and the grid has no internal or halfway walls, three steps per launch
+ * (a group of four as 2 + 2), else two, an odd remainder one single step; the
+ * multi-step kernels fetch their tiles by tensor copies with bounded waits (see
+ * LBRS_ETIMEOUT).  LBRS_F32U advances pairs of steps in one launch. */
 lbrs_status lbrs_step(lbrs_ctx* ctx, int64_t n);
 
 /* Adaptive lattice speed (D2Q4, LBRS_F64 or LBRS_F32, no internal walls): the
@@ -257,7 +258,7 @@ lbrs_status lbrs_step_adaptive(lbrs_ctx* ctx, int64_t n, double safety, double t
 lbrs_status lbrs_adaptive_state(lbrs_ctx* ctx, double* t, double* lambda, int64_t* steps, int* done);
 
 /* Wait for the context's stream; reports a CUDA error raised by earlier work,
- * and LBRS_ETIMEOUT if a tile copy of the two-step kernel did not arrive within
+ * and LBRS_ETIMEOUT if a tile copy of a multi-step kernel did not arrive within
  * its bounded wait (the blocks concerned left their tiles unwritten; setting a
  * state clears the flag).
  * With cfg.diag_every > 0, lbrs_step runs the FP64 diagnostics reduction of
