@@ -102,7 +102,7 @@ import workloads as W
 from paper_1504_07034_gb300.solver import Solver
 out = []
 for (nx, ny), steps, seg in (((64, 48), 23, 5), ((66, 18), 20, 4), ((34, 10), 9, 9), ((130, 50), 12, 1),
-                             ((2, 2), 7, 3), ((40, 8), 30, 6)):
+                             ((2, 2), 7, 3), ((40, 8), 30, 6), ((256, 96), 11, 5), ((200, 80), 9, 9)):
     omega = float(sys.argv[3])
     wl, target = W.adjoint_pulses(seed=2, n=max(nx, ny), steps=0, width=0.1, pulses=3, omega=omega)
     prim = np.ascontiguousarray(wl.prim[:, :ny, :nx])
@@ -140,7 +140,8 @@ def test_f32_fused_sweep_equals_push_sweep(tmp_path):
 def test_f32_omega1_moments_sweep_equals_full_sweeps(tmp_path):
     """At omega = 1 the FP32 sweep keeps its state as the 4 fields J_E^T g (the same for every
     population): the gradient must equal the 16-value fused sweep's and the push sweep's bit for
-    bit, over the same segmentations and grids."""
+    bit, over the same segmentations and grids (those of three or more tiles a side have interior
+    tiles, which gather without wrapping)."""
     import os
     import subprocess
     import sys
