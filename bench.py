@@ -100,10 +100,21 @@ def dist_env():
 
 
 def kernel_source_sha() -> str:
+    """Hash of the code that defines the three-step kernel's launches: the shared device helpers, the FP32
+    kernel file up to the end of the three-step kernel (everything it uses is defined above it), and the
+    three-step launcher with its tensor map and prefetch distance.  Changes elsewhere (the adjoint kernels,
+    other launchers) leave the traffic record valid."""
+    csrc = os.path.join(ROOT, "paper_1504_07034_gb300", "csrc")
+    with open(os.path.join(csrc, "lbrs_kernels.cuh"), "rb") as fh:
+        cuh = fh.read()
+    with open(os.path.join(csrc, "lbrs_kernels_f32.cu"), "rb") as fh:
+        f32 = fh.read()
+    end = f32.index(b"// Failure-detection self-test")
+    a = f32.index(b"// The distance of the three-step kernel's L2 prefetch")
+    b = f32.index(b"cudaError_t launch_step2_f32(")
     h = hashlib.sha256()
-    for rel in ("paper_1504_07034_gb300/csrc/lbrs_kernels.cuh", "paper_1504_07034_gb300/csrc/lbrs_kernels_f32.cu"):
-        with open(os.path.join(ROOT, rel), "rb") as fh:
-            h.update(fh.read())
+    for part in (cuh, f32[:end], f32[a:b]):
+        h.update(part)
     return h.hexdigest()[:16]
 
 
