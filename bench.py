@@ -482,10 +482,12 @@ PROFILE_CASES = {f.__name__[len("prof_"):]: f for f in (
 # ------------------------------------------------------------------ GPU arm
 
 def sod_measurement(Solver, stream, barrier):
-    """Sod shock tube, D1Q2, 1000 cells, t = 0.2 (461 steps): wall time of the FP64 and FP32 runs and the
-    density L1 against the exact Riemann solution (a latency-bound case, not a roofline case)."""
+    """Sod shock tube, D1Q2, 1000 cells, t = 0.2 (461 steps): wall time of the FP64 and FP32 runs (the
+    single-tube path, one launch a step, and the batched path as a batch of one) and the density L1 against
+    the exact Riemann solution (a latency-bound case, not a roofline case)."""
     import torch
     from workloads import riemann
+    from paper_1504_07034_gb300.solver import BatchSolver
     wl = workloads.from_config("sod_d1q2_1000")[1]
     exact = riemann.sample(wl.gamma, wl.meta["left"], wl.meta["right"], (wl.x - 0.5) / wl.t_final)[0]
     out = {"workload": "Sod D1Q2, 1000 cells on [0, 1], t = 0.2, %d steps, lambda %.4f" % (wl.steps, wl.lam)}
@@ -505,6 +507,27 @@ def sod_measurement(Solver, stream, barrier):
         out[precision] = {"ms": a.elapsed_time(b), "mlups": wl.nx * wl.steps / (a.elapsed_time(b) / 1e3) / 1e6,
                           "l1_rho_vs_exact_riemann": float(np.mean(np.abs(rho - exact)))}
         s.close()
+        # the same tube through the batched path, a batch of one (up to `halo` steps per launch in shared
+        # memory, the single-tube arithmetic): the latency-bound run in a handful of launches
+        bs = BatchSolver([wl.nx], [wl.lam], gamma=wl.gamma, omega=wl.omega, boundary="transmissive",
+                         precision=precision, stream=stream)
+        with torch.cuda.stream(stream):
+            bs.set_state(torch.from_numpy(wl.prim).cuda())
+            bs.run([wl.steps])                    # warm-up (graph capture)
+            bs.set_state(torch.from_numpy(wl.prim).cuda())
+            l0 = bs.launch_count
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            barrier()
+            a.record(stream)
+            bs.run([wl.steps])
+            b.record(stream)
+            barrier()
+            rho_b = bs.moments(torch.float64)[0].cpu().numpy()
+            launches = bs.launch_count - l0
+        out[precision]["batched_path"] = {
+            "ms": a.elapsed_time(b), "mlups": wl.nx * wl.steps / (a.elapsed_time(b) / 1e3) / 1e6,
+            "kernel_launches": launches, "max_abs_diff_rho_vs_single_tube_path": float(np.max(np.abs(rho_b - rho)))}
+        bs.close()
     # the rest-particle model (D1Q3), which the paper reports removes the D1Q2 staircase
     wl3 = workloads.sod(1000, lattice="d1q3")
     s = Solver.from_workload(wl3, precision="f64", stream=stream, lattice="d1q3")
