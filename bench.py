@@ -484,8 +484,9 @@ PROFILE_CASES = {f.__name__[len("prof_"):]: f for f in (
 
 def sod_measurement(Solver, stream, barrier):
     """Sod shock tube, D1Q2, 1000 cells, t = 0.2 (461 steps): wall time of the FP64 and FP32 runs (the
-    single-tube path, one launch a step, and the batched path as a batch of one) and the density L1 against
-    the exact Riemann solution (a latency-bound case, not a roofline case)."""
+    single-tube context: FP32 in blocks of up to 32 steps a launch, FP64 one step a launch; and the batched
+    path as a batch of one) and the density L1 against the exact Riemann solution (a latency-bound case,
+    not a roofline case)."""
     import torch
     from workloads import riemann
     from paper_1504_07034_gb300.solver import BatchSolver

@@ -40,6 +40,10 @@ struct BatchArgs {
     const int* __restrict__ tube_len;
     const int* __restrict__ tube_steps;     // steps of each tube in this run
     const T* __restrict__ tube_c;           // 1/(2 lambda_b)
+    // one tube (tiles == nullptr): tile blockIdx.x covers cells [blockIdx.x * TILE, + TILE) of a
+    // tube of one_len cells at offset 0, stepped one_steps - launch * H times (at most H), c = one_c
+    int one_len, one_steps;
+    T one_c;
     int tile_cells;                         // TILE
     int halo;                               // H
     int periodic;                           // 1: periodic tubes, 0: transmissive ends
@@ -56,15 +60,17 @@ __global__ void __launch_bounds__(BLOCK) batch1d_kernel(const BatchArgs<T> a)
     constexpr int P = 3 * Q;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
-    const int4 tile = __ldg(reinterpret_cast<const int4*>(a.tiles) + blockIdx.x);   // {tube, t0, len, pad}
+    const bool one = a.tiles == nullptr;
+    const int4 tile = one ? make_int4(0, (int)blockIdx.x * a.tile_cells, 0, 0)
+                          : __ldg(reinterpret_cast<const int4*>(a.tiles) + blockIdx.x);   // {tube, t0, len, pad}
     const int b = tile.x;
     const int H = a.halo;
     const int W = a.tile_cells + 2 * H;
-    const int len = a.tube_len[b];
-    const int ns = min(H, a.tube_steps[b] - a.launch * H);   // >= 1 for an active tile
-    const int64_t off = a.tube_off[b];
-    const T c = a.tube_c[b];
-    const int t0 = tile.y, tlen = tile.z;
+    const int len = one ? a.one_len : a.tube_len[b];
+    const int ns = min(H, (one ? a.one_steps : a.tube_steps[b]) - a.launch * H);   // >= 1 for an active tile
+    const int64_t off = one ? 0 : a.tube_off[b];
+    const T c = one ? a.one_c : a.tube_c[b];
+    const int t0 = tile.y, tlen = one ? min(a.tile_cells, len - t0) : tile.z;
     const int x0 = t0 - H;                  // tube coordinate of window slot 0
     // slots whose tube coordinate is outside [0, len) exist only for periodic tubes
 

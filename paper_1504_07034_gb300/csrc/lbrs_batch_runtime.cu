@@ -210,7 +210,7 @@ void plan(const lbrs_batch* B, const int64_t* steps, const lbrs_batch_tuning& t,
 template <typename T>
 BatchArgs<T> batch_args(const lbrs_batch* B, int from, const lbrs_batch_tuning& t, int launch)
 {
-    BatchArgs<T> a;
+    BatchArgs<T> a{};
     a.src = (const T*)B->f[from];
     a.dst = (T*)B->f[from ^ 1];
     a.N = B->N;

@@ -17,6 +17,7 @@
 
 #include "lbrs.h"
 #include "lbrs_kernels.cuh"
+#include "lbrs_batch.cuh"
 #include "lbrs_launch.h"
 
 using namespace lbrs;
@@ -288,6 +289,52 @@ cudaError_t launch_one_step(lbrs_ctx* ctx, int from, cudaStream_t s)
     if (ctx->f16) return launch_step_f16neq(f16_args(ctx, from), s);
     if (ctx->f32u) return launch_step_f32u(f16_args(ctx, from), s);
     return launch_step_f32(lat, step_args<float>(ctx, from), s);
+}
+
+// FP32 1-D (D1Q2, D1Q3) with both ends transmissive or both periodic: steps taken by the batched
+// tubes' temporal-blocking kernel as a tube of one, up to kOneHalo steps per launch in shared memory
+// (tiles of 4 kOneBlock - 2 kOneHalo cells; the single-tube arithmetic, bit-identical to one step a
+// launch).  LBRS_1D_BLOCKED=0 keeps one step a launch.
+constexpr int kOneBlock = 256, kOneCellsPerThread = 4, kOneHalo = 32;
+constexpr int kOneTile = kOneBlock * kOneCellsPerThread - 2 * kOneHalo;
+
+bool blocked_1d(const lbrs_ctx* ctx)
+{
+    static const int enabled = [] {
+        const char* e = getenv("LBRS_1D_BLOCKED");
+        return (e && !strcmp(e, "0")) ? 0 : 1;
+    }();
+    if (!enabled || ctx->f64 || (ctx->lattice != LBRS_D1Q2 && ctx->lattice != LBRS_D1Q3)) return false;
+    const int k0 = ctx->cfg.bc[0].kind, k1 = ctx->cfg.bc[1].kind;
+    return k0 == k1 && (k0 == LBRS_BC_TRANSMISSIVE || k0 == LBRS_BC_PERIODIC);
+}
+
+size_t blocked_1d_smem(const lbrs_ctx* ctx) { return 2 * 3 * (size_t)ctx->Q * (kOneTile + 2 * kOneHalo) * sizeof(float); }
+
+// m <= kOneHalo steps of a blocked 1-D context from buffer `from` in one launch.
+cudaError_t launch_blocked_1d(const lbrs_ctx* ctx, int from, int m, cudaStream_t s)
+{
+    BatchArgs<float> a{};
+    a.src = (const float*)ctx->f[from];
+    a.dst = (float*)ctx->f[from ^ 1];
+    a.N = ctx->N;
+    a.tiles = nullptr;
+    a.tile_cells = kOneTile;
+    a.halo = kOneHalo;
+    a.periodic = ctx->cfg.bc[0].kind == LBRS_BC_PERIODIC;
+    a.launch = 0;
+    a.q = ctx->Q;
+    a.om = (float)ctx->cfg.omega;
+    a.om1 = (float)(1.0 - ctx->cfg.omega);
+    a.gm1 = (float)(ctx->cfg.gamma - 1.0);
+    a.one_len = (int)ctx->cfg.nx;
+    a.one_steps = m;
+    a.one_c = (float)ctx->c;
+    const int ntiles = (int)((ctx->cfg.nx + kOneTile - 1) / kOneTile);
+    // the kernel's shared-memory limit is shared with the batched tubes, which set it per tuning
+    const cudaError_t e = prepare_batch_f32(kOneBlock, blocked_1d_smem(ctx), ctx->Q);
+    if (e != cudaSuccess) return e;
+    return launch_batch_f32(a, ntiles, kOneBlock, s);
 }
 
 // The FP32 distribution form's two-steps-per-launch kernel available for this context?
@@ -836,6 +883,17 @@ lbrs_status lbrs_step(lbrs_ctx* ctx, int64_t n)
 
 static lbrs_status step_plain(lbrs_ctx* ctx, int64_t n)
 {
+    if (blocked_1d(ctx)) {
+        for (int64_t left = n; left > 0;) {
+            const int m = (int)(left < kOneHalo ? left : kOneHalo);
+            LBRS_CUDA(ctx, launch_blocked_1d(ctx, ctx->cur, m, ctx->stream));
+            ctx->cur ^= 1;
+            ctx->step += m;
+            ctx->launches += 1;
+            left -= m;
+        }
+        return LBRS_OK;
+    }
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     LBRS_CUDA(ctx, cudaStreamIsCapturing(ctx->stream, &cap));
     int64_t left = n;
