@@ -468,6 +468,18 @@ __device__ __forceinline__ void issue_tile_copy(const CUtensorMap* tmap, float* 
             : "memory");
 }
 
+// An L2 prefetch of the boxes issue_tile_copy copies for tile (i0, j0).
+__device__ __forceinline__ void prefetch_tile_l2(const CUtensorMap* tmap, int i0, int j0)
+{
+    const int x0[4] = {i0, i0 - 4, i0 - 4, i0};
+    const int y0[4] = {j0, j0, j0 - 2, j0 - 2};
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"((uint64_t)tmap),
+                     "r"(x0[q]), "r"(y0[q]), "r"(q * 4)
+                     : "memory");
+}
+
 // Position of population q, field k of window slot (wi, wj) in the boxes.
 __device__ __forceinline__ int tall_pos(int q, int k, int wi, int wj)
 {
@@ -787,12 +799,14 @@ __device__ __forceinline__ void tall_phase2_obst(const StepArgs<float>& a, const
 // shared memory; 41.2 KB with the obstacle mask window of OBST).  Forms measured
 // slower: 32 x 8 tiles with a separate window buffer (the same time on a flushed
 // 1024^2 grid, 10 % less throughput on large grids); blocks reused for further
-// tiles with the next copy issued early (fewer resident warps); L2 prefetch of
-// later tiles (evicts halo rows still to be read).
+// tiles with the next copy issued early (fewer resident warps).  Once its boxes have
+// landed, a block asks the L2 for the boxes of the block `ahead` places later in launch
+// order (half a wave; an earlier form that prefetched the following tile's boxes early
+// evicted halo rows still to be read).
 template <bool STORE_U, bool OBST = false, bool HALF = false>
 __global__ void __launch_bounds__(kFTX * kFTY, 5)
     step2d_f32_fused2_tall_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs<float> a,
-                                  unsigned* wait_flag)
+                                  unsigned* wait_flag, int ahead)
 {
     static_assert(!(STORE_U && OBST), "the recording form has no internal walls");
     extern __shared__ unsigned char smem_dyn[];
@@ -814,6 +828,11 @@ __global__ void __launch_bounds__(kFTX * kFTY, 5)
     if (!__syncthreads_and(arrived)) {
         give_up_tile(bar, wait_flag);
         return;
+    }
+    if (threadIdx.x == 0 && ahead > 0) {
+        const int64_t later = (int64_t)blockIdx.y * gridDim.x + blockIdx.x + ahead;
+        if (later < (int64_t)gridDim.x * gridDim.y)
+            prefetch_tile_l2(&tmap, (int)(later % gridDim.x) * kFTX, (int)(later / gridDim.x) * kTY);
     }
     const int ti = threadIdx.x % kFTX, tj = threadIdx.x / kFTX;
     if (OBST && obst) {
@@ -1606,6 +1625,28 @@ static EncodeTiledFn encode_tiled()
     return fn;
 }
 
+// The distance of the two-step kernel's L2 prefetch (the boxes of the block that many places later
+// in launch order, after a block's own boxes have landed): half its resident blocks on the current
+// device, as for the three-step kernel (measured +1.5 % on the flushed 1024^2 grid, +3.9 % with
+// internal walls on 6144 x 2048); LBRS_F32_PREFETCH2=n > 1 sets it, =0 turns it off; 0 if the
+// query fails.
+static int step2_prefetch_ahead()
+{
+    static int v = [] {
+        const char* e = getenv("LBRS_F32_PREFETCH2");
+        if (e && !strcmp(e, "0")) return 0;
+        if (e && atoi(e) > 1) return atoi(e);
+        int dev = 0, sms = 0, per = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step2d_f32_fused2_tall_kernel<false>, kFTX * kFTY,
+                                                          kTallSmemBytes) != cudaSuccess)
+            return 0;
+        return sms * per / 2;
+    }();
+    return v;
+}
+
 bool encode_f32_tile_map(TileMap* map, const float* f, int64_t nx, int64_t ny)
 {
     static_assert(sizeof(map->bytes) == sizeof(CUtensorMap), "TileMap holds one CUtensorMap");
@@ -1632,6 +1673,7 @@ bool encode_f32_tile_map(TileMap* map, const float* f, int64_t nx, int64_t ny)
                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTallSmemBytes);
     });
     if (attr_err != cudaSuccess) return false;
+    step2_prefetch_ahead();   // its device queries now, not first inside a graph capture
     const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, 16};
     const cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)(nx * ny) * 4};
     const cuuint32_t box[3] = {(cuuint32_t)kPX, (cuuint32_t)kTPY, 4};
@@ -1726,6 +1768,7 @@ cudaError_t launch_step3_f32(const StepArgs<float>& a, const TileMap* map3, unsi
 
 cudaError_t launch_step2_f32(const StepArgs<float>& a, const TileMap* map, unsigned* wait_flag, cudaStream_t s)
 {
+    const int ahead = step2_prefetch_ahead();
     const bool rec = a.Uout != nullptr;
     const bool half = a.bc[2] == BC_WALL_HALFWAY || a.bc[3] == BC_WALL_HALFWAY;   // the variants that resolve it
     if (map && map->valid && wait_flag) {
@@ -1734,13 +1777,13 @@ cudaError_t launch_step2_f32(const StepArgs<float>& a, const TileMap* map, unsig
         const dim3 grid((unsigned)((a.nx + kFTX - 1) / kFTX), (unsigned)((a.ny + kTY - 1) / kTY));
         if (a.solid) {
             if (rec || half) return cudaErrorInvalidValue;   // no recording form or halfway walls with obstacles
-            step2d_f32_fused2_tall_kernel<false, true><<<grid, kFTX * kFTY, kTallObstSmemBytes, s>>>(m, a, wait_flag);
+            step2d_f32_fused2_tall_kernel<false, true><<<grid, kFTX * kFTY, kTallObstSmemBytes, s>>>(m, a, wait_flag, ahead);
         } else if (rec) {
-            if (half) step2d_f32_fused2_tall_kernel<true, false, true><<<grid, kFTX * kFTY, kTallSmemBytes, s>>>(m, a, wait_flag);
-            else step2d_f32_fused2_tall_kernel<true><<<grid, kFTX * kFTY, kTallSmemBytes, s>>>(m, a, wait_flag);
+            if (half) step2d_f32_fused2_tall_kernel<true, false, true><<<grid, kFTX * kFTY, kTallSmemBytes, s>>>(m, a, wait_flag, ahead);
+            else step2d_f32_fused2_tall_kernel<true><<<grid, kFTX * kFTY, kTallSmemBytes, s>>>(m, a, wait_flag, ahead);
         } else {
-            if (half) step2d_f32_fused2_tall_kernel<false, false, true><<<grid, kFTX * kFTY, kTallSmemBytes, s>>>(m, a, wait_flag);
-            else step2d_f32_fused2_tall_kernel<false><<<grid, kFTX * kFTY, kTallSmemBytes, s>>>(m, a, wait_flag);
+            if (half) step2d_f32_fused2_tall_kernel<false, false, true><<<grid, kFTX * kFTY, kTallSmemBytes, s>>>(m, a, wait_flag, ahead);
+            else step2d_f32_fused2_tall_kernel<false><<<grid, kFTX * kFTY, kTallSmemBytes, s>>>(m, a, wait_flag, ahead);
         }
     } else if (a.solid) {
         return cudaErrorInvalidValue;                // internal walls need the tensor-copy form
