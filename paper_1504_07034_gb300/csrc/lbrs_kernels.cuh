@@ -649,11 +649,80 @@ __global__ void __launch_bounds__(256) adapt_init_bound_kernel(const T* __restri
     block_max_into<256>(bnd, &st->bound_bits[st->slot_cur]);
 }
 
+// Population q of the Dirichlet ghost of a scalar D2Q4 side: f^eq of the side's profile value at
+// coordinate m along the side.
+template <typename T>
+__device__ __forceinline__ T ghost_population_2ds(const StepArgs<T>& a, const T* g, int m, int q)
+{
+    T e[4];
+    equilibria2ds<T>(profile_value<T>(g, m), a.c, e);
+    T v = e[0];
+#pragma unroll
+    for (int r = 1; r < 4; ++r)
+        if (r == q) v = e[r];
+    return v;
+}
+
 // ---------------------------------------------------------------- scalar D2Q4 step
 //
 // One thread per cell: pull the four populations (periodic wrap, transmissive
 // clamp, Dirichlet ghost f^eq of the side's profile value; x side first), then the
 // moment u, the equilibria and the relaxation.
+
+// The pull of cell (i, j) where a source lies beyond a side.
+template <typename T>
+__device__ __forceinline__ void pull_edge_2ds(const StepArgs<T>& a, int i, int j, T f[4])
+{
+    const int SX[4] = {-1, 1, 1, -1};
+    const int SY[4] = {-1, -1, 1, 1};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        int si = i - SX[q], sj = j - SY[q];
+        const int side_y = sj < 0 ? 2 : (sj >= a.ny ? 3 : -1);
+        const int side_x = si < 0 ? 0 : (si >= a.nx ? 1 : -1);
+        const int kind_y = side_y == 2 ? a.bc[2] : a.bc[3];
+        const int kind_x = side_x == 0 ? a.bc[0] : a.bc[1];
+        const T* g = nullptr;
+        int m = 0;
+        if (side_x >= 0) {
+            if (kind_x == BC_DIRICHLET) {
+                g = a.ghost + side_x * GHOST_STRIDE;
+                m = sj;
+            } else if (kind_x == BC_PERIODIC) {
+                si = si < 0 ? si + a.nx : si - a.nx;
+            } else {
+                si = si < 0 ? 0 : a.nx - 1;
+            }
+        }
+        if (!g && side_y >= 0) {
+            if (kind_y == BC_DIRICHLET) {
+                g = a.ghost + side_y * GHOST_STRIDE;
+                m = si;
+            } else if (kind_y == BC_PERIODIC) {
+                sj = sj < 0 ? sj + a.ny : sj - a.ny;
+            } else {
+                sj = sj < 0 ? 0 : a.ny - 1;
+            }
+        }
+        if (g) {
+            f[q] = ghost_population_2ds<T>(a, g, m, q);
+        } else {
+            f[q] = a.src[LBRS_IX(q * a.N + (int64_t)sj * a.nx + si, 4 * a.N, 8)];
+        }
+    }
+}
+
+// The moment, the equilibria and the relaxation of one cell.
+template <typename T>
+__device__ __forceinline__ void collide_2ds(const StepArgs<T>& a, const T f[4], T out[4])
+{
+    const T u = ((f[0] + f[1]) + f[2]) + f[3];
+    T e[4];
+    equilibria2ds<T>(u, a.c, e);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) out[q] = a.om1 * f[q] + a.om * e[q];
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) step2ds_kernel(const StepArgs<T> a)
 {
@@ -661,60 +730,18 @@ __global__ void __launch_bounds__(256) step2ds_kernel(const StepArgs<T> a)
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= a.nx || j >= a.ny) return;
     const int64_t c = (int64_t)j * a.nx + i;
-    const int SX[4] = {-1, 1, 1, -1};
-    const int SY[4] = {-1, -1, 1, 1};
     T f[4];
     if (i > 0 && i < a.nx - 1 && j > 0 && j < a.ny - 1) {
         const int64_t s[4] = {c + a.nx + 1, c + a.nx - 1, c - a.nx - 1, c - a.nx + 1};
 #pragma unroll
         for (int q = 0; q < 4; ++q) f[q] = a.src[LBRS_IX(q * a.N + s[q], 4 * a.N, 8)];
     } else {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            int si = i - SX[q], sj = j - SY[q];
-            const int side_y = sj < 0 ? 2 : (sj >= a.ny ? 3 : -1);
-            const int side_x = si < 0 ? 0 : (si >= a.nx ? 1 : -1);
-            const int kind_y = side_y == 2 ? a.bc[2] : a.bc[3];
-            const int kind_x = side_x == 0 ? a.bc[0] : a.bc[1];
-            const T* g = nullptr;
-            int m = 0;
-            if (side_x >= 0) {
-                if (kind_x == BC_DIRICHLET) {
-                    g = a.ghost + side_x * GHOST_STRIDE;
-                    m = sj;
-                } else if (kind_x == BC_PERIODIC) {
-                    si = si < 0 ? si + a.nx : si - a.nx;
-                } else {
-                    si = si < 0 ? 0 : a.nx - 1;
-                }
-            }
-            if (!g && side_y >= 0) {
-                if (kind_y == BC_DIRICHLET) {
-                    g = a.ghost + side_y * GHOST_STRIDE;
-                    m = si;
-                } else if (kind_y == BC_PERIODIC) {
-                    sj = sj < 0 ? sj + a.ny : sj - a.ny;
-                } else {
-                    sj = sj < 0 ? 0 : a.ny - 1;
-                }
-            }
-            if (g) {
-                T e[4];
-                equilibria2ds<T>(profile_value<T>(g, m), a.c, e);
-                f[q] = e[0];
-#pragma unroll
-                for (int r = 1; r < 4; ++r)
-                    if (r == q) f[q] = e[r];
-            } else {
-                f[q] = a.src[LBRS_IX(q * a.N + (int64_t)sj * a.nx + si, 4 * a.N, 8)];
-            }
-        }
+        pull_edge_2ds<T>(a, i, j, f);
     }
-    const T u = ((f[0] + f[1]) + f[2]) + f[3];
-    T e[4];
-    equilibria2ds<T>(u, a.c, e);
+    T out[4];
+    collide_2ds<T>(a, f, out);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) a.dst[LBRS_IX(q * a.N + c, 4 * a.N, 8)] = a.om1 * f[q] + a.om * e[q];
+    for (int q = 0; q < 4; ++q) a.dst[LBRS_IX(q * a.N + c, 4 * a.N, 8)] = out[q];
 }
 
 // ---------------------------------------------------------------- D1Q2 step

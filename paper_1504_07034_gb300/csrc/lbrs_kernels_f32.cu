@@ -1174,6 +1174,123 @@ __global__ void __launch_bounds__(kT3T, kT3B)
     f3_tile<kT3T, STORE_U>(a, s, i0, j0);
 }
 
+// ---------------------------------------------------------------- scalar D2Q4, two steps per launch
+//
+// One block of 256 threads per 32 x 16 tile; the state (4 populations of one field) is read and written
+// once per two steps, 32 B per cell and launch.  Phase 1 computes step n+1 on the 34 x 18 window (the tile
+// and one cell of halo) into shared memory with the single-step kernel's pull and collision; slots beyond
+// a periodic side compute the wrapped cell, slots beyond another side are not needed.  Phase 2 computes
+// step n+2 for the tile, taking population q from where the single-step pull resolves its source: within
+// the grid or beyond a periodic side the source's (unwrapped) slot, beyond a transmissive side the clamped
+// cell's slot, beyond a Dirichlet side the ghost of the side's profile (x side first).  The ghosts do not
+// change between the steps, so the result is bit-identical to two single steps.
+__global__ void __launch_bounds__(kFTX * kFTY) step2ds_fused2_kernel(const StepArgs<float> a)
+{
+    __shared__ float s_f[4 * kTWN];
+    const int i0 = blockIdx.x * kFTX, j0 = blockIdx.y * kTY;
+    const bool px = a.bc[0] == BC_PERIODIC, py = a.bc[2] == BC_PERIODIC;
+    // the window and every source of its slots inside the grid: direct offsets in both phases
+    const bool inside = i0 >= 2 && j0 >= 2 && i0 + kFTX + 2 <= a.nx && j0 + kTY + 2 <= a.ny;
+    if (inside) {
+        for (int w = threadIdx.x; w < kTWN; w += kFTX * kFTY) {
+            const int64_t c = (int64_t)(j0 - 1 + w / kFWX) * a.nx + (i0 - 1 + w % kFWX);
+            const int64_t src[4] = {c + a.nx + 1, c + a.nx - 1, c - a.nx - 1, c - a.nx + 1};
+            float f[4], out[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) f[q] = a.src[LBRS_IX(q * a.N + src[q], 4 * a.N, 51)];
+            collide_2ds<float>(a, f, out);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) s_f[LBRS_IX(q * kTWN + w, 4 * kTWN, 52)] = out[q];
+        }
+        __syncthreads();
+        const int ti = threadIdx.x % kFTX;
+        for (int tj = threadIdx.x / kFTX; tj < kTY; tj += kFTY) {
+            // the source x - c_q of cell (ti, tj) is window slot (ti + 1 - sx_q, tj + 1 - sy_q)
+            const int s0 = (tj + 1) * kFWX + ti + 1;
+            const int sl[4] = {s0 + kFWX + 1, s0 + kFWX - 1, s0 - kFWX - 1, s0 - kFWX + 1};
+            float f[4], out[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) f[q] = s_f[LBRS_IX(q * kTWN + sl[q], 4 * kTWN, 53)];
+            collide_2ds<float>(a, f, out);
+            const int64_t c = (int64_t)(j0 + tj) * a.nx + i0 + ti;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) a.dst[LBRS_IX(q * a.N + c, 4 * a.N, 53)] = out[q];
+        }
+        return;
+    }
+    for (int w = threadIdx.x; w < kTWN; w += kFTX * kFTY) {
+        int i = i0 - 1 + w % kFWX, j = j0 - 1 + w / kFWX;
+        if (i < 0 || i >= a.nx) {
+            if (!px) continue;
+            i = wrap_index(i, a.nx);
+        }
+        if (j < 0 || j >= a.ny) {
+            if (!py) continue;
+            j = wrap_index(j, a.ny);
+        }
+        float f[4];
+        if (i > 0 && i < a.nx - 1 && j > 0 && j < a.ny - 1) {
+            const int64_t c = (int64_t)j * a.nx + i;
+            const int64_t src[4] = {c + a.nx + 1, c + a.nx - 1, c - a.nx - 1, c - a.nx + 1};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) f[q] = a.src[LBRS_IX(q * a.N + src[q], 4 * a.N, 51)];
+        } else {
+            pull_edge_2ds<float>(a, i, j, f);
+        }
+        float out[4];
+        collide_2ds<float>(a, f, out);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) s_f[LBRS_IX(q * kTWN + w, 4 * kTWN, 52)] = out[q];
+    }
+    __syncthreads();
+    const int SX[4] = {-1, 1, 1, -1};
+    const int SY[4] = {-1, -1, 1, 1};
+    const int ti = threadIdx.x % kFTX;
+    for (int tj = threadIdx.x / kFTX; tj < kTY; tj += kFTY) {
+        const int i = i0 + ti, j = j0 + tj;
+        if (i >= a.nx || j >= a.ny) continue;
+        float f[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int si = i - SX[q], sj = j - SY[q];     // the source, wrapped or clamped as the single step does
+            int ui = si, uj = sj;                   // its slot: unwrapped beyond a periodic side
+            const int side_y = sj < 0 ? 2 : (sj >= a.ny ? 3 : -1);
+            const int side_x = si < 0 ? 0 : (si >= a.nx ? 1 : -1);
+            const int kind_y = side_y == 2 ? a.bc[2] : a.bc[3];
+            const int kind_x = side_x == 0 ? a.bc[0] : a.bc[1];
+            const float* g = nullptr;
+            int m = 0;
+            if (side_x >= 0) {
+                if (kind_x == BC_DIRICHLET) {
+                    g = a.ghost + side_x * GHOST_STRIDE;
+                    m = sj;
+                } else if (kind_x == BC_PERIODIC) {
+                    si = si < 0 ? si + a.nx : si - a.nx;
+                } else {
+                    si = si < 0 ? 0 : a.nx - 1;
+                    ui = si;
+                }
+            }
+            if (!g && side_y >= 0) {
+                if (kind_y == BC_DIRICHLET) {
+                    g = a.ghost + side_y * GHOST_STRIDE;
+                    m = si;
+                } else if (kind_y != BC_PERIODIC) {
+                    sj = sj < 0 ? 0 : a.ny - 1;
+                    uj = sj;
+                }
+            }
+            f[q] = g ? ghost_population_2ds<float>(a, g, m, q)
+                     : s_f[LBRS_IX(q * kTWN + (uj - (j0 - 1)) * kFWX + (ui - (i0 - 1)), 4 * kTWN, 53)];
+        }
+        float out[4];
+        collide_2ds<float>(a, f, out);
+        const int64_t c = (int64_t)j * a.nx + i;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) a.dst[LBRS_IX(q * a.N + c, 4 * a.N, 53)] = out[q];
+    }
+}
+
 // Failure-detection self-test: one block waits, with the tile kernels' bounded wait,
 // on an mbarrier that nothing completes (no copy, no arrival); the wait gives up after
 // `polls` polls and the block raises *wait_flag as the tile kernels do.  Nothing is in
@@ -1797,6 +1914,14 @@ cudaError_t launch_step2_f32(const StepArgs<float>& a, const TileMap* map, unsig
             else step2d_f32_fused2_kernel<false, false><<<grid, kFTX * kFTY, 0, s>>>(a);
         }
     }
+    return cudaGetLastError();
+}
+
+// Two scalar D2Q4 steps from a.src into a.dst (step2ds_fused2_kernel).
+cudaError_t launch_step2s_f32(const StepArgs<float>& a, cudaStream_t s)
+{
+    const dim3 grid((unsigned)((a.nx + kFTX - 1) / kFTX), (unsigned)((a.ny + kTY - 1) / kTY));
+    step2ds_fused2_kernel<<<grid, kFTX * kFTY, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -62,6 +62,8 @@ cudaError_t launch_step2_f32(const StepArgs<float>& a, const TileMap* map, unsig
 bool step3_f32_enabled();
 bool encode_f32_tile_map3(TileMap* map, const float* f, int64_t nx, int64_t ny);
 cudaError_t launch_step3_f32(const StepArgs<float>& a, const TileMap* map3, unsigned* wait_flag, cudaStream_t s);
+// Two scalar D2Q4 (2-D Burgers) steps per launch, FP32: a.src -> a.dst.
+cudaError_t launch_step2s_f32(const StepArgs<float>& a, cudaStream_t s);
 
 // Dirichlet ghost tables: ghost[side][q*K + k] = f^eq(U(prim[side])) for every
 // side whose kind is DIRICHLET, computed in FP64 and rounded to the storage type.

@@ -347,7 +347,20 @@ bool fused2_f32(const lbrs_ctx* ctx)
 
 // Does lbrs_step advance this context two steps per launch (FP32 distributions, or the
 // moments-only form)?
-bool fused2(const lbrs_ctx* ctx) { return fused2_f32(ctx) || (ctx->f32u && step2_f32u_enabled()); }
+// Scalar D2Q4 (2-D Burgers) in FP32: two steps per launch; LBRS_F32S_FUSE=0 keeps one.
+bool fused2_scalar(const lbrs_ctx* ctx)
+{
+    static const int enabled = [] {
+        const char* e = getenv("LBRS_F32S_FUSE");
+        return (e && !strcmp(e, "0")) ? 0 : 1;
+    }();
+    return enabled && !ctx->f64 && ctx->lattice == LBRS_D2Q4S;
+}
+
+bool fused2(const lbrs_ctx* ctx)
+{
+    return fused2_f32(ctx) || (ctx->f32u && step2_f32u_enabled()) || fused2_scalar(ctx);
+}
 
 unsigned* wait_flag(const lbrs_ctx* ctx) { return (unsigned*)(ctx->ws + ctx->L.wait_flag); }
 
@@ -383,6 +396,7 @@ cudaError_t launch_step3(const lbrs_ctx* ctx, int b, cudaStream_t s)
 cudaError_t launch_step2(const lbrs_ctx* ctx, int b, cudaStream_t s)
 {
     if (ctx->f32u) return launch_step2_f32u(f16_args(ctx, b), s);
+    if (fused2_scalar(ctx)) return launch_step2s_f32(step_args<float>(ctx, b), s);
     return launch_step2_f32(step_args<float>(ctx, b), &ctx->tmap[b], wait_flag(ctx), s);
 }
 

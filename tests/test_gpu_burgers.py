@@ -126,3 +126,45 @@ def test_scalar_lattice_rejections():
     with pytest.raises(abi.LbrsError):
         s.forward_checkpointed(4, 2)
     s.close()
+
+
+_FUSE_SCRIPT = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+sys.path.insert(0, sys.argv[1] + "/tests")
+from test_gpu_burgers import BC_SETS, scalar_case
+from paper_1504_07034_gb300.solver import Solver
+out = []
+for bcname in sorted(BC_SETS):
+    for shape in ((37, 29), (130, 18), (2, 3), (1, 1), (96, 40)):
+        for omega in (1.0, 1.3):
+            wl = scalar_case(*shape, BC_SETS[bcname], omega, 0, seed=5)
+            s = Solver.from_workload(wl, precision="f32")
+            s.set_state(torch.from_numpy(wl.prim).cuda())
+            for n in (1, 2, 7, 70):
+                s.step(n)
+                out.append(s.get_distributions().cpu().numpy().ravel())
+            s.close()
+np.save(sys.argv[2], np.concatenate(out))
+"""
+
+
+def test_f32_two_step_kernel_equals_single_steps(tmp_path):
+    """FP32 scalar D2Q4 advances two steps per launch (step2ds_fused2_kernel: the window's step n+1
+    in shared memory, then the tile's step n+2, with the single-step kernel's pull and collision);
+    the state must equal one step per launch (LBRS_F32S_FUSE=0) bit for bit on every side set,
+    ragged and one-cell grids, odd and even step counts and graph replay."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = tmp_path / "scalar_fuse.py"
+    script.write_text(_FUSE_SCRIPT)
+    res = {}
+    for name, env_add in (("fused", {}), ("single", {"LBRS_F32S_FUSE": "0"})):
+        out = tmp_path / f"{name}.npy"
+        subprocess.run([sys.executable, str(script), root, str(out)], check=True, env=dict(os.environ, **env_add),
+                       timeout=600)
+        res[name] = np.load(out)
+    assert np.all(np.isfinite(res["single"]))
+    assert np.array_equal(res["fused"], res["single"]), np.max(np.abs(res["fused"] - res["single"]))
