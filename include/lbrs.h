@@ -231,7 +231,8 @@ lbrs_status lbrs_set_state(lbrs_ctx* ctx, const void* W, int on_device, int dtyp
  * nx % 4 == 0 and the grid has no internal or halfway walls, three steps per launch
  * (a group of four as 2 + 2), else two, an odd remainder one single step; the
  * multi-step kernels fetch their tiles by tensor copies with bounded waits (see
- * LBRS_ETIMEOUT).  LBRS_F32U advances pairs of steps in one launch.  D1Q2 and D1Q3 in
+ * LBRS_ETIMEOUT).  LBRS_F32U and the scalar D2Q4S in LBRS_F32 advance pairs of steps in
+ * one launch.  D1Q2 and D1Q3 in
  * LBRS_F32 with both ends transmissive or both periodic advance up to 32 steps per
  * launch in shared memory (the batched tubes' kernel as a tube of one), bit-identical to
  * single steps. */
