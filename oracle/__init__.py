@@ -104,6 +104,8 @@ def lib():
         L.orc_run.argtypes = [P, dp, dp, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(_Check)]
         L.orc_run.restype = ctypes.c_int
         L.orc_totals.argtypes = [P, dp, ctypes.c_double, dp]
+        L.orc_boundary_flux.argtypes = [P, dp, dp, ctypes.c_double, dp, dp]
+        L.orc_boundary_flux.restype = ctypes.c_int
         L.orc_max_threads.restype = ctypes.c_int
         L.orc_adjoint_step.argtypes = [P, dp, dp, dp]
         L.orc_adjoint_step.restype = ctypes.c_int
@@ -273,6 +275,17 @@ class Oracle:
         out = np.empty(self.K)
         lib().orc_totals(ctypes.byref(self.p), _ptr(fs), float(cell_volume), _ptr(out))
         return out
+
+    def boundary_flux(self, fs, cell_volume: float):
+        """(inflow, outflow) per field of the next step across the domain's sides (orc_boundary_flux)."""
+        fs = self._dists(fs)
+        work = np.empty_like(fs)
+        fin, fout = np.empty(self.K), np.empty(self.K)
+        err = lib().orc_boundary_flux(ctypes.byref(self.p), _ptr(fs), _ptr(work), float(cell_volume), _ptr(fin),
+                                      _ptr(fout))
+        if err:
+            raise ValueError(f"oracle boundary flux error {err}")
+        return fin, fout
 
     # adjoint (periodic D2Q4 only) ----------------------------------------
     def adjoint_step(self, U_next, gbar):

@@ -687,6 +687,41 @@ void orc_totals(const orc_params* P, const double* fs, double cell_volume, doubl
     }
 }
 
+/* Boundary balance of the next step (D2Q4 and the scalar D2Q4, no internal walls): streaming
+ * (Section II.D) moves fs_q(y) to y + c_q.  A population whose destination lies beyond a non-periodic
+ * side leaves the domain (outflow); a cell whose pull source x - c_q lies beyond one receives what the
+ * side condition gives it, the streamed f_q(x) of orc_stream with the wall relations of Section II.E
+ * (inflow).  Per conserved field, both sums times cell_volume; `work` holds the streamed f
+ * ([Q][K][ny][nx], like fs).  Since the collision keeps the moments, the totals after one step are
+ * the totals before plus inflow minus outflow.  Returns 0, or the code of orc_stream, or 11 for
+ * another lattice or internal walls. */
+int orc_boundary_flux(const orc_params* P, const double* fs, double* work, double cell_volume, double* inflow,
+                      double* outflow)
+{
+    if (!two_d(P) || P->solid) return 11;
+    int err = orc_stream(P, fs, work);
+    if (err) return err;
+    const int64_t nx = P->nx, ny = P->ny, N = nx * ny;
+    const int Q = nq(P), K = nk(P);
+    const int px = P->bc_kind[0] == ORC_PERIODIC, py = P->bc_kind[2] == ORC_PERIODIC;
+    for (int k = 0; k < K; ++k) {
+        double in = 0.0, out = 0.0;
+        for (int q = 0; q < Q; ++q)
+            for (int64_t j = 0; j < ny; ++j)
+                for (int64_t i = 0; i < nx; ++i) {
+                    const int64_t c = j * nx + i;
+                    const int64_t si = i - SX2[q], sj = j - SY2[q], di = i + SX2[q], dj = j + SY2[q];
+                    if ((!px && (si < 0 || si >= nx)) || (!py && (sj < 0 || sj >= ny)))
+                        in += work[(q * K + k) * N + c];
+                    if ((!px && (di < 0 || di >= nx)) || (!py && (dj < 0 || dj >= ny)))
+                        out += fs[(q * K + k) * N + c];
+                }
+        inflow[k] = in * cell_volume;
+        outflow[k] = out * cell_volume;
+    }
+    return 0;
+}
+
 int orc_max_threads(void) { return omp_get_max_threads(); }
 
 /* ====================================================================== adjoint

@@ -113,3 +113,30 @@ def test_balance_rejects_forms_it_does_not_cover():
         s.boundary_flux()
     assert e.value.status == abi.LBRS_ESTATE
     s.close()
+
+
+@pytest.mark.parametrize("bcname", sorted(BC_SETS))
+@pytest.mark.parametrize("shape", [(64, 40), (37, 29)])
+def test_f64_balance_equals_the_oracles(bcname, shape):
+    """The FP64 library's inflow and outflow against the oracle's (orc_boundary_flux) after five steps of
+    the same state: the same populations summed in another order."""
+    import oracle
+    from paper_1504_07034_gb300.solver import Solver
+    nx, ny = shape
+    bc = BC_SETS[bcname]
+    if bc[0][0] == "periodic" and nx % 2:
+        nx += 1
+    if bc[2][0] == "periodic" and ny % 2:
+        ny += 1
+    wl = small_case(nx, ny, bcname, 1.3, steps=5)
+    o = oracle.Oracle.from_workload(wl)
+    fs, _ = o.run(o.init(o.prim_to_cons(wl.prim)), wl.steps)
+    fin_o, fout_o = o.boundary_flux(fs, wl.dx * wl.dx)
+    s = Solver.from_workload(wl, precision="f64")
+    s.set_state(torch.from_numpy(wl.prim).cuda())
+    s.step(wl.steps)
+    flux = s.boundary_flux()
+    s.close()
+    scale = np.max(np.abs(fin_o)) + np.max(np.abs(fout_o))
+    assert np.all(np.abs(np.array(flux["inflow"]) - fin_o) <= 1e-12 * scale), (flux["inflow"], fin_o)
+    assert np.all(np.abs(np.array(flux["outflow"]) - fout_o) <= 1e-12 * scale), (flux["outflow"], fout_o)

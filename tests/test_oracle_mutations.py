@@ -84,17 +84,25 @@ MUTANTS = {
     "halfway_wall_keeps_rho_v_sign": ("f[(q * K + k) * N + c] = sgn * (gm ? gm[m * K + k]",
                                       "f[(q * K + k) * N + c] = 1.0 * (gm ? gm[m * K + k]"),
     "halfway_wall_same_population": ("const int m = 3 - q;", "const int m = q ^ 1;"),
+    # boundary balance
+    "balance_outflow_tests_the_source": (
+        "if ((!px && (di < 0 || di >= nx)) || (!py && (dj < 0 || dj >= ny)))",
+        "if ((!px && (si < 0 || si >= nx)) || (!py && (sj < 0 || sj >= ny)))"),
+    "balance_inflow_misses_y_sides": (
+        "if ((!px && (si < 0 || si >= nx)) || (!py && (sj < 0 || sj >= ny)))\n                        in +=",
+        "if ((!px && (si < 0 || si >= nx)))\n                        in +="),
     "adjoint_relaxation_weights_swapped": ("gout[(q * 4 + k) * N + tj * nx + ti] = om1 * gq[q * 4 + k] + om * ubar[k];",
                                            "gout[(q * 4 + k) * N + tj * nx + ti] = om * gq[q * 4 + k] + om1 * ubar[k];"),
 }
 
 
 PIN_FILES = ("test_oracle_pins.py", "test_oracle_pins_d1q3.py", "test_oracle_adjoint.py", "test_oracle_obstacles.py",
-             "test_oracle_burgers.py", "test_oracle_adaptive.py", "test_oracle_halfway.py")
+             "test_oracle_burgers.py", "test_oracle_adaptive.py", "test_oracle_halfway.py", "test_oracle_balance.py")
 FEATURE_FILES = {"d1q3": "test_oracle_pins_d1q3.py", "adjoint": "test_oracle_adjoint.py",
                  "obstacle": "test_oracle_obstacles.py", "burgers": "test_oracle_burgers.py",
                  "profile": "test_oracle_burgers.py", "adaptive": "test_oracle_adaptive.py",
-                 "halfway": "test_oracle_halfway.py", "d2q4_bound": "test_oracle_adaptive.py"}
+                 "halfway": "test_oracle_halfway.py", "d2q4_bound": "test_oracle_adaptive.py",
+                 "balance": "test_oracle_balance.py"}
 
 
 def _first_file(name):
