@@ -430,6 +430,16 @@ def prof_burgers():
     return _prof_timed(lambda: [s.step(1) for _ in range(wl.steps)])
 
 
+def prof_burgers2():
+    """The same in calls of two steps (the two-steps-per-launch scalar kernel), 5 calls."""
+    import torch
+    from paper_1504_07034_gb300.solver import Solver
+    wl = workloads.burgers_2d(1, 4096, steps=10)
+    s = Solver.from_workload(wl, precision="f32")
+    s.set_state(torch.from_numpy(wl.prim).cuda())
+    return _prof_timed(lambda: [s.step(2) for _ in range(wl.steps // 2)])
+
+
 def prof_adaptive():
     """Adaptive lambda on the 1024 x 1024 quadrant problem in FP32, 10 single adaptive steps."""
     import torch
@@ -477,7 +487,7 @@ def prof_diagnostics():
 
 PROFILE_CASES = {f.__name__[len("prof_"):]: f for f in (
     prof_step2d_f32, prof_step2d_f32_flushed, prof_step2d_f32_flushed3, prof_step2d_f16neq, prof_step2d_f32u_flushed, prof_obstacles,
-    prof_burgers, prof_adaptive, prof_adjoint, prof_batch, prof_diagnostics)}
+    prof_burgers, prof_burgers2, prof_adaptive, prof_adjoint, prof_batch, prof_diagnostics)}
 
 
 # ------------------------------------------------------------------ GPU arm
