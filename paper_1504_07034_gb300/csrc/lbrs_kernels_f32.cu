@@ -1192,15 +1192,30 @@ __global__ void __launch_bounds__(kFTX * kFTY) step2ds_fused2_kernel(const StepA
     // the window and every source of its slots inside the grid: direct offsets in both phases
     const bool inside = i0 >= 2 && j0 >= 2 && i0 + kFTX + 2 <= a.nx && j0 + kTY + 2 <= a.ny;
     if (inside) {
-        for (int w = threadIdx.x; w < kTWN; w += kFTX * kFTY) {
-            const int64_t c = (int64_t)(j0 - 1 + w / kFWX) * a.nx + (i0 - 1 + w % kFWX);
-            const int64_t src[4] = {c + a.nx + 1, c + a.nx - 1, c - a.nx - 1, c - a.nx + 1};
-            float f[4], out[4];
+        // every load of the thread's window slots is issued before the first collision: the launch is
+        // bound by the latency of these loads, and three slots a thread keep three times as many in flight
+        constexpr int kThr = kFTX * kFTY, kPass = (kTWN + kThr - 1) / kThr;
+        static_assert((kPass - 1) * kThr <= kTWN, "every pass but the last is full");
+        float f[kPass][4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) f[q] = a.src[LBRS_IX(q * a.N + src[q], 4 * a.N, 51)];
-            collide_2ds<float>(a, f, out);
+        for (int p = 0; p < kPass; ++p) {
+            const int w = threadIdx.x + p * kThr;
+            if (p < kPass - 1 || w < kTWN) {
+                const int64_t c = (int64_t)(j0 - 1 + w / kFWX) * a.nx + (i0 - 1 + w % kFWX);
+                const int64_t src[4] = {c + a.nx + 1, c + a.nx - 1, c - a.nx - 1, c - a.nx + 1};
 #pragma unroll
-            for (int q = 0; q < 4; ++q) s_f[LBRS_IX(q * kTWN + w, 4 * kTWN, 52)] = out[q];
+                for (int q = 0; q < 4; ++q) f[p][q] = a.src[LBRS_IX(q * a.N + src[q], 4 * a.N, 51)];
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < kPass; ++p) {
+            const int w = threadIdx.x + p * kThr;
+            if (p < kPass - 1 || w < kTWN) {
+                float out[4];
+                collide_2ds<float>(a, f[p], out);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) s_f[LBRS_IX(q * kTWN + w, 4 * kTWN, 52)] = out[q];
+            }
         }
         __syncthreads();
         const int ti = threadIdx.x % kFTX;
