@@ -1176,21 +1176,23 @@ __global__ void __launch_bounds__(kT3T, kT3B)
 
 // ---------------------------------------------------------------- scalar D2Q4, two steps per launch
 //
-// One block of 256 threads per 32 x 16 tile; the state (4 populations of one field) is read and written
-// once per two steps, 32 B per cell and launch.  Phase 1 computes step n+1 on the 34 x 18 window (the tile
-// and one cell of halo) into shared memory with the single-step kernel's pull and collision; slots beyond
+// One block of 256 threads per 32 x TY tile (TY = 16, 24 or 32 rows); the state (4 populations of one
+// field) is read and written once per two steps, 32 B per cell and launch.  Phase 1 computes step n+1 on
+// the 34 x (TY + 2) window (the tile and one cell of halo) into shared memory with the single-step kernel's pull and collision; slots beyond
 // a periodic side compute the wrapped cell, slots beyond another side are not needed.  Phase 2 computes
 // step n+2 for the tile, taking population q from where the single-step pull resolves its source: within
 // the grid or beyond a periodic side the source's (unwrapped) slot, beyond a transmissive side the clamped
 // cell's slot, beyond a Dirichlet side the ghost of the side's profile (x side first).  The ghosts do not
 // change between the steps, so the result is bit-identical to two single steps.
+template <int TY>
 __global__ void __launch_bounds__(kFTX * kFTY) step2ds_fused2_kernel(const StepArgs<float> a)
 {
+    constexpr int kTWN = kFWX * (TY + 2);   // window slots: the tile and one cell of halo
     __shared__ float s_f[4 * kTWN];
-    const int i0 = blockIdx.x * kFTX, j0 = blockIdx.y * kTY;
+    const int i0 = blockIdx.x * kFTX, j0 = blockIdx.y * TY;
     const bool px = a.bc[0] == BC_PERIODIC, py = a.bc[2] == BC_PERIODIC;
     // the window and every source of its slots inside the grid: direct offsets in both phases
-    const bool inside = i0 >= 2 && j0 >= 2 && i0 + kFTX + 2 <= a.nx && j0 + kTY + 2 <= a.ny;
+    const bool inside = i0 >= 2 && j0 >= 2 && i0 + kFTX + 2 <= a.nx && j0 + TY + 2 <= a.ny;
     if (inside) {
         // every load of the thread's window slots is issued before the first collision: the launch is
         // bound by the latency of these loads, and three slots a thread keep three times as many in flight
@@ -1219,7 +1221,7 @@ __global__ void __launch_bounds__(kFTX * kFTY) step2ds_fused2_kernel(const StepA
         }
         __syncthreads();
         const int ti = threadIdx.x % kFTX;
-        for (int tj = threadIdx.x / kFTX; tj < kTY; tj += kFTY) {
+        for (int tj = threadIdx.x / kFTX; tj < TY; tj += kFTY) {
             // the source x - c_q of cell (ti, tj) is window slot (ti + 1 - sx_q, tj + 1 - sy_q)
             const int s0 = (tj + 1) * kFWX + ti + 1;
             const int sl[4] = {s0 + kFWX + 1, s0 + kFWX - 1, s0 - kFWX - 1, s0 - kFWX + 1};
@@ -1261,7 +1263,7 @@ __global__ void __launch_bounds__(kFTX * kFTY) step2ds_fused2_kernel(const StepA
     const int SX[4] = {-1, 1, 1, -1};
     const int SY[4] = {-1, -1, 1, 1};
     const int ti = threadIdx.x % kFTX;
-    for (int tj = threadIdx.x / kFTX; tj < kTY; tj += kFTY) {
+    for (int tj = threadIdx.x / kFTX; tj < TY; tj += kFTY) {
         const int i = i0 + ti, j = j0 + tj;
         if (i >= a.nx || j >= a.ny) continue;
         float f[4];
@@ -1612,15 +1614,18 @@ __global__ void __launch_bounds__(256) adj_pull_u_kernel(const AdjArgs<float> a)
     }
 }
 
-// Two steps kU^s -> kU^{s-2} on a 32 x 16 tile: phase 1 forms kU^{s-1} on the 34 x 18
-// window (4 fields per slot in shared memory), phase 2 kU^{s-2} for the tile.  A tile whose
+// Two steps kU^s -> kU^{s-2} on a 32 x TY tile (TY = 16, 24 or 32 rows): phase 1 forms kU^{s-1} on
+// the 34 x (TY + 2) window (4 fields per slot in shared memory), phase 2 kU^{s-2} for the tile.  A tile whose
 // window and the window's neighbours lie inside the grid gathers without wrapping (the same
-// cells, so the same values).
-__global__ void __launch_bounds__(kFTX * kFTY) adj_fused2_u_kernel(const AdjArgs<float> a, const float* __restrict__ U2)
+// cells, so the same values).  Six blocks per SM (40 registers, no spills): the sweep waits on its
+// gathers, and a sixth block hides more of that latency than the registers of a fifth buy.
+template <int TY>
+__global__ void __launch_bounds__(kFTX * kFTY, 6) adj_fused2_u_kernel(const AdjArgs<float> a, const float* __restrict__ U2)
 {
+    constexpr int kTWN = kFWX * (TY + 2);   // window slots: the tile and one cell of halo
     __shared__ float s_w[4 * kTWN];
-    const int i0 = blockIdx.x * kFTX, j0 = blockIdx.y * kTY;
-    const bool inside = i0 >= 2 && j0 >= 2 && i0 + kFTX + 2 <= a.nx && j0 + kTY + 2 <= a.ny;
+    const int i0 = blockIdx.x * kFTX, j0 = blockIdx.y * TY;
+    const bool inside = i0 >= 2 && j0 >= 2 && i0 + kFTX + 2 <= a.nx && j0 + TY + 2 <= a.ny;
     for (int w = threadIdx.x; w < kTWN; w += kFTX * kFTY) {
         float g[4][4], U[4], ubar[4];
         int64_t c;
@@ -1645,7 +1650,7 @@ __global__ void __launch_bounds__(kFTX * kFTY) adj_fused2_u_kernel(const AdjArgs
     }
     __syncthreads();
     const int ti = threadIdx.x % kFTX;
-    for (int tj = threadIdx.x / kFTX; tj < kTY; tj += kFTY) {
+    for (int tj = threadIdx.x / kFTX; tj < TY; tj += kFTY) {
         const int i = i0 + ti, j = j0 + tj;
         if (i >= a.nx || j >= a.ny) continue;
         // the source of population q, x + c_q, is window slot (ti + 1 + sx_q, tj + 1 + sy_q)
@@ -1933,11 +1938,34 @@ cudaError_t launch_step2_f32(const StepArgs<float>& a, const TileMap* map, unsig
 }
 
 // Two scalar D2Q4 steps from a.src into a.dst (step2ds_fused2_kernel).
+// Rows of a tile for the kernels with a tile-height parameter: a value of `allowed` (zero-terminated)
+// from the environment variable `name` (a tuning override), else `dflt`.
+static int tile_rows(const char* name, int dflt, const int* allowed)
+{
+    const char* e = getenv(name);
+    const int v = e ? atoi(e) : 0;
+    for (; *allowed; ++allowed)
+        if (v == *allowed) return v;
+    return dflt;
+}
+
+template <int TY, typename Kernel, typename... Args>
+static cudaError_t launch_tiled(Kernel k, int nx, int ny, cudaStream_t s, Args... args)
+{
+    const dim3 grid((unsigned)((nx + kFTX - 1) / kFTX), (unsigned)((ny + TY - 1) / TY));
+    k<<<grid, kFTX * kFTY, 0, s>>>(args...);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_step2s_f32(const StepArgs<float>& a, cudaStream_t s)
 {
-    const dim3 grid((unsigned)((a.nx + kFTX - 1) / kFTX), (unsigned)((a.ny + kTY - 1) / kTY));
-    step2ds_fused2_kernel<<<grid, kFTX * kFTY, 0, s>>>(a);
-    return cudaGetLastError();
+    // 32 rows measured fastest (8192^2 steady: 16 rows 339 k, 24 rows 399 k, 32 rows 406-408 k, 48 rows
+    // 361 k, 64 rows 351 k MLUPS)
+    static const int allowed[] = {16, 24, 32, 0};
+    static const int ty = tile_rows("LBRS_F32S_TILE_Y", 32, allowed);
+    if (ty == 24) return launch_tiled<24>(step2ds_fused2_kernel<24>, a.nx, a.ny, s, a);
+    if (ty == 16) return launch_tiled<16>(step2ds_fused2_kernel<16>, a.nx, a.ny, s, a);
+    return launch_tiled<32>(step2ds_fused2_kernel<32>, a.nx, a.ny, s, a);
 }
 
 // rcp_f32 over n inputs, for its error-bound test.
@@ -2056,9 +2084,12 @@ cudaError_t launch_adj_pull_u_f32(const AdjArgs<float>& a, cudaStream_t s)
 
 cudaError_t launch_adj_fused2_u_f32(const AdjArgs<float>& a, const float* U2, cudaStream_t s)
 {
-    const dim3 grid((unsigned)((a.nx + kFTX - 1) / kFTX), (unsigned)((a.ny + kTY - 1) / kTY));
-    adj_fused2_u_kernel<<<grid, kFTX * kFTY, 0, s>>>(a, U2);
-    return cudaGetLastError();
+    // 24 rows measured fastest (2048^2 x 2000 steps: sweep 77.5 ms at 16 rows, 74.6 ms at 24, 76.0 ms at 32)
+    static const int allowed[] = {16, 24, 32, 0};
+    static const int ty = tile_rows("LBRS_ADJU_TILE_Y", 24, allowed);
+    if (ty == 32) return launch_tiled<32>(adj_fused2_u_kernel<32>, a.nx, a.ny, s, a, U2);
+    if (ty == 16) return launch_tiled<16>(adj_fused2_u_kernel<16>, a.nx, a.ny, s, a, U2);
+    return launch_tiled<24>(adj_fused2_u_kernel<24>, a.nx, a.ny, s, a, U2);
 }
 
 cudaError_t launch_vjp_equilibrium_f32(const AdjArgs<float>& a, cudaStream_t s)
