@@ -101,15 +101,15 @@ def dist_env():
 
 def kernel_source_sha() -> str:
     """Hash of the code that defines the three-step kernel's launches: the shared device helpers, the FP32
-    kernel file up to the end of the three-step kernel (everything it uses is defined above it), and the
-    three-step launcher with its tensor map and prefetch distance.  Changes elsewhere (the adjoint kernels,
-    other launchers) leave the traffic record valid."""
+    kernel file up to the end of the three-step kernel (everything it uses is defined above it; the scalar
+    lattice's section follows it), and the three-step launcher with its tensor map and prefetch distance.
+    Changes elsewhere (the scalar and adjoint kernels, other launchers) leave the traffic record valid."""
     csrc = os.path.join(ROOT, "paper_1504_07034_gb300", "csrc")
     with open(os.path.join(csrc, "lbrs_kernels.cuh"), "rb") as fh:
         cuh = fh.read()
     with open(os.path.join(csrc, "lbrs_kernels_f32.cu"), "rb") as fh:
         f32 = fh.read()
-    end = f32.find(b"// Failure-detection self-test")
+    end = f32.find(b"// ---------------------------------------------------------------- scalar D2Q4, two steps per launch")
     a = f32.find(b"// The distance of the three-step kernel's L2 prefetch")
     b = f32.find(b"cudaError_t launch_step2_f32(")
     parts = (cuh, f32[:end], f32[a:b]) if min(end, a, b) >= 0 and a < b else (cuh, f32)   # markers moved: all
