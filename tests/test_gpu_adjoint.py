@@ -141,7 +141,8 @@ def test_f32_omega1_moments_sweep_equals_full_sweeps(tmp_path):
     """At omega = 1 the FP32 sweep keeps its state as the 4 fields J_E^T g (the same for every
     population): the gradient must equal the 16-value fused sweep's and the push sweep's bit for
     bit, over the same segmentations and grids (those of three or more tiles a side have interior
-    tiles, which gather without wrapping)."""
+    tiles, which gather without wrapping), at every tile height of its two-step kernel (24 rows by
+    default, 16 and 32 through LBRS_ADJU_TILE_Y)."""
     import os
     import subprocess
     import sys
@@ -149,13 +150,15 @@ def test_f32_omega1_moments_sweep_equals_full_sweeps(tmp_path):
     script = tmp_path / "sweep.py"
     script.write_text(_SWEEP_SCRIPT)
     res = {}
-    for name, env_add in (("uform", {}), ("full", {"LBRS_ADJ_UFORM": "0"}), ("push", {"LBRS_F32_FUSE": "0"})):
+    runs = (("uform", {}), ("uform16", {"LBRS_ADJU_TILE_Y": "16"}), ("uform32", {"LBRS_ADJU_TILE_Y": "32"}),
+            ("full", {"LBRS_ADJ_UFORM": "0"}), ("push", {"LBRS_F32_FUSE": "0"}))
+    for name, env_add in runs:
         out = tmp_path / f"{name}.npy"
         env = dict(os.environ, **env_add)
         subprocess.run([sys.executable, str(script), root, str(out), "1.0"], check=True, env=env, timeout=300)
         res[name] = np.load(out)
     assert np.all(np.isfinite(res["push"]))
-    for name in ("uform", "full"):
+    for name in ("uform", "uform16", "uform32", "full"):
         assert np.array_equal(res[name], res["push"]), (name, np.max(np.abs(res[name] - res["push"])))
 
 

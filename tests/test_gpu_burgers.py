@@ -136,7 +136,7 @@ from test_gpu_burgers import BC_SETS, scalar_case
 from paper_1504_07034_gb300.solver import Solver
 out = []
 for bcname in sorted(BC_SETS):
-    for shape in ((37, 29), (130, 18), (2, 3), (1, 1), (96, 40)):
+    for shape in ((37, 29), (130, 18), (2, 3), (1, 1), (96, 40), (100, 80)):
         for omega in (1.0, 1.3):
             wl = scalar_case(*shape, BC_SETS[bcname], omega, 0, seed=5)
             s = Solver.from_workload(wl, precision="f32")
@@ -153,7 +153,9 @@ def test_f32_two_step_kernel_equals_single_steps(tmp_path):
     """FP32 scalar D2Q4 advances two steps per launch (step2ds_fused2_kernel: the window's step n+1
     in shared memory, then the tile's step n+2, with the single-step kernel's pull and collision);
     the state must equal one step per launch (LBRS_F32S_FUSE=0) bit for bit on every side set,
-    ragged and one-cell grids, odd and even step counts and graph replay."""
+    ragged and one-cell grids, odd and even step counts and graph replay, at every tile height the
+    kernel takes (32 rows by default, 16 and 24 through LBRS_F32S_TILE_Y).  Interior tiles, which load
+    on direct offsets, occur on the 96 x 40 grid at 16 rows and on the 100 x 80 grid at every height."""
     import os
     import subprocess
     import sys
@@ -161,10 +163,13 @@ def test_f32_two_step_kernel_equals_single_steps(tmp_path):
     script = tmp_path / "scalar_fuse.py"
     script.write_text(_FUSE_SCRIPT)
     res = {}
-    for name, env_add in (("fused", {}), ("single", {"LBRS_F32S_FUSE": "0"})):
+    runs = (("fused", {}), ("fused16", {"LBRS_F32S_TILE_Y": "16"}), ("fused24", {"LBRS_F32S_TILE_Y": "24"}),
+            ("single", {"LBRS_F32S_FUSE": "0"}))
+    for name, env_add in runs:
         out = tmp_path / f"{name}.npy"
         subprocess.run([sys.executable, str(script), root, str(out)], check=True, env=dict(os.environ, **env_add),
                        timeout=600)
         res[name] = np.load(out)
     assert np.all(np.isfinite(res["single"]))
-    assert np.array_equal(res["fused"], res["single"]), np.max(np.abs(res["fused"] - res["single"]))
+    for name in ("fused", "fused16", "fused24"):
+        assert np.array_equal(res[name], res["single"]), (name, np.max(np.abs(res[name] - res["single"])))
