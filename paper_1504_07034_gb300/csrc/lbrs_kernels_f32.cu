@@ -1194,8 +1194,9 @@ __global__ void __launch_bounds__(kFTX * kFTY) step2ds_fused2_kernel(const StepA
     // the window and every source of its slots inside the grid: direct offsets in both phases
     const bool inside = i0 >= 2 && j0 >= 2 && i0 + kFTX + 2 <= a.nx && j0 + TY + 2 <= a.ny;
     if (inside) {
-        // every load of the thread's window slots is issued before the first collision: the launch is
-        // bound by the latency of these loads, and three slots a thread keep three times as many in flight
+        // every load of the thread's window slots (kPass of them: three at 16 rows, five at 32) is issued
+        // before the first collision: the phase is bound by the latency of these loads, and kPass slots a
+        // thread keep kPass times as many in flight as one slot at a time
         constexpr int kThr = kFTX * kFTY, kPass = (kTWN + kThr - 1) / kThr;
         static_assert((kPass - 1) * kThr <= kTWN, "every pass but the last is full");
         float f[kPass][4];
